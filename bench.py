@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Kernel K-means throughput on GB300: iterations/s of whole fits, plus K-build TFLOP/s.
+
+One step = one complete ``popcorn_fit`` through the C ABI on the rings workload
+(n = 20,000 points in the plane zero-padded to d = 8, k = 4, Gaussian kernel
+sigma = 0.5, random initial labels, passes until no label changes, at most
+100; K materialized in FP32 = 1.6 GB, larger than L2, so every pass streams it
+from HBM).  A step runs every row of the hot path: the K build (norms, Gram
+tiles, kernel epilogue), then per pass the K-streaming segmented reduction,
+the self-similarity sums, and the distance/argmin/histogram pass.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).  Under torchrun each rank runs an independent replica
+(the workload is one problem; there is no data-path collective) and the
+timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Kernel K-means iters/s + K-build TFLOP/s, FP32 vs BF16/batched at ≤1e-3 obj err"
+WORKLOAD = "rings"
+WORKLOAD_DESC = ("rings n=20000 d=8 (2 + 6 zero pad) k=4, Gaussian sigma=0.5, random init, "
+                 "passes to convergence (max 100), K materialized FP32 (1.6 GB)")
+FALLBACK_HBM_GBS = 6800.0
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink n (profiling captures only; the reported workload is scale 1)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured (MEASURED_PEAKS.json: STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, earlier GB300 copy measurement)"
+
+
+def recorded_traffic(kernel: str, src_file: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)[kernel]
+        with open(os.path.join(ROOT, "paper_2501_05587_gb300", "csrc", src_file), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if t.get("source_sha256") != sha:
+            return None
+        return float(t["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 100 ms during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            os.remove(self.path)
+        except Exception:
+            return None
+        sm, smax, reasons = [], 0.0, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], r[5:9]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample_rate(wl, n_sample: int, budget_s: float):
+    """The FP64 oracle as it stands, on the first n_sample points of the workload.
+
+    Returns (passes per second on the sample, sample description, passes, seconds).
+    """
+    import oracle
+
+    P = wl.P[:n_sample]
+    lab = wl.init_labels[:n_sample].copy()
+    t0 = time.perf_counter()
+    K = oracle.kernel_matrix(P, wl.kernel)
+    t_build = time.perf_counter() - t0
+    passes = 0
+    t1 = time.perf_counter()
+    while passes < wl.max_iter and time.perf_counter() - t1 < budget_s:
+        st = oracle.step(K, lab, wl.k)
+        passes += 1
+        lab = st["labels"]
+        if st["changed"] == 0:
+            break
+    t_loop = time.perf_counter() - t1
+    return passes, t_build, t_loop
+
+
+def oracle_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((int(i.get("num_threads", 1)) for i in threadpool_info()), default=1)
+        return n
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(wl, n_sample=16000, budget_s=25.0):
+    passes, t_build, t_loop = oracle_sample_rate(wl, n_sample, budget_s)
+    # per-pass and K-build work scale with n^2; convert to full-workload iters/s
+    scale = (n_sample / wl.n) ** 2
+    it_s = passes / t_loop * scale if t_loop > 0 else 0.0
+    return {"value": it_s, "unit": "iters/s", "cores": oracle_cores(), "kind": "oracle",
+            "sample": (f"first {n_sample} of {wl.n} points, {passes} FP64 passes in {t_loop:.2f} s "
+                       f"(K build {t_build:.2f} s); rate scaled by (n_sample/n)^2 = {scale:.4f} "
+                       f"to the full workload")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import synth
+
+    wl = synth.workload(WORKLOAD)
+    n_sample = 12000
+    for _ in range(args.warmup):
+        oracle_sample_rate(wl, 2000, 2.0)
+    t_all = 0.0
+    passes_all = 0
+    for _ in range(args.steps):
+        passes, t_build, t_loop = oracle_sample_rate(wl, n_sample, 15.0)
+        t_all += t_build + t_loop
+        passes_all += passes
+    scale = (n_sample / wl.n) ** 2
+    value = passes_all / t_all * scale
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "n": wl.n, "d": wl.d, "k": wl.k},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": oracle_cores(), "kind": "oracle",
+                             "sample": (f"each step: FP64 oracle K build + passes on the first {n_sample} "
+                                        f"points; whole-fit rate scaled by (n_sample/n)^2 = {scale:.4f}")},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    import synth
+    import paper_2501_05587_gb300 as pc
+
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    wl = synth.workload(WORKLOAD, scale=args.scale)
+    P = torch.from_numpy(wl.P).cuda()
+    lab = torch.from_numpy(wl.init_labels).cuda()
+    out = torch.empty_like(lab)
+
+    def step(timing=True):
+        return pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=True,
+                              timing=timing, labels_out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    results = []
+    with ClockSampler(local) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            results.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.summary()
+
+    iters = sum(r["iterations"] for r in results)
+    red_ms = sum(r["info"]["reduce_ms"] for r in results)
+    red_n = sum(r["info"]["reduce_launches"] for r in results)
+    asg_ms = sum(r["info"]["assign_ms"] for r in results)
+    kb_ms = sum(r["info"]["kbuild_ms"] for r in results)
+    launches = sum(r["info"]["kernel_launches"] for r in results)
+
+    # end to end through the same call with pinned host buffers (copies inside the timed region)
+    Ph = torch.from_numpy(wl.P).pin_memory()
+    Lh = torch.from_numpy(wl.init_labels).pin_memory()
+    Oh = torch.empty(wl.n, dtype=torch.int32).pin_memory()
+    for _ in range(args.warmup):
+        pc.popcorn_fit(Ph, wl.k, wl.kernel, Lh, max_iter=wl.max_iter, labels_out=Oh)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_res = [pc.popcorn_fit(Ph, wl.k, wl.kernel, Lh, max_iter=wl.max_iter, labels_out=Oh)
+               for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    barrier()
+
+    if dist is not None:
+        t = torch.tensor([ms, t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, t_e2e = float(t[0]), float(t[1])
+        c = torch.tensor([iters, sum(r["iterations"] for r in e2e_res), launches], dtype=torch.float64,
+                         device="cuda")
+        dist.all_reduce(c)
+        iters_all, e2e_iters_all, launches_all = float(c[0]), float(c[1]), int(c[2])
+    else:
+        iters_all, e2e_iters_all, launches_all = float(iters), float(sum(r["iterations"] for r in e2e_res)), launches
+
+    if rank == 0:
+        n, k = wl.n, wl.k
+        value = iters_all / (ms / 1e3)
+        kb_flops = float(n) * (n + 1) * wl.d           # algorithmic: n(n+1)/2 unique dot products, 2d flops each
+        alg_bytes = 4.0 * n * n + n                      # K read once + label bytes, per reduction launch
+        avg_red_ms = red_ms / max(red_n, 1)
+        peak, peak_src = peaks()
+        achieved = alg_bytes / (avg_red_ms / 1e3) / 1e9 if avg_red_ms > 0 else 0.0
+        traffic = recorded_traffic("reduce_kernel", "iterate.cu")
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "iters/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC if args.scale == 1.0 else f"{WORKLOAD} scaled x{args.scale}",
+                       "n": n, "d": wl.d, "k": k,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (K = 1.6 GB streamed every pass)",
+                       "passes_per_fit": iters / args.steps},
+            "kbuild_tflops": kb_flops / (kb_ms / args.steps / 1e3) / 1e12 if kb_ms > 0 else None,
+            "kbuild_ms": kb_ms / args.steps,
+            "loop_iters_per_s": iters / ((red_ms + asg_ms) / 1e3) if red_ms > 0 else None,
+            "breakdown_ms_per_step": {"kbuild": kb_ms / args.steps, "reduce": red_ms / args.steps,
+                                      "assign": asg_ms / args.steps},
+            "roofline": {"kernel": "reduce_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_red_ms},
+            "e2e": {"value": e2e_iters_all / t_e2e, "unit": "iters/s",
+                    "h2d_bytes_per_step": int(e2e_res[0]["info"]["h2d_bytes"]),
+                    "d2h_bytes_per_step": int(e2e_res[0]["info"]["d2h_bytes"])},
+            "gpu_launches": launches_all,
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

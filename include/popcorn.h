@@ -1,0 +1,213 @@
+/*
+ * popcorn.h -- C ABI of a GB300 (sm_103a) Kernel K-means engine.
+ *
+ * The method is the matrix formulation of Kernel K-means of "Popcorn:
+ * Accelerating Kernel K-means on GPUs through Sparse Linear Algebra"
+ * (arXiv 2501.05587):
+ *
+ *   K = kappa(P P^T)                     (Sec. 3.2, Alg. 2 line 1)
+ *   D = -2 K V^T + P~ + C~               (Eq. 11, Alg. 2 lines 7-10)
+ *   cl(i) = argmin_j D_ij                (Alg. 2 lines 11-13)
+ *
+ * where V (k x n) holds 1/|L_j| at (j, i) for every point i of cluster j
+ * (Eq. 8), P~ broadcasts diag(K) (Sec. 3.3) and C~ broadcasts the centroid
+ * norms ||c_j||^2 = diag(V K V^T) (Eq. 13), obtained from the entries
+ * (K V^T)_{i, cl(i)} (Eq. 14, "cnorms_gemv").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are row-major FP32.  P is n x d with leading dimension ldp >= d
+ *   (elements).  K is n x n with leading dimension ldk >= n.
+ * - Labels are 0-based int32 in [0, k).  (The paper draws labels in 1..k.)
+ * - "stream" is a cudaStream_t (a CUstream); NULL means the legacy default
+ *   stream.  Every call is stream-ordered on that stream.
+ * - Pointers documented as "device" must be device-accessible memory of the
+ *   current CUDA device.  Pointers documented as "host or device" are
+ *   classified with cudaPointerGetAttributes; host memory is copied in and out
+ *   by the library inside the call.
+ * - The caller owns every pointer it passes.  Calls allocate their temporary
+ *   workspace from a library-private, stream-ordered memory pool of the
+ *   current device (it keeps freed blocks for reuse) and release it before
+ *   returning.
+ * - Calls return a popcorn_status and never abort the process.  On an error
+ *   the outputs are unspecified, nothing is leaked, and
+ *   popcorn_last_error_message() describes the error of the calling thread.
+ * - k <= 256 (labels are kept as bytes on the device); n < 2^31.
+ */
+#ifndef POPCORN_H
+#define POPCORN_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define POPCORN_API __attribute__((visibility("default")))
+#else
+#define POPCORN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* popcorn_stream_t;  /* == cudaStream_t */
+
+typedef enum {
+    POPCORN_OK = 0,
+    POPCORN_ERR_INVALID = 1,      /* an argument is out of range or inconsistent            */
+    POPCORN_ERR_NOMEM = 2,        /* device workspace could not be allocated                */
+    POPCORN_ERR_CUDA = 3,         /* a CUDA runtime call or a kernel launch failed          */
+    POPCORN_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out; context still usable */
+    POPCORN_ERR_UNSUPPORTED = 5   /* valid request this build does not implement            */
+} popcorn_status;
+
+/* Kernel functions of Sec. 3.2 (and the linear kernel K = P P^T). */
+typedef enum {
+    POPCORN_LINEAR = 0,      /* kappa(x, y) = x . y                              */
+    POPCORN_POLYNOMIAL = 1,  /* kappa(x, y) = (gamma x . y + coef0)^degree       */
+    POPCORN_GAUSSIAN = 2     /* kappa(x, y) = exp(-gamma ||x - y||^2 / sigma^2)  */
+} popcorn_kernel_kind;
+
+typedef struct {
+    int32_t kind;    /* popcorn_kernel_kind                                  */
+    int32_t degree;  /* polynomial degree r >= 1 (integer)                  */
+    double gamma;    /* gamma > 0 (polynomial and Gaussian; 1 if unsure)    */
+    double coef0;    /* c (polynomial)                                      */
+    double sigma;    /* sigma > 0 (Gaussian)                                */
+} popcorn_kernel;
+
+/* Arithmetic used to form B = P P^T for the kernel matrix. */
+typedef enum {
+    POPCORN_FP32 = 0,    /* FP32 CUDA-core arithmetic; Gaussian distances from coordinate differences */
+    POPCORN_BF16 = 1,    /* tcgen05 tensor cores, BF16 operands, FP32 accumulate                       */
+    POPCORN_BF16X3 = 2,  /* tcgen05, split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate              */
+    POPCORN_FP8 = 3      /* reserved: FP8 E4M3 with per-row scales (recompute path)                   */
+} popcorn_precision;
+
+typedef struct {
+    int32_t precision;          /* popcorn_precision for the K build                         */
+    int32_t store_k;            /* 1: materialize K once (the paper's design)                */
+    int32_t check_convergence;  /* 1: stop when a pass changes no label (or on tol); 0: run
+                                   exactly max_iter passes (the paper's fixed-iteration mode) */
+    int32_t timing;             /* 1: record CUDA-event times per phase into popcorn_fit_info */
+    int64_t reserved[6];        /* must be zero                                              */
+} popcorn_options;
+
+/* Optional per-call report of popcorn_fit (all fields written by the call,
+   except the two caller-provided history arrays). */
+typedef struct {
+    double kbuild_ms;          /* K build (norms + kernel matrix), when timing = 1          */
+    double loop_ms;            /* all assignment passes, when timing = 1                    */
+    double reduce_ms;          /* sum over passes of the K-streaming reduction kernel       */
+    double assign_ms;          /* sum over passes of the distance/argmin kernel             */
+    double eval_ms;            /* final objective evaluation pass, if one was needed        */
+    int32_t reduce_launches;   /* launches of the K-streaming reduction kernel              */
+    int32_t assign_launches;   /* launches of the distance/argmin kernel                   */
+    int32_t kernel_launches;   /* all kernels this call launched                            */
+    int32_t converged;         /* 1 if a pass changed no label                              */
+    int64_t h2d_bytes;         /* host->device bytes the call copied                        */
+    int64_t d2h_bytes;         /* device->host bytes the call copied                        */
+    double* J_history;         /* caller-provided host array of >= max_iter doubles, or NULL:
+                                  J_t = J(labels before pass t)                             */
+    int32_t* changed_history;  /* caller-provided host array of >= max_iter ints, or NULL:
+                                  labels changed by pass t                                  */
+} popcorn_fit_info;
+
+/* Human-readable name of a status code (static storage). */
+POPCORN_API const char* popcorn_status_string(popcorn_status status);
+
+/* Message describing the last error returned on the calling thread (static
+   thread-local storage; empty after a successful call). */
+POPCORN_API const char* popcorn_last_error_message(void);
+
+/* Version of this library as MAJOR*10000 + MINOR*100 + PATCH. */
+POPCORN_API int32_t popcorn_version(void);
+
+/*
+ * popcorn_kernel_matrix -- K = kappa(P P^T) and diag(K).
+ *
+ * Sec. 3.2 (polynomial and Gaussian kernels from B = P P^T, Eq. 12 for the
+ * Gaussian) and Alg. 2 lines 1-2 (K once, P~ from diag(K)).
+ *
+ *   P      device, n x d FP32, leading dimension ldp >= d.
+ *   K      device, n x n FP32 output, leading dimension ldk >= n; ldk must be
+ *          a multiple of 4 and K 16-byte aligned.  The full square is written
+ *          (both triangles), symmetric.
+ *   kdiag  device, n FP32 output: kdiag[i] = K[i][i] (== 1 for Gaussian).
+ *   precision  POPCORN_FP32, POPCORN_BF16 or POPCORN_BF16X3.
+ *
+ * Errors: POPCORN_ERR_INVALID for n < 1, d < 1, ldp < d, ldk < n, ldk % 4,
+ * misaligned K, degree < 1 (polynomial), sigma <= 0 or gamma <= 0 (Gaussian);
+ * POPCORN_ERR_UNSUPPORTED for POPCORN_FP8.
+ */
+POPCORN_API popcorn_status popcorn_kernel_matrix(const float* P, int64_t n, int32_t d, int64_t ldp,
+                                     popcorn_kernel kern, int32_t precision,
+                                     float* K, int64_t ldk, float* kdiag,
+                                     popcorn_stream_t stream);
+
+/*
+ * popcorn_assign_step -- one pass of the loop body of Alg. 2 on a given K.
+ *
+ * From labels cl (Eq. 8 defines V from them): E = K V^T (Alg. 2 line 7,
+ * the paper's SpMM), ||c_j||^2 = sum over i in L_j of E_{i,j} / |L_j|
+ * (line 8-9, Eq. 14, the paper's SpMV), D = E-term + P~ + C~ (line 10) and
+ * new labels = row argmin of D (lines 11-13), ties to the lowest index, an
+ * empty cluster never chosen.
+ *
+ *   K, ldk     device, n x n FP32 (ldk % 4 == 0, 16-byte aligned).
+ *   kdiag      device, n FP32: diag(K).
+ *   labels     device, n int32 in [0, k): the current assignment.
+ *   new_labels device, n int32 output (may alias labels).
+ *   counts     device, k int32 output or NULL: |L_j| of the NEW labels.
+ *   E          device, n x k FP32 output (row-major, ld = k) or NULL:
+ *              E_ij = (K V^T)_ij for the CURRENT labels (0 for empty j).
+ *   cnorm      device, k FP64 output or NULL: ||c_j||^2 (0 for empty j).
+ *   objective  host, 1 double output or NULL: J(labels) = sum_i D_{i,cl(i)}.
+ *   changed    host, 1 int32 output or NULL: number of labels that changed.
+ * Host outputs are written after the call synchronizes the stream.
+ *
+ * Errors: POPCORN_ERR_INVALID for n < 2, k < 1, k > n, k > 256, bad ldk or
+ * alignment, or a label outside [0, k) (detected on the device).
+ */
+POPCORN_API popcorn_status popcorn_assign_step(const float* K, int64_t ldk, const float* kdiag, int64_t n,
+                                   int32_t k, const int32_t* labels, int32_t* new_labels,
+                                   int32_t* counts, float* E, double* cnorm,
+                                   double* objective, int32_t* changed,
+                                   popcorn_stream_t stream);
+
+/*
+ * popcorn_fit -- Kernel K-means (Alg. 2) from points and initial labels.
+ *
+ * Builds K once (Alg. 2 lines 1-2), then runs assignment passes (lines 6-15).
+ * Pass t computes D from labels cl_t, J_t = J(cl_t) and cl_{t+1} = argmin.
+ * Stopping (Alg. 1/2 "while iter < maxiter and centroids are changing"):
+ * always after max_iter passes; with opt->check_convergence also after a pass
+ * that changes no label, or after a pass t >= 1 with J_{t-1} - J_t <=
+ * tol * |J_t| when tol > 0.
+ *
+ *   P            host or device, n x d FP32, leading dimension ldp >= d.
+ *   k            number of clusters, 1 <= k < n, k <= 256.
+ *   init_labels  host or device, n int32 in [0, k).
+ *   max_iter     >= 0.  0 returns init_labels and their objective.
+ *   tol          >= 0, relative objective-decrease threshold (0 = off).
+ *   opt          options, or NULL for {FP32, store_k = 1, check_convergence = 1}.
+ *   labels_out   host or device, n int32 output (may alias init_labels).
+ *   objective_out    host, 1 double: J(labels_out) = sum_i ||phi(p_i) - c_cl(i)||^2.
+ *   iterations_out   host, 1 int32: passes performed.
+ *   info         host, optional report (NULL allowed).
+ *
+ * Errors: as popcorn_kernel_matrix, plus POPCORN_ERR_INVALID for k outside
+ * [1, n) or > 256, max_iter < 0, tol < 0, labels out of range, nonzero
+ * reserved fields; POPCORN_ERR_UNSUPPORTED for store_k = 0 or POPCORN_FP8 in
+ * this build; POPCORN_ERR_NOMEM when K does not fit in device memory.
+ */
+POPCORN_API popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, int32_t k,
+                           popcorn_kernel kern, const int32_t* init_labels, int32_t max_iter,
+                           double tol, const popcorn_options* opt, int32_t* labels_out,
+                           double* objective_out, int32_t* iterations_out,
+                           popcorn_fit_info* info, popcorn_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POPCORN_H */

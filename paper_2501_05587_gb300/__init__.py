@@ -1,0 +1,232 @@
+"""Python binding of the GB300 Kernel K-means library (``libpopcorn.so``).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+behind the C ABI of ``include/popcorn.h``.  Functions carry the C names:
+
+* ``popcorn_kernel_matrix`` -- K = kappa(P P^T) and diag(K) (Sec. 3.2).
+* ``popcorn_assign_step``   -- one pass of the loop body of Alg. 2 on a given K.
+* ``popcorn_fit``           -- Kernel K-means (Alg. 2) from points and labels.
+
+Device buffers are torch CUDA tensors (PyTorch supplies memory and streams);
+``popcorn_fit`` also accepts host buffers (CPU tensors or numpy arrays), which
+the library copies inside the call.  Importing this module fails loudly when
+the compiled library is missing: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "LIBRARY_PATH",
+    "PopcornError",
+    "popcorn_kernel_matrix",
+    "popcorn_assign_step",
+    "popcorn_fit",
+    "popcorn_version",
+    "kernel_spec",
+    "EXPORTED_SYMBOLS",
+]
+
+LIBRARY_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpopcorn.so")
+
+if not os.path.exists(LIBRARY_PATH):
+    raise ImportError(
+        f"{LIBRARY_PATH} is missing: build it with `python paper_2501_05587_gb300/build.py` "
+        "(nvcc, sm_103a). There is no CPU fallback.")
+
+_lib = ctypes.CDLL(LIBRARY_PATH)
+
+# names declared in include/popcorn.h
+EXPORTED_SYMBOLS = (
+    "popcorn_status_string",
+    "popcorn_last_error_message",
+    "popcorn_version",
+    "popcorn_kernel_matrix",
+    "popcorn_assign_step",
+    "popcorn_fit",
+)
+
+KIND = {"linear": 0, "polynomial": 1, "gaussian": 2}
+PRECISION = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp8": 3}
+
+
+class _Kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("degree", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("coef0", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("store_k", ctypes.c_int32),
+                ("check_convergence", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 6)]
+
+
+class _FitInfo(ctypes.Structure):
+    _fields_ = [("kbuild_ms", ctypes.c_double), ("loop_ms", ctypes.c_double),
+                ("reduce_ms", ctypes.c_double), ("assign_ms", ctypes.c_double),
+                ("eval_ms", ctypes.c_double), ("reduce_launches", ctypes.c_int32),
+                ("assign_launches", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("h2d_bytes", ctypes.c_int64),
+                ("d2h_bytes", ctypes.c_int64), ("J_history", ctypes.POINTER(ctypes.c_double)),
+                ("changed_history", ctypes.POINTER(ctypes.c_int32))]
+
+
+_vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+_lib.popcorn_status_string.restype = ctypes.c_char_p
+_lib.popcorn_status_string.argtypes = [ctypes.c_int]
+_lib.popcorn_last_error_message.restype = ctypes.c_char_p
+_lib.popcorn_last_error_message.argtypes = []
+_lib.popcorn_version.restype = _i32
+_lib.popcorn_version.argtypes = []
+_lib.popcorn_kernel_matrix.restype = ctypes.c_int
+_lib.popcorn_kernel_matrix.argtypes = [_vp, _i64, _i32, _i64, _Kernel, _i32, _vp, _i64, _vp, _vp]
+_lib.popcorn_assign_step.restype = ctypes.c_int
+_lib.popcorn_assign_step.argtypes = [_vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp,
+                                     ctypes.POINTER(_dbl), ctypes.POINTER(_i32), _vp]
+_lib.popcorn_fit.restype = ctypes.c_int
+_lib.popcorn_fit.argtypes = [_vp, _i64, _i32, _i64, _i32, _Kernel, _vp, _i32, _dbl,
+                             ctypes.POINTER(_Options), _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i32),
+                             ctypes.POINTER(_FitInfo), _vp]
+
+
+class PopcornError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        name = _lib.popcorn_status_string(status).decode()
+        msg = _lib.popcorn_last_error_message().decode()
+        super().__init__(f"{where}: {name}: {msg}")
+
+
+def _check(status: int, where: str) -> None:
+    if status != 0:
+        raise PopcornError(status, where)
+
+
+def popcorn_version() -> int:
+    return int(_lib.popcorn_version())
+
+
+def kernel_spec(kind: str = "gaussian", *, gamma: float = 1.0, coef0: float = 1.0, degree: int = 2,
+                sigma: float = 1.0) -> dict:
+    return {"kind": kind, "gamma": float(gamma), "coef0": float(coef0), "degree": int(degree),
+            "sigma": float(sigma)}
+
+
+def _kernel(kern: dict) -> _Kernel:
+    return _Kernel(KIND[kern["kind"]], int(kern.get("degree", 1)), float(kern.get("gamma", 1.0)),
+                   float(kern.get("coef0", 0.0)), float(kern.get("sigma", 1.0)))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(x):
+    """Address of a tensor or a numpy array (no copy)."""
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def popcorn_kernel_matrix(P, kernel: dict, precision: str = "fp32", K=None, kdiag=None, stream=None):
+    """K = kappa(P P^T) (full square, FP32) and diag(K) on the device of P.
+
+    P is an (n, d) float32 CUDA tensor (rows may be strided: ldp = P.stride(0)).
+    Returns (K, kdiag); K has a leading dimension rounded up to a multiple of 4
+    (the returned tensor is the (n, n) view).
+    """
+    torch = _torch()
+    assert P.is_cuda and P.dtype == torch.float32 and P.dim() == 2 and P.stride(1) == 1
+    n, d = P.shape
+    ldk = (n + 3) // 4 * 4
+    if K is None:
+        K = torch.empty((n, ldk), dtype=torch.float32, device=P.device)[:, :n]
+    if kdiag is None:
+        kdiag = torch.empty(n, dtype=torch.float32, device=P.device)
+    _check(_lib.popcorn_kernel_matrix(_ptr(P), n, d, P.stride(0), _kernel(kernel), PRECISION[precision],
+                                      _ptr(K), K.stride(0), _ptr(kdiag), _stream(stream)),
+           "popcorn_kernel_matrix")
+    return K, kdiag
+
+
+def popcorn_assign_step(K, kdiag, labels, k: int, want_E: bool = False, stream=None) -> dict:
+    """One pass of Alg. 2's loop body from ``labels`` on the device K.
+
+    Returns new labels, counts of the new labels, centroid norms ||c_j||^2,
+    J(labels), the number of changed labels and, with want_E, E = K V^T.
+    """
+    torch = _torch()
+    n = K.shape[0]
+    dev = K.device
+    labels = labels.to(device=dev, dtype=torch.int32).contiguous()
+    new = torch.empty(n, dtype=torch.int32, device=dev)
+    counts = torch.empty(k, dtype=torch.int32, device=dev)
+    cnorm = torch.empty(k, dtype=torch.float64, device=dev)
+    E = torch.empty((n, k), dtype=torch.float32, device=dev) if want_E else None
+    J = ctypes.c_double(0.0)
+    ch = ctypes.c_int32(0)
+    _check(_lib.popcorn_assign_step(_ptr(K), K.stride(0), _ptr(kdiag), n, int(k), _ptr(labels), _ptr(new),
+                                    _ptr(counts), _ptr(E) if E is not None else None, _ptr(cnorm),
+                                    ctypes.byref(J), ctypes.byref(ch), _stream(stream)),
+           "popcorn_assign_step")
+    return {"labels": new, "counts": counts, "cnorm": cnorm, "J": J.value, "changed": ch.value, "E": E}
+
+
+def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float = 0.0,
+                precision: str = "fp32", check_convergence: bool = True, timing: bool = False,
+                history: bool = False, labels_out=None, stream=None) -> dict:
+    """Kernel K-means (Alg. 2).  P and init_labels may live on the host or the device.
+
+    Returns {"labels", "objective", "iterations", "info"}; labels land where
+    ``labels_out`` lives (default: same place as init_labels).
+    """
+    torch = _torch()
+    host = isinstance(P, np.ndarray) or not P.is_cuda
+    if isinstance(P, np.ndarray):
+        P = np.ascontiguousarray(P, dtype=np.float32)
+        n, d = P.shape
+        ldp = d
+    else:
+        assert P.dtype == torch.float32 and P.dim() == 2 and P.stride(1) == 1
+        n, d = P.shape
+        ldp = P.stride(0)
+    if isinstance(init_labels, np.ndarray):
+        init_labels = np.ascontiguousarray(init_labels, dtype=np.int32)
+    else:
+        init_labels = init_labels.to(torch.int32).contiguous()
+    if labels_out is None:
+        if isinstance(init_labels, np.ndarray):
+            labels_out = np.empty(n, dtype=np.int32)
+        else:
+            labels_out = torch.empty(n, dtype=torch.int32, device=init_labels.device)
+    opt = _Options(PRECISION[precision], 1, 1 if check_convergence else 0, 1 if timing else 0,
+                   (ctypes.c_int64 * 6)())
+    info = _FitInfo()
+    Jh = (ctypes.c_double * max(1, max_iter))() if history else None
+    Ch = (ctypes.c_int32 * max(1, max_iter))() if history else None
+    if history:
+        info.J_history = ctypes.cast(Jh, ctypes.POINTER(ctypes.c_double))
+        info.changed_history = ctypes.cast(Ch, ctypes.POINTER(ctypes.c_int32))
+    obj = ctypes.c_double(0.0)
+    its = ctypes.c_int32(0)
+    _check(_lib.popcorn_fit(_ptr(P), n, d, ldp, int(k), _kernel(kernel), _ptr(init_labels), int(max_iter),
+                            float(tol), ctypes.byref(opt), _ptr(labels_out), ctypes.byref(obj),
+                            ctypes.byref(its), ctypes.byref(info), _stream(stream)),
+           "popcorn_fit")
+    out_info = {f: getattr(info, f) for f, _ in _FitInfo._fields_ if f not in ("J_history", "changed_history")}
+    if history:
+        out_info["J_history"] = list(Jh[: its.value])
+        out_info["changed_history"] = list(Ch[: its.value])
+    out_info["host_inputs"] = host
+    return {"labels": labels_out, "objective": obj.value, "iterations": its.value, "info": out_info}

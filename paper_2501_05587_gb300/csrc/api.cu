@@ -1,0 +1,515 @@
+// C ABI of the Kernel K-means engine: argument checks, workspace, and the
+// stream-ordered driver of Alg. 2 (K once, then assignment passes whose loop
+// control lives on the device).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "popcorn.h"
+#include "popcorn_internal.cuh"
+
+using namespace popcorn;
+
+namespace {
+
+thread_local std::string g_err;
+
+popcorn_status fail(popcorn_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define POPCORN_CUDA(call)                                                                    \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            cudaGetLastError();                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? POPCORN_ERR_NOMEM : POPCORN_ERR_CUDA, \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                     \
+        }                                                                                     \
+    } while (0)
+
+#define POPCORN_TRY(expr)                      \
+    do {                                       \
+        popcorn_status s_ = (expr);            \
+        if (s_ != POPCORN_OK) return s_;       \
+    } while (0)
+
+struct DeviceInfo {
+    int sms = 0;
+    int smem_optin = 0;
+    int reduce_smem = 0;   // dynamic shared memory usable by the reduction kernel
+    cudaMemPool_t pool = nullptr;
+    bool ready = false;
+};
+
+std::mutex g_dev_mu;
+DeviceInfo g_dev[64];
+
+// Per-device set-up, done once with that device current: SM count, shared
+// memory opt-in, and a private stream-ordered pool that keeps freed blocks.
+popcorn_status device_info(DeviceInfo** out) {
+    int dev = 0;
+    POPCORN_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(POPCORN_ERR_UNSUPPORTED, "device ordinal %d >= 64", dev);
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DeviceInfo& d = g_dev[dev];
+    if (!d.ready) {
+        POPCORN_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        POPCORN_CUDA(cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        POPCORN_CUDA(cudaMemPoolCreate(&d.pool, &props));
+        uint64_t thr = UINT64_MAX;
+        POPCORN_CUDA(cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        POPCORN_CUDA(configure_reduce_smem(d.smem_optin, &d.reduce_smem));
+        d.ready = true;
+    }
+    *out = &d;
+    return POPCORN_OK;
+}
+
+// Stream-ordered workspace: every block is returned to the pool (on the
+// stream) when the object goes out of scope, on success and on error paths.
+class Workspace {
+  public:
+    Workspace(cudaMemPool_t pool, cudaStream_t s) : pool_(pool), s_(s) {}
+    ~Workspace() {
+        for (void* p : blocks_) cudaFreeAsync(p, s_);
+    }
+    template <class T>
+    popcorn_status alloc(T** out, size_t count, const char* what) {
+        void* p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) & ~(size_t)255;
+        cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool_, s_);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? POPCORN_ERR_NOMEM : POPCORN_ERR_CUDA,
+                        "workspace for %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
+        }
+        blocks_.push_back(p);
+        *out = static_cast<T*>(p);
+        return POPCORN_OK;
+    }
+
+  private:
+    cudaMemPool_t pool_;
+    cudaStream_t s_;
+    std::vector<void*> blocks_;
+};
+
+// Pinned host staging for small device->host reads, grown on demand.
+struct PinnedScratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+thread_local PinnedScratch g_pinned;
+
+popcorn_status pinned(size_t bytes, void** out) {
+    if (g_pinned.bytes < bytes) {
+        if (g_pinned.p) cudaFreeHost(g_pinned.p);
+        g_pinned.p = nullptr;
+        g_pinned.bytes = 0;
+        POPCORN_CUDA(cudaMallocHost(&g_pinned.p, bytes));
+        g_pinned.bytes = bytes;
+    }
+    *out = g_pinned.p;
+    return POPCORN_OK;
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+popcorn_status check_kernel(const popcorn_kernel& kern, KernParams* kp) {
+    kp->kind = kern.kind;
+    kp->degree = kern.degree;
+    kp->gamma = (float)kern.gamma;
+    kp->coef0 = (float)kern.coef0;
+    kp->neg_gamma_over_sigma2 = 0.f;
+    switch (kern.kind) {
+        case POPCORN_LINEAR:
+            return POPCORN_OK;
+        case POPCORN_POLYNOMIAL:
+            if (kern.degree < 1 || kern.degree > 64)
+                return fail(POPCORN_ERR_INVALID, "polynomial degree %d outside [1, 64]", kern.degree);
+            if (!std::isfinite(kern.gamma) || !std::isfinite(kern.coef0))
+                return fail(POPCORN_ERR_INVALID, "polynomial gamma/coef0 must be finite");
+            return POPCORN_OK;
+        case POPCORN_GAUSSIAN:
+            if (!(kern.sigma > 0) || !std::isfinite(kern.sigma))
+                return fail(POPCORN_ERR_INVALID, "Gaussian sigma must be > 0 (got %g)", kern.sigma);
+            if (!(kern.gamma > 0) || !std::isfinite(kern.gamma))
+                return fail(POPCORN_ERR_INVALID, "Gaussian gamma must be > 0 (got %g)", kern.gamma);
+            kp->neg_gamma_over_sigma2 = (float)(-kern.gamma / (kern.sigma * kern.sigma));
+            return POPCORN_OK;
+        default:
+            return fail(POPCORN_ERR_INVALID, "unknown kernel kind %d", kern.kind);
+    }
+}
+
+popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, const KernParams& kp,
+                                   int precision, float* K, int64_t ldk, float* kdiag,
+                                   cudaStream_t s, int* launches) {
+    if (precision != POPCORN_FP32)
+        return fail(POPCORN_ERR_UNSUPPORTED, "precision %d is not available in this build", precision);
+    POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, kdiag, s, launches));
+    return POPCORN_OK;
+}
+
+struct EventPool {
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    popcorn_status get(cudaEvent_t* out) {
+        if (used == ev.size()) {
+            cudaEvent_t e;
+            POPCORN_CUDA(cudaEventCreate(&e));
+            ev.push_back(e);
+        }
+        *out = ev[used++];
+        return POPCORN_OK;
+    }
+};
+thread_local EventPool g_events;
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* popcorn_status_string(popcorn_status status) {
+    switch (status) {
+        case POPCORN_OK: return "POPCORN_OK";
+        case POPCORN_ERR_INVALID: return "POPCORN_ERR_INVALID";
+        case POPCORN_ERR_NOMEM: return "POPCORN_ERR_NOMEM";
+        case POPCORN_ERR_CUDA: return "POPCORN_ERR_CUDA";
+        case POPCORN_ERR_TIMEOUT: return "POPCORN_ERR_TIMEOUT";
+        case POPCORN_ERR_UNSUPPORTED: return "POPCORN_ERR_UNSUPPORTED";
+    }
+    return "POPCORN_ERR_UNKNOWN";
+}
+
+const char* popcorn_last_error_message(void) { return g_err.c_str(); }
+
+int32_t popcorn_version(void) { return 100; }
+
+popcorn_status popcorn_kernel_matrix(const float* P, int64_t n, int32_t d, int64_t ldp,
+                                     popcorn_kernel kern, int32_t precision, float* K, int64_t ldk,
+                                     float* kdiag, popcorn_stream_t stream) {
+    g_err.clear();
+    if (!P || !K || !kdiag) return fail(POPCORN_ERR_INVALID, "null pointer argument");
+    if (n < 1 || n >= (1LL << 31)) return fail(POPCORN_ERR_INVALID, "n = %lld outside [1, 2^31)", (long long)n);
+    if (d < 1) return fail(POPCORN_ERR_INVALID, "d = %d < 1", d);
+    if (ldp < d) return fail(POPCORN_ERR_INVALID, "ldp = %lld < d = %d", (long long)ldp, d);
+    if (ldk < n || ldk % 4 != 0)
+        return fail(POPCORN_ERR_INVALID, "ldk = %lld must be >= n and a multiple of 4", (long long)ldk);
+    if (reinterpret_cast<uintptr_t>(K) % 16 != 0) return fail(POPCORN_ERR_INVALID, "K must be 16-byte aligned");
+    KernParams kp;
+    POPCORN_TRY(check_kernel(kern, &kp));
+    DeviceInfo* dev;
+    POPCORN_TRY(device_info(&dev));
+    int launches = 0;
+    return build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, kdiag, (cudaStream_t)stream,
+                               &launches);
+}
+
+popcorn_status popcorn_assign_step(const float* K, int64_t ldk, const float* kdiag, int64_t n, int32_t k,
+                                   const int32_t* labels, int32_t* new_labels, int32_t* counts, float* E,
+                                   double* cnorm, double* objective, int32_t* changed,
+                                   popcorn_stream_t stream) {
+    g_err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!K || !kdiag || !labels || !new_labels) return fail(POPCORN_ERR_INVALID, "null pointer argument");
+    if (n < 2 || n >= (1LL << 31)) return fail(POPCORN_ERR_INVALID, "n = %lld outside [2, 2^31)", (long long)n);
+    if (k < 1 || k > n || k > kMaxClusters)
+        return fail(POPCORN_ERR_INVALID, "k = %d outside [1, min(n, %d)]", k, kMaxClusters);
+    if (ldk < n || ldk % 4 != 0)
+        return fail(POPCORN_ERR_INVALID, "ldk = %lld must be >= n and a multiple of 4", (long long)ldk);
+    if (reinterpret_cast<uintptr_t>(K) % 16 != 0) return fail(POPCORN_ERR_INVALID, "K must be 16-byte aligned");
+    DeviceInfo* dev;
+    POPCORN_TRY(device_info(&dev));
+    const int ni = (int)n;
+    ReducePlan plan = plan_reduce(ni, k, dev->sms, dev->reduce_smem);
+    if (plan.grid == 0) return fail(POPCORN_ERR_UNSUPPORTED, "n = %d is too large for the materialized path", ni);
+
+    Workspace ws(dev->pool, s);
+    PassBuffers b{};
+    b.K = K;
+    b.ldk = ldk;
+    b.kdiag = kdiag;
+    b.n = ni;
+    b.k = k;
+    const size_t nlab = ((size_t)ni + 15) & ~(size_t)15;
+    POPCORN_TRY(ws.alloc(&b.lab32, ni, "labels"));
+    POPCORN_TRY(ws.alloc(&b.lab8, nlab, "label bytes"));
+    POPCORN_TRY(ws.alloc(&b.counts, 2 * (size_t)k, "counts"));
+    POPCORN_TRY(ws.alloc(&b.Spart, (size_t)plan.nseg * ni * k, "segment sums"));
+    POPCORN_TRY(ws.alloc(&b.zpart, (size_t)plan.grid * k, "block partials"));
+    POPCORN_TRY(ws.alloc(&b.zsum, (size_t)k, "z sums"));
+    POPCORN_TRY(ws.alloc(&b.cnorm, (size_t)k, "centroid norms"));
+    POPCORN_TRY(ws.alloc(&b.invm, (size_t)k, "inverse cluster sizes"));
+    POPCORN_TRY(ws.alloc(&b.st, 1, "loop state"));
+    POPCORN_TRY(ws.alloc(&b.J_hist, 1, "objective history"));
+    POPCORN_TRY(ws.alloc(&b.changed_hist, 1, "change history"));
+    b.E_out = E;
+
+    POPCORN_CUDA(cudaMemsetAsync(b.counts, 0, 2 * (size_t)k * sizeof(int32_t), s));
+    POPCORN_CUDA(launch_init_state(b.st, 1, 0, 0.0, s));
+    POPCORN_CUDA(launch_init_labels(labels, ni, k, b.lab32, b.lab8, b.counts, b.st, s));
+    POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
+    POPCORN_CUDA(launch_reduce(b, plan, 0, s));
+    if (cnorm) POPCORN_CUDA(cudaMemcpyAsync(cnorm, b.cnorm, (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    POPCORN_CUDA(launch_assign(b, plan, s));
+    POPCORN_CUDA(cudaMemcpyAsync(new_labels, b.lab32, (size_t)ni * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (counts) POPCORN_CUDA(cudaMemcpyAsync(counts, b.counts + k, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    void* host;
+    POPCORN_TRY(pinned(sizeof(LoopState), &host));
+    POPCORN_CUDA(cudaMemcpyAsync(host, b.st, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+    POPCORN_CUDA(cudaStreamSynchronize(s));
+    LoopState hs;
+    memcpy(&hs, host, sizeof hs);
+    if (hs.bad_label) return fail(POPCORN_ERR_INVALID, "a label is outside [0, %d)", k);
+    if (objective) *objective = hs.J_last;
+    if (changed) *changed = hs.last_changed;
+    return POPCORN_OK;
+}
+
+popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, int32_t k, popcorn_kernel kern,
+                           const int32_t* init_labels, int32_t max_iter, double tol,
+                           const popcorn_options* opt_in, int32_t* labels_out, double* objective_out,
+                           int32_t* iterations_out, popcorn_fit_info* info, popcorn_stream_t stream) {
+    g_err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    popcorn_options opt;
+    memset(&opt, 0, sizeof opt);
+    opt.precision = POPCORN_FP32;
+    opt.store_k = 1;
+    opt.check_convergence = 1;
+    if (opt_in) opt = *opt_in;
+    if (!P || !init_labels || !labels_out || !objective_out || !iterations_out)
+        return fail(POPCORN_ERR_INVALID, "null pointer argument");
+    if (n < 2 || n >= (1LL << 31)) return fail(POPCORN_ERR_INVALID, "n = %lld outside [2, 2^31)", (long long)n);
+    if (d < 1) return fail(POPCORN_ERR_INVALID, "d = %d < 1", d);
+    if (ldp < d) return fail(POPCORN_ERR_INVALID, "ldp = %lld < d = %d", (long long)ldp, d);
+    if (k < 1 || k >= n || k > kMaxClusters)
+        return fail(POPCORN_ERR_INVALID, "k = %d outside [1, min(n - 1, %d)]", k, kMaxClusters);
+    if (max_iter < 0) return fail(POPCORN_ERR_INVALID, "max_iter = %d < 0", max_iter);
+    if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
+    for (int r = 0; r < 6; ++r)
+        if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
+    if (opt.store_k != 1) return fail(POPCORN_ERR_UNSUPPORTED, "store_k = 0 (recompute path) is not available in this build");
+    KernParams kp;
+    POPCORN_TRY(check_kernel(kern, &kp));
+    DeviceInfo* dev;
+    POPCORN_TRY(device_info(&dev));
+    const int ni = (int)n;
+    const int64_t ldk = (n + 3) / 4 * 4;
+    ReducePlan plan = plan_reduce(ni, k, dev->sms, dev->reduce_smem);
+    if (plan.grid == 0) return fail(POPCORN_ERR_UNSUPPORTED, "n = %d is too large for the materialized path", ni);
+    const bool timing = opt.timing != 0;
+    int launches = 0;
+    int64_t h2d = 0, d2h = 0;
+
+    Workspace ws(dev->pool, s);
+    const float* Pd = P;
+    int64_t ldpd = ldp;
+    if (!is_device_pointer(P)) {
+        float* tmp;
+        POPCORN_TRY(ws.alloc(&tmp, (size_t)ni * d, "points"));
+        POPCORN_CUDA(cudaMemcpy2DAsync(tmp, (size_t)d * sizeof(float), P, (size_t)ldp * sizeof(float),
+                                       (size_t)d * sizeof(float), (size_t)ni, cudaMemcpyHostToDevice, s));
+        h2d += (int64_t)ni * d * sizeof(float);
+        Pd = tmp;
+        ldpd = d;
+    }
+    const int32_t* Ld = init_labels;
+    if (!is_device_pointer(init_labels)) {
+        int32_t* tmp;
+        POPCORN_TRY(ws.alloc(&tmp, (size_t)ni, "initial labels"));
+        POPCORN_CUDA(cudaMemcpyAsync(tmp, init_labels, (size_t)ni * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        h2d += (int64_t)ni * sizeof(int32_t);
+        Ld = tmp;
+    }
+
+    PassBuffers b{};
+    float* K;
+    float* kdiag;
+    POPCORN_TRY(ws.alloc(&K, (size_t)ni * (size_t)ldk, "kernel matrix"));
+    POPCORN_TRY(ws.alloc(&kdiag, (size_t)ni, "diag(K)"));
+    const size_t nlab = ((size_t)ni + 15) & ~(size_t)15;
+    const int hist_len = max_iter > 0 ? max_iter : 1;
+    b.K = K;
+    b.ldk = ldk;
+    b.kdiag = kdiag;
+    b.n = ni;
+    b.k = k;
+    POPCORN_TRY(ws.alloc(&b.lab32, ni, "labels"));
+    POPCORN_TRY(ws.alloc(&b.lab8, nlab, "label bytes"));
+    POPCORN_TRY(ws.alloc(&b.counts, 2 * (size_t)k, "counts"));
+    POPCORN_TRY(ws.alloc(&b.Spart, (size_t)plan.nseg * ni * k, "segment sums"));
+    POPCORN_TRY(ws.alloc(&b.zpart, (size_t)plan.grid * k, "block partials"));
+    POPCORN_TRY(ws.alloc(&b.zsum, (size_t)k, "z sums"));
+    POPCORN_TRY(ws.alloc(&b.cnorm, (size_t)k, "centroid norms"));
+    POPCORN_TRY(ws.alloc(&b.invm, (size_t)k, "inverse cluster sizes"));
+    POPCORN_TRY(ws.alloc(&b.st, 1, "loop state"));
+    POPCORN_TRY(ws.alloc(&b.J_hist, (size_t)hist_len, "objective history"));
+    POPCORN_TRY(ws.alloc(&b.changed_hist, (size_t)hist_len, "change history"));
+    b.E_out = nullptr;
+
+    g_events.used = 0;
+    cudaEvent_t ev_b0 = nullptr, ev_b1 = nullptr, ev_l1 = nullptr, ev_e1 = nullptr;
+    std::vector<cudaEvent_t> ev_r, ev_a;   // before/after each reduction and assignment launch
+    if (timing) {
+        POPCORN_TRY(g_events.get(&ev_b0));
+        POPCORN_CUDA(cudaEventRecord(ev_b0, s));
+    }
+    POPCORN_CUDA(cudaMemsetAsync(b.counts, 0, 2 * (size_t)k * sizeof(int32_t), s));
+    POPCORN_CUDA(launch_init_state(b.st, max_iter, opt.check_convergence ? 1 : 0, tol, s));
+    POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, kdiag, s, &launches));
+    POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
+    POPCORN_CUDA(launch_init_labels(Ld, ni, k, b.lab32, b.lab8, b.counts, b.st, s));
+    launches += 3;
+    if (timing) {
+        POPCORN_TRY(g_events.get(&ev_b1));
+        POPCORN_CUDA(cudaEventRecord(ev_b1, s));
+    }
+
+    // Assignment passes.  With convergence checking, the host polls the
+    // device "done" flag one chunk behind, so at most one chunk of passes is
+    // launched after convergence (those return at once on the device).
+    const int chunk = 4;
+    void* hpin;
+    POPCORN_TRY(pinned(2 * sizeof(int32_t) + sizeof(LoopState), &hpin));
+    volatile int32_t* hflag = static_cast<int32_t*>(hpin);
+    cudaEvent_t poll_ev[2] = {nullptr, nullptr};
+    if (opt.check_convergence) {
+        POPCORN_TRY(g_events.get(&poll_ev[0]));
+        POPCORN_TRY(g_events.get(&poll_ev[1]));
+    }
+    int launched = 0, pending = -1, slot = 0;
+    while (launched < max_iter) {
+        const int m = (max_iter - launched < chunk) ? (max_iter - launched) : chunk;
+        for (int t = 0; t < m; ++t) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+            if (timing) {
+                POPCORN_TRY(g_events.get(&e0));
+                POPCORN_TRY(g_events.get(&e1));
+                POPCORN_TRY(g_events.get(&e2));
+                POPCORN_CUDA(cudaEventRecord(e0, s));
+            }
+            POPCORN_CUDA(launch_reduce(b, plan, 0, s));
+            if (timing) POPCORN_CUDA(cudaEventRecord(e1, s));
+            POPCORN_CUDA(launch_assign(b, plan, s));
+            if (timing) {
+                POPCORN_CUDA(cudaEventRecord(e2, s));
+                ev_r.push_back(e0);
+                ev_r.push_back(e1);
+                ev_a.push_back(e1);
+                ev_a.push_back(e2);
+            }
+            launches += 2;
+        }
+        launched += m;
+        if (opt.check_convergence && launched < max_iter) {
+            POPCORN_CUDA(cudaMemcpyAsync((void*)(hflag + slot), &b.st->done, sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, s));
+            POPCORN_CUDA(cudaEventRecord(poll_ev[slot], s));
+            if (pending >= 0) {
+                POPCORN_CUDA(cudaEventSynchronize(poll_ev[pending]));
+                if (hflag[pending]) break;
+            }
+            pending = slot;
+            slot ^= 1;
+        }
+    }
+    if (timing) {
+        POPCORN_TRY(g_events.get(&ev_l1));
+        POPCORN_CUDA(cudaEventRecord(ev_l1, s));
+    }
+    // J(labels_out): reuses J of the last pass when it changed nothing
+    POPCORN_CUDA(launch_reduce(b, plan, 1, s));
+    launches += 1;
+    if (timing) {
+        POPCORN_TRY(g_events.get(&ev_e1));
+        POPCORN_CUDA(cudaEventRecord(ev_e1, s));
+    }
+
+    LoopState* hs_pin = reinterpret_cast<LoopState*>(static_cast<char*>(hpin) + 2 * sizeof(int32_t));
+    POPCORN_CUDA(cudaMemcpyAsync(hs_pin, b.st, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+    d2h += sizeof(LoopState);
+    if (is_device_pointer(labels_out)) {
+        POPCORN_CUDA(cudaMemcpyAsync(labels_out, b.lab32, (size_t)ni * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    } else {
+        POPCORN_CUDA(cudaMemcpyAsync(labels_out, b.lab32, (size_t)ni * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        d2h += (int64_t)ni * sizeof(int32_t);
+    }
+    POPCORN_CUDA(cudaStreamSynchronize(s));
+    LoopState hs;
+    memcpy(&hs, hs_pin, sizeof hs);
+    if (hs.bad_label) return fail(POPCORN_ERR_INVALID, "an initial label is outside [0, %d)", k);
+    *objective_out = hs.J_eval;
+    *iterations_out = hs.iter;
+
+    if (info) {
+        const int iters = hs.iter;
+        if (iters > 0 && (info->J_history || info->changed_history)) {
+            if (info->J_history)
+                POPCORN_CUDA(cudaMemcpy(info->J_history, b.J_hist, (size_t)iters * sizeof(double), cudaMemcpyDeviceToHost));
+            if (info->changed_history)
+                POPCORN_CUDA(cudaMemcpy(info->changed_history, b.changed_hist, (size_t)iters * sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost));
+        }
+        info->converged = hs.converged;
+        info->kernel_launches = launches;
+        // passes that did work (launches after convergence return at once)
+        const bool eval_ran = !(hs.iter > 0 && hs.last_changed == 0);
+        info->reduce_launches = iters + (eval_ran ? 1 : 0);
+        info->assign_launches = iters;
+        info->h2d_bytes = h2d;
+        info->d2h_bytes = d2h;
+        info->kbuild_ms = info->loop_ms = info->reduce_ms = info->assign_ms = info->eval_ms = 0.0;
+        if (timing) {
+            info->kbuild_ms = elapsed(ev_b0, ev_b1);
+            info->loop_ms = elapsed(ev_b1, ev_l1);
+            info->eval_ms = elapsed(ev_l1, ev_e1);
+            double r = 0, a = 0;
+            for (size_t t = 0; t + 1 < ev_r.size() && t < 2 * (size_t)iters; t += 2) r += elapsed(ev_r[t], ev_r[t + 1]);
+            for (size_t t = 0; t + 1 < ev_a.size() && t < 2 * (size_t)iters; t += 2) a += elapsed(ev_a[t], ev_a[t + 1]);
+            info->reduce_ms = r;
+            info->assign_ms = a;
+        }
+    }
+    return POPCORN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,570 @@
+// Per-pass kernels of Kernel K-means (Alg. 2, lines 6-15).
+//
+// reduce_kernel  -- streams K once per pass.  For every row i and cluster c it
+//                   forms the segment sums S_ic = sum_{j in L_c} K_ij, i.e.
+//                   (K V^T)_ic * |L_c| (the paper's SpMM, Alg. 2 line 7).  It
+//                   also accumulates, in FP64, sum_{i in L_c} S_{i,c} -- the
+//                   entries of z (Eq. 14) grouped by cluster, which is the
+//                   paper's SpMV V z (Alg. 2 lines 8-9) -- and its last block
+//                   turns them into ||c_c||^2 and the objective J.
+// assign_kernel  -- D_ic = K_ii - 2 S_ic/|L_c| + ||c_c||^2 (Alg. 2 line 10),
+//                   the row argmin (lines 11-13), new labels, the cluster
+//                   sizes of the new labels (warp-aggregated atomics) and the
+//                   loop-control decision of the pass.
+//
+// V is never built: a label byte per column is all the K-stream needs.  E and
+// D are never stored (E only on request for tests).
+#include "popcorn_internal.cuh"
+
+#include <cuda/std/limits>
+
+namespace popcorn {
+namespace {
+
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// hi + lo += x without rounding loss (Knuth's TwoSum; FP32 pipe only).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += e;
+}
+
+template <int UNR, bool LAB_SMEM>
+__device__ __forceinline__ void load_batch(const float4* row4, const uint32_t* lab4, int q, int q1,
+                                           float4 (&v)[UNR], uint32_t (&L)[UNR]) {
+#pragma unroll
+    for (int t = 0; t < UNR; ++t) {
+        const int qq = q + 32 * t;
+        if (qq < q1) {
+            v[t] = ld_stream(row4 + qq);
+            L[t] = LAB_SMEM ? lab4[qq] : __ldg(lab4 + qq);
+        } else {
+            v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            L[t] = 0u;
+        }
+    }
+}
+
+// Cluster whose warp total lane `lane` holds after butterfly<KB>.
+template <int KB>
+__device__ __forceinline__ int bfly_cluster(int lane) {
+    int c = 0;
+#pragma unroll
+    for (int w = KB >> 1, off = 16; w >= 1; w >>= 1, off >>= 1)
+        if (lane & off) c += w;
+    return c;
+}
+
+// Reduce-scatter of KB per-lane partials over the warp: each level halves
+// the values a lane carries (one half goes to the partner, the other half is
+// kept), then the remaining levels all-reduce the single value left.
+template <int KB>
+__device__ __forceinline__ float butterfly(const float (&acc)[KB], int lane) {
+    float v[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) v[t] = acc[t];
+    int off = 16;
+#pragma unroll
+    for (int cnt = KB; cnt > 1; cnt >>= 1, off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int t = 0; t < cnt / 2; ++t) {
+            const float send = up ? v[t] : v[t + cnt / 2];
+            const float keep = up ? v[t + cnt / 2] : v[t];
+            v[t] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+#pragma unroll
+    for (; off > 0; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+    return v[0];
+}
+
+struct ReduceArgs {
+    const float* K;
+    int64_t ldk;
+    int n, k, nseg, seglen;
+    const uint8_t* lab8;
+    float* Spart;
+    double* zpart;
+    double* zsum;
+    double* cnorm;
+    double* invm;
+    const int32_t* counts;
+    LoopState* st;
+    double* J_hist;
+    int eval_only;
+};
+
+// Per-lane partial sums live in lane-private shared-memory columns acc[c][lane]
+// (bank = lane: a conflict-free scatter for any k).  At the end of a unit the
+// warp reduces them: for k <= KB each lane pulls its k partials into
+// registers and a butterfly reduce-scatter leaves one cluster total per lane
+// group; for larger k (KB == 0) lane c walks row c in rotated order.  UNR
+// float4 per lane per batch; the next batch -- across unit boundaries too --
+// is in flight while the current one is scattered.
+template <int KB, int UNR, bool LAB_SMEM>
+__global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceArgs a) {
+    LoopState* st = a.st;
+    if (a.eval_only) {
+        // J(final labels) is already known when the last pass changed nothing
+        if (st->iter > 0 && st->last_changed == 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) st->J_eval = st->J_last;
+            return;
+        }
+    } else if (st->done) {
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = a.n, k = a.k, nseg = a.nseg;
+    const int W = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nlab = LAB_SMEM ? ((n + 15) & ~15) : 0;
+    uint8_t* slab = smem;
+    float* sacc = reinterpret_cast<float*>(smem + nlab);
+    const int nacc = W * k * 32;
+    float* zhi = sacc + nacc;                 // per-warp float-float z partials
+    float* zlo = zhi + W * k;
+
+    if (LAB_SMEM) {
+        const uint4* src = reinterpret_cast<const uint4*>(a.lab8);
+        uint4* dst = reinterpret_cast<uint4*>(slab);
+        for (int t = threadIdx.x; t < nlab / 16; t += blockDim.x) dst[t] = src[t];
+    }
+    for (int t = threadIdx.x; t < nacc; t += blockDim.x) sacc[t] = 0.f;
+    for (int t = threadIdx.x; t < 2 * W * k; t += blockDim.x) zhi[t] = 0.f;
+    __syncthreads();
+
+    const uint8_t* labs = LAB_SMEM ? slab : a.lab8;
+    const uint32_t* lab4 = reinterpret_cast<const uint32_t*>(labs);
+    float* accw = sacc + (size_t)warp * k * 32;   // this warp's [k][32] block
+    float* accl = accw + lane;
+    float* zwh = zhi + (size_t)warp * k;
+    float* zwl = zlo + (size_t)warp * k;
+
+    auto scatter = [&](uint32_t l, float x) {
+#ifdef POPCORN_REDUCE_ATOMIC
+        atomicAdd(accl + l * 32, x);
+#else
+        accl[l * 32] += x;
+#endif
+    };
+
+    // unit indices fit in 32 bits: n < 2^31 / nseg is checked on the host
+    const int units = n * nseg;
+    const int GW = (int)gridDim.x * W;
+    int u = (int)blockIdx.x * W + warp;
+    if (u < units) {
+        auto geom = [&](int uu, int& ii, int& ss, int& cc1, int& qqb, int& qq1, const float4*& r4) {
+            ii = uu / nseg;
+            ss = uu - ii * nseg;
+            const int c0 = ss * a.seglen;
+            cc1 = min(n, c0 + a.seglen);
+            qqb = c0 >> 2;
+            qq1 = cc1 >> 2;
+            r4 = reinterpret_cast<const float4*>(a.K + (int64_t)ii * a.ldk);
+        };
+        int i, s, c1, qb, q1;
+        const float4* row4;
+        geom(u, i, s, c1, qb, q1, row4);
+        float4 v[UNR];
+        uint32_t L[UNR];
+        load_batch<UNR, LAB_SMEM>(row4, lab4, qb + lane, q1, v, L);
+        while (true) {
+            const bool last = qb + 32 * UNR >= q1;
+            const int un = last ? u + GW : u;
+            int in_ = i, sn = s, c1n = c1, qbn = qb + 32 * UNR, q1n = q1;
+            const float4* row4n = row4;
+            float4 vn[UNR];
+            uint32_t Ln[UNR];
+            if (last && un < units) geom(un, in_, sn, c1n, qbn, q1n, row4n);
+            if (!last || un < units) load_batch<UNR, LAB_SMEM>(row4n, lab4, qbn + lane, q1n, vn, Ln);
+#pragma unroll
+            for (int t = 0; t < UNR; ++t) {
+                scatter(L[t] & 0xffu, v[t].x);
+                scatter((L[t] >> 8) & 0xffu, v[t].y);
+                scatter((L[t] >> 16) & 0xffu, v[t].z);
+                scatter(L[t] >> 24, v[t].w);
+            }
+            if (last) {
+                {   // ragged tail of the row (n not a multiple of 4)
+                    const int j = (q1 << 2) + lane;
+                    if (j < c1) scatter(labs[j], a.K[(int64_t)i * a.ldk + j]);
+                }
+                const int li = labs[i];
+                float* out = a.Spart + ((int64_t)i * nseg + s) * k;   // layout [i][s][c]
+                __syncwarp();
+                if constexpr (KB > 0) {
+                    float part[KB];
+#pragma unroll
+                    for (int c = 0; c < KB; ++c) {
+                        part[c] = c < k ? accl[c * 32] : 0.f;
+                        if (c < k) accl[c * 32] = 0.f;
+                    }
+                    const float tot = butterfly<KB>(part, lane);
+                    const int c = bfly_cluster<KB>(lane);
+                    if ((lane & (32 / KB - 1)) == 0 && c < k) {
+                        out[c] = tot;
+                        if (c == li) ff_add(zwh[c], zwl[c], tot);
+                    }
+                } else {
+                    for (int cb = 0; cb < k; cb += 32) {
+                        const int c = cb + lane;
+                        if (c < k) {
+                            // lane c walks row c of the warp block in rotated order: conflict-free
+                            float tot = 0.f;
+                            float* row = accw + (size_t)c * 32;
+#pragma unroll 8
+                            for (int j = 0; j < 32; ++j) {
+                                const int idx = (j + lane) & 31;
+                                tot += row[idx];
+                                row[idx] = 0.f;
+                            }
+                            out[c] = tot;
+                            if (c == li) ff_add(zwh[c], zwl[c], tot);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (un >= units) break;
+                u = un;
+                i = in_;
+                s = sn;
+                c1 = c1n;
+                q1 = q1n;
+                row4 = row4n;
+            }
+            qb = qbn;
+#pragma unroll
+            for (int t = 0; t < UNR; ++t) {
+                v[t] = vn[t];
+                L[t] = Ln[t];
+            }
+        }
+    }
+    __syncthreads();
+
+    // block partial of sum_{i in L_c} S_ic, fixed warp order
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < W; ++w) t += (double)zhi[(size_t)w * k + c] + (double)zlo[(size_t)w * k + c];
+        a.zpart[(size_t)blockIdx.x * k + c] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int am_last;
+    if (threadIdx.x == 0) am_last = (atomicAdd(&st->reduce_ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+
+    // last block: ||c_c||^2 = (1/m_c^2) sum_{i in L_c} S_ic, J = trace K - sum_c (1/m_c) sum_{i in L_c} S_ic
+    const int32_t* m = a.counts + (size_t)(st->iter & 1) * k;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(a.zpart + (size_t)b * k + c);
+        const double mc = (double)__ldcg(m + c);
+        const double inv = mc > 0 ? 1.0 / mc : 0.0;
+        a.zsum[c] = t;
+        a.invm[c] = inv;
+        a.cnorm[c] = t * inv * inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double J = st->trace;
+        for (int c = 0; c < k; ++c) {
+            J -= __ldcg(a.zsum + c) * __ldcg(a.invm + c);
+        }
+        if (a.eval_only) {
+            st->J_eval = J;
+        } else {
+            a.J_hist[st->iter] = J;
+            st->J_last = J;
+        }
+        st->reduce_ticket = 0u;
+    }
+}
+
+struct AssignArgs {
+    int n, k, nseg;
+    const float* Spart;
+    const float* kdiag;
+    const double* cnorm;
+    const double* invm;
+    int32_t* counts;
+    int32_t* lab32;
+    uint8_t* lab8;
+    LoopState* st;
+    int32_t* changed_hist;
+    float* E_out;
+};
+
+__global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) {
+    LoopState* st = a.st;
+    if (st->done) return;
+    __shared__ int hist[kMaxClusters];
+    __shared__ int am_last;
+    const int n = a.n, k = a.k;
+    const int it = st->iter;
+    const int32_t* m = a.counts + (size_t)(it & 1) * k;
+    int32_t* mnext = a.counts + (size_t)((it + 1) & 1) * k;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) hist[c] = 0;
+    __syncthreads();
+
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int newl = 0, changed = 0;
+    if (i < n) {
+        const int li = a.lab32[i];
+        const double kd = (double)a.kdiag[i];
+        double best = cuda::std::numeric_limits<double>::infinity();
+        int bi = li;
+        const float* Si = a.Spart + (int64_t)i * a.nseg * k;
+        for (int c = 0; c < k; ++c) {
+            const int mc = m[c];
+            float hi = 0.f, lo = 0.f;
+#pragma unroll 8
+            for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[(int64_t)s * k + c]);
+            const double E = ((double)hi + (double)lo) * a.invm[c];   // (K V^T)_ic
+            if (a.E_out) a.E_out[(int64_t)i * k + c] = (float)E;
+            if (mc == 0) continue;
+            const double D = fma(-2.0, E, kd + a.cnorm[c]);
+            if (D < best) {
+                best = D;
+                bi = c;
+            }
+        }
+        newl = bi;
+        changed = (bi != li);
+        a.lab32[i] = bi;
+        a.lab8[i] = (uint8_t)bi;
+    }
+    // cluster sizes of the new labels: one shared atomic per distinct label in the warp
+    const unsigned act = __ballot_sync(0xffffffffu, i < n);
+    if (i < n) {
+        const unsigned peers = __match_any_sync(act, newl);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[newl], __popc(peers));
+    }
+    const int block_changed = __syncthreads_count(changed);
+    for (int c = threadIdx.x; c < k; c += blockDim.x)
+        if (hist[c]) atomicAdd(mnext + c, hist[c]);
+    if (threadIdx.x == 0 && block_changed) atomicAdd(&st->changed_acc, (unsigned)block_changed);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(&st->assign_ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+
+    // last block: the counts of this pass are consumed; clear them for pass it + 2
+    int32_t* mcur = a.counts + (size_t)(it & 1) * k;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) mcur[c] = 0;
+    if (threadIdx.x == 0) {
+        const int ch = (int)atomicExch(&st->changed_acc, 0u);
+        a.changed_hist[it] = ch;
+        st->last_changed = ch;
+        st->iter = it + 1;
+        int done = (it + 1 >= st->max_iter);
+        if (st->check_conv) {
+            if (ch == 0) {
+                done = 1;
+                st->converged = 1;
+            }
+            if (st->tol > 0.0 && it >= 1 && st->J_prev - st->J_last <= st->tol * fabs(st->J_last)) done = 1;
+        }
+        st->J_prev = st->J_last;
+        st->done = done;
+        st->assign_ticket = 0u;
+    }
+}
+
+__global__ void init_state_kernel(LoopState* st, int max_iter, int check_conv, double tol) {
+    st->iter = 0;
+    st->done = (max_iter <= 0);
+    st->converged = 0;
+    st->max_iter = max_iter;
+    st->check_conv = check_conv;
+    st->last_changed = -1;
+    st->reduce_ticket = 0u;
+    st->assign_ticket = 0u;
+    st->changed_acc = 0u;
+    st->bad_label = 0;
+    st->tol = tol;
+    st->trace = 0.0;
+    st->J_last = 0.0;
+    st->J_prev = 0.0;
+    st->J_eval = 0.0;
+}
+
+// sum of diag(K) in FP64; one block, fixed reduction order
+__global__ void __launch_bounds__(1024) trace_kernel(const float* __restrict__ kdiag, int n, LoopState* st) {
+    __shared__ double part[1024];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t += (double)kdiag[i];
+    part[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st->trace = part[0];
+}
+
+__global__ void __launch_bounds__(256) init_labels_kernel(const int32_t* __restrict__ in, int n, int k,
+                                                          int32_t* lab32, uint8_t* lab8, int nlab,
+                                                          int32_t* counts, LoopState* st) {
+    __shared__ int hist[kMaxClusters];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) hist[c] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        int l = in[i];
+        if (l < 0 || l >= k) {
+            atomicExch(&st->bad_label, 1);
+            l = 0;
+        }
+        lab32[i] = l;
+        lab8[i] = (uint8_t)l;
+        atomicAdd(&hist[l], 1);
+    } else if (i < nlab) {
+        lab8[i] = 0;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x)
+        if (hist[c]) atomicAdd(counts + c, hist[c]);
+}
+
+}  // namespace
+
+namespace {
+
+using ReduceFn = void (*)(ReduceArgs);
+
+ReduceFn reduce_fn(int variant, bool lab_smem) {
+    switch (variant) {
+        case kReduceBfly4: return lab_smem ? reduce_kernel<4, 4, true> : reduce_kernel<4, 4, false>;
+        case kReduceBfly8: return lab_smem ? reduce_kernel<8, 4, true> : reduce_kernel<8, 4, false>;
+        default: return lab_smem ? reduce_kernel<0, 4, true> : reduce_kernel<0, 4, false>;
+    }
+}
+
+}  // namespace
+
+ReducePlan plan_reduce(int n, int k, int num_sms, int smem_budget) {
+    ReducePlan p{};
+    p.variant = k <= 4 ? kReduceBfly4 : (k <= 8 ? kReduceBfly8 : kReduceRotated);
+    const size_t nlab = ((size_t)n + 15) & ~(size_t)15;
+    const size_t per_warp = (size_t)k * 32 * sizeof(float) + 2 * (size_t)k * sizeof(float);
+    p.labels_in_smem = nlab + per_warp * 4 <= (size_t)smem_budget;
+    const size_t base = p.labels_in_smem ? nlab : 0;
+    int w = (int)(((size_t)smem_budget - base) / per_warp);
+    if (w > kReduceMaxWarps) w = kReduceMaxWarps;
+    if (w < 1) w = 1;
+    p.warps = w;
+    p.smem = base + per_warp * w;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reduce_fn(p.variant, p.labels_in_smem), 32 * w, p.smem);
+    cudaGetLastError();
+    if (per_sm < 1) per_sm = 1;
+    p.grid = num_sms * per_sm;
+    // split rows into segments so that each warp gets ~16 units (row, segment);
+    // the next unit's loads overlap the current unit's reduction
+    const long long warps_total = (long long)p.grid * w;
+    long long nseg = (16 * warps_total + n - 1) / n;
+    if (nseg < 1) nseg = 1;
+    long long seglen = (n + nseg - 1) / nseg;
+    seglen = (seglen + 127) / 128 * 128;
+    if (seglen < 1024) seglen = 1024;
+    p.seglen = (int)seglen;
+    p.nseg = (int)((n + seglen - 1) / seglen);
+    if ((long long)n * p.nseg >= (1LL << 31)) p.grid = 0;   // unit indices would overflow: caller rejects
+    return p;
+}
+
+cudaError_t launch_init_state(LoopState* st, int max_iter, int check_conv, double tol, cudaStream_t s) {
+    init_state_kernel<<<1, 1, 0, s>>>(st, max_iter, check_conv, tol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const float* kdiag, int n, LoopState* st, cudaStream_t s) {
+    trace_kernel<<<1, 1024, 0, s>>>(kdiag, n, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_labels(const int32_t* in, int n, int k, int32_t* lab32, uint8_t* lab8,
+                               int32_t* counts, LoopState* st, cudaStream_t s) {
+    const int nlab = (n + 15) & ~15;
+    init_labels_kernel<<<(nlab + 255) / 256, 256, 0, s>>>(in, n, k, lab32, lab8, nlab, counts, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const PassBuffers& b, const ReducePlan& plan, int eval_only, cudaStream_t s) {
+    ReduceArgs a;
+    a.K = b.K;
+    a.ldk = b.ldk;
+    a.n = b.n;
+    a.k = b.k;
+    a.nseg = plan.nseg;
+    a.seglen = plan.seglen;
+    a.lab8 = b.lab8;
+    a.Spart = b.Spart;
+    a.zpart = b.zpart;
+    a.zsum = b.zsum;
+    a.cnorm = b.cnorm;
+    a.invm = b.invm;
+    a.counts = b.counts;
+    a.st = b.st;
+    a.J_hist = b.J_hist;
+    a.eval_only = eval_only;
+    reduce_fn(plan.variant, plan.labels_in_smem)<<<plan.grid, plan.warps * 32, plan.smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assign(const PassBuffers& b, const ReducePlan& plan, cudaStream_t s) {
+    AssignArgs a;
+    a.n = b.n;
+    a.k = b.k;
+    a.nseg = plan.nseg;
+    a.Spart = b.Spart;
+    a.kdiag = b.kdiag;
+    a.cnorm = b.cnorm;
+    a.invm = b.invm;
+    a.counts = b.counts;
+    a.lab32 = b.lab32;
+    a.lab8 = b.lab8;
+    a.st = b.st;
+    a.changed_hist = b.changed_hist;
+    a.E_out = b.E_out;
+    assign_kernel<<<(b.n + kAssignThreads - 1) / kAssignThreads, kAssignThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Opt the reduction kernels into the largest dynamic shared memory the device
+// allows next to their static shared memory; *usable receives that size.
+cudaError_t configure_reduce_smem(int optin, int* usable) {
+    size_t st = 0;
+    for (int v = 0; v < 3; ++v)
+        for (int l = 0; l < 2; ++l) {
+            cudaFuncAttributes fa;
+            cudaError_t e = cudaFuncGetAttributes(&fa, reduce_fn(v, l != 0));
+            if (e != cudaSuccess) return e;
+            if (fa.sharedSizeBytes > st) st = fa.sharedSizeBytes;
+        }
+    const int bytes = optin - (int)((st + 127) / 128 * 128);
+    for (int v = 0; v < 3; ++v)
+        for (int l = 0; l < 2; ++l) {
+            cudaError_t e = cudaFuncSetAttribute(reduce_fn(v, l != 0), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e != cudaSuccess) return e;
+        }
+    *usable = bytes;
+    return cudaSuccess;
+}
+
+}  // namespace popcorn

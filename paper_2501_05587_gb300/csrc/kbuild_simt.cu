@@ -1,0 +1,182 @@
+// FP32 CUDA-core build of the kernel matrix K = kappa(P P^T).
+//
+// Sec. 3.2: B = P P^T, then the kernel function elementwise (polynomial:
+// (gamma B + c)^r; Gaussian: exp(-gamma ||p_i - p_j||^2 / sigma^2)).  The
+// paper forms B with GEMM or SYRK plus a triangle copy and a separate
+// transform pass (Sec. 4.2); here one kernel computes each upper-triangle
+// 128 x 128 tile once, applies kappa in registers and stores the tile and its
+// transpose, so B never exists in memory and no copy pass runs.  In this FP32
+// form the Gaussian squared distance is summed from coordinate differences,
+// which keeps full relative accuracy for near-duplicate points (the norm
+// expansion of Eq. 12 cancels there).
+#include "popcorn_internal.cuh"
+
+#include <math.h>
+
+namespace popcorn {
+namespace {
+
+constexpr int TILE = 128;
+constexpr int KC = 8;           // depth of one shared-memory slice
+constexpr int LDS = TILE + 4;   // padded row: conflict-free transposed fill
+
+__device__ __forceinline__ void tri_coords(long long t, int T, int* bi, int* bj) {
+    // t enumerates the upper triangle row by row: row b starts at off(b) = b*T - b*(b-1)/2.
+    double Td = (double)T;
+    double disc = (2.0 * Td + 1.0) * (2.0 * Td + 1.0) - 8.0 * (double)t;
+    int b = (int)floor(((2.0 * Td + 1.0) - sqrt(disc)) * 0.5);
+    if (b < 0) b = 0;
+    if (b > T - 1) b = T - 1;
+    auto off = [&](long long r) { return r * (long long)T - r * (r - 1) / 2; };
+    while (b > 0 && off(b) > t) --b;
+    while (b < T - 1 && off(b + 1) <= t) ++b;
+    *bi = b;
+    *bj = b + (int)(t - off(b));
+}
+
+template <int KIND>
+__device__ __forceinline__ float apply_kernel(float v, const KernParams& kp) {
+    if (KIND == POPCORN_LINEAR) return v;
+    if (KIND == POPCORN_POLYNOMIAL) {
+        float base = fmaf(kp.gamma, v, kp.coef0);
+        float r = base;
+        for (int e = 1; e < kp.degree; ++e) r *= base;
+        return r;
+    }
+    return expf(kp.neg_gamma_over_sigma2 * v);   // v = ||p_i - p_j||^2
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restrict__ P, int n, int d,
+                                                          int64_t ldp, KernParams kp,
+                                                          float* __restrict__ K, int64_t ldk,
+                                                          float* __restrict__ kdiag, int T) {
+    __shared__ __align__(16) float As[KC][LDS];
+    __shared__ __align__(16) float Bs[KC][LDS];
+    int bi, bj;
+    tri_coords((long long)blockIdx.x, T, &bi, &bj);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int row0 = bi * TILE, col0 = bj * TILE;
+
+    float acc[8][8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+
+    for (int l0 = 0; l0 < d; l0 += KC) {
+#pragma unroll
+        for (int e = tid; e < TILE * KC; e += 256) {
+            int r = e / KC, l = e % KC;
+            int gl = l0 + l;
+            float va = 0.f, vb = 0.f;
+            if (gl < d) {
+                if (row0 + r < n) va = __ldg(P + (int64_t)(row0 + r) * ldp + gl);
+                if (col0 + r < n) vb = __ldg(P + (int64_t)(col0 + r) * ldp + gl);
+            }
+            As[l][r] = va;
+            Bs[l][r] = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < KC; ++l) {
+            float4 a0 = *reinterpret_cast<const float4*>(&As[l][ty * 4]);
+            float4 a1 = *reinterpret_cast<const float4*>(&As[l][64 + ty * 4]);
+            float4 b0 = *reinterpret_cast<const float4*>(&Bs[l][tx * 4]);
+            float4 b1 = *reinterpret_cast<const float4*>(&Bs[l][64 + tx * 4]);
+            float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int x = 0; x < 8; ++x)
+#pragma unroll
+                for (int y = 0; y < 8; ++y) {
+                    if (KIND == POPCORN_GAUSSIAN) {
+                        float t = a[x] - b[y];
+                        acc[x][y] = fmaf(t, t, acc[x][y]);
+                    } else {
+                        acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+                    }
+                }
+        }
+        __syncthreads();
+    }
+
+    // epilogue: kappa, diagonal, store tile and (off-diagonal tiles) its transpose
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = apply_kernel<KIND>(acc[x][y], kp);
+
+    if (bi == bj) {
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            int r = row0 + ty * 4 + (x & 3) + 64 * (x >> 2);
+#pragma unroll
+            for (int y = 0; y < 8; ++y) {
+                int c = col0 + tx * 4 + (y & 3) + 64 * (y >> 2);
+                if (r == c && r < n) {
+                    if (KIND == POPCORN_GAUSSIAN) acc[x][y] = 1.0f;
+                    kdiag[r] = acc[x][y];
+                }
+            }
+        }
+    }
+
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        int r = row0 + ty * 4 + (x & 3) + 64 * (x >> 2);
+        if (r >= n) continue;
+        float* Kr = K + (int64_t)r * ldk;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int c = col0 + 64 * h + tx * 4;
+            float4 v = make_float4(acc[x][4 * h], acc[x][4 * h + 1], acc[x][4 * h + 2], acc[x][4 * h + 3]);
+            if (c + 3 < n) {
+                *reinterpret_cast<float4*>(Kr + c) = v;
+            } else {
+                if (c < n) Kr[c] = v.x;
+                if (c + 1 < n) Kr[c + 1] = v.y;
+                if (c + 2 < n) Kr[c + 2] = v.z;
+            }
+        }
+    }
+    if (bi != bj) {
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+            int c = col0 + tx * 4 + (y & 3) + 64 * (y >> 2);
+            if (c >= n) continue;
+            float* Kc = K + (int64_t)c * ldk;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                int r = row0 + 64 * g + ty * 4;   // row0 tiles are full (bi < bj => rows < n)
+                float4 v = make_float4(acc[4 * g][y], acc[4 * g + 1][y], acc[4 * g + 2][y], acc[4 * g + 3][y]);
+                *reinterpret_cast<float4*>(Kc + r) = v;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp, float* K,
+                               int64_t ldk, float* kdiag, cudaStream_t s, int* launches) {
+    const int T = (n + TILE - 1) / TILE;
+    const long long tiles = (long long)T * (T + 1) / 2;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)tiles), block(256);
+    switch (kp.kind) {
+        case POPCORN_LINEAR:
+            kbuild_simt_kernel<POPCORN_LINEAR><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            break;
+        case POPCORN_POLYNOMIAL:
+            kbuild_simt_kernel<POPCORN_POLYNOMIAL><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            break;
+        default:
+            kbuild_simt_kernel<POPCORN_GAUSSIAN><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            break;
+    }
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace popcorn

@@ -1,0 +1,92 @@
+"""The C ABI library builds, loads and exports every symbol include/popcorn.h declares.
+
+CPU-only: argument validation returns before any CUDA call, so it is checked
+here too; nothing in this file runs a kernel.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "popcorn.h")
+
+
+@pytest.fixture(scope="module")
+def pc():
+    import __graft_entry__ as ge
+    b = ge._build_module()
+    if not os.path.exists(b.LIB):
+        b.build()
+    import paper_2501_05587_gb300 as mod
+    return mod
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"POPCORN_API\s+[\w\s\*]+?\b(popcorn_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("popcorn_kernel_matrix", "popcorn_fit", "popcorn_assign_step",
+                     "popcorn_status_string", "popcorn_last_error_message", "popcorn_version"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(pc):
+    lib = ctypes.CDLL(pc.LIBRARY_PATH)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(pc.EXPORTED_SYMBOLS) == set(_declared())
+
+
+def test_status_strings_and_version(pc):
+    lib = ctypes.CDLL(pc.LIBRARY_PATH)
+    lib.popcorn_status_string.restype = ctypes.c_char_p
+    assert lib.popcorn_status_string(0) == b"POPCORN_OK"
+    assert lib.popcorn_status_string(1) == b"POPCORN_ERR_INVALID"
+    assert lib.popcorn_status_string(4) == b"POPCORN_ERR_TIMEOUT"
+    assert lib.popcorn_status_string(99) == b"POPCORN_ERR_UNKNOWN"
+    assert pc.popcorn_version() >= 100
+
+
+def test_invalid_arguments_rejected_before_any_cuda_call(pc):
+    lib = pc._lib
+    kern = pc._Kernel(2, 1, 1.0, 0.0, 1.0)
+    # null pointers
+    st = lib.popcorn_fit(None, 10, 2, 2, 2, kern, None, 5, 0.0, None, None, None, None, None, None)
+    assert st == 1
+    assert b"null" in lib.popcorn_last_error_message()
+    P = np.zeros((10, 2), np.float32)
+    lab = np.zeros(10, np.int32)
+    out = np.zeros(10, np.int32)
+    obj = ctypes.c_double()
+    its = ctypes.c_int32()
+
+    def fit(n=10, d=2, ldp=2, k=2, kern=kern, max_iter=5, tol=0.0, opt=None):
+        return lib.popcorn_fit(P.ctypes.data, n, d, ldp, k, kern, lab.ctypes.data, max_iter, tol, opt,
+                               out.ctypes.data, ctypes.byref(obj), ctypes.byref(its), None, None)
+
+    assert fit(k=10) == 1            # k must be < n
+    assert fit(k=0) == 1
+    assert fit(k=300, n=1000) == 1   # k > 256
+    assert fit(d=0) == 1
+    assert fit(ldp=1) == 1
+    assert fit(max_iter=-1) == 1
+    assert fit(tol=-1.0) == 1
+    assert fit(kern=pc._Kernel(2, 1, 1.0, 0.0, 0.0)) == 1        # sigma = 0
+    assert fit(kern=pc._Kernel(1, 0, 1.0, 1.0, 1.0)) == 1        # degree 0
+    assert fit(kern=pc._Kernel(7, 1, 1.0, 1.0, 1.0)) == 1        # unknown kind
+    bad = pc._Options(0, 1, 1, 0, (ctypes.c_int64 * 6)(1, 0, 0, 0, 0, 0))
+    assert fit(opt=ctypes.byref(bad)) == 1                       # reserved must be zero
+    rec = pc._Options(0, 0, 1, 0, (ctypes.c_int64 * 6)())
+    assert fit(opt=ctypes.byref(rec)) == 5                       # recompute path not in this build
+    # kernel matrix: ldk must be a multiple of 4 and >= n
+    st = lib.popcorn_kernel_matrix(P.ctypes.data, 10, 2, 2, kern, 0, out.ctypes.data, 10, out.ctypes.data, None)
+    assert st == 1
+    st = lib.popcorn_assign_step(P.ctypes.data, 16, P.ctypes.data, 10, 0, lab.ctypes.data, lab.ctypes.data,
+                                 None, None, None, None, None, None)
+    assert st == 1
