@@ -206,6 +206,42 @@ POPCORN_API popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int
                            double* objective_out, int32_t* iterations_out,
                            popcorn_fit_info* info, popcorn_stream_t stream);
 
+/*
+ * popcorn_assign_step_noalloc -- popcorn_assign_step without any allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory, for example a host framework that owns all
+ * device memory through its own allocator, or a long-running loop that
+ * forbids allocation once it has started.  It computes exactly what
+ * popcorn_assign_step computes (same kernels, same launch plan), with the
+ * same arguments, layouts and ownership, but it calls no cudaMalloc,
+ * cudaFree, pool or pinned-host allocation: its temporary buffers live in one
+ * statically allocated device array of POPCORN_NOALLOC_SCRATCH_BYTES bytes.
+ *
+ *   - Every GPU that loads this library holds that array until the process
+ *     exits.
+ *   - The first call on a device does a one-time set-up for that device (it
+ *     looks up the array's device address and sets kernel attributes); make
+ *     that first call before any stream capture.
+ *   - A step needs about 4 * k * max(n, ~80,000) + 5 n bytes (grows with the
+ *     row segmentation of the K stream).  A request that does not fit returns
+ *     POPCORN_ERR_INVALID with the needed and available sizes in
+ *     popcorn_last_error_message(); nothing is launched.
+ *   - All calls share the array and it keeps the last call's contents (the
+ *     call itself clears what must start at zero).  Calls that overlap on
+ *     the GPU -- on two streams, or from two host threads -- race on it and
+ *     give wrong results: serialize them.
+ *
+ * Errors: as popcorn_assign_step, plus the size limit above.
+ */
+#define POPCORN_NOALLOC_SCRATCH_BYTES (32ll * 1024 * 1024)
+
+POPCORN_API popcorn_status popcorn_assign_step_noalloc(const float* K, int64_t ldk, const float* kdiag,
+                                                       int64_t n, int32_t k, const int32_t* labels,
+                                                       int32_t* new_labels, int32_t* counts, float* E,
+                                                       double* cnorm, double* objective, int32_t* changed,
+                                                       popcorn_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

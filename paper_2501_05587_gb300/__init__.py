@@ -25,6 +25,8 @@ __all__ = [
     "popcorn_kernel_matrix",
     "popcorn_assign_step",
     "popcorn_fit",
+    "popcorn_assign_step_noalloc",
+    "NOALLOC_SCRATCH_BYTES",
     "popcorn_version",
     "kernel_spec",
     "EXPORTED_SYMBOLS",
@@ -47,6 +49,7 @@ EXPORTED_SYMBOLS = (
     "popcorn_kernel_matrix",
     "popcorn_assign_step",
     "popcorn_fit",
+    "popcorn_assign_step_noalloc",
 )
 
 KIND = {"linear": 0, "polynomial": 1, "gaussian": 2}
@@ -86,6 +89,8 @@ _lib.popcorn_kernel_matrix.argtypes = [_vp, _i64, _i32, _i64, _Kernel, _i32, _vp
 _lib.popcorn_assign_step.restype = ctypes.c_int
 _lib.popcorn_assign_step.argtypes = [_vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp,
                                      ctypes.POINTER(_dbl), ctypes.POINTER(_i32), _vp]
+_lib.popcorn_assign_step_noalloc.restype = ctypes.c_int
+_lib.popcorn_assign_step_noalloc.argtypes = _lib.popcorn_assign_step.argtypes
 _lib.popcorn_fit.restype = ctypes.c_int
 _lib.popcorn_fit.argtypes = [_vp, _i64, _i32, _i64, _i32, _Kernel, _vp, _i32, _dbl,
                              ctypes.POINTER(_Options), _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i32),
@@ -160,12 +165,7 @@ def popcorn_kernel_matrix(P, kernel: dict, precision: str = "fp32", K=None, kdia
     return K, kdiag
 
 
-def popcorn_assign_step(K, kdiag, labels, k: int, want_E: bool = False, stream=None) -> dict:
-    """One pass of Alg. 2's loop body from ``labels`` on the device K.
-
-    Returns new labels, counts of the new labels, centroid norms ||c_j||^2,
-    J(labels), the number of changed labels and, with want_E, E = K V^T.
-    """
+def _assign_step(fn, where, K, kdiag, labels, k, want_E, stream):
     torch = _torch()
     n = K.shape[0]
     dev = K.device
@@ -176,11 +176,36 @@ def popcorn_assign_step(K, kdiag, labels, k: int, want_E: bool = False, stream=N
     E = torch.empty((n, k), dtype=torch.float32, device=dev) if want_E else None
     J = ctypes.c_double(0.0)
     ch = ctypes.c_int32(0)
-    _check(_lib.popcorn_assign_step(_ptr(K), K.stride(0), _ptr(kdiag), n, int(k), _ptr(labels), _ptr(new),
-                                    _ptr(counts), _ptr(E) if E is not None else None, _ptr(cnorm),
-                                    ctypes.byref(J), ctypes.byref(ch), _stream(stream)),
-           "popcorn_assign_step")
+    _check(fn(_ptr(K), K.stride(0), _ptr(kdiag), n, int(k), _ptr(labels), _ptr(new), _ptr(counts),
+              _ptr(E) if E is not None else None, _ptr(cnorm), ctypes.byref(J), ctypes.byref(ch),
+              _stream(stream)), where)
     return {"labels": new, "counts": counts, "cnorm": cnorm, "J": J.value, "changed": ch.value, "E": E}
+
+
+def popcorn_assign_step(K, kdiag, labels, k: int, want_E: bool = False, stream=None) -> dict:
+    """One pass of Alg. 2's loop body from ``labels`` on the device K.
+
+    Returns new labels, counts of the new labels, centroid norms ||c_j||^2,
+    J(labels), the number of changed labels and, with want_E, E = K V^T.
+    """
+    return _assign_step(_lib.popcorn_assign_step, "popcorn_assign_step", K, kdiag, labels, k, want_E, stream)
+
+
+# size of the static device scratch array of popcorn_assign_step_noalloc (include/popcorn.h)
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def popcorn_assign_step_noalloc(K, kdiag, labels, k: int, want_E: bool = False, stream=None) -> dict:
+    """popcorn_assign_step for callers that may not allocate device memory.
+
+    Same results and arguments; the library's temporaries live in one static
+    device array of NOALLOC_SCRATCH_BYTES (calls must not overlap on the GPU).
+    The output tensors this wrapper returns are allocated here by torch for
+    convenience; a caller that cannot allocate passes its own buffers to the
+    C entry point directly.
+    """
+    return _assign_step(_lib.popcorn_assign_step_noalloc, "popcorn_assign_step_noalloc", K, kdiag, labels, k,
+                        want_E, stream)
 
 
 def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float = 0.0,

@@ -205,6 +205,8 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 }  // namespace
 
+void popcorn::set_error_message(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* popcorn_status_string(popcorn_status status) {

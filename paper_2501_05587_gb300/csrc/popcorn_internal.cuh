@@ -57,6 +57,9 @@ struct ReducePlan {
     bool labels_in_smem;
 };
 
+// Sets the message popcorn_last_error_message() returns on this thread (api.cu).
+void set_error_message(const char* msg);
+
 // ---- K build (kbuild_simt.cu) ------------------------------------------------
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp,
                                float* K, int64_t ldk, float* kdiag, cudaStream_t s, int* launches);
