@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink n (profiling captures only; the reported workload is scale 1)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["rings", "blobs", "images"],
+                    help="rings (default, the reported line), blobs, images")
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3"],
+                    help="K-build precision (default: the workload's)")
     return ap.parse_args()
 
 
@@ -235,14 +239,16 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    wl = synth.workload(WORKLOAD, scale=args.scale)
+    wl = synth.workload(args.workload, scale=args.scale)
+    if args.precision:
+        wl.precision = args.precision
     P = torch.from_numpy(wl.P).cuda()
     lab = torch.from_numpy(wl.init_labels).cuda()
     out = torch.empty_like(lab)
 
     def step(timing=True):
-        return pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=True,
-                              timing=timing, labels_out=out)
+        return pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
+                              precision=wl.precision, timing=timing, labels_out=out)
 
     for _ in range(args.warmup):
         step()
@@ -275,13 +281,16 @@ def main():
     Ph = torch.from_numpy(wl.P).pin_memory()
     Lh = torch.from_numpy(wl.init_labels).pin_memory()
     Oh = torch.empty(wl.n, dtype=torch.int32).pin_memory()
+    def host_step():
+        return pc.popcorn_fit(Ph, wl.k, wl.kernel, Lh, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
+                              precision=wl.precision, labels_out=Oh)
+
     for _ in range(args.warmup):
-        pc.popcorn_fit(Ph, wl.k, wl.kernel, Lh, max_iter=wl.max_iter, labels_out=Oh)
+        host_step()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_res = [pc.popcorn_fit(Ph, wl.k, wl.kernel, Lh, max_iter=wl.max_iter, labels_out=Oh)
-               for _ in range(args.steps)]
+    e2e_res = [host_step() for _ in range(args.steps)]
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     barrier()
@@ -317,12 +326,14 @@ def main():
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32",
+            "dtype": "f32" if wl.precision == "fp32" else f"{wl.precision} operands, f32 accumulate/K",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC if args.scale == 1.0 else f"{WORKLOAD} scaled x{args.scale}",
+            "config": {"workload": (WORKLOAD_DESC if args.workload == WORKLOAD and args.scale == 1.0
+                                    else f"{wl.name} scaled x{args.scale}"),
+                       "precision": wl.precision,
                        "n": n, "d": wl.d, "k": k,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (K = 1.6 GB streamed every pass)",
+                       "l2": f"inputs larger than L2 (K = {4 * wl.n * wl.n / 1e9:.2f} GB streamed every pass)",
                        "passes_per_fit": iters / args.steps},
             "kbuild_tflops": kb_flops / (kb_ms / args.steps / 1e3) / 1e12 if kb_ms > 0 else None,
             "kbuild_ms": kb_ms / args.steps,
@@ -339,7 +350,7 @@ def main():
             "gpu_launches": launches_all,
             "clocks": clk,
         }
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -77,6 +77,7 @@ popcorn_status device_info(DeviceInfo** out) {
         uint64_t thr = UINT64_MAX;
         POPCORN_CUDA(cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &thr));
         POPCORN_CUDA(configure_reduce_smem(d.smem_optin, &d.reduce_smem));
+        POPCORN_CUDA(configure_kbuild_tc());
         d.ready = true;
     }
     *out = &d;
@@ -170,12 +171,24 @@ popcorn_status check_kernel(const popcorn_kernel& kern, KernParams* kp) {
     }
 }
 
+// K = kappa(P P^T) on stream s.  FP32: CUDA-core tiles.  BF16 / BF16X3: tcgen05
+// tiles; their operand copies come from `ws`, and *err (device) reports a
+// timed-out wait inside the kernel.
 popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, const KernParams& kp,
-                                   int precision, float* K, int64_t ldk, float* kdiag,
-                                   cudaStream_t s, int* launches) {
-    if (precision != POPCORN_FP32)
-        return fail(POPCORN_ERR_UNSUPPORTED, "precision %d is not available in this build", precision);
-    POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, kdiag, s, launches));
+                                   int precision, float* K, int64_t ldk, float* kdiag, Workspace* ws,
+                                   int* err, int num_sms, cudaStream_t s, int* launches) {
+    if (precision == POPCORN_FP32) {
+        POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, kdiag, s, launches));
+        return POPCORN_OK;
+    }
+    if (precision != POPCORN_BF16 && precision != POPCORN_BF16X3)
+        return fail(POPCORN_ERR_UNSUPPORTED, "precision %d is not available for a stored K", precision);
+    unsigned char* w;
+    POPCORN_TRY(ws->alloc(&w, kbuild_tc_workspace(n, d, precision), "BF16 operands"));
+    cudaError_t e = launch_kbuild_tc(P, n, d, ldp, kp, precision, K, ldk, kdiag, w, err, num_sms, s, launches);
+    if (e == cudaErrorInvalidValue)
+        return fail(POPCORN_ERR_CUDA, "tensor map creation failed (cuTensorMapEncodeTiled unavailable or rejected)");
+    POPCORN_CUDA(e);
     return POPCORN_OK;
 }
 
@@ -241,8 +254,21 @@ popcorn_status popcorn_kernel_matrix(const float* P, int64_t n, int32_t d, int64
     DeviceInfo* dev;
     POPCORN_TRY(device_info(&dev));
     int launches = 0;
-    return build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, kdiag, (cudaStream_t)stream,
-                               &launches);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == POPCORN_FP32)
+        return build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, kdiag, nullptr, nullptr, dev->sms, s,
+                                   &launches);
+    Workspace ws(dev->pool, s);
+    int* err;
+    POPCORN_TRY(ws.alloc(&err, 1, "error flag"));
+    POPCORN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    POPCORN_TRY(build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, kdiag, &ws, err, dev->sms, s,
+                                    &launches));
+    int herr = 0;
+    POPCORN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    POPCORN_CUDA(cudaStreamSynchronize(s));
+    if (herr) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the tensor-core K build ran out");
+    return POPCORN_OK;
 }
 
 popcorn_status popcorn_assign_step(const float* K, int64_t ldk, const float* kdiag, int64_t n, int32_t k,
@@ -397,7 +423,8 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     }
     POPCORN_CUDA(cudaMemsetAsync(b.counts, 0, 2 * (size_t)k * sizeof(int32_t), s));
     POPCORN_CUDA(launch_init_state(b.st, max_iter, opt.check_convergence ? 1 : 0, tol, s));
-    POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, kdiag, s, &launches));
+    POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, kdiag, &ws, &b.st->kbuild_err,
+                                    dev->sms, s, &launches));
     POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
     POPCORN_CUDA(launch_init_labels(Ld, ni, k, b.lab32, b.lab8, b.counts, b.st, s));
     launches += 3;
@@ -479,6 +506,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     LoopState hs;
     memcpy(&hs, hs_pin, sizeof hs);
     if (hs.bad_label) return fail(POPCORN_ERR_INVALID, "an initial label is outside [0, %d)", k);
+    if (hs.kbuild_err) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the tensor-core K build ran out");
     *objective_out = hs.J_eval;
     *iterations_out = hs.iter;
 

@@ -396,6 +396,7 @@ __global__ void init_state_kernel(LoopState* st, int max_iter, int check_conv, d
     st->assign_ticket = 0u;
     st->changed_acc = 0u;
     st->bad_label = 0;
+    st->kbuild_err = 0;
     st->tol = tol;
     st->trace = 0.0;
     st->J_last = 0.0;

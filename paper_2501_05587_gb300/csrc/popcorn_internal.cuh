@@ -34,6 +34,8 @@ struct LoopState {
     uint32_t assign_ticket;
     uint32_t changed_acc;    // labels changed in the running pass
     int32_t bad_label;       // an input label was outside [0, k)
+    int32_t kbuild_err;      // the tensor-core K build timed out in a bounded wait
+    int32_t pad0;
     double tol;
     double trace;          // sum_i K_ii in FP64
     double J_last;         // J(labels before the last pass)
@@ -63,6 +65,17 @@ void set_error_message(const char* msg);
 // ---- K build (kbuild_simt.cu) ------------------------------------------------
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp,
                                float* K, int64_t ldk, float* kdiag, cudaStream_t s, int* launches);
+
+// ---- K build on tensor cores (kbuild_tc.cu) ---------------------------------
+// Workspace bytes for the BF16 operand copies and row norms.
+size_t kbuild_tc_workspace(int n, int d, int precision);
+// Opt the tcgen05 kernel into its shared memory (once per device).
+cudaError_t configure_kbuild_tc();
+// precision POPCORN_BF16 or POPCORN_BF16X3; *err (device) becomes nonzero if a
+// bounded wait inside the kernel ran out.
+cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
+                             int64_t ldk, float* kdiag, void* workspace, int* err, int num_sms, cudaStream_t s,
+                             int* launches);
 
 // ---- iteration kernels (iterate.cu) -----------------------------------------
 // Opt the reduction kernels into the largest dynamic shared memory the device
