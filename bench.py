@@ -50,9 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink n (profiling captures only; the reported workload is scale 1)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["rings", "blobs", "images"],
-                    help="rings (default, the reported line), blobs, images")
-    ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=["rings", "blobs", "images", "mixture"],
+                    help="rings (default, the reported line), blobs, images, mixture (recompute path)")
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3", "fp8"],
                     help="K-build precision (default: the workload's)")
     return ap.parse_args()
 
@@ -248,7 +248,7 @@ def main():
 
     def step(timing=True):
         return pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
-                              precision=wl.precision, timing=timing, labels_out=out)
+                              precision=wl.precision, timing=timing, labels_out=out, store_k=wl.store_k)
 
     for _ in range(args.warmup):
         step()
@@ -283,7 +283,7 @@ def main():
     Oh = torch.empty(wl.n, dtype=torch.int32).pin_memory()
     def host_step():
         return pc.popcorn_fit(Ph, wl.k, wl.kernel, Lh, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
-                              precision=wl.precision, labels_out=Oh)
+                              precision=wl.precision, labels_out=Oh, store_k=wl.store_k)
 
     for _ in range(args.warmup):
         host_step()

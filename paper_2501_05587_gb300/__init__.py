@@ -210,11 +210,12 @@ def popcorn_assign_step_noalloc(K, kdiag, labels, k: int, want_E: bool = False, 
 
 def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float = 0.0,
                 precision: str = "fp32", check_convergence: bool = True, timing: bool = False,
-                history: bool = False, labels_out=None, stream=None) -> dict:
+                history: bool = False, labels_out=None, store_k: bool = True, stream=None) -> dict:
     """Kernel K-means (Alg. 2).  P and init_labels may live on the host or the device.
 
-    Returns {"labels", "objective", "iterations", "info"}; labels land where
-    ``labels_out`` lives (default: same place as init_labels).
+    ``store_k=False`` selects the recompute path (K never stored; precision
+    "bf16" or "fp8").  Returns {"labels", "objective", "iterations", "info"};
+    labels land where ``labels_out`` lives (default: same place as init_labels).
     """
     torch = _torch()
     host = isinstance(P, np.ndarray) or not P.is_cuda
@@ -235,7 +236,7 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
             labels_out = np.empty(n, dtype=np.int32)
         else:
             labels_out = torch.empty(n, dtype=torch.int32, device=init_labels.device)
-    opt = _Options(PRECISION[precision], 1, 1 if check_convergence else 0, 1 if timing else 0,
+    opt = _Options(PRECISION[precision], 1 if store_k else 0, 1 if check_convergence else 0, 1 if timing else 0,
                    (ctypes.c_int64 * 6)())
     info = _FitInfo()
     Jh = (ctypes.c_double * max(1, max_iter))() if history else None

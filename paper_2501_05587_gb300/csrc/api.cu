@@ -50,6 +50,7 @@ struct DeviceInfo {
     int sms = 0;
     int smem_optin = 0;
     int reduce_smem = 0;   // dynamic shared memory usable by the reduction kernel
+    int recompute_smem = 0;
     cudaMemPool_t pool = nullptr;
     bool ready = false;
 };
@@ -78,6 +79,7 @@ popcorn_status device_info(DeviceInfo** out) {
         POPCORN_CUDA(cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &thr));
         POPCORN_CUDA(configure_reduce_smem(d.smem_optin, &d.reduce_smem));
         POPCORN_CUDA(configure_kbuild_tc());
+        POPCORN_CUDA(configure_recompute(d.smem_optin, &d.recompute_smem));
         d.ready = true;
     }
     *out = &d;
@@ -220,6 +222,210 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 
 void popcorn::set_error_message(const char* msg) { g_err = msg; }
 
+
+namespace {
+
+// Kernel K-means without a stored K: operand rows once, then every pass
+// recomputes the tiles it needs (recompute.cu), reduces z and assigns.
+popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, int32_t k, const KernParams& kp,
+                             const int32_t* init_labels, int32_t max_iter, double tol, const popcorn_options& opt,
+                             int32_t* labels_out, double* objective_out, int32_t* iterations_out,
+                             popcorn_fit_info* info, cudaStream_t s, DeviceInfo* dev) {
+    const int ni = (int)n;
+    const RecomputePlan rp = plan_recompute(ni, d, k, opt.precision, dev->sms, dev->recompute_smem);
+    if (!rp.ok)
+        return fail(POPCORN_ERR_UNSUPPORTED, "the recompute path needs d <= %d (%s) and k <= 255",
+                    opt.precision == POPCORN_FP8 ? 512 : 256, opt.precision == POPCORN_FP8 ? "FP8" : "BF16");
+    const bool timing = opt.timing != 0;
+    int launches = 0;
+    int64_t h2d = 0, d2h = 0;
+    Workspace ws(dev->pool, s);
+    const float* Pd = P;
+    int64_t ldpd = ldp;
+    if (!is_device_pointer(P)) {
+        float* tmp;
+        POPCORN_TRY(ws.alloc(&tmp, (size_t)ni * d, "points"));
+        POPCORN_CUDA(cudaMemcpy2DAsync(tmp, (size_t)d * sizeof(float), P, (size_t)ldp * sizeof(float),
+                                       (size_t)d * sizeof(float), (size_t)ni, cudaMemcpyHostToDevice, s));
+        h2d += (int64_t)ni * d * sizeof(float);
+        Pd = tmp;
+        ldpd = d;
+    }
+    const int32_t* Ld = init_labels;
+    if (!is_device_pointer(init_labels)) {
+        int32_t* tmp;
+        POPCORN_TRY(ws.alloc(&tmp, (size_t)ni, "initial labels"));
+        POPCORN_CUDA(cudaMemcpyAsync(tmp, init_labels, (size_t)ni * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        h2d += (int64_t)ni * sizeof(int32_t);
+        Ld = tmp;
+    }
+    RecomputeBuffers rb{};
+    const int nb = recompute_sort_blocks(ni);
+    POPCORN_TRY(ws.alloc(&rb.Q, (size_t)ni * rp.row_bytes, "operand rows"));
+    POPCORN_TRY(ws.alloc(&rb.norms, (size_t)ni, "row norms"));
+    POPCORN_TRY(ws.alloc(&rb.knorms, (size_t)ni, "epilogue row norms"));
+    POPCORN_TRY(ws.alloc(&rb.scales, (size_t)ni, "row scales"));
+    POPCORN_TRY(ws.alloc(&rb.Qs, (size_t)rp.ncols * rp.row_bytes, "sorted operand rows"));
+    POPCORN_TRY(ws.alloc(&rb.snorm, (size_t)rp.ncols, "sorted norms"));
+    POPCORN_TRY(ws.alloc(&rb.sscale, (size_t)rp.ncols, "sorted scales"));
+    POPCORN_TRY(ws.alloc(&rb.slab, (size_t)rp.ncols, "sorted labels"));
+    POPCORN_TRY(ws.alloc(&rb.blockhist, (size_t)nb * k, "sort histograms"));
+    POPCORN_TRY(ws.alloc(&rb.blockoff, (size_t)nb * k, "sort offsets"));
+    PassBuffers b{};
+    float* kdiag;
+    POPCORN_TRY(ws.alloc(&kdiag, (size_t)ni, "diag(K)"));
+    const size_t nlab = ((size_t)ni + 15) & ~(size_t)15;
+    const int hist_len = max_iter > 0 ? max_iter : 1;
+    const int zblocks = (ni + kZReduceRows - 1) / kZReduceRows;
+    b.K = nullptr;
+    b.ldk = 0;
+    b.kdiag = kdiag;
+    b.n = ni;
+    b.k = k;
+    POPCORN_TRY(ws.alloc(&b.lab32, ni, "labels"));
+    POPCORN_TRY(ws.alloc(&b.lab8, nlab, "label bytes"));
+    POPCORN_TRY(ws.alloc(&b.counts, 2 * (size_t)k, "counts"));
+    POPCORN_TRY(ws.alloc(&b.Spart, (size_t)rp.nseg * ni * k, "segment sums"));
+    POPCORN_TRY(ws.alloc(&b.zpart, (size_t)zblocks * k, "block partials"));
+    POPCORN_TRY(ws.alloc(&b.zsum, (size_t)k, "z sums"));
+    POPCORN_TRY(ws.alloc(&b.cnorm, (size_t)k, "centroid norms"));
+    POPCORN_TRY(ws.alloc(&b.invm, (size_t)k, "inverse cluster sizes"));
+    POPCORN_TRY(ws.alloc(&b.st, 1, "loop state"));
+    POPCORN_TRY(ws.alloc(&b.J_hist, (size_t)hist_len, "objective history"));
+    POPCORN_TRY(ws.alloc(&b.changed_hist, (size_t)hist_len, "change history"));
+    b.E_out = nullptr;
+
+    g_events.used = 0;
+    cudaEvent_t ev_b0 = nullptr, ev_b1 = nullptr, ev_l1 = nullptr, ev_e1 = nullptr;
+    std::vector<cudaEvent_t> ev_r, ev_a;
+    if (timing) {
+        POPCORN_TRY(g_events.get(&ev_b0));
+        POPCORN_CUDA(cudaEventRecord(ev_b0, s));
+    }
+    POPCORN_CUDA(cudaMemsetAsync(b.counts, 0, 2 * (size_t)k * sizeof(int32_t), s));
+    // padding rows of the sorted copy are read by the MMAs (their results are skipped):
+    // keep them finite
+    POPCORN_CUDA(cudaMemsetAsync(rb.Qs, 0, (size_t)rp.ncols * rp.row_bytes, s));
+    POPCORN_CUDA(cudaMemsetAsync(rb.snorm, 0, (size_t)rp.ncols * sizeof(float), s));
+    POPCORN_CUDA(cudaMemsetAsync(rb.sscale, 0, (size_t)rp.ncols * sizeof(float), s));
+    POPCORN_CUDA(launch_init_state(b.st, max_iter, opt.check_convergence ? 1 : 0, tol, s));
+    POPCORN_CUDA(launch_quantize(Pd, ni, d, ldpd, kp, rp, rb, kdiag, s));
+    POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
+    POPCORN_CUDA(launch_init_labels(Ld, ni, k, b.lab32, b.lab8, b.counts, b.st, s));
+    launches += 4;
+    if (timing) {
+        POPCORN_TRY(g_events.get(&ev_b1));
+        POPCORN_CUDA(cudaEventRecord(ev_b1, s));
+    }
+    const int chunk = 4;
+    void* hpin;
+    POPCORN_TRY(pinned(2 * sizeof(int32_t) + sizeof(LoopState), &hpin));
+    volatile int32_t* hflag = static_cast<int32_t*>(hpin);
+    cudaEvent_t poll_ev[2] = {nullptr, nullptr};
+    if (opt.check_convergence) {
+        POPCORN_TRY(g_events.get(&poll_ev[0]));
+        POPCORN_TRY(g_events.get(&poll_ev[1]));
+    }
+    int launched = 0, pending = -1, slot = 0;
+    while (launched < max_iter) {
+        const int m = (max_iter - launched < chunk) ? (max_iter - launched) : chunk;
+        for (int t = 0; t < m; ++t) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+            if (timing) {
+                POPCORN_TRY(g_events.get(&e0));
+                POPCORN_TRY(g_events.get(&e1));
+                POPCORN_TRY(g_events.get(&e2));
+                POPCORN_CUDA(cudaEventRecord(e0, s));
+            }
+            cudaError_t e = launch_recompute_pass(b, kp, rp, rb, &b.st->kbuild_err, 0, s);
+            if (e == cudaErrorInvalidValue) return fail(POPCORN_ERR_CUDA, "tensor map creation failed");
+            POPCORN_CUDA(e);
+            POPCORN_CUDA(launch_zreduce(b, rp.nseg, 0, s));
+            if (timing) POPCORN_CUDA(cudaEventRecord(e1, s));
+            POPCORN_CUDA(launch_assign_nseg(b, rp.nseg, s));
+            if (timing) {
+                POPCORN_CUDA(cudaEventRecord(e2, s));
+                ev_r.push_back(e0);
+                ev_r.push_back(e1);
+                ev_a.push_back(e1);
+                ev_a.push_back(e2);
+            }
+            launches += 6;
+        }
+        launched += m;
+        if (opt.check_convergence && launched < max_iter) {
+            POPCORN_CUDA(cudaMemcpyAsync((void*)(hflag + slot), &b.st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            POPCORN_CUDA(cudaEventRecord(poll_ev[slot], s));
+            if (pending >= 0) {
+                POPCORN_CUDA(cudaEventSynchronize(poll_ev[pending]));
+                if (hflag[pending]) break;
+            }
+            pending = slot;
+            slot ^= 1;
+        }
+    }
+    if (timing) {
+        POPCORN_TRY(g_events.get(&ev_l1));
+        POPCORN_CUDA(cudaEventRecord(ev_l1, s));
+    }
+    {
+        cudaError_t e = launch_recompute_pass(b, kp, rp, rb, &b.st->kbuild_err, 1, s);
+        if (e == cudaErrorInvalidValue) return fail(POPCORN_ERR_CUDA, "tensor map creation failed");
+        POPCORN_CUDA(e);
+        POPCORN_CUDA(launch_zreduce(b, rp.nseg, 1, s));
+        launches += 5;
+    }
+    if (timing) {
+        POPCORN_TRY(g_events.get(&ev_e1));
+        POPCORN_CUDA(cudaEventRecord(ev_e1, s));
+    }
+    LoopState* hs_pin = reinterpret_cast<LoopState*>(static_cast<char*>(hpin) + 2 * sizeof(int32_t));
+    POPCORN_CUDA(cudaMemcpyAsync(hs_pin, b.st, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+    d2h += sizeof(LoopState);
+    if (is_device_pointer(labels_out)) {
+        POPCORN_CUDA(cudaMemcpyAsync(labels_out, b.lab32, (size_t)ni * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    } else {
+        POPCORN_CUDA(cudaMemcpyAsync(labels_out, b.lab32, (size_t)ni * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        d2h += (int64_t)ni * sizeof(int32_t);
+    }
+    POPCORN_CUDA(cudaStreamSynchronize(s));
+    LoopState hs;
+    memcpy(&hs, hs_pin, sizeof hs);
+    if (hs.bad_label) return fail(POPCORN_ERR_INVALID, "an initial label is outside [0, %d)", k);
+    if (hs.kbuild_err) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the recompute kernel ran out");
+    *objective_out = hs.J_eval;
+    *iterations_out = hs.iter;
+    if (info) {
+        const int iters = hs.iter;
+        if (iters > 0 && info->J_history)
+            POPCORN_CUDA(cudaMemcpy(info->J_history, b.J_hist, (size_t)iters * sizeof(double), cudaMemcpyDeviceToHost));
+        if (iters > 0 && info->changed_history)
+            POPCORN_CUDA(cudaMemcpy(info->changed_history, b.changed_hist, (size_t)iters * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost));
+        const bool eval_ran = !(hs.iter > 0 && hs.last_changed == 0);
+        info->converged = hs.converged;
+        info->kernel_launches = launches;
+        info->reduce_launches = iters + (eval_ran ? 1 : 0);
+        info->assign_launches = iters;
+        info->h2d_bytes = h2d;
+        info->d2h_bytes = d2h;
+        info->kbuild_ms = info->loop_ms = info->reduce_ms = info->assign_ms = info->eval_ms = 0.0;
+        if (timing) {
+            info->kbuild_ms = elapsed(ev_b0, ev_b1);
+            info->loop_ms = elapsed(ev_b1, ev_l1);
+            info->eval_ms = elapsed(ev_l1, ev_e1);
+            double r = 0, a2 = 0;
+            for (size_t t = 0; t + 1 < ev_r.size() && t < 2 * (size_t)iters; t += 2) r += elapsed(ev_r[t], ev_r[t + 1]);
+            for (size_t t = 0; t + 1 < ev_a.size() && t < 2 * (size_t)iters; t += 2) a2 += elapsed(ev_a[t], ev_a[t + 1]);
+            info->reduce_ms = r;
+            info->assign_ms = a2;
+        }
+    }
+    return POPCORN_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* popcorn_status_string(popcorn_status status) {
@@ -355,11 +561,18 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
     for (int r = 0; r < 6; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
-    if (opt.store_k != 1) return fail(POPCORN_ERR_UNSUPPORTED, "store_k = 0 (recompute path) is not available in this build");
+    if (opt.store_k != 0 && opt.store_k != 1) return fail(POPCORN_ERR_INVALID, "store_k must be 0 or 1");
+    if (opt.store_k == 0 && opt.precision != POPCORN_BF16 && opt.precision != POPCORN_FP8)
+        return fail(POPCORN_ERR_UNSUPPORTED, "the recompute path (store_k = 0) runs in POPCORN_BF16 or POPCORN_FP8");
+    if (opt.store_k == 1 && opt.precision == POPCORN_FP8)
+        return fail(POPCORN_ERR_UNSUPPORTED, "POPCORN_FP8 is available on the recompute path (store_k = 0) only");
     KernParams kp;
     POPCORN_TRY(check_kernel(kern, &kp));
     DeviceInfo* dev;
     POPCORN_TRY(device_info(&dev));
+    if (opt.store_k == 0)
+        return fit_recompute(P, n, d, ldp, k, kp, init_labels, max_iter, tol, opt, labels_out, objective_out,
+                             iterations_out, info, s, dev);
     const int ni = (int)n;
     const int64_t ldk = (n + 3) / 4 * 4;
     ReducePlan plan = plan_reduce(ni, k, dev->sms, dev->reduce_smem);

@@ -88,6 +88,36 @@ __device__ __forceinline__ float butterfly(const float (&acc)[KB], int lane) {
     return v[0];
 }
 
+// Last block of a pass's reduction, all its threads: sum the per-block FP64
+// partials of sum_{i in L_c} S_ic in block order, then ||c_c||^2 =
+// (1/m_c^2) sum_{i in L_c} S_ic (Eq. 13/14), 1/m_c, and
+// J = trace K - sum_c (1/m_c) sum_{i in L_c} S_ic.
+__device__ void finalize_pass(const double* zpart, int nblocks, int k, const int32_t* counts, double* zsum,
+                              double* cnorm, double* invm, LoopState* st, double* J_hist, int eval_only) {
+    const int32_t* m = counts + (size_t)(st->iter & 1) * k;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < nblocks; ++b) t += __ldcg(zpart + (size_t)b * k + c);
+        const double mc = (double)__ldcg(m + c);
+        const double inv = mc > 0 ? 1.0 / mc : 0.0;
+        zsum[c] = t;
+        invm[c] = inv;
+        cnorm[c] = t * inv * inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double J = st->trace;
+        for (int c = 0; c < k; ++c) J -= __ldcg(zsum + c) * __ldcg(invm + c);
+        if (eval_only) {
+            st->J_eval = J;
+        } else {
+            J_hist[st->iter] = J;
+            st->J_last = J;
+        }
+        st->reduce_ticket = 0u;
+    }
+}
+
 struct ReduceArgs {
     const float* K;
     int64_t ldk;
@@ -266,31 +296,7 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceA
     if (!am_last) return;
     __threadfence();
 
-    // last block: ||c_c||^2 = (1/m_c^2) sum_{i in L_c} S_ic, J = trace K - sum_c (1/m_c) sum_{i in L_c} S_ic
-    const int32_t* m = a.counts + (size_t)(st->iter & 1) * k;
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        double t = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(a.zpart + (size_t)b * k + c);
-        const double mc = (double)__ldcg(m + c);
-        const double inv = mc > 0 ? 1.0 / mc : 0.0;
-        a.zsum[c] = t;
-        a.invm[c] = inv;
-        a.cnorm[c] = t * inv * inv;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double J = st->trace;
-        for (int c = 0; c < k; ++c) {
-            J -= __ldcg(a.zsum + c) * __ldcg(a.invm + c);
-        }
-        if (a.eval_only) {
-            st->J_eval = J;
-        } else {
-            a.J_hist[st->iter] = J;
-            st->J_last = J;
-        }
-        st->reduce_ticket = 0u;
-    }
+    finalize_pass(a.zpart, (int)gridDim.x, k, a.counts, a.zsum, a.cnorm, a.invm, st, a.J_hist, a.eval_only);
 }
 
 struct AssignArgs {
@@ -383,6 +389,61 @@ __global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) {
         st->done = done;
         st->assign_ticket = 0u;
     }
+}
+
+
+// sum_{i in L_c} S_ic for the recompute path, from Spart[i][s][c]: a block takes
+// kZReduceRows consecutive rows; thread c sums its cluster's rows in row
+// order (deterministic), then the last block finalizes the pass.
+struct ZArgs {
+    int n, k, nseg;
+    const float* Spart;
+    const uint8_t* lab8;
+    double* zpart;
+    double* zsum;
+    double* cnorm;
+    double* invm;
+    const int32_t* counts;
+    LoopState* st;
+    double* J_hist;
+    int eval_only;
+};
+
+__global__ void __launch_bounds__(kZReduceRows) zreduce_kernel(ZArgs a) {
+    LoopState* st = a.st;
+    if (pass_skip(st, a.eval_only)) {
+        if (a.eval_only && blockIdx.x == 0 && threadIdx.x == 0) st->J_eval = st->J_last;
+        return;
+    }
+    __shared__ int lab_s[kZReduceRows];
+    __shared__ double val_s[kZReduceRows];
+    __shared__ int am_last;
+    const int i = blockIdx.x * kZReduceRows + threadIdx.x;
+    int l = -1;
+    double v = 0.0;
+    if (i < a.n) {
+        l = a.lab8[i];
+        const float* Si = a.Spart + (int64_t)i * a.nseg * a.k + l;
+        float hi = 0.f, lo = 0.f;
+        for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[(int64_t)s * a.k]);
+        v = (double)hi + (double)lo;
+    }
+    lab_s[threadIdx.x] = l;
+    val_s[threadIdx.x] = v;
+    __syncthreads();
+    for (int c = threadIdx.x; c < a.k; c += blockDim.x) {
+        double t = 0.0;
+        for (int r = 0; r < kZReduceRows; ++r)
+            if (lab_s[r] == c) t += val_s[r];
+        a.zpart[(size_t)blockIdx.x * a.k + c] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(&st->reduce_ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    finalize_pass(a.zpart, (int)gridDim.x, a.k, a.counts, a.zsum, a.cnorm, a.invm, st, a.J_hist, a.eval_only);
 }
 
 __global__ void init_state_kernel(LoopState* st, int max_iter, int check_conv, double tol) {
@@ -526,6 +587,31 @@ cudaError_t launch_reduce(const PassBuffers& b, const ReducePlan& plan, int eval
     a.eval_only = eval_only;
     reduce_fn(plan.variant, plan.labels_in_smem)<<<plan.grid, plan.warps * 32, plan.smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_t s) {
+    ZArgs a;
+    a.n = b.n;
+    a.k = b.k;
+    a.nseg = nseg;
+    a.Spart = b.Spart;
+    a.lab8 = b.lab8;
+    a.zpart = b.zpart;
+    a.zsum = b.zsum;
+    a.cnorm = b.cnorm;
+    a.invm = b.invm;
+    a.counts = b.counts;
+    a.st = b.st;
+    a.J_hist = b.J_hist;
+    a.eval_only = eval;
+    zreduce_kernel<<<(b.n + kZReduceRows - 1) / kZReduceRows, kZReduceRows, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s) {
+    ReducePlan p{};
+    p.nseg = nseg;
+    return launch_assign(b, p, s);
 }
 
 cudaError_t launch_assign(const PassBuffers& b, const ReducePlan& plan, cudaStream_t s) {

@@ -31,16 +31,21 @@
 #include <cuda_runtime.h>
 
 #include "popcorn_internal.cuh"
+#include "tc_common.cuh"
 
 namespace popcorn {
 namespace {
+
+using namespace tc;
+
+__device__ __forceinline__ void epi_bar() { named_bar<128>(1); }   // the 4 epilogue warps
+constexpr uint32_t kIdesc = idesc_bf16(128, 128);
 
 constexpr int BM = 128, BN = 128, BK = 64;   // tile rows, tile cols, bf16 depth per stage
 constexpr int STAGES = 4;
 constexpr int TILE_BYTES = BM * BK * 2;      // 16 KB per operand tile
 constexpr int STG_BYTES = 128 * 32 * 4;      // one 128 x 32 FP32 staging chunk
 constexpr int NTHREADS = 192;                // 6 warps
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 // shared-memory layout (offsets from a 1024-aligned base)
 constexpr int OFF_A = 0;
@@ -61,137 +66,6 @@ struct TcArgs {
     float* kdiag;
     int* err;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: false when this CTA aborted (here or in another role).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63) == 0) {
-            if (*abort_flag) return false;
-            if (globaltimer() - t0 > kWaitLimitNs) {
-                *abort_flag = 1;
-                atomicExch(err, 1);
-                return false;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
-                 ::"l"(map), "r"(x), "r"(y), "r"(src)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void bulk_wait_read() {
-    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void epi_bar() {   // named barrier over the 4 epilogue warps
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row core groups 1024 bytes apart (SBO); LBO unused for this
-// layout (encoded 1); descriptor version 1 (bits 46-47); swizzle mode 2.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int x = 0; x < 32; ++x) v[x] = __uint_as_float(r[x]);
-}
 
 __device__ __forceinline__ void tri_coords(long long t, int T, int* bi, int* bj) {
     double Td = (double)T;
@@ -327,7 +201,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         // 16 bf16 = 32 bytes further along K inside the 128-byte swizzled row
-                        mma_bf16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), (kb | kk) ? 1u : 0u);
+                        mma_bf16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), kIdesc, (kb | kk) ? 1u : 0u);
                     }
                     mma_commit(empty_bar(stage));   // stage free once these MMAs have read it
                     if (++stage == STAGES) {
@@ -363,9 +237,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 rj_s[et] = j < a.n ? a.norms[j] : 0.f;
             }
             if (!mbar_wait(accf_bar(ab), use & 1u, abort_flag, a.err)) ok = false;
-            // all epilogue threads must agree before touching TMEM or the staging buffers
-            epi_bar();
-            if (!ok || *abort_flag) {
+            // all epilogue threads agree (one barrier, one AND) before touching TMEM or staging
+            if (!named_bar_all(1, 128, ok && !*abort_flag)) {
                 ok = false;
                 break;
             }
@@ -465,6 +338,8 @@ __global__ void __launch_bounds__(256) prep_operands_kernel(const float* __restr
     if (lane == 0) norms[warp] = nrm;
 }
 
+}  // namespace
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -479,7 +354,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap* m, CUtensorMapDataType dt, void* base, uint64_t inner, uint64_t outer,
+bool make_tensor_map_2d(CUtensorMap* m, CUtensorMapDataType dt, void* base, uint64_t inner, uint64_t outer,
               uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle sw) {
     auto fn = encode_fn();
     if (!fn) return false;
@@ -491,7 +366,6 @@ bool make_map(CUtensorMap* m, CUtensorMapDataType dt, void* base, uint64_t inner
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-}  // namespace
 
 size_t kbuild_tc_workspace(int n, int d, int precision) {
     const size_t dpad = ((size_t)d + BK - 1) / BK * BK;
@@ -522,13 +396,13 @@ cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernPara
     if (launches) ++*launches;
 
     CUtensorMap ma, mb, mkd, mkt;
-    if (!make_map(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, (uint64_t)lda, (uint64_t)n, (uint64_t)lda * 2, BK, BM,
+    if (!make_tensor_map_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, (uint64_t)lda, (uint64_t)n, (uint64_t)lda * 2, BK, BM,
                   CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !make_map(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, x3 ? B : A, (uint64_t)lda, (uint64_t)n, (uint64_t)lda * 2,
+        !make_tensor_map_2d(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, x3 ? B : A, (uint64_t)lda, (uint64_t)n, (uint64_t)lda * 2,
                   BK, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !make_map(&mkd, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, K, (uint64_t)n, (uint64_t)n, (uint64_t)ldk * 4, 32, BM,
+        !make_tensor_map_2d(&mkd, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, K, (uint64_t)n, (uint64_t)n, (uint64_t)ldk * 4, 32, BM,
                   CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !make_map(&mkt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, K, (uint64_t)n, (uint64_t)n, (uint64_t)ldk * 4, BM, 32,
+        !make_tensor_map_2d(&mkt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, K, (uint64_t)n, (uint64_t)n, (uint64_t)ldk * 4, BM, 32,
                   CU_TENSOR_MAP_SWIZZLE_NONE))
         return cudaErrorInvalidValue;
 

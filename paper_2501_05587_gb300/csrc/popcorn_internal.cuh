@@ -1,6 +1,7 @@
 // Internal declarations of the CUDA path (not part of the public ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -77,6 +78,59 @@ cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernPara
                              int64_t ldk, float* kdiag, void* workspace, int* err, int num_sms, cudaStream_t s,
                              int* launches);
 
+// 2-D tiled TMA descriptor over a row-major matrix (inner = contiguous extent
+// in elements, row_bytes = pitch); false if the driver entry point is missing
+// or rejects the arguments.
+bool make_tensor_map_2d(CUtensorMap* m, CUtensorMapDataType dt, void* base, uint64_t inner, uint64_t outer,
+                        uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle sw);
+
+// Dynamic shared memory a kernel may request next to `static_bytes` of its own.
+inline int optin_minus_static(int optin, size_t static_bytes) {
+    return optin - (int)((static_bytes + 127) / 128 * 128);
+}
+
+// A pass kernel returns at once when the loop has stopped (ordinary passes) or
+// when the final objective is already known (eval pass: the last pass
+// changed no label, so J(labels_out) = J of that pass).
+__device__ __forceinline__ bool pass_skip(const LoopState* st, int eval) {
+    return eval ? (st->iter > 0 && st->last_changed == 0) : (st->done != 0);
+}
+
+// ---- recompute path (recompute.cu): K never stored ---------------------------
+struct RecomputePlan {
+    int fp8;            // 1: E4M3 operands with per-row scales; 0: BF16
+    int dpad;           // padded feature count (elements)
+    int row_bytes;      // operand row pitch in bytes (multiple of 128)
+    int nkb;            // 128-byte k-blocks per row
+    int npad;           // n rounded up to 128
+    int ncols;          // sorted column space: n + 31 k rounded up to 128 (clusters padded to 32)
+    int nseg, seglen;   // column segments (units = row blocks x segments)
+    int stages;         // column k-block ring depth
+    int eg;             // epilogue warpgroups (1 or 2)
+    int threads;        // 64 + 128 * eg
+    int off_b, off_meta, off_acc, off_bar, off_misc;
+    int smem;
+    int grid;
+    bool ok;            // false: d or k too large for this path
+};
+
+struct RecomputeBuffers {
+    unsigned char* Q;     // n x row_bytes operand rows, original order
+    float* norms;         // n FP32 norms of the represented rows
+    float* knorms;        // n norms as the epilogue uses them (c2-scaled for the Gaussian)
+    float* scales;        // n row scales (1 for BF16)
+    unsigned char* Qs;    // ncols x row_bytes, cluster order, each cluster padded to 32 rows
+    float* snorm;         // ncols epilogue norms in cluster order
+    float* sscale;        // ncols scales in cluster order
+    uint8_t* slab;        // ncols labels in cluster order (0xFF on padding)
+    int* blockhist;       // sort blocks x k
+    int* blockoff;        // sort blocks x k
+};
+
+RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, int smem_budget);
+cudaError_t configure_recompute(int smem_optin, int* usable);
+int recompute_sort_blocks(int n);
+
 // ---- iteration kernels (iterate.cu) -----------------------------------------
 // Opt the reduction kernels into the largest dynamic shared memory the device
 // allows (call once per device, with it current, before plan_reduce);
@@ -109,9 +163,21 @@ struct PassBuffers {
     float* E_out;         // optional n x k
 };
 
+// Operand rows for the recompute path, their norms and scales, and diag K.
+cudaError_t launch_quantize(const float* P, int n, int d, int64_t ldp, KernParams kp, const RecomputePlan& p,
+                            const RecomputeBuffers& rb, float* kdiag, cudaStream_t s);
+// Sort by label + fused tile/kernel/segment-sum kernel -> b.Spart.
+cudaError_t launch_recompute_pass(const PassBuffers& b, KernParams kp, const RecomputePlan& p,
+                                  const RecomputeBuffers& rb, int* err, int eval, cudaStream_t s);
+// sum_{i in L_c} S_ic from b.Spart (nseg segments) and the pass finalization
+// (||c||^2, 1/|L_c|, J); blocks of kZReduceRows rows.
+constexpr int kZReduceRows = 1024;
+cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_t s);
+
 // One assignment pass = reduction (E, z, J) + distance/argmin.
 cudaError_t launch_reduce(const PassBuffers& b, const ReducePlan& plan, int eval_only,
                           cudaStream_t s);
 cudaError_t launch_assign(const PassBuffers& b, const ReducePlan& plan, cudaStream_t s);
+cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s);
 
 }  // namespace popcorn

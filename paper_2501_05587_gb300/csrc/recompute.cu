@@ -1,0 +1,679 @@
+// Recompute path: Kernel K-means passes without a stored K.
+//
+// The paper stores K (Sec. 4.2), which caps n at what HBM holds.  This path
+// recomputes, every pass, the tiles of B = Q Q^T that the K stream would read
+// (Q = the points in BF16, or FP8 E4M3 with a per-row scale), applies kappa in
+// the epilogue and folds the result straight into the per-row cluster sums
+// S_ic = sum_{j in L_c} K_ij -- the quantity the paper's SpMM produces (Alg. 2
+// line 7).  The columns are visited in cluster order: each pass first sorts
+// the points by label (a stable counting sort) and gathers their operand rows,
+// so a 128-column block spans only a few runs of equal labels and every
+// thread adds kappa into a running register sum, flushing it to its
+// shared-memory accumulator only when the (warp-uniform) label changes.
+//
+// Per pass:  sort_hist -> sort_scan -> sort_scatter (gather) -> recompute_kernel
+//            -> zreduce (iterate.cu) -> assign (iterate.cu).
+//
+// recompute_kernel: one persistent CTA per SM, 192 threads:
+//   warp 0   TMA: the unit's 128-row block of Q once (resident), then the
+//            column blocks' k-blocks through a ring;
+//   warp 1   tcgen05.mma (kind::f16 for BF16, kind::f8f6f4 for E4M3) into one
+//            of two 128-column TMEM accumulators;
+//   warps 2-5  epilogue: tcgen05.ld, dequantize (FP8: s_i s_j), kappa, run sums.
+// A unit is (row block, column segment); its sums go to Spart[i][s][c], the
+// layout the assign kernel reads.  All waits are bounded as in kbuild_tc.cu.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include "popcorn_internal.cuh"
+#include "tc_common.cuh"
+
+namespace popcorn {
+namespace {
+
+using namespace tc;
+
+constexpr int RM = 128;                 // rows per block (MMA M)
+constexpr int RN = 128;                 // columns per block (MMA N)
+constexpr int KBB = 128;                // operand bytes per row per k-block (64 BF16 / 128 E4M3)
+constexpr int KB_TILE = RM * KBB;       // 16 KB
+constexpr int kNoLabel = 0xFF;          // padding columns beyond n
+constexpr int MS = 4;                   // column-metadata ring slots
+constexpr int META_LAB = 0, META_KN = 128, META_SC = 128 + 512, META_BYTES = 128 + 512 + 512;
+
+struct RcArgs {
+    int n, ncols, nseg, seglen, nkb, k, fp8, eg;   // ncols: padded column space (multiple of 128)
+    int stages;                         // B ring depth
+    int off_b, off_meta, off_acc, off_bar, off_misc;   // shared-memory layout (bytes from the aligned base)
+    KernParams kp;
+    const float* rnorm;                 // row norms of the represented rows, original order
+    const float* rscale;                // FP8 row scales, original order (1 for BF16)
+    const uint8_t* slab;                // npad labels in sorted order, kNoLabel past n
+    const float* sknorm;                // npad: c2 * norm (Gaussian; raw norm otherwise), sorted order, 0 past n
+    const float* sscale;                // npad scales in sorted order, 0 past n
+    float* Spart;                       // [n][nseg][k]
+    LoopState* st;
+    int* err;
+    int eval;                           // 1: the final objective pass (runs after the loop stopped)
+};
+
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// kappa of one accumulator value b for row constants (ar, si) and column
+// constants (kn, sj); Gaussian: exp2(min(c2 (r_i + r_j) - 2 c2 b', 0)) with
+// b' = b (BF16) or s_i s_j b (FP8) and c2 = -gamma log2(e) / sigma^2.  A
+// padding column has kn = -inf: the Gaussian term is exp2(-inf) = 0 by
+// itself, the other kernels are masked.
+template <bool FP8, int KIND>
+__device__ __forceinline__ float kappa_rc(float b, float ar, float si, float kn, float sj, float m2c2,
+                                          const KernParams& kp) {
+    if (KIND == POPCORN_GAUSSIAN) {
+        const float coef = FP8 ? m2c2 * si * sj : m2c2;
+        return ex2(fminf(fmaf(coef, b, ar + kn), 0.f));
+    }
+    const float bb = FP8 ? b * (si * sj) : b;
+    float r = bb;
+    if (KIND == POPCORN_POLYNOMIAL) {
+        const float base = fmaf(kp.gamma, bb, kp.coef0);
+        r = base;
+        for (int e = 1; e < kp.degree; ++e) r *= base;
+    }
+    return kn == -INFINITY ? 0.f : r;
+}
+
+template <bool FP8, int KIND>
+__global__ void __launch_bounds__(64 + 256, 1)
+    recompute_kernel(const __grid_constant__ CUtensorMap map_rows, const __grid_constant__ CUtensorMap map_cols,
+                     RcArgs a) {
+    if (pass_skip(a.st, a.eval)) return;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t sbase = smem_u32(smem);
+    const int S = a.stages;
+    const int EW = 4 * a.eg;            // epilogue warps
+    const uint32_t bar0 = sbase + a.off_bar;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * S + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
+    auto mfull_bar = [&](int m) { return bar0 + 8u * (2 * S + 4 + m); };
+    auto mempty_bar = [&](int m) { return bar0 + 8u * (2 * S + 4 + MS + m); };
+    const uint32_t afull_bar = bar0 + 8u * (2 * S + 4 + 2 * MS);
+    const uint32_t aempty_bar = afull_bar + 8u;
+    const uint32_t down_bar = afull_bar + 16u;
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(smem + a.off_misc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + a.off_misc + 4);
+    unsigned char* meta = smem + a.off_meta;
+    float* acc_s = reinterpret_cast<float*>(smem + a.off_acc);   // [eg][k][128]
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf_bar(b), 1);
+            mbar_init(acce_bar(b), EW);
+        }
+        for (int m = 0; m < MS; ++m) {
+            mbar_init(mfull_bar(m), 1);
+            mbar_init(mempty_bar(m), EW);
+        }
+        mbar_init(afull_bar, 1);
+        mbar_init(aempty_bar, 1);
+        mbar_init(down_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32((const void*)tmem_slot)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int T = (a.n + RM - 1) / RM;
+    const int units = T * a.nseg;
+    const int G = gridDim.x;
+    auto unit_cols = [&](int u, int* I, int* s, int* jb0, int* jb1) {
+        *I = u / a.nseg;
+        *s = u - *I * a.nseg;
+        const int c0 = *s * a.seglen;
+        const int c1 = min(a.ncols, c0 + a.seglen);
+        *jb0 = c0 / RN;
+        *jb1 = (c1 + RN - 1) / RN;
+    };
+    constexpr uint32_t idesc = FP8 ? idesc_e4m3(RM, RN) : idesc_bf16(RM, RN);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer: row block, column metadata, column k-blocks ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            int ucount = 0, bc = 0;
+            bool ok = true;
+            bool a_issued = false;
+            uint32_t a_parity = 0;
+            uint32_t issued_mask = 0, issued_par = 0;    // per B stage
+            uint32_t missued_mask = 0, missued_par = 0;  // per metadata slot
+            for (int u = blockIdx.x; u < units && ok; u += G, ++ucount) {
+                int I, s, jb0, jb1;
+                unit_cols(u, &I, &s, &jb0, &jb1);
+                if (!mbar_wait(aempty_bar, ((uint32_t)ucount & 1u) ^ 1u, abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(afull_bar, (uint32_t)(a.nkb * KB_TILE));
+                for (int kb = 0; kb < a.nkb; ++kb)
+                    tma_load_2d(sbase + kb * KB_TILE, &map_rows, kb * (FP8 ? KBB : KBB / 2), I * RM, afull_bar);
+                a_issued = true;
+                a_parity = (uint32_t)ucount & 1u;
+                for (int jb = jb0; jb < jb1 && ok; ++jb, ++bc) {
+                    const int ms = bc % MS;
+                    const uint32_t mpar = (uint32_t)(bc / MS) & 1u;
+                    if (!mbar_wait(mempty_bar(ms), mpar ^ 1u, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t mdst = sbase + a.off_meta + ms * META_BYTES;
+                    mbar_arrive_expect_tx(mfull_bar(ms), META_BYTES);
+                    bulk_load_1d(mdst + META_LAB, a.slab + (size_t)jb * RN, 128, mfull_bar(ms));
+                    bulk_load_1d(mdst + META_KN, a.sknorm + (size_t)jb * RN, 512, mfull_bar(ms));
+                    bulk_load_1d(mdst + META_SC, a.sscale + (size_t)jb * RN, 512, mfull_bar(ms));
+                    missued_mask |= 1u << ms;
+                    missued_par = (missued_par & ~(1u << ms)) | (mpar << ms);
+                    for (int kb = 0; kb < a.nkb; ++kb) {
+                        if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(full_bar(stage), KB_TILE);
+                        tma_load_2d(sbase + a.off_b + stage * KB_TILE, &map_cols, kb * (FP8 ? KBB : KBB / 2),
+                                    jb * RN, full_bar(stage));
+                        issued_mask |= 1u << stage;
+                        issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
+                        if (++stage == S) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                // aborted: let this CTA's own copies land before shared memory goes away
+                auto drain = [&](uint32_t bar, uint32_t par) {
+                    const unsigned long long t0 = globaltimer();
+                    while (!mbar_try_wait(bar, par) && globaltimer() - t0 < kWaitLimitNs) {
+                    }
+                };
+                for (int s2 = 0; s2 < S; ++s2)
+                    if (issued_mask >> s2 & 1u) drain(full_bar(s2), issued_par >> s2 & 1u);
+                for (int m = 0; m < MS; ++m)
+                    if (missued_mask >> m & 1u) drain(mfull_bar(m), missued_par >> m & 1u);
+                if (a_issued) drain(afull_bar, a_parity);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            int ucount = 0, bc = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < units && ok; u += G, ++ucount) {
+                int I, s, jb0, jb1;
+                unit_cols(u, &I, &s, &jb0, &jb1);
+                if (!mbar_wait(afull_bar, (uint32_t)ucount & 1u, abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                for (int jb = jb0; jb < jb1 && ok; ++jb, ++bc) {
+                    const int ab = bc & 1;
+                    if (!mbar_wait(acce_bar(ab), ((uint32_t)(bc >> 1) & 1u) ^ 1u, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem + (uint32_t)(ab * RN);
+                    for (int kb = 0; kb < a.nkb; ++kb) {
+                        if (!mbar_wait(full_bar(stage), phase, abort_flag, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = sbase + kb * KB_TILE;
+                        const uint32_t sb = sbase + a.off_b + stage * KB_TILE;
+#pragma unroll
+                        for (int kk = 0; kk < KBB / 32; ++kk) {   // 32 bytes of K per instruction
+                            if (FP8)
+                                mma_e4m3(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
+                                         (kb | kk) ? 1u : 0u);
+                            else
+                                mma_bf16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
+                                         (kb | kk) ? 1u : 0u);
+                        }
+                        mma_commit(empty_bar(stage));
+                        if (++stage == S) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit(accf_bar(ab));
+                }
+                mma_commit(aempty_bar);   // the resident row block is free once these MMAs finish
+            }
+            mma_commit(down_bar);
+            const unsigned long long t0 = globaltimer();
+            while (!mbar_try_wait(down_bar, 0) && globaltimer() - t0 < kWaitLimitNs) {
+            }
+        }
+    } else if (warp < 2 + EW) {
+        // ---------------- epilogue: EG warpgroups, group g takes chunks g, g + EG, ... ----------------
+        const int g = (warp - 2) >> 2;
+        const int q = warp & 3;
+        const int row_local = 32 * q + lane;
+        float* myacc = acc_s + (size_t)g * a.k * 128 + row_local;   // column row_local of acc_g[k][128]
+        const float m2c2 = -2.f * a.kp.neg_gamma_over_sigma2 * 1.4426950408889634f;
+        const float c2 = a.kp.neg_gamma_over_sigma2 * 1.4426950408889634f;
+        const KernParams kp = a.kp;
+        const int nch = (RN / 32) / a.eg;            // chunks per group per block
+        int bc = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < units && ok; u += G) {
+            int I, s, jb0, jb1;
+            unit_cols(u, &I, &s, &jb0, &jb1);
+            const int row = I * RM + row_local;
+            const float ar = row < a.n ? (KIND == POPCORN_GAUSSIAN ? c2 * a.rnorm[row] : 0.f) : 0.f;
+            const float si = row < a.n ? a.rscale[row] : 0.f;
+            for (int c = 0; c < a.k; ++c) myacc[c * 128] = 0.f;
+            int cur = kNoLabel;
+            float run = 0.f;
+            for (int jb = jb0; jb < jb1; ++jb, ++bc) {
+                const int ab = bc & 1;
+                const int ms = bc % MS;
+                bool got = mbar_wait(mfull_bar(ms), (uint32_t)(bc / MS) & 1u, abort_flag, a.err);
+                got = got && mbar_wait(accf_bar(ab), (uint32_t)(bc >> 1) & 1u, abort_flag, a.err);
+                if (__any_sync(0xffffffffu, !got)) {
+                    ok = false;   // leave the block loop; the unit-end barrier below is still reached
+                    break;
+                }
+                tc_fence_after();
+                const unsigned char* mp = meta + ms * META_BYTES;
+                const uint8_t* ml = mp + META_LAB;
+                const float* mk = reinterpret_cast<const float*>(mp + META_KN);
+                const float* msc = reinterpret_cast<const float*>(mp + META_SC);
+                for (int h = 0; h < nch; h += 2) {
+                    // two chunks per TMEM round trip
+                    const int ca = g + a.eg * h, cb = g + a.eg * (h + 1);
+                    uint32_t ra[32], rb[32];
+                    tmem_ld32_nowait(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * RN + 32 * ca), ra);
+                    tmem_ld32_nowait(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * RN + 32 * cb), rb);
+                    tmem_ld_wait();
+                    if (h + 2 >= nch) {
+                        // this warp has read its share of the accumulator
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acce_bar(ab));
+                    }
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        // every cluster's run of columns is padded to a multiple of 32, so a
+                        // chunk holds one label (kNoLabel: padding, skipped)
+                        const int ch = half ? cb : ca;
+                        const uint32_t* r = half ? rb : ra;
+                        const int lab = ml[32 * ch];
+                        if (lab == kNoLabel) continue;
+                        const float* kn = mk + 32 * ch;
+                        const float* sc = msc + 32 * ch;
+                        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+                        for (int x = 0; x < 32; x += 4) {
+                            p0 += kappa_rc<FP8, KIND>(__uint_as_float(r[x]), ar, si, kn[x], sc[x], m2c2, kp);
+                            p1 += kappa_rc<FP8, KIND>(__uint_as_float(r[x + 1]), ar, si, kn[x + 1], sc[x + 1], m2c2, kp);
+                            p2 += kappa_rc<FP8, KIND>(__uint_as_float(r[x + 2]), ar, si, kn[x + 2], sc[x + 2], m2c2, kp);
+                            p3 += kappa_rc<FP8, KIND>(__uint_as_float(r[x + 3]), ar, si, kn[x + 3], sc[x + 3], m2c2, kp);
+                        }
+                        if (lab != cur) {   // warp-uniform
+                            if (cur != kNoLabel) myacc[cur * 128] += run;
+                            cur = lab;
+                            run = 0.f;
+                        }
+                        run += (p0 + p1) + (p2 + p3);
+                    }
+                }
+                // this warp is done with the metadata slot
+                __syncwarp();
+                if (lane == 0) mbar_arrive(mempty_bar(ms));
+            }
+            if (ok && cur != kNoLabel) myacc[cur * 128] += run;
+            // every epilogue warp arrives here once per unit, aborted or not; the AND tells
+            // all of them whether to go on.  Then group 0 combines the groups' accumulators.
+            if (!named_bar_all(1, 128 * a.eg, ok && !*abort_flag)) {
+                ok = false;
+                break;
+            }
+            if (g == 0 && row < a.n) {
+                float* out = a.Spart + ((int64_t)row * a.nseg + s) * a.k;
+                for (int c = 0; c < a.k; ++c) {
+                    float v = myacc[c * 128];
+                    for (int g2 = 1; g2 < a.eg; ++g2) v += myacc[(size_t)g2 * a.k * 128 + c * 128];
+                    out[c] = v;
+                }
+            }
+            named_bar_n(1, 128 * a.eg);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- operand preparation (once per fit)
+// One warp per row: BF16 copy (or E4M3 with scale amax/448), the represented
+// row's FP32 norm, its scale, and diag K = kappa(p_i, p_i).
+__global__ void __launch_bounds__(256) quantize_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
+                                                       int dpad, int fp8, KernParams kp, unsigned char* __restrict__ Q,
+                                                       float* __restrict__ norms, float* __restrict__ knorms,
+                                                       float* __restrict__ scales, float* __restrict__ kdiag) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const float* p = P + (int64_t)w * ldp;
+    float scale = 1.f;
+    if (fp8) {
+        float amax = 0.f;
+        for (int l = lane; l < d; l += 32) amax = fmaxf(amax, fabsf(p[l]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        scale = amax > 0.f ? amax / 448.f : 1.f;
+    }
+    float nrm = 0.f;
+    for (int l = lane; l < dpad; l += 32) {
+        const float x = l < d ? p[l] : 0.f;
+        float rep;
+        if (fp8) {
+            const __nv_fp8_storage_t qv = __nv_cvt_float_to_fp8(x / scale, __NV_SATFINITE, __NV_E4M3);
+            Q[(int64_t)w * dpad + l] = qv;
+            const __half_raw hr = __nv_cvt_fp8_to_halfraw(qv, __NV_E4M3);
+            rep = __half2float(__half(hr)) * scale;
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            reinterpret_cast<__nv_bfloat16*>(Q)[(int64_t)w * dpad + l] = h;
+            rep = __bfloat162float(h);
+        }
+        nrm = fmaf(rep, rep, nrm);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    if (lane == 0) {
+        norms[w] = nrm;
+        // the epilogue works in base 2: c2 * r with c2 = -gamma log2(e) / sigma^2
+        knorms[w] = kp.kind == POPCORN_GAUSSIAN ? kp.neg_gamma_over_sigma2 * 1.4426950408889634f * nrm : nrm;
+        scales[w] = scale;
+        float kd;
+        if (kp.kind == POPCORN_GAUSSIAN) {
+            kd = 1.f;
+        } else if (kp.kind == POPCORN_POLYNOMIAL) {
+            const float base = fmaf(kp.gamma, nrm, kp.coef0);
+            kd = base;
+            for (int e = 1; e < kp.degree; ++e) kd *= base;
+        } else {
+            kd = nrm;
+        }
+        kdiag[w] = kd;
+    }
+}
+
+// ---------------------------------------------------------------- stable counting sort by label
+constexpr int SORT_THREADS = 1024;
+
+__global__ void __launch_bounds__(SORT_THREADS) sort_hist_kernel(const uint8_t* __restrict__ lab, int n, int k,
+                                                                 int* __restrict__ blockhist, const LoopState* st,
+                                                                 int eval) {
+    if (pass_skip(st, eval)) return;
+    __shared__ int h[kMaxClusters];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) h[c] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&h[lab[i]], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) blockhist[(size_t)blockIdx.x * k + c] = h[c];
+}
+
+// blockoff[b][c] = (padded start of cluster c) + (points with label c in blocks < b),
+// where cluster c starts at sum_{c' < c} round_up(|L_c'|, 32): every cluster's
+// columns fill whole 32-column chunks.
+__global__ void __launch_bounds__(kMaxClusters) sort_scan_kernel(const int* __restrict__ blockhist, int nb, int k,
+                                                                 int* __restrict__ blockoff, int ncols,
+                                                                 uint8_t* __restrict__ slab, float* __restrict__ snorm,
+                                                                 float* __restrict__ sscale, const LoopState* st,
+                                                                 int eval) {
+    if (pass_skip(st, eval)) return;
+    __shared__ int tot[kMaxClusters];
+    __shared__ int total;
+    const int c = threadIdx.x;
+    int t = 0;
+    if (c < k)
+        for (int b = 0; b < nb; ++b) t += blockhist[(size_t)b * k + c];
+    tot[c] = c < k ? t : 0;
+    __syncthreads();
+    if (c < k) {
+        int base = 0;
+        for (int c2 = 0; c2 < c; ++c2) base += (tot[c2] + 31) & ~31;
+        int run = base;
+        for (int b = 0; b < nb; ++b) {
+            blockoff[(size_t)b * k + c] = run;
+            run += blockhist[(size_t)b * k + c];
+        }
+        // this cluster's padding up to its next 32-column boundary: no cluster, zero weight
+        for (int pos = base + t; pos < base + ((t + 31) & ~31); ++pos) {
+            slab[pos] = (uint8_t)kNoLabel;
+            snorm[pos] = -INFINITY;
+            sscale[pos] = 0.f;
+        }
+        if (c == k - 1) total = base + ((t + 31) & ~31);
+    }
+    __syncthreads();
+    for (int pos = total + c; pos < ncols; pos += blockDim.x) {
+        slab[pos] = (uint8_t)kNoLabel;
+        snorm[pos] = -INFINITY;
+        sscale[pos] = 0.f;
+    }
+}
+
+// Position of every point in cluster order (stable: by block, then warp, then
+// lane) and a gather of its operand row, norm, scale and label.
+__global__ void __launch_bounds__(SORT_THREADS) sort_scatter_kernel(
+    const uint8_t* __restrict__ lab, int n, int k, const int* __restrict__ blockoff, const unsigned char* __restrict__ Q,
+    int row_bytes, const float* __restrict__ norms, const float* __restrict__ scales, unsigned char* __restrict__ Qs,
+    float* __restrict__ snorm, float* __restrict__ sscale, uint8_t* __restrict__ slab, const LoopState* st, int eval) {
+    if (pass_skip(st, eval)) return;
+    __shared__ int wcount[SORT_THREADS / 32][kMaxClusters];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < (SORT_THREADS / 32) * kMaxClusters; t += blockDim.x) (&wcount[0][0])[t] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n;
+    const int l = valid ? lab[i] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, l);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wcount[warp][l] = __popc(peers);
+    __syncthreads();
+    // exclusive prefix over warps, per label
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        int run = 0;
+        for (int w = 0; w < SORT_THREADS / 32; ++w) {
+            const int v = wcount[w][c];
+            wcount[w][c] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    if (!valid) return;
+    const int pos = blockoff[(size_t)blockIdx.x * k + l] + wcount[warp][l] + rank;
+    const uint4* src = reinterpret_cast<const uint4*>(Q + (int64_t)i * row_bytes);
+    uint4* dst = reinterpret_cast<uint4*>(Qs + (int64_t)pos * row_bytes);
+    for (int t = 0; t < row_bytes / 16; ++t) dst[t] = src[t];
+    snorm[pos] = norms[i];   // (the c2-scaled norm for the Gaussian)
+    sscale[pos] = scales[i];
+    slab[pos] = (uint8_t)l;
+}
+
+using RcFn = void (*)(const CUtensorMap, const CUtensorMap, RcArgs);
+
+RcFn recompute_fn(bool fp8, int kind) {
+    switch (kind) {
+        case POPCORN_LINEAR: return fp8 ? recompute_kernel<true, POPCORN_LINEAR> : recompute_kernel<false, POPCORN_LINEAR>;
+        case POPCORN_POLYNOMIAL:
+            return fp8 ? recompute_kernel<true, POPCORN_POLYNOMIAL> : recompute_kernel<false, POPCORN_POLYNOMIAL>;
+        default: return fp8 ? recompute_kernel<true, POPCORN_GAUSSIAN> : recompute_kernel<false, POPCORN_GAUSSIAN>;
+    }
+}
+
+bool make_map_u8(CUtensorMap* m, void* base, uint64_t inner_bytes, uint64_t rows, bool fp8) {
+    // BF16 maps count elements of 2 bytes, E4M3 maps elements of 1 byte
+    return make_tensor_map_2d(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base,
+                              fp8 ? inner_bytes : inner_bytes / 2, rows, inner_bytes, fp8 ? KBB : KBB / 2, RM,
+                              CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, int smem_budget) {
+    RecomputePlan p{};
+    p.fp8 = precision == POPCORN_FP8;
+    const int elem = p.fp8 ? 1 : 2;
+    const int per_kb = KBB / elem;                         // elements per k-block
+    p.dpad = (d + per_kb - 1) / per_kb * per_kb;
+    p.row_bytes = p.dpad * elem;
+    p.nkb = p.row_bytes / KBB;
+    p.npad = (n + RN - 1) / RN * RN;
+    // sorted column space: clusters padded to 32-column chunks
+    p.ncols = (n + 31 * k + RN - 1) / RN * RN;
+    const int T = p.npad / RM;
+    long long nseg = (32LL * num_sms + T - 1) / T;
+    const long long maxseg = p.ncols / RN;
+    if (nseg > maxseg) nseg = maxseg;
+    if (nseg < 1) nseg = 1;
+    long long seglen = (p.ncols + nseg - 1) / nseg;
+    seglen = (seglen + RN - 1) / RN * RN;
+    p.seglen = (int)seglen;
+    p.nseg = (int)((p.ncols + seglen - 1) / seglen);
+    // shared memory: resident row block, B ring, metadata ring, accumulators, barriers;
+    // two epilogue warpgroups when their accumulators leave room for >= 3 stages
+    p.off_b = p.nkb * KB_TILE;
+    const int meta = MS * META_BYTES;
+    int eg = 2, stages = 0;
+    for (; eg >= 1; --eg) {
+        const int acc = eg * k * 128 * 4;
+        const int fixed = p.off_b + meta + acc + 64 * 8 + 64 + 1024;
+        stages = (smem_budget - fixed) / KB_TILE;
+        if (stages >= 3 || eg == 1) break;
+    }
+    if (stages > 8) stages = 8;
+    p.eg = eg;
+    p.threads = 64 + 128 * eg;
+    p.stages = stages;
+    p.off_meta = p.off_b + stages * KB_TILE;
+    p.off_acc = p.off_meta + meta;
+    p.off_bar = p.off_acc + eg * k * 128 * 4;
+    p.off_misc = p.off_bar + 64 * 8;
+    p.smem = p.off_misc + 64 + 1024;
+    p.ok = p.nkb <= 4 && stages >= 2 && k <= 255;
+    p.grid = num_sms;
+    return p;
+}
+
+cudaError_t configure_recompute(int smem_optin, int* usable) {
+    size_t st = 0;
+    for (int f = 0; f < 2; ++f)
+        for (int kind = 0; kind < 3; ++kind) {
+            cudaFuncAttributes fa;
+            cudaError_t e = cudaFuncGetAttributes(&fa, recompute_fn(f != 0, kind));
+            if (e != cudaSuccess) return e;
+            if (fa.sharedSizeBytes > st) st = fa.sharedSizeBytes;
+        }
+    const int bytes = optin_minus_static(smem_optin, st);
+    for (int f = 0; f < 2; ++f)
+        for (int kind = 0; kind < 3; ++kind) {
+            cudaError_t e = cudaFuncSetAttribute(recompute_fn(f != 0, kind), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 bytes);
+            if (e != cudaSuccess) return e;
+        }
+    *usable = bytes;
+    return cudaSuccess;
+}
+
+cudaError_t launch_quantize(const float* P, int n, int d, int64_t ldp, KernParams kp, const RecomputePlan& p,
+                            const RecomputeBuffers& rb, float* kdiag, cudaStream_t s) {
+    quantize_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(P, n, d, ldp, p.dpad, p.fp8, kp, rb.Q, rb.norms, rb.knorms,
+                                                         rb.scales, kdiag);
+    return cudaGetLastError();
+}
+
+int recompute_sort_blocks(int n) { return (n + SORT_THREADS - 1) / SORT_THREADS; }
+
+cudaError_t launch_recompute_pass(const PassBuffers& b, KernParams kp, const RecomputePlan& p,
+                                  const RecomputeBuffers& rb, int* err, int eval, cudaStream_t s) {
+    const int n = b.n, k = b.k;
+    const int nb = recompute_sort_blocks(n);
+    sort_hist_kernel<<<nb, SORT_THREADS, 0, s>>>(b.lab8, n, k, rb.blockhist, b.st, eval);
+    sort_scan_kernel<<<1, kMaxClusters, 0, s>>>(rb.blockhist, nb, k, rb.blockoff, p.ncols, rb.slab, rb.snorm,
+                                                rb.sscale, b.st, eval);
+    sort_scatter_kernel<<<nb, SORT_THREADS, 0, s>>>(b.lab8, n, k, rb.blockoff, rb.Q, p.row_bytes, rb.knorms,
+                                                    rb.scales, rb.Qs, rb.snorm, rb.sscale, rb.slab, b.st, eval);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    RcArgs a;
+    a.n = n;
+    a.ncols = p.ncols;
+    a.nseg = p.nseg;
+    a.seglen = p.seglen;
+    a.nkb = p.nkb;
+    a.k = k;
+    a.fp8 = p.fp8;
+    a.eg = p.eg;
+    a.stages = p.stages;
+    a.off_b = p.off_b;
+    a.off_meta = p.off_meta;
+    a.off_acc = p.off_acc;
+    a.off_bar = p.off_bar;
+    a.off_misc = p.off_misc;
+    a.kp = kp;
+    a.rnorm = rb.norms;
+    a.rscale = rb.scales;
+    a.slab = rb.slab;
+    a.sknorm = rb.snorm;
+    a.sscale = rb.sscale;
+    a.Spart = b.Spart;
+    a.st = b.st;
+    a.err = err;
+    a.eval = eval;
+    CUtensorMap mr, mc;
+    if (!make_map_u8(&mr, rb.Q, (uint64_t)p.row_bytes, (uint64_t)n, p.fp8) ||
+        !make_map_u8(&mc, rb.Qs, (uint64_t)p.row_bytes, (uint64_t)p.ncols, p.fp8))
+        return cudaErrorInvalidValue;
+    recompute_fn(p.fp8 != 0, kp.kind)<<<p.grid, p.threads, p.smem, s>>>(mr, mc, a);
+    return cudaGetLastError();
+}
+
+}  // namespace popcorn

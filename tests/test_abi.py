@@ -83,7 +83,11 @@ def test_invalid_arguments_rejected_before_any_cuda_call(pc):
     bad = pc._Options(0, 1, 1, 0, (ctypes.c_int64 * 6)(1, 0, 0, 0, 0, 0))
     assert fit(opt=ctypes.byref(bad)) == 1                       # reserved must be zero
     rec = pc._Options(0, 0, 1, 0, (ctypes.c_int64 * 6)())
-    assert fit(opt=ctypes.byref(rec)) == 5                       # recompute path not in this build
+    assert fit(opt=ctypes.byref(rec)) == 5                       # recompute path needs BF16 or FP8
+    fp8k = pc._Options(3, 1, 1, 0, (ctypes.c_int64 * 6)())
+    assert fit(opt=ctypes.byref(fp8k)) == 5                      # FP8 only without a stored K
+    badk = pc._Options(0, 2, 1, 0, (ctypes.c_int64 * 6)())
+    assert fit(opt=ctypes.byref(badk)) == 1                      # store_k must be 0 or 1
     # kernel matrix: ldk must be a multiple of 4 and >= n
     st = lib.popcorn_kernel_matrix(P.ctypes.data, 10, 2, 2, kern, 0, out.ctypes.data, 10, out.ctypes.data, None)
     assert st == 1

@@ -1,0 +1,156 @@
+"""GPU parity of the recompute path (K never stored; store_k = 0).
+
+The recompute kernel evaluates kappa on the quantized points it streams:
+  * BF16: kappa of the BF16-rounded points (norms of the rounded rows);
+  * FP8:  kappa of s_i * e4m3(p_i / s_i) with s_i = max|p_i| / 448, both the
+          scale and the quotient rounded in FP32 exactly as the kernel does.
+Against the FP64 oracle on those same quantized points only FP32 accumulation
+(and the hardware exp2) remains, so a first pass must reproduce J to 1e-5 and
+the labels except near-ties below 1e-5 of the row scale.  Whole fits are
+checked pass by pass the same way (tests/test_gpu_parity.py's rule).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+from tests.parity import label_mismatches, rel_err  # noqa: E402
+from tests.test_gpu_tc import bf16_round  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_05587_gb300 as mod
+    return mod
+
+
+def e4m3_round(x):
+    """Round to the nearest FP8 E4M3 value (ties to even), saturating at +-448."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.minimum(np.abs(x), 448.0)
+    e = np.floor(np.log2(np.maximum(a, 2.0 ** -10)))
+    e = np.maximum(e, -6.0)                       # subnormals share the exponent of 2^-6
+    q = 2.0 ** (e - 3.0)                          # spacing: 3 mantissa bits
+    r = np.minimum(np.round(a / q) * q, 448.0)
+    return np.sign(x) * r
+
+
+def fp8_represented(P):
+    """What the FP8 path computes with: s_i * e4m3(p_i / s_i), in FP32 like the kernel."""
+    P = np.asarray(P, dtype=np.float32)
+    amax = np.abs(P).max(axis=1)
+    s = np.where(amax > 0, amax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    qv = e4m3_round((P / s[:, None]).astype(np.float32)).astype(np.float32)
+    return (qv * s[:, None]).astype(np.float32)
+
+
+def test_e4m3_round_helper():
+    v = np.array([0.0, 1.0, 1.0625, 1.1875, 448.0, 500.0, -3.3, 2.0 ** -9, 0.01], np.float64)
+    r = e4m3_round(v)
+    assert r[0] == 0 and r[1] == 1.0
+    assert r[2] == 1.0                  # halfway between 1 (8/8) and 1.125 (9/8): to the even 8/8
+    assert r[3] == 1.25                 # halfway between 1.125 (9/8) and 1.25 (10/8): to the even 10/8
+    assert r[4] == 448.0 and r[5] == 448.0
+    assert r[6] == -3.25
+    assert r[7] == 2.0 ** -9            # smallest subnormal
+    assert abs(r[8] - 0.009765625) < 1e-12   # 0.01 -> 5 * 2^-9
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _gauss(s):
+    return {"kind": "gaussian", "gamma": 1.0, "coef0": 0.0, "degree": 1, "sigma": float(s)}
+
+
+def _first_pass(pc, P, lab, k, kern, precision):
+    r = pc.popcorn_fit(_dev(P), k, kern, _dev(lab), max_iter=1, check_convergence=False, precision=precision,
+                       store_k=False, history=True)
+    Pq = bf16_round(P) if precision == "bf16" else fp8_represented(P)
+    st = oracle.step(oracle.kernel_matrix(Pq, kern), lab, k)
+    return r, st
+
+
+@pytest.mark.parametrize("precision,n,d,k", [
+    ("bf16", 300, 1, 3), ("bf16", 1000, 100, 20), ("bf16", 2053, 128, 100), ("bf16", 700, 192, 160),
+    ("fp8", 300, 1, 3), ("fp8", 1000, 100, 20), ("fp8", 2053, 128, 100), ("fp8", 700, 256, 255),
+])
+def test_recompute_first_pass_matches_oracle_on_quantized_points(pc, precision, n, d, k):
+    P = synth.mixture_varied_sigma(n, d, min(k, 50), seed=n + d)
+    lab = synth.init_labels(n, k, seed=n)
+    kern = _gauss(np.sqrt(d) * 0.7)
+    r, st = _first_pass(pc, P, lab, k, kern, precision)
+    assert rel_err(r["info"]["J_history"][0], st["J"]) <= 1e-5, (r["info"]["J_history"][0], st["J"])
+    assert label_mismatches(r["labels"].cpu().numpy(), st, rel=1e-5)[0] == 0
+
+
+@pytest.mark.parametrize("kern", [{"kind": "linear", "gamma": 1.0, "coef0": 0.0, "degree": 1, "sigma": 1.0},
+                                  {"kind": "polynomial", "gamma": 0.5, "coef0": 1.0, "degree": 2, "sigma": 1.0}],
+                         ids=["linear", "poly2"])
+def test_recompute_other_kernels(pc, kern):
+    P = synth.gaussian_blobs(900, 16, 6, seed=5, box=2.0)
+    lab = synth.init_labels(900, 6, seed=6)
+    r, st = _first_pass(pc, P, lab, 6, kern, "bf16")
+    assert rel_err(r["info"]["J_history"][0], st["J"]) <= 1e-5
+    assert label_mismatches(r["labels"].cpu().numpy(), st, rel=1e-5)[0] == 0
+
+
+def test_recompute_small_integers_exact_objective(pc):
+    # small integers are exact in BF16 and the products exact in FP32: J matches to rounding
+    P = synth.small_integer_points(500, 8, seed=2)
+    lab = synth.init_labels(500, 5, seed=3)
+    kern = {"kind": "polynomial", "gamma": 1.0, "coef0": 1.0, "degree": 2, "sigma": 1.0}
+    r, st = _first_pass(pc, P, lab, 5, kern, "bf16")
+    assert rel_err(r["info"]["J_history"][0], st["J"]) <= 1e-7
+    assert np.array_equal(r["labels"].cpu().numpy(), st["labels"])
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_recompute_fit_pass_by_pass(pc, precision):
+    wl = synth.workload("mixture", scale=0.01)          # n = 2000, d = 128, k = 100, Gaussian sigma 8
+    Pq = bf16_round(wl.P) if precision == "bf16" else fp8_represented(wl.P)
+    Ko = oracle.kernel_matrix(Pq, wl.kernel)
+    P, lab = _dev(wl.P), _dev(wl.init_labels)
+    r = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=6, check_convergence=False, precision=precision,
+                       store_k=False, history=True)
+    prev = wl.init_labels
+    for t in range(r["iterations"]):
+        nxt = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=t + 1, check_convergence=False,
+                             precision=precision, store_k=False)["labels"].cpu().numpy()
+        st = oracle.step(Ko, prev, wl.k)
+        assert rel_err(r["info"]["J_history"][t], st["J"]) <= 1e-5, t
+        assert label_mismatches(nxt, st, rel=1e-5)[0] == 0, t
+        prev = nxt
+    assert np.array_equal(prev, r["labels"].cpu().numpy())
+    assert rel_err(r["objective"], oracle.objective(Ko, prev, wl.k)) <= 1e-5
+
+
+def test_recompute_matches_materialized_bf16(pc):
+    """Same arithmetic two ways: stored BF16 K vs recomputed BF16 tiles."""
+    P = synth.mixture_varied_sigma(1500, 64, 10, seed=9)
+    lab = synth.init_labels(1500, 10, seed=10)
+    kern = _gauss(8.0)
+    a = pc.popcorn_fit(_dev(P), 10, kern, _dev(lab), max_iter=1, check_convergence=False, precision="bf16",
+                       history=True)
+    b = pc.popcorn_fit(_dev(P), 10, kern, _dev(lab), max_iter=1, check_convergence=False, precision="bf16",
+                       store_k=False, history=True)
+    assert rel_err(b["info"]["J_history"][0], a["info"]["J_history"][0]) <= 1e-5
+
+
+def test_recompute_subsample_objective_vs_fp64(pc):
+    """The mixture workload's first 20,000 points: FP8 and BF16 recompute fits, objective of
+    their labels against the FP64 oracle on the raw points (reported bars: BF16 1e-3, FP8 3e-2)."""
+    wl = synth.workload("mixture", scale=0.1)            # n = 20,000
+    Ko = oracle.kernel_matrix(wl.P, wl.kernel)
+    for precision, bar in (("bf16", 1e-3), ("fp8", 3e-2)):
+        r = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), max_iter=wl.max_iter,
+                           check_convergence=False, precision=precision, store_k=False, history=True)
+        labels = r["labels"].cpu().numpy()
+        J_true = oracle.objective(Ko, labels, wl.k)
+        assert rel_err(r["objective"], J_true) <= bar, (precision, r["objective"], J_true)
