@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink n (profiling captures only; the reported workload is scale 1)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["rings", "blobs", "images", "mixture"],
-                    help="rings (default, the reported line), blobs, images, mixture (recompute path)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["rings", "blobs", "images", "mixture", "batched"],
+                    help="rings (default, the reported line), blobs, images, mixture (recompute path), "
+                         "batched (256 instances in one graph)")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3", "fp8"],
                     help="K-build precision (default: the workload's)")
     return ap.parse_args()
@@ -217,11 +218,64 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_batched(args):
+    """256 independent instances (n in [500, 8000], d in {8, 32, 64}, k in [4, 64], polynomial and
+    Gaussian kernels), 30 passes each, one popcorn_fit_batched call per step."""
+    import torch
+
+    import synth
+    import paper_2501_05587_gb300 as pc
+
+    prec = args.precision or "fp32"
+    wls = synth.batched_instances(int(256 * args.scale) or 1, seed=0)
+    insts = [{"P": torch.from_numpy(w.P).cuda(), "k": w.k, "kernel": w.kernel,
+              "init_labels": torch.from_numpy(w.init_labels).cuda()} for w in wls]
+
+    def step():
+        return pc.popcorn_fit_batched(insts, max_iter=30, precision=prec, check_convergence=False, timing=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res = [step() for _ in range(args.steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    passes = sum(sum(r["iterations"]) for r in res)
+    kbytes = sum(4.0 * w.n * w.n for w in wls)
+    graph_ms = sum(r["info"]["loop_ms"] for r in res) / len(res)
+    # the same instances as separate popcorn_fit calls (the unbatched form), one sweep
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for x in insts:
+        pc.popcorn_fit(x["P"], x["k"], x["kernel"], x["init_labels"], max_iter=30, precision=prec,
+                       check_convergence=False)
+    e3.record()
+    torch.cuda.synchronize()
+    seq_ms = e2.elapsed_time(e3)
+    line = {"metric": METRIC, "value": passes / (ms / 1e3), "unit": "instance-passes/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"batched: {len(wls)} instances, 30 passes each, K stored FP32 "
+                                   f"({kbytes / 1e9:.1f} GB)", "precision": prec},
+            "graph_ms": graph_ms, "effective_GBps_of_K_reads": kbytes * 30 / (graph_ms / 1e3) / 1e9,
+            "separate_fits_ms": seq_ms, "batched_speedup_vs_separate_fits": seq_ms / (ms / args.steps),
+            "gpu_launches": sum(r["info"]["kernel_launches"] for r in res)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import torch
 

@@ -206,6 +206,41 @@ POPCORN_API popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int
                            double* objective_out, int32_t* iterations_out,
                            popcorn_fit_info* info, popcorn_stream_t stream);
 
+/* One clustering problem of a batch (all pointers device memory). */
+typedef struct {
+    const float* P;             /* n x d FP32, leading dimension ldp >= d                  */
+    int64_t n;                  /* points, 2 <= n < 2^31                                   */
+    int32_t d;                  /* features >= 1                                           */
+    int64_t ldp;
+    int32_t k;                  /* clusters, 1 <= k < n, k <= 256                          */
+    popcorn_kernel kern;        /* each instance has its own kernel function               */
+    const int32_t* init_labels; /* n labels in [0, k)                                      */
+    int32_t* labels_out;        /* n labels (may alias init_labels)                        */
+} popcorn_instance;
+
+/*
+ * popcorn_fit_batched -- many independent Kernel K-means problems at once.
+ *
+ * Each instance runs Alg. 2 exactly as popcorn_fit would, with the shared
+ * max_iter, tol and options (store_k must be 1).  The whole batch -- the K
+ * builds of all instances, max_iter assignment passes over every instance
+ * that has not stopped, the final objective pass -- is captured once into a
+ * CUDA graph and launched on `stream`; an instance that converges stops
+ * doing work on the device while the others go on.  Instances of uneven n,
+ * d, k and kernel share every launch: work is flattened over (instance,
+ * tile / row segment / row block).
+ *
+ *   instances        host array of `count` descriptors.
+ *   objectives_out   host, count doubles: J(labels_out) per instance.
+ *   iterations_out   host, count ints: passes per instance.
+ *   info             optional; loop_ms (timing = 1) is the graph's time.
+ * Errors: as popcorn_fit for each instance (the message names the index).
+ */
+POPCORN_API popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* instances, int32_t max_iter,
+                                               double tol, const popcorn_options* opt, double* objectives_out,
+                                               int32_t* iterations_out, popcorn_fit_info* info,
+                                               popcorn_stream_t stream);
+
 /*
  * popcorn_assign_step_noalloc -- popcorn_assign_step without any allocation.
  *

@@ -25,6 +25,7 @@ __all__ = [
     "popcorn_kernel_matrix",
     "popcorn_assign_step",
     "popcorn_fit",
+    "popcorn_fit_batched",
     "popcorn_assign_step_noalloc",
     "NOALLOC_SCRATCH_BYTES",
     "popcorn_version",
@@ -50,6 +51,7 @@ EXPORTED_SYMBOLS = (
     "popcorn_assign_step",
     "popcorn_fit",
     "popcorn_assign_step_noalloc",
+    "popcorn_fit_batched",
 )
 
 KIND = {"linear": 0, "polynomial": 1, "gaussian": 2}
@@ -77,6 +79,12 @@ class _FitInfo(ctypes.Structure):
                 ("changed_history", ctypes.POINTER(ctypes.c_int32))]
 
 
+class _Instance(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("ldp", ctypes.c_int64),
+                ("k", ctypes.c_int32), ("kern", _Kernel), ("init_labels", ctypes.c_void_p),
+                ("labels_out", ctypes.c_void_p)]
+
+
 _vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
 _lib.popcorn_status_string.restype = ctypes.c_char_p
 _lib.popcorn_status_string.argtypes = [ctypes.c_int]
@@ -91,6 +99,9 @@ _lib.popcorn_assign_step.argtypes = [_vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, 
                                      ctypes.POINTER(_dbl), ctypes.POINTER(_i32), _vp]
 _lib.popcorn_assign_step_noalloc.restype = ctypes.c_int
 _lib.popcorn_assign_step_noalloc.argtypes = _lib.popcorn_assign_step.argtypes
+_lib.popcorn_fit_batched.restype = ctypes.c_int
+_lib.popcorn_fit_batched.argtypes = [_i32, ctypes.POINTER(_Instance), _i32, _dbl, ctypes.POINTER(_Options),
+                                     ctypes.POINTER(_dbl), ctypes.POINTER(_i32), ctypes.POINTER(_FitInfo), _vp]
 _lib.popcorn_fit.restype = ctypes.c_int
 _lib.popcorn_fit.argtypes = [_vp, _i64, _i32, _i64, _i32, _Kernel, _vp, _i32, _dbl,
                              ctypes.POINTER(_Options), _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i32),
@@ -256,3 +267,37 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
         out_info["changed_history"] = list(Ch[: its.value])
     out_info["host_inputs"] = host
     return {"labels": labels_out, "objective": obj.value, "iterations": its.value, "info": out_info}
+
+
+def popcorn_fit_batched(instances, max_iter: int, tol: float = 0.0, precision: str = "fp32",
+                        check_convergence: bool = True, timing: bool = False, stream=None) -> dict:
+    """Many independent fits in one captured CUDA graph.
+
+    ``instances``: list of dicts {"P": (n, d) float32 CUDA tensor, "k": int, "kernel": dict,
+    "init_labels": (n,) int32 CUDA tensor, optional "labels_out"}.  Returns
+    {"labels": [tensor], "objectives": [float], "iterations": [int], "info": dict}.
+    """
+    torch = _torch()
+    arr = (_Instance * len(instances))()
+    outs = []
+    keep = []
+    for t, x in enumerate(instances):
+        P = x["P"]
+        assert P.is_cuda and P.dtype == torch.float32 and P.dim() == 2 and P.stride(1) == 1
+        lab = x["init_labels"].to(torch.int32).contiguous()
+        out = x.get("labels_out")
+        if out is None:
+            out = torch.empty(P.shape[0], dtype=torch.int32, device=P.device)
+        keep += [P, lab, out]
+        outs.append(out)
+        arr[t] = _Instance(P.data_ptr(), P.shape[0], P.shape[1], P.stride(0), int(x["k"]), _kernel(x["kernel"]),
+                           lab.data_ptr(), out.data_ptr())
+    opt = _Options(PRECISION[precision], 1, 1 if check_convergence else 0, 1 if timing else 0,
+                   (ctypes.c_int64 * 6)())
+    objs = (ctypes.c_double * len(instances))()
+    its = (ctypes.c_int32 * len(instances))()
+    info = _FitInfo()
+    _check(_lib.popcorn_fit_batched(len(instances), arr, int(max_iter), float(tol), ctypes.byref(opt), objs, its,
+                                    ctypes.byref(info), _stream(stream)), "popcorn_fit_batched")
+    out_info = {f: getattr(info, f) for f, _ in _FitInfo._fields_ if f not in ("J_history", "changed_history")}
+    return {"labels": outs, "objectives": list(objs), "iterations": list(its), "info": out_info}

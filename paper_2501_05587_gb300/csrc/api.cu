@@ -51,6 +51,7 @@ struct DeviceInfo {
     int smem_optin = 0;
     int reduce_smem = 0;   // dynamic shared memory usable by the reduction kernel
     int recompute_smem = 0;
+    int batched_smem = 0;
     cudaMemPool_t pool = nullptr;
     bool ready = false;
 };
@@ -80,6 +81,8 @@ popcorn_status device_info(DeviceInfo** out) {
         POPCORN_CUDA(configure_reduce_smem(d.smem_optin, &d.reduce_smem));
         POPCORN_CUDA(configure_kbuild_tc());
         POPCORN_CUDA(configure_recompute(d.smem_optin, &d.recompute_smem));
+        POPCORN_CUDA(configure_batched(d.smem_optin));
+        d.batched_smem = d.smem_optin - 1024;
         d.ready = true;
     }
     *out = &d;
@@ -751,6 +754,223 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
             info->reduce_ms = r;
             info->assign_ms = a;
         }
+    }
+    return POPCORN_OK;
+}
+
+
+popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, int32_t max_iter, double tol,
+                                   const popcorn_options* opt_in, double* objectives_out, int32_t* iterations_out,
+                                   popcorn_fit_info* info, popcorn_stream_t stream) {
+    g_err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    popcorn_options opt;
+    memset(&opt, 0, sizeof opt);
+    opt.precision = POPCORN_FP32;
+    opt.store_k = 1;
+    opt.check_convergence = 1;
+    if (opt_in) opt = *opt_in;
+    if (count < 1 || !inst || !objectives_out || !iterations_out)
+        return fail(POPCORN_ERR_INVALID, "count must be >= 1 and the output arrays non-null");
+    if (max_iter < 0) return fail(POPCORN_ERR_INVALID, "max_iter = %d < 0", max_iter);
+    if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
+    for (int r = 0; r < 6; ++r)
+        if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
+    if (opt.store_k != 1) return fail(POPCORN_ERR_UNSUPPORTED, "batched mode stores K (store_k = 1)");
+    if (opt.precision != POPCORN_FP32 && opt.precision != POPCORN_BF16 && opt.precision != POPCORN_BF16X3)
+        return fail(POPCORN_ERR_UNSUPPORTED, "batched mode runs in FP32, BF16 or BF16X3");
+    DeviceInfo* dev;
+    POPCORN_TRY(device_info(&dev));
+
+    // ---- layout of every instance, flattened work prefixes
+    std::vector<BatchInst> h(count);
+    std::vector<size_t> off(count);
+    BatchPlan bp{};
+    bp.count = count;
+    size_t bytes = 0;
+    size_t tc_ws = 0;
+    auto take = [&](size_t nbytes) {
+        const size_t o = bytes;
+        bytes += (nbytes + 255) & ~(size_t)255;
+        return o;
+    };
+    struct Offs {
+        size_t K, kdiag, lab32, lab8, counts, Spart, zpart, zsum, cnorm, invm, st, J, ch;
+    };
+    std::vector<Offs> o(count);
+    const int hist_len = max_iter > 0 ? max_iter : 1;
+    for (int t = 0; t < count; ++t) {
+        const popcorn_instance& x = inst[t];
+        if (!x.P || !x.init_labels || !x.labels_out) return fail(POPCORN_ERR_INVALID, "instance %d: null pointer", t);
+        if (x.n < 2 || x.n >= (1LL << 31)) return fail(POPCORN_ERR_INVALID, "instance %d: n = %lld", t, (long long)x.n);
+        if (x.d < 1 || x.ldp < x.d) return fail(POPCORN_ERR_INVALID, "instance %d: d = %d, ldp = %lld", t, x.d, (long long)x.ldp);
+        if (x.k < 1 || x.k >= x.n || x.k > kMaxClusters)
+            return fail(POPCORN_ERR_INVALID, "instance %d: k = %d outside [1, min(n - 1, %d)]", t, x.k, kMaxClusters);
+        if (!is_device_pointer(x.P) || !is_device_pointer(x.init_labels) || !is_device_pointer(x.labels_out))
+            return fail(POPCORN_ERR_INVALID, "instance %d: batched mode takes device pointers", t);
+        KernParams kp;
+        popcorn_status ks = check_kernel(x.kern, &kp);
+        if (ks != POPCORN_OK) return fail(ks, "instance %d: %s", t, g_err.c_str());
+        const int n = (int)x.n, k = x.k;
+        BatchInst& b = h[t];
+        memset(&b, 0, sizeof b);
+        b.P = x.P;
+        b.ldp = x.ldp;
+        b.d = x.d;
+        b.kp = kp;
+        b.T = (n + 127) / 128;
+        b.tile0 = bp.tiles;
+        bp.tiles += (long long)b.T * (b.T + 1) / 2;
+        b.ldk = (n + 3) / 4 * 4;
+        b.n = n;
+        b.k = k;
+        b.seglen = kBatchSeg;
+        b.nseg = (n + kBatchSeg - 1) / kBatchSeg;
+        b.init_labels = x.init_labels;
+        b.labels_out = x.labels_out;
+        b.unit0 = bp.units;
+        bp.units += n * b.nseg;
+        b.zblock0 = bp.zblocks;
+        bp.zblocks += (n + kZReduceRows - 1) / kZReduceRows;
+        b.ablock0 = bp.ablocks;
+        bp.ablocks += (n + kAssignThreads - 1) / kAssignThreads;
+        b.lblock0 = bp.lblocks;
+        bp.lblocks += (n + kBatchLabelThreads - 1) / kBatchLabelThreads;
+        if (k > bp.kmax) bp.kmax = k;
+        const int zb = (n + kZReduceRows - 1) / kZReduceRows;
+        o[t].K = take((size_t)n * b.ldk * 4);
+        o[t].kdiag = take((size_t)n * 4);
+        o[t].lab32 = take((size_t)n * 4);
+        o[t].lab8 = take(((size_t)n + 15) & ~(size_t)15);
+        o[t].counts = take(2 * (size_t)k * 4);
+        o[t].Spart = take((size_t)n * b.nseg * k * 4);
+        o[t].zpart = take((size_t)zb * k * 8);
+        o[t].zsum = take((size_t)k * 8);
+        o[t].cnorm = take((size_t)k * 8);
+        o[t].invm = take((size_t)k * 8);
+        o[t].st = take(sizeof(LoopState));
+        o[t].J = take((size_t)hist_len * 8);
+        o[t].ch = take((size_t)hist_len * 4);
+        if (opt.precision != POPCORN_FP32) {
+            const size_t w = kbuild_tc_workspace(n, x.d, opt.precision);
+            if (w > tc_ws) tc_ws = w;
+        }
+    }
+    if (bp.units <= 0 || bp.units >= (1 << 30)) return fail(POPCORN_ERR_UNSUPPORTED, "batch too large");
+    plan_batched_reduce(&bp, dev->sms, dev->batched_smem);
+    const size_t inst_off = take(sizeof(BatchInst) * (size_t)count);
+    const size_t tc_off = tc_ws ? take(tc_ws) : 0;
+    const size_t err_off = take(sizeof(int));
+
+    Workspace ws(dev->pool, s);
+    unsigned char* base;
+    POPCORN_TRY(ws.alloc(&base, bytes, "batch workspace"));
+    for (int t = 0; t < count; ++t) {
+        BatchInst& b = h[t];
+        b.K = reinterpret_cast<float*>(base + o[t].K);
+        b.kdiag = reinterpret_cast<float*>(base + o[t].kdiag);
+        b.lab32 = reinterpret_cast<int32_t*>(base + o[t].lab32);
+        b.lab8 = base + o[t].lab8;
+        b.counts = reinterpret_cast<int32_t*>(base + o[t].counts);
+        b.Spart = reinterpret_cast<float*>(base + o[t].Spart);
+        b.zpart = reinterpret_cast<double*>(base + o[t].zpart);
+        b.zsum = reinterpret_cast<double*>(base + o[t].zsum);
+        b.cnorm = reinterpret_cast<double*>(base + o[t].cnorm);
+        b.invm = reinterpret_cast<double*>(base + o[t].invm);
+        b.st = reinterpret_cast<LoopState*>(base + o[t].st);
+        b.J_hist = reinterpret_cast<double*>(base + o[t].J);
+        b.changed_hist = reinterpret_cast<int32_t*>(base + o[t].ch);
+    }
+    BatchInst* dI = reinterpret_cast<BatchInst*>(base + inst_off);
+    POPCORN_CUDA(cudaMemcpyAsync(dI, h.data(), sizeof(BatchInst) * (size_t)count, cudaMemcpyHostToDevice, s));
+    int* err = reinterpret_cast<int*>(base + err_off);
+    POPCORN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+
+    // ---- capture the whole batch once
+    cudaStream_t cs;
+    POPCORN_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } sg{cs};
+    int launches = 0;
+    popcorn_status cap = POPCORN_OK;
+    POPCORN_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    auto step = [&](cudaError_t e, const char* what) {
+        if (cap == POPCORN_OK && e != cudaSuccess) {
+            cudaGetLastError();
+            cap = fail(POPCORN_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+        }
+    };
+    step(launch_batched_init(dI, bp, max_iter, opt.check_convergence ? 1 : 0, tol, cs), "batched init");
+    launches += 2;
+    if (opt.precision == POPCORN_FP32) {
+        step(launch_batched_kbuild_simt(dI, bp, cs), "batched K build");
+        launches += 1;
+    } else {
+        for (int t = 0; t < count && cap == POPCORN_OK; ++t) {
+            const BatchInst& b = h[t];
+            step(launch_kbuild_tc(b.P, b.n, b.d, b.ldp, b.kp, opt.precision, b.K, b.ldk, b.kdiag, base + tc_off, err,
+                                  dev->sms, cs, &launches),
+                 "tensor-core K build");
+        }
+    }
+    step(launch_batched_trace(dI, bp, cs), "batched trace");
+    launches += 1;
+    for (int it = 0; it < max_iter && cap == POPCORN_OK; ++it) {
+        step(launch_batched_pass(dI, bp, 0, cs), "batched pass");
+        launches += 3;
+    }
+    step(launch_batched_pass(dI, bp, 1, cs), "batched objective pass");
+    step(launch_batched_copy_labels(dI, bp, cs), "batched label copy");
+    launches += 3;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (cap != POPCORN_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return cap;
+    }
+    POPCORN_CUDA(ec);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    POPCORN_CUDA(ei);
+    struct ExecGuard {
+        cudaGraphExec_t e;
+        ~ExecGuard() { cudaGraphExecDestroy(e); }
+    } eg{exec};
+
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timing = opt.timing != 0;
+    g_events.used = 0;
+    if (timing) {
+        POPCORN_TRY(g_events.get(&e0));
+        POPCORN_TRY(g_events.get(&e1));
+        POPCORN_CUDA(cudaEventRecord(e0, s));
+    }
+    POPCORN_CUDA(cudaGraphLaunch(exec, s));
+    if (timing) POPCORN_CUDA(cudaEventRecord(e1, s));
+    std::vector<LoopState> hs(count);
+    int herr = 0;
+    for (int t = 0; t < count; ++t)
+        POPCORN_CUDA(cudaMemcpyAsync(&hs[t], h[t].st, sizeof(LoopState), cudaMemcpyDeviceToHost, s));
+    POPCORN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    POPCORN_CUDA(cudaStreamSynchronize(s));
+    for (int t = 0; t < count; ++t) {
+        if (hs[t].bad_label) return fail(POPCORN_ERR_INVALID, "instance %d: an initial label is outside [0, %d)", t, h[t].k);
+        objectives_out[t] = hs[t].J_eval;
+        iterations_out[t] = hs[t].iter;
+    }
+    if (herr) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the tensor-core K build ran out");
+    if (info) {
+        int conv = 1;
+        for (int t = 0; t < count; ++t) conv &= hs[t].converged;
+        info->converged = conv;
+        info->kernel_launches = launches;
+        info->reduce_launches = info->assign_launches = max_iter;
+        info->h2d_bytes = info->d2h_bytes = 0;
+        info->kbuild_ms = info->reduce_ms = info->assign_ms = info->eval_ms = 0.0;
+        info->loop_ms = timing ? elapsed(e0, e1) : 0.0;
     }
     return POPCORN_OK;
 }

@@ -313,7 +313,9 @@ struct AssignArgs {
     float* E_out;
 };
 
-__global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) {
+// One block of the distance/argmin pass: rows [block * blockDim, ...), and
+// the pass's loop control when this is the last of nblocks blocks to finish.
+__device__ __forceinline__ void assign_body(const AssignArgs& a, int block, int nblocks) {
     LoopState* st = a.st;
     if (st->done) return;
     __shared__ int hist[kMaxClusters];
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) {
     for (int c = threadIdx.x; c < k; c += blockDim.x) hist[c] = 0;
     __syncthreads();
 
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = block * blockDim.x + threadIdx.x;
     int newl = 0, changed = 0;
     if (i < n) {
         const int li = a.lab32[i];
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) {
     if (threadIdx.x == 0 && block_changed) atomicAdd(&st->changed_acc, (unsigned)block_changed);
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) am_last = (atomicAdd(&st->assign_ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) am_last = (atomicAdd(&st->assign_ticket, 1u) == (unsigned)nblocks - 1);
     __syncthreads();
     if (!am_last) return;
     __threadfence();
@@ -391,6 +393,8 @@ __global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) { assign_body(a, blockIdx.x, gridDim.x); }
+
 
 // sum_{i in L_c} S_ic for the recompute path, from Spart[i][s][c]: a block takes
 // kZReduceRows consecutive rows; thread c sums its cluster's rows in row
@@ -409,16 +413,16 @@ struct ZArgs {
     int eval_only;
 };
 
-__global__ void __launch_bounds__(kZReduceRows) zreduce_kernel(ZArgs a) {
+__device__ __forceinline__ void zreduce_body(const ZArgs& a, int block, int nblocks) {
     LoopState* st = a.st;
     if (pass_skip(st, a.eval_only)) {
-        if (a.eval_only && blockIdx.x == 0 && threadIdx.x == 0) st->J_eval = st->J_last;
+        if (a.eval_only && block == 0 && threadIdx.x == 0) st->J_eval = st->J_last;
         return;
     }
     __shared__ int lab_s[kZReduceRows];
     __shared__ double val_s[kZReduceRows];
     __shared__ int am_last;
-    const int i = blockIdx.x * kZReduceRows + threadIdx.x;
+    const int i = block * kZReduceRows + threadIdx.x;
     int l = -1;
     double v = 0.0;
     if (i < a.n) {
@@ -435,18 +439,20 @@ __global__ void __launch_bounds__(kZReduceRows) zreduce_kernel(ZArgs a) {
         double t = 0.0;
         for (int r = 0; r < kZReduceRows; ++r)
             if (lab_s[r] == c) t += val_s[r];
-        a.zpart[(size_t)blockIdx.x * a.k + c] = t;
+        a.zpart[(size_t)block * a.k + c] = t;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) am_last = (atomicAdd(&st->reduce_ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) am_last = (atomicAdd(&st->reduce_ticket, 1u) == (unsigned)nblocks - 1);
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    finalize_pass(a.zpart, (int)gridDim.x, a.k, a.counts, a.zsum, a.cnorm, a.invm, st, a.J_hist, a.eval_only);
+    finalize_pass(a.zpart, nblocks, a.k, a.counts, a.zsum, a.cnorm, a.invm, st, a.J_hist, a.eval_only);
 }
 
-__global__ void init_state_kernel(LoopState* st, int max_iter, int check_conv, double tol) {
+__global__ void __launch_bounds__(kZReduceRows) zreduce_kernel(ZArgs a) { zreduce_body(a, blockIdx.x, gridDim.x); }
+
+__device__ __forceinline__ void init_state_fn(LoopState* st, int max_iter, int check_conv, double tol) {
     st->iter = 0;
     st->done = (max_iter <= 0);
     st->converged = 0;
@@ -465,8 +471,12 @@ __global__ void init_state_kernel(LoopState* st, int max_iter, int check_conv, d
     st->J_eval = 0.0;
 }
 
+__global__ void init_state_kernel(LoopState* st, int max_iter, int check_conv, double tol) {
+    init_state_fn(st, max_iter, check_conv, tol);
+}
+
 // sum of diag(K) in FP64; one block, fixed reduction order
-__global__ void __launch_bounds__(1024) trace_kernel(const float* __restrict__ kdiag, int n, LoopState* st) {
+__device__ __forceinline__ void trace_body(const float* __restrict__ kdiag, int n, LoopState* st) {
     __shared__ double part[1024];
     double t = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) t += (double)kdiag[i];
@@ -479,13 +489,16 @@ __global__ void __launch_bounds__(1024) trace_kernel(const float* __restrict__ k
     if (threadIdx.x == 0) st->trace = part[0];
 }
 
-__global__ void __launch_bounds__(256) init_labels_kernel(const int32_t* __restrict__ in, int n, int k,
-                                                          int32_t* lab32, uint8_t* lab8, int nlab,
-                                                          int32_t* counts, LoopState* st) {
+__global__ void __launch_bounds__(1024) trace_kernel(const float* __restrict__ kdiag, int n, LoopState* st) {
+    trace_body(kdiag, n, st);
+}
+
+__device__ __forceinline__ void init_labels_body(const int32_t* __restrict__ in, int n, int k, int32_t* lab32,
+                                                 uint8_t* lab8, int nlab, int32_t* counts, LoopState* st, int block) {
     __shared__ int hist[kMaxClusters];
     for (int c = threadIdx.x; c < k; c += blockDim.x) hist[c] = 0;
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = block * blockDim.x + threadIdx.x;
     if (i < n) {
         int l = in[i];
         if (l < 0 || l >= k) {
@@ -501,6 +514,12 @@ __global__ void __launch_bounds__(256) init_labels_kernel(const int32_t* __restr
     __syncthreads();
     for (int c = threadIdx.x; c < k; c += blockDim.x)
         if (hist[c]) atomicAdd(counts + c, hist[c]);
+}
+
+__global__ void __launch_bounds__(256) init_labels_kernel(const int32_t* __restrict__ in, int n, int k,
+                                                          int32_t* lab32, uint8_t* lab8, int nlab,
+                                                          int32_t* counts, LoopState* st) {
+    init_labels_body(in, n, k, lab32, lab8, nlab, counts, st, blockIdx.x);
 }
 
 }  // namespace
@@ -652,6 +671,259 @@ cudaError_t configure_reduce_smem(int optin, int* usable) {
         }
     *usable = bytes;
     return cudaSuccess;
+}
+
+namespace {
+
+// ------------------------------------------------------------------ batched mode
+
+// Instance holding flattened index x of a prefix field (fields ascend with t).
+template <class F>
+__device__ __forceinline__ int find_inst(const BatchInst* I, int count, long long x, F field) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (field(I[mid]) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void batched_init_kernel(const BatchInst* I, int count, int max_iter, int check_conv, double tol) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) {
+        init_state_fn(I[t].st, max_iter, check_conv, tol);
+        for (int c = 0; c < 2 * I[t].k; ++c) I[t].counts[c] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kBatchLabelThreads) batched_labels_kernel(const BatchInst* I, int count) {
+    const int t = find_inst(I, count, blockIdx.x, [](const BatchInst& x) { return (long long)x.lblock0; });
+    const BatchInst& b = I[t];
+    init_labels_body(b.init_labels, b.n, b.k, b.lab32, b.lab8, (b.n + 15) & ~15, b.counts, b.st,
+                     blockIdx.x - b.lblock0);
+}
+
+__global__ void __launch_bounds__(kBatchLabelThreads) batched_copy_labels_kernel(const BatchInst* I, int count) {
+    const int t = find_inst(I, count, blockIdx.x, [](const BatchInst& x) { return (long long)x.lblock0; });
+    const BatchInst& b = I[t];
+    const int i = (blockIdx.x - b.lblock0) * blockDim.x + threadIdx.x;
+    if (i < b.n) b.labels_out[i] = b.lab32[i];
+}
+
+__global__ void __launch_bounds__(1024) batched_trace_kernel(const BatchInst* I) {
+    const BatchInst& b = I[blockIdx.x];
+    trace_body(b.kdiag, b.n, b.st);
+}
+
+__global__ void __launch_bounds__(kZReduceRows) batched_zreduce_kernel(const BatchInst* I, int count, int eval) {
+    const int t = find_inst(I, count, blockIdx.x, [](const BatchInst& x) { return (long long)x.zblock0; });
+    const BatchInst& b = I[t];
+    ZArgs a;
+    a.n = b.n;
+    a.k = b.k;
+    a.nseg = b.nseg;
+    a.Spart = b.Spart;
+    a.lab8 = b.lab8;
+    a.zpart = b.zpart;
+    a.zsum = b.zsum;
+    a.cnorm = b.cnorm;
+    a.invm = b.invm;
+    a.counts = b.counts;
+    a.st = b.st;
+    a.J_hist = b.J_hist;
+    a.eval_only = eval;
+    zreduce_body(a, blockIdx.x - b.zblock0, (b.n + kZReduceRows - 1) / kZReduceRows);
+}
+
+__global__ void __launch_bounds__(kAssignThreads) batched_assign_kernel(const BatchInst* I, int count) {
+    const int t = find_inst(I, count, blockIdx.x, [](const BatchInst& x) { return (long long)x.ablock0; });
+    const BatchInst& b = I[t];
+    AssignArgs a;
+    a.n = b.n;
+    a.k = b.k;
+    a.nseg = b.nseg;
+    a.Spart = b.Spart;
+    a.kdiag = b.kdiag;
+    a.cnorm = b.cnorm;
+    a.invm = b.invm;
+    a.counts = b.counts;
+    a.lab32 = b.lab32;
+    a.lab8 = b.lab8;
+    a.st = b.st;
+    a.changed_hist = b.changed_hist;
+    a.E_out = nullptr;
+    assign_body(a, blockIdx.x - b.ablock0, (b.n + kAssignThreads - 1) / kAssignThreads);
+}
+
+// K stream over the units (instance, row, segment) of every instance still
+// running: lane-private shared-memory cluster columns as in reduce_kernel,
+// labels read through L1, the next batch in flight while the current one is
+// scattered (across unit boundaries too), and per unit a butterfly reduction
+// for k <= 8 or the rotated walk for larger k.  z and J come from the batched
+// z kernel that follows.
+__global__ void __launch_bounds__(kReduceMaxWarps * 32, 2)
+    batched_reduce_kernel(const BatchInst* I, int count, int units, int kmax, int eval) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int W = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* accw = reinterpret_cast<float*>(smem) + (size_t)warp * kmax * 32;
+    float* accl = accw + lane;
+    for (int t = lane; t < kmax * 32; t += 32) accw[t] = 0.f;
+    __syncwarp();
+    const int GW = (int)gridDim.x * W;
+
+    // next unit at or after u that belongs to an instance still running
+    struct Geo {
+        const BatchInst* b;
+        int u, i, sg, c1, qb, q1;
+        const float4* row4;
+        const uint32_t* lab4;
+    };
+    auto geom = [&](int u, Geo& g) -> bool {
+        for (; u < units; u += GW) {
+            const int t = find_inst(I, count, u, [](const BatchInst& x) { return (long long)x.unit0; });
+            const BatchInst* b = I + t;
+            if (pass_skip(b->st, eval)) continue;
+            const int lu = u - b->unit0;
+            g.b = b;
+            g.u = u;
+            g.i = lu / b->nseg;
+            g.sg = lu - g.i * b->nseg;
+            const int c0 = g.sg * b->seglen;
+            g.c1 = min(b->n, c0 + b->seglen);
+            g.qb = c0 >> 2;
+            g.q1 = g.c1 >> 2;
+            g.row4 = reinterpret_cast<const float4*>(b->K + (int64_t)g.i * b->ldk);
+            g.lab4 = reinterpret_cast<const uint32_t*>(b->lab8);
+            return true;
+        }
+        return false;
+    };
+    Geo cur;
+    if (!geom((int)blockIdx.x * W + warp, cur)) return;
+    float4 v[4];
+    uint32_t L[4];
+    load_batch<4, false>(cur.row4, cur.lab4, cur.qb + lane, cur.q1, v, L);
+    while (true) {
+        const bool last = cur.qb + 128 >= cur.q1;
+        Geo nxt = cur;
+        bool more = true;
+        if (last) {
+            more = geom(cur.u + GW, nxt);
+        } else {
+            nxt.qb = cur.qb + 128;
+        }
+        float4 vn[4];
+        uint32_t Ln[4];
+        if (more) load_batch<4, false>(nxt.row4, nxt.lab4, nxt.qb + lane, nxt.q1, vn, Ln);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            accl[(L[x] & 0xffu) * 32] += v[x].x;
+            accl[((L[x] >> 8) & 0xffu) * 32] += v[x].y;
+            accl[((L[x] >> 16) & 0xffu) * 32] += v[x].z;
+            accl[(L[x] >> 24) * 32] += v[x].w;
+        }
+        if (last) {
+            const BatchInst& b = *cur.b;
+            {
+                const int j = (cur.q1 << 2) + lane;
+                if (j < cur.c1) accl[(int)b.lab8[j] * 32] += b.K[(int64_t)cur.i * b.ldk + j];
+            }
+            __syncwarp();
+            float* out = b.Spart + ((int64_t)cur.i * b.nseg + cur.sg) * b.k;
+            if (b.k <= 8) {
+                float part[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    part[c] = c < b.k ? accl[c * 32] : 0.f;
+                    if (c < b.k) accl[c * 32] = 0.f;
+                }
+                const float tot = butterfly<8>(part, lane);
+                const int c = bfly_cluster<8>(lane);
+                if ((lane & 3) == 0 && c < b.k) out[c] = tot;
+            } else {
+                for (int cb = 0; cb < b.k; cb += 32) {
+                    const int c = cb + lane;
+                    if (c < b.k) {
+                        float tot = 0.f;
+                        float* rowp = accw + (size_t)c * 32;
+#pragma unroll 8
+                        for (int j = 0; j < 32; ++j) {
+                            const int idx = (j + lane) & 31;
+                            tot += rowp[idx];
+                            rowp[idx] = 0.f;
+                        }
+                        out[c] = tot;
+                    }
+                }
+            }
+            __syncwarp();
+            if (!more) break;
+            cur = nxt;
+        } else {
+            cur.qb = nxt.qb;
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            v[x] = vn[x];
+            L[x] = Ln[x];
+        }
+    }
+}
+
+}  // namespace
+
+void plan_batched_reduce(BatchPlan* bp, int num_sms, int smem_budget) {
+    const size_t per_warp = (size_t)bp->kmax * 32 * sizeof(float);
+    int w = (int)((size_t)smem_budget / per_warp);
+    if (w > kReduceMaxWarps) w = kReduceMaxWarps;
+    if (w < 1) w = 1;
+    bp->warps = w;
+    bp->smem = per_warp * w;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_reduce_kernel, 32 * w, bp->smem);
+    cudaGetLastError();
+    if (per_sm < 1) per_sm = 1;
+    bp->grid = num_sms * per_sm;
+}
+
+cudaError_t configure_batched(int smem_optin) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, batched_reduce_kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batched_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin_minus_static(smem_optin, fa.sharedSizeBytes));
+}
+
+cudaError_t launch_batched_init(const BatchInst* dI, const BatchPlan& bp, int max_iter, int check_conv, double tol,
+                                cudaStream_t s) {
+    batched_init_kernel<<<(bp.count + 127) / 128, 128, 0, s>>>(dI, bp.count, max_iter, check_conv, tol);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batched_labels_kernel<<<bp.lblocks, kBatchLabelThreads, 0, s>>>(dI, bp.count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_trace(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s) {
+    batched_trace_kernel<<<bp.count, 1024, 0, s>>>(dI);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_pass(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s) {
+    batched_reduce_kernel<<<bp.grid, bp.warps * 32, bp.smem, s>>>(dI, bp.count, bp.units, bp.kmax, eval);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batched_zreduce_kernel<<<bp.zblocks, kZReduceRows, 0, s>>>(dI, bp.count, eval);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || eval) return e;
+    batched_assign_kernel<<<bp.ablocks, kAssignThreads, 0, s>>>(dI, bp.count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_copy_labels(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s) {
+    batched_copy_labels_kernel<<<bp.lblocks, kBatchLabelThreads, 0, s>>>(dI, bp.count);
+    return cudaGetLastError();
 }
 
 }  // namespace popcorn

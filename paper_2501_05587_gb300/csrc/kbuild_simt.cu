@@ -46,15 +46,15 @@ __device__ __forceinline__ float apply_kernel(float v, const KernParams& kp) {
     return expf(kp.neg_gamma_over_sigma2 * v);   // v = ||p_i - p_j||^2
 }
 
+// One upper-triangle tile (number `tile`) of K: 256 threads, 8 x 8 outputs each.
 template <int KIND>
-__global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restrict__ P, int n, int d,
-                                                          int64_t ldp, KernParams kp,
-                                                          float* __restrict__ K, int64_t ldk,
-                                                          float* __restrict__ kdiag, int T) {
+__device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, int d, int64_t ldp,
+                                            const KernParams& kp, float* __restrict__ K, int64_t ldk,
+                                            float* __restrict__ kdiag, int T, long long tile) {
     __shared__ __align__(16) float As[KC][LDS];
     __shared__ __align__(16) float Bs[KC][LDS];
     int bi, bj;
-    tri_coords((long long)blockIdx.x, T, &bi, &bj);
+    tri_coords(tile, T, &bi, &bj);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int row0 = bi * TILE, col0 = bj * TILE;
 
@@ -156,7 +156,41 @@ __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restric
     }
 }
 
+template <int KIND>
+__global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
+                                                          KernParams kp, float* __restrict__ K, int64_t ldk,
+                                                          float* __restrict__ kdiag, int T) {
+    kbuild_tile<KIND>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x);
+}
+
+// All instances of a batch: flattened tile b belongs to the instance whose
+// tile0 is the largest one <= b.
+__global__ void __launch_bounds__(256) batched_kbuild_kernel(const BatchInst* I, int count) {
+    const long long b = blockIdx.x;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (I[mid].tile0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchInst& x = I[lo];
+    const long long t = b - x.tile0;
+    switch (x.kp.kind) {
+        case POPCORN_LINEAR: kbuild_tile<POPCORN_LINEAR>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t); break;
+        case POPCORN_POLYNOMIAL:
+            kbuild_tile<POPCORN_POLYNOMIAL>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t);
+            break;
+        default: kbuild_tile<POPCORN_GAUSSIAN>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t); break;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batched_kbuild_simt(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s) {
+    if (bp.tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    batched_kbuild_kernel<<<(unsigned)bp.tiles, 256, 0, s>>>(dI, bp.count);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp, float* K,
                                int64_t ldk, float* kdiag, cudaStream_t s, int* launches) {

@@ -375,6 +375,7 @@ size_t kbuild_tc_workspace(int n, int d, int precision) {
 }
 
 cudaError_t configure_kbuild_tc() {
+    encode_fn();
     return cudaFuncSetAttribute(kbuild_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 

@@ -70,7 +70,8 @@ cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernPa
 // ---- K build on tensor cores (kbuild_tc.cu) ---------------------------------
 // Workspace bytes for the BF16 operand copies and row norms.
 size_t kbuild_tc_workspace(int n, int d, int precision);
-// Opt the tcgen05 kernel into its shared memory (once per device).
+// Opt the tcgen05 kernel into its shared memory (once per device) and look up
+// the driver's tensor-map encoder (so no lookup happens during stream capture).
 cudaError_t configure_kbuild_tc();
 // precision POPCORN_BF16 or POPCORN_BF16X3; *err (device) becomes nonzero if a
 // bounded wait inside the kernel ran out.
@@ -179,5 +180,60 @@ cudaError_t launch_reduce(const PassBuffers& b, const ReducePlan& plan, int eval
                           cudaStream_t s);
 cudaError_t launch_assign(const PassBuffers& b, const ReducePlan& plan, cudaStream_t s);
 cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s);
+
+// ---- batched mode (iterate.cu, kbuild_simt.cu) --------------------------------
+// One clustering instance of a batch, device-resident.  Flattened work of all
+// instances (K tiles, K-stream units, z blocks, assign blocks, label blocks)
+// is located by binary search over the *0 prefix fields.
+struct BatchInst {
+    const float* P;
+    int64_t ldp;
+    int d;
+    KernParams kp;
+    int T;                    // 128-row tiles of K
+    long long tile0;          // first flattened upper-triangle tile
+    float* K;
+    int64_t ldk;
+    float* kdiag;
+    int n, k, nseg, seglen;
+    uint8_t* lab8;
+    int32_t* lab32;
+    int32_t* counts;
+    float* Spart;
+    double* zpart;
+    double* zsum;
+    double* cnorm;
+    double* invm;
+    LoopState* st;
+    double* J_hist;
+    int32_t* changed_hist;
+    const int32_t* init_labels;
+    int32_t* labels_out;
+    int unit0, zblock0, ablock0, lblock0;
+};
+
+struct BatchPlan {
+    int count;
+    long long tiles;          // K tiles of all instances
+    int units, zblocks, ablocks, lblocks;
+    int kmax;
+    int warps, grid;          // batched K-stream launch
+    size_t smem;
+};
+
+constexpr int kBatchLabelThreads = 256;
+constexpr int kBatchSeg = 8192;       // columns per K-stream unit in batched mode (whole rows for n <= 8192)
+
+// per instance: loop state, labels/counts, (after the K build) trace of K
+cudaError_t launch_batched_init(const BatchInst* dI, const BatchPlan& bp, int max_iter, int check_conv, double tol,
+                                cudaStream_t s);
+cudaError_t launch_batched_trace(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s);
+cudaError_t launch_batched_kbuild_simt(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s);
+// one pass over every instance that has not stopped (K stream, z, argmin)
+cudaError_t launch_batched_pass(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s);
+cudaError_t launch_batched_copy_labels(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s);
+// warps / grid / shared memory of the batched K stream for clusters up to kmax
+void plan_batched_reduce(BatchPlan* bp, int num_sms, int smem_budget);
+cudaError_t configure_batched(int smem_optin);
 
 }  // namespace popcorn

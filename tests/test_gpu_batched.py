@@ -1,0 +1,109 @@
+"""GPU parity of batched mode (popcorn_fit_batched): many instances in one graph.
+
+Every instance must behave like an independent fit:
+  * one pass from given labels: new labels equal the oracle's step except
+    near-ties below 1e-6 of the row scale, and the objective of the new labels
+    matches the oracle to 1e-6 (FP32);
+  * whole fits: each instance's result equals a separate popcorn_fit of that
+    instance (same method, same pass count) up to FP32 summation order, and
+    converged labels are fixed points of the oracle's step;
+  * instances that converge early stop while the others go on.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+from tests.parity import FP32_OBJ_REL, label_mismatches, rel_err  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_05587_gb300 as mod
+    return mod
+
+
+def _batch(count=10, seed=3, n_lo=150, n_hi=1500):
+    wls = synth.batched_instances(count, seed=seed, n_lo=n_lo, n_hi=n_hi)
+    insts = [{"P": torch.from_numpy(w.P).cuda(), "k": w.k, "kernel": w.kernel,
+              "init_labels": torch.from_numpy(w.init_labels).cuda()} for w in wls]
+    return wls, insts
+
+
+def test_batched_one_pass_matches_oracle(pc):
+    wls, insts = _batch()
+    r = pc.popcorn_fit_batched(insts, max_iter=1, check_convergence=False)
+    for t, w in enumerate(wls):
+        Ko = oracle.kernel_matrix(w.P, w.kernel)
+        st = oracle.step(Ko, w.init_labels, w.k)
+        lab = r["labels"][t].cpu().numpy()
+        assert r["iterations"][t] == 1
+        assert label_mismatches(lab, st)[0] == 0, t
+        assert rel_err(r["objectives"][t], oracle.objective(Ko, lab, w.k)) <= FP32_OBJ_REL, t
+
+
+def test_batched_equals_separate_fits(pc):
+    wls, insts = _batch(count=8, seed=5)
+    r = pc.popcorn_fit_batched(insts, max_iter=40)
+    for t, w in enumerate(wls):
+        one = pc.popcorn_fit(insts[t]["P"], w.k, w.kernel, insts[t]["init_labels"], max_iter=40)
+        lab = r["labels"][t].cpu().numpy()
+        if np.array_equal(lab, one["labels"].cpu().numpy()):
+            assert r["iterations"][t] == one["iterations"]
+            assert rel_err(r["objectives"][t], one["objective"]) <= FP32_OBJ_REL
+        Ko = oracle.kernel_matrix(w.P, w.kernel)
+        assert rel_err(r["objectives"][t], oracle.objective(Ko, lab, w.k)) <= FP32_OBJ_REL
+        if r["iterations"][t] < 40:                      # converged: a fixed point of the oracle's step
+            assert label_mismatches(lab, oracle.step(Ko, lab, w.k))[0] == 0
+
+
+def test_batched_uneven_convergence_and_zero_iterations(pc):
+    wls, insts = _batch(count=6, seed=9)
+    r = pc.popcorn_fit_batched(insts, max_iter=100)
+    assert len(set(r["iterations"])) > 1                 # instances stop at different passes
+    r0 = pc.popcorn_fit_batched(insts, max_iter=0)
+    for t, w in enumerate(wls):
+        assert r0["iterations"][t] == 0
+        assert np.array_equal(r0["labels"][t].cpu().numpy(), w.init_labels)
+        Ko = oracle.kernel_matrix(w.P, w.kernel)
+        assert rel_err(r0["objectives"][t], oracle.objective(Ko, w.init_labels, w.k)) <= FP32_OBJ_REL
+
+
+def test_batched_bf16x3_objective(pc):
+    """bf16x3 keeps each coordinate to 2^-17 and drops lo*lo (2^-18), so B moves by <= 2^-16 of
+    sum |p_l q_l|; the degree-2 polynomial doubles that in K (~3e-5) and J's cancellation
+    (J well below trace K) amplifies it: bar 1e-4."""
+    wls, insts = _batch(count=6, seed=11)
+    r = pc.popcorn_fit_batched(insts, max_iter=10, precision="bf16x3", check_convergence=False)
+    for t, w in enumerate(wls):
+        Ko = oracle.kernel_matrix(w.P, w.kernel)
+        lab = r["labels"][t].cpu().numpy()
+        assert rel_err(r["objectives"][t], oracle.objective(Ko, lab, w.k)) <= 1e-4, t
+
+
+def test_batched_rejects_bad_instance(pc):
+    wls, insts = _batch(count=3, seed=1)
+    insts[1] = dict(insts[1], k=10_000)
+    with pytest.raises(pc.PopcornError) as ei:
+        pc.popcorn_fit_batched(insts, max_iter=3)
+    assert ei.value.status == 1 and "instance 1" in str(ei.value)
+
+
+def test_batched_full_size_sampled(pc):
+    """The 256-instance batch of the batched workload (n in [500, 8000]): sampled
+    instances checked against the oracle after a full 30-pass run."""
+    wls = synth.batched_instances(256, seed=0)
+    insts = [{"P": torch.from_numpy(w.P).cuda(), "k": w.k, "kernel": w.kernel,
+              "init_labels": torch.from_numpy(w.init_labels).cuda()} for w in wls]
+    r = pc.popcorn_fit_batched(insts, max_iter=30, check_convergence=False)
+    for t in (0, 1, 77, 200, 255):
+        w = wls[t]
+        Ko = oracle.kernel_matrix(w.P, w.kernel)
+        lab = r["labels"][t].cpu().numpy()
+        assert r["iterations"][t] == 30
+        assert rel_err(r["objectives"][t], oracle.objective(Ko, lab, w.k)) <= FP32_OBJ_REL, t
