@@ -41,6 +41,20 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+def aggregate_over_ranks(times, counts, dist, device):
+    """Whole-job figures of replicas run by every rank: the max of each time over
+    ranks (the job ends with its slowest rank) and the sum of each count."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(x) for x in times], [float(x) for x in counts]
+    import torch
+
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return t.tolist(), c.tolist()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,16 +363,9 @@ def main():
     t_e2e = time.perf_counter() - t0
     barrier()
 
-    if dist is not None:
-        t = torch.tensor([ms, t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, t_e2e = float(t[0]), float(t[1])
-        c = torch.tensor([iters, sum(r["iterations"] for r in e2e_res), launches], dtype=torch.float64,
-                         device="cuda")
-        dist.all_reduce(c)
-        iters_all, e2e_iters_all, launches_all = float(c[0]), float(c[1]), int(c[2])
-    else:
-        iters_all, e2e_iters_all, launches_all = float(iters), float(sum(r["iterations"] for r in e2e_res)), launches
+    (ms, t_e2e), (iters_all, e2e_iters_all, launches_all) = aggregate_over_ranks(
+        [ms, t_e2e], [iters, sum(r["iterations"] for r in e2e_res), launches], dist, "cuda")
+    launches_all = int(launches_all)
 
     if rank == 0:
         n, k = wl.n, wl.k
@@ -404,6 +411,28 @@ def main():
             "gpu_launches": launches_all,
             "clocks": clk,
         }
+        if args.workload == WORKLOAD and args.scale == 1.0:
+            # the same fits with K stored in FP16: half the bytes per pass (an extra, not the headline)
+            def step16():
+                return pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=True,
+                                      timing=True, labels_out=out, k_storage="fp16")
+            for _ in range(args.warmup):
+                step16()
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            r16 = [step16() for _ in range(args.steps)]
+            f1.record(stream)
+            torch.cuda.synchronize()
+            ms16 = f0.elapsed_time(f1)
+            it16 = sum(r["iterations"] for r in r16)
+            red16 = sum(r["info"]["reduce_ms"] for r in r16) / max(1, sum(r["info"]["reduce_launches"] for r in r16))
+            line["k_fp16"] = {"value": it16 / (ms16 / 1e3), "unit": "iters/s", "passes_per_fit": it16 / args.steps,
+                              "objective_rel_diff_vs_fp32_k": abs(r16[0]["objective"] - results[0]["objective"])
+                              / abs(results[0]["objective"]),
+                              "reduce_avg_launch_ms": red16,
+                              "reduce_GBps": (2.0 * n * n + n) / (red16 / 1e3) / 1e9 if red16 > 0 else None}
         if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)

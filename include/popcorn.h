@@ -83,13 +83,23 @@ typedef enum {
     POPCORN_FP8 = 3      /* reserved: FP8 E4M3 with per-row scales (recompute path)                   */
 } popcorn_precision;
 
+/* Element type of a stored K (the paper stores FP32). */
+typedef enum {
+    POPCORN_K_FP32 = 0,
+    POPCORN_K_FP16 = 1,   /* half the bytes per pass; values must fit FP16 (e.g. Gaussian K <= 1) */
+    POPCORN_K_BF16 = 2    /* half the bytes per pass; FP32 range, 8 significant bits             */
+} popcorn_k_storage;
+
 typedef struct {
     int32_t precision;          /* popcorn_precision for the K build                         */
     int32_t store_k;            /* 1: materialize K once (the paper's design)                */
     int32_t check_convergence;  /* 1: stop when a pass changes no label (or on tol); 0: run
                                    exactly max_iter passes (the paper's fixed-iteration mode) */
     int32_t timing;             /* 1: record CUDA-event times per phase into popcorn_fit_info */
-    int64_t reserved[6];        /* must be zero                                              */
+    int32_t k_storage;          /* popcorn_k_storage of the stored K (FP32 build only for the
+                                   half types); 0 = FP32                                    */
+    int32_t reserved32;         /* must be zero                                              */
+    int64_t reserved[5];        /* must be zero                                              */
 } popcorn_options;
 
 /* Optional per-call report of popcorn_fit (all fields written by the call,

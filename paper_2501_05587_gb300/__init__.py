@@ -66,7 +66,11 @@ class _Kernel(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("store_k", ctypes.c_int32),
                 ("check_convergence", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 6)]
+                ("k_storage", ctypes.c_int32), ("reserved32", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 5)]
+
+
+K_STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 
 
 class _FitInfo(ctypes.Structure):
@@ -221,11 +225,13 @@ def popcorn_assign_step_noalloc(K, kdiag, labels, k: int, want_E: bool = False, 
 
 def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float = 0.0,
                 precision: str = "fp32", check_convergence: bool = True, timing: bool = False,
-                history: bool = False, labels_out=None, store_k: bool = True, stream=None) -> dict:
+                history: bool = False, labels_out=None, store_k: bool = True, k_storage: str = "fp32",
+                stream=None) -> dict:
     """Kernel K-means (Alg. 2).  P and init_labels may live on the host or the device.
 
     ``store_k=False`` selects the recompute path (K never stored; precision
-    "bf16" or "fp8").  Returns {"labels", "objective", "iterations", "info"};
+    "bf16" or "fp8").  ``k_storage`` ("fp32", "fp16", "bf16") is the element
+    type of a stored K.  Returns {"labels", "objective", "iterations", "info"};
     labels land where ``labels_out`` lives (default: same place as init_labels).
     """
     torch = _torch()
@@ -248,7 +254,7 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
         else:
             labels_out = torch.empty(n, dtype=torch.int32, device=init_labels.device)
     opt = _Options(PRECISION[precision], 1 if store_k else 0, 1 if check_convergence else 0, 1 if timing else 0,
-                   (ctypes.c_int64 * 6)())
+                   K_STORAGE[k_storage], 0, (ctypes.c_int64 * 5)())
     info = _FitInfo()
     Jh = (ctypes.c_double * max(1, max_iter))() if history else None
     Ch = (ctypes.c_int32 * max(1, max_iter))() if history else None
@@ -292,8 +298,8 @@ def popcorn_fit_batched(instances, max_iter: int, tol: float = 0.0, precision: s
         outs.append(out)
         arr[t] = _Instance(P.data_ptr(), P.shape[0], P.shape[1], P.stride(0), int(x["k"]), _kernel(x["kernel"]),
                            lab.data_ptr(), out.data_ptr())
-    opt = _Options(PRECISION[precision], 1, 1 if check_convergence else 0, 1 if timing else 0,
-                   (ctypes.c_int64 * 6)())
+    opt = _Options(PRECISION[precision], 1, 1 if check_convergence else 0, 1 if timing else 0, 0, 0,
+                   (ctypes.c_int64 * 5)())
     objs = (ctypes.c_double * len(instances))()
     its = (ctypes.c_int32 * len(instances))()
     info = _FitInfo()

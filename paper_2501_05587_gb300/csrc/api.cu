@@ -180,17 +180,20 @@ popcorn_status check_kernel(const popcorn_kernel& kern, KernParams* kp) {
 // tiles; their operand copies come from `ws`, and *err (device) reports a
 // timed-out wait inside the kernel.
 popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, const KernParams& kp,
-                                   int precision, float* K, int64_t ldk, float* kdiag, Workspace* ws,
+                                   int precision, void* K, int64_t ldk, int k_storage, float* kdiag, Workspace* ws,
                                    int* err, int num_sms, cudaStream_t s, int* launches) {
     if (precision == POPCORN_FP32) {
-        POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, kdiag, s, launches));
+        POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, k_storage, kdiag, s, launches));
         return POPCORN_OK;
     }
+    if (k_storage != POPCORN_K_FP32)
+        return fail(POPCORN_ERR_UNSUPPORTED, "FP16/BF16 K storage comes from the FP32 build in this build");
     if (precision != POPCORN_BF16 && precision != POPCORN_BF16X3)
         return fail(POPCORN_ERR_UNSUPPORTED, "precision %d is not available for a stored K", precision);
     unsigned char* w;
     POPCORN_TRY(ws->alloc(&w, kbuild_tc_workspace(n, d, precision), "BF16 operands"));
-    cudaError_t e = launch_kbuild_tc(P, n, d, ldp, kp, precision, K, ldk, kdiag, w, err, num_sms, s, launches);
+    cudaError_t e = launch_kbuild_tc(P, n, d, ldp, kp, precision, static_cast<float*>(K), ldk, kdiag, w, err, num_sms,
+                                     s, launches);
     if (e == cudaErrorInvalidValue)
         return fail(POPCORN_ERR_CUDA, "tensor map creation failed (cuTensorMapEncodeTiled unavailable or rejected)");
     POPCORN_CUDA(e);
@@ -465,14 +468,14 @@ popcorn_status popcorn_kernel_matrix(const float* P, int64_t n, int32_t d, int64
     int launches = 0;
     cudaStream_t s = (cudaStream_t)stream;
     if (precision == POPCORN_FP32)
-        return build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, kdiag, nullptr, nullptr, dev->sms, s,
-                                   &launches);
+        return build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, POPCORN_K_FP32, kdiag, nullptr, nullptr,
+                                   dev->sms, s, &launches);
     Workspace ws(dev->pool, s);
     int* err;
     POPCORN_TRY(ws.alloc(&err, 1, "error flag"));
     POPCORN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    POPCORN_TRY(build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, kdiag, &ws, err, dev->sms, s,
-                                    &launches));
+    POPCORN_TRY(build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, POPCORN_K_FP32, kdiag, &ws, err,
+                                    dev->sms, s, &launches));
     int herr = 0;
     POPCORN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     POPCORN_CUDA(cudaStreamSynchronize(s));
@@ -562,8 +565,11 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         return fail(POPCORN_ERR_INVALID, "k = %d outside [1, min(n - 1, %d)]", k, kMaxClusters);
     if (max_iter < 0) return fail(POPCORN_ERR_INVALID, "max_iter = %d < 0", max_iter);
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
-    for (int r = 0; r < 6; ++r)
+    if (opt.reserved32 != 0) return fail(POPCORN_ERR_INVALID, "options.reserved32 must be 0");
+    for (int r = 0; r < 5; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
+    if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)
+        return fail(POPCORN_ERR_INVALID, "unknown k_storage %d", opt.k_storage);
     if (opt.store_k != 0 && opt.store_k != 1) return fail(POPCORN_ERR_INVALID, "store_k must be 0 or 1");
     if (opt.store_k == 0 && opt.precision != POPCORN_BF16 && opt.precision != POPCORN_FP8)
         return fail(POPCORN_ERR_UNSUPPORTED, "the recompute path (store_k = 0) runs in POPCORN_BF16 or POPCORN_FP8");
@@ -577,8 +583,10 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         return fit_recompute(P, n, d, ldp, k, kp, init_labels, max_iter, tol, opt, labels_out, objective_out,
                              iterations_out, info, s, dev);
     const int ni = (int)n;
-    const int64_t ldk = (n + 3) / 4 * 4;
-    ReducePlan plan = plan_reduce(ni, k, dev->sms, dev->reduce_smem);
+    const int ks = opt.k_storage;
+    const size_t kelem = ks == POPCORN_K_FP32 ? 4 : 2;
+    const int64_t ldk = ks == POPCORN_K_FP32 ? (n + 3) / 4 * 4 : (n + 7) / 8 * 8;   // 16-byte rows
+    ReducePlan plan = plan_reduce(ni, k, dev->sms, dev->reduce_smem, ks);
     if (plan.grid == 0) return fail(POPCORN_ERR_UNSUPPORTED, "n = %d is too large for the materialized path", ni);
     const bool timing = opt.timing != 0;
     int launches = 0;
@@ -606,14 +614,15 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     }
 
     PassBuffers b{};
-    float* K;
+    unsigned char* K;
     float* kdiag;
-    POPCORN_TRY(ws.alloc(&K, (size_t)ni * (size_t)ldk, "kernel matrix"));
+    POPCORN_TRY(ws.alloc(&K, (size_t)ni * (size_t)ldk * kelem, "kernel matrix"));
     POPCORN_TRY(ws.alloc(&kdiag, (size_t)ni, "diag(K)"));
     const size_t nlab = ((size_t)ni + 15) & ~(size_t)15;
     const int hist_len = max_iter > 0 ? max_iter : 1;
     b.K = K;
     b.ldk = ldk;
+    b.k_storage = ks;
     b.kdiag = kdiag;
     b.n = ni;
     b.k = k;
@@ -639,7 +648,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     }
     POPCORN_CUDA(cudaMemsetAsync(b.counts, 0, 2 * (size_t)k * sizeof(int32_t), s));
     POPCORN_CUDA(launch_init_state(b.st, max_iter, opt.check_convergence ? 1 : 0, tol, s));
-    POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, kdiag, &ws, &b.st->kbuild_err,
+    POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, ks, kdiag, &ws, &b.st->kbuild_err,
                                     dev->sms, s, &launches));
     POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
     POPCORN_CUDA(launch_init_labels(Ld, ni, k, b.lab32, b.lab8, b.counts, b.st, s));
@@ -774,8 +783,11 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         return fail(POPCORN_ERR_INVALID, "count must be >= 1 and the output arrays non-null");
     if (max_iter < 0) return fail(POPCORN_ERR_INVALID, "max_iter = %d < 0", max_iter);
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
-    for (int r = 0; r < 6; ++r)
+    if (opt.reserved32 != 0) return fail(POPCORN_ERR_INVALID, "options.reserved32 must be 0");
+    for (int r = 0; r < 5; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
+    if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)
+        return fail(POPCORN_ERR_INVALID, "unknown k_storage %d", opt.k_storage);
     if (opt.store_k != 1) return fail(POPCORN_ERR_UNSUPPORTED, "batched mode stores K (store_k = 1)");
     if (opt.precision != POPCORN_FP32 && opt.precision != POPCORN_BF16 && opt.precision != POPCORN_BF16X3)
         return fail(POPCORN_ERR_UNSUPPORTED, "batched mode runs in FP32, BF16 or BF16X3");

@@ -17,6 +17,8 @@
 #include "popcorn_internal.cuh"
 
 #include <cuda/std/limits>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace popcorn {
 namespace {
@@ -29,6 +31,49 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) {
     return v;
 }
 
+// 16 bytes of a K row: 4 FP32 or 8 FP16 / BF16 elements, and their labels.
+template <typename TK> struct KVec;
+template <> struct KVec<float> {
+    static constexpr int N = 4;
+    using Lab = uint32_t;
+    __device__ static void unpack(const float4& r, float (&o)[4]) {
+        o[0] = r.x; o[1] = r.y; o[2] = r.z; o[3] = r.w;
+    }
+    __device__ static uint32_t label(const Lab& L, int e) { return (L >> (8 * e)) & 0xffu; }
+};
+template <> struct KVec<__half> {
+    static constexpr int N = 8;
+    using Lab = uint2;
+    __device__ static void unpack(const float4& r, float (&o)[8]) {
+        const uint32_t w[4] = {__float_as_uint(r.x), __float_as_uint(r.y), __float_as_uint(r.z), __float_as_uint(r.w)};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[t]));
+            o[2 * t] = f.x;
+            o[2 * t + 1] = f.y;
+        }
+    }
+    __device__ static uint32_t label(const Lab& L, int e) { return ((e < 4 ? L.x : L.y) >> (8 * (e & 3))) & 0xffu; }
+};
+template <> struct KVec<__nv_bfloat16> {
+    static constexpr int N = 8;
+    using Lab = uint2;
+    __device__ static void unpack(const float4& r, float (&o)[8]) {
+        const uint32_t w[4] = {__float_as_uint(r.x), __float_as_uint(r.y), __float_as_uint(r.z), __float_as_uint(r.w)};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[t]));
+            o[2 * t] = f.x;
+            o[2 * t + 1] = f.y;
+        }
+    }
+    __device__ static uint32_t label(const Lab& L, int e) { return ((e < 4 ? L.x : L.y) >> (8 * (e & 3))) & 0xffu; }
+};
+
+__device__ __forceinline__ float kval(float v) { return v; }
+__device__ __forceinline__ float kval(__half v) { return __half2float(v); }
+__device__ __forceinline__ float kval(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 // hi + lo += x without rounding loss (Knuth's TwoSum; FP32 pipe only).
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
     const float s = hi + x;
@@ -38,9 +83,9 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
     lo += e;
 }
 
-template <int UNR, bool LAB_SMEM>
-__device__ __forceinline__ void load_batch(const float4* row4, const uint32_t* lab4, int q, int q1,
-                                           float4 (&v)[UNR], uint32_t (&L)[UNR]) {
+template <int UNR, bool LAB_SMEM, typename LabT = uint32_t>
+__device__ __forceinline__ void load_batch(const float4* row4, const LabT* lab4, int q, int q1,
+                                           float4 (&v)[UNR], LabT (&L)[UNR]) {
 #pragma unroll
     for (int t = 0; t < UNR; ++t) {
         const int qq = q + 32 * t;
@@ -49,7 +94,7 @@ __device__ __forceinline__ void load_batch(const float4* row4, const uint32_t* l
             L[t] = LAB_SMEM ? lab4[qq] : __ldg(lab4 + qq);
         } else {
             v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-            L[t] = 0u;
+            L[t] = LabT{};
         }
     }
 }
@@ -119,7 +164,7 @@ __device__ void finalize_pass(const double* zpart, int nblocks, int k, const int
 }
 
 struct ReduceArgs {
-    const float* K;
+    const void* K;        // TK elements, row pitch ldk elements (16-byte aligned rows)
     int64_t ldk;
     int n, k, nseg, seglen;
     const uint8_t* lab8;
@@ -141,8 +186,11 @@ struct ReduceArgs {
 // group; for larger k (KB == 0) lane c walks row c in rotated order.  UNR
 // float4 per lane per batch; the next batch -- across unit boundaries too --
 // is in flight while the current one is scattered.
-template <int KB, int UNR, bool LAB_SMEM>
+template <int KB, int UNR, bool LAB_SMEM, typename TK>
 __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceArgs a) {
+    using V = KVec<TK>;
+    using LabT = typename V::Lab;
+    constexpr int NV = V::N;
     LoopState* st = a.st;
     if (a.eval_only) {
         // J(final labels) is already known when the last pass changed nothing
@@ -174,7 +222,8 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceA
     __syncthreads();
 
     const uint8_t* labs = LAB_SMEM ? slab : a.lab8;
-    const uint32_t* lab4 = reinterpret_cast<const uint32_t*>(labs);
+    const LabT* lab4 = reinterpret_cast<const LabT*>(labs);
+    const TK* Kb = static_cast<const TK*>(a.K);
     float* accw = sacc + (size_t)warp * k * 32;   // this warp's [k][32] block
     float* accl = accw + lane;
     float* zwh = zhi + (size_t)warp * k;
@@ -198,36 +247,36 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceA
             ss = uu - ii * nseg;
             const int c0 = ss * a.seglen;
             cc1 = min(n, c0 + a.seglen);
-            qqb = c0 >> 2;
-            qq1 = cc1 >> 2;
-            r4 = reinterpret_cast<const float4*>(a.K + (int64_t)ii * a.ldk);
+            qqb = c0 / NV;
+            qq1 = cc1 / NV;
+            r4 = reinterpret_cast<const float4*>(Kb + (int64_t)ii * a.ldk);
         };
         int i, s, c1, qb, q1;
         const float4* row4;
         geom(u, i, s, c1, qb, q1, row4);
         float4 v[UNR];
-        uint32_t L[UNR];
-        load_batch<UNR, LAB_SMEM>(row4, lab4, qb + lane, q1, v, L);
+        LabT L[UNR];
+        load_batch<UNR, LAB_SMEM, LabT>(row4, lab4, qb + lane, q1, v, L);
         while (true) {
             const bool last = qb + 32 * UNR >= q1;
             const int un = last ? u + GW : u;
             int in_ = i, sn = s, c1n = c1, qbn = qb + 32 * UNR, q1n = q1;
             const float4* row4n = row4;
             float4 vn[UNR];
-            uint32_t Ln[UNR];
+            LabT Ln[UNR];
             if (last && un < units) geom(un, in_, sn, c1n, qbn, q1n, row4n);
-            if (!last || un < units) load_batch<UNR, LAB_SMEM>(row4n, lab4, qbn + lane, q1n, vn, Ln);
+            if (!last || un < units) load_batch<UNR, LAB_SMEM, LabT>(row4n, lab4, qbn + lane, q1n, vn, Ln);
 #pragma unroll
             for (int t = 0; t < UNR; ++t) {
-                scatter(L[t] & 0xffu, v[t].x);
-                scatter((L[t] >> 8) & 0xffu, v[t].y);
-                scatter((L[t] >> 16) & 0xffu, v[t].z);
-                scatter(L[t] >> 24, v[t].w);
+                float e[NV];
+                V::unpack(v[t], e);
+#pragma unroll
+                for (int x = 0; x < NV; ++x) scatter(V::label(L[t], x), e[x]);
             }
             if (last) {
-                {   // ragged tail of the row (n not a multiple of 4)
-                    const int j = (q1 << 2) + lane;
-                    if (j < c1) scatter(labs[j], a.K[(int64_t)i * a.ldk + j]);
+                {   // ragged tail of the row (n not a multiple of the vector width)
+                    const int j = q1 * NV + lane;
+                    if (j < c1) scatter(labs[j], kval(Kb[(int64_t)i * a.ldk + j]));
                 }
                 const int li = labs[i];
                 float* out = a.Spart + ((int64_t)i * nseg + s) * k;   // layout [i][s][c]
@@ -528,18 +577,28 @@ namespace {
 
 using ReduceFn = void (*)(ReduceArgs);
 
-ReduceFn reduce_fn(int variant, bool lab_smem) {
+// 16-byte loads per lane per batch: 4 for FP32 K, 2 for half types (8 elements each)
+template <typename TK>
+ReduceFn reduce_fn_t(int variant, bool lab_smem) {
+    constexpr int U = sizeof(TK) == 4 ? 4 : 2;
     switch (variant) {
-        case kReduceBfly4: return lab_smem ? reduce_kernel<4, 4, true> : reduce_kernel<4, 4, false>;
-        case kReduceBfly8: return lab_smem ? reduce_kernel<8, 4, true> : reduce_kernel<8, 4, false>;
-        default: return lab_smem ? reduce_kernel<0, 4, true> : reduce_kernel<0, 4, false>;
+        case kReduceBfly4: return lab_smem ? reduce_kernel<4, U, true, TK> : reduce_kernel<4, U, false, TK>;
+        case kReduceBfly8: return lab_smem ? reduce_kernel<8, U, true, TK> : reduce_kernel<8, U, false, TK>;
+        default: return lab_smem ? reduce_kernel<0, U, true, TK> : reduce_kernel<0, U, false, TK>;
     }
+}
+
+ReduceFn reduce_fn(int variant, bool lab_smem, int k_storage = POPCORN_K_FP32) {
+    if (k_storage == POPCORN_K_FP16) return reduce_fn_t<__half>(variant, lab_smem);
+    if (k_storage == POPCORN_K_BF16) return reduce_fn_t<__nv_bfloat16>(variant, lab_smem);
+    return reduce_fn_t<float>(variant, lab_smem);
 }
 
 }  // namespace
 
-ReducePlan plan_reduce(int n, int k, int num_sms, int smem_budget) {
+ReducePlan plan_reduce(int n, int k, int num_sms, int smem_budget, int k_storage) {
     ReducePlan p{};
+    p.k_storage = k_storage;
     p.variant = k <= 4 ? kReduceBfly4 : (k <= 8 ? kReduceBfly8 : kReduceRotated);
     const size_t nlab = ((size_t)n + 15) & ~(size_t)15;
     const size_t per_warp = (size_t)k * 32 * sizeof(float) + 2 * (size_t)k * sizeof(float);
@@ -551,7 +610,8 @@ ReducePlan plan_reduce(int n, int k, int num_sms, int smem_budget) {
     p.warps = w;
     p.smem = base + per_warp * w;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reduce_fn(p.variant, p.labels_in_smem), 32 * w, p.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reduce_fn(p.variant, p.labels_in_smem, k_storage), 32 * w,
+                                                  p.smem);
     cudaGetLastError();
     if (per_sm < 1) per_sm = 1;
     p.grid = num_sms * per_sm;
@@ -604,7 +664,7 @@ cudaError_t launch_reduce(const PassBuffers& b, const ReducePlan& plan, int eval
     a.st = b.st;
     a.J_hist = b.J_hist;
     a.eval_only = eval_only;
-    reduce_fn(plan.variant, plan.labels_in_smem)<<<plan.grid, plan.warps * 32, plan.smem, s>>>(a);
+    reduce_fn(plan.variant, plan.labels_in_smem, plan.k_storage)<<<plan.grid, plan.warps * 32, plan.smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -656,19 +716,22 @@ cudaError_t launch_assign(const PassBuffers& b, const ReducePlan& plan, cudaStre
 // allows next to their static shared memory; *usable receives that size.
 cudaError_t configure_reduce_smem(int optin, int* usable) {
     size_t st = 0;
-    for (int v = 0; v < 3; ++v)
-        for (int l = 0; l < 2; ++l) {
-            cudaFuncAttributes fa;
-            cudaError_t e = cudaFuncGetAttributes(&fa, reduce_fn(v, l != 0));
-            if (e != cudaSuccess) return e;
-            if (fa.sharedSizeBytes > st) st = fa.sharedSizeBytes;
-        }
+    for (int ks = 0; ks < 3; ++ks)
+        for (int v = 0; v < 3; ++v)
+            for (int l = 0; l < 2; ++l) {
+                cudaFuncAttributes fa;
+                cudaError_t e = cudaFuncGetAttributes(&fa, reduce_fn(v, l != 0, ks));
+                if (e != cudaSuccess) return e;
+                if (fa.sharedSizeBytes > st) st = fa.sharedSizeBytes;
+            }
     const int bytes = optin - (int)((st + 127) / 128 * 128);
-    for (int v = 0; v < 3; ++v)
-        for (int l = 0; l < 2; ++l) {
-            cudaError_t e = cudaFuncSetAttribute(reduce_fn(v, l != 0), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            if (e != cudaSuccess) return e;
-        }
+    for (int ks = 0; ks < 3; ++ks)
+        for (int v = 0; v < 3; ++v)
+            for (int l = 0; l < 2; ++l) {
+                cudaError_t e = cudaFuncSetAttribute(reduce_fn(v, l != 0, ks), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     bytes);
+                if (e != cudaSuccess) return e;
+            }
     *usable = bytes;
     return cudaSuccess;
 }

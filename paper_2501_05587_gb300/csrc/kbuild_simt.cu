@@ -11,6 +11,8 @@
 // expansion of Eq. 12 cancels there).
 #include "popcorn_internal.cuh"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 namespace popcorn {
@@ -46,10 +48,43 @@ __device__ __forceinline__ float apply_kernel(float v, const KernParams& kp) {
     return expf(kp.neg_gamma_over_sigma2 * v);   // v = ||p_i - p_j||^2
 }
 
+// Stored element type of K and its 4-wide packed store.
+template <typename TK> struct KStore;
+template <> struct KStore<float> {
+    __device__ static float round(float v) { return v; }
+    __device__ static void put4(float* p, float a, float b, float c, float d) {
+        *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+    }
+    __device__ static void put1(float* p, float a) { *p = a; }
+};
+template <> struct KStore<__half> {
+    __device__ static float round(float v) { return __half2float(__float2half_rn(v)); }
+    __device__ static void put4(__half* p, float a, float b, float c, float d) {
+        __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&lo);
+        u.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(p) = u;
+    }
+    __device__ static void put1(__half* p, float a) { *p = __float2half_rn(a); }
+};
+template <> struct KStore<__nv_bfloat16> {
+    __device__ static float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+    __device__ static void put4(__nv_bfloat16* p, float a, float b, float c, float d) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&lo);
+        u.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(p) = u;
+    }
+    __device__ static void put1(__nv_bfloat16* p, float a) { *p = __float2bfloat16_rn(a); }
+};
+
 // One upper-triangle tile (number `tile`) of K: 256 threads, 8 x 8 outputs each.
-template <int KIND>
+// kdiag receives the stored (rounded) diagonal so that diag K and K agree.
+template <int KIND, typename TK = float>
 __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, int d, int64_t ldp,
-                                            const KernParams& kp, float* __restrict__ K, int64_t ldk,
+                                            const KernParams& kp, TK* __restrict__ K, int64_t ldk,
                                             float* __restrict__ kdiag, int T, long long tile) {
     __shared__ __align__(16) float As[KC][LDS];
     __shared__ __align__(16) float Bs[KC][LDS];
@@ -116,7 +151,7 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
                 int c = col0 + tx * 4 + (y & 3) + 64 * (y >> 2);
                 if (r == c && r < n) {
                     if (KIND == POPCORN_GAUSSIAN) acc[x][y] = 1.0f;
-                    kdiag[r] = acc[x][y];
+                    kdiag[r] = KStore<TK>::round(acc[x][y]);
                 }
             }
         }
@@ -126,17 +161,17 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
     for (int x = 0; x < 8; ++x) {
         int r = row0 + ty * 4 + (x & 3) + 64 * (x >> 2);
         if (r >= n) continue;
-        float* Kr = K + (int64_t)r * ldk;
+        TK* Kr = K + (int64_t)r * ldk;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             int c = col0 + 64 * h + tx * 4;
-            float4 v = make_float4(acc[x][4 * h], acc[x][4 * h + 1], acc[x][4 * h + 2], acc[x][4 * h + 3]);
+            const float v0 = acc[x][4 * h], v1 = acc[x][4 * h + 1], v2 = acc[x][4 * h + 2], v3 = acc[x][4 * h + 3];
             if (c + 3 < n) {
-                *reinterpret_cast<float4*>(Kr + c) = v;
+                KStore<TK>::put4(Kr + c, v0, v1, v2, v3);
             } else {
-                if (c < n) Kr[c] = v.x;
-                if (c + 1 < n) Kr[c + 1] = v.y;
-                if (c + 2 < n) Kr[c + 2] = v.z;
+                if (c < n) KStore<TK>::put1(Kr + c, v0);
+                if (c + 1 < n) KStore<TK>::put1(Kr + c + 1, v1);
+                if (c + 2 < n) KStore<TK>::put1(Kr + c + 2, v2);
             }
         }
     }
@@ -145,22 +180,42 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         for (int y = 0; y < 8; ++y) {
             int c = col0 + tx * 4 + (y & 3) + 64 * (y >> 2);
             if (c >= n) continue;
-            float* Kc = K + (int64_t)c * ldk;
+            TK* Kc = K + (int64_t)c * ldk;
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
                 int r = row0 + 64 * g + ty * 4;   // row0 tiles are full (bi < bj => rows < n)
-                float4 v = make_float4(acc[4 * g][y], acc[4 * g + 1][y], acc[4 * g + 2][y], acc[4 * g + 3][y]);
-                *reinterpret_cast<float4*>(Kc + r) = v;
+                KStore<TK>::put4(Kc + r, acc[4 * g][y], acc[4 * g + 1][y], acc[4 * g + 2][y], acc[4 * g + 3][y]);
             }
         }
     }
 }
 
-template <int KIND>
+template <int KIND, typename TK>
 __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
-                                                          KernParams kp, float* __restrict__ K, int64_t ldk,
+                                                          KernParams kp, TK* __restrict__ K, int64_t ldk,
                                                           float* __restrict__ kdiag, int T) {
-    kbuild_tile<KIND>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x);
+    kbuild_tile<KIND, TK>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x);
+}
+
+template <typename TK>
+cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernParams kp, TK* K, int64_t ldk,
+                              float* kdiag, cudaStream_t s) {
+    const int T = (n + TILE - 1) / TILE;
+    const long long tiles = (long long)T * (T + 1) / 2;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)tiles), block(256);
+    switch (kp.kind) {
+        case POPCORN_LINEAR:
+            kbuild_simt_kernel<POPCORN_LINEAR, TK><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            break;
+        case POPCORN_POLYNOMIAL:
+            kbuild_simt_kernel<POPCORN_POLYNOMIAL, TK><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            break;
+        default:
+            kbuild_simt_kernel<POPCORN_GAUSSIAN, TK><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            break;
+    }
+    return cudaGetLastError();
 }
 
 // All instances of a batch: flattened tile b belongs to the instance whose
@@ -192,25 +247,14 @@ cudaError_t launch_batched_kbuild_simt(const BatchInst* dI, const BatchPlan& bp,
     return cudaGetLastError();
 }
 
-cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp, float* K,
-                               int64_t ldk, float* kdiag, cudaStream_t s, int* launches) {
-    const int T = (n + TILE - 1) / TILE;
-    const long long tiles = (long long)T * (T + 1) / 2;
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)tiles), block(256);
-    switch (kp.kind) {
-        case POPCORN_LINEAR:
-            kbuild_simt_kernel<POPCORN_LINEAR><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
-            break;
-        case POPCORN_POLYNOMIAL:
-            kbuild_simt_kernel<POPCORN_POLYNOMIAL><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
-            break;
-        default:
-            kbuild_simt_kernel<POPCORN_GAUSSIAN><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
-            break;
-    }
+cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp, void* K, int64_t ldk,
+                               int k_storage, float* kdiag, cudaStream_t s, int* launches) {
     if (launches) ++*launches;
-    return cudaGetLastError();
+    if (k_storage == POPCORN_K_FP16)
+        return launch_simt_typed(P, n, d, ldp, kp, static_cast<__half*>(K), ldk, kdiag, s);
+    if (k_storage == POPCORN_K_BF16)
+        return launch_simt_typed(P, n, d, ldp, kp, static_cast<__nv_bfloat16*>(K), ldk, kdiag, s);
+    return launch_simt_typed(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
 }
 
 }  // namespace popcorn

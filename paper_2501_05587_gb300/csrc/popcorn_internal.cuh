@@ -52,6 +52,7 @@ enum { kReduceBfly4 = 0, kReduceBfly8 = 1, kReduceRotated = 2 };
 // Launch geometry of the K-streaming reduction (segment-split rows).
 struct ReducePlan {
     int variant;     // kReduceBfly4 / kReduceBfly8 / kReduceRotated
+    int k_storage;   // element type of K (popcorn_k_storage)
     int grid;        // blocks
     int warps;       // warps per block
     int nseg;        // column segments per row
@@ -64,8 +65,9 @@ struct ReducePlan {
 void set_error_message(const char* msg);
 
 // ---- K build (kbuild_simt.cu) ------------------------------------------------
+// K is float, __half or __nv_bfloat16 by k_storage (popcorn_k_storage); ldk in elements.
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp,
-                               float* K, int64_t ldk, float* kdiag, cudaStream_t s, int* launches);
+                               void* K, int64_t ldk, int k_storage, float* kdiag, cudaStream_t s, int* launches);
 
 // ---- K build on tensor cores (kbuild_tc.cu) ---------------------------------
 // Workspace bytes for the BF16 operand copies and row norms.
@@ -137,7 +139,7 @@ int recompute_sort_blocks(int n);
 // allows (call once per device, with it current, before plan_reduce);
 // *usable receives the dynamic bytes plan_reduce may use.
 cudaError_t configure_reduce_smem(int optin, int* usable);
-ReducePlan plan_reduce(int n, int k, int num_sms, int smem_optin);
+ReducePlan plan_reduce(int n, int k, int num_sms, int smem_optin, int k_storage = 0);
 
 cudaError_t launch_init_state(LoopState* st, int max_iter, int check_conv, double tol,
                               cudaStream_t s);
@@ -146,8 +148,9 @@ cudaError_t launch_init_labels(const int32_t* in, int n, int k, int32_t* lab32, 
                                int32_t* counts, LoopState* st, cudaStream_t s);
 
 struct PassBuffers {
-    const float* K;
-    int64_t ldk;
+    const void* K;        // float / __half / __nv_bfloat16 by k_storage
+    int64_t ldk;          // elements
+    int k_storage;        // popcorn_k_storage
     const float* kdiag;
     int n, k;
     int32_t* lab32;
