@@ -279,7 +279,8 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceA
                     if (j < c1) scatter(labs[j], kval(Kb[(int64_t)i * a.ldk + j]));
                 }
                 const int li = labs[i];
-                float* out = a.Spart + ((int64_t)i * nseg + s) * k;   // layout [i][s][c]
+                // layout [s][c][i] (i fastest): cluster c of this unit at out[c * n]
+                float* out = a.Spart + (size_t)s * k * n + i;
                 __syncwarp();
                 if constexpr (KB > 0) {
                     float part[KB];
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceA
                     const float tot = butterfly<KB>(part, lane);
                     const int c = bfly_cluster<KB>(lane);
                     if ((lane & (32 / KB - 1)) == 0 && c < k) {
-                        out[c] = tot;
+                        out[(size_t)c * n] = tot;
                         if (c == li) ff_add(zwh[c], zwl[c], tot);
                     }
                 } else {
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceA
                                 tot += row[idx];
                                 row[idx] = 0.f;
                             }
-                            out[c] = tot;
+                            out[(size_t)c * n] = tot;
                             if (c == li) ff_add(zwh[c], zwl[c], tot);
                         }
                     }
@@ -383,12 +384,13 @@ __device__ __forceinline__ void assign_body(const AssignArgs& a, int block, int 
         const double kd = (double)a.kdiag[i];
         double best = cuda::std::numeric_limits<double>::infinity();
         int bi = li;
-        const float* Si = a.Spart + (int64_t)i * a.nseg * k;
+        const float* Si = a.Spart + i;               // [s][c][i]: consecutive threads, consecutive rows
+        const size_t cs = (size_t)n, ss = (size_t)k * n;
         for (int c = 0; c < k; ++c) {
             const int mc = m[c];
             float hi = 0.f, lo = 0.f;
 #pragma unroll 8
-            for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[(int64_t)s * k + c]);
+            for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[s * ss + c * cs]);
             const double E = ((double)hi + (double)lo) * a.invm[c];   // (K V^T)_ic
             if (a.E_out) a.E_out[(int64_t)i * k + c] = (float)E;
             if (mc == 0) continue;
@@ -445,7 +447,7 @@ __device__ __forceinline__ void assign_body(const AssignArgs& a, int block, int 
 __global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) { assign_body(a, blockIdx.x, gridDim.x); }
 
 
-// sum_{i in L_c} S_ic for the recompute path, from Spart[i][s][c]: a block takes
+// sum_{i in L_c} S_ic for the recompute path, from Spart[s][c][i]: a block takes
 // kZReduceRows consecutive rows; thread c sums its cluster's rows in row
 // order (deterministic), then the last block finalizes the pass.
 struct ZArgs {
@@ -476,9 +478,9 @@ __device__ __forceinline__ void zreduce_body(const ZArgs& a, int block, int nblo
     double v = 0.0;
     if (i < a.n) {
         l = a.lab8[i];
-        const float* Si = a.Spart + (int64_t)i * a.nseg * a.k + l;
+        const float* Si = a.Spart + (size_t)l * a.n + i;
         float hi = 0.f, lo = 0.f;
-        for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[(int64_t)s * a.k]);
+        for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[(size_t)s * a.k * a.n]);
         v = (double)hi + (double)lo;
     }
     lab_s[threadIdx.x] = l;
@@ -894,7 +896,7 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2)
                 if (j < cur.c1) accl[(int)b.lab8[j] * 32] += b.K[(int64_t)cur.i * b.ldk + j];
             }
             __syncwarp();
-            float* out = b.Spart + ((int64_t)cur.i * b.nseg + cur.sg) * b.k;
+            float* out = b.Spart + (size_t)cur.sg * b.k * b.n + cur.i;   // [s][c][i]
             if (b.k <= 8) {
                 float part[8];
 #pragma unroll
@@ -904,7 +906,7 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2)
                 }
                 const float tot = butterfly<8>(part, lane);
                 const int c = bfly_cluster<8>(lane);
-                if ((lane & 3) == 0 && c < b.k) out[c] = tot;
+                if ((lane & 3) == 0 && c < b.k) out[(size_t)c * b.n] = tot;
             } else {
                 for (int cb = 0; cb < b.k; cb += 32) {
                     const int c = cb + lane;
@@ -917,7 +919,7 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2)
                             tot += rowp[idx];
                             rowp[idx] = 0.f;
                         }
-                        out[c] = tot;
+                        out[(size_t)c * b.n] = tot;
                     }
                 }
             }

@@ -68,9 +68,12 @@ struct TcArgs {
 };
 
 __device__ __forceinline__ void tri_coords(long long t, int T, int* bi, int* bj) {
-    double Td = (double)T;
-    double disc = (2.0 * Td + 1.0) * (2.0 * Td + 1.0) - 8.0 * (double)t;
-    int b = (int)floor(((2.0 * Td + 1.0) - sqrt(disc)) * 0.5);
+    // t enumerates the upper triangle row by row: row b starts at off(b) = b*T - b*(b-1)/2.
+    // An FP32 estimate of the quadratic's root, then exact integer correction (no FP64:
+    // GB300 runs FP64 at a small fraction of the FP32 rate).
+    const float Tf = (float)T;
+    const float disc = fmaxf((2.f * Tf + 1.f) * (2.f * Tf + 1.f) - 8.f * (float)t, 0.f);
+    int b = (int)(((2.f * Tf + 1.f) - sqrtf(disc)) * 0.5f);
     if (b < 0) b = 0;
     if (b > T - 1) b = T - 1;
     auto off = [&](long long r) { return r * (long long)T - r * (r - 1) / 2; };

@@ -110,6 +110,7 @@ struct RecomputePlan {
     int nseg, seglen;   // column segments (units = row blocks x segments)
     int stages;         // column k-block ring depth
     int eg;             // epilogue warpgroups (1 or 2)
+    int rbp;            // 128-row blocks per unit (2: each column tile feeds two MMAs)
     int threads;        // 64 + 128 * eg
     int off_b, off_meta, off_acc, off_bar, off_misc;
     int smem;
@@ -156,7 +157,7 @@ struct PassBuffers {
     int32_t* lab32;
     uint8_t* lab8;        // n rounded up to 16, zero padded
     int32_t* counts;      // [2][k] ping-pong, indexed by pass parity
-    float* Spart;         // [n][nseg][k] per-segment cluster sums
+    float* Spart;         // [nseg][k][n] per-segment cluster sums (row index fastest)
     double* zpart;        // [grid][k]
     double* zsum;         // [k]
     double* cnorm;        // [k]

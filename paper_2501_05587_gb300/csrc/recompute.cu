@@ -20,8 +20,8 @@
 //   warp 1   tcgen05.mma (kind::f16 for BF16, kind::f8f6f4 for E4M3) into one
 //            of two 128-column TMEM accumulators;
 //   warps 2-5  epilogue: tcgen05.ld, dequantize (FP8: s_i s_j), kappa, run sums.
-// A unit is (row block, column segment); its sums go to Spart[i][s][c], the
-// layout the assign kernel reads.  All waits are bounded as in kbuild_tc.cu.
+// A unit is (row block(s), column segment); its sums go to Spart[s][c][i],
+// the layout the assign kernel reads.  All waits are bounded as in kbuild_tc.cu.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -45,6 +45,7 @@ constexpr int META_LAB = 0, META_KN = 128, META_SC = 128 + 512, META_BYTES = 128
 
 struct RcArgs {
     int n, ncols, nseg, seglen, nkb, k, fp8, eg;   // ncols: padded column space (multiple of 128)
+    int rbp;                            // 128-row blocks per unit (1 or 2): each column tile feeds rbp MMAs
     int stages;                         // B ring depth
     int off_b, off_meta, off_acc, off_bar, off_misc;   // shared-memory layout (bytes from the aligned base)
     KernParams kp;
@@ -132,10 +133,11 @@ __global__ void __launch_bounds__(64 + 256, 1)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    const uint32_t tmem_cols = a.rbp == 2 ? 512u : 256u;   // 2 buffers x rbp accumulators x 128 columns
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32((const void*)tmem_slot)),
-                     "r"(256)
+                     "r"(tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(64 + 256, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int T = (a.n + RM - 1) / RM;
+    const int T = (a.n + RM * a.rbp - 1) / (RM * a.rbp);   // row-block groups
     const int units = T * a.nseg;
     const int G = gridDim.x;
     auto unit_cols = [&](int u, int* I, int* s, int* jb0, int* jb1) {
@@ -175,9 +177,11 @@ __global__ void __launch_bounds__(64 + 256, 1)
                     ok = false;
                     break;
                 }
-                mbar_arrive_expect_tx(afull_bar, (uint32_t)(a.nkb * KB_TILE));
-                for (int kb = 0; kb < a.nkb; ++kb)
-                    tma_load_2d(sbase + kb * KB_TILE, &map_rows, kb * (FP8 ? KBB : KBB / 2), I * RM, afull_bar);
+                mbar_arrive_expect_tx(afull_bar, (uint32_t)(a.rbp * a.nkb * KB_TILE));
+                for (int h = 0; h < a.rbp; ++h)
+                    for (int kb = 0; kb < a.nkb; ++kb)
+                        tma_load_2d(sbase + (h * a.nkb + kb) * KB_TILE, &map_rows, kb * (FP8 ? KBB : KBB / 2),
+                                    (I * a.rbp + h) * RM, afull_bar);
                 a_issued = true;
                 a_parity = (uint32_t)ucount & 1u;
                 for (int jb = jb0; jb < jb1 && ok; ++jb, ++bc) {
@@ -246,23 +250,26 @@ __global__ void __launch_bounds__(64 + 256, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t d_tmem = tmem + (uint32_t)(ab * RN);
                     for (int kb = 0; kb < a.nkb; ++kb) {
                         if (!mbar_wait(full_bar(stage), phase, abort_flag, a.err)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sa = sbase + kb * KB_TILE;
                         const uint32_t sb = sbase + a.off_b + stage * KB_TILE;
+                        for (int h = 0; h < a.rbp; ++h) {
+                            // accumulator (buffer ab, row block h) at TMEM column (ab * rbp + h) * 128
+                            const uint32_t d_tmem = tmem + (uint32_t)((ab * a.rbp + h) * RN);
+                            const uint32_t sa = sbase + (h * a.nkb + kb) * KB_TILE;
 #pragma unroll
-                        for (int kk = 0; kk < KBB / 32; ++kk) {   // 32 bytes of K per instruction
-                            if (FP8)
-                                mma_e4m3(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
-                                         (kb | kk) ? 1u : 0u);
-                            else
-                                mma_bf16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
-                                         (kb | kk) ? 1u : 0u);
+                            for (int kk = 0; kk < KBB / 32; ++kk) {   // 32 bytes of K per instruction
+                                if (FP8)
+                                    mma_e4m3(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
+                                             (kb | kk) ? 1u : 0u);
+                                else
+                                    mma_bf16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
+                                             (kb | kk) ? 1u : 0u);
+                            }
                         }
                         mma_commit(empty_bar(stage));
                         if (++stage == S) {
@@ -281,21 +288,24 @@ __global__ void __launch_bounds__(64 + 256, 1)
             }
         }
     } else if (warp < 2 + EW) {
-        // ---------------- epilogue: EG warpgroups, group g takes chunks g, g + EG, ... ----------------
+        // ---------------- epilogue: group g -> row block g % rbp, chunk subset g / rbp ----------------
         const int g = (warp - 2) >> 2;
         const int q = warp & 3;
+        const int hb = g % a.rbp;                    // row block of the pair
+        const int gpr = a.eg / a.rbp;                // groups per row block (split the columns)
+        const int gsub = g / a.rbp;
         const int row_local = 32 * q + lane;
         float* myacc = acc_s + (size_t)g * a.k * 128 + row_local;   // column row_local of acc_g[k][128]
         const float m2c2 = -2.f * a.kp.neg_gamma_over_sigma2 * 1.4426950408889634f;
         const float c2 = a.kp.neg_gamma_over_sigma2 * 1.4426950408889634f;
         const KernParams kp = a.kp;
-        const int nch = (RN / 32) / a.eg;            // chunks per group per block
+        const int nch = (RN / 32) / gpr;             // chunks per group per block
         int bc = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < units && ok; u += G) {
             int I, s, jb0, jb1;
             unit_cols(u, &I, &s, &jb0, &jb1);
-            const int row = I * RM + row_local;
+            const int row = (I * a.rbp + hb) * RM + row_local;
             const float ar = row < a.n ? (KIND == POPCORN_GAUSSIAN ? c2 * a.rnorm[row] : 0.f) : 0.f;
             const float si = row < a.n ? a.rscale[row] : 0.f;
             for (int c = 0; c < a.k; ++c) myacc[c * 128] = 0.f;
@@ -315,12 +325,13 @@ __global__ void __launch_bounds__(64 + 256, 1)
                 const uint8_t* ml = mp + META_LAB;
                 const float* mk = reinterpret_cast<const float*>(mp + META_KN);
                 const float* msc = reinterpret_cast<const float*>(mp + META_SC);
+                const uint32_t tacc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((ab * a.rbp + hb) * RN);
                 for (int h = 0; h < nch; h += 2) {
                     // two chunks per TMEM round trip
-                    const int ca = g + a.eg * h, cb = g + a.eg * (h + 1);
+                    const int ca = gsub + gpr * h, cb = gsub + gpr * (h + 1);
                     uint32_t ra[32], rb[32];
-                    tmem_ld32_nowait(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * RN + 32 * ca), ra);
-                    tmem_ld32_nowait(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * RN + 32 * cb), rb);
+                    tmem_ld32_nowait(tacc + (uint32_t)(32 * ca), ra);
+                    tmem_ld32_nowait(tacc + (uint32_t)(32 * cb), rb);
                     tmem_ld_wait();
                     if (h + 2 >= nch) {
                         // this warp has read its share of the accumulator
@@ -365,12 +376,12 @@ __global__ void __launch_bounds__(64 + 256, 1)
                 ok = false;
                 break;
             }
-            if (g == 0 && row < a.n) {
-                float* out = a.Spart + ((int64_t)row * a.nseg + s) * a.k;
+            if (gsub == 0 && row < a.n) {
+                float* out = a.Spart + (size_t)s * a.k * a.n + row;   // [s][c][i]: rows of a warp coalesce
                 for (int c = 0; c < a.k; ++c) {
                     float v = myacc[c * 128];
-                    for (int g2 = 1; g2 < a.eg; ++g2) v += myacc[(size_t)g2 * a.k * 128 + c * 128];
-                    out[c] = v;
+                    for (int g2 = 1; g2 < gpr; ++g2) v += myacc[(size_t)g2 * a.rbp * a.k * 128 + c * 128];
+                    out[(size_t)c * a.n] = v;
                 }
             }
             named_bar_n(1, 128 * a.eg);
@@ -381,7 +392,7 @@ __global__ void __launch_bounds__(64 + 256, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
     }
 }
 
@@ -578,24 +589,43 @@ RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, in
     seglen = (seglen + RN - 1) / RN * RN;
     p.seglen = (int)seglen;
     p.nseg = (int)((p.ncols + seglen - 1) / seglen);
-    // shared memory: resident row block, B ring, metadata ring, accumulators, barriers;
-    // two epilogue warpgroups when their accumulators leave room for >= 3 stages
-    p.off_b = p.nkb * KB_TILE;
+    // shared memory: resident row blocks, B ring, metadata ring, accumulators, barriers.
+    // Prefer two row blocks per unit (each column tile then feeds two MMAs, halving
+    // the operand traffic from L2 per flop), one epilogue warpgroup per row block;
+    // fall back to one row block split over two warpgroups, then to one warpgroup.
     const int meta = MS * META_BYTES;
-    int eg = 2, stages = 0;
-    for (; eg >= 1; --eg) {
+    int rbp = 2, eg = 2, stages = 0;
+    const int cand[3][2] = {{2, 2}, {1, 2}, {1, 1}};
+    for (int ci = 0; ci < 3; ++ci) {
+        rbp = cand[ci][0];
+        eg = cand[ci][1];
+        const int off_b = rbp * p.nkb * KB_TILE;
         const int acc = eg * k * 128 * 4;
-        const int fixed = p.off_b + meta + acc + 64 * 8 + 64 + 1024;
+        const int fixed = off_b + meta + acc + 64 * 8 + 64 + 1024;
         stages = (smem_budget - fixed) / KB_TILE;
-        if (stages >= 3 || eg == 1) break;
+        if (stages >= 3 || ci == 2) break;
     }
-    if (stages > 8) stages = 8;
+    p.off_b = rbp * p.nkb * KB_TILE;
+    if (stages > 12) stages = 12;
+    p.rbp = rbp;
     p.eg = eg;
     p.threads = 64 + 128 * eg;
     p.stages = stages;
     p.off_meta = p.off_b + stages * KB_TILE;
     p.off_acc = p.off_meta + meta;
     p.off_bar = p.off_acc + eg * k * 128 * 4;
+    // units: groups of rbp row blocks x column segments (recomputed for the row-block groups)
+    {
+        const int Tg = (p.npad / RM + rbp - 1) / rbp;
+        long long ns = (16LL * num_sms + Tg - 1) / Tg;
+        const long long maxseg = p.ncols / RN;
+        if (ns > maxseg) ns = maxseg;
+        if (ns < 1) ns = 1;
+        long long sl = (p.ncols + ns - 1) / ns;
+        sl = (sl + RN - 1) / RN * RN;
+        p.seglen = (int)sl;
+        p.nseg = (int)((p.ncols + sl - 1) / sl);
+    }
     p.off_misc = p.off_bar + 64 * 8;
     p.smem = p.off_misc + 64 + 1024;
     p.ok = p.nkb <= 4 && stages >= 2 && k <= 255;
@@ -652,6 +682,7 @@ cudaError_t launch_recompute_pass(const PassBuffers& b, KernParams kp, const Rec
     a.k = k;
     a.fp8 = p.fp8;
     a.eg = p.eg;
+    a.rbp = p.rbp;
     a.stages = p.stages;
     a.off_b = p.off_b;
     a.off_meta = p.off_meta;
