@@ -277,6 +277,7 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
     POPCORN_TRY(ws.alloc(&rb.slab, (size_t)rp.ncols, "sorted labels"));
     POPCORN_TRY(ws.alloc(&rb.blockhist, (size_t)nb * k, "sort histograms"));
     POPCORN_TRY(ws.alloc(&rb.blockoff, (size_t)nb * k, "sort offsets"));
+    POPCORN_TRY(ws.alloc(&rb.maxkn, 1, "largest row exponent"));
     PassBuffers b{};
     float* kdiag;
     POPCORN_TRY(ws.alloc(&kdiag, (size_t)ni, "diag(K)"));
@@ -291,7 +292,7 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
     POPCORN_TRY(ws.alloc(&b.lab32, ni, "labels"));
     POPCORN_TRY(ws.alloc(&b.lab8, nlab, "label bytes"));
     POPCORN_TRY(ws.alloc(&b.counts, 2 * (size_t)k, "counts"));
-    POPCORN_TRY(ws.alloc(&b.Spart, (size_t)rp.nseg * ni * k, "segment sums"));
+    POPCORN_TRY(ws.alloc(&b.Spart, (size_t)rp.nslot * ni * k, "segment sums"));
     POPCORN_TRY(ws.alloc(&b.zpart, (size_t)zblocks * k, "block partials"));
     POPCORN_TRY(ws.alloc(&b.zsum, (size_t)k, "z sums"));
     POPCORN_TRY(ws.alloc(&b.cnorm, (size_t)k, "centroid norms"));
@@ -314,6 +315,7 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
     POPCORN_CUDA(cudaMemsetAsync(rb.Qs, 0, (size_t)rp.ncols * rp.row_bytes, s));
     POPCORN_CUDA(cudaMemsetAsync(rb.snorm, 0, (size_t)rp.ncols * sizeof(float), s));
     POPCORN_CUDA(cudaMemsetAsync(rb.sscale, 0, (size_t)rp.ncols * sizeof(float), s));
+    POPCORN_CUDA(cudaMemsetAsync(rb.maxkn, 0, sizeof(int), s));
     POPCORN_CUDA(launch_init_state(b.st, max_iter, opt.check_convergence ? 1 : 0, tol, s));
     POPCORN_CUDA(launch_quantize(Pd, ni, d, ldpd, kp, rp, rb, kdiag, s));
     POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
@@ -346,9 +348,9 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
             cudaError_t e = launch_recompute_pass(b, kp, rp, rb, &b.st->kbuild_err, 0, s);
             if (e == cudaErrorInvalidValue) return fail(POPCORN_ERR_CUDA, "tensor map creation failed");
             POPCORN_CUDA(e);
-            POPCORN_CUDA(launch_zreduce(b, rp.nseg, 0, s));
+            POPCORN_CUDA(launch_zreduce(b, rp.nslot, 0, s));
             if (timing) POPCORN_CUDA(cudaEventRecord(e1, s));
-            POPCORN_CUDA(launch_assign_nseg(b, rp.nseg, s));
+            POPCORN_CUDA(launch_assign_nseg(b, rp.nslot, s));
             if (timing) {
                 POPCORN_CUDA(cudaEventRecord(e2, s));
                 ev_r.push_back(e0);
@@ -378,7 +380,7 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
         cudaError_t e = launch_recompute_pass(b, kp, rp, rb, &b.st->kbuild_err, 1, s);
         if (e == cudaErrorInvalidValue) return fail(POPCORN_ERR_CUDA, "tensor map creation failed");
         POPCORN_CUDA(e);
-        POPCORN_CUDA(launch_zreduce(b, rp.nseg, 1, s));
+        POPCORN_CUDA(launch_zreduce(b, rp.nslot, 1, s));
         launches += 5;
     }
     if (timing) {

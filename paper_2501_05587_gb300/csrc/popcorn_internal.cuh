@@ -109,10 +109,12 @@ struct RecomputePlan {
     int ncols;          // sorted column space: n + 31 k rounded up to 128 (clusters padded to 32)
     int nseg, seglen;   // column segments (units = row blocks x segments)
     int stages;         // column k-block ring depth
-    int eg;             // epilogue warpgroups (1 or 2)
+    int nslot;          // Spart slots: nseg x epilogue groups per row block
+    int eg;             // epilogue warpgroups
     int rbp;            // 128-row blocks per unit (2: each column tile feeds two MMAs)
     int threads;        // 64 + 128 * eg
-    int off_b, off_meta, off_acc, off_bar, off_misc;
+    float fact_limit;   // Gaussian: row factor exp2(c2 r_i) taken out while max |c2| r_i < this
+    int off_b, off_meta, off_bar, off_misc;
     int smem;
     int grid;
     bool ok;            // false: d or k too large for this path
@@ -129,6 +131,7 @@ struct RecomputeBuffers {
     uint8_t* slab;        // ncols labels in cluster order (0xFF on padding)
     int* blockhist;       // sort blocks x k
     int* blockoff;        // sort blocks x k
+    int* maxkn;           // bits of max_i |c2| r_i (Gaussian; zeroed before quantize)
 };
 
 RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, int smem_budget);

@@ -22,6 +22,8 @@
 //   warps 2-5  epilogue: tcgen05.ld, dequantize (FP8: s_i s_j), kappa, run sums.
 // A unit is (row block(s), column segment); its sums go to Spart[s][c][i],
 // the layout the assign kernel reads.  All waits are bounded as in kbuild_tc.cu.
+#include <cmath>
+#include <type_traits>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -44,21 +46,25 @@ constexpr int MS = 4;                   // column-metadata ring slots
 constexpr int META_LAB = 0, META_KN = 128, META_SC = 128 + 512, META_BYTES = 128 + 512 + 512;
 
 struct RcArgs {
-    int n, ncols, nseg, seglen, nkb, k, fp8, eg;   // ncols: padded column space (multiple of 128)
+    int n, ncols, nseg, seglen, nkb, k, fp8;   // ncols: padded column space (multiple of 128)
     int rbp;                            // 128-row blocks per unit (1 or 2): each column tile feeds rbp MMAs
     int stages;                         // B ring depth
-    int off_b, off_meta, off_acc, off_bar, off_misc;   // shared-memory layout (bytes from the aligned base)
+    int off_b, off_meta, off_bar, off_misc;   // shared-memory layout (bytes from the aligned base)
+    float fact_limit;                   // Gaussian: factor exp2(c2 r_i) out when max_i |c2| r_i is below this
     KernParams kp;
     const float* rnorm;                 // row norms of the represented rows, original order
     const float* rscale;                // FP8 row scales, original order (1 for BF16)
     const uint8_t* slab;                // npad labels in sorted order, kNoLabel past n
     const float* sknorm;                // npad: c2 * norm (Gaussian; raw norm otherwise), sorted order, 0 past n
     const float* sscale;                // npad scales in sorted order, 0 past n
-    float* Spart;                       // [n][nseg][k]
+    const int* maxkn;                   // bits of max_i |c2| r_i (Gaussian)
+    float* Spart;                       // [nseg * (kEpiGroups / rbp)][k][n]
     LoopState* st;
     int* err;
     int eval;                           // 1: the final objective pass (runs after the loop stopped)
 };
+
+constexpr int kEpiGroups = 4;           // epilogue warpgroups
 
 __device__ __forceinline__ float ex2(float x) {
     float y;
@@ -66,30 +72,75 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
-// kappa of one accumulator value b for row constants (ar, si) and column
-// constants (kn, sj); Gaussian: exp2(min(c2 (r_i + r_j) - 2 c2 b', 0)) with
-// b' = b (BF16) or s_i s_j b (FP8) and c2 = -gamma log2(e) / sigma^2.  A
-// padding column has kn = -inf: the Gaussian term is exp2(-inf) = 0 by
-// itself, the other kernels are masked.
-template <bool FP8, int KIND>
-__device__ __forceinline__ float kappa_rc(float b, float ar, float si, float kn, float sj, float m2c2,
-                                          const KernParams& kp) {
-    if (KIND == POPCORN_GAUSSIAN) {
-        const float coef = FP8 ? m2c2 * si * sj : m2c2;
-        return ex2(fminf(fmaf(coef, b, ar + kn), 0.f));
+// Per-thread view of one 32-column chunk in the 16x256b TMEM fragments: thread
+// t = 4 g + m of a warp holds rows g, g + 8 (fragment ra, lanes 0-15 of the warp's
+// 32) and g + 16, g + 24 (rb, lanes 16-31), each at columns 8 rep + 2 m + {0, 1},
+// rep = 0..3.  Row slot ri = 2 (half) + (row >= +8).  Each column constant then
+// serves four rows of a thread instead of one, which keeps the shared-memory
+// reads of kn_j / s_j (one 8-byte pair per rep, four distinct addresses per
+// warp) far below the exp2 rate.
+struct RowConsts {
+    float rowc[4];   // -2 c2 (BF16) or -2 c2 s_i (FP8): the coefficient of b in the exponent
+    float ar[4];     // c2 r_i (Gaussian, clamped form)
+    float si[4];     // s_i (FP8 dot kernels)
+};
+
+__device__ __forceinline__ uint32_t frag(const uint32_t (&ra)[16], const uint32_t (&rb)[16], int ri, int x) {
+    return ri < 2 ? ra[x] : rb[x];
+}
+
+// Adds this thread's share of the chunk to run[ri] (packed pairs of partial sums).
+//  Gaussian, factored: exp2(kn_j + coef b) with kn_j = c2 r_j; the caller later
+//    multiplies by exp2(c2 r_i).  Padding columns (kn = -inf) give exp2(-inf) = 0.
+//  Gaussian, clamped:  exp2(min(c2 (r_i + r_j) - 2 c2 b', 0)) (distance >= 0), used
+//    when exp2(|c2| r_i) could overflow.
+//  Linear / polynomial of b' = b (BF16) or s_i s_j b (FP8); padding masked.
+template <bool FP8, int KIND, bool FACT>
+__device__ __forceinline__ void chunk_accumulate(const uint32_t (&ra)[16], const uint32_t (&rb)[16],
+                                                 const float2 (&knp)[4], const float2 (&scp)[4], const RowConsts& rc,
+                                                 const KernParams& kp, unsigned long long (&run)[4]) {
+#pragma unroll
+    for (int rep = 0; rep < 4; ++rep) {
+#pragma unroll
+        for (int ri = 0; ri < 4; ++ri) {
+            const int x = 4 * rep + 2 * (ri & 1);
+            const float b0 = __uint_as_float(frag(ra, rb, ri, x)), b1 = __uint_as_float(frag(ra, rb, ri, x + 1));
+            if (KIND == POPCORN_GAUSSIAN && FACT) {
+                const unsigned long long rc2 = f2pack(rc.rowc[ri], rc.rowc[ri]);
+                const unsigned long long coef = FP8 ? f2mul(rc2, f2pack(scp[rep].x, scp[rep].y)) : rc2;
+                const unsigned long long t = f2fma(coef, f2pack(b0, b1), f2pack(knp[rep].x, knp[rep].y));
+                float e0, e1;
+                f2unpack(t, e0, e1);
+                run[ri] = f2add(run[ri], f2pack(ex2(e0), ex2(e1)));
+            } else if (KIND == POPCORN_GAUSSIAN) {
+                const float c0 = FP8 ? rc.rowc[ri] * scp[rep].x : rc.rowc[ri];
+                const float c1 = FP8 ? rc.rowc[ri] * scp[rep].y : rc.rowc[ri];
+                const float v0 = ex2(fminf(fmaf(c0, b0, rc.ar[ri] + knp[rep].x), 0.f));
+                const float v1 = ex2(fminf(fmaf(c1, b1, rc.ar[ri] + knp[rep].y), 0.f));
+                run[ri] = f2add(run[ri], f2pack(v0, v1));
+            } else {
+                const float bb0 = FP8 ? b0 * (rc.si[ri] * scp[rep].x) : b0;
+                const float bb1 = FP8 ? b1 * (rc.si[ri] * scp[rep].y) : b1;
+                float v0 = bb0, v1 = bb1;
+                if (KIND == POPCORN_POLYNOMIAL) {
+                    const float base0 = fmaf(kp.gamma, bb0, kp.coef0), base1 = fmaf(kp.gamma, bb1, kp.coef0);
+                    v0 = base0;
+                    v1 = base1;
+                    for (int e = 1; e < kp.degree; ++e) {
+                        v0 *= base0;
+                        v1 *= base1;
+                    }
+                }
+                v0 = knp[rep].x == -INFINITY ? 0.f : v0;
+                v1 = knp[rep].y == -INFINITY ? 0.f : v1;
+                run[ri] = f2add(run[ri], f2pack(v0, v1));
+            }
+        }
     }
-    const float bb = FP8 ? b * (si * sj) : b;
-    float r = bb;
-    if (KIND == POPCORN_POLYNOMIAL) {
-        const float base = fmaf(kp.gamma, bb, kp.coef0);
-        r = base;
-        for (int e = 1; e < kp.degree; ++e) r *= base;
-    }
-    return kn == -INFINITY ? 0.f : r;
 }
 
 template <bool FP8, int KIND>
-__global__ void __launch_bounds__(64 + 256, 1)
+__global__ void __launch_bounds__(64 + 128 * kEpiGroups, 1)
     recompute_kernel(const __grid_constant__ CUtensorMap map_rows, const __grid_constant__ CUtensorMap map_cols,
                      RcArgs a) {
     if (pass_skip(a.st, a.eval)) return;
@@ -98,7 +149,7 @@ __global__ void __launch_bounds__(64 + 256, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t sbase = smem_u32(smem);
     const int S = a.stages;
-    const int EW = 4 * a.eg;            // epilogue warps
+    constexpr int EW = 4 * kEpiGroups;  // epilogue warps
     const uint32_t bar0 = sbase + a.off_bar;
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
@@ -112,7 +163,6 @@ __global__ void __launch_bounds__(64 + 256, 1)
     volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(smem + a.off_misc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + a.off_misc + 4);
     unsigned char* meta = smem + a.off_meta;
-    float* acc_s = reinterpret_cast<float*>(smem + a.off_acc);   // [eg][k][128]
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -158,7 +208,6 @@ __global__ void __launch_bounds__(64 + 256, 1)
         *jb1 = (c1 + RN - 1) / RN;
     };
     constexpr uint32_t idesc = FP8 ? idesc_e4m3(RM, RN) : idesc_bf16(RM, RN);
-
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer: row block, column metadata, column k-blocks ----------------
@@ -288,104 +337,132 @@ __global__ void __launch_bounds__(64 + 256, 1)
             }
         }
     } else if (warp < 2 + EW) {
-        // ---------------- epilogue: group g -> row block g % rbp, chunk subset g / rbp ----------------
+        // ---------------- epilogue ----------------
+        // Warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31, i.e. 32 rows.  Group
+        // g = (w - 2) / 4 takes row block g % rbp of the pair and the 32-column chunks
+        // [gsub nch, gsub nch + nch) of every column block, gsub = g / rbp, nch = rbp.
+        // The columns arrive in cluster order, so each (row, cluster) sum of a unit is
+        // one run: it is written to Spart once, when the label changes, and the
+        // clusters the unit does not meet get zeros -- no shared-memory accumulators.
         const int g = (warp - 2) >> 2;
         const int q = warp & 3;
-        const int hb = g % a.rbp;                    // row block of the pair
-        const int gpr = a.eg / a.rbp;                // groups per row block (split the columns)
+        const int hb = g % a.rbp;
+        const int gpr = kEpiGroups / a.rbp;          // groups per row block: Spart slots per segment
         const int gsub = g / a.rbp;
-        const int row_local = 32 * q + lane;
-        float* myacc = acc_s + (size_t)g * a.k * 128 + row_local;   // column row_local of acc_g[k][128]
-        const float m2c2 = -2.f * a.kp.neg_gamma_over_sigma2 * 1.4426950408889634f;
+        const int nch = a.rbp;                       // = 4 / gpr
+        const int ch0 = gsub * nch;
+        const int gq = lane >> 2, m = lane & 3;      // fragment row group and column pair
         const float c2 = a.kp.neg_gamma_over_sigma2 * 1.4426950408889634f;
+        const float m2c2 = -2.f * c2;
         const KernParams kp = a.kp;
-        const int nch = (RN / 32) / gpr;             // chunks per group per block
-        int bc = 0;
-        bool ok = true;
-        for (int u = blockIdx.x; u < units && ok; u += G) {
-            int I, s, jb0, jb1;
-            unit_cols(u, &I, &s, &jb0, &jb1);
-            const int row = (I * a.rbp + hb) * RM + row_local;
-            const float ar = row < a.n ? (KIND == POPCORN_GAUSSIAN ? c2 * a.rnorm[row] : 0.f) : 0.f;
-            const float si = row < a.n ? a.rscale[row] : 0.f;
-            for (int c = 0; c < a.k; ++c) myacc[c * 128] = 0.f;
-            int cur = kNoLabel;
-            float run = 0.f;
-            for (int jb = jb0; jb < jb1; ++jb, ++bc) {
-                const int ab = bc & 1;
-                const int ms = bc % MS;
-                bool got = mbar_wait(mfull_bar(ms), (uint32_t)(bc / MS) & 1u, abort_flag, a.err);
-                got = got && mbar_wait(accf_bar(ab), (uint32_t)(bc >> 1) & 1u, abort_flag, a.err);
-                if (__any_sync(0xffffffffu, !got)) {
-                    ok = false;   // leave the block loop; the unit-end barrier below is still reached
-                    break;
-                }
-                tc_fence_after();
-                const unsigned char* mp = meta + ms * META_BYTES;
-                const uint8_t* ml = mp + META_LAB;
-                const float* mk = reinterpret_cast<const float*>(mp + META_KN);
-                const float* msc = reinterpret_cast<const float*>(mp + META_SC);
-                const uint32_t tacc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((ab * a.rbp + hb) * RN);
-                for (int h = 0; h < nch; h += 2) {
-                    // two chunks per TMEM round trip
-                    const int ca = gsub + gpr * h, cb = gsub + gpr * (h + 1);
-                    uint32_t ra[32], rb[32];
-                    tmem_ld32_nowait(tacc + (uint32_t)(32 * ca), ra);
-                    tmem_ld32_nowait(tacc + (uint32_t)(32 * cb), rb);
-                    tmem_ld_wait();
-                    if (h + 2 >= nch) {
-                        // this warp has read its share of the accumulator
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(acce_bar(ab));
-                    }
+        auto body = [&](auto fact_tag) {
+            constexpr bool FACT = decltype(fact_tag)::value;
+            int bc = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < units && ok; u += G) {
+                int I, s, jb0, jb1;
+                unit_cols(u, &I, &s, &jb0, &jb1);
+                const int rbase = (I * a.rbp + hb) * RM + 32 * q;
+                RowConsts rc;
 #pragma unroll
-                    for (int half = 0; half < 2; ++half) {
+                for (int ri = 0; ri < 4; ++ri) {
+                    const int row = rbase + 16 * (ri >> 1) + gq + 8 * (ri & 1);
+                    const bool v = row < a.n;
+                    const float si = v ? a.rscale[row] : 0.f;
+                    rc.si[ri] = si;
+                    rc.rowc[ri] = FP8 ? m2c2 * si : m2c2;
+                    rc.ar[ri] = v && KIND == POPCORN_GAUSSIAN ? c2 * a.rnorm[row] : 0.f;
+                }
+                // lane 4 gq + m writes row slot m of its quad: the warp's 32 rows, once each
+                const int wrow = rbase + 16 * (m >> 1) + gq + 8 * (m & 1);
+                const bool wvalid = wrow < a.n;
+                const float wfin = FACT ? ex2(m == 0 ? rc.ar[0] : m == 1 ? rc.ar[1] : m == 2 ? rc.ar[2] : rc.ar[3])
+                                        : 1.f;
+                float* out = a.Spart + (size_t)(s * gpr + gsub) * a.k * a.n + wrow;   // [slot][c][i]
+                int cur = -1, nextc = 0;
+                unsigned long long run[4] = {0ull, 0ull, 0ull, 0ull};
+                // write the finished run of cluster c (and zeros for the clusters skipped before it)
+                auto emit = [&](int c) {
+                    float v[4];
+#pragma unroll
+                    for (int ri = 0; ri < 4; ++ri) {
+                        float lo, hi;
+                        f2unpack(run[ri], lo, hi);
+                        v[ri] = lo + hi;
+                        v[ri] += __shfl_xor_sync(0xffffffffu, v[ri], 1);
+                        v[ri] += __shfl_xor_sync(0xffffffffu, v[ri], 2);
+                    }
+                    const float mine = (m == 0 ? v[0] : m == 1 ? v[1] : m == 2 ? v[2] : v[3]) * wfin;
+                    if (wvalid) {
+                        for (int z = nextc; z < c; ++z) out[(size_t)z * a.n] = 0.f;
+                        out[(size_t)c * a.n] = mine;
+                    }
+                    nextc = c + 1;
+                };
+                for (int jb = jb0; jb < jb1; ++jb, ++bc) {
+                    const int ab = bc & 1;
+                    const int ms = bc % MS;
+                    bool got = mbar_wait(mfull_bar(ms), (uint32_t)(bc / MS) & 1u, abort_flag, a.err);
+                    got = got && mbar_wait(accf_bar(ab), (uint32_t)(bc >> 1) & 1u, abort_flag, a.err);
+                    if (__any_sync(0xffffffffu, !got)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned char* mp = meta + ms * META_BYTES;
+                    const uint8_t* ml = mp + META_LAB;
+                    const float* mk = reinterpret_cast<const float*>(mp + META_KN);
+                    const float* msc = reinterpret_cast<const float*>(mp + META_SC);
+                    const uint32_t tacc =
+                        tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((ab * a.rbp + hb) * RN + 32 * ch0);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (h >= nch) break;
+                        uint32_t ra[16], rb[16];
+                        tmem_ld16x256_x4_nowait(tacc + 32u * h, ra);
+                        tmem_ld16x256_x4_nowait(tacc + 32u * h + (16u << 16), rb);
+                        tmem_ld_wait();
+                        if (h == nch - 1) {
+                            // this warp has read its share of the accumulator
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(acce_bar(ab));
+                        }
                         // every cluster's run of columns is padded to a multiple of 32, so a
-                        // chunk holds one label (kNoLabel: padding, skipped)
-                        const int ch = half ? cb : ca;
-                        const uint32_t* r = half ? rb : ra;
+                        // chunk holds one label (kNoLabel: padding past the last cluster)
+                        const int ch = ch0 + h;
                         const int lab = ml[32 * ch];
                         if (lab == kNoLabel) continue;
-                        const float* kn = mk + 32 * ch;
-                        const float* sc = msc + 32 * ch;
-                        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-#pragma unroll
-                        for (int x = 0; x < 32; x += 4) {
-                            p0 += kappa_rc<FP8, KIND>(__uint_as_float(r[x]), ar, si, kn[x], sc[x], m2c2, kp);
-                            p1 += kappa_rc<FP8, KIND>(__uint_as_float(r[x + 1]), ar, si, kn[x + 1], sc[x + 1], m2c2, kp);
-                            p2 += kappa_rc<FP8, KIND>(__uint_as_float(r[x + 2]), ar, si, kn[x + 2], sc[x + 2], m2c2, kp);
-                            p3 += kappa_rc<FP8, KIND>(__uint_as_float(r[x + 3]), ar, si, kn[x + 3], sc[x + 3], m2c2, kp);
-                        }
                         if (lab != cur) {   // warp-uniform
-                            if (cur != kNoLabel) myacc[cur * 128] += run;
+                            if (cur >= 0) emit(cur);
                             cur = lab;
-                            run = 0.f;
+#pragma unroll
+                            for (int ri = 0; ri < 4; ++ri) run[ri] = 0ull;
                         }
-                        run += (p0 + p1) + (p2 + p3);
+                        float2 knp[4], scp[4];
+#pragma unroll
+                        for (int rep = 0; rep < 4; ++rep) {
+                            knp[rep] = *reinterpret_cast<const float2*>(mk + 32 * ch + 8 * rep + 2 * m);
+                            scp[rep] = FP8 || KIND != POPCORN_GAUSSIAN
+                                           ? *reinterpret_cast<const float2*>(msc + 32 * ch + 8 * rep + 2 * m)
+                                           : make_float2(1.f, 1.f);
+                        }
+                        chunk_accumulate<FP8, KIND, FACT>(ra, rb, knp, scp, rc, kp, run);
                     }
+                    // this warp is done with the metadata slot
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(mempty_bar(ms));
                 }
-                // this warp is done with the metadata slot
-                __syncwarp();
-                if (lane == 0) mbar_arrive(mempty_bar(ms));
+                if (!ok) break;
+                if (cur >= 0) emit(cur);
+                if (wvalid)
+                    for (int z = nextc; z < a.k; ++z) out[(size_t)z * a.n] = 0.f;
             }
-            if (ok && cur != kNoLabel) myacc[cur * 128] += run;
-            // every epilogue warp arrives here once per unit, aborted or not; the AND tells
-            // all of them whether to go on.  Then group 0 combines the groups' accumulators.
-            if (!named_bar_all(1, 128 * a.eg, ok && !*abort_flag)) {
-                ok = false;
-                break;
-            }
-            if (gsub == 0 && row < a.n) {
-                float* out = a.Spart + (size_t)s * a.k * a.n + row;   // [s][c][i]: rows of a warp coalesce
-                for (int c = 0; c < a.k; ++c) {
-                    float v = myacc[c * 128];
-                    for (int g2 = 1; g2 < gpr; ++g2) v += myacc[(size_t)g2 * a.rbp * a.k * 128 + c * 128];
-                    out[(size_t)c * a.n] = v;
-                }
-            }
-            named_bar_n(1, 128 * a.eg);
-        }
+        };
+        if (KIND == POPCORN_GAUSSIAN && __int_as_float(*a.maxkn) < a.fact_limit)
+            body(std::true_type{});
+        else
+            body(std::false_type{});
     }
 
     tc_fence_before();
@@ -402,7 +479,8 @@ __global__ void __launch_bounds__(64 + 256, 1)
 __global__ void __launch_bounds__(256) quantize_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
                                                        int dpad, int fp8, KernParams kp, unsigned char* __restrict__ Q,
                                                        float* __restrict__ norms, float* __restrict__ knorms,
-                                                       float* __restrict__ scales, float* __restrict__ kdiag) {
+                                                       float* __restrict__ scales, float* __restrict__ kdiag,
+                                                       int* __restrict__ maxkn) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= n) return;
@@ -436,7 +514,10 @@ __global__ void __launch_bounds__(256) quantize_kernel(const float* __restrict__
     if (lane == 0) {
         norms[w] = nrm;
         // the epilogue works in base 2: c2 * r with c2 = -gamma log2(e) / sigma^2
-        knorms[w] = kp.kind == POPCORN_GAUSSIAN ? kp.neg_gamma_over_sigma2 * 1.4426950408889634f * nrm : nrm;
+        const float kn = kp.kind == POPCORN_GAUSSIAN ? kp.neg_gamma_over_sigma2 * 1.4426950408889634f * nrm : nrm;
+        knorms[w] = kn;
+        // max_i |c2| r_i (non-negative floats order like their bit patterns)
+        if (kp.kind == POPCORN_GAUSSIAN) atomicMax(maxkn, __float_as_int(fabsf(kn)));
         scales[w] = scale;
         float kd;
         if (kp.kind == POPCORN_GAUSSIAN) {
@@ -580,41 +661,26 @@ RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, in
     p.npad = (n + RN - 1) / RN * RN;
     // sorted column space: clusters padded to 32-column chunks
     p.ncols = (n + 31 * k + RN - 1) / RN * RN;
-    const int T = p.npad / RM;
-    long long nseg = (32LL * num_sms + T - 1) / T;
-    const long long maxseg = p.ncols / RN;
-    if (nseg > maxseg) nseg = maxseg;
-    if (nseg < 1) nseg = 1;
-    long long seglen = (p.ncols + nseg - 1) / nseg;
-    seglen = (seglen + RN - 1) / RN * RN;
-    p.seglen = (int)seglen;
-    p.nseg = (int)((p.ncols + seglen - 1) / seglen);
-    // shared memory: resident row blocks, B ring, metadata ring, accumulators, barriers.
-    // Prefer two row blocks per unit (each column tile then feeds two MMAs, halving
-    // the operand traffic from L2 per flop), one epilogue warpgroup per row block;
-    // fall back to one row block split over two warpgroups, then to one warpgroup.
+    // shared memory: resident row blocks, B ring, metadata ring, barriers.  Prefer two
+    // row blocks per unit (each column tile then feeds two MMAs, halving the operand
+    // traffic from L2 per flop); fall back to one when fewer than 3 ring stages fit.
     const int meta = MS * META_BYTES;
-    int rbp = 2, eg = 2, stages = 0;
-    const int cand[3][2] = {{2, 2}, {1, 2}, {1, 1}};
-    for (int ci = 0; ci < 3; ++ci) {
-        rbp = cand[ci][0];
-        eg = cand[ci][1];
-        const int off_b = rbp * p.nkb * KB_TILE;
-        const int acc = eg * k * 128 * 4;
-        const int fixed = off_b + meta + acc + 64 * 8 + 64 + 1024;
-        stages = (smem_budget - fixed) / KB_TILE;
-        if (stages >= 3 || ci == 2) break;
+    const int fixed = meta + 64 * 8 + 64 + 1024;
+    int rbp = 2;
+    int stages = (smem_budget - rbp * p.nkb * KB_TILE - fixed) / KB_TILE;
+    if (stages < 3) {
+        rbp = 1;
+        stages = (smem_budget - rbp * p.nkb * KB_TILE - fixed) / KB_TILE;
     }
-    p.off_b = rbp * p.nkb * KB_TILE;
     if (stages > 12) stages = 12;
     p.rbp = rbp;
-    p.eg = eg;
-    p.threads = 64 + 128 * eg;
+    p.eg = kEpiGroups;
+    p.threads = 64 + 128 * kEpiGroups;
     p.stages = stages;
+    p.off_b = rbp * p.nkb * KB_TILE;
     p.off_meta = p.off_b + stages * KB_TILE;
-    p.off_acc = p.off_meta + meta;
-    p.off_bar = p.off_acc + eg * k * 128 * 4;
-    // units: groups of rbp row blocks x column segments (recomputed for the row-block groups)
+    p.off_bar = p.off_meta + meta;
+    // units: groups of rbp row blocks x column segments, about 16 per SM
     {
         const int Tg = (p.npad / RM + rbp - 1) / rbp;
         long long ns = (16LL * num_sms + Tg - 1) / Tg;
@@ -626,6 +692,11 @@ RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, in
         p.seglen = (int)sl;
         p.nseg = (int)((p.ncols + sl - 1) / sl);
     }
+    // every epilogue group writes its own slot of each segment
+    p.nslot = p.nseg * (kEpiGroups / rbp);
+    // factored Gaussian: exp2(x_ij) with x_ij <= |c2| r_i summed over up to ncols
+    // columns must stay finite: |c2| r_i + log2(ncols) well below 128
+    p.fact_limit = 120.f - std::log2((float)p.ncols);
     p.off_misc = p.off_bar + 64 * 8;
     p.smem = p.off_misc + 64 + 1024;
     p.ok = p.nkb <= 4 && stages >= 2 && k <= 255;
@@ -656,7 +727,7 @@ cudaError_t configure_recompute(int smem_optin, int* usable) {
 cudaError_t launch_quantize(const float* P, int n, int d, int64_t ldp, KernParams kp, const RecomputePlan& p,
                             const RecomputeBuffers& rb, float* kdiag, cudaStream_t s) {
     quantize_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(P, n, d, ldp, p.dpad, p.fp8, kp, rb.Q, rb.norms, rb.knorms,
-                                                         rb.scales, kdiag);
+                                                         rb.scales, kdiag, rb.maxkn);
     return cudaGetLastError();
 }
 
@@ -681,12 +752,10 @@ cudaError_t launch_recompute_pass(const PassBuffers& b, KernParams kp, const Rec
     a.nkb = p.nkb;
     a.k = k;
     a.fp8 = p.fp8;
-    a.eg = p.eg;
     a.rbp = p.rbp;
     a.stages = p.stages;
     a.off_b = p.off_b;
     a.off_meta = p.off_meta;
-    a.off_acc = p.off_acc;
     a.off_bar = p.off_bar;
     a.off_misc = p.off_misc;
     a.kp = kp;
@@ -695,6 +764,8 @@ cudaError_t launch_recompute_pass(const PassBuffers& b, KernParams kp, const Rec
     a.slab = rb.slab;
     a.sknorm = rb.snorm;
     a.sscale = rb.sscale;
+    a.maxkn = rb.maxkn;
+    a.fact_limit = p.fact_limit;
     a.Spart = b.Spart;
     a.st = b.st;
     a.err = err;
