@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=["rings", "blobs", "images", "mixture", "batched"],
                     help="rings (default, the reported line), blobs, images, mixture (recompute path), "
                          "batched (256 instances in one graph)")
+    ap.add_argument("--autotune", default="on", choices=["on", "off"],
+                    help="time candidate schedules in the warm-up (batched and recompute paths)")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3", "fp8"],
                     help="K-build precision (default: the workload's)")
     return ap.parse_args()
@@ -87,6 +89,43 @@ def peaks():
         return float(m["hbm_gbs"]), "measured (MEASURED_PEAKS.json: STREAM-style copy)"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, earlier GB300 copy measurement)"
+
+
+# exp2 unit (MUFU) rate measured on GB300: 32 ex2.approx per clock per SM (152 SMs)
+XU_EX2_PER_CLK_SM = 32
+GB300_SMS = 152
+
+
+def recompute_rooflines(wl, avg_ms: float, clk: dict):
+    """Rooflines of one recompute pass (sort + tiles + reduction), the binding one first.
+
+    tensor: 2 n^2 d algorithmic MMA flops against the measured BF16 burst peak (FP8:
+    twice that, the nominal FP8/BF16 ratio); alu: n^2 exp2 evaluations (Gaussian)
+    against 32 per clock per SM at the maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        bf16, src = float(m["bf16_tflops"]), "measured bf16 burst (MEASURED_PEAKS.json)"
+        sm_mhz = float(m.get("sm_max_mhz", 2070.0))
+    except Exception:
+        bf16, src, sm_mhz = 1900.0, "fallback 1.9 PFLOP/s bf16", 2070.0
+    peak_t = bf16 * (2.0 if wl.precision == "fp8" else 1.0)
+    n, d = float(wl.n), float(wl.d)
+    sec = avg_ms / 1e3 if avg_ms > 0 else float("inf")
+    t_ach = 2.0 * n * n * d / sec / 1e12
+    tensor = {"kernel": "recompute_kernel", "bound": "tensor", "achieved": t_ach, "peak": peak_t,
+              "unit": "TFLOP/s", "frac": t_ach / peak_t, "traffic": None,
+              "peak_source": src + (" x2 for FP8 (nominal ratio)" if wl.precision == "fp8" else ""),
+              "algorithmic_flops_per_launch": 2.0 * n * n * d, "avg_launch_ms": avg_ms}
+    peak_x = XU_EX2_PER_CLK_SM * GB300_SMS * sm_mhz * 1e6 / 1e12
+    x_ach = n * n / sec / 1e12
+    alu = {"kernel": "recompute_kernel", "bound": "alu", "achieved": x_ach, "peak": peak_x,
+           "unit": "Texp2/s", "frac": x_ach / peak_x, "traffic": None,
+           "peak_source": f"{XU_EX2_PER_CLK_SM} ex2/clk/SM x {GB300_SMS} SMs x {sm_mhz:.0f} MHz (ex2 microbenchmark)",
+           "algorithmic_exp2_per_launch": n * n, "avg_launch_ms": avg_ms}
+    if wl.kernel["kind"] != "gaussian":
+        return tensor, None
+    return (tensor, alu) if tensor["frac"] >= alu["frac"] else (alu, tensor)
 
 
 def recorded_traffic(kernel: str, src_file: str):
@@ -246,7 +285,8 @@ def run_batched(args):
               "init_labels": torch.from_numpy(w.init_labels).cuda()} for w in wls]
 
     def step():
-        return pc.popcorn_fit_batched(insts, max_iter=30, precision=prec, check_convergence=False, timing=True)
+        return pc.popcorn_fit_batched(insts, max_iter=30, precision=prec, check_convergence=False, timing=True,
+                                      autotune=args.autotune == "on")
 
     for _ in range(args.warmup):
         step()
@@ -278,7 +318,10 @@ def run_batched(args):
                                    f"({kbytes / 1e9:.1f} GB)", "precision": prec},
             "graph_ms": graph_ms, "effective_GBps_of_K_reads": kbytes * 30 / (graph_ms / 1e3) / 1e9,
             "separate_fits_ms": seq_ms, "batched_speedup_vs_separate_fits": seq_ms / (ms / args.steps),
-            "gpu_launches": sum(r["info"]["kernel_launches"] for r in res)}
+            "gpu_launches": sum(r["info"]["kernel_launches"] for r in res),
+            "schedule": {"autotune": args.autotune, "columns_per_unit": res[-1]["info"]["schedule"][0],
+                         "warps_per_block": res[-1]["info"]["schedule"][1],
+                         "blocks_per_sm": res[-1]["info"]["schedule"][2]}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -314,9 +357,13 @@ def main():
     lab = torch.from_numpy(wl.init_labels).cuda()
     out = torch.empty_like(lab)
 
+    # the recompute path's schedule (row blocks per tile, units per SM) is autotuned in the warm-up
+    tune = args.autotune == "on" and not wl.store_k
+
     def step(timing=True):
         return pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
-                              precision=wl.precision, timing=timing, labels_out=out, store_k=wl.store_k)
+                              precision=wl.precision, timing=timing, labels_out=out, store_k=wl.store_k,
+                              autotune=tune)
 
     for _ in range(args.warmup):
         step()
@@ -351,7 +398,7 @@ def main():
     Oh = torch.empty(wl.n, dtype=torch.int32).pin_memory()
     def host_step():
         return pc.popcorn_fit(Ph, wl.k, wl.kernel, Lh, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
-                              precision=wl.precision, labels_out=Oh, store_k=wl.store_k)
+                              precision=wl.precision, labels_out=Oh, store_k=wl.store_k, autotune=tune)
 
     for _ in range(args.warmup):
         host_step()
@@ -376,6 +423,14 @@ def main():
         peak, peak_src = peaks()
         achieved = alg_bytes / (avg_red_ms / 1e3) / 1e9 if avg_red_ms > 0 else 0.0
         traffic = recorded_traffic("reduce_kernel", "iterate.cu")
+        roof = {"kernel": "reduce_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_red_ms}
+        roof2 = None
+        if not wl.store_k:
+            # recompute pass: tensor cores (2 n^2 d flops) and the exp2 unit (n^2 kernel values)
+            roof, roof2 = recompute_rooflines(wl, avg_red_ms, clk)
         line = {
             "metric": METRIC,
             "value": value,
@@ -401,16 +456,18 @@ def main():
             "loop_iters_per_s": iters / ((red_ms + asg_ms) / 1e3) if red_ms > 0 else None,
             "breakdown_ms_per_step": {"kbuild": kb_ms / args.steps, "reduce": red_ms / args.steps,
                                       "assign": asg_ms / args.steps},
-            "roofline": {"kernel": "reduce_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_src,
-                         "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_red_ms},
+            "roofline": roof,
             "e2e": {"value": e2e_iters_all / t_e2e, "unit": "iters/s",
                     "h2d_bytes_per_step": int(e2e_res[0]["info"]["h2d_bytes"]),
                     "d2h_bytes_per_step": int(e2e_res[0]["info"]["d2h_bytes"])},
             "gpu_launches": launches_all,
             "clocks": clk,
         }
+        if roof2 is not None:
+            line["roofline_secondary"] = roof2
+            line["schedule"] = {"autotune": args.autotune, "row_blocks_per_tile": results[-1]["info"]["schedule"][0],
+                                "column_segments": results[-1]["info"]["schedule"][1],
+                                "units_per_sm_target": results[-1]["info"]["schedule"][2]}
         if args.workload == WORKLOAD and args.scale == 1.0:
             # the same fits with K stored in FP16: half the bytes per pass (an extra, not the headline)
             def step16():

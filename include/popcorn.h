@@ -98,7 +98,13 @@ typedef struct {
     int32_t timing;             /* 1: record CUDA-event times per phase into popcorn_fit_info */
     int32_t k_storage;          /* popcorn_k_storage of the stored K (FP32 build only for the
                                    half types); 0 = FP32                                    */
-    int32_t reserved32;         /* must be zero                                              */
+    int32_t autotune;           /* 1: pick the schedule by timing candidates on this workload
+                                   (first call per workload signature; later calls reuse the
+                                   cached choice, see popcorn_autotune_entries); 0: fixed
+                                   heuristics.  Used by popcorn_fit_batched (K-stream unit
+                                   length, warps per block, blocks per SM) and by the
+                                   recompute path of popcorn_fit (row blocks per tile, units
+                                   per SM).  Results differ only by summation order.        */
     int64_t reserved[5];        /* must be zero                                              */
 } popcorn_options;
 
@@ -120,6 +126,14 @@ typedef struct {
                                   J_t = J(labels before pass t)                             */
     int32_t* changed_history;  /* caller-provided host array of >= max_iter ints, or NULL:
                                   labels changed by pass t                                  */
+    int32_t tune_cache_hit;    /* autotune = 1: the schedule came from the cache            */
+    int32_t tune_candidates;   /* autotune = 1: schedules this call timed (0 on a cache hit)  */
+    double tune_ms;            /* host wall time this call spent timing candidates           */
+    int32_t schedule[4];       /* the schedule used (tuned or heuristic):
+                                  batched: {columns per K-stream unit, warps per block,
+                                            blocks per SM, 0};
+                                  recompute: {row blocks per tile, column segments,
+                                              units per SM target, 0}; zeros otherwise     */
 } popcorn_fit_info;
 
 /* Human-readable name of a status code (static storage). */
@@ -279,6 +293,20 @@ POPCORN_API popcorn_status popcorn_fit_batched(int32_t count, const popcorn_inst
  *
  * Errors: as popcorn_assign_step, plus the size limit above.
  */
+/*
+ * Autotune cache (options.autotune = 1).
+ *
+ * The paper has no counterpart: its kernels have fixed launch shapes.  Tuned
+ * schedules are kept per workload signature (bucketed sizes, precision, SM
+ * count) for the life of the process; if the environment variable
+ * POPCORN_TUNE_CACHE names a writable file, entries are appended to it and
+ * read back by later processes.  popcorn_autotune_entries returns how many
+ * signatures are cached; popcorn_autotune_clear forgets them (the file is not
+ * touched).  Both are thread-safe and never fail.
+ */
+POPCORN_API int32_t popcorn_autotune_entries(void);
+POPCORN_API void popcorn_autotune_clear(void);
+
 #define POPCORN_NOALLOC_SCRATCH_BYTES (32ll * 1024 * 1024)
 
 POPCORN_API popcorn_status popcorn_assign_step_noalloc(const float* K, int64_t ldk, const float* kdiag,

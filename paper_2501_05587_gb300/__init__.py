@@ -29,6 +29,8 @@ __all__ = [
     "popcorn_assign_step_noalloc",
     "NOALLOC_SCRATCH_BYTES",
     "popcorn_version",
+    "popcorn_autotune_entries",
+    "popcorn_autotune_clear",
     "kernel_spec",
     "EXPORTED_SYMBOLS",
 ]
@@ -52,6 +54,8 @@ EXPORTED_SYMBOLS = (
     "popcorn_fit",
     "popcorn_assign_step_noalloc",
     "popcorn_fit_batched",
+    "popcorn_autotune_entries",
+    "popcorn_autotune_clear",
 )
 
 KIND = {"linear": 0, "polynomial": 1, "gaussian": 2}
@@ -66,7 +70,7 @@ class _Kernel(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("store_k", ctypes.c_int32),
                 ("check_convergence", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("k_storage", ctypes.c_int32), ("reserved32", ctypes.c_int32),
+                ("k_storage", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("reserved", ctypes.c_int64 * 5)]
 
 
@@ -80,7 +84,9 @@ class _FitInfo(ctypes.Structure):
                 ("assign_launches", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("J_history", ctypes.POINTER(ctypes.c_double)),
-                ("changed_history", ctypes.POINTER(ctypes.c_int32))]
+                ("changed_history", ctypes.POINTER(ctypes.c_int32)), ("tune_cache_hit", ctypes.c_int32),
+                ("tune_candidates", ctypes.c_int32), ("tune_ms", ctypes.c_double),
+                ("schedule", ctypes.c_int32 * 4)]
 
 
 class _Instance(ctypes.Structure):
@@ -106,6 +112,10 @@ _lib.popcorn_assign_step_noalloc.argtypes = _lib.popcorn_assign_step.argtypes
 _lib.popcorn_fit_batched.restype = ctypes.c_int
 _lib.popcorn_fit_batched.argtypes = [_i32, ctypes.POINTER(_Instance), _i32, _dbl, ctypes.POINTER(_Options),
                                      ctypes.POINTER(_dbl), ctypes.POINTER(_i32), ctypes.POINTER(_FitInfo), _vp]
+_lib.popcorn_autotune_entries.restype = _i32
+_lib.popcorn_autotune_entries.argtypes = []
+_lib.popcorn_autotune_clear.restype = None
+_lib.popcorn_autotune_clear.argtypes = []
 _lib.popcorn_fit.restype = ctypes.c_int
 _lib.popcorn_fit.argtypes = [_vp, _i64, _i32, _i64, _i32, _Kernel, _vp, _i32, _dbl,
                              ctypes.POINTER(_Options), _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i32),
@@ -223,10 +233,26 @@ def popcorn_assign_step_noalloc(K, kdiag, labels, k: int, want_E: bool = False, 
                         want_E, stream)
 
 
+def _info_dict(info) -> dict:
+    out = {f: getattr(info, f) for f, _ in _FitInfo._fields_ if f not in ("J_history", "changed_history", "schedule")}
+    out["schedule"] = list(info.schedule)
+    return out
+
+
+def popcorn_autotune_entries() -> int:
+    """Workload signatures with a tuned schedule in this process's cache."""
+    return int(_lib.popcorn_autotune_entries())
+
+
+def popcorn_autotune_clear() -> None:
+    """Forget every tuned schedule of this process (a cache file is left alone)."""
+    _lib.popcorn_autotune_clear()
+
+
 def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float = 0.0,
                 precision: str = "fp32", check_convergence: bool = True, timing: bool = False,
                 history: bool = False, labels_out=None, store_k: bool = True, k_storage: str = "fp32",
-                stream=None) -> dict:
+                autotune: bool = False, stream=None) -> dict:
     """Kernel K-means (Alg. 2).  P and init_labels may live on the host or the device.
 
     ``store_k=False`` selects the recompute path (K never stored; precision
@@ -254,7 +280,7 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
         else:
             labels_out = torch.empty(n, dtype=torch.int32, device=init_labels.device)
     opt = _Options(PRECISION[precision], 1 if store_k else 0, 1 if check_convergence else 0, 1 if timing else 0,
-                   K_STORAGE[k_storage], 0, (ctypes.c_int64 * 5)())
+                   K_STORAGE[k_storage], 1 if autotune else 0, (ctypes.c_int64 * 5)())
     info = _FitInfo()
     Jh = (ctypes.c_double * max(1, max_iter))() if history else None
     Ch = (ctypes.c_int32 * max(1, max_iter))() if history else None
@@ -267,7 +293,7 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
                             float(tol), ctypes.byref(opt), _ptr(labels_out), ctypes.byref(obj),
                             ctypes.byref(its), ctypes.byref(info), _stream(stream)),
            "popcorn_fit")
-    out_info = {f: getattr(info, f) for f, _ in _FitInfo._fields_ if f not in ("J_history", "changed_history")}
+    out_info = _info_dict(info)
     if history:
         out_info["J_history"] = list(Jh[: its.value])
         out_info["changed_history"] = list(Ch[: its.value])
@@ -276,7 +302,8 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
 
 
 def popcorn_fit_batched(instances, max_iter: int, tol: float = 0.0, precision: str = "fp32",
-                        check_convergence: bool = True, timing: bool = False, stream=None) -> dict:
+                        check_convergence: bool = True, timing: bool = False, autotune: bool = False,
+                        stream=None) -> dict:
     """Many independent fits in one captured CUDA graph.
 
     ``instances``: list of dicts {"P": (n, d) float32 CUDA tensor, "k": int, "kernel": dict,
@@ -298,12 +325,12 @@ def popcorn_fit_batched(instances, max_iter: int, tol: float = 0.0, precision: s
         outs.append(out)
         arr[t] = _Instance(P.data_ptr(), P.shape[0], P.shape[1], P.stride(0), int(x["k"]), _kernel(x["kernel"]),
                            lab.data_ptr(), out.data_ptr())
-    opt = _Options(PRECISION[precision], 1, 1 if check_convergence else 0, 1 if timing else 0, 0, 0,
-                   (ctypes.c_int64 * 5)())
+    opt = _Options(PRECISION[precision], 1, 1 if check_convergence else 0, 1 if timing else 0, 0,
+                   1 if autotune else 0, (ctypes.c_int64 * 5)())
     objs = (ctypes.c_double * len(instances))()
     its = (ctypes.c_int32 * len(instances))()
     info = _FitInfo()
     _check(_lib.popcorn_fit_batched(len(instances), arr, int(max_iter), float(tol), ctypes.byref(opt), objs, its,
                                     ctypes.byref(info), _stream(stream)), "popcorn_fit_batched")
-    out_info = {f: getattr(info, f) for f, _ in _FitInfo._fields_ if f not in ("J_history", "changed_history")}
+    out_info = _info_dict(info)
     return {"labels": outs, "objectives": list(objs), "iterations": list(its), "info": out_info}

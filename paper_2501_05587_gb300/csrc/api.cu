@@ -3,6 +3,7 @@
 // control lives on the device).
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -238,7 +239,19 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
                              int32_t* labels_out, double* objective_out, int32_t* iterations_out,
                              popcorn_fit_info* info, cudaStream_t s, DeviceInfo* dev) {
     const int ni = (int)n;
-    const RecomputePlan rp = plan_recompute(ni, d, k, opt.precision, dev->sms, dev->recompute_smem);
+    RecomputePlan rp = plan_recompute(ni, d, k, opt.precision, dev->sms, dev->recompute_smem);
+    // schedules the autotuner may time: row blocks per tile x units per SM
+    std::vector<RecomputePlan> cands;
+    int max_nslot = rp.nslot;
+    if (opt.autotune && rp.ok) {
+        for (int rbp : {2, 1})
+            for (int upsm : {8, 16, 32}) {
+                const RecomputePlan c = plan_recompute(ni, d, k, opt.precision, dev->sms, dev->recompute_smem, rbp, upsm);
+                if (!c.ok) continue;
+                cands.push_back(c);
+                max_nslot = c.nslot > max_nslot ? c.nslot : max_nslot;
+            }
+    }
     if (!rp.ok)
         return fail(POPCORN_ERR_UNSUPPORTED, "the recompute path needs d <= %d (%s) and k <= 255",
                     opt.precision == POPCORN_FP8 ? 512 : 256, opt.precision == POPCORN_FP8 ? "FP8" : "BF16");
@@ -292,7 +305,7 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
     POPCORN_TRY(ws.alloc(&b.lab32, ni, "labels"));
     POPCORN_TRY(ws.alloc(&b.lab8, nlab, "label bytes"));
     POPCORN_TRY(ws.alloc(&b.counts, 2 * (size_t)k, "counts"));
-    POPCORN_TRY(ws.alloc(&b.Spart, (size_t)rp.nslot * ni * k, "segment sums"));
+    POPCORN_TRY(ws.alloc(&b.Spart, (size_t)max_nslot * ni * k, "segment sums"));
     POPCORN_TRY(ws.alloc(&b.zpart, (size_t)zblocks * k, "block partials"));
     POPCORN_TRY(ws.alloc(&b.zsum, (size_t)k, "z sums"));
     POPCORN_TRY(ws.alloc(&b.cnorm, (size_t)k, "centroid norms"));
@@ -321,6 +334,49 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
     POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
     POPCORN_CUDA(launch_init_labels(Ld, ni, k, b.lab32, b.lab8, b.counts, b.st, s));
     launches += 4;
+    int tune_hit = 0, tune_cands = 0;
+    double tune_ms = 0.0;
+    if (opt.autotune && !cands.empty()) {
+        const TuneKey key{2, opt.precision, log2_bucket((double)ni), d, k, kp.kind, 0, dev->sms};
+        TuneValue best{};
+        if (tune_lookup(key, &best)) {
+            tune_hit = 1;
+        } else {
+            // time one pass of every candidate on the initial labels (a pass only
+            // rewrites its scratch: the sorted copies and the segment sums)
+            const auto w0 = std::chrono::steady_clock::now();
+            cudaEvent_t t0, t1;
+            POPCORN_TRY(g_events.get(&t0));
+            POPCORN_TRY(g_events.get(&t1));
+            best.ms = 3.0e38f;
+            for (const RecomputePlan& c : cands) {
+                float ms = 3.0e38f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    POPCORN_CUDA(cudaEventRecord(t0, s));
+                    cudaError_t e = launch_recompute_pass(b, kp, c, rb, &b.st->kbuild_err, 0, s);
+                    if (e == cudaErrorInvalidValue) return fail(POPCORN_ERR_CUDA, "tensor map creation failed");
+                    POPCORN_CUDA(e);
+                    POPCORN_CUDA(cudaEventRecord(t1, s));
+                    POPCORN_CUDA(cudaEventSynchronize(t1));
+                    float el = 0.f;
+                    POPCORN_CUDA(cudaEventElapsedTime(&el, t0, t1));
+                    if (rep > 0 && el < ms) ms = el;   // rep 0 warms up
+                }
+                ++tune_cands;
+                if (ms < best.ms) {
+                    best.ms = ms;
+                    best.p[0] = c.rbp;
+                    best.p[1] = c.units_per_sm;
+                    best.p[2] = 0;
+                    best.p[3] = 0;
+                }
+            }
+            tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+            tune_store(key, best);
+        }
+        for (const RecomputePlan& c : cands)
+            if (c.rbp == best.p[0] && c.units_per_sm == best.p[1]) rp = c;
+    }
     if (timing) {
         POPCORN_TRY(g_events.get(&ev_b1));
         POPCORN_CUDA(cudaEventRecord(ev_b1, s));
@@ -417,6 +473,13 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
         info->assign_launches = iters;
         info->h2d_bytes = h2d;
         info->d2h_bytes = d2h;
+        info->tune_cache_hit = tune_hit;
+        info->tune_candidates = tune_cands;
+        info->tune_ms = tune_ms;
+        info->schedule[0] = rp.rbp;
+        info->schedule[1] = rp.nseg;
+        info->schedule[2] = rp.units_per_sm;
+        info->schedule[3] = 0;
         info->kbuild_ms = info->loop_ms = info->reduce_ms = info->assign_ms = info->eval_ms = 0.0;
         if (timing) {
             info->kbuild_ms = elapsed(ev_b0, ev_b1);
@@ -567,7 +630,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         return fail(POPCORN_ERR_INVALID, "k = %d outside [1, min(n - 1, %d)]", k, kMaxClusters);
     if (max_iter < 0) return fail(POPCORN_ERR_INVALID, "max_iter = %d < 0", max_iter);
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
-    if (opt.reserved32 != 0) return fail(POPCORN_ERR_INVALID, "options.reserved32 must be 0");
+    if (opt.autotune != 0 && opt.autotune != 1) return fail(POPCORN_ERR_INVALID, "options.autotune must be 0 or 1");
     for (int r = 0; r < 5; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
     if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)
@@ -748,6 +811,9 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         }
         info->converged = hs.converged;
         info->kernel_launches = launches;
+        info->tune_cache_hit = info->tune_candidates = 0;
+        info->tune_ms = 0.0;
+        for (int q = 0; q < 4; ++q) info->schedule[q] = 0;
         // passes that did work (launches after convergence return at once)
         const bool eval_ran = !(hs.iter > 0 && hs.last_changed == 0);
         info->reduce_launches = iters + (eval_ran ? 1 : 0);
@@ -785,7 +851,7 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         return fail(POPCORN_ERR_INVALID, "count must be >= 1 and the output arrays non-null");
     if (max_iter < 0) return fail(POPCORN_ERR_INVALID, "max_iter = %d < 0", max_iter);
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
-    if (opt.reserved32 != 0) return fail(POPCORN_ERR_INVALID, "options.reserved32 must be 0");
+    if (opt.autotune != 0 && opt.autotune != 1) return fail(POPCORN_ERR_INVALID, "options.autotune must be 0 or 1");
     for (int r = 0; r < 5; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
     if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)
@@ -813,6 +879,9 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
     };
     std::vector<Offs> o(count);
     const int hist_len = max_iter > 0 ? max_iter : 1;
+    // K-stream unit lengths the autotuner may pick (Spart is sized for the shortest)
+    static const int kSegCand[] = {2048, 4096, 8192, 16384};
+    const int min_seglen = opt.autotune ? kSegCand[0] : kBatchSeg;
     for (int t = 0; t < count; ++t) {
         const popcorn_instance& x = inst[t];
         if (!x.P || !x.init_labels || !x.labels_out) return fail(POPCORN_ERR_INVALID, "instance %d: null pointer", t);
@@ -838,8 +907,8 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         b.ldk = (n + 3) / 4 * 4;
         b.n = n;
         b.k = k;
-        b.seglen = kBatchSeg;
-        b.nseg = (n + kBatchSeg - 1) / kBatchSeg;
+        b.seglen = min_seglen;
+        b.nseg = (n + min_seglen - 1) / min_seglen;
         b.init_labels = x.init_labels;
         b.labels_out = x.labels_out;
         b.unit0 = bp.units;
@@ -899,6 +968,98 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
     POPCORN_CUDA(cudaMemcpyAsync(dI, h.data(), sizeof(BatchInst) * (size_t)count, cudaMemcpyHostToDevice, s));
     int* err = reinterpret_cast<int*>(base + err_off);
     POPCORN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+
+    // ---- schedule of the batched K stream: unit length, warps per block, blocks per SM
+    auto set_seglen = [&](int seglen) {
+        bp.units = 0;
+        for (int t = 0; t < count; ++t) {
+            h[t].seglen = seglen;
+            h[t].nseg = (h[t].n + seglen - 1) / seglen;
+            h[t].unit0 = bp.units;
+            bp.units += h[t].n * h[t].nseg;
+        }
+    };
+    int sched[3] = {kBatchSeg, 0, 0};
+    int tune_hit = 0, tune_cands = 0;
+    double tune_ms = 0.0;
+    if (opt.autotune) {
+        double sum_n2 = 0.0, max_n = 0.0;
+        for (int t = 0; t < count; ++t) {
+            sum_n2 += (double)h[t].n * h[t].n;
+            max_n = h[t].n > max_n ? h[t].n : max_n;
+        }
+        const TuneKey key{1, opt.precision, count, bp.kmax, log2_bucket(sum_n2), log2_bucket(max_n),
+                          opt.k_storage, dev->sms};
+        TuneValue best{};
+        if (tune_lookup(key, &best)) {
+            tune_hit = 1;
+        } else {
+            // K and the initial labels are needed to time the stream: build them now
+            // (the captured graph below builds them again for the real run)
+            const auto w0 = std::chrono::steady_clock::now();
+            POPCORN_CUDA(launch_batched_init(dI, bp, max_iter, opt.check_convergence ? 1 : 0, tol, s));
+            if (opt.precision == POPCORN_FP32) {
+                POPCORN_CUDA(launch_batched_kbuild_simt(dI, bp, s));
+            } else {
+                for (int t = 0; t < count; ++t)
+                    POPCORN_CUDA(launch_kbuild_tc(h[t].P, h[t].n, h[t].d, h[t].ldp, h[t].kp, opt.precision, h[t].K,
+                                                  h[t].ldk, h[t].kdiag, base + tc_off, err, dev->sms, s, nullptr));
+            }
+            cudaEvent_t t0, t1;
+            g_events.used = 0;
+            POPCORN_TRY(g_events.get(&t0));
+            POPCORN_TRY(g_events.get(&t1));
+            best.ms = 3.0e38f;
+            static const int kWarpCand[] = {4, 8, 16};
+            static const int kPerSmCand[] = {1, 2};
+            for (int seglen : kSegCand)
+                for (int w : kWarpCand)
+                    for (int ps : kPerSmCand) {
+                        BatchPlan cand = bp;
+                        set_seglen(seglen);
+                        cand.units = bp.units;
+                        plan_batched_reduce(&cand, dev->sms, dev->batched_smem, w, ps);
+                        if (cand.warps != w || cand.per_sm != ps) continue;   // does not fit: skip
+                        POPCORN_CUDA(cudaMemcpyAsync(dI, h.data(), sizeof(BatchInst) * (size_t)count,
+                                                     cudaMemcpyHostToDevice, s));
+                        POPCORN_CUDA(launch_batched_reduce(dI, cand, 0, s));   // warm-up
+                        float ms = 3.0e38f;
+                        for (int rep = 0; rep < 2; ++rep) {
+                            POPCORN_CUDA(cudaEventRecord(t0, s));
+                            POPCORN_CUDA(launch_batched_reduce(dI, cand, 0, s));
+                            POPCORN_CUDA(cudaEventRecord(t1, s));
+                            POPCORN_CUDA(cudaEventSynchronize(t1));
+                            float e = 0.f;
+                            POPCORN_CUDA(cudaEventElapsedTime(&e, t0, t1));
+                            ms = e < ms ? e : ms;
+                        }
+                        ++tune_cands;
+                        if (ms < best.ms) {
+                            best.ms = ms;
+                            best.p[0] = seglen;
+                            best.p[1] = w;
+                            best.p[2] = ps;
+                            best.p[3] = 0;
+                        }
+                    }
+            int herr = 0;
+            POPCORN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            POPCORN_CUDA(cudaStreamSynchronize(s));
+            if (herr) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the tensor-core K build ran out");
+            if (tune_cands == 0) return fail(POPCORN_ERR_UNSUPPORTED, "no batched schedule fits this device");
+            tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+            tune_store(key, best);
+        }
+        sched[0] = best.p[0];
+        sched[1] = best.p[1];
+        sched[2] = best.p[2];
+    }
+    set_seglen(sched[0]);
+    plan_batched_reduce(&bp, dev->sms, dev->batched_smem, sched[1], sched[2]);
+    sched[1] = bp.warps;
+    sched[2] = bp.per_sm;
+    if (bp.units <= 0 || bp.units >= (1 << 30)) return fail(POPCORN_ERR_UNSUPPORTED, "batch too large");
+    POPCORN_CUDA(cudaMemcpyAsync(dI, h.data(), sizeof(BatchInst) * (size_t)count, cudaMemcpyHostToDevice, s));
 
     // ---- capture the whole batch once
     cudaStream_t cs;
@@ -985,6 +1146,13 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         info->h2d_bytes = info->d2h_bytes = 0;
         info->kbuild_ms = info->reduce_ms = info->assign_ms = info->eval_ms = 0.0;
         info->loop_ms = timing ? elapsed(e0, e1) : 0.0;
+        info->tune_cache_hit = tune_hit;
+        info->tune_candidates = tune_cands;
+        info->tune_ms = tune_ms;
+        info->schedule[0] = sched[0];
+        info->schedule[1] = sched[1];
+        info->schedule[2] = sched[2];
+        info->schedule[3] = 0;
     }
     return POPCORN_OK;
 }

@@ -939,18 +939,26 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2)
 
 }  // namespace
 
-void plan_batched_reduce(BatchPlan* bp, int num_sms, int smem_budget) {
+void plan_batched_reduce(BatchPlan* bp, int num_sms, int smem_budget, int warps, int per_sm_req) {
     const size_t per_warp = (size_t)bp->kmax * 32 * sizeof(float);
     int w = (int)((size_t)smem_budget / per_warp);
     if (w > kReduceMaxWarps) w = kReduceMaxWarps;
+    if (warps > 0 && warps < w) w = warps;
     if (w < 1) w = 1;
     bp->warps = w;
     bp->smem = per_warp * w;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_reduce_kernel, 32 * w, bp->smem);
     cudaGetLastError();
+    if (per_sm_req > 0 && per_sm_req < per_sm) per_sm = per_sm_req;
     if (per_sm < 1) per_sm = 1;
+    bp->per_sm = per_sm;
     bp->grid = num_sms * per_sm;
+}
+
+cudaError_t launch_batched_reduce(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s) {
+    batched_reduce_kernel<<<bp.grid, bp.warps * 32, bp.smem, s>>>(dI, bp.count, bp.units, bp.kmax, eval);
+    return cudaGetLastError();
 }
 
 cudaError_t configure_batched(int smem_optin) {

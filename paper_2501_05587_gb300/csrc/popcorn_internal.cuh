@@ -110,6 +110,7 @@ struct RecomputePlan {
     int nseg, seglen;   // column segments (units = row blocks x segments)
     int stages;         // column k-block ring depth
     int nslot;          // Spart slots: nseg x epilogue groups per row block
+    int units_per_sm;   // the unit-count target nseg was derived from
     int eg;             // epilogue warpgroups
     int rbp;            // 128-row blocks per unit (2: each column tile feeds two MMAs)
     int threads;        // 64 + 128 * eg
@@ -134,7 +135,10 @@ struct RecomputeBuffers {
     int* maxkn;           // bits of max_i |c2| r_i (Gaussian; zeroed before quantize)
 };
 
-RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, int smem_budget);
+// rbp_req: 0 = two row blocks per tile when 3 ring stages fit, else one; 1 or 2 = that
+// many (ok = false if it does not fit).  units_per_sm: column-segment target (0 = 16).
+RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, int smem_budget, int rbp_req = 0,
+                             int units_per_sm = 0);
 cudaError_t configure_recompute(int smem_optin, int* usable);
 int recompute_sort_blocks(int n);
 
@@ -224,7 +228,7 @@ struct BatchPlan {
     long long tiles;          // K tiles of all instances
     int units, zblocks, ablocks, lblocks;
     int kmax;
-    int warps, grid;          // batched K-stream launch
+    int warps, grid, per_sm;  // batched K-stream launch
     size_t smem;
 };
 
@@ -239,8 +243,26 @@ cudaError_t launch_batched_kbuild_simt(const BatchInst* dI, const BatchPlan& bp,
 // one pass over every instance that has not stopped (K stream, z, argmin)
 cudaError_t launch_batched_pass(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s);
 cudaError_t launch_batched_copy_labels(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s);
-// warps / grid / shared memory of the batched K stream for clusters up to kmax
-void plan_batched_reduce(BatchPlan* bp, int num_sms, int smem_budget);
+// warps / grid / shared memory of the batched K stream for clusters up to kmax;
+// warps = 0 / per_sm = 0 pick the largest that fits / the occupancy limit
+void plan_batched_reduce(BatchPlan* bp, int num_sms, int smem_budget, int warps = 0, int per_sm = 0);
+// the batched K stream alone (what the autotuner times)
+cudaError_t launch_batched_reduce(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s);
+
+// ---- autotune cache (autotune.cu) ---------------------------------------------
+struct TuneKey {
+    int32_t target;       // 1: batched K stream, 2: recompute pass
+    int32_t precision;
+    int32_t a, b, c, d, e;   // target-specific size buckets
+    int32_t sms;
+};
+struct TuneValue {
+    int32_t p[4];         // the chosen schedule (target-specific)
+    float ms;             // its measured time
+};
+int32_t log2_bucket(double x);   // round(4 log2 x): quarter-octave buckets
+bool tune_lookup(const TuneKey& k, TuneValue* v);
+void tune_store(const TuneKey& k, const TuneValue& v);
 cudaError_t configure_batched(int smem_optin);
 
 }  // namespace popcorn

@@ -42,7 +42,9 @@ constexpr int RN = 128;                 // columns per block (MMA N)
 constexpr int KBB = 128;                // operand bytes per row per k-block (64 BF16 / 128 E4M3)
 constexpr int KB_TILE = RM * KBB;       // 16 KB
 constexpr int kNoLabel = 0xFF;          // padding columns beyond n
-constexpr int MS = 4;                   // column-metadata ring slots
+constexpr int MS = 16;                  // column-metadata ring slots: deep enough that the epilogue,
+                                        // which frees them, never limits how far the copies run ahead
+constexpr int NBAR = 96;                // mbarrier slots reserved (2 stages + 4 + 2 MS + 3 used)
 constexpr int META_LAB = 0, META_KN = 128, META_SC = 128 + 512, META_BYTES = 128 + 512 + 512;
 
 struct RcArgs {
@@ -650,7 +652,8 @@ bool make_map_u8(CUtensorMap* m, void* base, uint64_t inner_bytes, uint64_t rows
 
 // ---------------------------------------------------------------- host side
 
-RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, int smem_budget) {
+RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, int smem_budget, int rbp_req,
+                             int units_per_sm) {
     RecomputePlan p{};
     p.fp8 = precision == POPCORN_FP8;
     const int elem = p.fp8 ? 1 : 2;
@@ -665,10 +668,10 @@ RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, in
     // row blocks per unit (each column tile then feeds two MMAs, halving the operand
     // traffic from L2 per flop); fall back to one when fewer than 3 ring stages fit.
     const int meta = MS * META_BYTES;
-    const int fixed = meta + 64 * 8 + 64 + 1024;
-    int rbp = 2;
+    const int fixed = meta + NBAR * 8 + 64 + 1024;
+    int rbp = rbp_req == 1 ? 1 : 2;
     int stages = (smem_budget - rbp * p.nkb * KB_TILE - fixed) / KB_TILE;
-    if (stages < 3) {
+    if (stages < 3 && rbp_req == 0) {
         rbp = 1;
         stages = (smem_budget - rbp * p.nkb * KB_TILE - fixed) / KB_TILE;
     }
@@ -680,10 +683,11 @@ RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, in
     p.off_b = rbp * p.nkb * KB_TILE;
     p.off_meta = p.off_b + stages * KB_TILE;
     p.off_bar = p.off_meta + meta;
-    // units: groups of rbp row blocks x column segments, about 16 per SM
+    // units: groups of rbp row blocks x column segments, about units_per_sm per SM
     {
         const int Tg = (p.npad / RM + rbp - 1) / rbp;
-        long long ns = (16LL * num_sms + Tg - 1) / Tg;
+        p.units_per_sm = units_per_sm > 0 ? units_per_sm : 16;
+        long long ns = ((long long)p.units_per_sm * num_sms + Tg - 1) / Tg;
         const long long maxseg = p.ncols / RN;
         if (ns > maxseg) ns = maxseg;
         if (ns < 1) ns = 1;
@@ -697,7 +701,7 @@ RecomputePlan plan_recompute(int n, int d, int k, int precision, int num_sms, in
     // factored Gaussian: exp2(x_ij) with x_ij <= |c2| r_i summed over up to ncols
     // columns must stay finite: |c2| r_i + log2(ncols) well below 128
     p.fact_limit = 120.f - std::log2((float)p.ncols);
-    p.off_misc = p.off_bar + 64 * 8;
+    p.off_misc = p.off_bar + NBAR * 8;
     p.smem = p.off_misc + 64 + 1024;
     p.ok = p.nkb <= 4 && stages >= 2 && k <= 255;
     p.grid = num_sms;

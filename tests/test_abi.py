@@ -83,7 +83,7 @@ def test_invalid_arguments_rejected_before_any_cuda_call(pc):
     bad = pc._Options(0, 1, 1, 0, 0, 0, (ctypes.c_int64 * 5)(1, 0, 0, 0, 0))
     assert fit(opt=ctypes.byref(bad)) == 1                       # reserved must be zero
     bad32 = pc._Options(0, 1, 1, 0, 0, 3, (ctypes.c_int64 * 5)())
-    assert fit(opt=ctypes.byref(bad32)) == 1
+    assert fit(opt=ctypes.byref(bad32)) == 1                     # autotune must be 0 or 1
     badks = pc._Options(0, 1, 1, 0, 7, 0, (ctypes.c_int64 * 5)())
     assert fit(opt=ctypes.byref(badks)) == 1                     # unknown K storage type
     rec = pc._Options(0, 0, 1, 0, 0, 0, (ctypes.c_int64 * 5)())
@@ -98,3 +98,29 @@ def test_invalid_arguments_rejected_before_any_cuda_call(pc):
     st = lib.popcorn_assign_step(P.ctypes.data, 16, P.ctypes.data, 10, 0, lab.ctypes.data, lab.ctypes.data,
                                  None, None, None, None, None, None)
     assert st == 1
+
+
+def test_autotune_cache_entries_and_clear(pc):
+    """The tuned-schedule cache is host state: counting and clearing it touch no GPU."""
+    pc.popcorn_autotune_clear()
+    assert pc.popcorn_autotune_entries() == 0
+
+
+def test_autotune_cache_file_is_read_by_a_new_process(pc, tmp_path):
+    """Entries persisted in POPCORN_TUNE_CACHE are loaded by the next process (no GPU
+    needed: reading the cache is host work); malformed lines are ignored and a later
+    line with the same key replaces an earlier one."""
+    import subprocess
+    import sys
+    path = tmp_path / "tune.txt"
+    path.write_text("1 0 256 64 130 52 0 152 : 4096 8 2 0 3.500000\n"
+                    "this line is not an entry\n"
+                    "2 3 70 128 100 2 0 152 : 2 16 0 0 9.250000\n"
+                    "1 0 256 64 130 52 0 152 : 8192 16 1 0 3.000000\n")
+    code = ("import paper_2501_05587_gb300 as pc; print(pc.popcorn_autotune_entries()); "
+            "pc.popcorn_autotune_clear(); print(pc.popcorn_autotune_entries())")
+    env = dict(os.environ, POPCORN_TUNE_CACHE=str(path))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.split() == ["2", "0"]
+    assert path.read_text().count("\n") == 4        # clearing leaves the file alone
