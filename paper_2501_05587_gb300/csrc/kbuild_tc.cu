@@ -2,24 +2,34 @@
 //
 // Sec. 3.2 forms B = P P^T with GEMM or SYRK and then applies the kernel
 // function elementwise (Gaussian through Eq. 12 from B and the row norms).
-// Here one persistent kernel walks the upper-triangle 128 x 128 tiles of B:
+// Here one persistent kernel walks the tiles (p, j) of the upper triangle,
+// where a tile is a pair of 128-row blocks (2p, 2p + 1) against one
+// 128-column block j >= 2p:
 //
-//   warp 0  (one lane)  TMA loads of 128 x 64 BF16 operand tiles into a
-//                       4-stage shared-memory ring (128-byte swizzle);
-//   warp 1  (one lane)  tcgen05.mma kind::f16 (BF16 x BF16 -> FP32) into one
-//                       of two 128-column TMEM accumulators;
-//   warps 2-5           epilogue: tcgen05.ld the accumulator, apply kappa
-//                       with FP32 row norms, stage the tile and its transpose
-//                       in shared memory and TMA-store both into K.
+//   warp 0  (one lane)  TMA loads, per 64-deep k-block, of the 256 rows of the
+//                       row pair and the 128 rows of the column block (128-byte
+//                       swizzle) into a ring of stages;
+//   warp 1  (one lane)  tcgen05.mma kind::f16 (BF16 x BF16 -> FP32, M = N = 128)
+//                       into the two 128-column TMEM accumulators of the tile
+//                       (double-buffered: 512 columns);
+//   warps 2-5           epilogue: tcgen05.ld the accumulators, apply kappa with
+//                       FP32 row norms, stage each 128 x 32 chunk and its
+//                       transpose in shared memory and TMA-store both into K.
 //
-// Double-buffered TMEM lets the MMAs of tile t+1 run under the epilogue of
-// tile t.  Precision modes:
-//   BF16    A = B = bf16(P);  norms of the rounded rows, so the Gaussian
-//           distance r_i + r_j - 2 B_ij is the distance of the rounded points.
-//   BF16X3  A = [hi | hi | lo], B = [hi | lo | hi] with hi = bf16(p),
-//           lo = bf16(p - hi): one GEMM of depth 3d gives
-//           hi.hi + hi.lo + lo.hi, which recovers ~16 significant bits of
-//           the cross term that the Gaussian's cancellation needs.
+// Why row pairs: an SM takes in about 36 bytes per clock from L2 whichever path
+// it uses (TMA, bulk copy, cp.async or vector loads), and a 128 x 128 tile moves
+// 32 KB per k-block for 4 MMAs -- three times what that allows at the MMA rate.
+// Sharing each column block between two row blocks cuts the bytes per MMA by a
+// quarter; block (2p + 1, 2p), below the diagonal, is computed and not stored.
+//
+// Precision modes (operand matrix W, one row per point):
+//   BF16    W = bf16(P);  norms of the rounded rows, so the Gaussian distance
+//           r_i + r_j - 2 B_ij is the distance of the rounded points.
+//   BF16X3  W = [hi | lo] with hi = bf16(p), lo = bf16(p - hi); each stage
+//           holds the hi and lo parts of both operands once and the MMAs form
+//           hi.hi + hi.lo + lo.hi (~16 significant bits of the cross term that
+//           the Gaussian's cancellation needs) -- 2 d loaded instead of the 3 d
+//           a [hi|hi|lo] x [hi|lo|hi] GEMM would stream.
 //
 // Every mbarrier wait is bounded (about 2 s by %globaltimer).  A wait that
 // runs out sets *err, raises a shared abort flag that ends every role's loop,
@@ -41,46 +51,41 @@ using namespace tc;
 __device__ __forceinline__ void epi_bar() { named_bar<128>(1); }   // the 4 epilogue warps
 constexpr uint32_t kIdesc = idesc_bf16(128, 128);
 
-constexpr int BM = 128, BN = 128, BK = 64;   // tile rows, tile cols, bf16 depth per stage
-constexpr int STAGES = 4;
-constexpr int TILE_BYTES = BM * BK * 2;      // 16 KB per operand tile
+constexpr int BM = 128, BK = 64;             // block rows / columns, bf16 depth per k-block
+constexpr int ROWS_BYTES = 2 * BM * BK * 2;  // 32 KB: 256 rows of one part (hi or lo)
+constexpr int COLS_BYTES = BM * BK * 2;      // 16 KB: 128 rows of one part
 constexpr int STG_BYTES = 128 * 32 * 4;      // one 128 x 32 FP32 staging chunk
 constexpr int NTHREADS = 192;                // 6 warps
-
-// shared-memory layout (offsets from a 1024-aligned base)
-constexpr int OFF_A = 0;
-constexpr int OFF_B = OFF_A + STAGES * TILE_BYTES;
-constexpr int OFF_SD = OFF_B + STAGES * TILE_BYTES;   // 2 direct staging chunks (128B swizzle)
-constexpr int OFF_ST = OFF_SD + 2 * STG_BYTES;         // 2 transposed staging chunks (no swizzle)
-constexpr int OFF_RJ = OFF_ST + 2 * STG_BYTES;         // 128 column norms
-constexpr int OFF_BAR = OFF_RJ + 128 * 4;
-constexpr int NBAR = 2 * STAGES + 4 + 1;
-constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
-constexpr int SMEM_BYTES = OFF_MISC + 16 + 1024;       // + slack for 1024 alignment
+constexpr int MAX_STAGES = 4;
+constexpr int RING_BYTES = 192 * 1024;       // operand ring
+constexpr uint32_t kTmemCols = 512;          // 2 buffers x 2 row blocks x 128 columns
 
 struct TcArgs {
-    int n, T, nkb;            // rows, tile rows, 64-deep k-blocks
-    long long tiles;          // T (T + 1) / 2
+    int n, T, T2, nkb;        // rows, 128-blocks, row pairs, 64-deep k-blocks per part
+    int dpad;                 // elements per part (W row = [hi | lo] for BF16X3)
+    int x3;                   // 1: BF16X3 (three products per k-step)
+    int stages, stage_bytes;  // ring: 48 KB (BF16) or 96 KB (BF16X3) stages
+    int nstg;                 // staging buffers per kind (2, or 1 when the ring needs the room)
+    int off_sd, off_st, off_rj, off_bar, off_misc;
+    long long tiles;          // sum_p (T - 2 p)
     KernParams kp;
     const float* norms;       // row norms of the represented rows (Gaussian)
     float* kdiag;
     int* err;
 };
 
-__device__ __forceinline__ void tri_coords(long long t, int T, int* bi, int* bj) {
-    // t enumerates the upper triangle row by row: row b starts at off(b) = b*T - b*(b-1)/2.
-    // An FP32 estimate of the quadratic's root, then exact integer correction (no FP64:
-    // GB300 runs FP64 at a small fraction of the FP32 rate).
-    const float Tf = (float)T;
-    const float disc = fmaxf((2.f * Tf + 1.f) * (2.f * Tf + 1.f) - 8.f * (float)t, 0.f);
-    int b = (int)(((2.f * Tf + 1.f) - sqrtf(disc)) * 0.5f);
-    if (b < 0) b = 0;
-    if (b > T - 1) b = T - 1;
-    auto off = [&](long long r) { return r * (long long)T - r * (r - 1) / 2; };
-    while (b > 0 && off(b) > t) --b;
-    while (b < T - 1 && off(b + 1) <= t) ++b;
-    *bi = b;
-    *bj = b + (int)(t - off(b));
+// tile t -> (row pair p, column block j): row pair p holds tiles j = 2p .. T-1 and
+// starts at off(p) = p T - p (p - 1); a binary search over p (no floating point).
+__device__ __forceinline__ void pair_coords(long long t, int T, int T2, int* p, int* j) {
+    int lo = 0, hi = T2 - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const long long off = (long long)mid * T - (long long)mid * (mid - 1);
+        if (off <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    *p = lo;
+    *j = 2 * lo + (int)(t - ((long long)lo * T - (long long)lo * (lo - 1)));
 }
 
 __device__ __forceinline__ float kappa(float b, float ri, float rj, const KernParams& kp) {
@@ -96,25 +101,26 @@ __device__ __forceinline__ float kappa(float b, float ri, float rj, const KernPa
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-    kbuild_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+    kbuild_tc_kernel(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_c,
                      const __grid_constant__ CUtensorMap map_kd, const __grid_constant__ CUtensorMap map_kt,
                      TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar0 = sbase + OFF_BAR;
+    const uint32_t bar0 = sbase + a.off_bar;
+    const int S = a.stages;
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
-    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
-    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
-    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
-    const uint32_t down_bar = bar0 + 8u * (2 * STAGES + 4);
-    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(smem + OFF_MISC);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + OFF_MISC + 4);
-    float* rj_s = reinterpret_cast<float*>(smem + OFF_RJ);
+    auto empty_bar = [&](int s) { return bar0 + 8u * (MAX_STAGES + s); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * MAX_STAGES + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * MAX_STAGES + 2 + b); };
+    const uint32_t down_bar = bar0 + 8u * (2 * MAX_STAGES + 4);
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(smem + a.off_misc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + a.off_misc + 4);
+    float* rj_s = reinterpret_cast<float*>(smem + a.off_rj);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
@@ -126,10 +132,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {   // whole warp: allocate 256 TMEM columns (two 128-column accumulators)
+    if (warp == 1) {   // whole warp: all 512 TMEM columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32((const void*)tmem_slot)),
-                     "r"(256)
+                     "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -138,30 +144,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    // stage layout: rows-hi (32 KB) | cols-hi (16 KB) [| rows-lo (32 KB) | cols-lo (16 KB)]
+    constexpr uint32_t kRowsHi = 0, kColsHi = ROWS_BYTES, kRowsLo = ROWS_BYTES + COLS_BYTES,
+                       kColsLo = 2 * ROWS_BYTES + COLS_BYTES;
     const long long G = gridDim.x;
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t issued_parity[STAGES];
-            bool issued[STAGES];
-            for (int s = 0; s < STAGES; ++s) issued[s] = false;
+            uint32_t issued_parity[MAX_STAGES];
+            bool issued[MAX_STAGES];
+            for (int s = 0; s < MAX_STAGES; ++s) issued[s] = false;
             bool ok = true;
             for (long long t = blockIdx.x; t < a.tiles && ok; t += G) {
-                int bi, bj;
-                tri_coords(t, a.T, &bi, &bj);
+                int p, j;
+                pair_coords(t, a.T, a.T2, &p, &j);
                 for (int kb = 0; kb < a.nkb; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.err)) {
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(full_bar(stage), 2 * TILE_BYTES);
-                    tma_load_2d(sbase + OFF_A + stage * TILE_BYTES, &map_a, kb * BK, bi * BM, full_bar(stage));
-                    tma_load_2d(sbase + OFF_B + stage * TILE_BYTES, &map_b, kb * BK, bj * BN, full_bar(stage));
+                    const uint32_t st = sbase + (uint32_t)(stage * a.stage_bytes);
+                    mbar_arrive_expect_tx(full_bar(stage), (uint32_t)a.stage_bytes);
+                    tma_load_2d(st + kRowsHi, &map_r, kb * BK, p * 2 * BM, full_bar(stage));
+                    tma_load_2d(st + kColsHi, &map_c, kb * BK, j * BM, full_bar(stage));
+                    if (a.x3) {
+                        tma_load_2d(st + kRowsLo, &map_r, a.dpad + kb * BK, p * 2 * BM, full_bar(stage));
+                        tma_load_2d(st + kColsLo, &map_c, a.dpad + kb * BK, j * BM, full_bar(stage));
+                    }
                     issued[stage] = true;
                     issued_parity[stage] = phase;
-                    if (++stage == STAGES) {
+                    if (++stage == S) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -169,7 +183,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (!ok) {
                 // aborted: let this CTA's own copies land before shared memory goes away
-                for (int s = 0; s < STAGES; ++s)
+                for (int s = 0; s < S; ++s)
                     if (issued[s]) {
                         const unsigned long long t0 = globaltimer();
                         while (!mbar_try_wait(full_bar(s), issued_parity[s]) && globaltimer() - t0 < kWaitLimitNs) {
@@ -192,28 +206,36 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(ab * BN);
                 for (int kb = 0; kb < a.nkb; ++kb) {
                     if (!mbar_wait(full_bar(stage), phase, abort_flag, a.err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = sbase + OFF_A + stage * TILE_BYTES;
-                    const uint32_t sb = sbase + OFF_B + stage * TILE_BYTES;
+                    const uint32_t st = sbase + (uint32_t)(stage * a.stage_bytes);
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t d_tmem = tmem + (uint32_t)(ab * 2 * BM + h * BM);
+                        const uint32_t rh = st + kRowsHi + h * (BM * BK * 2);   // row block h of the pair
+                        const uint32_t rl = st + kRowsLo + h * (BM * BK * 2);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        // 16 bf16 = 32 bytes further along K inside the 128-byte swizzled row
-                        mma_bf16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), kIdesc, (kb | kk) ? 1u : 0u);
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            // 16 bf16 = 32 bytes further along K inside the 128-byte swizzled row
+                            mma_bf16(d_tmem, sw128_desc(rh + kk * 32), sw128_desc(st + kColsHi + kk * 32), kIdesc,
+                                     (kb | kk) ? 1u : 0u);
+                            if (a.x3) {
+                                mma_bf16(d_tmem, sw128_desc(rh + kk * 32), sw128_desc(st + kColsLo + kk * 32), kIdesc, 1u);
+                                mma_bf16(d_tmem, sw128_desc(rl + kk * 32), sw128_desc(st + kColsHi + kk * 32), kIdesc, 1u);
+                            }
+                        }
                     }
                     mma_commit(empty_bar(stage));   // stage free once these MMAs have read it
-                    if (++stage == STAGES) {
+                    if (++stage == S) {
                         stage = 0;
                         phase ^= 1u;
                     }
                 }
                 if (!ok) break;
-                mma_commit(accf_bar(ab));           // accumulator ready for the epilogue
+                mma_commit(accf_bar(ab));           // both accumulators ready for the epilogue
             }
             // all MMAs issued by this thread complete before TMEM is released
             mma_commit(down_bar);
@@ -229,15 +251,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         int chunk_ctr = 0;
         bool ok = true;
         for (long long t = blockIdx.x; t < a.tiles; t += G, ++lt) {
-            int bi, bj;
-            tri_coords(t, a.T, &bi, &bj);
+            int p, j;
+            pair_coords(t, a.T, a.T2, &p, &j);
             const int ab = lt & 1;
             const uint32_t use = (uint32_t)(lt >> 1);
-            // column norms of this tile's J block
+            // column norms of this tile's column block j
             if (a.kp.kind == POPCORN_GAUSSIAN) {
-                const int j = bj * BN + et;
+                const int col = j * BM + et;
                 epi_bar();   // previous tile finished reading rj_s
-                rj_s[et] = j < a.n ? a.norms[j] : 0.f;
+                rj_s[et] = col < a.n ? a.norms[col] : 0.f;
             }
             if (!mbar_wait(accf_bar(ab), use & 1u, abort_flag, a.err)) ok = false;
             // all epilogue threads agree (one barrier, one AND) before touching TMEM or staging
@@ -247,49 +269,58 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             tc_fence_after();
             const int row_local = 32 * q + lane;
-            const int row = bi * BM + row_local;
-            const float ri = (a.kp.kind == POPCORN_GAUSSIAN && row < a.n) ? a.norms[row] : 0.f;
-            const bool diag = (bi == bj);
-            for (int c = 0; c < BN / 32; ++c) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * BN + 32 * c), v);
-                if (c == BN / 32 - 1) {
-                    // accumulator fully read: hand it back to the MMA warp
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(acce_bar(ab));
-                }
-#pragma unroll
-                for (int x = 0; x < 32; ++x) {
-                    v[x] = kappa(v[x], ri, rj_s[32 * c + x], a.kp);
-                    if (diag && 32 * c + x == row_local) {
-                        if (a.kp.kind == POPCORN_GAUSSIAN) v[x] = 1.f;
-                        if (row < a.n) a.kdiag[row] = v[x];
+            for (int h = 0; h < 2; ++h) {
+                const int rb = 2 * p + h;             // 128-row block of K
+                const int row = rb * BM + row_local;
+                const float ri = (a.kp.kind == POPCORN_GAUSSIAN && row < a.n) ? a.norms[row] : 0.f;
+                // blocks past the matrix and block (2p + 1, 2p) below the diagonal are not stored
+                const bool store = rb < a.T && rb <= j;
+                const bool diag = (rb == j);
+                for (int c = 0; c < BM / 32; ++c) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ab * 2 * BM + h * BM + 32 * c), v);
+                    if (h == 1 && c == BM / 32 - 1) {
+                        // both accumulators fully read: hand the buffer back to the MMA warp
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acce_bar(ab));
                     }
-                }
-                const int sbuf = chunk_ctr & 1;
-                ++chunk_ctr;
-                // the store that used this staging buffer two chunks ago has read it
-                if (et == 0) bulk_wait_read<1>();
-                epi_bar();
-                float* sd = reinterpret_cast<float*>(smem + OFF_SD + sbuf * STG_BYTES);
-                float* st = reinterpret_cast<float*>(smem + OFF_ST + sbuf * STG_BYTES);
-                // direct chunk: row row_local, 8 x 16-byte pieces, piece j at j ^ (row % 8)
+                    if (!store) continue;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float4 w = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                    *reinterpret_cast<float4*>(sd + row_local * 32 + ((j ^ (row_local & 7)) * 4)) = w;
-                }
-                if (!diag) {
+                    for (int x = 0; x < 32; ++x) {
+                        v[x] = kappa(v[x], ri, rj_s[32 * c + x], a.kp);
+                        if (diag && 32 * c + x == row_local) {
+                            if (a.kp.kind == POPCORN_GAUSSIAN) v[x] = 1.f;
+                            if (row < a.n) a.kdiag[row] = v[x];
+                        }
+                    }
+                    const int sbuf = a.nstg == 2 ? (chunk_ctr & 1) : 0;
+                    ++chunk_ctr;
+                    // the store that last used this staging buffer has read it
+                    if (et == 0) {
+                        if (a.nstg == 2) bulk_wait_read<1>();
+                        else bulk_wait_read<0>();
+                    }
+                    epi_bar();
+                    float* sd = reinterpret_cast<float*>(smem + a.off_sd + sbuf * STG_BYTES);
+                    float* sx = reinterpret_cast<float*>(smem + a.off_st + sbuf * STG_BYTES);
+                    // direct chunk: row row_local, 8 x 16-byte pieces, piece i at i ^ (row % 8)
 #pragma unroll
-                    for (int x = 0; x < 32; ++x) st[x * 128 + row_local] = v[x];
-                }
-                fence_proxy_async();
-                epi_bar();
-                if (et == 0) {
-                    tma_store_2d(&map_kd, bj * BN + 32 * c, bi * BM, smem_u32(sd));
-                    if (!diag) tma_store_2d(&map_kt, bi * BM, bj * BN + 32 * c, smem_u32(st));
-                    bulk_commit();
+                    for (int i = 0; i < 8; ++i) {
+                        float4 w = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        *reinterpret_cast<float4*>(sd + row_local * 32 + ((i ^ (row_local & 7)) * 4)) = w;
+                    }
+                    if (!diag) {
+#pragma unroll
+                        for (int x = 0; x < 32; ++x) sx[x * 128 + row_local] = v[x];
+                    }
+                    fence_proxy_async();
+                    epi_bar();
+                    if (et == 0) {
+                        tma_store_2d(&map_kd, j * BM + 32 * c, rb * BM, smem_u32(sd));
+                        if (!diag) tma_store_2d(&map_kt, rb * BM, j * BM + 32 * c, smem_u32(sx));
+                        bulk_commit();
+                    }
                 }
             }
         }
@@ -301,38 +332,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
 }
 
-// FP32 rows -> BF16 operand rows (and hi/lo split), zero padding, FP32 norms of
-// the represented rows.  One warp per row.
+// FP32 rows -> BF16 operand rows W (BF16X3: [hi | lo]), zero padding, FP32 norms
+// of the represented rows.  One warp per row.
 __global__ void __launch_bounds__(256) prep_operands_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
-                                                            int dpad, int x3, __nv_bfloat16* __restrict__ A,
-                                                            __nv_bfloat16* __restrict__ B, float* __restrict__ norms) {
+                                                            int dpad, int x3, __nv_bfloat16* __restrict__ W,
+                                                            float* __restrict__ norms) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n) return;
-    const int64_t lda = (int64_t)(x3 ? 3 : 1) * dpad;
-    __nv_bfloat16* ar = A + (int64_t)warp * lda;
-    __nv_bfloat16* br = B ? B + (int64_t)warp * lda : nullptr;
+    const int64_t ldw = (int64_t)(x3 ? 2 : 1) * dpad;
+    __nv_bfloat16* wr = W + (int64_t)warp * ldw;
     float nrm = 0.f;
     for (int l = lane; l < dpad; l += 32) {
         const float p = l < d ? P[(int64_t)warp * ldp + l] : 0.f;
         const __nv_bfloat16 hi = __float2bfloat16_rn(p);
         const float hf = __bfloat162float(hi);
+        wr[l] = hi;
         if (!x3) {
-            ar[l] = hi;
             nrm = fmaf(hf, hf, nrm);
         } else {
             const __nv_bfloat16 lo = __float2bfloat16_rn(p - hf);
             const float rep = hf + __bfloat162float(lo);
-            ar[l] = hi;
-            ar[dpad + l] = hi;
-            ar[2 * dpad + l] = lo;
-            br[l] = hi;
-            br[dpad + l] = lo;
-            br[2 * dpad + l] = hi;
+            wr[dpad + l] = lo;
             nrm = fmaf(rep, rep, nrm);
         }
     }
@@ -372,14 +397,19 @@ bool make_tensor_map_2d(CUtensorMap* m, CUtensorMapDataType dt, void* base, uint
 
 size_t kbuild_tc_workspace(int n, int d, int precision) {
     const size_t dpad = ((size_t)d + BK - 1) / BK * BK;
-    const size_t lda = (precision == POPCORN_BF16X3 ? 3 : 1) * dpad;
-    const size_t ops = (precision == POPCORN_BF16X3 ? 2 : 1) * (size_t)n * lda * 2;
+    const size_t ldw = (precision == POPCORN_BF16X3 ? 2 : 1) * dpad;
+    const size_t ops = (size_t)n * ldw * 2;
     return ((ops + 255) & ~(size_t)255) + (size_t)n * 4 + 256;
 }
 
+// shared memory the kernel is configured for: the largest layout below (BF16X3:
+// a full 192 KB ring and one staging buffer of each kind), the column norms,
+// barriers and slack for the 1024-byte alignment
+constexpr int kSmemBytes = RING_BYTES + 2 * STG_BYTES + BM * 4 + 16 * 8 + 16 + 1024;
+
 cudaError_t configure_kbuild_tc() {
     encode_fn();
-    return cudaFuncSetAttribute(kbuild_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    return cudaFuncSetAttribute(kbuild_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
 
 cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
@@ -387,40 +417,54 @@ cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernPara
                              int* launches) {
     const int dpad = (d + BK - 1) / BK * BK;
     const int x3 = precision == POPCORN_BF16X3 ? 1 : 0;
-    const int64_t lda = (int64_t)(x3 ? 3 : 1) * dpad;
-    __nv_bfloat16* A = static_cast<__nv_bfloat16*>(workspace);
-    const size_t abytes = (size_t)n * lda * 2;
-    __nv_bfloat16* B = x3 ? A + (size_t)n * lda : nullptr;
-    const size_t ops = (x3 ? 2 : 1) * abytes;
+    const int64_t ldw = (int64_t)(x3 ? 2 : 1) * dpad;
+    __nv_bfloat16* W = static_cast<__nv_bfloat16*>(workspace);
+    const size_t ops = (size_t)n * ldw * 2;
     float* norms = reinterpret_cast<float*>(static_cast<char*>(workspace) + ((ops + 255) & ~(size_t)255));
 
-    prep_operands_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(P, n, d, ldp, dpad, x3, A, B, norms);
+    prep_operands_kernel<<<(n * 32 + 255) / 256, 256, 0, s>>>(P, n, d, ldp, dpad, x3, W, norms);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (launches) ++*launches;
 
-    CUtensorMap ma, mb, mkd, mkt;
-    if (!make_tensor_map_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, (uint64_t)lda, (uint64_t)n, (uint64_t)lda * 2, BK, BM,
-                  CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !make_tensor_map_2d(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, x3 ? B : A, (uint64_t)lda, (uint64_t)n, (uint64_t)lda * 2,
-                  BK, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
+    CUtensorMap mr, mc, mkd, mkt;
+    if (!make_tensor_map_2d(&mr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, W, (uint64_t)ldw, (uint64_t)n, (uint64_t)ldw * 2, BK,
+                            2 * BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_tensor_map_2d(&mc, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, W, (uint64_t)ldw, (uint64_t)n, (uint64_t)ldw * 2, BK,
+                            BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
         !make_tensor_map_2d(&mkd, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, K, (uint64_t)n, (uint64_t)n, (uint64_t)ldk * 4, 32, BM,
-                  CU_TENSOR_MAP_SWIZZLE_128B) ||
+                            CU_TENSOR_MAP_SWIZZLE_128B) ||
         !make_tensor_map_2d(&mkt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, K, (uint64_t)n, (uint64_t)n, (uint64_t)ldk * 4, BM, 32,
-                  CU_TENSOR_MAP_SWIZZLE_NONE))
+                            CU_TENSOR_MAP_SWIZZLE_NONE))
         return cudaErrorInvalidValue;
 
     TcArgs a;
     a.n = n;
     a.T = (n + BM - 1) / BM;
-    a.nkb = (int)(lda / BK);
-    a.tiles = (long long)a.T * (a.T + 1) / 2;
+    a.T2 = (a.T + 1) / 2;
+    a.dpad = dpad;
+    a.nkb = dpad / BK;
+    a.x3 = x3;
+    // BF16: 3 stages of 48 KB; BF16X3: 2 stages of 96 KB (hi and lo of both operands)
+    a.stage_bytes = x3 ? 2 * (ROWS_BYTES + COLS_BYTES) : ROWS_BYTES + COLS_BYTES;
+    a.stages = x3 ? 2 : 3;
+    // staging: two buffers of each kind when the ring leaves room, else one
+    const int ring = a.stages * a.stage_bytes;
+    a.nstg = ring + 4 * STG_BYTES <= RING_BYTES + 2 * STG_BYTES ? 2 : 1;
+    a.off_sd = ring;
+    a.off_st = a.off_sd + a.nstg * STG_BYTES;
+    a.off_rj = a.off_st + a.nstg * STG_BYTES;
+    a.off_bar = a.off_rj + BM * 4;
+    a.off_misc = a.off_bar + 16 * 8;
+    a.tiles = (long long)a.T2 * a.T - (long long)a.T2 * (a.T2 - 1);
     a.kp = kp;
     a.norms = norms;
     a.kdiag = kdiag;
     a.err = err;
+    const int smem = a.off_misc + 16 + 1024;
+    if (smem > kSmemBytes) return cudaErrorInvalidConfiguration;
     const int grid = (int)(a.tiles < num_sms ? a.tiles : num_sms);
-    kbuild_tc_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(ma, mb, mkd, mkt, a);
+    kbuild_tc_kernel<<<grid, NTHREADS, smem, s>>>(mr, mc, mkd, mkt, a);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
