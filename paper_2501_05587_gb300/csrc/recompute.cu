@@ -283,17 +283,25 @@ __global__ void __launch_bounds__(64 + 128 * kEpiGroups, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
+            // This thread shares its sub-partition with four busy epilogue warps, so the
+            // loop keeps its own instructions few: descriptors are advanced by adds (the
+            // 14-bit address field of a 1024-aligned tile never carries).
             int stage = 0;
             uint32_t phase = 0;
             int ucount = 0, bc = 0;
             bool ok = true;
+            const uint64_t bdesc0 = sw128_desc(sbase + a.off_b);   // stage 0, first 32 bytes of K
+            const uint64_t adesc0 = sw128_desc(sbase);             // resident rows in shared memory
+            constexpr uint32_t kStageStep = KB_TILE >> 4;          // descriptor units per 16 KB tile
             for (int u = blockIdx.x; u < units && ok; u += G, ++ucount) {
                 int I, s, jb0, jb1;
                 unit_cols(u, &I, &s, &jb0, &jb1);
+                // the unit's resident row blocks have landed in shared memory
                 if (!mbar_wait(afull_bar, (uint32_t)ucount & 1u, abort_flag, a.err)) {
                     ok = false;
                     break;
                 }
+                tc_fence_after();
                 for (int jb = jb0; jb < jb1 && ok; ++jb, ++bc) {
                     const int ab = bc & 1;
                     if (!mbar_wait(acce_bar(ab), ((uint32_t)(bc >> 1) & 1u) ^ 1u, abort_flag, a.err)) {
@@ -307,19 +315,23 @@ __global__ void __launch_bounds__(64 + 128 * kEpiGroups, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sb = sbase + a.off_b + stage * KB_TILE;
+                        const uint64_t bd = bdesc0 + (uint64_t)(stage * kStageStep);
                         for (int h = 0; h < a.rbp; ++h) {
                             // accumulator (buffer ab, row block h) at TMEM column (ab * rbp + h) * 128
                             const uint32_t d_tmem = tmem + (uint32_t)((ab * a.rbp + h) * RN);
-                            const uint32_t sa = sbase + (h * a.nkb + kb) * KB_TILE;
-#pragma unroll
-                            for (int kk = 0; kk < KBB / 32; ++kk) {   // 32 bytes of K per instruction
-                                if (FP8)
-                                    mma_e4m3(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
-                                             (kb | kk) ? 1u : 0u);
-                                else
-                                    mma_bf16(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
-                                             (kb | kk) ? 1u : 0u);
+                            const uint64_t ad = adesc0 + (uint64_t)((h * a.nkb + kb) * kStageStep);
+                            const uint32_t acc0 = kb ? 1u : 0u;
+                            // 32 bytes of K per instruction: +2 in the descriptor's address field
+                            if (FP8) {
+                                mma_e4m3(d_tmem, ad, bd, idesc, acc0);
+                                mma_e4m3(d_tmem, ad + 2, bd + 2, idesc, 1u);
+                                mma_e4m3(d_tmem, ad + 4, bd + 4, idesc, 1u);
+                                mma_e4m3(d_tmem, ad + 6, bd + 6, idesc, 1u);
+                            } else {
+                                mma_bf16(d_tmem, ad, bd, idesc, acc0);
+                                mma_bf16(d_tmem, ad + 2, bd + 2, idesc, 1u);
+                                mma_bf16(d_tmem, ad + 4, bd + 4, idesc, 1u);
+                                mma_bf16(d_tmem, ad + 6, bd + 6, idesc, 1u);
                             }
                         }
                         mma_commit(empty_bar(stage));
