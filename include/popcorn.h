@@ -105,7 +105,17 @@ typedef struct {
                                    length, warps per block, blocks per SM) and by the
                                    recompute path of popcorn_fit (row blocks per tile, units
                                    per SM).  Results differ only by summation order.        */
-    int64_t reserved[5];        /* must be zero                                              */
+    int32_t k_pass;             /* how a pass reads a stored FP32 K: 0 = the full square, row
+                                   by row (the paper's read of K; the default); 1 = only the
+                                   128-blocks on and above the diagonal, each element feeding
+                                   its row's and (by symmetry) its column's cluster sums: half
+                                   the bytes, but slower on GB300 so far (shared-memory atomics
+                                   for the column sums).  1 needs a PSD kernel (Gaussian,
+                                   linear, polynomial with gamma, coef0 >= 0); other kernels,
+                                   FP16/BF16 K and the recompute path read as 0 / their own
+                                   scheme                                                   */
+    int32_t reserved_pad;       /* must be zero                                              */
+    int64_t reserved[4];        /* must be zero                                              */
 } popcorn_options;
 
 /* Optional per-call report of popcorn_fit (all fields written by the call,

@@ -71,10 +71,12 @@ class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("store_k", ctypes.c_int32),
                 ("check_convergence", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("k_storage", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 5)]
+                ("k_pass", ctypes.c_int32), ("reserved_pad", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 4)]
 
 
 K_STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+K_PASS = {"full": 0, "symmetric": 1}
 
 
 class _FitInfo(ctypes.Structure):
@@ -252,7 +254,7 @@ def popcorn_autotune_clear() -> None:
 def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float = 0.0,
                 precision: str = "fp32", check_convergence: bool = True, timing: bool = False,
                 history: bool = False, labels_out=None, store_k: bool = True, k_storage: str = "fp32",
-                autotune: bool = False, stream=None) -> dict:
+                autotune: bool = False, k_pass: str = "full", stream=None) -> dict:
     """Kernel K-means (Alg. 2).  P and init_labels may live on the host or the device.
 
     ``store_k=False`` selects the recompute path (K never stored; precision
@@ -280,7 +282,7 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
         else:
             labels_out = torch.empty(n, dtype=torch.int32, device=init_labels.device)
     opt = _Options(PRECISION[precision], 1 if store_k else 0, 1 if check_convergence else 0, 1 if timing else 0,
-                   K_STORAGE[k_storage], 1 if autotune else 0, (ctypes.c_int64 * 5)())
+                   K_STORAGE[k_storage], 1 if autotune else 0, K_PASS[k_pass], 0, (ctypes.c_int64 * 4)())
     info = _FitInfo()
     Jh = (ctypes.c_double * max(1, max_iter))() if history else None
     Ch = (ctypes.c_int32 * max(1, max_iter))() if history else None
@@ -326,7 +328,7 @@ def popcorn_fit_batched(instances, max_iter: int, tol: float = 0.0, precision: s
         arr[t] = _Instance(P.data_ptr(), P.shape[0], P.shape[1], P.stride(0), int(x["k"]), _kernel(x["kernel"]),
                            lab.data_ptr(), out.data_ptr())
     opt = _Options(PRECISION[precision], 1, 1 if check_convergence else 0, 1 if timing else 0, 0,
-                   1 if autotune else 0, (ctypes.c_int64 * 5)())
+                   1 if autotune else 0, 0, 0, (ctypes.c_int64 * 4)())
     objs = (ctypes.c_double * len(instances))()
     its = (ctypes.c_int32 * len(instances))()
     info = _FitInfo()

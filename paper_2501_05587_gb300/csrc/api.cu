@@ -53,6 +53,7 @@ struct DeviceInfo {
     int reduce_smem = 0;   // dynamic shared memory usable by the reduction kernel
     int recompute_smem = 0;
     int batched_smem = 0;
+    int sym_smem = 0;
     cudaMemPool_t pool = nullptr;
     bool ready = false;
 };
@@ -83,6 +84,7 @@ popcorn_status device_info(DeviceInfo** out) {
         POPCORN_CUDA(configure_kbuild_tc());
         POPCORN_CUDA(configure_recompute(d.smem_optin, &d.recompute_smem));
         POPCORN_CUDA(configure_batched(d.smem_optin));
+        POPCORN_CUDA(configure_reduce_sym(d.smem_optin, &d.sym_smem));
         d.batched_smem = d.smem_optin - 1024;
         d.ready = true;
     }
@@ -631,7 +633,9 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     if (max_iter < 0) return fail(POPCORN_ERR_INVALID, "max_iter = %d < 0", max_iter);
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
     if (opt.autotune != 0 && opt.autotune != 1) return fail(POPCORN_ERR_INVALID, "options.autotune must be 0 or 1");
-    for (int r = 0; r < 5; ++r)
+    if (opt.k_pass != 0 && opt.k_pass != 1) return fail(POPCORN_ERR_INVALID, "options.k_pass must be 0 or 1");
+    if (opt.reserved_pad != 0) return fail(POPCORN_ERR_INVALID, "options.reserved_pad must be 0");
+    for (int r = 0; r < 4; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
     if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)
         return fail(POPCORN_ERR_INVALID, "unknown k_storage %d", opt.k_storage);
@@ -653,6 +657,18 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     const int64_t ldk = ks == POPCORN_K_FP32 ? (n + 3) / 4 * 4 : (n + 7) / 8 * 8;   // 16-byte rows
     ReducePlan plan = plan_reduce(ni, k, dev->sms, dev->reduce_smem, ks);
     if (plan.grid == 0) return fail(POPCORN_ERR_UNSUPPORTED, "n = %d is too large for the materialized path", ni);
+    // symmetric pass (FP32 K, k_pass = 1): upper-triangle blocks, row and column sums
+    SymPlan sym{};
+    // (PSD kernels only: there |K_ij| <= max_i K_ii bounds its fixed-point column sums)
+    const bool psd = kp.kind != POPCORN_POLYNOMIAL || (kp.gamma >= 0.f && kp.coef0 >= 0.f);
+    if (ks == POPCORN_K_FP32 && opt.k_pass == 1 && psd) sym = plan_reduce_sym(ni, k, dev->sms, dev->sym_smem);
+    const bool use_sym = sym.ok;
+    const int nslots = use_sym ? sym.nseg + 1 : plan.nseg;
+    if (use_sym) {
+        plan.nseg = nslots;                 // the consumers read all slots from the row's segment on
+        plan.sym_seglen = sym.seglen;
+    }
+    const int zblocks = (ni + kZReduceRows - 1) / kZReduceRows;
     const bool timing = opt.timing != 0;
     int launches = 0;
     int64_t h2d = 0, d2h = 0;
@@ -694,8 +710,27 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     POPCORN_TRY(ws.alloc(&b.lab32, ni, "labels"));
     POPCORN_TRY(ws.alloc(&b.lab8, nlab, "label bytes"));
     POPCORN_TRY(ws.alloc(&b.counts, 2 * (size_t)k, "counts"));
-    POPCORN_TRY(ws.alloc(&b.Spart, (size_t)plan.nseg * ni * k, "segment sums"));
-    POPCORN_TRY(ws.alloc(&b.zpart, (size_t)plan.grid * k, "block partials"));
+    POPCORN_TRY(ws.alloc(&b.Spart, (size_t)nslots * ni * k, "segment sums"));
+    POPCORN_TRY(ws.alloc(&b.zpart, (size_t)(use_sym ? zblocks : plan.grid) * k, "block partials"));
+    unsigned long long* Cpart = nullptr;
+    int4* d_items = nullptr;
+    int* d_seg_item = nullptr;
+    if (use_sym) {
+        POPCORN_TRY(ws.alloc(&Cpart, sym.items.size() * (size_t)k * sym.seglen, "column partials"));
+        POPCORN_TRY(ws.alloc(&d_items, sym.items.size(), "pass items"));
+        POPCORN_TRY(ws.alloc(&d_seg_item, sym.seg_item.size(), "segment item ranges"));
+        POPCORN_CUDA(cudaMemcpyAsync(d_items, sym.items.data(), sym.items.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice, s));
+        POPCORN_CUDA(cudaMemcpyAsync(d_seg_item, sym.seg_item.data(), sym.seg_item.size() * sizeof(int),
+                                     cudaMemcpyHostToDevice, s));
+    }
+    // one pass's reduction: the K stream and, for the symmetric pass, the fold and z
+    auto reduce_pass = [&](int eval) -> cudaError_t {
+        if (!use_sym) return launch_reduce(b, plan, eval, s);
+        cudaError_t e = launch_reduce_sym(b, sym, d_items, d_seg_item, Cpart, eval, s);
+        if (e != cudaSuccess) return e;
+        return launch_zreduce(b, nslots, eval, s, sym.seglen);
+    };
     POPCORN_TRY(ws.alloc(&b.zsum, (size_t)k, "z sums"));
     POPCORN_TRY(ws.alloc(&b.cnorm, (size_t)k, "centroid norms"));
     POPCORN_TRY(ws.alloc(&b.invm, (size_t)k, "inverse cluster sizes"));
@@ -746,7 +781,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
                 POPCORN_TRY(g_events.get(&e2));
                 POPCORN_CUDA(cudaEventRecord(e0, s));
             }
-            POPCORN_CUDA(launch_reduce(b, plan, 0, s));
+            POPCORN_CUDA(reduce_pass(0));
             if (timing) POPCORN_CUDA(cudaEventRecord(e1, s));
             POPCORN_CUDA(launch_assign(b, plan, s));
             if (timing) {
@@ -776,7 +811,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         POPCORN_CUDA(cudaEventRecord(ev_l1, s));
     }
     // J(labels_out): reuses J of the last pass when it changed nothing
-    POPCORN_CUDA(launch_reduce(b, plan, 1, s));
+    POPCORN_CUDA(reduce_pass(1));
     launches += 1;
     if (timing) {
         POPCORN_TRY(g_events.get(&ev_e1));
@@ -852,7 +887,9 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
     if (max_iter < 0) return fail(POPCORN_ERR_INVALID, "max_iter = %d < 0", max_iter);
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
     if (opt.autotune != 0 && opt.autotune != 1) return fail(POPCORN_ERR_INVALID, "options.autotune must be 0 or 1");
-    for (int r = 0; r < 5; ++r)
+    if (opt.k_pass != 0 && opt.k_pass != 1) return fail(POPCORN_ERR_INVALID, "options.k_pass must be 0 or 1");
+    if (opt.reserved_pad != 0) return fail(POPCORN_ERR_INVALID, "options.reserved_pad must be 0");
+    for (int r = 0; r < 4; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
     if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)
         return fail(POPCORN_ERR_INVALID, "unknown k_storage %d", opt.k_storage);

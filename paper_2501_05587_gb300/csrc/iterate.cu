@@ -15,6 +15,7 @@
 // V is never built: a label byte per column is all the K-stream needs.  E and
 // D are never stored (E only on request for tests).
 #include "popcorn_internal.cuh"
+#include "stream_common.cuh"
 
 #include <cuda/std/limits>
 #include <cuda_bf16.h>
@@ -23,13 +24,7 @@
 namespace popcorn {
 namespace {
 
-__device__ __forceinline__ float4 ld_stream(const float4* p) {
-    float4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
-    return v;
-}
+using namespace stream;
 
 // 16 bytes of a K row: 4 FP32 or 8 FP16 / BF16 elements, and their labels.
 template <typename TK> struct KVec;
@@ -74,15 +69,6 @@ __device__ __forceinline__ float kval(float v) { return v; }
 __device__ __forceinline__ float kval(__half v) { return __half2float(v); }
 __device__ __forceinline__ float kval(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// hi + lo += x without rounding loss (Knuth's TwoSum; FP32 pipe only).
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
-    const float s = hi + x;
-    const float bb = s - hi;
-    const float e = (hi - (s - bb)) + (x - bb);
-    hi = s;
-    lo += e;
-}
-
 template <int UNR, bool LAB_SMEM, typename LabT = uint32_t>
 __device__ __forceinline__ void load_batch(const float4* row4, const LabT* lab4, int q, int q1,
                                            float4 (&v)[UNR], LabT (&L)[UNR]) {
@@ -97,40 +83,6 @@ __device__ __forceinline__ void load_batch(const float4* row4, const LabT* lab4,
             L[t] = LabT{};
         }
     }
-}
-
-// Cluster whose warp total lane `lane` holds after butterfly<KB>.
-template <int KB>
-__device__ __forceinline__ int bfly_cluster(int lane) {
-    int c = 0;
-#pragma unroll
-    for (int w = KB >> 1, off = 16; w >= 1; w >>= 1, off >>= 1)
-        if (lane & off) c += w;
-    return c;
-}
-
-// Reduce-scatter of KB per-lane partials over the warp: each level halves
-// the values a lane carries (one half goes to the partner, the other half is
-// kept), then the remaining levels all-reduce the single value left.
-template <int KB>
-__device__ __forceinline__ float butterfly(const float (&acc)[KB], int lane) {
-    float v[KB];
-#pragma unroll
-    for (int t = 0; t < KB; ++t) v[t] = acc[t];
-    int off = 16;
-#pragma unroll
-    for (int cnt = KB; cnt > 1; cnt >>= 1, off >>= 1) {
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int t = 0; t < cnt / 2; ++t) {
-            const float send = up ? v[t] : v[t + cnt / 2];
-            const float keep = up ? v[t + cnt / 2] : v[t];
-            v[t] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-        }
-    }
-#pragma unroll
-    for (; off > 0; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
-    return v[0];
 }
 
 // Last block of a pass's reduction, all its threads: sum the per-block FP64
@@ -351,6 +303,7 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceA
 
 struct AssignArgs {
     int n, k, nseg;
+    int sym_seglen;           // > 0: symmetric pass -- row i's slots start at its block's segment
     const float* Spart;
     const float* kdiag;
     const double* cnorm;
@@ -386,11 +339,12 @@ __device__ __forceinline__ void assign_body(const AssignArgs& a, int block, int 
         int bi = li;
         const float* Si = a.Spart + i;               // [s][c][i]: consecutive threads, consecutive rows
         const size_t cs = (size_t)n, ss = (size_t)k * n;
+        const int s0 = a.sym_seglen ? ((i >> 7) << 7) / a.sym_seglen : 0;
         for (int c = 0; c < k; ++c) {
             const int mc = m[c];
             float hi = 0.f, lo = 0.f;
 #pragma unroll 8
-            for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[s * ss + c * cs]);
+            for (int s = s0; s < a.nseg; ++s) ff_add(hi, lo, Si[s * ss + c * cs]);
             const double E = ((double)hi + (double)lo) * a.invm[c];   // (K V^T)_ic
             if (a.E_out) a.E_out[(int64_t)i * k + c] = (float)E;
             if (mc == 0) continue;
@@ -452,6 +406,7 @@ __global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) { 
 // order (deterministic), then the last block finalizes the pass.
 struct ZArgs {
     int n, k, nseg;
+    int sym_seglen;           // > 0: symmetric pass (see AssignArgs)
     const float* Spart;
     const uint8_t* lab8;
     double* zpart;
@@ -480,7 +435,8 @@ __device__ __forceinline__ void zreduce_body(const ZArgs& a, int block, int nblo
         l = a.lab8[i];
         const float* Si = a.Spart + (size_t)l * a.n + i;
         float hi = 0.f, lo = 0.f;
-        for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[(size_t)s * a.k * a.n]);
+        const int s0 = a.sym_seglen ? ((i >> 7) << 7) / a.sym_seglen : 0;
+        for (int s = s0; s < a.nseg; ++s) ff_add(hi, lo, Si[(size_t)s * a.k * a.n]);
         v = (double)hi + (double)lo;
     }
     lab_s[threadIdx.x] = l;
@@ -529,15 +485,27 @@ __global__ void init_state_kernel(LoopState* st, int max_iter, int check_conv, d
 // sum of diag(K) in FP64; one block, fixed reduction order
 __device__ __forceinline__ void trace_body(const float* __restrict__ kdiag, int n, LoopState* st) {
     __shared__ double part[1024];
+    __shared__ float pmax[1024];
     double t = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) t += (double)kdiag[i];
+    float mx = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        t += (double)kdiag[i];
+        mx = fmaxf(mx, fabsf(kdiag[i]));
+    }
     part[threadIdx.x] = t;
+    pmax[threadIdx.x] = mx;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        if (threadIdx.x < o) {
+            part[threadIdx.x] += part[threadIdx.x + o];
+            pmax[threadIdx.x] = fmaxf(pmax[threadIdx.x], pmax[threadIdx.x + o]);
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) st->trace = part[0];
+    if (threadIdx.x == 0) {
+        st->trace = part[0];
+        st->kdiag_max = pmax[0];
+    }
 }
 
 __global__ void __launch_bounds__(1024) trace_kernel(const float* __restrict__ kdiag, int n, LoopState* st) {
@@ -670,11 +638,12 @@ cudaError_t launch_reduce(const PassBuffers& b, const ReducePlan& plan, int eval
     return cudaGetLastError();
 }
 
-cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_t s) {
+cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_t s, int sym_seglen) {
     ZArgs a;
     a.n = b.n;
     a.k = b.k;
     a.nseg = nseg;
+    a.sym_seglen = sym_seglen;
     a.Spart = b.Spart;
     a.lab8 = b.lab8;
     a.zpart = b.zpart;
@@ -689,9 +658,10 @@ cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s) {
+cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s, int sym_seglen) {
     ReducePlan p{};
     p.nseg = nseg;
+    p.sym_seglen = sym_seglen;
     return launch_assign(b, p, s);
 }
 
@@ -700,6 +670,7 @@ cudaError_t launch_assign(const PassBuffers& b, const ReducePlan& plan, cudaStre
     a.n = b.n;
     a.k = b.k;
     a.nseg = plan.nseg;
+    a.sym_seglen = plan.sym_seglen;
     a.Spart = b.Spart;
     a.kdiag = b.kdiag;
     a.cnorm = b.cnorm;
@@ -788,6 +759,7 @@ __global__ void __launch_bounds__(kZReduceRows) batched_zreduce_kernel(const Bat
     a.n = b.n;
     a.k = b.k;
     a.nseg = b.nseg;
+    a.sym_seglen = 0;
     a.Spart = b.Spart;
     a.lab8 = b.lab8;
     a.zpart = b.zpart;
@@ -808,6 +780,7 @@ __global__ void __launch_bounds__(kAssignThreads) batched_assign_kernel(const Ba
     a.n = b.n;
     a.k = b.k;
     a.nseg = b.nseg;
+    a.sym_seglen = 0;
     a.Spart = b.Spart;
     a.kdiag = b.kdiag;
     a.cnorm = b.cnorm;

@@ -1,6 +1,8 @@
 // Internal declarations of the CUDA path (not part of the public ABI).
 #pragma once
 
+#include <vector>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -42,6 +44,7 @@ struct LoopState {
     double J_last;         // J(labels before the last pass)
     double J_prev;         // J(labels before the pass before)
     double J_eval;         // J(final labels)
+    double kdiag_max;      // max_i |K_ii|: bounds every |K_ij| of a PSD kernel (symmetric pass)
 };
 
 // Variants of the K-streaming reduction, by how a warp reduces its per-lane
@@ -59,7 +62,27 @@ struct ReducePlan {
     int seglen;      // columns per segment (multiple of 128)
     size_t smem;     // dynamic shared memory per block
     bool labels_in_smem;
+    int sym_seglen;  // consumers of a symmetric pass: segment length (0 = full-square pass)
 };
+
+// Symmetric K stream (reduce_sym.cu): upper-triangle blocks only, row sums
+// plus column sums; items = (column segment, run of 128-row blocks).
+struct SymPlan {
+    bool ok;
+    int warps, grid;
+    int seglen, nseg;        // Spart has nseg + 1 slots (the last: folded column sums)
+    int fbits;               // fractional bits of the fixed-point column sums
+    size_t smem;
+    bool labels_in_smem;
+    std::vector<int4> items;     // {segment, first row block, end row block, 0}
+    std::vector<int> seg_item;   // items of segment s: [seg_item[s], seg_item[s + 1])
+};
+SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_budget);
+cudaError_t configure_reduce_sym(int smem_optin, int* usable);
+// reduce_sym_kernel then sym_fold_kernel; Cpart: items x k x seglen 64-bit fixed-point words.
+// Valid for PSD kernels only (|K_ij| <= max_i K_ii bounds the fixed-point range).
+cudaError_t launch_reduce_sym(const struct PassBuffers& b, const SymPlan& p, const int4* d_items,
+                              const int* d_seg_item, unsigned long long* Cpart, int eval_only, cudaStream_t s);
 
 // Sets the message popcorn_last_error_message() returns on this thread (api.cu).
 void set_error_message(const char* msg);
@@ -184,13 +207,13 @@ cudaError_t launch_recompute_pass(const PassBuffers& b, KernParams kp, const Rec
 // sum_{i in L_c} S_ic from b.Spart (nseg segments) and the pass finalization
 // (||c||^2, 1/|L_c|, J); blocks of kZReduceRows rows.
 constexpr int kZReduceRows = 1024;
-cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_t s);
+cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_t s, int sym_seglen = 0);
 
 // One assignment pass = reduction (E, z, J) + distance/argmin.
 cudaError_t launch_reduce(const PassBuffers& b, const ReducePlan& plan, int eval_only,
                           cudaStream_t s);
 cudaError_t launch_assign(const PassBuffers& b, const ReducePlan& plan, cudaStream_t s);
-cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s);
+cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s, int sym_seglen = 0);
 
 // ---- batched mode (iterate.cu, kbuild_simt.cu) --------------------------------
 // One clustering instance of a batch, device-resident.  Flattened work of all

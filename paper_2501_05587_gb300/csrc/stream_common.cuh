@@ -1,0 +1,62 @@
+// Building blocks of the K-streaming reductions (iterate.cu, reduce_sym.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace popcorn {
+namespace stream {
+
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// hi + lo += x without rounding loss (Knuth's TwoSum; FP32 pipe only).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += e;
+}
+
+// Cluster whose warp total lane `lane` holds after butterfly<KB>.
+template <int KB>
+__device__ __forceinline__ int bfly_cluster(int lane) {
+    int c = 0;
+#pragma unroll
+    for (int w = KB >> 1, off = 16; w >= 1; w >>= 1, off >>= 1)
+        if (lane & off) c += w;
+    return c;
+}
+
+// Reduce-scatter of KB per-lane partials over the warp: each level halves
+// the values a lane carries (one half goes to the partner, the other half is
+// kept), then the remaining levels all-reduce the single value left.
+template <int KB>
+__device__ __forceinline__ float butterfly(const float (&acc)[KB], int lane) {
+    float v[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) v[t] = acc[t];
+    int off = 16;
+#pragma unroll
+    for (int cnt = KB; cnt > 1; cnt >>= 1, off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int t = 0; t < cnt / 2; ++t) {
+            const float send = up ? v[t] : v[t + cnt / 2];
+            const float keep = up ? v[t + cnt / 2] : v[t];
+            v[t] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+#pragma unroll
+    for (; off > 0; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+    return v[0];
+}
+
+}  // namespace stream
+}  // namespace popcorn

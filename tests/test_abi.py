@@ -80,18 +80,22 @@ def test_invalid_arguments_rejected_before_any_cuda_call(pc):
     assert fit(kern=pc._Kernel(2, 1, 1.0, 0.0, 0.0)) == 1        # sigma = 0
     assert fit(kern=pc._Kernel(1, 0, 1.0, 1.0, 1.0)) == 1        # degree 0
     assert fit(kern=pc._Kernel(7, 1, 1.0, 1.0, 1.0)) == 1        # unknown kind
-    bad = pc._Options(0, 1, 1, 0, 0, 0, (ctypes.c_int64 * 5)(1, 0, 0, 0, 0))
+    bad = pc._Options(0, 1, 1, 0, 0, 0, 0, 0, (ctypes.c_int64 * 4)(1, 0, 0, 0))
     assert fit(opt=ctypes.byref(bad)) == 1                       # reserved must be zero
-    bad32 = pc._Options(0, 1, 1, 0, 0, 3, (ctypes.c_int64 * 5)())
+    bad32 = pc._Options(0, 1, 1, 0, 0, 3, 0, 0, (ctypes.c_int64 * 4)())
     assert fit(opt=ctypes.byref(bad32)) == 1                     # autotune must be 0 or 1
-    badks = pc._Options(0, 1, 1, 0, 7, 0, (ctypes.c_int64 * 5)())
+    badks = pc._Options(0, 1, 1, 0, 7, 0, 0, 0, (ctypes.c_int64 * 4)())
     assert fit(opt=ctypes.byref(badks)) == 1                     # unknown K storage type
-    rec = pc._Options(0, 0, 1, 0, 0, 0, (ctypes.c_int64 * 5)())
+    rec = pc._Options(0, 0, 1, 0, 0, 0, 0, 0, (ctypes.c_int64 * 4)())
     assert fit(opt=ctypes.byref(rec)) == 5                       # recompute path needs BF16 or FP8
-    fp8k = pc._Options(3, 1, 1, 0, 0, 0, (ctypes.c_int64 * 5)())
+    fp8k = pc._Options(3, 1, 1, 0, 0, 0, 0, 0, (ctypes.c_int64 * 4)())
     assert fit(opt=ctypes.byref(fp8k)) == 5                      # FP8 only without a stored K
-    badk = pc._Options(0, 2, 1, 0, 0, 0, (ctypes.c_int64 * 5)())
+    badk = pc._Options(0, 2, 1, 0, 0, 0, 0, 0, (ctypes.c_int64 * 4)())
     assert fit(opt=ctypes.byref(badk)) == 1                      # store_k must be 0 or 1
+    badp = pc._Options(0, 1, 1, 0, 0, 0, 2, 0, (ctypes.c_int64 * 4)())
+    assert fit(opt=ctypes.byref(badp)) == 1                      # k_pass must be 0 (full) or 1 (symmetric)
+    badpad = pc._Options(0, 1, 1, 0, 0, 0, 0, 5, (ctypes.c_int64 * 4)())
+    assert fit(opt=ctypes.byref(badpad)) == 1                    # padding must be zero
     # kernel matrix: ldk must be a multiple of 4 and >= n
     st = lib.popcorn_kernel_matrix(P.ctypes.data, 10, 2, 2, kern, 0, out.ctypes.data, 10, out.ctypes.data, None)
     assert st == 1
