@@ -71,6 +71,9 @@ def parse():
                     help="time candidate schedules in the warm-up (batched and recompute paths)")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3", "fp8"],
                     help="K-build precision (default: the workload's)")
+    ap.add_argument("--compare", default=None, choices=["paper"],
+                    help="paper: also time the paper's formulation through library calls (cuBLAS GEMM + "
+                         "elementwise kernel function, cuSPARSE SpMM/SpMV per pass) on the same inputs")
     return ap.parse_args()
 
 
@@ -326,8 +329,124 @@ def run_batched(args):
     return 0
 
 
+def run_paper_pipeline(args):
+    """The paper's formulation on the same GPU, through library calls only (a comparator:
+    none of this is on the library's path).
+
+    K build (Sec. 3.2, Alg. 2 lines 1-2): B = P P^T by a cuBLAS GEMM (torch.matmul; FP32 with
+    TF32 off, or BF16 operands for --precision bf16), then the kernel function as elementwise
+    passes.  Each pass (Alg. 2 lines 7-14): V (k x n, CSR, V_cj = 1/|L_c|) times K by a
+    cuSPARSE SpMM, the gather e_i = (V K)_{cl(i), i}, z = V e by a cuSPARSE SpMV (Eq. 14),
+    D = diag(K) - 2 (V K)^T + z, the row argmin and the new counts.  Same inputs and number of
+    passes as one popcorn_fit of the same workload; one JSON line with both."""
+    import torch
+
+    import synth
+    import paper_2501_05587_gb300 as pc
+
+    torch.backends.cuda.matmul.allow_tf32 = False
+    wl = synth.workload(args.workload, scale=args.scale)
+    prec = args.precision or wl.precision
+    if prec not in ("fp32", "bf16") or not wl.store_k:
+        print(json.dumps({"compare": "paper", "unavailable": "the comparator covers stored-K FP32/BF16 fits"}))
+        return 0
+    P = torch.from_numpy(wl.P).cuda()
+    lab0 = torch.from_numpy(wl.init_labels).cuda()
+    n, k = wl.n, wl.k
+    kern = wl.kernel
+    # ours first: the pass count the paper pipeline then runs
+    ours = pc.popcorn_fit(P, k, kern, lab0, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
+                          precision=prec, timing=True)
+    passes = int(ours["iterations"])
+    for _ in range(max(args.warmup - 1, 0)):
+        pc.popcorn_fit(P, k, kern, lab0, max_iter=passes, check_convergence=False, precision=prec, timing=True)
+    torch.cuda.synchronize()
+    o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    o0.record()
+    ours = pc.popcorn_fit(P, k, kern, lab0, max_iter=passes, check_convergence=False, precision=prec, timing=True)
+    o1.record()
+    torch.cuda.synchronize()
+    ours_ms = o0.elapsed_time(o1)
+
+    def kbuild():
+        if prec == "bf16":
+            Pb = P.to(torch.bfloat16)
+            K = (Pb @ Pb.T).float()
+            r = (Pb.float() * Pb.float()).sum(1)
+        else:
+            K = P @ P.T
+            r = (P * P).sum(1)
+        if kern["kind"] == "gaussian":
+            K.mul_(-2.0).add_(r[:, None]).add_(r[None, :]).clamp_min_(0.0)
+            K.mul_(-kern["gamma"] / (kern["sigma"] ** 2)).exp_()
+            K.fill_diagonal_(1.0)
+        elif kern["kind"] == "polynomial":
+            K.mul_(kern["gamma"]).add_(kern["coef0"]).pow_(kern["degree"])
+        return K
+
+    ar = torch.arange(n, device="cuda")
+
+    def one_pass(K, kd, labels):
+        counts = torch.bincount(labels, minlength=k)
+        inv = torch.where(counts > 0, 1.0 / counts.clamp_min(1).float(), torch.zeros_like(counts, dtype=torch.float32))
+        order = torch.argsort(labels, stable=True)
+        crow = torch.zeros(k + 1, dtype=torch.int64, device="cuda")
+        crow[1:] = torch.cumsum(counts, 0)
+        V = torch.sparse_csr_tensor(crow, order, inv[labels[order]], size=(k, n))
+        VK = torch.sparse.mm(V, K)                             # SpMM: (K V^T)^T
+        e = VK[labels, ar]                                      # gather
+        z = torch.sparse.mm(V, e[:, None]).squeeze(1)           # SpMV: z_c = ||c_c||^2
+        D = kd[:, None] - 2.0 * VK.T + z[None, :]
+        D[:, counts == 0] = float("inf")
+        return D.argmin(1), D
+
+    def fit():
+        K = kbuild()
+        kd = torch.diagonal(K).clone()
+        labels = lab0.long()
+        for _ in range(passes):
+            labels, D = one_pass(K, kd, labels)
+        return K, kd, labels
+
+    for _ in range(args.warmup):
+        fit()
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    K = kbuild()
+    e1.record()
+    kd = torch.diagonal(K).clone()
+    labels = lab0.long()
+    for _ in range(passes):
+        labels, D = one_pass(K, kd, labels)
+    e2.record()
+    torch.cuda.synchronize()
+    kb_ms, loop_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    # objective of the final labels, as Alg. 2 defines it: sum_i D_{i, cl(i)} with the last centroids
+    _, D = one_pass(K, kd, labels)
+    J_paper = float(D[ar, labels].double().sum())
+    same = float((labels.int() == ours["labels"]).float().mean())
+    line = {"compare": "paper", "workload": wl.name, "precision": prec, "n": n, "d": wl.d, "k": k,
+            "passes": passes,
+            "paper_pipeline": {"kbuild_ms": kb_ms, "loop_ms": loop_ms, "iters_per_s": passes / ((kb_ms + loop_ms) / 1e3),
+                               "per_pass_ms": loop_ms / passes,
+                               "kbuild_tflops_gemm": 2.0 * n * n * wl.d / (kb_ms / 1e3) / 1e12,
+                               "libraries": "cuBLAS GEMM (torch.matmul), cuSPARSE SpMM/SpMV (torch.sparse CSR)"},
+            "ours": {"kbuild_ms": ours["info"]["kbuild_ms"], "loop_ms": ours["info"]["loop_ms"],
+                     "iters_per_s": passes / (ours_ms / 1e3),
+                     "per_pass_ms": ours["info"]["loop_ms"] / passes},
+            "speedup_whole_fit": ((kb_ms + loop_ms) / ours_ms),
+            "speedup_per_pass": (loop_ms / passes) / (ours["info"]["loop_ms"] / passes),
+            "labels_equal_fraction": same,
+            "objective_ours": ours["objective"], "objective_paper_pipeline": J_paper}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.compare == "paper":
+        return run_paper_pipeline(args)
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
