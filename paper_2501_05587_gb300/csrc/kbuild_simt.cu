@@ -19,8 +19,8 @@ namespace popcorn {
 namespace {
 
 constexpr int TILE = 128;
-constexpr int KC = 8;           // depth of one shared-memory slice
-constexpr int LDS = TILE + 4;   // padded row: conflict-free transposed fill
+constexpr int KC = 16;          // depth of one shared-memory slice (double-buffered)
+constexpr int LDS = TILE + 4;   // padded row
 
 __device__ __forceinline__ void tri_coords(long long t, int T, int* bi, int* bj) {
     // t enumerates the upper triangle row by row: row b starts at off(b) = b*T - b*(b-1)/2.
@@ -83,17 +83,52 @@ template <> struct KStore<__nv_bfloat16> {
 };
 
 // One upper-triangle tile (number `tile`) of K: 256 threads, 8 x 8 outputs each.
+// The depth loop runs over KC-wide slices of the two 128-row operand blocks,
+// double-buffered in shared memory: while a slice is consumed, the next one is
+// already in flight into registers (float4 loads when rows are 16-byte aligned).
 // kdiag receives the stored (rounded) diagonal so that diag K and K agree.
+struct TileSmem {
+    float As[2][KC][LDS];
+    float Bs[2][KC][LDS];
+};
+
 template <int KIND, typename TK = float>
 __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, int d, int64_t ldp,
                                             const KernParams& kp, TK* __restrict__ K, int64_t ldk,
-                                            float* __restrict__ kdiag, int T, long long tile) {
-    __shared__ __align__(16) float As[KC][LDS];
-    __shared__ __align__(16) float Bs[KC][LDS];
+                                            float* __restrict__ kdiag, int T, long long tile, TileSmem& sm) {
+    auto& As = sm.As;
+    auto& Bs = sm.Bs;
     int bi, bj;
     tri_coords(tile, T, &bi, &bj);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int row0 = bi * TILE, col0 = bj * TILE;
+    const bool vec = (ldp & 3) == 0 && ((uintptr_t)P & 15) == 0;
+
+    // slice fill: thread tid carries float4 f = (tid >> 7) + 2 rep of row tid & 127, rep = 0, 1
+    const int fr = tid & 127;
+    auto fetch = [&](int base, int l0, int rep) -> float4 {
+        const int r = base + fr, gl = l0 + 4 * ((tid >> 7) + 2 * rep);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < n) {
+            const float* p = P + (int64_t)r * ldp + gl;
+            if (vec && gl + 3 < d) {
+                v = __ldg(reinterpret_cast<const float4*>(p));
+            } else {
+                if (gl < d) v.x = __ldg(p);
+                if (gl + 1 < d) v.y = __ldg(p + 1);
+                if (gl + 2 < d) v.z = __ldg(p + 2);
+                if (gl + 3 < d) v.w = __ldg(p + 3);
+            }
+        }
+        return v;
+    };
+    auto put = [&](float (*S)[LDS], int rep, const float4& v) {
+        const int l = 4 * ((tid >> 7) + 2 * rep);
+        S[l][fr] = v.x;
+        S[l + 1][fr] = v.y;
+        S[l + 2][fr] = v.z;
+        S[l + 3][fr] = v.w;
+    };
 
     float acc[8][8];
 #pragma unroll
@@ -101,26 +136,27 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
 #pragma unroll
         for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
 
+    float4 na0 = fetch(row0, 0, 0), na1 = fetch(row0, 0, 1), nb0 = fetch(col0, 0, 0), nb1 = fetch(col0, 0, 1);
+    put(As[0], 0, na0);
+    put(As[0], 1, na1);
+    put(Bs[0], 0, nb0);
+    put(Bs[0], 1, nb1);
+    __syncthreads();
+    int buf = 0;
     for (int l0 = 0; l0 < d; l0 += KC) {
-#pragma unroll
-        for (int e = tid; e < TILE * KC; e += 256) {
-            int r = e / KC, l = e % KC;
-            int gl = l0 + l;
-            float va = 0.f, vb = 0.f;
-            if (gl < d) {
-                if (row0 + r < n) va = __ldg(P + (int64_t)(row0 + r) * ldp + gl);
-                if (col0 + r < n) vb = __ldg(P + (int64_t)(col0 + r) * ldp + gl);
-            }
-            As[l][r] = va;
-            Bs[l][r] = vb;
+        const bool more = l0 + KC < d;
+        if (more) {
+            na0 = fetch(row0, l0 + KC, 0);
+            na1 = fetch(row0, l0 + KC, 1);
+            nb0 = fetch(col0, l0 + KC, 0);
+            nb1 = fetch(col0, l0 + KC, 1);
         }
-        __syncthreads();
 #pragma unroll
         for (int l = 0; l < KC; ++l) {
-            float4 a0 = *reinterpret_cast<const float4*>(&As[l][ty * 4]);
-            float4 a1 = *reinterpret_cast<const float4*>(&As[l][64 + ty * 4]);
-            float4 b0 = *reinterpret_cast<const float4*>(&Bs[l][tx * 4]);
-            float4 b1 = *reinterpret_cast<const float4*>(&Bs[l][64 + tx * 4]);
+            float4 a0 = *reinterpret_cast<const float4*>(&As[buf][l][ty * 4]);
+            float4 a1 = *reinterpret_cast<const float4*>(&As[buf][l][64 + ty * 4]);
+            float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][l][tx * 4]);
+            float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][l][64 + tx * 4]);
             float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -135,9 +171,16 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
                     }
                 }
         }
+        if (more) {
+            // the other buffer was last read before the previous barrier
+            put(As[buf ^ 1], 0, na0);
+            put(As[buf ^ 1], 1, na1);
+            put(Bs[buf ^ 1], 0, nb0);
+            put(Bs[buf ^ 1], 1, nb1);
+        }
         __syncthreads();
+        buf ^= 1;
     }
-
     // epilogue: kappa, diagonal, store tile and (off-diagonal tiles) its transpose
 #pragma unroll
     for (int x = 0; x < 8; ++x)
@@ -196,7 +239,8 @@ template <int KIND, typename TK>
 __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
                                                           KernParams kp, TK* __restrict__ K, int64_t ldk,
                                                           float* __restrict__ kdiag, int T) {
-    kbuild_tile<KIND, TK>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x);
+    __shared__ __align__(16) TileSmem sm;
+    kbuild_tile<KIND, TK>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm);
 }
 
 template <typename TK>
@@ -232,12 +276,15 @@ __global__ void __launch_bounds__(256) batched_kbuild_kernel(const BatchInst* I,
     }
     const BatchInst& x = I[lo];
     const long long t = b - x.tile0;
+    __shared__ __align__(16) TileSmem sm;   // one copy for the three kernel functions
     switch (x.kp.kind) {
-        case POPCORN_LINEAR: kbuild_tile<POPCORN_LINEAR>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t); break;
-        case POPCORN_POLYNOMIAL:
-            kbuild_tile<POPCORN_POLYNOMIAL>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t);
+        case POPCORN_LINEAR:
+            kbuild_tile<POPCORN_LINEAR>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t, sm);
             break;
-        default: kbuild_tile<POPCORN_GAUSSIAN>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t); break;
+        case POPCORN_POLYNOMIAL:
+            kbuild_tile<POPCORN_POLYNOMIAL>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t, sm);
+            break;
+        default: kbuild_tile<POPCORN_GAUSSIAN>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t, sm); break;
     }
 }
 
