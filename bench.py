@@ -71,6 +71,9 @@ def parse():
                     help="time candidate schedules in the warm-up (batched and recompute paths)")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3", "fp8"],
                     help="K-build precision (default: the workload's)")
+    ap.add_argument("--k-pass", default="full", choices=["full", "symmetric"],
+                    help="how a pass reads a stored FP32 K: the full square, or the blocks on and above the "
+                         "diagonal (row and column sums, then a fold)")
     ap.add_argument("--compare", default=None, choices=["paper"],
                     help="paper: also time the paper's formulation through library calls (cuBLAS GEMM + "
                          "elementwise kernel function, cuSPARSE SpMM/SpMV per pass) on the same inputs")
@@ -482,7 +485,7 @@ def main():
     def step(timing=True):
         return pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
                               precision=wl.precision, timing=timing, labels_out=out, store_k=wl.store_k,
-                              autotune=tune)
+                              autotune=tune, k_pass=args.k_pass)
 
     for _ in range(args.warmup):
         step()
@@ -517,7 +520,8 @@ def main():
     Oh = torch.empty(wl.n, dtype=torch.int32).pin_memory()
     def host_step():
         return pc.popcorn_fit(Ph, wl.k, wl.kernel, Lh, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
-                              precision=wl.precision, labels_out=Oh, store_k=wl.store_k, autotune=tune)
+                              precision=wl.precision, labels_out=Oh, store_k=wl.store_k, autotune=tune,
+                              k_pass=args.k_pass)
 
     for _ in range(args.warmup):
         host_step()
@@ -547,6 +551,20 @@ def main():
                 "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_red_ms}
         roof2 = None
+        if wl.store_k and args.k_pass == "symmetric" and wl.precision == "fp32" and k <= 8:
+            # stream (the blocks on and above the diagonal; slots written) + fold (slots read,
+            # slot 0 written): the CUDA events bracket both launches
+            T = (n + 127) // 128
+            tri = 0.0
+            for I in range(T):
+                rows = min(128, n - 128 * I)
+                tri += rows * (n - 128 * I)          # real elements of blocks (I, J >= I)
+            slots = 4.0 * T * k * n
+            alg_bytes = 4.0 * tri + 2.0 * slots + 4.0 * k * n + 2.0 * n   # K, slots out and in, slot 0, labels
+            achieved = alg_bytes / (avg_red_ms / 1e3) / 1e9 if avg_red_ms > 0 else 0.0
+            roof = {"kernel": "reduce_sym_kernel + sym_fold_kernel", "bound": "hbm", "achieved": achieved,
+                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                    "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_red_ms}
         if not wl.store_k:
             # recompute pass: tensor cores (2 n^2 d flops) and the exp2 unit (n^2 kernel values)
             roof, roof2 = recompute_rooflines(wl, avg_red_ms, clk)

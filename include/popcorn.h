@@ -107,13 +107,13 @@ typedef struct {
                                    per SM).  Results differ only by summation order.        */
     int32_t k_pass;             /* how a pass reads a stored FP32 K: 0 = the full square, row
                                    by row (the paper's read of K; the default); 1 = only the
-                                   128-blocks on and above the diagonal, each element feeding
-                                   its row's and (by symmetry) its column's cluster sums: half
-                                   the bytes, but slower on GB300 so far (shared-memory atomics
-                                   for the column sums).  1 needs a PSD kernel (Gaussian,
-                                   linear, polynomial with gamma, coef0 >= 0); other kernels,
-                                   FP16/BF16 K and the recompute path read as 0 / their own
-                                   scheme                                                   */
+                                   128 x 128 blocks on and above the diagonal (K is symmetric):
+                                   a block's row sums serve its rows and its column sums its
+                                   columns' rows, written to one slot per block and folded, so
+                                   a pass reads half of K plus 8 k n ceil(n / 128) bytes of
+                                   slots.  1 needs k <= 8; larger k, FP16/BF16 K and the
+                                   recompute path read as 0 / their own scheme.  Results
+                                   differ from 0 only by summation order                    */
     int32_t reserved_pad;       /* must be zero                                              */
     int64_t reserved[4];        /* must be zero                                              */
 } popcorn_options;

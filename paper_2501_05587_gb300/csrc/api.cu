@@ -53,7 +53,6 @@ struct DeviceInfo {
     int reduce_smem = 0;   // dynamic shared memory usable by the reduction kernel
     int recompute_smem = 0;
     int batched_smem = 0;
-    int sym_smem = 0;
     cudaMemPool_t pool = nullptr;
     bool ready = false;
 };
@@ -84,7 +83,7 @@ popcorn_status device_info(DeviceInfo** out) {
         POPCORN_CUDA(configure_kbuild_tc());
         POPCORN_CUDA(configure_recompute(d.smem_optin, &d.recompute_smem));
         POPCORN_CUDA(configure_batched(d.smem_optin));
-        POPCORN_CUDA(configure_reduce_sym(d.smem_optin, &d.sym_smem));
+        POPCORN_CUDA(configure_reduce_sym(d.smem_optin));
         d.batched_smem = d.smem_optin - 1024;
         d.ready = true;
     }
@@ -355,7 +354,7 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
                 float ms = 3.0e38f;
                 for (int rep = 0; rep < 3; ++rep) {
                     POPCORN_CUDA(cudaEventRecord(t0, s));
-                    cudaError_t e = launch_recompute_pass(b, kp, c, rb, &b.st->kbuild_err, 0, s);
+                    cudaError_t e = launch_recompute_pass(b, kp, c, rb, &b.st->wait_err, 0, s);
                     if (e == cudaErrorInvalidValue) return fail(POPCORN_ERR_CUDA, "tensor map creation failed");
                     POPCORN_CUDA(e);
                     POPCORN_CUDA(cudaEventRecord(t1, s));
@@ -403,7 +402,7 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
                 POPCORN_TRY(g_events.get(&e2));
                 POPCORN_CUDA(cudaEventRecord(e0, s));
             }
-            cudaError_t e = launch_recompute_pass(b, kp, rp, rb, &b.st->kbuild_err, 0, s);
+            cudaError_t e = launch_recompute_pass(b, kp, rp, rb, &b.st->wait_err, 0, s);
             if (e == cudaErrorInvalidValue) return fail(POPCORN_ERR_CUDA, "tensor map creation failed");
             POPCORN_CUDA(e);
             POPCORN_CUDA(launch_zreduce(b, rp.nslot, 0, s));
@@ -435,7 +434,7 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
         POPCORN_CUDA(cudaEventRecord(ev_l1, s));
     }
     {
-        cudaError_t e = launch_recompute_pass(b, kp, rp, rb, &b.st->kbuild_err, 1, s);
+        cudaError_t e = launch_recompute_pass(b, kp, rp, rb, &b.st->wait_err, 1, s);
         if (e == cudaErrorInvalidValue) return fail(POPCORN_ERR_CUDA, "tensor map creation failed");
         POPCORN_CUDA(e);
         POPCORN_CUDA(launch_zreduce(b, rp.nslot, 1, s));
@@ -458,7 +457,7 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
     LoopState hs;
     memcpy(&hs, hs_pin, sizeof hs);
     if (hs.bad_label) return fail(POPCORN_ERR_INVALID, "an initial label is outside [0, %d)", k);
-    if (hs.kbuild_err) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the recompute kernel ran out");
+    if (hs.wait_err) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the recompute kernel ran out");
     *objective_out = hs.J_eval;
     *iterations_out = hs.iter;
     if (info) {
@@ -657,18 +656,13 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     const int64_t ldk = ks == POPCORN_K_FP32 ? (n + 3) / 4 * 4 : (n + 7) / 8 * 8;   // 16-byte rows
     ReducePlan plan = plan_reduce(ni, k, dev->sms, dev->reduce_smem, ks);
     if (plan.grid == 0) return fail(POPCORN_ERR_UNSUPPORTED, "n = %d is too large for the materialized path", ni);
-    // symmetric pass (FP32 K, k_pass = 1): upper-triangle blocks, row and column sums
+    // symmetric pass (FP32 K, k <= kSymMaxK, k_pass = 1): the blocks on and above the
+    // diagonal, row and column sums into T slots, folded into slot 0
     SymPlan sym{};
-    // (PSD kernels only: there |K_ij| <= max_i K_ii bounds its fixed-point column sums)
-    const bool psd = kp.kind != POPCORN_POLYNOMIAL || (kp.gamma >= 0.f && kp.coef0 >= 0.f);
-    if (ks == POPCORN_K_FP32 && opt.k_pass == 1 && psd) sym = plan_reduce_sym(ni, k, dev->sms, dev->sym_smem);
+    if (ks == POPCORN_K_FP32 && opt.k_pass == 1) sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin);
     const bool use_sym = sym.ok;
-    const int nslots = use_sym ? sym.nseg + 1 : plan.nseg;
-    if (use_sym) {
-        plan.nseg = nslots;                 // the consumers read all slots from the row's segment on
-        plan.sym_seglen = sym.seglen;
-    }
-    const int zblocks = (ni + kZReduceRows - 1) / kZReduceRows;
+    const int nslots = use_sym ? sym.T : plan.nseg;
+    if (use_sym) plan.nseg = 1;             // the assignment reads the folded slot only
     const bool timing = opt.timing != 0;
     int launches = 0;
     int64_t h2d = 0, d2h = 0;
@@ -711,25 +705,11 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     POPCORN_TRY(ws.alloc(&b.lab8, nlab, "label bytes"));
     POPCORN_TRY(ws.alloc(&b.counts, 2 * (size_t)k, "counts"));
     POPCORN_TRY(ws.alloc(&b.Spart, (size_t)nslots * ni * k, "segment sums"));
-    POPCORN_TRY(ws.alloc(&b.zpart, (size_t)(use_sym ? zblocks : plan.grid) * k, "block partials"));
-    unsigned long long* Cpart = nullptr;
-    int4* d_items = nullptr;
-    int* d_seg_item = nullptr;
-    if (use_sym) {
-        POPCORN_TRY(ws.alloc(&Cpart, sym.items.size() * (size_t)k * sym.seglen, "column partials"));
-        POPCORN_TRY(ws.alloc(&d_items, sym.items.size(), "pass items"));
-        POPCORN_TRY(ws.alloc(&d_seg_item, sym.seg_item.size(), "segment item ranges"));
-        POPCORN_CUDA(cudaMemcpyAsync(d_items, sym.items.data(), sym.items.size() * sizeof(int4),
-                                     cudaMemcpyHostToDevice, s));
-        POPCORN_CUDA(cudaMemcpyAsync(d_seg_item, sym.seg_item.data(), sym.seg_item.size() * sizeof(int),
-                                     cudaMemcpyHostToDevice, s));
-    }
-    // one pass's reduction: the K stream and, for the symmetric pass, the fold and z
+    POPCORN_TRY(ws.alloc(&b.zpart, (size_t)(use_sym ? sym.fold_blocks : plan.grid) * k, "block partials"));
+    // one pass's reduction: the K stream (for the symmetric pass: stream, then fold with z)
     auto reduce_pass = [&](int eval) -> cudaError_t {
         if (!use_sym) return launch_reduce(b, plan, eval, s);
-        cudaError_t e = launch_reduce_sym(b, sym, d_items, d_seg_item, Cpart, eval, s);
-        if (e != cudaSuccess) return e;
-        return launch_zreduce(b, nslots, eval, s, sym.seglen);
+        return launch_reduce_sym(b, sym, &b.st->wait_err, eval, s);
     };
     POPCORN_TRY(ws.alloc(&b.zsum, (size_t)k, "z sums"));
     POPCORN_TRY(ws.alloc(&b.cnorm, (size_t)k, "centroid norms"));
@@ -748,7 +728,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     }
     POPCORN_CUDA(cudaMemsetAsync(b.counts, 0, 2 * (size_t)k * sizeof(int32_t), s));
     POPCORN_CUDA(launch_init_state(b.st, max_iter, opt.check_convergence ? 1 : 0, tol, s));
-    POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, ks, kdiag, &ws, &b.st->kbuild_err,
+    POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, ks, kdiag, &ws, &b.st->wait_err,
                                     dev->sms, s, &launches));
     POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
     POPCORN_CUDA(launch_init_labels(Ld, ni, k, b.lab32, b.lab8, b.counts, b.st, s));
@@ -791,7 +771,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
                 ev_a.push_back(e1);
                 ev_a.push_back(e2);
             }
-            launches += 2;
+            launches += use_sym ? 3 : 2;
         }
         launched += m;
         if (opt.check_convergence && launched < max_iter) {
@@ -812,7 +792,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     }
     // J(labels_out): reuses J of the last pass when it changed nothing
     POPCORN_CUDA(reduce_pass(1));
-    launches += 1;
+    launches += use_sym ? 2 : 1;
     if (timing) {
         POPCORN_TRY(g_events.get(&ev_e1));
         POPCORN_CUDA(cudaEventRecord(ev_e1, s));
@@ -831,7 +811,8 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     LoopState hs;
     memcpy(&hs, hs_pin, sizeof hs);
     if (hs.bad_label) return fail(POPCORN_ERR_INVALID, "an initial label is outside [0, %d)", k);
-    if (hs.kbuild_err) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the tensor-core K build ran out");
+    if (hs.wait_err)
+        return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the tensor-core K build or the symmetric pass ran out");
     *objective_out = hs.J_eval;
     *iterations_out = hs.iter;
 
@@ -949,7 +930,7 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         b.init_labels = x.init_labels;
         b.labels_out = x.labels_out;
         b.unit0 = bp.units;
-        bp.units += n * b.nseg;
+        bp.units += batch_units(n, b.nseg);
         b.zblock0 = bp.zblocks;
         bp.zblocks += (n + kZReduceRows - 1) / kZReduceRows;
         b.ablock0 = bp.ablocks;
@@ -1013,7 +994,7 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
             h[t].seglen = seglen;
             h[t].nseg = (h[t].n + seglen - 1) / seglen;
             h[t].unit0 = bp.units;
-            bp.units += h[t].n * h[t].nseg;
+            bp.units += batch_units(h[t].n, h[t].nseg);
         }
     };
     int sched[3] = {kBatchSeg, 0, 0};

@@ -85,36 +85,6 @@ __device__ __forceinline__ void load_batch(const float4* row4, const LabT* lab4,
     }
 }
 
-// Last block of a pass's reduction, all its threads: sum the per-block FP64
-// partials of sum_{i in L_c} S_ic in block order, then ||c_c||^2 =
-// (1/m_c^2) sum_{i in L_c} S_ic (Eq. 13/14), 1/m_c, and
-// J = trace K - sum_c (1/m_c) sum_{i in L_c} S_ic.
-__device__ void finalize_pass(const double* zpart, int nblocks, int k, const int32_t* counts, double* zsum,
-                              double* cnorm, double* invm, LoopState* st, double* J_hist, int eval_only) {
-    const int32_t* m = counts + (size_t)(st->iter & 1) * k;
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        double t = 0.0;
-        for (int b = 0; b < nblocks; ++b) t += __ldcg(zpart + (size_t)b * k + c);
-        const double mc = (double)__ldcg(m + c);
-        const double inv = mc > 0 ? 1.0 / mc : 0.0;
-        zsum[c] = t;
-        invm[c] = inv;
-        cnorm[c] = t * inv * inv;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double J = st->trace;
-        for (int c = 0; c < k; ++c) J -= __ldcg(zsum + c) * __ldcg(invm + c);
-        if (eval_only) {
-            st->J_eval = J;
-        } else {
-            J_hist[st->iter] = J;
-            st->J_last = J;
-        }
-        st->reduce_ticket = 0u;
-    }
-}
-
 struct ReduceArgs {
     const void* K;        // TK elements, row pitch ldk elements (16-byte aligned rows)
     int64_t ldk;
@@ -303,7 +273,6 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceA
 
 struct AssignArgs {
     int n, k, nseg;
-    int sym_seglen;           // > 0: symmetric pass -- row i's slots start at its block's segment
     const float* Spart;
     const float* kdiag;
     const double* cnorm;
@@ -339,12 +308,11 @@ __device__ __forceinline__ void assign_body(const AssignArgs& a, int block, int 
         int bi = li;
         const float* Si = a.Spart + i;               // [s][c][i]: consecutive threads, consecutive rows
         const size_t cs = (size_t)n, ss = (size_t)k * n;
-        const int s0 = a.sym_seglen ? ((i >> 7) << 7) / a.sym_seglen : 0;
         for (int c = 0; c < k; ++c) {
             const int mc = m[c];
             float hi = 0.f, lo = 0.f;
 #pragma unroll 8
-            for (int s = s0; s < a.nseg; ++s) ff_add(hi, lo, Si[s * ss + c * cs]);
+            for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[s * ss + c * cs]);
             const double E = ((double)hi + (double)lo) * a.invm[c];   // (K V^T)_ic
             if (a.E_out) a.E_out[(int64_t)i * k + c] = (float)E;
             if (mc == 0) continue;
@@ -406,7 +374,6 @@ __global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) { 
 // order (deterministic), then the last block finalizes the pass.
 struct ZArgs {
     int n, k, nseg;
-    int sym_seglen;           // > 0: symmetric pass (see AssignArgs)
     const float* Spart;
     const uint8_t* lab8;
     double* zpart;
@@ -435,8 +402,7 @@ __device__ __forceinline__ void zreduce_body(const ZArgs& a, int block, int nblo
         l = a.lab8[i];
         const float* Si = a.Spart + (size_t)l * a.n + i;
         float hi = 0.f, lo = 0.f;
-        const int s0 = a.sym_seglen ? ((i >> 7) << 7) / a.sym_seglen : 0;
-        for (int s = s0; s < a.nseg; ++s) ff_add(hi, lo, Si[(size_t)s * a.k * a.n]);
+        for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[(size_t)s * a.k * a.n]);
         v = (double)hi + (double)lo;
     }
     lab_s[threadIdx.x] = l;
@@ -470,7 +436,7 @@ __device__ __forceinline__ void init_state_fn(LoopState* st, int max_iter, int c
     st->assign_ticket = 0u;
     st->changed_acc = 0u;
     st->bad_label = 0;
-    st->kbuild_err = 0;
+    st->wait_err = 0;
     st->tol = tol;
     st->trace = 0.0;
     st->J_last = 0.0;
@@ -485,27 +451,15 @@ __global__ void init_state_kernel(LoopState* st, int max_iter, int check_conv, d
 // sum of diag(K) in FP64; one block, fixed reduction order
 __device__ __forceinline__ void trace_body(const float* __restrict__ kdiag, int n, LoopState* st) {
     __shared__ double part[1024];
-    __shared__ float pmax[1024];
     double t = 0.0;
-    float mx = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        t += (double)kdiag[i];
-        mx = fmaxf(mx, fabsf(kdiag[i]));
-    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t += (double)kdiag[i];
     part[threadIdx.x] = t;
-    pmax[threadIdx.x] = mx;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            part[threadIdx.x] += part[threadIdx.x + o];
-            pmax[threadIdx.x] = fmaxf(pmax[threadIdx.x], pmax[threadIdx.x + o]);
-        }
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        st->trace = part[0];
-        st->kdiag_max = pmax[0];
-    }
+    if (threadIdx.x == 0) st->trace = part[0];
 }
 
 __global__ void __launch_bounds__(1024) trace_kernel(const float* __restrict__ kdiag, int n, LoopState* st) {
@@ -638,12 +592,11 @@ cudaError_t launch_reduce(const PassBuffers& b, const ReducePlan& plan, int eval
     return cudaGetLastError();
 }
 
-cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_t s, int sym_seglen) {
+cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_t s) {
     ZArgs a;
     a.n = b.n;
     a.k = b.k;
     a.nseg = nseg;
-    a.sym_seglen = sym_seglen;
     a.Spart = b.Spart;
     a.lab8 = b.lab8;
     a.zpart = b.zpart;
@@ -658,10 +611,9 @@ cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s, int sym_seglen) {
+cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s) {
     ReducePlan p{};
     p.nseg = nseg;
-    p.sym_seglen = sym_seglen;
     return launch_assign(b, p, s);
 }
 
@@ -670,7 +622,6 @@ cudaError_t launch_assign(const PassBuffers& b, const ReducePlan& plan, cudaStre
     a.n = b.n;
     a.k = b.k;
     a.nseg = plan.nseg;
-    a.sym_seglen = plan.sym_seglen;
     a.Spart = b.Spart;
     a.kdiag = b.kdiag;
     a.cnorm = b.cnorm;
@@ -759,7 +710,6 @@ __global__ void __launch_bounds__(kZReduceRows) batched_zreduce_kernel(const Bat
     a.n = b.n;
     a.k = b.k;
     a.nseg = b.nseg;
-    a.sym_seglen = 0;
     a.Spart = b.Spart;
     a.lab8 = b.lab8;
     a.zpart = b.zpart;
@@ -780,7 +730,6 @@ __global__ void __launch_bounds__(kAssignThreads) batched_assign_kernel(const Ba
     a.n = b.n;
     a.k = b.k;
     a.nseg = b.nseg;
-    a.sym_seglen = 0;
     a.Spart = b.Spart;
     a.kdiag = b.kdiag;
     a.cnorm = b.cnorm;

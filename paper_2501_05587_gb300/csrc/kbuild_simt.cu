@@ -22,22 +22,6 @@ constexpr int TILE = 128;
 constexpr int KC = 16;          // depth of one shared-memory slice (double-buffered)
 constexpr int LDS = TILE + 4;   // padded row
 
-__device__ __forceinline__ void tri_coords(long long t, int T, int* bi, int* bj) {
-    // t enumerates the upper triangle row by row: row b starts at off(b) = b*T - b*(b-1)/2.
-    // An FP32 estimate of the quadratic's root, then exact integer correction (no FP64:
-    // GB300 runs FP64 at a small fraction of the FP32 rate).
-    const float Tf = (float)T;
-    const float disc = fmaxf((2.f * Tf + 1.f) * (2.f * Tf + 1.f) - 8.f * (float)t, 0.f);
-    int b = (int)(((2.f * Tf + 1.f) - sqrtf(disc)) * 0.5f);
-    if (b < 0) b = 0;
-    if (b > T - 1) b = T - 1;
-    auto off = [&](long long r) { return r * (long long)T - r * (r - 1) / 2; };
-    while (b > 0 && off(b) > t) --b;
-    while (b < T - 1 && off(b + 1) <= t) ++b;
-    *bi = b;
-    *bj = b + (int)(t - off(b));
-}
-
 template <int KIND>
 __device__ __forceinline__ float apply_kernel(float v, const KernParams& kp) {
     if (KIND == POPCORN_LINEAR) return v;
@@ -92,7 +76,7 @@ struct TileSmem {
     float Bs[2][KC][LDS];
 };
 
-template <int KIND, typename TK = float>
+template <int KIND, typename TK = float, bool ONE_SLICE = false>
 __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, int d, int64_t ldp,
                                             const KernParams& kp, TK* __restrict__ K, int64_t ldk,
                                             float* __restrict__ kdiag, int T, long long tile, TileSmem& sm) {
@@ -144,7 +128,7 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
     __syncthreads();
     int buf = 0;
     for (int l0 = 0; l0 < d; l0 += KC) {
-        const bool more = l0 + KC < d;
+        const bool more = !ONE_SLICE && l0 + KC < d;
         if (more) {
             na0 = fetch(row0, l0 + KC, 0);
             na1 = fetch(row0, l0 + KC, 1);
@@ -243,6 +227,17 @@ __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restric
     kbuild_tile<KIND, TK>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm);
 }
 
+// d <= KC: the depth loop is one slice, so no next slice is held in registers;
+// the lighter kernel fits two blocks per SM, which overlaps one block's stores
+// with the other's loads (small d is store-bound)
+template <int KIND, typename TK>
+__global__ void __launch_bounds__(256, 2) kbuild_simt_small_kernel(const float* __restrict__ P, int n, int d,
+                                                                   int64_t ldp, KernParams kp, TK* __restrict__ K,
+                                                                   int64_t ldk, float* __restrict__ kdiag, int T) {
+    __shared__ __align__(16) TileSmem sm;
+    kbuild_tile<KIND, TK, true>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm);
+}
+
 template <typename TK>
 cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernParams kp, TK* K, int64_t ldk,
                               float* kdiag, cudaStream_t s) {
@@ -250,6 +245,22 @@ cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernPar
     const long long tiles = (long long)T * (T + 1) / 2;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     dim3 grid((unsigned)tiles), block(256);
+    if (d <= KC) {
+        switch (kp.kind) {
+            case POPCORN_LINEAR:
+                kbuild_simt_small_kernel<POPCORN_LINEAR, TK><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+                break;
+            case POPCORN_POLYNOMIAL:
+                kbuild_simt_small_kernel<POPCORN_POLYNOMIAL, TK>
+                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+                break;
+            default:
+                kbuild_simt_small_kernel<POPCORN_GAUSSIAN, TK>
+                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+                break;
+        }
+        return cudaGetLastError();
+    }
     switch (kp.kind) {
         case POPCORN_LINEAR:
             kbuild_simt_kernel<POPCORN_LINEAR, TK><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);

@@ -37,14 +37,13 @@ struct LoopState {
     uint32_t assign_ticket;
     uint32_t changed_acc;    // labels changed in the running pass
     int32_t bad_label;       // an input label was outside [0, k)
-    int32_t kbuild_err;      // the tensor-core K build timed out in a bounded wait
+    int32_t wait_err;      // a bounded wait ran out (tensor-core K build, recompute or symmetric stream)
     int32_t pad0;
     double tol;
     double trace;          // sum_i K_ii in FP64
     double J_last;         // J(labels before the last pass)
     double J_prev;         // J(labels before the pass before)
     double J_eval;         // J(final labels)
-    double kdiag_max;      // max_i |K_ii|: bounds every |K_ij| of a PSD kernel (symmetric pass)
 };
 
 // Variants of the K-streaming reduction, by how a warp reduces its per-lane
@@ -62,27 +61,44 @@ struct ReducePlan {
     int seglen;      // columns per segment (multiple of 128)
     size_t smem;     // dynamic shared memory per block
     bool labels_in_smem;
-    int sym_seglen;  // consumers of a symmetric pass: segment length (0 = full-square pass)
 };
 
-// Symmetric K stream (reduce_sym.cu): upper-triangle blocks only, row sums
-// plus column sums; items = (column segment, run of 128-row blocks).
+// Symmetric K stream (reduce_sym.cu): each 128 x 128 block on and above the
+// diagonal is read once.  Block (I, J) gives the row sums of block I (slot J)
+// and, off the diagonal, the column sums of block J (slot I), so Spart holds T
+// slots; the fold sums them into slot 0 (the assignment then reads slot 0
+// only) and forms z and J.  FP32 K, k <= kSymMaxK.
+constexpr int kSymMaxK = 8;
 struct SymPlan {
     bool ok;
-    int warps, grid;
-    int seglen, nseg;        // Spart has nseg + 1 slots (the last: folded column sums)
-    int fbits;               // fractional bits of the fixed-point column sums
+    int T;              // 128-blocks per side = Spart slots
+    long long items;    // blocks on and above the diagonal
+    int grid;           // persistent CTAs of the stream kernel
+    int fold_blocks;    // row chunks of the fold (zpart rows)
     size_t smem;
-    bool labels_in_smem;
-    std::vector<int4> items;     // {segment, first row block, end row block, 0}
-    std::vector<int> seg_item;   // items of segment s: [seg_item[s], seg_item[s + 1])
 };
-SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_budget);
-cudaError_t configure_reduce_sym(int smem_optin, int* usable);
-// reduce_sym_kernel then sym_fold_kernel; Cpart: items x k x seglen 64-bit fixed-point words.
-// Valid for PSD kernels only (|K_ij| <= max_i K_ii bounds the fixed-point range).
-cudaError_t launch_reduce_sym(const struct PassBuffers& b, const SymPlan& p, const int4* d_items,
-                              const int* d_seg_item, unsigned long long* Cpart, int eval_only, cudaStream_t s);
+SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin);
+cudaError_t configure_reduce_sym(int smem_optin);
+// err: set when a bounded wait of the stream kernel runs out.
+cudaError_t launch_reduce_sym(const struct PassBuffers& b, const SymPlan& p, int* err, int eval_only,
+                              cudaStream_t s);
+
+// Upper-triangle block (bi, bj), bi <= bj, of number t when the T x T block
+// triangle is enumerated row by row (row b starts at b T - b (b - 1) / 2).  An
+// FP32 estimate of the quadratic's root, then exact integer correction (no
+// FP64: GB300 runs FP64 at a small fraction of the FP32 rate).
+__device__ __forceinline__ void tri_coords(long long t, int T, int* bi, int* bj) {
+    const float Tf = (float)T;
+    const float disc = fmaxf((2.f * Tf + 1.f) * (2.f * Tf + 1.f) - 8.f * (float)t, 0.f);
+    int b = (int)(((2.f * Tf + 1.f) - sqrtf(disc)) * 0.5f);
+    if (b < 0) b = 0;
+    if (b > T - 1) b = T - 1;
+    auto off = [&](long long r) { return r * (long long)T - r * (r - 1) / 2; };
+    while (b > 0 && off(b) > t) --b;
+    while (b < T - 1 && off(b + 1) <= t) ++b;
+    *bi = b;
+    *bj = b + (int)(t - off(b));
+}
 
 // Sets the message popcorn_last_error_message() returns on this thread (api.cu).
 void set_error_message(const char* msg);
@@ -207,13 +223,13 @@ cudaError_t launch_recompute_pass(const PassBuffers& b, KernParams kp, const Rec
 // sum_{i in L_c} S_ic from b.Spart (nseg segments) and the pass finalization
 // (||c||^2, 1/|L_c|, J); blocks of kZReduceRows rows.
 constexpr int kZReduceRows = 1024;
-cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_t s, int sym_seglen = 0);
+cudaError_t launch_zreduce(const PassBuffers& b, int nseg, int eval, cudaStream_t s);
 
 // One assignment pass = reduction (E, z, J) + distance/argmin.
 cudaError_t launch_reduce(const PassBuffers& b, const ReducePlan& plan, int eval_only,
                           cudaStream_t s);
 cudaError_t launch_assign(const PassBuffers& b, const ReducePlan& plan, cudaStream_t s);
-cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s, int sym_seglen = 0);
+cudaError_t launch_assign_nseg(const PassBuffers& b, int nseg, cudaStream_t s);
 
 // ---- batched mode (iterate.cu, kbuild_simt.cu) --------------------------------
 // One clustering instance of a batch, device-resident.  Flattened work of all
@@ -257,6 +273,8 @@ struct BatchPlan {
 
 constexpr int kBatchLabelThreads = 256;
 constexpr int kBatchSeg = 8192;       // columns per K-stream unit in batched mode (whole rows for n <= 8192)
+// K-stream units of one instance in batched mode
+inline int batch_units(int n, int nseg) { return n * nseg; }
 
 // per instance: loop state, labels/counts, (after the K build) trace of K
 cudaError_t launch_batched_init(const BatchInst* dI, const BatchPlan& bp, int max_iter, int check_conv, double tol,

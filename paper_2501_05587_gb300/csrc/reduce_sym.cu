@@ -1,339 +1,412 @@
-// Symmetric K stream: one pass over the upper triangle of K.
+// Symmetric K stream: one pass over the 128 x 128 blocks of K on and above
+// the diagonal.
 //
-// K is symmetric (K = kappa(P P^T), Sec. 3.2), so S_ic = sum_{j in L_c} K_ij
-// (the paper's SpMM, Alg. 2 line 7) splits into the part with j in or after
-// row i's 128-column block, read along row i, and the part with j before it,
-// which equals the column sums sum_{j in L_c} K_ji over rows j of earlier
-// blocks.  Reading only the blocks on and above the diagonal gives both: every
-// element K_ij of an off-diagonal block is added to row i's sum of cluster
-// cl(j) AND to column j's sum of cluster cl(i).  The diagonal blocks are read
-// whole and feed row sums only.  That halves the bytes a pass reads.
+// K is symmetric (K = kappa(P P^T), Sec. 3.2).  The segment sums of the
+// paper's SpMM (Alg. 2 line 7), S_ic = sum_{j in L_c} K_ij, split by the
+// 128-column block J that holds j.  For J >= I (I: the block of row i) the
+// part is a row sum of block (I, J); for J < I it equals
+// sum_{j in L_c, j in J} K_ji, a column sum of block (J, I).  So one read of
+// every block (I, J), I <= J, gives all parts: its row sums go to slot J of
+// the rows of block I and, for I < J, its column sums to slot I of the rows of
+// block J.  A pass reads about half of K; every (slot, cluster, row) of Spart
+// is written exactly once.
 //
-// Work: column segments of L columns; an item is (segment s, a range of
-// 128-row blocks whose rows reach into s).  A CTA takes items in turn; its
-// warps take the item's rows.  Per row the warp streams float4s from the
-// start of the row's block (or the segment) to the segment end:
-//   * row sums in lane-private shared-memory columns acc[c][lane] (as in
-//     reduce_kernel), reduced at the row's end into Spart[s][c][i];
-//   * column sums (blocks after the row's own) into the CTA's colacc[c][j]
-//     with shared-memory atomic adds: cl(i) is the same for the whole row,
-//     so a lane's adds go to its own columns.  Warps add to the same columns
-//     in no fixed order, so the adds are 64-bit integer (fixed point, F
-//     fractional bits of max_i K_ii): integer sums do not depend on order,
-//     and for a PSD kernel |K_ij| <= max_i K_ii keeps n terms inside 63 bits.
-//     colacc is stored [c][e][q] (column c0 + 4 q + e): a warp's adds for one
-//     element e of its float4s hit 32 consecutive words.
-// At an item's end colacc goes to Cpart[item]; sym_fold_kernel then sums the
-// items of each segment into Spart[nseg][c][j] (fixed order).  The distance
-// and z kernels read, for row i, the segments from the one holding row i's
-// block on, plus slot nseg.
-#include <algorithm>
-#include <vector>
-
+// reduce_sym_kernel: persistent and warp-specialized, one CTA per SM, blocks
+//   taken in turn.  One producer thread TMA-loads each block (four 32-column
+//   boxes, 128-byte swizzle) and its 2 x 128 labels into a 3-deep ring.  The
+//   row group (4 warps, lane = row) reads a row as float4s, conflict-free
+//   under the swizzle, and multiplies each element into KB cluster sums with
+//   the one-hot weights of its column's label (the cluster bucketing of V
+//   written as FMAs: no data-dependent addressing, no atomics).  The column
+//   group (4 warps) takes the rows in steps of one: lane l holds columns
+//   4l..4l+3 and adds the row into KB sums per column with that row's weights;
+//   its 4 warps split the rows and their partials are added in warp order.
+//   Both groups write their sums straight to Spart.  Deterministic.
+// sym_fold_kernel: S_ic = the T slots summed in slot order (float-float),
+//   written to slot 0, the per-block FP64 partials of sum_{i in L_c} S_ic (z,
+//   Eq. 14), and in its last block the pass finalization (||c||^2, J).  The
+//   assignment then reads slot 0 alone.
 #include "popcorn_internal.cuh"
 #include "stream_common.cuh"
+#include "tc_common.cuh"
 
 namespace popcorn {
 namespace {
 
 using namespace stream;
 
+constexpr int kB = 128;                        // block edge
+constexpr int kBoxCols = 32;                   // TMA box: 32 floats (one 128-byte swizzle row) x 128 rows
+constexpr int kBoxBytes = kBoxCols * kB * 4;   // 16 KB
+constexpr int kTileBytes = 4 * kBoxBytes;      // 64 KB: one block
+constexpr int kGroup = 256;                    // threads of the row group and of the column group
+constexpr int kSymThreads = 2 * kGroup + 32;   // + the producer warp
+constexpr int kConsumerWarps = 2 * kGroup / 32;
+constexpr int kBarRows = 1, kBarCols = 2;      // named barriers of the two groups
+constexpr int kFoldThreads = 256;
+
+// Dynamic shared memory, in order: the block ring (1024-byte aligned for the
+// swizzle), the label ring (row labels, then column labels), the block
+// coordinates of each stage, the row group's one-hot weights (per 4-column
+// chunk and cluster, the chunk's 4 weights), the column group's (per row and
+// cluster, the weight twice), the two groups' partial sums, barriers and the
+// abort flag.  KB <= 4 keeps 3 blocks in flight, KB = 8 two.
+constexpr int align128(int x) { return (x + 127) & ~127; }
+
+template <int KB>
+struct SymLayout {
+    static constexpr int stages = KB <= 4 ? 3 : 2;
+    static constexpr int tiles = 0;
+    static constexpr int labels = tiles + stages * kTileBytes;
+    static constexpr int ij = align128(labels + stages * 2 * kB);
+    static constexpr int wt = align128(ij + stages * 8);
+    static constexpr int wd = align128(wt + kB * KB * 4);
+    static constexpr int rowpart = align128(wd + kB * KB * 8);
+    static constexpr int colpart = align128(rowpart + 4 * KB * kB * 4);
+    static constexpr int bars = align128(colpart + 8 * KB * kB * 4);
+    static constexpr int flag = bars + 2 * stages * 8;
+    static constexpr int bytes = flag + 16 + 1024;   // + slack for the 1024-byte alignment
+};
+
 struct SymArgs {
-    const float* K;           // FP32 rows, pitch ldk (multiple of 4)
     int64_t ldk;
-    int n, k, seglen, nseg;   // seglen: multiple of 128
-    const int4* items;        // {segment, first row block, end row block, 0}
-    int nitems;
+    int n, k, T, nlab;
+    long long items;
     const uint8_t* lab8;
-    float* Spart;             // [nseg + 1][k][n]
-    unsigned long long* Cpart;   // [nitems][k][4][seglen / 4], fixed point
-    int fbits;                // fractional bits: 61 - ceil(log2 n)
+    float* Spart;              // [T][k][n]
     const LoopState* st;
+    int* err;
     int eval_only;
 };
 
-// Fixed-point scale 2^F / max_i |K_ii| (capped so that a zero diagonal stays finite);
-// the K stream and the fold compute it the same way.
-__device__ __forceinline__ float fixed_scale(const LoopState* st, int fbits) {
-    return fminf(exp2f((float)fbits) / fmaxf((float)st->kdiag_max, 1e-30f), 0x1p100f);
+// 16 bytes at (row r, 16-byte chunk j) of a 32-column box under the 128-byte
+// swizzle (chunk j of row r sits at chunk j ^ (r mod 8)); xr = r mod 8
+__device__ __forceinline__ ulonglong2 box_ld(const unsigned char* box, int r, int j, int xr) {
+    return *reinterpret_cast<const ulonglong2*>(box + r * 128 + ((j ^ xr) << 4));
 }
 
-template <int KB, int UNR, bool LAB_SMEM>
-__global__ void __launch_bounds__(kReduceMaxWarps * 32, 1) reduce_sym_kernel(SymArgs a) {
+template <int KB>
+__global__ void __launch_bounds__(kSymThreads, 1)
+    reduce_sym_kernel(const __grid_constant__ CUtensorMap map, SymArgs a) {
+    using L = SymLayout<KB>;
+    constexpr int S = L::stages;
     if (pass_skip(a.st, a.eval_only)) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int n = a.n, k = a.k, L = a.seglen, L4 = a.seglen / 4;
-    const int W = blockDim.x >> 5;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = tc::smem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nlab = LAB_SMEM ? ((n + 15) & ~15) : 0;
-    uint8_t* slab = smem;
-    unsigned long long* colacc = reinterpret_cast<unsigned long long*>(smem + nlab);   // [k][4][L4]
-    float* sacc = reinterpret_cast<float*>(colacc + (size_t)k * L);                     // [W][k][32]
-    const float scale = fixed_scale(a.st, a.fbits);
-    if (LAB_SMEM) {
-        const uint4* src = reinterpret_cast<const uint4*>(a.lab8);
-        uint4* dst = reinterpret_cast<uint4*>(slab);
-        for (int t = threadIdx.x; t < nlab / 16; t += blockDim.x) dst[t] = src[t];
+    const int n = a.n, k = a.k;
+    auto full_bar = [&](int s) { return sbase + L::bars + 8u * s; };
+    auto empty_bar = [&](int s) { return sbase + L::bars + 8u * (S + s); };
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::flag);
+    int2* ij = reinterpret_cast<int2*>(smem + L::ij);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(full_bar(s), 1);
+            tc::mbar_init(empty_bar(s), kConsumerWarps);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int t = threadIdx.x; t < k * L; t += blockDim.x) colacc[t] = 0ull;
-    for (int t = threadIdx.x; t < W * k * 32; t += blockDim.x) sacc[t] = 0.f;
     __syncthreads();
-    const uint8_t* labs = LAB_SMEM ? slab : a.lab8;
-    const uint32_t* lab4 = reinterpret_cast<const uint32_t*>(labs);
-    float* accw = sacc + (size_t)warp * k * 32;
-    float* accl = accw + lane;
 
-    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
-        const int4 item = a.items[it];
-        const int s = item.x;
-        const int c0 = s * L, c1 = min(n, c0 + L);
-        const int q1 = c1 >> 2;                       // full float4s of the segment
-        const int row_end = min(n, item.z * 128);
-        // cursor of this warp: row i, float4 base qb (lane 0's), diagonal end dend
-        struct Cur {
-            int i, qb, dend, li;
-            const float4* row4;
-        };
-        auto open_row = [&](int i, Cur& c) -> bool {
-            if (i >= row_end) return false;
-            const int blk0 = (i >> 7) << 7;
-            c.i = i;
-            c.qb = max(c0, blk0) >> 2;
-            c.dend = blk0 + 128;
-            c.li = labs[i];
-            c.row4 = reinterpret_cast<const float4*>(a.K + (int64_t)i * a.ldk);
-            return true;
-        };
-        auto load = [&](const Cur& c, float4 (&v)[UNR], uint32_t (&Lb)[UNR]) {
+    const long long G = gridDim.x;
+    const long long nmine = (long long)blockIdx.x < a.items ? (a.items - 1 - blockIdx.x) / G + 1 : 0;
+
+    if (warp == kConsumerWarps) {
+        // producer: one thread loads block after block (and its labels) into the ring
+        if (lane == 0) {
+            const uint64_t stream_once = tc::l2_evict_first();   // K is read once per pass
+            long long t = 0;
+            for (; t < nmine; ++t) {
+                const int s = (int)(t % S);
+                if (t >= S && !tc::mbar_wait(empty_bar(s), (uint32_t)((t / S) - 1) & 1u, abort_flag, a.err)) break;
+                int I, J;
+                tri_coords(blockIdx.x + t * G, a.T, &I, &J);
+                ij[s] = make_int2(I, J);   // published by the arrive below (release)
+                const int lbI = min(kB, a.nlab - I * kB), lbJ = min(kB, a.nlab - J * kB);
+                tc::mbar_arrive_expect_tx(full_bar(s), (uint32_t)(kTileBytes + lbI + lbJ));
+                const uint32_t dst = sbase + L::tiles + (uint32_t)s * kTileBytes;
 #pragma unroll
-            for (int t = 0; t < UNR; ++t) {
-                const int q = c.qb + lane + 32 * t;
-                if (q < q1) {
-                    v[t] = ld_stream(c.row4 + q);
-                    Lb[t] = LAB_SMEM ? lab4[q] : __ldg(lab4 + q);
-                } else {
-                    v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    Lb[t] = 0u;
-                }
+                for (int b = 0; b < 4; ++b)
+                    tc::tma_load_2d_hint(dst + b * kBoxBytes, &map, J * kB + kBoxCols * b, I * kB, full_bar(s),
+                                         stream_once);
+                const uint32_t ldst = sbase + L::labels + (uint32_t)s * 2 * kB;
+                tc::bulk_load_1d(ldst, a.lab8 + (size_t)I * kB, (uint32_t)lbI, full_bar(s));
+                tc::bulk_load_1d(ldst + kB, a.lab8 + (size_t)J * kB, (uint32_t)lbJ, full_bar(s));
             }
-        };
-        Cur cur;
-        if (open_row(item.y * 128 + warp, cur)) {
-            float4 v[UNR];
-            uint32_t Lb[UNR];
-            load(cur, v, Lb);
-            while (true) {
-                const bool last = cur.qb + 32 * UNR >= q1;
-                Cur nxt = cur;
-                bool more = true;
-                if (last) more = open_row(cur.i + W, nxt);
-                else nxt.qb = cur.qb + 32 * UNR;
-                float4 vn[UNR];
-                uint32_t Ln[UNR];
-                if (more) load(nxt, vn, Ln);
-                unsigned long long* colrow = colacc + (size_t)cur.li * L - (c0 >> 2);   // [e * L4 + q]
-#pragma unroll
-                for (int t = 0; t < UNR; ++t) {
-                    const int q = cur.qb + lane + 32 * t;
-                    const float e4[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) accl[((Lb[t] >> (8 * e)) & 0xffu) * 32] += e4[e];
-                    // a float4 never straddles the block boundary (both multiples of 4)
-                    if (q < q1 && 4 * q >= cur.dend) {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            atomicAdd(colrow + e * L4 + q, (unsigned long long)__float2ll_rn(e4[e] * scale));
+            if (*abort_flag) {
+                // leaving early: let this thread's copies land before the CTA's memory goes
+                // (bounded; the consumers may never have waited for them)
+                for (long long t2 = t > S ? t - S : 0; t2 < t; ++t2) {
+                    const uint32_t bar = full_bar((int)(t2 % S)), par = (uint32_t)(t2 / S) & 1u;
+                    const unsigned long long t0 = tc::globaltimer();
+                    while (!tc::mbar_try_wait(bar, par) && tc::globaltimer() - t0 < tc::kWaitLimitNs) {
                     }
-                }
-                if (last) {
-                    {   // ragged tail of the row (n not a multiple of 4)
-                        const int j = 4 * q1 + lane;
-                        if (j < c1) {
-                            const float x = a.K[(int64_t)cur.i * a.ldk + j];
-                            accl[(int)labs[j] * 32] += x;
-                            if (j >= cur.dend)
-                                atomicAdd(colacc + (size_t)cur.li * L + ((j - c0) & 3) * L4 + ((j - c0) >> 2),
-                                          (unsigned long long)__float2ll_rn(x * scale));
-                        }
-                    }
-                    float* out = a.Spart + (size_t)s * k * n + cur.i;   // [s][c][i]
-                    __syncwarp();
-                    if constexpr (KB > 0) {
-                        float part[KB];
-#pragma unroll
-                        for (int c = 0; c < KB; ++c) {
-                            part[c] = c < k ? accl[c * 32] : 0.f;
-                            if (c < k) accl[c * 32] = 0.f;
-                        }
-                        const float tot = butterfly<KB>(part, lane);
-                        const int c = bfly_cluster<KB>(lane);
-                        if ((lane & (32 / KB - 1)) == 0 && c < k) out[(size_t)c * n] = tot;
-                    } else {
-                        for (int cb = 0; cb < k; cb += 32) {
-                            const int c = cb + lane;
-                            if (c < k) {
-                                float tot = 0.f;
-                                float* rowp = accw + (size_t)c * 32;
-#pragma unroll 8
-                                for (int j = 0; j < 32; ++j) {
-                                    const int idx = (j + lane) & 31;
-                                    tot += rowp[idx];
-                                    rowp[idx] = 0.f;
-                                }
-                                out[(size_t)c * n] = tot;
-                            }
-                        }
-                    }
-                    __syncwarp();
-                    if (!more) break;
-                }
-                cur = nxt;
-#pragma unroll
-                for (int t = 0; t < UNR; ++t) {
-                    v[t] = vn[t];
-                    Lb[t] = Ln[t];
                 }
             }
         }
-        // this item's column sums: to Cpart, and cleared for the next item
-        __syncthreads();
-        ulonglong2* dst = reinterpret_cast<ulonglong2*>(a.Cpart + (size_t)it * k * L);
-        ulonglong2* src = reinterpret_cast<ulonglong2*>(colacc);
-        for (int t = threadIdx.x; t < k * L / 2; t += blockDim.x) {
-            dst[t] = src[t];
-            src[t] = make_ulonglong2(0ull, 0ull);
+        return;
+    }
+
+    const uint64_t keep = tc::l2_evict_last();   // the slots are read back by the fold
+    const bool rowg = warp < kConsumerWarps / 2;
+    const int u = threadIdx.x & (kGroup - 1);   // thread within its group
+    const int bar_id = rowg ? kBarRows : kBarCols;
+    const int gw = u >> 5;                      // warp within its group
+    const int xr = lane & 7;                    // row mod 8 of every row this lane reads (row group)
+    for (long long t = 0; t < nmine; ++t) {
+        const int s = (int)(t % S);
+        const bool ok = tc::mbar_wait(full_bar(s), (uint32_t)(t / S) & 1u, abort_flag, a.err);
+        if (!tc::named_bar_all(bar_id, kGroup, ok)) break;   // the group leaves together
+        const int2 bij = ij[s];
+        const int I = bij.x, J = bij.y;
+        const unsigned char* tile = smem + L::tiles + (size_t)s * kTileBytes;
+        const uint8_t* lab = smem + L::labels + s * 2 * kB;
+        if (rowg) {
+            // row sums of block I over the columns of block J -> slot J.  The columns
+            // are split into NPART parts of BOXES boxes; a part's rows go to WPP warps,
+            // RPL rows a lane (lane, lane + 32).
+            constexpr int RPL = KB <= 4 ? 2 : 1;      // two rows per lane halve the weight reads
+            constexpr int NPART = 2 * RPL, BOXES = 4 / NPART, WPP = 4 / RPL;
+            float* wt = reinterpret_cast<float*>(smem + L::wt);
+            if (u < kB) {
+                const int l = J * kB + u < n ? (int)lab[kB + u] : -1;
+#pragma unroll
+                for (int c = 0; c < KB; ++c) wt[((u >> 2) * KB + c) * 4 + (u & 3)] = l == c ? 1.f : 0.f;
+            }
+            tc::named_bar<kGroup>(kBarRows);
+            const int part = gw / WPP;
+            const int r0 = 32 * RPL * (gw % WPP) + lane;
+            unsigned long long sa[RPL][KB], sb[RPL][KB];   // columns 4m, 4m + 1 and 4m + 2, 4m + 3
+#pragma unroll
+            for (int e = 0; e < RPL; ++e)
+#pragma unroll
+                for (int c = 0; c < KB; ++c) sa[e][c] = sb[e][c] = 0ull;
+#pragma unroll
+            for (int bx = 0; bx < BOXES; ++bx) {
+                const int box_id = part * BOXES + bx;
+                const unsigned char* box = tile + box_id * kBoxBytes;
+                const ulonglong2* w2 = reinterpret_cast<const ulonglong2*>(wt) + box_id * 8 * KB;
+#pragma unroll 2
+                for (int j = 0; j < 8; ++j) {
+                    ulonglong2 v[RPL];
+#pragma unroll
+                    for (int e = 0; e < RPL; ++e) v[e] = box_ld(box, r0 + 32 * e, j, xr);
+#pragma unroll
+                    for (int c = 0; c < KB; ++c) {
+                        const ulonglong2 w = w2[j * KB + c];
+#pragma unroll
+                        for (int e = 0; e < RPL; ++e) {
+                            sa[e][c] = tc::f2fma(v[e].x, w.x, sa[e][c]);
+                            sb[e][c] = tc::f2fma(v[e].y, w.y, sb[e][c]);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(empty_bar(s));   // this warp is done with the stage
+            float* prt = reinterpret_cast<float*>(smem + L::rowpart);
+#pragma unroll
+            for (int c = 0; c < KB; ++c)
+#pragma unroll
+                for (int e = 0; e < RPL; ++e) {
+                    float x, y;
+                    tc::f2unpack(tc::f2add(sa[e][c], sb[e][c]), x, y);
+                    prt[(part * KB + c) * kB + r0 + 32 * e] = x + y;
+                }
+            tc::named_bar<kGroup>(kBarRows);
+            if (u < kB && I * kB + u < n) {
+                float* out = a.Spart + (size_t)J * k * n + I * kB + u;
+                for (int c = 0; c < k; ++c) {
+                    const float* pp = prt + c * kB + u;
+                    float v = pp[0];
+#pragma unroll
+                    for (int q = 1; q < NPART; ++q) v += pp[q * KB * kB];
+                    tc::st_hint(out + (size_t)c * n, v, keep);
+                }
+            }
+        } else if (I == J) {
+            // a diagonal block: its row sums already cover it
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(empty_bar(s));
+        } else {
+            // column sums of block J over the rows of block I -> slot I.  Warp gw: rows
+            // 16 gw .. 16 gw + 15; lane: columns 4 lane .. 4 lane + 3.
+            unsigned long long* wd = reinterpret_cast<unsigned long long*>(smem + L::wd);
+            if (u < kB) {
+                const int l = I * kB + u < n ? (int)lab[u] : -1;
+#pragma unroll
+                for (int c = 0; c < KB; ++c) wd[u * KB + c] = l == c ? tc::f2pack(1.f, 1.f) : 0ull;
+            }
+            tc::named_bar<kGroup>(kBarCols);
+            const unsigned char* box = tile + (lane >> 3) * kBoxBytes;
+            const int j = lane & 7;
+            unsigned long long p[KB], q[KB];
+#pragma unroll
+            for (int c = 0; c < KB; ++c) p[c] = q[c] = 0ull;
+#pragma unroll 4
+            for (int rr = 0; rr < 16; ++rr) {
+                const int r = 16 * gw + rr;
+                const ulonglong2 v = box_ld(box, r, j, rr & 7);
+                const ulonglong2* wr = reinterpret_cast<const ulonglong2*>(wd + r * KB);
+#pragma unroll
+                for (int c2 = 0; c2 < KB / 2; ++c2) {
+                    const ulonglong2 w = wr[c2];
+                    p[2 * c2] = tc::f2fma(v.x, w.x, p[2 * c2]);
+                    q[2 * c2] = tc::f2fma(v.y, w.x, q[2 * c2]);
+                    p[2 * c2 + 1] = tc::f2fma(v.x, w.y, p[2 * c2 + 1]);
+                    q[2 * c2 + 1] = tc::f2fma(v.y, w.y, q[2 * c2 + 1]);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(empty_bar(s));
+            // the 8 warps' partials, added in warp order
+            float* part = reinterpret_cast<float*>(smem + L::colpart);
+#pragma unroll
+            for (int c = 0; c < KB; ++c) {
+                float x0, y0, x1, y1;
+                tc::f2unpack(p[c], x0, y0);
+                tc::f2unpack(q[c], x1, y1);
+                *reinterpret_cast<float4*>(part + (gw * KB + c) * kB + 4 * lane) = make_float4(x0, y0, x1, y1);
+            }
+            tc::named_bar<kGroup>(kBarCols);
+            if (u < kB && J * kB + u < n) {
+                float* out = a.Spart + (size_t)I * k * n + J * kB + u;
+                for (int c = 0; c < k; ++c) {
+                    const float* pp = part + c * kB + u;
+                    float v = pp[0];
+#pragma unroll
+                    for (int w = 1; w < 8; ++w) v += pp[w * KB * kB];
+                    tc::st_hint(out + (size_t)c * n, v, keep);
+                }
+            }
         }
-        __syncthreads();
     }
 }
 
-// Spart[nseg][c][j] = the column sums of j over the items of j's segment: an exact
-// integer sum, then scaled back.
-__global__ void __launch_bounds__(256) sym_fold_kernel(const unsigned long long* __restrict__ Cpart,
-                                                        const int* __restrict__ seg_item, int n, int k, int seglen,
-                                                        int nseg, int fbits, float* __restrict__ Spart,
-                                                        const LoopState* st, int eval_only) {
-    if (pass_skip(st, eval_only)) return;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+struct FoldArgs {
+    int n, k, T;
+    float* Spart;
+    const uint8_t* lab8;
+    double* zpart;             // [gridDim.x][k]
+    double* zsum;
+    double* cnorm;
+    double* invm;
+    const int32_t* counts;
+    LoopState* st;
+    double* J_hist;
+    int eval_only;
+};
+
+// Block (x, c): rows x * 256 ... of cluster c.
+__global__ void __launch_bounds__(kFoldThreads) sym_fold_kernel(FoldArgs a) {
+    LoopState* st = a.st;
+    if (pass_skip(st, a.eval_only)) {
+        if (a.eval_only && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->J_eval = st->J_last;
+        return;
+    }
+    __shared__ double wsum[kFoldThreads / 32];
+    __shared__ int am_last;
     const int c = blockIdx.y;
-    if (j >= n) return;
-    const int s = j / seglen, jj = j - s * seglen, L4 = seglen / 4;
-    const size_t off = (size_t)c * seglen + (size_t)(jj & 3) * L4 + (jj >> 2);
-    unsigned long long acc = 0ull;
-    for (int it = seg_item[s]; it < seg_item[s + 1]; ++it) acc += Cpart[(size_t)it * k * seglen + off];
-    const double scale = (double)fixed_scale(st, fbits);
-    Spart[((size_t)nseg * k + c) * n + j] = (float)((double)(long long)acc / scale);
-}
-
-using SymFn = void (*)(SymArgs);
-
-SymFn sym_fn(int k, bool lab_smem) {
-    if (k <= 4) return lab_smem ? reduce_sym_kernel<4, 4, true> : reduce_sym_kernel<4, 4, false>;
-    if (k <= 8) return lab_smem ? reduce_sym_kernel<8, 4, true> : reduce_sym_kernel<8, 4, false>;
-    return lab_smem ? reduce_sym_kernel<0, 4, true> : reduce_sym_kernel<0, 4, false>;
+    const int i = blockIdx.x * kFoldThreads + threadIdx.x;
+    const int n = a.n;
+    double zc = 0.0;
+    if (i < n) {
+        float* p = a.Spart + (size_t)c * n + i;
+        const size_t ss = (size_t)a.k * n;
+        // two interleaved float-float sums keep more loads in flight
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+        int s = 0;
+#pragma unroll 4
+        for (; s + 2 <= a.T; s += 2) {
+            ff_add(h0, l0, p[(size_t)s * ss]);
+            ff_add(h1, l1, p[(size_t)(s + 1) * ss]);
+        }
+        if (s < a.T) ff_add(h0, l0, p[(size_t)s * ss]);
+        const double S = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+        *p = (float)S;
+        if ((int)a.lab8[i] == c) zc = S;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) zc += __shfl_xor_sync(0xffffffffu, zc, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = zc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kFoldThreads / 32; ++w) t += wsum[w];
+        a.zpart[(size_t)blockIdx.x * a.k + c] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(&st->reduce_ticket, 1u) == gridDim.x * gridDim.y - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    finalize_pass(a.zpart, (int)gridDim.x, a.k, a.counts, a.zsum, a.cnorm, a.invm, st, a.J_hist, a.eval_only);
 }
 
 }  // namespace
 
-cudaError_t configure_reduce_sym(int smem_optin, int* usable) {
-    size_t st = 0;
-    for (int kk : {4, 8, 16})
-        for (int ls = 0; ls < 2; ++ls) {
-            cudaFuncAttributes fa;
-            cudaError_t e = cudaFuncGetAttributes(&fa, sym_fn(kk, ls != 0));
-            if (e != cudaSuccess) return e;
-            if (fa.sharedSizeBytes > st) st = fa.sharedSizeBytes;
-        }
-    const int bytes = optin_minus_static(smem_optin, st);
-    for (int kk : {4, 8, 16})
-        for (int ls = 0; ls < 2; ++ls) {
-            cudaError_t e = cudaFuncSetAttribute(sym_fn(kk, ls != 0), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            if (e != cudaSuccess) return e;
-        }
-    *usable = bytes;
-    return cudaSuccess;
+cudaError_t configure_reduce_sym(int smem_optin) {
+    if (smem_optin < SymLayout<4>::bytes || smem_optin < SymLayout<8>::bytes)
+        return cudaSuccess;   // plan_reduce_sym then declines
+    cudaError_t e = cudaFuncSetAttribute(reduce_sym_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SymLayout<4>::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(reduce_sym_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SymLayout<8>::bytes);
 }
 
-// Segment length, shared memory and the item list (host side, once per fit).
-SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_budget) {
+SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin) {
     SymPlan p{};
-    p.warps = kReduceMaxWarps;
-    const size_t nlab = ((size_t)n + 15) & ~(size_t)15;
-    const size_t rowacc = (size_t)p.warps * k * 32 * 4;
-    // labels in shared memory when a useful segment still fits beside them
-    p.labels_in_smem = nlab + rowacc + (size_t)k * 1024 * 8 <= (size_t)smem_budget;
-    const size_t base = (p.labels_in_smem ? nlab : 0) + rowacc;
-    if (base + (size_t)k * 128 * 8 > (size_t)smem_budget) return p;   // ok = false: k too large
-    long long L = (long long)(((size_t)smem_budget - base) / ((size_t)k * 8)) / 128 * 128;
-    const long long npad = (n + 127) / 128 * 128;
-    if (L > 8192) L = 8192;
-    if (L > npad) L = npad;
-    p.seglen = (int)L;
-    p.nseg = (int)((n + L - 1) / L);
-    p.smem = base + (size_t)k * L * 8;
-    int lg = 0;
-    while ((1LL << lg) < (long long)n) ++lg;
-    p.fbits = 61 - lg;
-    // items: per segment, runs of row blocks of about equal work (elements read),
-    // about three items per CTA in all
-    const int T = (n + 127) / 128;
-    std::vector<double> seg_work(p.nseg, 0.0);
-    double total = 0.0;
-    for (int s = 0; s < p.nseg; ++s) {
-        const long long c0 = (long long)s * L, c1 = std::min<long long>(n, c0 + L);
-        for (int r = 0; r < T && 128LL * r < c1; ++r) {
-            const double w = 128.0 * (double)(c1 - std::max<long long>(c0, 128LL * r));
-            seg_work[s] += w;
-        }
-        total += seg_work[s];
-    }
-    const double target = total / (3.0 * num_sms);
-    p.seg_item.assign(p.nseg + 1, 0);
-    for (int s = 0; s < p.nseg; ++s) {
-        p.seg_item[s] = (int)p.items.size();
-        const long long c0 = (long long)s * L, c1 = std::min<long long>(n, c0 + L);
-        int r0 = 0;
-        double acc = 0.0;
-        int r = 0;
-        for (; r < T && 128LL * r < c1; ++r) {
-            acc += 128.0 * (double)(c1 - std::max<long long>(c0, 128LL * r));
-            if (acc >= target) {
-                p.items.push_back({s, r0, r + 1, 0});
-                r0 = r + 1;
-                acc = 0.0;
-            }
-        }
-        if (r0 < r) p.items.push_back({s, r0, r, 0});
-    }
-    p.seg_item[p.nseg] = (int)p.items.size();
-    p.grid = (int)std::min<size_t>((size_t)num_sms, p.items.size());
-    p.ok = p.grid > 0;
+    if (k < 1 || k > kSymMaxK || n < 1 || smem_optin < SymLayout<4>::bytes || smem_optin < SymLayout<8>::bytes)
+        return p;
+    p.T = (n + kB - 1) / kB;
+    p.items = (long long)p.T * (p.T + 1) / 2;
+    p.grid = (int)(p.items < num_sms ? p.items : num_sms);
+    p.fold_blocks = (n + kFoldThreads - 1) / kFoldThreads;
+    p.smem = k <= 4 ? SymLayout<4>::bytes : SymLayout<8>::bytes;
+    p.ok = true;
     return p;
 }
 
-cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, const int4* d_items, const int* d_seg_item,
-                              unsigned long long* Cpart, int eval_only, cudaStream_t s) {
+cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, int eval_only, cudaStream_t s) {
+    CUtensorMap map;
+    if (!make_tensor_map_2d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, const_cast<void*>(b.K), (uint64_t)b.n,
+                            (uint64_t)b.n, (uint64_t)b.ldk * 4, kBoxCols, kB, CU_TENSOR_MAP_SWIZZLE_128B))
+        return cudaErrorInvalidValue;
     SymArgs a;
-    a.K = static_cast<const float*>(b.K);
     a.ldk = b.ldk;
     a.n = b.n;
     a.k = b.k;
-    a.seglen = p.seglen;
-    a.nseg = p.nseg;
-    a.items = d_items;
-    a.nitems = (int)p.items.size();
+    a.T = p.T;
+    a.nlab = (b.n + 15) & ~15;
+    a.items = p.items;
     a.lab8 = b.lab8;
     a.Spart = b.Spart;
-    a.Cpart = Cpart;
-    a.fbits = p.fbits;
     a.st = b.st;
+    a.err = err;
     a.eval_only = eval_only;
-    sym_fn(b.k, p.labels_in_smem)<<<p.grid, p.warps * 32, p.smem, s>>>(a);
+    if (b.k <= 4) reduce_sym_kernel<4><<<p.grid, kSymThreads, p.smem, s>>>(map, a);
+    else reduce_sym_kernel<8><<<p.grid, kSymThreads, p.smem, s>>>(map, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 fg((b.n + 255) / 256, b.k);
-    sym_fold_kernel<<<fg, 256, 0, s>>>(Cpart, d_seg_item, b.n, b.k, p.seglen, p.nseg, p.fbits, b.Spart, b.st,
-                                        eval_only);
+    FoldArgs f;
+    f.n = b.n;
+    f.k = b.k;
+    f.T = p.T;
+    f.Spart = b.Spart;
+    f.lab8 = b.lab8;
+    f.zpart = b.zpart;
+    f.zsum = b.zsum;
+    f.cnorm = b.cnorm;
+    f.invm = b.invm;
+    f.counts = b.counts;
+    f.st = b.st;
+    f.J_hist = b.J_hist;
+    f.eval_only = eval_only;
+    sym_fold_kernel<<<dim3((unsigned)p.fold_blocks, (unsigned)b.k), kFoldThreads, 0, s>>>(f);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,11 @@
-// Building blocks of the K-streaming reductions (iterate.cu, reduce_sym.cu).
+// Building blocks of the K-streaming reductions (iterate.cu, reduce_sym.cu) and the
+// pass finalization they share.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "popcorn_internal.cuh"
 
 namespace popcorn {
 namespace stream {
@@ -56,6 +59,36 @@ __device__ __forceinline__ float butterfly(const float (&acc)[KB], int lane) {
 #pragma unroll
     for (; off > 0; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
     return v[0];
+}
+
+// Last block of a pass's reduction, all its threads: sum the per-block FP64
+// partials of sum_{i in L_c} S_ic in block order, then ||c_c||^2 =
+// (1/m_c^2) sum_{i in L_c} S_ic (Eq. 13/14), 1/m_c, and
+// J = trace K - sum_c (1/m_c) sum_{i in L_c} S_ic.
+__device__ inline void finalize_pass(const double* zpart, int nblocks, int k, const int32_t* counts, double* zsum,
+                                     double* cnorm, double* invm, LoopState* st, double* J_hist, int eval_only) {
+    const int32_t* m = counts + (size_t)(st->iter & 1) * k;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < nblocks; ++b) t += __ldcg(zpart + (size_t)b * k + c);
+        const double mc = (double)__ldcg(m + c);
+        const double inv = mc > 0 ? 1.0 / mc : 0.0;
+        zsum[c] = t;
+        invm[c] = inv;
+        cnorm[c] = t * inv * inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double J = st->trace;
+        for (int c = 0; c < k; ++c) J -= __ldcg(zsum + c) * __ldcg(invm + c);
+        if (eval_only) {
+            st->J_eval = J;
+        } else {
+            J_hist[st->iter] = J;
+            st->J_last = J;
+        }
+        st->reduce_ticket = 0u;
+    }
 }
 
 }  // namespace stream

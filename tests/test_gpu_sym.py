@@ -1,12 +1,13 @@
 """GPU parity of the symmetric pass (popcorn_fit with a stored FP32 K, k_pass = 1).
 
-The pass reads only the 128-blocks on and above the diagonal: each off-diagonal
-element feeds its row's cluster sum and, by K's symmetry, its column's.  So one
-pass from given labels must be the oracle's step exactly as the full-square
-pass is (labels equal except near-ties, objective within the FP32 bar), and
-whole fits must agree with the full-square pass up to FP32 summation order.
-The cases cover a ragged n (not a multiple of 4 or 128), a single block,
-several column segments, k <= 4 / <= 8 (butterfly) and k > 8 (rotated walk).
+The pass reads only the 128 x 128 blocks on and above the diagonal: a block's row
+sums give one part of S_ic for its rows and, by K's symmetry, its column sums the
+part of its columns' rows; a fold kernel adds the parts.  So one pass from given
+labels must be the oracle's step exactly as the full-square pass is (labels equal
+except near-ties, objective within the FP32 bar), and whole fits must agree with the
+full-square pass up to FP32 summation order.  The cases cover a single ragged block,
+ragged n over several blocks, n a multiple of 128, k at its bound (8), a kernel
+that is not positive semi-definite (symmetry is all the pass needs) and many blocks.
 """
 import numpy as np
 import pytest
@@ -32,14 +33,17 @@ def _gauss(s):
 
 
 POLY2 = {"kind": "polynomial", "gamma": 1.0, "coef0": 1.0, "degree": 2, "sigma": 1.0}
+POLY3_NEG = {"kind": "polynomial", "gamma": 0.5, "coef0": -1.0, "degree": 3, "sigma": 1.0}   # not PSD
 
 CASES = [
     # (n, d, k, kernel, seed)
     (97, 3, 3, _gauss(1.0), 1),          # one block, ragged
-    (333, 5, 4, POLY2, 2),               # k <= 4
-    (1030, 9, 8, _gauss(2.0), 3),        # k <= 8, ragged (n % 4 = 2)
-    (2001, 6, 13, _gauss(1.5), 4),       # k > 8
-    (9001, 4, 5, _gauss(1.0), 5),        # several column segments at k = 5
+    (333, 5, 4, POLY2, 2),               # three blocks, ragged
+    (1030, 9, 8, _gauss(2.0), 3),        # ragged (n % 4 = 2)
+    (2001, 6, 2, _gauss(1.5), 4),
+    (1280, 4, 8, _gauss(1.0), 6),        # n a multiple of 128, k at the bound
+    (700, 3, 5, POLY3_NEG, 7),           # negative entries: symmetry suffices
+    (9001, 4, 5, _gauss(1.0), 5),        # 71 blocks per side
 ]
 
 
@@ -78,7 +82,7 @@ def test_symmetric_fit_matches_full_square(pc, n, d, k, kern, seed):
 
 
 def test_symmetric_rings_bench_size_matches_full_square(pc):
-    """The bench workload (rings, n = 20,000: three column segments at k = 4) to
+    """The bench workload (rings, n = 20,000: 157 blocks per side, k = 4) to
     convergence: the symmetric and the full-square pass reach the same labels in the
     same number of passes, objectives within the FP32 bar."""
     wl = synth.workload("rings")
@@ -93,8 +97,8 @@ def test_symmetric_rings_bench_size_matches_full_square(pc):
 
 
 def test_symmetric_pass_is_deterministic(pc):
-    """Column sums are added as 64-bit integers (fixed point), so the order in which warps
-    add them does not change a bit of the result: two runs agree exactly."""
+    """No atomics: every partial is written once and folded in slot order, so runs
+    agree bit for bit."""
     wl = synth.workload("rings", scale=0.3)
     P = torch.from_numpy(wl.P).cuda()
     L0 = torch.from_numpy(wl.init_labels).cuda()
@@ -104,3 +108,20 @@ def test_symmetric_pass_is_deterministic(pc):
         assert r["info"]["J_history"] == runs[0]["info"]["J_history"]
         assert r["objective"] == runs[0]["objective"]
         assert np.array_equal(r["labels"].cpu().numpy(), runs[0]["labels"].cpu().numpy())
+
+
+def test_symmetric_pass_launches_and_fallback(pc):
+    """k_pass = "symmetric" runs the stream and the fold (one launch more per pass than
+    the full square); above the cluster bound it falls back to the full-square pass,
+    with results identical to it."""
+    P = torch.from_numpy(synth.gaussian_blobs(600, 3, 6, seed=9, box=3.0)).cuda()
+    lab = torch.from_numpy(synth.init_labels(600, 6, seed=19)).cuda()
+    a = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_pass="symmetric")
+    b = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_pass="full")
+    assert a["info"]["kernel_launches"] == b["info"]["kernel_launches"] + a["iterations"] + 1
+    lab12 = torch.from_numpy(synth.init_labels(600, 12, seed=29)).cuda()
+    c = pc.popcorn_fit(P, 12, _gauss(1.0), lab12, max_iter=5, check_convergence=False, k_pass="symmetric")
+    d = pc.popcorn_fit(P, 12, _gauss(1.0), lab12, max_iter=5, check_convergence=False, k_pass="full")
+    assert c["info"]["kernel_launches"] == d["info"]["kernel_launches"]
+    assert np.array_equal(c["labels"].cpu().numpy(), d["labels"].cpu().numpy())
+    assert c["objective"] == d["objective"]
