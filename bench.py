@@ -71,9 +71,9 @@ def parse():
                     help="time candidate schedules in the warm-up (batched and recompute paths)")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16", "bf16x3", "fp8"],
                     help="K-build precision (default: the workload's)")
-    ap.add_argument("--k-pass", default="full", choices=["full", "symmetric"],
-                    help="how a pass reads a stored FP32 K: the full square, or the blocks on and above the "
-                         "diagonal (row and column sums, then a fold)")
+    ap.add_argument("--k-pass", default="auto", choices=["auto", "full", "symmetric"],
+                    help="how a pass reads a stored FP32 K: the library's choice, the full square, or the blocks "
+                         "on and above the diagonal (row and column sums, then a fold)")
     ap.add_argument("--compare", default=None, choices=["paper"],
                     help="paper: also time the paper's formulation through library calls (cuBLAS GEMM + "
                          "elementwise kernel function, cuSPARSE SpMM/SpMV per pass) on the same inputs")
@@ -551,20 +551,23 @@ def main():
                 "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_red_ms}
         roof2 = None
-        if wl.store_k and args.k_pass == "symmetric" and wl.precision == "fp32" and k <= 8:
-            # stream (the blocks on and above the diagonal; slots written) + fold (slots read,
-            # slot 0 written): the CUDA events bracket both launches
+        if results[-1]["info"]["k_pass_used"] == 1:
+            # symmetric pass: the stream kernel alone (its CUDA-event time is the pass's
+            # reduction minus the fold, both recorded by the library on the launch stream)
             T = (n + 127) // 128
-            tri = 0.0
-            for I in range(T):
-                rows = min(128, n - 128 * I)
-                tri += rows * (n - 128 * I)          # real elements of blocks (I, J >= I)
-            slots = 4.0 * T * k * n
-            alg_bytes = 4.0 * tri + 2.0 * slots + 4.0 * k * n + 2.0 * n   # K, slots out and in, slot 0, labels
-            achieved = alg_bytes / (avg_red_ms / 1e3) / 1e9 if avg_red_ms > 0 else 0.0
-            roof = {"kernel": "reduce_sym_kernel + sym_fold_kernel", "bound": "hbm", "achieved": achieved,
-                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                    "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_red_ms}
+            tri = sum(min(128, n - 128 * I) * (n - 128 * I) for I in range(T))   # elements of blocks (I, J >= I)
+            fold_ms = sum(r["info"]["fold_ms"] for r in results)
+            passes = sum(r["iterations"] for r in results)
+            avg_stream_ms = (red_ms - fold_ms) / max(passes, 1)
+            alg_bytes = 4.0 * tri + 4.0 * T * k * n + 256.0 * T * (T + 1) / 2   # K blocks, slots, labels
+            achieved = alg_bytes / (avg_stream_ms / 1e3) / 1e9 if avg_stream_ms > 0 else 0.0
+            roof = {"kernel": "reduce_sym_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "traffic": recorded_traffic("reduce_sym_kernel",
+                                                                                         "reduce_sym.cu"),
+                    "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
+                    "avg_launch_ms": avg_stream_ms,
+                    "pass": "symmetric: blocks on and above the diagonal, then sym_fold_kernel",
+                    "fold_avg_launch_ms": fold_ms / max(passes, 1)}
         if not wl.store_k:
             # recompute pass: tensor cores (2 n^2 d flops) and the exp2 unit (n^2 kernel values)
             roof, roof2 = recompute_rooflines(wl, avg_red_ms, clk)
@@ -586,7 +589,10 @@ def main():
                        "precision": wl.precision,
                        "n": n, "d": wl.d, "k": k,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": f"inputs larger than L2 (K = {4 * wl.n * wl.n / 1e9:.2f} GB streamed every pass)",
+                       "l2": (f"inputs larger than L2 (K = {4 * wl.n * wl.n / 1e9:.2f} GB; "
+                              + ("its upper triangle of 128-blocks" if results[-1]["info"]["k_pass_used"] == 1
+                                 else "all of it") + " streamed every pass)"),
+                       "k_pass": {0: "recompute", 1: "symmetric", 2: "full"}[results[-1]["info"]["k_pass_used"]],
                        "passes_per_fit": iters / args.steps},
             "kbuild_tflops": kb_flops / (kb_ms / args.steps / 1e3) / 1e12 if kb_ms > 0 else None,
             "kbuild_ms": kb_ms / args.steps,

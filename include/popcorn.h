@@ -105,15 +105,17 @@ typedef struct {
                                    length, warps per block, blocks per SM) and by the
                                    recompute path of popcorn_fit (row blocks per tile, units
                                    per SM).  Results differ only by summation order.        */
-    int32_t k_pass;             /* how a pass reads a stored FP32 K: 0 = the full square, row
-                                   by row (the paper's read of K; the default); 1 = only the
-                                   128 x 128 blocks on and above the diagonal (K is symmetric):
-                                   a block's row sums serve its rows and its column sums its
-                                   columns' rows, written to one slot per block and folded, so
-                                   a pass reads half of K plus 8 k n ceil(n / 128) bytes of
-                                   slots.  1 needs k <= 8; larger k, FP16/BF16 K and the
-                                   recompute path read as 0 / their own scheme.  Results
-                                   differ from 0 only by summation order                    */
+    int32_t k_pass;             /* how a pass reads a stored FP32 K.  0 = automatic (the
+                                   default): the symmetric read below wherever it applies
+                                   (FP32 K, k <= 8), else the full square.  1 = symmetric:
+                                   only the 128 x 128 blocks on and above the diagonal (K is
+                                   symmetric); a block's row sums serve its rows and its
+                                   column sums its columns' rows, written to one slot per
+                                   block and folded, so a pass reads half of K plus
+                                   8 k n ceil(n / 128) bytes of slots; where it does not
+                                   apply the full square runs.  2 = the full square, row by
+                                   row (the paper's read of K).  The recompute path has its
+                                   own scheme.  Results differ only by summation order      */
     int32_t reserved_pad;       /* must be zero                                              */
     int64_t reserved[4];        /* must be zero                                              */
 } popcorn_options;
@@ -144,6 +146,10 @@ typedef struct {
                                             blocks per SM, 0};
                                   recompute: {row blocks per tile, column segments,
                                               units per SM target, 0}; zeros otherwise     */
+    double fold_ms;            /* symmetric pass: the slot fold kernel, summed over passes
+                                  (part of reduce_ms), when timing = 1                      */
+    int32_t k_pass_used;       /* stored K: 1 = symmetric pass, 2 = full square; 0 recompute */
+    int32_t reserved_info;     /* zero                                                     */
 } popcorn_fit_info;
 
 /* Human-readable name of a status code (static storage). */

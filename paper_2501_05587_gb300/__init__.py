@@ -76,7 +76,7 @@ class _Options(ctypes.Structure):
 
 
 K_STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
-K_PASS = {"full": 0, "symmetric": 1}
+K_PASS = {"auto": 0, "symmetric": 1, "full": 2}
 
 
 class _FitInfo(ctypes.Structure):
@@ -88,7 +88,8 @@ class _FitInfo(ctypes.Structure):
                 ("d2h_bytes", ctypes.c_int64), ("J_history", ctypes.POINTER(ctypes.c_double)),
                 ("changed_history", ctypes.POINTER(ctypes.c_int32)), ("tune_cache_hit", ctypes.c_int32),
                 ("tune_candidates", ctypes.c_int32), ("tune_ms", ctypes.c_double),
-                ("schedule", ctypes.c_int32 * 4)]
+                ("schedule", ctypes.c_int32 * 4), ("fold_ms", ctypes.c_double),
+                ("k_pass_used", ctypes.c_int32), ("reserved_info", ctypes.c_int32)]
 
 
 class _Instance(ctypes.Structure):
@@ -254,12 +255,13 @@ def popcorn_autotune_clear() -> None:
 def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float = 0.0,
                 precision: str = "fp32", check_convergence: bool = True, timing: bool = False,
                 history: bool = False, labels_out=None, store_k: bool = True, k_storage: str = "fp32",
-                autotune: bool = False, k_pass: str = "full", stream=None) -> dict:
+                autotune: bool = False, k_pass: str = "auto", stream=None) -> dict:
     """Kernel K-means (Alg. 2).  P and init_labels may live on the host or the device.
 
     ``store_k=False`` selects the recompute path (K never stored; precision
     "bf16" or "fp8").  ``k_storage`` ("fp32", "fp16", "bf16") is the element
-    type of a stored K.  Returns {"labels", "objective", "iterations", "info"};
+    type of a stored K.  ``k_pass`` ("auto", "symmetric", "full") is how a pass
+    reads a stored FP32 K.  Returns {"labels", "objective", "iterations", "info"};
     labels land where ``labels_out`` lives (default: same place as init_labels).
     """
     torch = _torch()

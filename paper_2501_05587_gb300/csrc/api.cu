@@ -477,6 +477,9 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
         info->tune_cache_hit = tune_hit;
         info->tune_candidates = tune_cands;
         info->tune_ms = tune_ms;
+        info->fold_ms = 0.0;
+        info->k_pass_used = 0;
+        info->reserved_info = 0;
         info->schedule[0] = rp.rbp;
         info->schedule[1] = rp.nseg;
         info->schedule[2] = rp.units_per_sm;
@@ -632,7 +635,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     if (max_iter < 0) return fail(POPCORN_ERR_INVALID, "max_iter = %d < 0", max_iter);
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
     if (opt.autotune != 0 && opt.autotune != 1) return fail(POPCORN_ERR_INVALID, "options.autotune must be 0 or 1");
-    if (opt.k_pass != 0 && opt.k_pass != 1) return fail(POPCORN_ERR_INVALID, "options.k_pass must be 0 or 1");
+    if (opt.k_pass < 0 || opt.k_pass > 2) return fail(POPCORN_ERR_INVALID, "options.k_pass must be 0, 1 or 2");
     if (opt.reserved_pad != 0) return fail(POPCORN_ERR_INVALID, "options.reserved_pad must be 0");
     for (int r = 0; r < 4; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
@@ -656,10 +659,10 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     const int64_t ldk = ks == POPCORN_K_FP32 ? (n + 3) / 4 * 4 : (n + 7) / 8 * 8;   // 16-byte rows
     ReducePlan plan = plan_reduce(ni, k, dev->sms, dev->reduce_smem, ks);
     if (plan.grid == 0) return fail(POPCORN_ERR_UNSUPPORTED, "n = %d is too large for the materialized path", ni);
-    // symmetric pass (FP32 K, k <= kSymMaxK, k_pass = 1): the blocks on and above the
+    // symmetric pass (FP32 K, k <= kSymMaxK; k_pass 0 or 1): the blocks on and above the
     // diagonal, row and column sums into T slots, folded into slot 0
     SymPlan sym{};
-    if (ks == POPCORN_K_FP32 && opt.k_pass == 1) sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin);
+    if (ks == POPCORN_K_FP32 && opt.k_pass != 2) sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin);
     const bool use_sym = sym.ok;
     const int nslots = use_sym ? sym.T : plan.nseg;
     if (use_sym) plan.nseg = 1;             // the assignment reads the folded slot only
@@ -707,9 +710,9 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     POPCORN_TRY(ws.alloc(&b.Spart, (size_t)nslots * ni * k, "segment sums"));
     POPCORN_TRY(ws.alloc(&b.zpart, (size_t)(use_sym ? sym.fold_blocks : plan.grid) * k, "block partials"));
     // one pass's reduction: the K stream (for the symmetric pass: stream, then fold with z)
-    auto reduce_pass = [&](int eval) -> cudaError_t {
+    auto reduce_pass = [&](int eval, cudaEvent_t mid) -> cudaError_t {
         if (!use_sym) return launch_reduce(b, plan, eval, s);
-        return launch_reduce_sym(b, sym, &b.st->wait_err, eval, s);
+        return launch_reduce_sym(b, sym, &b.st->wait_err, eval, s, mid);
     };
     POPCORN_TRY(ws.alloc(&b.zsum, (size_t)k, "z sums"));
     POPCORN_TRY(ws.alloc(&b.cnorm, (size_t)k, "centroid norms"));
@@ -722,6 +725,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     g_events.used = 0;
     cudaEvent_t ev_b0 = nullptr, ev_b1 = nullptr, ev_l1 = nullptr, ev_e1 = nullptr;
     std::vector<cudaEvent_t> ev_r, ev_a;   // before/after each reduction and assignment launch
+    std::vector<cudaEvent_t> ev_f;         // symmetric pass: between stream and fold, after the fold
     if (timing) {
         POPCORN_TRY(g_events.get(&ev_b0));
         POPCORN_CUDA(cudaEventRecord(ev_b0, s));
@@ -754,14 +758,15 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     while (launched < max_iter) {
         const int m = (max_iter - launched < chunk) ? (max_iter - launched) : chunk;
         for (int t = 0; t < m; ++t) {
-            cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+            cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, em = nullptr;
             if (timing) {
                 POPCORN_TRY(g_events.get(&e0));
                 POPCORN_TRY(g_events.get(&e1));
                 POPCORN_TRY(g_events.get(&e2));
+                if (use_sym) POPCORN_TRY(g_events.get(&em));
                 POPCORN_CUDA(cudaEventRecord(e0, s));
             }
-            POPCORN_CUDA(reduce_pass(0));
+            POPCORN_CUDA(reduce_pass(0, em));
             if (timing) POPCORN_CUDA(cudaEventRecord(e1, s));
             POPCORN_CUDA(launch_assign(b, plan, s));
             if (timing) {
@@ -770,6 +775,10 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
                 ev_r.push_back(e1);
                 ev_a.push_back(e1);
                 ev_a.push_back(e2);
+                if (use_sym) {
+                    ev_f.push_back(em);
+                    ev_f.push_back(e1);
+                }
             }
             launches += use_sym ? 3 : 2;
         }
@@ -791,7 +800,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         POPCORN_CUDA(cudaEventRecord(ev_l1, s));
     }
     // J(labels_out): reuses J of the last pass when it changed nothing
-    POPCORN_CUDA(reduce_pass(1));
+    POPCORN_CUDA(reduce_pass(1, nullptr));
     launches += use_sym ? 2 : 1;
     if (timing) {
         POPCORN_TRY(g_events.get(&ev_e1));
@@ -829,6 +838,9 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         info->kernel_launches = launches;
         info->tune_cache_hit = info->tune_candidates = 0;
         info->tune_ms = 0.0;
+        info->fold_ms = 0.0;
+        info->k_pass_used = 0;
+        info->reserved_info = 0;
         for (int q = 0; q < 4; ++q) info->schedule[q] = 0;
         // passes that did work (launches after convergence return at once)
         const bool eval_ran = !(hs.iter > 0 && hs.last_changed == 0);
@@ -846,7 +858,11 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
             for (size_t t = 0; t + 1 < ev_a.size() && t < 2 * (size_t)iters; t += 2) a += elapsed(ev_a[t], ev_a[t + 1]);
             info->reduce_ms = r;
             info->assign_ms = a;
+            double f = 0;
+            for (size_t t = 0; t + 1 < ev_f.size() && t < 2 * (size_t)iters; t += 2) f += elapsed(ev_f[t], ev_f[t + 1]);
+            info->fold_ms = f;
         }
+        info->k_pass_used = use_sym ? 1 : 2;
     }
     return POPCORN_OK;
 }
@@ -868,7 +884,7 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
     if (max_iter < 0) return fail(POPCORN_ERR_INVALID, "max_iter = %d < 0", max_iter);
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
     if (opt.autotune != 0 && opt.autotune != 1) return fail(POPCORN_ERR_INVALID, "options.autotune must be 0 or 1");
-    if (opt.k_pass != 0 && opt.k_pass != 1) return fail(POPCORN_ERR_INVALID, "options.k_pass must be 0 or 1");
+    if (opt.k_pass < 0 || opt.k_pass > 2) return fail(POPCORN_ERR_INVALID, "options.k_pass must be 0, 1 or 2");
     if (opt.reserved_pad != 0) return fail(POPCORN_ERR_INVALID, "options.reserved_pad must be 0");
     for (int r = 0; r < 4; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
@@ -1167,6 +1183,9 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         info->tune_cache_hit = tune_hit;
         info->tune_candidates = tune_cands;
         info->tune_ms = tune_ms;
+        info->fold_ms = 0.0;
+        info->k_pass_used = 0;
+        info->reserved_info = 0;
         info->schedule[0] = sched[0];
         info->schedule[1] = sched[1];
         info->schedule[2] = sched[2];

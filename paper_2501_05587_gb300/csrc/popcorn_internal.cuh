@@ -79,9 +79,10 @@ struct SymPlan {
 };
 SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin);
 cudaError_t configure_reduce_sym(int smem_optin);
-// err: set when a bounded wait of the stream kernel runs out.
+// err: set when a bounded wait of the stream kernel runs out; `between` (may be
+// null) is recorded on s after the stream kernel, before the fold.
 cudaError_t launch_reduce_sym(const struct PassBuffers& b, const SymPlan& p, int* err, int eval_only,
-                              cudaStream_t s);
+                              cudaStream_t s, cudaEvent_t between);
 
 // Upper-triangle block (bi, bj), bi <= bj, of number t when the T x T block
 // triangle is enumerated row by row (row b starts at b T - b (b - 1) / 2).  An

@@ -371,7 +371,8 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin) {
     return p;
 }
 
-cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, int eval_only, cudaStream_t s) {
+cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, int eval_only, cudaStream_t s,
+                              cudaEvent_t between) {
     CUtensorMap map;
     if (!make_tensor_map_2d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, const_cast<void*>(b.K), (uint64_t)b.n,
                             (uint64_t)b.n, (uint64_t)b.ldk * 4, kBoxCols, kB, CU_TENSOR_MAP_SWIZZLE_128B))
@@ -392,6 +393,7 @@ cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, 
     else reduce_sym_kernel<8><<<p.grid, kSymThreads, p.smem, s>>>(map, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (between && (e = cudaEventRecord(between, s)) != cudaSuccess) return e;
     FoldArgs f;
     f.n = b.n;
     f.k = b.k;

@@ -92,8 +92,8 @@ def test_invalid_arguments_rejected_before_any_cuda_call(pc):
     assert fit(opt=ctypes.byref(fp8k)) == 5                      # FP8 only without a stored K
     badk = pc._Options(0, 2, 1, 0, 0, 0, 0, 0, (ctypes.c_int64 * 4)())
     assert fit(opt=ctypes.byref(badk)) == 1                      # store_k must be 0 or 1
-    badp = pc._Options(0, 1, 1, 0, 0, 0, 2, 0, (ctypes.c_int64 * 4)())
-    assert fit(opt=ctypes.byref(badp)) == 1                      # k_pass must be 0 (full) or 1 (symmetric)
+    badp = pc._Options(0, 1, 1, 0, 0, 0, 3, 0, (ctypes.c_int64 * 4)())
+    assert fit(opt=ctypes.byref(badp)) == 1                      # k_pass must be 0 (auto), 1 or 2
     badpad = pc._Options(0, 1, 1, 0, 0, 0, 0, 5, (ctypes.c_int64 * 4)())
     assert fit(opt=ctypes.byref(badpad)) == 1                    # padding must be zero
     # kernel matrix: ldk must be a multiple of 4 and >= n

@@ -112,16 +112,23 @@ def test_symmetric_pass_is_deterministic(pc):
 
 def test_symmetric_pass_launches_and_fallback(pc):
     """k_pass = "symmetric" runs the stream and the fold (one launch more per pass than
-    the full square); above the cluster bound it falls back to the full-square pass,
+    the full square) and is what "auto" picks for an FP32 K with k <= 8; above the
+    cluster bound, or with a half-precision K, both fall back to the full-square pass,
     with results identical to it."""
     P = torch.from_numpy(synth.gaussian_blobs(600, 3, 6, seed=9, box=3.0)).cuda()
     lab = torch.from_numpy(synth.init_labels(600, 6, seed=19)).cuda()
     a = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_pass="symmetric")
     b = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_pass="full")
+    auto = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False)
+    assert a["info"]["k_pass_used"] == 1 and b["info"]["k_pass_used"] == 2 and auto["info"]["k_pass_used"] == 1
+    assert auto["objective"] == a["objective"]
     assert a["info"]["kernel_launches"] == b["info"]["kernel_launches"] + a["iterations"] + 1
+    h = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_storage="fp16")
+    assert h["info"]["k_pass_used"] == 2
     lab12 = torch.from_numpy(synth.init_labels(600, 12, seed=29)).cuda()
     c = pc.popcorn_fit(P, 12, _gauss(1.0), lab12, max_iter=5, check_convergence=False, k_pass="symmetric")
     d = pc.popcorn_fit(P, 12, _gauss(1.0), lab12, max_iter=5, check_convergence=False, k_pass="full")
     assert c["info"]["kernel_launches"] == d["info"]["kernel_launches"]
+    assert c["info"]["k_pass_used"] == 2
     assert np.array_equal(c["labels"].cpu().numpy(), d["labels"].cpu().numpy())
     assert c["objective"] == d["objective"]
