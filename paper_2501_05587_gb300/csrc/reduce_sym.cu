@@ -14,14 +14,16 @@
 // reduce_sym_kernel: persistent and warp-specialized, one CTA per SM, blocks
 //   taken in turn.  One producer thread TMA-loads each block (four 32-column
 //   boxes, 128-byte swizzle) and its 2 x 128 labels into a 3-deep ring.  The
-//   row group (4 warps, lane = row) reads a row as float4s, conflict-free
-//   under the swizzle, and multiplies each element into KB cluster sums with
-//   the one-hot weights of its column's label (the cluster bucketing of V
-//   written as FMAs: no data-dependent addressing, no atomics).  The column
-//   group (4 warps) takes the rows in steps of one: lane l holds columns
-//   4l..4l+3 and adds the row into KB sums per column with that row's weights;
-//   its 4 warps split the rows and their partials are added in warp order.
-//   Both groups write their sums straight to Spart.  Deterministic.
+//   row group (8 warps, a lane owns rows) reads its rows as float4 chunks,
+//   conflict-free under the swizzle, and multiplies each element into KB
+//   cluster sums with the one-hot weights of its column's label (the cluster
+//   bucketing of V written as FMAs: no data-dependent addressing, no atomics).
+//   The column group (8 warps) takes the rows one at a time: lane l holds
+//   columns 4l..4l+3 and adds the row into KB sums per column with that row's
+//   one-hot weight.  One-hot weights are made in registers from label bytes,
+//   so shared memory carries little besides the block itself.  Each group's
+//   warps split its work and their partials are added in warp order before
+//   the slot stores.  Deterministic.
 // sym_fold_kernel: S_ic = the T slots summed in slot order (float-float),
 //   written to slot 0, the per-block FP64 partials of sum_{i in L_c} S_ic (z,
 //   Eq. 14), and in its last block the pass finalization (||c||^2, J).  The
@@ -47,22 +49,20 @@ constexpr int kFoldThreads = 256;
 
 // Dynamic shared memory, in order: the block ring (1024-byte aligned for the
 // swizzle), the label ring (row labels, then column labels), the block
-// coordinates of each stage, the row group's one-hot weights (per 4-column
-// chunk and cluster, the chunk's 4 weights), the column group's (per row and
-// cluster, the weight twice), the two groups' partial sums, barriers and the
+// coordinates of each stage, the two groups' partial sums, barriers and the
 // abort flag.  KB <= 4 keeps 3 blocks in flight, KB = 8 two.
 constexpr int align128(int x) { return (x + 127) & ~127; }
 
 template <int KB>
 struct SymLayout {
     static constexpr int stages = KB <= 4 ? 3 : 2;
+    static constexpr int rpl = KB <= 4 ? 4 : 2;      // rows per lane in the row group
+    static constexpr int nparts = 8 * rpl / 4;        // column parts of the row group (8 warps)
     static constexpr int tiles = 0;
     static constexpr int labels = tiles + stages * kTileBytes;
     static constexpr int ij = align128(labels + stages * 2 * kB);
-    static constexpr int wt = align128(ij + stages * 8);
-    static constexpr int wd = align128(wt + kB * KB * 4);
-    static constexpr int rowpart = align128(wd + kB * KB * 8);
-    static constexpr int colpart = align128(rowpart + 4 * KB * kB * 4);
+    static constexpr int rowpart = align128(ij + stages * 8);
+    static constexpr int colpart = align128(rowpart + nparts * KB * kB * 4);
     static constexpr int bars = align128(colpart + 8 * KB * kB * 4);
     static constexpr int flag = bars + 2 * stages * 8;
     static constexpr int bytes = flag + 16 + 1024;   // + slack for the 1024-byte alignment
@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(kSymThreads, 1)
     const int u = threadIdx.x & (kGroup - 1);   // thread within its group
     const int bar_id = rowg ? kBarRows : kBarCols;
     const int gw = u >> 5;                      // warp within its group
-    const int xr = lane & 7;                    // row mod 8 of every row this lane reads (row group)
+    // A group's barrier at the top of block t + 1 also orders the reads of its
+    // partials (block t) before their next writes.
     for (long long t = 0; t < nmine; ++t) {
         const int s = (int)(t % S);
         const bool ok = tc::mbar_wait(full_bar(s), (uint32_t)(t / S) & 1u, abort_flag, a.err);
@@ -164,44 +165,38 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         const unsigned char* tile = smem + L::tiles + (size_t)s * kTileBytes;
         const uint8_t* lab = smem + L::labels + s * 2 * kB;
         if (rowg) {
-            // row sums of block I over the columns of block J -> slot J.  The columns
-            // are split into NPART parts of BOXES boxes; a part's rows go to WPP warps,
-            // RPL rows a lane (lane, lane + 32).
-            constexpr int RPL = KB <= 4 ? 2 : 1;      // two rows per lane halve the weight reads
-            constexpr int NPART = 2 * RPL, BOXES = 4 / NPART, WPP = 4 / RPL;
-            float* wt = reinterpret_cast<float*>(smem + L::wt);
-            if (u < kB) {
-                const int l = J * kB + u < n ? (int)lab[kB + u] : -1;
-#pragma unroll
-                for (int c = 0; c < KB; ++c) wt[((u >> 2) * KB + c) * 4 + (u & 3)] = l == c ? 1.f : 0.f;
-            }
-            tc::named_bar<kGroup>(kBarRows);
-            const int part = gw / WPP;
-            const int r0 = 32 * RPL * (gw % WPP) + lane;
-            unsigned long long sa[RPL][KB], sb[RPL][KB];   // columns 4m, 4m + 1 and 4m + 2, 4m + 3
+            // row sums of block I over the columns of block J -> slot J.  The 32 four-column
+            // chunks are split into NPART parts; a part's 128 rows go to WPR warps, RPL rows
+            // a lane (lane + 32 e).  A chunk's one-hot weights are built in registers from
+            // its 4 labels (one broadcast word), pairs of columns per fma.rn.f32x2.
+            constexpr int RPL = L::rpl, NPART = L::nparts, WPR = 4 / RPL, CH = 32 / NPART;
+            const int part = gw / WPR;
+            const int r0 = 32 * RPL * (gw % WPR) + lane;
+            const int xr = lane & 7;             // every row this lane reads is r0 mod 8
+            const int cols_left = n - J * kB;    // columns of block J inside K
+            unsigned long long acc[RPL][KB];
 #pragma unroll
             for (int e = 0; e < RPL; ++e)
 #pragma unroll
-                for (int c = 0; c < KB; ++c) sa[e][c] = sb[e][c] = 0ull;
-#pragma unroll
-            for (int bx = 0; bx < BOXES; ++bx) {
-                const int box_id = part * BOXES + bx;
-                const unsigned char* box = tile + box_id * kBoxBytes;
-                const ulonglong2* w2 = reinterpret_cast<const ulonglong2*>(wt) + box_id * 8 * KB;
+                for (int c = 0; c < KB; ++c) acc[e][c] = 0ull;
 #pragma unroll 2
-                for (int j = 0; j < 8; ++j) {
-                    ulonglong2 v[RPL];
+            for (int jj = 0; jj < CH; ++jj) {
+                const int q = part * CH + jj;    // chunk: columns 4 q .. 4 q + 3
+                const unsigned char* box = tile + (q >> 3) * kBoxBytes;
+                const uint32_t lw = *reinterpret_cast<const uint32_t*>(lab + kB + 4 * q);
+                int l[4];
 #pragma unroll
-                    for (int e = 0; e < RPL; ++e) v[e] = box_ld(box, r0 + 32 * e, j, xr);
+                for (int x = 0; x < 4; ++x) l[x] = 4 * q + x < cols_left ? (int)((lw >> (8 * x)) & 0xffu) : -1;
+                ulonglong2 v[RPL];
 #pragma unroll
-                    for (int c = 0; c < KB; ++c) {
-                        const ulonglong2 w = w2[j * KB + c];
+                for (int e = 0; e < RPL; ++e) v[e] = box_ld(box, r0 + 32 * e, q & 7, xr);
 #pragma unroll
-                        for (int e = 0; e < RPL; ++e) {
-                            sa[e][c] = tc::f2fma(v[e].x, w.x, sa[e][c]);
-                            sb[e][c] = tc::f2fma(v[e].y, w.y, sb[e][c]);
-                        }
-                    }
+                for (int c = 0; c < KB; ++c) {
+                    const unsigned long long w01 = tc::f2pack(l[0] == c ? 1.f : 0.f, l[1] == c ? 1.f : 0.f);
+                    const unsigned long long w23 = tc::f2pack(l[2] == c ? 1.f : 0.f, l[3] == c ? 1.f : 0.f);
+#pragma unroll
+                    for (int e = 0; e < RPL; ++e)
+                        acc[e][c] = tc::f2fma(v[e].y, w23, tc::f2fma(v[e].x, w01, acc[e][c]));
                 }
             }
             __syncwarp();
@@ -212,7 +207,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
 #pragma unroll
                 for (int e = 0; e < RPL; ++e) {
                     float x, y;
-                    tc::f2unpack(tc::f2add(sa[e][c], sb[e][c]), x, y);
+                    tc::f2unpack(acc[e][c], x, y);
                     prt[(part * KB + c) * kB + r0 + 32 * e] = x + y;
                 }
             tc::named_bar<kGroup>(kBarRows);
@@ -222,7 +217,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                     const float* pp = prt + c * kB + u;
                     float v = pp[0];
 #pragma unroll
-                    for (int q = 1; q < NPART; ++q) v += pp[q * KB * kB];
+                    for (int p = 1; p < NPART; ++p) v += pp[p * KB * kB];
                     tc::st_hint(out + (size_t)c * n, v, keep);
                 }
             }
@@ -232,31 +227,30 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             if (lane == 0) tc::mbar_arrive(empty_bar(s));
         } else {
             // column sums of block J over the rows of block I -> slot I.  Warp gw: rows
-            // 16 gw .. 16 gw + 15; lane: columns 4 lane .. 4 lane + 3.
-            unsigned long long* wd = reinterpret_cast<unsigned long long*>(smem + L::wd);
-            if (u < kB) {
-                const int l = I * kB + u < n ? (int)lab[u] : -1;
-#pragma unroll
-                for (int c = 0; c < KB; ++c) wd[u * KB + c] = l == c ? tc::f2pack(1.f, 1.f) : 0ull;
-            }
-            tc::named_bar<kGroup>(kBarCols);
+            // 16 gw .. 16 gw + 15; lane: columns 4 lane .. 4 lane + 3.  A row's one-hot
+            // weight comes from its label (a broadcast word per 4 rows), in registers.
             const unsigned char* box = tile + (lane >> 3) * kBoxBytes;
             const int j = lane & 7;
+            const int rows_left = n - I * kB;
             unsigned long long p[KB], q[KB];
 #pragma unroll
             for (int c = 0; c < KB; ++c) p[c] = q[c] = 0ull;
-#pragma unroll 4
-            for (int rr = 0; rr < 16; ++rr) {
-                const int r = 16 * gw + rr;
-                const ulonglong2 v = box_ld(box, r, j, rr & 7);
-                const ulonglong2* wr = reinterpret_cast<const ulonglong2*>(wd + r * KB);
+            const unsigned long long one2 = tc::f2pack(1.f, 1.f);
 #pragma unroll
-                for (int c2 = 0; c2 < KB / 2; ++c2) {
-                    const ulonglong2 w = wr[c2];
-                    p[2 * c2] = tc::f2fma(v.x, w.x, p[2 * c2]);
-                    q[2 * c2] = tc::f2fma(v.y, w.x, q[2 * c2]);
-                    p[2 * c2 + 1] = tc::f2fma(v.x, w.y, p[2 * c2 + 1]);
-                    q[2 * c2 + 1] = tc::f2fma(v.y, w.y, q[2 * c2 + 1]);
+            for (int r4 = 0; r4 < 4; ++r4) {
+                const int rb = 16 * gw + 4 * r4;
+                const uint32_t lw = *reinterpret_cast<const uint32_t*>(lab + rb);
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const int r = rb + x;
+                    const int l = r < rows_left ? (int)((lw >> (8 * x)) & 0xffu) : -1;
+                    const ulonglong2 v = box_ld(box, r, j, r & 7);
+#pragma unroll
+                    for (int c = 0; c < KB; ++c) {
+                        const unsigned long long w = l == c ? one2 : 0ull;
+                        p[c] = tc::f2fma(v.x, w, p[c]);
+                        q[c] = tc::f2fma(v.y, w, q[c]);
+                    }
                 }
             }
             __syncwarp();
