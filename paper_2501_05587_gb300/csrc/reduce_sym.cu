@@ -15,15 +15,14 @@
 //   taken in turn.  One producer thread TMA-loads each block (four 32-column
 //   boxes, 128-byte swizzle) and its 2 x 128 labels into a 3-deep ring.  The
 //   row group (8 warps, a lane owns rows) reads its rows as float4 chunks,
-//   conflict-free under the swizzle, and multiplies each element into KB
-//   cluster sums with the one-hot weights of its column's label (the cluster
-//   bucketing of V written as FMAs: no data-dependent addressing, no atomics).
-//   The column group (8 warps) takes the rows one at a time: lane l holds
-//   columns 4l..4l+3 and adds the row into KB sums per column with that row's
-//   one-hot weight.  One-hot weights are made in registers from label bytes,
-//   so shared memory carries little besides the block itself.  Each group's
-//   warps split its work and their partials are added in warp order before
-//   the slot stores.  Deterministic.
+//   conflict-free under the swizzle, and adds each element to the sum of its
+//   column's cluster.  The column group (8 warps) takes the rows one at a time:
+//   lane l holds columns 4l..4l+3 and adds the row to the sums of the row's
+//   cluster.  Either way the cluster is a label byte that is the same for the
+//   whole warp, so the bucketing of V is a uniform branch: no data-dependent
+//   addressing, no atomics, and shared memory carries little besides the block
+//   itself.  Each group's warps split its work and their partials are added in
+//   warp order before the slot stores.  Deterministic.
 // sym_fold_kernel: S_ic = the T slots summed in slot order (float-float),
 //   written to slot 0, the per-block FP64 partials of sum_{i in L_c} S_ic (z,
 //   Eq. 14), and in its last block the pass finalization (||c||^2, J).  The
@@ -85,11 +84,35 @@ __device__ __forceinline__ ulonglong2 box_ld(const unsigned char* box, int r, in
     return *reinterpret_cast<const ulonglong2*>(box + r * 128 + ((j ^ xr) << 4));
 }
 
+// acc[c] += v for the one c equal to the warp-uniform label l (nothing for l
+// outside [0, KB)): a uniform branch, no one-hot arithmetic
+template <int KB, typename T, typename F>
+__device__ __forceinline__ void add_to_cluster(int l, T (&acc)[KB], F&& add) {
+    switch (l) {
+#define POPCORN_SYM_CASE(c) \
+    case c:                 \
+        if (c < KB) add(acc[c < KB ? c : 0]); \
+        break;
+        POPCORN_SYM_CASE(0)
+        POPCORN_SYM_CASE(1)
+        POPCORN_SYM_CASE(2)
+        POPCORN_SYM_CASE(3)
+        POPCORN_SYM_CASE(4)
+        POPCORN_SYM_CASE(5)
+        POPCORN_SYM_CASE(6)
+        POPCORN_SYM_CASE(7)
+#undef POPCORN_SYM_CASE
+        default:
+            break;
+    }
+}
+
 template <int KB>
 __global__ void __launch_bounds__(kSymThreads, 1)
     reduce_sym_kernel(const __grid_constant__ CUtensorMap map, SymArgs a) {
     using L = SymLayout<KB>;
     constexpr int S = L::stages;
+    static_assert(KB <= 8, "add_to_cluster has 8 cases");
     if (pass_skip(a.st, a.eval_only)) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -174,29 +197,34 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             const int r0 = 32 * RPL * (gw % WPR) + lane;
             const int xr = lane & 7;             // every row this lane reads is r0 mod 8
             const int cols_left = n - J * kB;    // columns of block J inside K
-            unsigned long long acc[RPL][KB];
+            float acc[KB][RPL];   // per cluster, this lane's rows
 #pragma unroll
             for (int e = 0; e < RPL; ++e)
 #pragma unroll
-                for (int c = 0; c < KB; ++c) acc[e][c] = 0ull;
+                for (int c = 0; c < KB; ++c) acc[c][e] = 0.f;
 #pragma unroll 2
             for (int jj = 0; jj < CH; ++jj) {
                 const int q = part * CH + jj;    // chunk: columns 4 q .. 4 q + 3
                 const unsigned char* box = tile + (q >> 3) * kBoxBytes;
                 const uint32_t lw = *reinterpret_cast<const uint32_t*>(lab + kB + 4 * q);
-                int l[4];
+                float4 v[RPL];
 #pragma unroll
-                for (int x = 0; x < 4; ++x) l[x] = 4 * q + x < cols_left ? (int)((lw >> (8 * x)) & 0xffu) : -1;
-                ulonglong2 v[RPL];
+                for (int e = 0; e < RPL; ++e) {
+                    const ulonglong2 raw = box_ld(box, r0 + 32 * e, q & 7, xr);
+                    v[e] = *reinterpret_cast<const float4*>(&raw);
+                }
 #pragma unroll
-                for (int e = 0; e < RPL; ++e) v[e] = box_ld(box, r0 + 32 * e, q & 7, xr);
+                for (int x = 0; x < 4; ++x) {
+                    const int l = 4 * q + x < cols_left ? (int)((lw >> (8 * x)) & 0xffu) : -1;
+                    float col[RPL];
 #pragma unroll
-                for (int c = 0; c < KB; ++c) {
-                    const unsigned long long w01 = tc::f2pack(l[0] == c ? 1.f : 0.f, l[1] == c ? 1.f : 0.f);
-                    const unsigned long long w23 = tc::f2pack(l[2] == c ? 1.f : 0.f, l[3] == c ? 1.f : 0.f);
+                    for (int e = 0; e < RPL; ++e) col[e] = (&v[e].x)[x];
+                    // the column's cluster takes the element of each of this lane's rows (one
+                    // uniform branch per column)
+                    add_to_cluster<KB>(l, acc, [&](float (&dst)[RPL]) {
 #pragma unroll
-                    for (int e = 0; e < RPL; ++e)
-                        acc[e][c] = tc::f2fma(v[e].y, w23, tc::f2fma(v[e].x, w01, acc[e][c]));
+                        for (int e = 0; e < RPL; ++e) dst[e] += col[e];
+                    });
                 }
             }
             __syncwarp();
@@ -206,9 +234,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             for (int c = 0; c < KB; ++c)
 #pragma unroll
                 for (int e = 0; e < RPL; ++e) {
-                    float x, y;
-                    tc::f2unpack(acc[e][c], x, y);
-                    prt[(part * KB + c) * kB + r0 + 32 * e] = x + y;
+                    prt[(part * KB + c) * kB + r0 + 32 * e] = acc[c][e];
                 }
             tc::named_bar<kGroup>(kBarRows);
             if (u < kB && I * kB + u < n) {
@@ -232,25 +258,24 @@ __global__ void __launch_bounds__(kSymThreads, 1)
             const unsigned char* box = tile + (lane >> 3) * kBoxBytes;
             const int j = lane & 7;
             const int rows_left = n - I * kB;
-            unsigned long long p[KB], q[KB];
+            unsigned long long pq[KB][2];   // columns (4 lane, 4 lane + 1) and (4 lane + 2, 4 lane + 3)
 #pragma unroll
-            for (int c = 0; c < KB; ++c) p[c] = q[c] = 0ull;
-            const unsigned long long one2 = tc::f2pack(1.f, 1.f);
+            for (int c = 0; c < KB; ++c) pq[c][0] = pq[c][1] = 0ull;
 #pragma unroll
             for (int r4 = 0; r4 < 4; ++r4) {
                 const int rb = 16 * gw + 4 * r4;
                 const uint32_t lw = *reinterpret_cast<const uint32_t*>(lab + rb);
+                ulonglong2 v[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) v[x] = box_ld(box, rb + x, j, (rb + x) & 7);
 #pragma unroll
                 for (int x = 0; x < 4; ++x) {
-                    const int r = rb + x;
-                    const int l = r < rows_left ? (int)((lw >> (8 * x)) & 0xffu) : -1;
-                    const ulonglong2 v = box_ld(box, r, j, r & 7);
-#pragma unroll
-                    for (int c = 0; c < KB; ++c) {
-                        const unsigned long long w = l == c ? one2 : 0ull;
-                        p[c] = tc::f2fma(v.x, w, p[c]);
-                        q[c] = tc::f2fma(v.y, w, q[c]);
-                    }
+                    const int l = rb + x < rows_left ? (int)((lw >> (8 * x)) & 0xffu) : -1;
+                    // the row's cluster takes the row
+                    add_to_cluster<KB>(l, pq, [&](unsigned long long (&dst)[2]) {
+                        dst[0] = tc::f2add(dst[0], v[x].x);
+                        dst[1] = tc::f2add(dst[1], v[x].y);
+                    });
                 }
             }
             __syncwarp();
@@ -260,8 +285,8 @@ __global__ void __launch_bounds__(kSymThreads, 1)
 #pragma unroll
             for (int c = 0; c < KB; ++c) {
                 float x0, y0, x1, y1;
-                tc::f2unpack(p[c], x0, y0);
-                tc::f2unpack(q[c], x1, y1);
+                tc::f2unpack(pq[c][0], x0, y0);
+                tc::f2unpack(pq[c][1], x1, y1);
                 *reinterpret_cast<float4*>(part + (gw * KB + c) * kB + 4 * lane) = make_float4(x0, y0, x1, y1);
             }
             tc::named_bar<kGroup>(kBarCols);
