@@ -408,11 +408,17 @@ __device__ __forceinline__ void zreduce_body(const ZArgs& a, int block, int nblo
     lab_s[threadIdx.x] = l;
     val_s[threadIdx.x] = v;
     __syncthreads();
-    for (int c = threadIdx.x; c < a.k; c += blockDim.x) {
-        double t = 0.0;
-        for (int r = 0; r < kZReduceRows; ++r)
-            if (lab_s[r] == c) t += val_s[r];
-        a.zpart[(size_t)block * a.k + c] = t;
+    // warp w: clusters w, w + 32, ...; lanes stride the rows, a butterfly adds them (fixed order)
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int c = warp; c < a.k; c += nw) {
+            double t = 0.0;
+            for (int r = lane; r < kZReduceRows; r += 32)
+                if (lab_s[r] == c) t += val_s[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) a.zpart[(size_t)block * a.k + c] = t;
+        }
     }
     __threadfence();
     __syncthreads();

@@ -61,26 +61,38 @@ __device__ __forceinline__ float butterfly(const float (&acc)[KB], int lane) {
     return v[0];
 }
 
-// Last block of a pass's reduction, all its threads: sum the per-block FP64
-// partials of sum_{i in L_c} S_ic in block order, then ||c_c||^2 =
+// Last block of a pass's reduction, all its threads (a multiple of 32): sum the
+// per-block FP64 partials of sum_{i in L_c} S_ic, then ||c_c||^2 =
 // (1/m_c^2) sum_{i in L_c} S_ic (Eq. 13/14), 1/m_c, and
-// J = trace K - sum_c (1/m_c) sum_{i in L_c} S_ic.
+// J = trace K - sum_c (1/m_c) sum_{i in L_c} S_ic.  Warp w takes clusters
+// w, w + nw, ...; its lanes split the blocks and a butterfly adds them, so the
+// partials are read 32 at a time rather than one after another.  Every order
+// is fixed: the result is deterministic.
 __device__ inline void finalize_pass(const double* zpart, int nblocks, int k, const int32_t* counts, double* zsum,
                                      double* cnorm, double* invm, LoopState* st, double* J_hist, int eval_only) {
+    __shared__ double jpart[32];
     const int32_t* m = counts + (size_t)(st->iter & 1) * k;
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double jw = 0.0;
+    for (int c = warp; c < k; c += nw) {
         double t = 0.0;
-        for (int b = 0; b < nblocks; ++b) t += __ldcg(zpart + (size_t)b * k + c);
+        for (int b = lane; b < nblocks; b += 32) t += __ldcg(zpart + (size_t)b * k + c);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         const double mc = (double)__ldcg(m + c);
         const double inv = mc > 0 ? 1.0 / mc : 0.0;
-        zsum[c] = t;
-        invm[c] = inv;
-        cnorm[c] = t * inv * inv;
+        if (lane == 0) {
+            zsum[c] = t;
+            invm[c] = inv;
+            cnorm[c] = t * inv * inv;
+        }
+        jw += t * inv;
     }
+    if (lane == 0 && warp < 32) jpart[warp] = jw;
     __syncthreads();
     if (threadIdx.x == 0) {
         double J = st->trace;
-        for (int c = 0; c < k; ++c) J -= __ldcg(zsum + c) * __ldcg(invm + c);
+        for (int w = 0; w < nw && w < 32; ++w) J -= jpart[w];
         if (eval_only) {
             st->J_eval = J;
         } else {
