@@ -181,11 +181,12 @@ popcorn_status check_kernel(const popcorn_kernel& kern, KernParams* kp) {
 // K = kappa(P P^T) on stream s.  FP32: CUDA-core tiles.  BF16 / BF16X3: tcgen05
 // tiles; their operand copies come from `ws`, and *err (device) reports a
 // timed-out wait inside the kernel.
+// packed: the FP32 build writes the block-packed upper triangle (symmetric pass only).
 popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, const KernParams& kp,
                                    int precision, void* K, int64_t ldk, int k_storage, float* kdiag, Workspace* ws,
-                                   int* err, int num_sms, cudaStream_t s, int* launches) {
+                                   int* err, int num_sms, cudaStream_t s, int* launches, bool packed = false) {
     if (precision == POPCORN_FP32) {
-        POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, k_storage, kdiag, s, launches));
+        POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, k_storage, kdiag, s, launches, packed));
         return POPCORN_OK;
     }
     if (k_storage != POPCORN_K_FP32)
@@ -664,6 +665,10 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     SymPlan sym{};
     if (ks == POPCORN_K_FP32 && opt.k_pass != 2) sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin);
     const bool use_sym = sym.ok;
+    // With the symmetric pass and the FP32 build, K is stored block-packed: the upper triangle
+    // of 128 x 128 tiles only (half the memory; each value written once).
+    sym.packed = use_sym && opt.precision == POPCORN_FP32;
+    const size_t k_bytes = sym.packed ? (size_t)sym.items * 128 * 128 * 4 : (size_t)ni * (size_t)ldk * kelem;
     const int nslots = use_sym ? sym.T : plan.nseg;
     if (use_sym) plan.nseg = 1;             // the assignment reads the folded slot only
     const bool timing = opt.timing != 0;
@@ -694,7 +699,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     PassBuffers b{};
     unsigned char* K;
     float* kdiag;
-    POPCORN_TRY(ws.alloc(&K, (size_t)ni * (size_t)ldk * kelem, "kernel matrix"));
+    POPCORN_TRY(ws.alloc(&K, k_bytes, "kernel matrix"));
     POPCORN_TRY(ws.alloc(&kdiag, (size_t)ni, "diag(K)"));
     const size_t nlab = ((size_t)ni + 15) & ~(size_t)15;
     const int hist_len = max_iter > 0 ? max_iter : 1;
@@ -733,7 +738,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     POPCORN_CUDA(cudaMemsetAsync(b.counts, 0, 2 * (size_t)k * sizeof(int32_t), s));
     POPCORN_CUDA(launch_init_state(b.st, max_iter, opt.check_convergence ? 1 : 0, tol, s));
     POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, ks, kdiag, &ws, &b.st->wait_err,
-                                    dev->sms, s, &launches));
+                                    dev->sms, s, &launches, sym.packed));
     POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
     POPCORN_CUDA(launch_init_labels(Ld, ni, k, b.lab32, b.lab8, b.counts, b.st, s));
     launches += 3;

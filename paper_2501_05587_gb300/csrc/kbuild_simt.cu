@@ -76,7 +76,7 @@ struct TileSmem {
     float Bs[2][KC][LDS];
 };
 
-template <int KIND, typename TK = float, bool ONE_SLICE = false>
+template <int KIND, typename TK = float, bool ONE_SLICE = false, bool PACKED = false>
 __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, int d, int64_t ldp,
                                             const KernParams& kp, TK* __restrict__ K, int64_t ldk,
                                             float* __restrict__ kdiag, int T, long long tile, TileSmem& sm) {
@@ -186,6 +186,26 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         }
     }
 
+    if constexpr (PACKED) {
+        // block-packed upper triangle: tile t is 64 KB at K + t * 128 * 128, as four boxes of
+        // 128 rows x 32 columns with the 128-byte swizzle (16-byte chunk j of row r stored at
+        // chunk j ^ (r mod 8)), the layout the symmetric pass loads with one bulk copy.  The
+        // whole tile is written: entries past n are finite and no pass reads them.
+        static_assert(sizeof(TK) == 4, "packed storage holds FP32 K");
+        float* B = reinterpret_cast<float*>(K) + (size_t)tile * (TILE * TILE);
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int rl = ty * 4 + (x & 3) + 64 * (x >> 2);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cl = 64 * h + tx * 4;
+                const int j = (cl & 31) >> 2;
+                *reinterpret_cast<float4*>(B + (cl >> 5) * (TILE * 32) + rl * 32 + ((j ^ (rl & 7)) << 2)) =
+                    make_float4(acc[x][4 * h], acc[x][4 * h + 1], acc[x][4 * h + 2], acc[x][4 * h + 3]);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
         int r = row0 + ty * 4 + (x & 3) + 64 * (x >> 2);
@@ -219,26 +239,26 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
     }
 }
 
-template <int KIND, typename TK>
+template <int KIND, typename TK, bool PACKED>
 __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
                                                           KernParams kp, TK* __restrict__ K, int64_t ldk,
                                                           float* __restrict__ kdiag, int T) {
     __shared__ __align__(16) TileSmem sm;
-    kbuild_tile<KIND, TK>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm);
+    kbuild_tile<KIND, TK, false, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm);
 }
 
 // d <= KC: the depth loop is one slice, so no next slice is held in registers;
 // the lighter kernel fits two blocks per SM, which overlaps one block's stores
 // with the other's loads (small d is store-bound)
-template <int KIND, typename TK>
+template <int KIND, typename TK, bool PACKED>
 __global__ void __launch_bounds__(256, 2) kbuild_simt_small_kernel(const float* __restrict__ P, int n, int d,
                                                                    int64_t ldp, KernParams kp, TK* __restrict__ K,
                                                                    int64_t ldk, float* __restrict__ kdiag, int T) {
     __shared__ __align__(16) TileSmem sm;
-    kbuild_tile<KIND, TK, true>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm);
+    kbuild_tile<KIND, TK, true, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm);
 }
 
-template <typename TK>
+template <typename TK, bool PACKED>
 cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernParams kp, TK* K, int64_t ldk,
                               float* kdiag, cudaStream_t s) {
     const int T = (n + TILE - 1) / TILE;
@@ -248,14 +268,15 @@ cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernPar
     if (d <= KC) {
         switch (kp.kind) {
             case POPCORN_LINEAR:
-                kbuild_simt_small_kernel<POPCORN_LINEAR, TK><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+                kbuild_simt_small_kernel<POPCORN_LINEAR, TK, PACKED>
+                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
                 break;
             case POPCORN_POLYNOMIAL:
-                kbuild_simt_small_kernel<POPCORN_POLYNOMIAL, TK>
+                kbuild_simt_small_kernel<POPCORN_POLYNOMIAL, TK, PACKED>
                     <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
                 break;
             default:
-                kbuild_simt_small_kernel<POPCORN_GAUSSIAN, TK>
+                kbuild_simt_small_kernel<POPCORN_GAUSSIAN, TK, PACKED>
                     <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
                 break;
         }
@@ -263,13 +284,14 @@ cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernPar
     }
     switch (kp.kind) {
         case POPCORN_LINEAR:
-            kbuild_simt_kernel<POPCORN_LINEAR, TK><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            kbuild_simt_kernel<POPCORN_LINEAR, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
             break;
         case POPCORN_POLYNOMIAL:
-            kbuild_simt_kernel<POPCORN_POLYNOMIAL, TK><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            kbuild_simt_kernel<POPCORN_POLYNOMIAL, TK, PACKED>
+                <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
             break;
         default:
-            kbuild_simt_kernel<POPCORN_GAUSSIAN, TK><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            kbuild_simt_kernel<POPCORN_GAUSSIAN, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
             break;
     }
     return cudaGetLastError();
@@ -308,13 +330,18 @@ cudaError_t launch_batched_kbuild_simt(const BatchInst* dI, const BatchPlan& bp,
 }
 
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp, void* K, int64_t ldk,
-                               int k_storage, float* kdiag, cudaStream_t s, int* launches) {
+                               int k_storage, float* kdiag, cudaStream_t s, int* launches, bool packed) {
     if (launches) ++*launches;
+    if (packed) {
+        if (k_storage != POPCORN_K_FP32) return cudaErrorInvalidValue;
+        return launch_simt_typed<float, true>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
+    }
     if (k_storage == POPCORN_K_FP16)
-        return launch_simt_typed(P, n, d, ldp, kp, static_cast<__half*>(K), ldk, kdiag, s);
+        return launch_simt_typed<__half, false>(P, n, d, ldp, kp, static_cast<__half*>(K), ldk, kdiag, s);
     if (k_storage == POPCORN_K_BF16)
-        return launch_simt_typed(P, n, d, ldp, kp, static_cast<__nv_bfloat16*>(K), ldk, kdiag, s);
-    return launch_simt_typed(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
+        return launch_simt_typed<__nv_bfloat16, false>(P, n, d, ldp, kp, static_cast<__nv_bfloat16*>(K), ldk, kdiag,
+                                                       s);
+    return launch_simt_typed<float, false>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
 }
 
 }  // namespace popcorn

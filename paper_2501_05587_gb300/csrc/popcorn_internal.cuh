@@ -76,6 +76,7 @@ struct SymPlan {
     int grid;           // persistent CTAs of the stream kernel
     int fold_blocks;    // row chunks of the fold (zpart rows)
     size_t smem;
+    bool packed;        // K is block-packed (set by the caller with the K build it chose)
 };
 SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin);
 cudaError_t configure_reduce_sym(int smem_optin);
@@ -106,8 +107,12 @@ void set_error_message(const char* msg);
 
 // ---- K build (kbuild_simt.cu) ------------------------------------------------
 // K is float, __half or __nv_bfloat16 by k_storage (popcorn_k_storage); ldk in elements.
+// packed: FP32 K as the block-packed upper triangle of 128 x 128 tiles (tile t of
+// the row-by-row triangle at K + t * 16384 floats, swizzled boxes: see
+// kbuild_simt.cu), read by the symmetric pass; ldk is then unused.
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp,
-                               void* K, int64_t ldk, int k_storage, float* kdiag, cudaStream_t s, int* launches);
+                               void* K, int64_t ldk, int k_storage, float* kdiag, cudaStream_t s, int* launches,
+                               bool packed = false);
 
 // ---- K build on tensor cores (kbuild_tc.cu) ---------------------------------
 // Workspace bytes for the BF16 operand copies and row norms.

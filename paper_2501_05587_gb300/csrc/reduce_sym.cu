@@ -12,8 +12,11 @@
 // is written exactly once.
 //
 // reduce_sym_kernel: persistent and warp-specialized, one CTA per SM, blocks
-//   taken in turn.  One producer thread TMA-loads each block (four 32-column
-//   boxes, 128-byte swizzle) and its 2 x 128 labels into a 3-deep ring.  The
+//   taken in turn.  One producer thread loads each block (four 32-column
+//   boxes, 128-byte swizzle) and its 2 x 128 labels into a 3-deep ring: four
+//   TMA tensor loads from a full-square K, or one 64 KB bulk copy when K is
+//   stored block-packed (upper triangle only, each block already in the box
+//   layout: half the memory, and a K build that writes each value once).  The
 //   row group (8 warps, a lane owns rows) reads its rows as float4 chunks,
 //   conflict-free under the swizzle, and adds each element to the sum of its
 //   column's cluster.  The column group (8 warps) takes the rows one at a time:
@@ -27,6 +30,8 @@
 //   written to slot 0, the per-block FP64 partials of sum_{i in L_c} S_ic (z,
 //   Eq. 14), and in its last block the pass finalization (||c||^2, J).  The
 //   assignment then reads slot 0 alone.
+#include <cstring>
+
 #include "popcorn_internal.cuh"
 #include "stream_common.cuh"
 #include "tc_common.cuh"
@@ -68,6 +73,7 @@ struct SymLayout {
 };
 
 struct SymArgs {
+    const float* Kp;           // block-packed K (one bulk copy per block), or null: TMA from the full square
     int64_t ldk;
     int n, k, T, nlab;
     long long items;
@@ -150,10 +156,16 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 const int lbI = min(kB, a.nlab - I * kB), lbJ = min(kB, a.nlab - J * kB);
                 tc::mbar_arrive_expect_tx(full_bar(s), (uint32_t)(kTileBytes + lbI + lbJ));
                 const uint32_t dst = sbase + L::tiles + (uint32_t)s * kTileBytes;
+                if (a.Kp) {
+                    // the block is stored in exactly the swizzled box layout the loads below produce
+                    const long long tri = (long long)I * a.T - (long long)I * (I - 1) / 2 + (J - I);
+                    tc::bulk_load_1d_hint(dst, a.Kp + tri * (kB * kB), (uint32_t)kTileBytes, full_bar(s), stream_once);
+                } else {
 #pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    tc::tma_load_2d_hint(dst + b * kBoxBytes, &map, J * kB + kBoxCols * b, I * kB, full_bar(s),
-                                         stream_once);
+                    for (int b = 0; b < 4; ++b)
+                        tc::tma_load_2d_hint(dst + b * kBoxBytes, &map, J * kB + kBoxCols * b, I * kB, full_bar(s),
+                                             stream_once);
+                }
                 const uint32_t ldst = sbase + L::labels + (uint32_t)s * 2 * kB;
                 tc::bulk_load_1d(ldst, a.lab8 + (size_t)I * kB, (uint32_t)lbI, full_bar(s));
                 tc::bulk_load_1d(ldst + kB, a.lab8 + (size_t)J * kB, (uint32_t)lbJ, full_bar(s));
@@ -393,10 +405,13 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin) {
 cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, int eval_only, cudaStream_t s,
                               cudaEvent_t between) {
     CUtensorMap map;
-    if (!make_tensor_map_2d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, const_cast<void*>(b.K), (uint64_t)b.n,
-                            (uint64_t)b.n, (uint64_t)b.ldk * 4, kBoxCols, kB, CU_TENSOR_MAP_SWIZZLE_128B))
+    memset(&map, 0, sizeof map);
+    if (!p.packed && !make_tensor_map_2d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, const_cast<void*>(b.K),
+                                         (uint64_t)b.n, (uint64_t)b.n, (uint64_t)b.ldk * 4, kBoxCols, kB,
+                                         CU_TENSOR_MAP_SWIZZLE_128B))
         return cudaErrorInvalidValue;
     SymArgs a;
+    a.Kp = p.packed ? static_cast<const float*>(b.K) : nullptr;
     a.ldk = b.ldk;
     a.n = b.n;
     a.k = b.k;
