@@ -151,13 +151,7 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2) reduce_kernel(ReduceA
     float* zwh = zhi + (size_t)warp * k;
     float* zwl = zlo + (size_t)warp * k;
 
-    auto scatter = [&](uint32_t l, float x) {
-#ifdef POPCORN_REDUCE_ATOMIC
-        atomicAdd(accl + l * 32, x);
-#else
-        accl[l * 32] += x;
-#endif
-    };
+    auto scatter = [&](uint32_t l, float x) { accl[l * 32] += x; };
 
     // unit indices fit in 32 bits: n < 2^31 / nseg is checked on the host
     const int units = n * nseg;
