@@ -13,7 +13,8 @@
 //
 // reduce_sym_kernel: persistent and warp-specialized, one CTA per SM, blocks
 //   taken in turn.  One producer thread loads each block (four 32-column
-//   boxes, 128-byte swizzle) and its 2 x 128 labels into a 3-deep ring: four
+//   boxes, 128-byte swizzle) and its 2 x 128 labels into a ring 3 blocks deep
+//   (2 for k > 4): four
 //   TMA tensor loads from a full-square K, or one 64 KB bulk copy when K is
 //   stored block-packed (upper triangle only, each block already in the box
 //   layout: half the memory, and a K build that writes each value once).  The
