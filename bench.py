@@ -494,24 +494,30 @@ def main():
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    results = []
+    results, prof = [], []
     with ClockSampler(local) as clocks:
         barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
-            results.append(step())
+            results.append(step(timing=False))
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
+        # The same fits again with the library's per-kernel CUDA events (on the launch stream):
+        # the phase breakdown and the roofline kernel's launch time come from these.  The events
+        # cost a few percent of a fit, so they stay out of the timed region above.
+        for _ in range(args.steps):
+            prof.append(step(timing=True))
+        torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.summary()
 
     iters = sum(r["iterations"] for r in results)
-    red_ms = sum(r["info"]["reduce_ms"] for r in results)
-    red_n = sum(r["info"]["reduce_launches"] for r in results)
-    asg_ms = sum(r["info"]["assign_ms"] for r in results)
-    kb_ms = sum(r["info"]["kbuild_ms"] for r in results)
+    red_ms = sum(r["info"]["reduce_ms"] for r in prof)
+    red_n = sum(r["info"]["reduce_launches"] for r in prof)
+    asg_ms = sum(r["info"]["assign_ms"] for r in prof)
+    kb_ms = sum(r["info"]["kbuild_ms"] for r in prof)
     launches = sum(r["info"]["kernel_launches"] for r in results)
 
     # end to end through the same call with pinned host buffers (copies inside the timed region)
@@ -556,8 +562,8 @@ def main():
             # reduction minus the fold, both recorded by the library on the launch stream)
             T = (n + 127) // 128
             tri = sum(min(128, n - 128 * I) * (n - 128 * I) for I in range(T))   # elements of blocks (I, J >= I)
-            fold_ms = sum(r["info"]["fold_ms"] for r in results)
-            passes = sum(r["iterations"] for r in results)
+            fold_ms = sum(r["info"]["fold_ms"] for r in prof)
+            passes = sum(r["iterations"] for r in prof)
             avg_stream_ms = (red_ms - fold_ms) / max(passes, 1)
             alg_bytes = 4.0 * tri + 4.0 * T * k * n + 256.0 * T * (T + 1) / 2   # K blocks, slots, labels
             achieved = alg_bytes / (avg_stream_ms / 1e3) / 1e9 if avg_stream_ms > 0 else 0.0
