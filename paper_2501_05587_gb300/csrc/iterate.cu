@@ -360,7 +360,10 @@ __device__ __forceinline__ void assign_body(const AssignArgs& a, int block, int 
     }
 }
 
-__global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) { assign_body(a, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) {
+    grid_dependency_wait();   // S, z and the loop state come from the pass's reduction
+    assign_body(a, blockIdx.x, gridDim.x);
+}
 
 
 // sum_{i in L_c} S_ic for the recompute path, from Spart[s][c][i]: a block takes
@@ -632,8 +635,7 @@ cudaError_t launch_assign(const PassBuffers& b, const ReducePlan& plan, cudaStre
     a.st = b.st;
     a.changed_hist = b.changed_hist;
     a.E_out = b.E_out;
-    assign_kernel<<<(b.n + kAssignThreads - 1) / kAssignThreads, kAssignThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(assign_kernel, dim3((b.n + kAssignThreads - 1) / kAssignThreads), dim3(kAssignThreads), 0, s, a);
 }
 
 // Opt the reduction kernels into the largest dynamic shared memory the device

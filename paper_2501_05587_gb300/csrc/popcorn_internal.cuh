@@ -1,6 +1,7 @@
 // Internal declarations of the CUDA path (not part of the public ABI).
 #pragma once
 
+#include <utility>
 #include <vector>
 
 #include <cuda.h>
@@ -84,6 +85,30 @@ cudaError_t configure_reduce_sym(int smem_optin);
 // null) is recorded on s after the stream kernel, before the fold.
 cudaError_t launch_reduce_sym(const struct PassBuffers& b, const SymPlan& p, int* err, int eval_only,
                               cudaStream_t s, cudaEvent_t between);
+
+// Launch with programmatic dependent launch: the grid may be scheduled while the
+// previous kernel in the stream is still finishing, and it must call
+// grid_dependency_wait() before it touches anything that kernel wrote.  This
+// hides the launch latency between the kernels of a pass.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// Waits until the grids this one depends on have completed and their writes are
+// visible (returns at once for a launch without a programmatic dependency).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Upper-triangle block (bi, bj), bi <= bj, of number t when the T x T block
 // triangle is enumerated row by row (row b starts at b T - b (b - 1) / 2).  An

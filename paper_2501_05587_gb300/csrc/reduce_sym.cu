@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
     using L = SymLayout<KB>;
     constexpr int S = L::stages;
     static_assert(KB <= 8, "add_to_cluster has 8 cases");
+    grid_dependency_wait();   // the labels and the loop state come from the previous pass
     if (pass_skip(a.st, a.eval_only)) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -333,6 +334,7 @@ struct FoldArgs {
 
 // Block (x, c): rows x * 256 ... of cluster c.
 __global__ void __launch_bounds__(kFoldThreads) sym_fold_kernel(FoldArgs a) {
+    grid_dependency_wait();   // the slots come from the stream kernel
     LoopState* st = a.st;
     if (pass_skip(st, a.eval_only)) {
         if (a.eval_only && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->J_eval = st->J_last;
@@ -424,9 +426,8 @@ cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, 
     a.st = b.st;
     a.err = err;
     a.eval_only = eval_only;
-    if (b.k <= 4) reduce_sym_kernel<4><<<p.grid, kSymThreads, p.smem, s>>>(map, a);
-    else reduce_sym_kernel<8><<<p.grid, kSymThreads, p.smem, s>>>(map, a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = b.k <= 4 ? launch_pdl(reduce_sym_kernel<4>, dim3(p.grid), dim3(kSymThreads), p.smem, s, map, a)
+                             : launch_pdl(reduce_sym_kernel<8>, dim3(p.grid), dim3(kSymThreads), p.smem, s, map, a);
     if (e != cudaSuccess) return e;
     if (between && (e = cudaEventRecord(between, s)) != cudaSuccess) return e;
     FoldArgs f;
@@ -443,8 +444,7 @@ cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, 
     f.st = b.st;
     f.J_hist = b.J_hist;
     f.eval_only = eval_only;
-    sym_fold_kernel<<<dim3((unsigned)p.fold_blocks, (unsigned)b.k), kFoldThreads, 0, s>>>(f);
-    return cudaGetLastError();
+    return launch_pdl(sym_fold_kernel, dim3((unsigned)p.fold_blocks, (unsigned)b.k), dim3(kFoldThreads), 0, s, f);
 }
 
 }  // namespace popcorn
