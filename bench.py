@@ -601,6 +601,8 @@ def main():
                        "k_pass": {0: "recompute", 1: "symmetric", 2: "full"}[results[-1]["info"]["k_pass_used"]],
                        "passes_per_fit": iters / args.steps},
             "kbuild_tflops": kb_flops / (kb_ms / args.steps / 1e3) / 1e12 if kb_ms > 0 else None,
+            "kbuild_tflops_gemm_equivalent": (2.0 * n * n * wl.d / (kb_ms / args.steps / 1e3) / 1e12
+                                              if kb_ms > 0 else None),
             "kbuild_ms": kb_ms / args.steps,
             "loop_iters_per_s": iters / ((red_ms + asg_ms) / 1e3) if red_ms > 0 else None,
             "breakdown_ms_per_step": {"kbuild": kb_ms / args.steps, "reduce": red_ms / args.steps,
