@@ -80,7 +80,8 @@ typedef enum {
     POPCORN_FP32 = 0,    /* FP32 CUDA-core arithmetic; Gaussian distances from coordinate differences */
     POPCORN_BF16 = 1,    /* tcgen05 tensor cores, BF16 operands, FP32 accumulate                       */
     POPCORN_BF16X3 = 2,  /* tcgen05, split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate              */
-    POPCORN_FP8 = 3      /* reserved: FP8 E4M3 with per-row scales (recompute path)                   */
+    POPCORN_FP8 = 3      /* tcgen05, FP8 E4M3 operands with per-row scales s_i = max|p_i| / 448, FP32
+                            accumulate; the recompute path (store_k = 0) only                          */
 } popcorn_precision;
 
 /* Element type of a stored K (the paper stores FP32). */
@@ -237,8 +238,13 @@ POPCORN_API popcorn_status popcorn_assign_step(const float* K, int64_t ldk, cons
  *
  * Errors: as popcorn_kernel_matrix, plus POPCORN_ERR_INVALID for k outside
  * [1, n) or > 256, max_iter < 0, tol < 0, labels out of range, nonzero
- * reserved fields; POPCORN_ERR_UNSUPPORTED for store_k = 0 or POPCORN_FP8 in
- * this build; POPCORN_ERR_NOMEM when K does not fit in device memory.
+ * reserved fields; POPCORN_ERR_UNSUPPORTED for store_k = 1 with POPCORN_FP8
+ * (FP8 runs on the recompute path only), for store_k = 0 with POPCORN_FP32 or
+ * POPCORN_BF16X3 (the recompute path runs in POPCORN_BF16 or POPCORN_FP8), and
+ * for a recompute request with d or k beyond its limits (d <= 256 for BF16,
+ * d <= 512 for FP8); POPCORN_ERR_NOMEM when K (or the workspace) does not fit
+ * in device memory; POPCORN_ERR_TIMEOUT when a bounded wait inside a
+ * tensor-core or symmetric-pass kernel ran out (the context stays usable).
  */
 POPCORN_API popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, int32_t k,
                            popcorn_kernel kern, const int32_t* init_labels, int32_t max_iter,

@@ -21,17 +21,20 @@ What it computes, in the paper's notation (Sec. 3):
   the row argmin (ties to the lowest cluster index), the objective
   J = sum_i D_{i, cl(i)} (the K-means objective of Sec. 2.1 in feature space),
   and per-row margins used by the parity rule.
-* ``fit`` -- the loop of Alg. 2 with the stopping reading documented in
-  the design doc: stop after max_iter passes, or (when convergence checking is on)
-  when a pass changes no label, or when the objective drop is at most
-  tol * |J|.  The returned objective is J(labels_out).
+* ``fit`` -- the loop of Alg. 2.  The paper's loop condition ("while the
+  centroids are changing", Alg. 1/2) is read as: the centroids depend only on
+  the labels, so the loop stops after a pass that changes no label (when
+  convergence checking is on), or after a pass whose objective drop is at most
+  tol * |J| (tol > 0), and always after max_iter passes.  The returned
+  objective is J(labels_out).
 
 Pins (tests/test_oracle_*.py): brute force over all labelings for n <= 8,
 the linear kernel against Lloyd's algorithm in input space (Sec. 2.1), the
 degree-2 polynomial kernel against Lloyd on an explicit feature map,
 hand-derived golden cases (tests/golden/), kernel closed forms and invariants
-(symmetry, Gaussian diagonal 1, monotone objective).  No function here is
-"parity unpinned".
+(symmetry, Gaussian diagonal 1, monotone objective), and hand-worked rows for
+the ``margin`` / ``scale`` outputs of ``step`` (a best-distance tie, k = 1, an
+empty cluster, a singleton with D = 0).  No function here is "parity unpinned".
 """
 from __future__ import annotations
 

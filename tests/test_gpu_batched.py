@@ -95,15 +95,24 @@ def test_batched_rejects_bad_instance(pc):
 
 
 def test_batched_full_size_sampled(pc):
-    """The 256-instance batch of the batched workload (n in [500, 8000]): sampled
-    instances checked against the oracle after a full 30-pass run."""
+    """The 256-instance batch of the batched workload (n in [500, 8000]) in one graph, 29
+    and 30 passes (deterministic runs: the 29-pass labels are the 30-pass run's labels
+    before its last pass).  For sampled instances the oracle's step from the GPU's labels
+    after pass 29 must give the GPU's labels after pass 30 (element by element up to
+    exempt near-ties) and J of those labels; the reported objectives are J of the labels
+    returned."""
     wls = synth.batched_instances(256, seed=0)
     insts = [{"P": torch.from_numpy(w.P).cuda(), "k": w.k, "kernel": w.kernel,
               "init_labels": torch.from_numpy(w.init_labels).cuda()} for w in wls]
+    r29 = pc.popcorn_fit_batched(insts, max_iter=29, check_convergence=False)
+    l29 = [x.cpu().numpy() for x in r29["labels"]]
     r = pc.popcorn_fit_batched(insts, max_iter=30, check_convergence=False)
     for t in (0, 1, 77, 200, 255):
         w = wls[t]
         Ko = oracle.kernel_matrix(w.P, w.kernel)
         lab = r["labels"][t].cpu().numpy()
-        assert r["iterations"][t] == 30
+        assert r["iterations"][t] == 30 and r29["iterations"][t] == 29
+        st = oracle.step(Ko, l29[t], w.k)
+        assert rel_err(r29["objectives"][t], st["J"]) <= FP32_OBJ_REL, t
+        assert label_mismatches(lab, st)[0] == 0, t
         assert rel_err(r["objectives"][t], oracle.objective(Ko, lab, w.k)) <= FP32_OBJ_REL, t

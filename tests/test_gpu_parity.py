@@ -254,11 +254,14 @@ def test_fit_repeatable_and_timing_info(pc):
     assert inf["kbuild_ms"] > 0 and inf["reduce_ms"] > 0 and inf["loop_ms"] >= inf["reduce_ms"]
 
 
-# ------------------------------------------------------------------ full-size checks (bench configuration)
+# ------------------------------------------------------------------ full-size checks
 
 def test_full_size_rings_sampled(pc):
-    """n = 20000 rings in the launch configuration the bench times: sampled rows of K
-    and E against the oracle row by row, J against trace K - sum ||..|| identity."""
+    """n = 20000 rings through popcorn_kernel_matrix (full-square FP32 K) and
+    popcorn_assign_step (the full-square pass): sampled rows of K and E against the
+    oracle row by row, J against the identity trace K - sum |L_c| ||c_c||^2.  The
+    symmetric pass that popcorn_fit runs on this workload is checked against the
+    oracle's step at this size in test_gpu_sym.py."""
     wl = synth.workload("rings")
     P = _dev(wl.P)
     K, kd = pc.popcorn_kernel_matrix(P, wl.kernel)
@@ -291,3 +294,23 @@ def test_full_size_rings_fit_monotone(pc):
     if r["info"]["converged"]:
         assert r["info"]["changed_history"][-1] == 0
         assert rel_err(r["objective"], J[-1]) <= 1e-12
+
+
+def test_fit_reports_nomem_and_stays_usable(pc):
+    """A stored K that cannot fit in device memory (n = 400,000: 320 GB even as the
+    packed upper triangle) is refused with POPCORN_ERR_NOMEM before any kernel runs,
+    nothing is leaked, and the next call works."""
+    n = 400_000
+    P = np.zeros((n, 1), dtype=np.float32)
+    P[:, 0] = np.linspace(-1.0, 1.0, n, dtype=np.float32)
+    lab = (np.arange(n) % 4).astype(np.int32)
+    free0 = torch.cuda.mem_get_info()[0]
+    with pytest.raises(pc.PopcornError) as ei:
+        pc.popcorn_fit(P, 4, _gauss(1.0), lab, max_iter=2)
+    assert ei.value.status == 2, str(ei.value)
+    assert "kernel matrix" in str(ei.value)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+    wl = synth.workload("blobs", scale=0.1)
+    r = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), max_iter=3)
+    assert r["iterations"] >= 1

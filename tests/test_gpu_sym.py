@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 import synth  # noqa: E402
-from tests.parity import FP32_OBJ_REL, label_mismatches, rel_err  # noqa: E402
+from tests.parity import FP32_OBJ_REL, label_mismatches, oracle_kernel_matrix, rel_err  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -132,3 +132,38 @@ def test_symmetric_pass_launches_and_fallback(pc):
     assert c["info"]["k_pass_used"] == 2
     assert np.array_equal(c["labels"].cpu().numpy(), d["labels"].cpu().numpy())
     assert c["objective"] == d["objective"]
+
+
+def test_full_size_rings_symmetric_pass_is_the_oracle_step(pc):
+    """The rings workload at full size (n = 20,000, k = 4: 157 blocks per side, K stored
+    block-packed) through the symmetric pass that popcorn_fit picks for it: the first pass
+    from the random initial labels, a pass from the structured labels reached after 20
+    passes, and the converged labels, each against the oracle's step on the FP64 K
+    (labels element by element up to exempt near-ties, J within the FP32 bar)."""
+    wl = synth.workload("rings")
+    Ko = oracle_kernel_matrix(wl.P, wl.kernel)
+    P = torch.from_numpy(wl.P).cuda()
+    L0 = torch.from_numpy(wl.init_labels).cuda()
+
+    def fit(t, **kw):
+        return pc.popcorn_fit(P, wl.k, wl.kernel, L0, max_iter=t, check_convergence=False, history=True, **kw)
+
+    r1 = fit(1)
+    assert r1["info"]["k_pass_used"] == 1
+    st = oracle.step(Ko, wl.init_labels, wl.k)
+    got = r1["labels"].cpu().numpy()
+    assert label_mismatches(got, st)[0] == 0
+    assert rel_err(r1["info"]["J_history"][0], st["J"]) <= FP32_OBJ_REL
+    assert rel_err(r1["objective"], oracle.objective(Ko, got, wl.k)) <= FP32_OBJ_REL
+    a, b = fit(20), fit(21)
+    la = a["labels"].cpu().numpy()
+    st = oracle.step(Ko, la, wl.k)
+    assert label_mismatches(b["labels"].cpu().numpy(), st)[0] == 0
+    assert rel_err(b["info"]["J_history"][20], st["J"]) <= FP32_OBJ_REL
+    assert b["info"]["changed_history"][20] == int((b["labels"].cpu().numpy() != la).sum())
+    c = pc.popcorn_fit(P, wl.k, wl.kernel, L0, max_iter=wl.max_iter, history=True)
+    assert c["info"]["converged"] == 1 and c["info"]["k_pass_used"] == 1
+    lc = c["labels"].cpu().numpy()
+    st = oracle.step(Ko, lc, wl.k)
+    assert label_mismatches(lc, st)[0] == 0               # a fixed point of the oracle's step
+    assert rel_err(c["objective"], st["J"]) <= FP32_OBJ_REL

@@ -11,9 +11,10 @@ import pytest
 import oracle
 from oracle import kkmeans
 import synth
-from tests.test_oracle_pins import lloyd_step
+from tests.test_oracle_pins import lloyd_step, margin_pins_hold
 
 _orig = kkmeans.distances
+_orig_step = kkmeans.step
 
 
 def _mut_drop_cnorm(K, labels, k):
@@ -91,3 +92,55 @@ def test_unmutated_oracle_passes_condensed_pins():
 def test_each_mutant_is_caught(mutant, monkeypatch):
     monkeypatch.setattr(kkmeans, "distances", mutant)
     assert not _pins_pass()
+
+
+# ---- mistakes in the margin / scale outputs of step (they decide every parity exemption)
+
+def _smut_margin_inf(K, labels, k):
+    st = _orig_step(K, labels, k)
+    return {**st, "margin": np.full_like(st["margin"], np.inf)}
+
+
+def _smut_scale_huge(K, labels, k):
+    st = _orig_step(K, labels, k)
+    return {**st, "scale": st["scale"] * 1e6}
+
+
+def _smut_margin_to_worst(K, labels, k):
+    # largest finite distance minus the best: the wrong order statistic
+    st = _orig_step(K, labels, k)
+    D = np.where(np.isfinite(st["D"]), st["D"], -np.inf)
+    return {**st, "margin": D.max(axis=1) - st["D"].min(axis=1)}
+
+
+def _smut_scale_no_floor(K, labels, k):
+    st = _orig_step(K, labels, k)
+    return {**st, "scale": np.abs(st["D"].min(axis=1))}
+
+
+def _smut_scale_from_second(K, labels, k):
+    st = _orig_step(K, labels, k)
+    part = np.sort(st["D"], axis=1)
+    second = part[:, 1] if k > 1 else part[:, 0]
+    second = np.where(np.isfinite(second), second, part[:, 0])
+    return {**st, "scale": np.maximum(np.abs(second), st["kdiag"])}
+
+
+def _smut_margin_own_cluster(K, labels, k):
+    # distance to the current cluster minus the best, instead of second-best minus best
+    st = _orig_step(K, labels, k)
+    own = st["D"][np.arange(len(labels)), np.asarray(labels)]
+    return {**st, "margin": own - st["D"].min(axis=1)}
+
+
+STEP_MUTANTS = [_smut_margin_inf, _smut_scale_huge, _smut_margin_to_worst, _smut_scale_no_floor,
+                _smut_scale_from_second, _smut_margin_own_cluster]
+
+
+def test_unmutated_step_passes_margin_pins():
+    assert margin_pins_hold(oracle.step)
+
+
+@pytest.mark.parametrize("mutant", STEP_MUTANTS, ids=lambda f: f.__name__)
+def test_each_margin_mutant_is_caught(mutant):
+    assert not margin_pins_hold(mutant)

@@ -317,3 +317,66 @@ def test_tolerance_stop():
     Jh = loose["J_history"]
     if loose["iterations"] < full["iterations"]:
         assert Jh[-2] - Jh[-1] <= 1e-1 * abs(Jh[-1])
+
+
+# ---------------------------------------------------------------- margin and scale of a step
+#
+# Every GPU parity test excuses a label mismatch only where the oracle's margin
+# (second-best minus best distance of the row) is below 1e-6 times its scale
+# max(|best D|, K_ii).  These pins fix both outputs on rows worked out by hand
+# with the linear kernel in one dimension, where D_ic = (x_i - mean of cluster c)^2
+# and every value below is a dyadic rational, exact in FP64.
+
+MARGIN_CASES = [
+    # points, labels, k, expected margin per row, expected scale per row, expected new labels
+    # centroids 0.5, 6.5, 20 (a singleton); cluster 3 empty (its D column is +inf)
+    ([0.0, 1.0, 3.0, 10.0, 20.0], [0, 0, 1, 1, 2], 4,
+     [42.0, 30.0, 6.0, 78.0, 182.25],          # e.g. x=10: D = (90.25, 12.25, 100, inf)
+     [0.25, 1.0, 9.0, 100.0, 400.0],           # x=20: best D = 0 (singleton), floored by K_ii = 400
+     [0, 0, 0, 1, 2]),
+    # k = 1: no second cluster, margin +inf; scale = max(|D|, K_ii), D = (1, 1)
+    ([0.0, 2.0], [0, 0], 1, [math.inf, math.inf], [1.0, 4.0], [0, 0]),
+    # k = 2 with one cluster empty: the second-best is +inf, so the margin is +inf
+    ([0.0, 2.0], [0, 0], 2, [math.inf, math.inf], [1.0, 4.0], [0, 0]),
+    # centroids 0, 2, 5.5: x = 1 is equidistant from clusters 0 and 1 (margin 0, tie to 0)
+    ([0.0, 2.0, 1.0, 10.0], [0, 1, 2, 2], 3,
+     [4.0, 4.0, 0.0, 64.0 - 20.25],            # x=0: D = (0, 4, 30.25); x=10: D = (100, 64, 20.25)
+     [0.0, 4.0, 1.0, 100.0],                    # x=0: best D = 0 and K_ii = 0
+     [0, 1, 0, 2]),
+]
+
+
+def margin_pins_hold(step_fn) -> bool:
+    """True when step_fn reproduces every hand-worked margin, scale and label above."""
+    for pts, lab, k, margin, scale, new in MARGIN_CASES:
+        K = oracle.kernel_matrix(np.array(pts)[:, None], _kern("linear"))
+        st = step_fn(K, lab, k)
+        m = np.asarray(st["margin"], dtype=float)
+        s = np.asarray(st["scale"], dtype=float)
+        if not np.array_equal(np.isinf(m), np.isinf(np.array(margin))):
+            return False
+        fin = np.isfinite(margin)
+        if not np.allclose(m[fin], np.array(margin)[fin], rtol=0, atol=1e-12):
+            return False
+        if not np.allclose(s, scale, rtol=0, atol=1e-12):
+            return False
+        if st["labels"].tolist() != new:
+            return False
+    return True
+
+
+def test_step_margin_and_scale_hand_worked():
+    assert margin_pins_hold(oracle.step)
+
+
+def test_parity_exemption_uses_margin_and_scale():
+    """The parity rule excuses a flipped label only on a near-tie row: on the tied row of
+    the last case a GPU label of 1 is exempt; on every other row a flip is not."""
+    from tests.parity import label_mismatches
+
+    pts, lab, k = [0.0, 2.0, 1.0, 10.0], [0, 1, 2, 2], 3
+    K = oracle.kernel_matrix(np.array(pts)[:, None], _kern("linear"))
+    st = oracle.step(K, lab, k)
+    assert label_mismatches([0, 1, 1, 2], st) == (0, 1)      # the tie: exempt
+    assert label_mismatches([1, 1, 0, 2], st) == (1, 0)      # margin 4 on scale 0 -> 4 > 0: not exempt
+    assert label_mismatches([0, 1, 0, 1], st) == (1, 0)
