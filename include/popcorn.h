@@ -108,16 +108,23 @@ typedef struct {
                                    per SM).  Results differ only by summation order.        */
     int32_t k_pass;             /* how a pass reads a stored FP32 K.  0 = automatic (the
                                    default): the symmetric read below wherever it applies
-                                   (FP32 K, k <= 8), else the full square.  1 = symmetric:
+                                   (FP32 K, k <= 16), else the full square.  1 = symmetric:
                                    only the 128 x 128 blocks on and above the diagonal (K is
-                                   symmetric); a block's row sums serve its rows and its
-                                   column sums its columns' rows, written to one slot per
-                                   block and folded, so a pass reads half of K plus
-                                   8 k n ceil(n / 128) bytes of slots; where it does not
-                                   apply the full square runs.  2 = the full square, row by
-                                   row (the paper's read of K).  The recompute path has its
-                                   own scheme.  Results differ only by summation order      */
-    int32_t reserved_pad;       /* must be zero                                              */
+                                   symmetric, and is then stored as that packed triangle); a
+                                   block's row sums serve its rows and its column sums its
+                                   columns' rows.  Blocks are taken in super-tiles of a x a
+                                   (sym_tile below); each super-tile writes one slot per row
+                                   it touches, and the slots are folded, so a pass reads half
+                                   of K plus about 8 k n ceil(n / 128a) bytes of slots; where
+                                   it does not apply the full square runs.  2 = the full
+                                   square, row by row (the paper's read of K).  The
+                                   recompute path has its own scheme.  Results differ only
+                                   by summation order                                       */
+    int32_t sym_tile;           /* super-tile edge a of the symmetric pass, in 128-blocks:
+                                   0 = automatic (the largest of 4, 2, 1 that leaves about 16
+                                   super-tiles per SM); 1, 2 or 4 to force one (a forced
+                                   edge whose shared memory does not fit falls back to the
+                                   full square)                                            */
     int64_t reserved[4];        /* must be zero                                              */
 } popcorn_options;
 
@@ -146,11 +153,20 @@ typedef struct {
                                   batched: {columns per K-stream unit, warps per block,
                                             blocks per SM, 0};
                                   recompute: {row blocks per tile, column segments,
-                                              units per SM target, 0}; zeros otherwise     */
+                                              units per SM target, 0};
+                                  symmetric pass: {super-tile edge, block ring depth,
+                                                   slots, register accumulators per row};
+                                  zeros otherwise                                           */
     double fold_ms;            /* symmetric pass: the slot fold kernel, summed over passes
                                   (part of reduce_ms), when timing = 1                      */
     int32_t k_pass_used;       /* stored K: 1 = symmetric pass, 2 = full square; 0 recompute */
     int32_t reserved_info;     /* zero                                                     */
+    float* E_out;              /* caller-provided DEVICE array of n x k floats (row-major,
+                                  ld = k), or NULL.  Stored-K fits with max_iter >= 1: E =
+                                  K V^T of the labels the last assignment pass started
+                                  from (the E that pass took its argmin from; with
+                                  max_iter = 1 those are init_labels).  Ignored by the
+                                  recompute path and by popcorn_fit_batched               */
 } popcorn_fit_info;
 
 /* Human-readable name of a status code (static storage). */

@@ -71,7 +71,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("store_k", ctypes.c_int32),
                 ("check_convergence", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("k_storage", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("k_pass", ctypes.c_int32), ("reserved_pad", ctypes.c_int32),
+                ("k_pass", ctypes.c_int32), ("sym_tile", ctypes.c_int32),
                 ("reserved", ctypes.c_int64 * 4)]
 
 
@@ -89,7 +89,8 @@ class _FitInfo(ctypes.Structure):
                 ("changed_history", ctypes.POINTER(ctypes.c_int32)), ("tune_cache_hit", ctypes.c_int32),
                 ("tune_candidates", ctypes.c_int32), ("tune_ms", ctypes.c_double),
                 ("schedule", ctypes.c_int32 * 4), ("fold_ms", ctypes.c_double),
-                ("k_pass_used", ctypes.c_int32), ("reserved_info", ctypes.c_int32)]
+                ("k_pass_used", ctypes.c_int32), ("reserved_info", ctypes.c_int32),
+                ("E_out", ctypes.c_void_p)]
 
 
 class _Instance(ctypes.Structure):
@@ -237,7 +238,8 @@ def popcorn_assign_step_noalloc(K, kdiag, labels, k: int, want_E: bool = False, 
 
 
 def _info_dict(info) -> dict:
-    out = {f: getattr(info, f) for f, _ in _FitInfo._fields_ if f not in ("J_history", "changed_history", "schedule")}
+    out = {f: getattr(info, f) for f, _ in _FitInfo._fields_
+           if f not in ("J_history", "changed_history", "schedule", "E_out")}
     out["schedule"] = list(info.schedule)
     return out
 
@@ -255,13 +257,17 @@ def popcorn_autotune_clear() -> None:
 def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float = 0.0,
                 precision: str = "fp32", check_convergence: bool = True, timing: bool = False,
                 history: bool = False, labels_out=None, store_k: bool = True, k_storage: str = "fp32",
-                autotune: bool = False, k_pass: str = "auto", stream=None) -> dict:
+                autotune: bool = False, k_pass: str = "auto", sym_tile: int = 0, E_out=None,
+                stream=None) -> dict:
     """Kernel K-means (Alg. 2).  P and init_labels may live on the host or the device.
 
     ``store_k=False`` selects the recompute path (K never stored; precision
     "bf16" or "fp8").  ``k_storage`` ("fp32", "fp16", "bf16") is the element
     type of a stored K.  ``k_pass`` ("auto", "symmetric", "full") is how a pass
-    reads a stored FP32 K.  Returns {"labels", "objective", "iterations", "info"};
+    reads a stored FP32 K; ``sym_tile`` (0 = automatic, 1, 2, 4) is the super-tile edge of
+    the symmetric pass.  ``E_out`` (an (n, k) float32 CUDA tensor) receives E = K V^T of the
+    labels the last pass started from (stored-K fits).  Returns {"labels", "objective",
+    "iterations", "info"};
     labels land where ``labels_out`` lives (default: same place as init_labels).
     """
     torch = _torch()
@@ -284,8 +290,13 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
         else:
             labels_out = torch.empty(n, dtype=torch.int32, device=init_labels.device)
     opt = _Options(PRECISION[precision], 1 if store_k else 0, 1 if check_convergence else 0, 1 if timing else 0,
-                   K_STORAGE[k_storage], 1 if autotune else 0, K_PASS[k_pass], 0, (ctypes.c_int64 * 4)())
+                   K_STORAGE[k_storage], 1 if autotune else 0, K_PASS[k_pass], int(sym_tile),
+                   (ctypes.c_int64 * 4)())
     info = _FitInfo()
+    if E_out is not None:
+        assert E_out.is_cuda and E_out.dtype == torch.float32 and E_out.is_contiguous()
+        assert tuple(E_out.shape) == (n, int(k))
+        info.E_out = E_out.data_ptr()
     Jh = (ctypes.c_double * max(1, max_iter))() if history else None
     Ch = (ctypes.c_int32 * max(1, max_iter))() if history else None
     if history:

@@ -108,6 +108,10 @@ class Workspace {
         cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool_, s_);
         if (e != cudaSuccess) {
             cudaGetLastError();
+            // a failed request can leave the pool holding what it reserved while trying;
+            // hand every unused byte back to the device
+            cudaMemPoolTrimTo(pool_, 0);
+            cudaGetLastError();
             return fail(e == cudaErrorMemoryAllocation ? POPCORN_ERR_NOMEM : POPCORN_ERR_CUDA,
                         "workspace for %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
         }
@@ -181,7 +185,7 @@ popcorn_status check_kernel(const popcorn_kernel& kern, KernParams* kp) {
 // K = kappa(P P^T) on stream s.  FP32: CUDA-core tiles.  BF16 / BF16X3: tcgen05
 // tiles; their operand copies come from `ws`, and *err (device) reports a
 // timed-out wait inside the kernel.
-// packed: the FP32 build writes the block-packed upper triangle (symmetric pass only).
+// packed: the build writes the block-packed upper triangle (symmetric pass only).
 popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, const KernParams& kp,
                                    int precision, void* K, int64_t ldk, int k_storage, float* kdiag, Workspace* ws,
                                    int* err, int num_sms, cudaStream_t s, int* launches, bool packed = false) {
@@ -196,7 +200,7 @@ popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, co
     unsigned char* w;
     POPCORN_TRY(ws->alloc(&w, kbuild_tc_workspace(n, d, precision), "BF16 operands"));
     cudaError_t e = launch_kbuild_tc(P, n, d, ldp, kp, precision, static_cast<float*>(K), ldk, kdiag, w, err, num_sms,
-                                     s, launches);
+                                     s, launches, packed);
     if (e == cudaErrorInvalidValue)
         return fail(POPCORN_ERR_CUDA, "tensor map creation failed (cuTensorMapEncodeTiled unavailable or rejected)");
     POPCORN_CUDA(e);
@@ -637,7 +641,8 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
     if (opt.autotune != 0 && opt.autotune != 1) return fail(POPCORN_ERR_INVALID, "options.autotune must be 0 or 1");
     if (opt.k_pass < 0 || opt.k_pass > 2) return fail(POPCORN_ERR_INVALID, "options.k_pass must be 0, 1 or 2");
-    if (opt.reserved_pad != 0) return fail(POPCORN_ERR_INVALID, "options.reserved_pad must be 0");
+    if (opt.sym_tile != 0 && opt.sym_tile != 1 && opt.sym_tile != 2 && opt.sym_tile != 4)
+        return fail(POPCORN_ERR_INVALID, "options.sym_tile must be 0, 1, 2 or 4");
     for (int r = 0; r < 4; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
     if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)
@@ -663,13 +668,15 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // symmetric pass (FP32 K, k <= kSymMaxK; k_pass 0 or 1): the blocks on and above the
     // diagonal, row and column sums into T slots, folded into slot 0
     SymPlan sym{};
-    if (ks == POPCORN_K_FP32 && opt.k_pass != 2) sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin);
+    if (ks == POPCORN_K_FP32 && opt.k_pass != 2)
+        sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin, opt.sym_tile);
     const bool use_sym = sym.ok;
-    // With the symmetric pass and the FP32 build, K is stored block-packed: the upper triangle
-    // of 128 x 128 tiles only (half the memory; each value written once).
-    sym.packed = use_sym && opt.precision == POPCORN_FP32;
+    // With the symmetric pass, K is stored block-packed: the upper triangle of 128 x 128
+    // tiles only (half the memory; each value written once), by the FP32 build and by the
+    // tensor-core builds alike.
+    sym.packed = use_sym;
     const size_t k_bytes = sym.packed ? (size_t)sym.items * 128 * 128 * 4 : (size_t)ni * (size_t)ldk * kelem;
-    const int nslots = use_sym ? sym.T : plan.nseg;
+    const int nslots = use_sym ? sym.nslots : plan.nseg;
     if (use_sym) plan.nseg = 1;             // the assignment reads the folded slot only
     const bool timing = opt.timing != 0;
     int launches = 0;
@@ -725,7 +732,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     POPCORN_TRY(ws.alloc(&b.st, 1, "loop state"));
     POPCORN_TRY(ws.alloc(&b.J_hist, (size_t)hist_len, "objective history"));
     POPCORN_TRY(ws.alloc(&b.changed_hist, (size_t)hist_len, "change history"));
-    b.E_out = nullptr;
+    b.E_out = info ? info->E_out : nullptr;   // written by every assignment pass; the last one stays
 
     g_events.used = 0;
     cudaEvent_t ev_b0 = nullptr, ev_b1 = nullptr, ev_l1 = nullptr, ev_e1 = nullptr;
@@ -847,6 +854,12 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         info->k_pass_used = 0;
         info->reserved_info = 0;
         for (int q = 0; q < 4; ++q) info->schedule[q] = 0;
+        if (use_sym) {
+            info->schedule[0] = sym.a;
+            info->schedule[1] = sym.stages;
+            info->schedule[2] = sym.nslots;
+            info->schedule[3] = sym.kb;
+        }
         // passes that did work (launches after convergence return at once)
         const bool eval_ran = !(hs.iter > 0 && hs.last_changed == 0);
         info->reduce_launches = iters + (eval_ran ? 1 : 0);
@@ -890,7 +903,8 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
     if (opt.autotune != 0 && opt.autotune != 1) return fail(POPCORN_ERR_INVALID, "options.autotune must be 0 or 1");
     if (opt.k_pass < 0 || opt.k_pass > 2) return fail(POPCORN_ERR_INVALID, "options.k_pass must be 0, 1 or 2");
-    if (opt.reserved_pad != 0) return fail(POPCORN_ERR_INVALID, "options.reserved_pad must be 0");
+    if (opt.sym_tile != 0 && opt.sym_tile != 1 && opt.sym_tile != 2 && opt.sym_tile != 4)
+        return fail(POPCORN_ERR_INVALID, "options.sym_tile must be 0, 1, 2 or 4");
     for (int r = 0; r < 4; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
     if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)

@@ -14,7 +14,10 @@
 //                       (double-buffered: 512 columns);
 //   warps 2-5           epilogue: tcgen05.ld the accumulators, apply kappa with
 //                       FP32 row norms, stage each 128 x 32 chunk and its
-//                       transpose in shared memory and TMA-store both into K.
+//                       transpose in shared memory and TMA-store both into K --
+//                       or, for the block-packed upper triangle the symmetric
+//                       pass reads, bulk-copy the swizzled chunk alone to its
+//                       place in the packed tile (each value stored once).
 //
 // Why row pairs: an SM takes in about 36 bytes per clock from L2 whichever path
 // it uses (TMA, bulk copy, cp.async or vector loads), and a 128 x 128 tile moves
@@ -35,6 +38,8 @@
 // runs out sets *err, raises a shared abort flag that ends every role's loop,
 // waits (bounded again) for the CTA's own TMA copies and MMAs in flight,
 // frees TMEM and returns; the host reports POPCORN_ERR_TIMEOUT.
+#include <cstring>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -68,6 +73,8 @@ struct TcArgs {
     int nstg;                 // staging buffers per kind (2, or 1 when the ring needs the room)
     int off_sd, off_st, off_rj, off_bar, off_misc;
     long long tiles;          // sum_p (T - 2 p)
+    float* Kp;                // block-packed K (tile (I, J), I <= J, at its row-by-row triangle index
+                              // times 16384 floats, four swizzled 128 x 32 boxes), or null
     KernParams kp;
     const float* norms;       // row norms of the represented rows (Gaussian)
     float* kdiag;
@@ -310,15 +317,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         float4 w = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
                         *reinterpret_cast<float4*>(sd + row_local * 32 + ((i ^ (row_local & 7)) * 4)) = w;
                     }
-                    if (!diag) {
+                    if (!diag && !a.Kp) {
 #pragma unroll
                         for (int x = 0; x < 32; ++x) sx[x * 128 + row_local] = v[x];
                     }
                     fence_proxy_async();
                     epi_bar();
                     if (et == 0) {
-                        tma_store_2d(&map_kd, j * BM + 32 * c, rb * BM, smem_u32(sd));
-                        if (!diag) tma_store_2d(&map_kt, rb * BM, j * BM + 32 * c, smem_u32(sx));
+                        if (a.Kp) {
+                            // the staged chunk is box c of packed tile (rb, j), byte for byte
+                            const long long tri = (long long)rb * a.T - (long long)rb * (rb - 1) / 2 + (j - rb);
+                            bulk_store_1d(a.Kp + tri * (BM * BM) + c * (BM * 32), smem_u32(sd), (uint32_t)STG_BYTES);
+                        } else {
+                            tma_store_2d(&map_kd, j * BM + 32 * c, rb * BM, smem_u32(sd));
+                            if (!diag) tma_store_2d(&map_kt, rb * BM, j * BM + 32 * c, smem_u32(sx));
+                        }
                         bulk_commit();
                     }
                 }
@@ -414,7 +427,7 @@ cudaError_t configure_kbuild_tc() {
 
 cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
                              int64_t ldk, float* kdiag, void* workspace, int* err, int num_sms, cudaStream_t s,
-                             int* launches) {
+                             int* launches, bool packed) {
     const int dpad = (d + BK - 1) / BK * BK;
     const int x3 = precision == POPCORN_BF16X3 ? 1 : 0;
     const int64_t ldw = (int64_t)(x3 ? 2 : 1) * dpad;
@@ -428,14 +441,18 @@ cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernPara
     if (launches) ++*launches;
 
     CUtensorMap mr, mc, mkd, mkt;
+    memset(&mkd, 0, sizeof mkd);
+    memset(&mkt, 0, sizeof mkt);
     if (!make_tensor_map_2d(&mr, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, W, (uint64_t)ldw, (uint64_t)n, (uint64_t)ldw * 2, BK,
                             2 * BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
         !make_tensor_map_2d(&mc, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, W, (uint64_t)ldw, (uint64_t)n, (uint64_t)ldw * 2, BK,
-                            BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !make_tensor_map_2d(&mkd, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, K, (uint64_t)n, (uint64_t)n, (uint64_t)ldk * 4, 32, BM,
-                            CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !make_tensor_map_2d(&mkt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, K, (uint64_t)n, (uint64_t)n, (uint64_t)ldk * 4, BM, 32,
-                            CU_TENSOR_MAP_SWIZZLE_NONE))
+                            BM, CU_TENSOR_MAP_SWIZZLE_128B))
+        return cudaErrorInvalidValue;
+    // the full-square stores go through tensor maps; the packed stores are plain bulk copies
+    if (!packed && (!make_tensor_map_2d(&mkd, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, K, (uint64_t)n, (uint64_t)n,
+                                        (uint64_t)ldk * 4, 32, BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+                    !make_tensor_map_2d(&mkt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, K, (uint64_t)n, (uint64_t)n,
+                                        (uint64_t)ldk * 4, BM, 32, CU_TENSOR_MAP_SWIZZLE_NONE)))
         return cudaErrorInvalidValue;
 
     TcArgs a;
@@ -457,6 +474,7 @@ cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernPara
     a.off_bar = a.off_rj + BM * 4;
     a.off_misc = a.off_bar + 16 * 8;
     a.tiles = (long long)a.T2 * a.T - (long long)a.T2 * (a.T2 - 1);
+    a.Kp = packed ? K : nullptr;
     a.kp = kp;
     a.norms = norms;
     a.kdiag = kdiag;

@@ -65,21 +65,30 @@ struct ReducePlan {
 };
 
 // Symmetric K stream (reduce_sym.cu): each 128 x 128 block on and above the
-// diagonal is read once.  Block (I, J) gives the row sums of block I (slot J)
-// and, off the diagonal, the column sums of block J (slot I), so Spart holds T
+// diagonal is read once.  Blocks are handed out in super-tiles of a x a blocks;
+// a super-tile's row sums go to one slot of its rows and its column sums to one
+// slot of its columns' rows, so Spart holds nslots = ceil(T / a) (+1 when a > 1)
 // slots; the fold sums them into slot 0 (the assignment then reads slot 0
 // only) and forms z and J.  FP32 K, k <= kSymMaxK.
-constexpr int kSymMaxK = 8;
+constexpr int kSymMaxK = 16;
 struct SymPlan {
     bool ok;
-    int T;              // 128-blocks per side = Spart slots
+    int kb;             // register accumulators per row / column: 4, 8 or 16 (>= k)
+    int T;              // 128-blocks per side
+    int a;              // super-tile edge in blocks (1, 2 or 4)
+    int Ts;             // super-tiles per side
+    int nslots;         // Spart slots
+    int stages;         // block ring depth
     long long items;    // blocks on and above the diagonal
+    long long units;    // super-tiles on and above the diagonal
     int grid;           // persistent CTAs of the stream kernel
     int fold_blocks;    // row chunks of the fold (zpart rows)
     size_t smem;
     bool packed;        // K is block-packed (set by the caller with the K build it chose)
 };
-SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin);
+// a_req / stages_req: 0 = the heuristic choice, else that super-tile edge / ring depth
+// (ok = false if it does not fit)
+SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req = 0, int stages_req = 0);
 cudaError_t configure_reduce_sym(int smem_optin);
 // err: set when a bounded wait of the stream kernel runs out; `between` (may be
 // null) is recorded on s after the stream kernel, before the fold.
@@ -147,9 +156,11 @@ size_t kbuild_tc_workspace(int n, int d, int precision);
 cudaError_t configure_kbuild_tc();
 // precision POPCORN_BF16 or POPCORN_BF16X3; *err (device) becomes nonzero if a
 // bounded wait inside the kernel ran out.
+// packed: K is the block-packed upper triangle (as the FP32 build writes it for the
+// symmetric pass); ldk is then unused.
 cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
                              int64_t ldk, float* kdiag, void* workspace, int* err, int num_sms, cudaStream_t s,
-                             int* launches);
+                             int* launches, bool packed = false);
 
 // 2-D tiled TMA descriptor over a row-major matrix (inner = contiguous extent
 // in elements, row_bytes = pitch); false if the driver entry point is missing

@@ -6,8 +6,14 @@ part of its columns' rows; a fold kernel adds the parts.  So one pass from given
 labels must be the oracle's step exactly as the full-square pass is (labels equal
 except near-ties, objective within the FP32 bar), and whole fits must agree with the
 full-square pass up to FP32 summation order.  The cases cover a single ragged block,
-ragged n over several blocks, n a multiple of 128, k at its bound (8), a kernel
-that is not positive semi-definite (symmetry is all the pass needs) and many blocks.
+ragged n over several blocks, n a multiple of 128, k up to its bound (16), a kernel
+that is not positive semi-definite (symmetry is all the pass needs) and many blocks,
+each with every super-tile edge (1, 2, 4: a super-tile's row and column sums are kept
+over its a x a blocks before they are stored).  The images workload runs through it
+at a tenth of its size against the full oracle step (FP32 build and the packed
+tensor-core BF16X3 build), and at full size (n = 70,000, 547 blocks per side) on
+sampled rows of E = K V^T that the oracle computes row by row, with every row's
+argmin re-derived from E.
 """
 import numpy as np
 import pytest
@@ -44,15 +50,23 @@ CASES = [
     (1280, 4, 8, _gauss(1.0), 6),        # n a multiple of 128, k at the bound
     (700, 3, 5, POLY3_NEG, 7),           # negative entries: symmetry suffices
     (9001, 4, 5, _gauss(1.0), 5),        # 71 blocks per side
+    (1100, 7, 12, _gauss(2.0), 8),       # 16 register accumulators, ragged
+    (2500, 5, 16, _gauss(1.5), 9),       # k at the bound (16)
+    (3000, 6, 10, POLY2, 10),
+    (9001, 4, 16, _gauss(1.0), 11),
 ]
 
 
+@pytest.mark.parametrize("sym_tile", [0, 1, 2, 4])
 @pytest.mark.parametrize("n,d,k,kern,seed", CASES)
-def test_symmetric_pass_is_the_oracle_step(pc, n, d, k, kern, seed):
+def test_symmetric_pass_is_the_oracle_step(pc, n, d, k, kern, seed, sym_tile):
     P = synth.gaussian_blobs(n, d, k, seed=seed, box=3.0)
     lab = synth.init_labels(n, k, seed=seed + 100)
     r = pc.popcorn_fit(torch.from_numpy(P).cuda(), k, kern, torch.from_numpy(lab).cuda(), max_iter=1,
-                       check_convergence=False, k_pass="symmetric")
+                       check_convergence=False, k_pass="symmetric", sym_tile=sym_tile)
+    assert r["info"]["k_pass_used"] == 1
+    if sym_tile:
+        assert r["info"]["schedule"][0] == sym_tile
     Ko = oracle.kernel_matrix(P, kern)
     st = oracle.step(Ko, lab, k)
     got = r["labels"].cpu().numpy()
@@ -96,14 +110,15 @@ def test_symmetric_rings_bench_size_matches_full_square(pc):
     assert rel_err(a["objective"], b["objective"]) <= FP32_OBJ_REL
 
 
-def test_symmetric_pass_is_deterministic(pc):
+@pytest.mark.parametrize("name,sym_tile", [("rings", 0), ("rings", 2), ("images", 4)])
+def test_symmetric_pass_is_deterministic(pc, name, sym_tile):
     """No atomics: every partial is written once and folded in slot order, so runs
     agree bit for bit."""
-    wl = synth.workload("rings", scale=0.3)
+    wl = synth.workload(name, scale=0.3 if name == "rings" else 0.05)
     P = torch.from_numpy(wl.P).cuda()
     L0 = torch.from_numpy(wl.init_labels).cuda()
     runs = [pc.popcorn_fit(P, wl.k, wl.kernel, L0, max_iter=10, check_convergence=False, history=True,
-                           k_pass="symmetric") for _ in range(3)]
+                           k_pass="symmetric", sym_tile=sym_tile) for _ in range(3)]
     for r in runs[1:]:
         assert r["info"]["J_history"] == runs[0]["info"]["J_history"]
         assert r["objective"] == runs[0]["objective"]
@@ -112,7 +127,7 @@ def test_symmetric_pass_is_deterministic(pc):
 
 def test_symmetric_pass_launches_and_fallback(pc):
     """k_pass = "symmetric" runs the stream and the fold (one launch more per pass than
-    the full square) and is what "auto" picks for an FP32 K with k <= 8; above the
+    the full square) and is what "auto" picks for an FP32 K with k <= 16; above the
     cluster bound, or with a half-precision K, both fall back to the full-square pass,
     with results identical to it."""
     P = torch.from_numpy(synth.gaussian_blobs(600, 3, 6, seed=9, box=3.0)).cuda()
@@ -125,9 +140,9 @@ def test_symmetric_pass_launches_and_fallback(pc):
     assert a["info"]["kernel_launches"] == b["info"]["kernel_launches"] + a["iterations"] + 1
     h = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_storage="fp16")
     assert h["info"]["k_pass_used"] == 2
-    lab12 = torch.from_numpy(synth.init_labels(600, 12, seed=29)).cuda()
-    c = pc.popcorn_fit(P, 12, _gauss(1.0), lab12, max_iter=5, check_convergence=False, k_pass="symmetric")
-    d = pc.popcorn_fit(P, 12, _gauss(1.0), lab12, max_iter=5, check_convergence=False, k_pass="full")
+    lab20 = torch.from_numpy(synth.init_labels(600, 20, seed=29)).cuda()
+    c = pc.popcorn_fit(P, 20, _gauss(1.0), lab20, max_iter=5, check_convergence=False, k_pass="symmetric")
+    d = pc.popcorn_fit(P, 20, _gauss(1.0), lab20, max_iter=5, check_convergence=False, k_pass="full")
     assert c["info"]["kernel_launches"] == d["info"]["kernel_launches"]
     assert c["info"]["k_pass_used"] == 2
     assert np.array_equal(c["labels"].cpu().numpy(), d["labels"].cpu().numpy())
@@ -167,3 +182,68 @@ def test_full_size_rings_symmetric_pass_is_the_oracle_step(pc):
     st = oracle.step(Ko, lc, wl.k)
     assert label_mismatches(lc, st)[0] == 0               # a fixed point of the oracle's step
     assert rel_err(c["objective"], st["J"]) <= FP32_OBJ_REL
+
+
+@pytest.mark.parametrize("precision,rel", [("fp32", FP32_OBJ_REL), ("bf16x3", 1e-5)])
+def test_images_tenth_symmetric_pass_is_the_oracle_step(pc, precision, rel):
+    """The images workload at a tenth of its size (n = 7,000, d = 784, k = 10: 55 blocks
+    per side) through the symmetric pass with K block-packed by the FP32 build or by the
+    tensor-core BF16X3 build: the first pass and a pass from the labels reached after 5
+    passes against the oracle's step on the FP64 K (BF16X3 K carries ~1e-6 relative
+    error, so its bars are 1e-5)."""
+    wl = synth.workload("images", scale=0.1)
+    Ko = oracle_kernel_matrix(wl.P, wl.kernel)
+    P = torch.from_numpy(wl.P).cuda()
+    L0 = torch.from_numpy(wl.init_labels).cuda()
+
+    def fit(t):
+        return pc.popcorn_fit(P, wl.k, wl.kernel, L0, max_iter=t, check_convergence=False, history=True,
+                              precision=precision)
+
+    r1 = fit(1)
+    assert r1["info"]["k_pass_used"] == 1
+    st = oracle.step(Ko, wl.init_labels, wl.k)
+    assert label_mismatches(r1["labels"].cpu().numpy(), st, rel=rel)[0] == 0
+    assert rel_err(r1["info"]["J_history"][0], st["J"]) <= rel
+    a, b = fit(5), fit(6)
+    st = oracle.step(Ko, a["labels"].cpu().numpy(), wl.k)
+    assert label_mismatches(b["labels"].cpu().numpy(), st, rel=rel)[0] == 0
+    assert rel_err(b["info"]["J_history"][5], st["J"]) <= rel
+    assert rel_err(b["objective"], oracle.objective(Ko, b["labels"].cpu().numpy(), wl.k)) <= rel
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_full_size_images_symmetric_pass_sampled(pc, precision):
+    """The images workload at full size (n = 70,000, d = 784, k = 10; K block-packed,
+    547 blocks per side, super-tiles of 4 x 4) in the configuration the bench times: one
+    pass from the initial labels.  Sampled rows of E = K V^T (first, last, block edges,
+    the ragged tail, random rows) against the oracle's K rows; J against the identity
+    J = trace K - sum_c sum_{i in L_c} E_ic; and every row's new label against the argmin
+    of D = K_ii - 2 E + ||c||^2 rebuilt from E in FP64 (near-ties exempt)."""
+    wl = synth.workload("images")
+    n, k = wl.n, wl.k
+    P = torch.from_numpy(wl.P).cuda()
+    L0 = torch.from_numpy(wl.init_labels).cuda()
+    E = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    r = pc.popcorn_fit(P, k, wl.kernel, L0, max_iter=1, check_convergence=False, history=True,
+                       precision=precision, E_out=E)
+    assert r["info"]["k_pass_used"] == 1 and r["info"]["schedule"][0] == 4
+    Eg = E.cpu().numpy().astype(np.float64)
+    lab = wl.init_labels.astype(np.int64)
+    m = np.bincount(lab, minlength=k).astype(np.float64)
+    rng = np.random.default_rng(1)
+    rows = np.unique(np.concatenate([[0, 1, 127, 128, 129, n - 129, n - 2, n - 1],
+                                     rng.choice(n, 40, replace=False)]))
+    Kr = oracle.kernel_matrix(wl.P[rows], wl.kernel, Q=wl.P)
+    Eo = np.stack([Kr[:, lab == c].sum(axis=1) / m[c] for c in range(k)], axis=1)
+    assert np.max(np.abs(Eg[rows] - Eo)) <= 1e-5 * np.abs(Eo).max()
+    z = np.array([Eg[lab == c, c].sum() / m[c] for c in range(k)])
+    trace = float(n)                                   # Gaussian: K_ii = 1
+    J_E = trace - sum(Eg[lab == c, c].sum() for c in range(k))
+    assert rel_err(r["info"]["J_history"][0], J_E) <= 1e-6
+    D = 1.0 - 2.0 * Eg + z[None, :]
+    pred = np.argmin(D, axis=1)
+    part = np.partition(D, 1, axis=1)
+    exempt = (part[:, 1] - part[:, 0]) < 1e-6 * np.maximum(np.abs(part[:, 0]), 1.0)
+    got = r["labels"].cpu().numpy()
+    assert int(((got != pred) & ~exempt).sum()) == 0

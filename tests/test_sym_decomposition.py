@@ -2,14 +2,18 @@
 
 K is symmetric, so the segment sums S_ic = sum_{j in L_c} K_ij can be taken from
 the 128 x 128 blocks on and above the diagonal alone: block (I, J), I <= J, gives
-the row sums of its rows (slot J of the rows of block I) and, off the diagonal,
-its column sums (slot I of the rows of block J).  Every (slot, cluster, row) is
+the row sums of its rows and, off the diagonal, the column sums of its columns'
+rows.  The pass hands out super-tiles of a x a blocks: super-tile (Is, Js),
+Is <= Js, accumulates the row sums of each of its block rows over its columns and
+stores them to slot Js of those rows, and the column sums of each of its block
+columns over its rows, stored to slot Is of those rows -- or, for a diagonal
+super-tile with a > 1, to the extra slot Ts.  Every (slot, cluster, row) is
 written exactly once, and the slots of a row add up to S.  This test builds the
-slots exactly as described (numpy, no GPU) for ragged n and compares their sum
-with the plain definition, so a wrong slot, a missing block or a double-counted
-diagonal would show.  It also checks the block-packed, swizzled tile layout the
-K build writes and the stream's loads expect: every element of the triangle is
-stored once, at a distinct offset, inside its tile.
+slots exactly as described (numpy, no GPU) for ragged n and every super-tile edge,
+and compares their sum with the plain definition, so a wrong slot, a missing block
+or a double-counted diagonal would show.  It also checks the block-packed, swizzled
+tile layout the K builds write and the stream's loads expect: every element of the
+triangle is stored once, at a distinct offset, inside its tile.
 """
 import numpy as np
 import pytest
@@ -17,33 +21,46 @@ import pytest
 B = 128
 
 
-def _slots(K, lab, k):
+def _slots(K, lab, k, a):
     n = K.shape[0]
     T = (n + B - 1) // B
-    slots = np.full((T, k, n), np.nan)
-    for I in range(T):
-        rI = slice(I * B, min(n, I * B + B))
-        for J in range(I, T):
-            cJ = slice(J * B, min(n, J * B + B))
-            blk = K[rI, cJ]
-            for c in range(k):
-                # row sums of block (I, J) over its columns of cluster c -> slot J, rows of I
-                assert np.all(np.isnan(slots[J, c, rI]))
-                slots[J, c, rI] = blk[:, lab[cJ] == c].sum(axis=1)
-                if I != J:
-                    # column sums over its rows of cluster c -> slot I, rows of J
-                    assert np.all(np.isnan(slots[I, c, cJ]))
-                    slots[I, c, cJ] = blk[lab[rI] == c, :].sum(axis=0)
+    Ts = (T + a - 1) // a
+    slots = np.full((Ts + (1 if a > 1 else 0), k, n), np.nan)
+
+    def rows(I):
+        return slice(I * B, min(n, I * B + B))
+
+    def store(slot, I, v):
+        assert np.all(np.isnan(slots[slot, :, rows(I)]))
+        slots[slot, :, rows(I)] = v
+
+    for Is in range(Ts):
+        for Js in range(Is, Ts):
+            I0, I1, J0, J1 = Is * a, min(Is * a + a, T), Js * a, min(Js * a + a, T)
+            colacc = {J: np.zeros((k, rows(J).stop - rows(J).start)) for J in range(J0, J1)}
+            for I in range(I0, I1):
+                rowacc = np.zeros((k, rows(I).stop - rows(I).start))
+                for J in range(max(I, J0), J1):
+                    blk = K[rows(I), rows(J)]
+                    for c in range(k):
+                        rowacc[c] += blk[:, lab[rows(J)] == c].sum(axis=1)    # row sums
+                        if I != J:
+                            colacc[J][c] += blk[lab[rows(I)] == c, :].sum(axis=0)   # column sums
+                    if J == J1 - 1:
+                        store(Js, I, rowacc)
+                    if I == min(J, I1 - 1) and (I != J or a > 1):
+                        store(Ts if Is == Js else Is, J, colacc[J])
     return slots
 
 
-@pytest.mark.parametrize("n,k", [(1, 1), (97, 3), (128, 2), (300, 4), (513, 8)])
-def test_slots_sum_to_segment_sums(n, k):
+@pytest.mark.parametrize("a", [1, 2, 4])
+@pytest.mark.parametrize("n,k", [(1, 1), (97, 3), (128, 2), (300, 4), (513, 8), (1100, 16)])
+def test_slots_sum_to_segment_sums(n, k, a):
     rng = np.random.default_rng(n * 31 + k)
     X = rng.standard_normal((n, 3))
     K = np.exp(-((X[:, None, :] - X[None, :, :]) ** 2).sum(-1))    # a symmetric K
     lab = rng.integers(0, k, size=n)
-    slots = _slots(K, lab, k)
+    slots = _slots(K, lab, k, a)
     assert not np.isnan(slots).any()                                 # every slot written
     S = np.stack([K[:, lab == c].sum(axis=1) for c in range(k)])     # [c][i]
     np.testing.assert_allclose(slots.sum(axis=0), S, rtol=1e-12, atol=1e-12)
