@@ -1,15 +1,25 @@
 #!/usr/bin/env python3
 """Kernel K-means throughput on GB300: iterations/s of whole fits, plus K-build TFLOP/s.
 
-One step = one complete ``popcorn_fit`` through the C ABI on the rings workload
-(n = 20,000 points in the plane zero-padded to d = 8, k = 4, Gaussian kernel
-sigma = 0.5, random initial labels, passes until no label changes, at most
-100; K materialized in FP32 = 1.6 GB, larger than L2, so every pass streams it
-from HBM).  A step runs every row of the hot path: the K build (norms, Gram
-tiles, kernel epilogue), then per pass the K-streaming segmented reduction,
-the self-similarity sums, and the distance/argmin/histogram pass.
+One step = one complete ``popcorn_fit`` through the C ABI on the images workload
+(n = 70,000 points, d = 784: integers 0..255 / 255 with 80% of each row zeroed,
+an MNIST-shaped stand-in; k = 10, Gaussian kernel sigma = 28, random initial
+labels, 50 fixed passes; K stored in FP32 as the block-packed upper triangle,
+9.9 GB, far larger than L2, so every pass streams it from HBM).  A step runs
+every row of the hot path: the K build (norms, Gram tiles, kernel epilogue),
+then per pass the K-streaming segmented reduction (the symmetric pass: blocks on
+and above the diagonal, row and column sums), the self-similarity sums, and the
+distance/argmin/histogram pass.
+
+``value`` is the plain FP32 form (CUDA-core K build).  The same line carries the
+BF16X3 and BF16 forms (tensor-core K builds) with their objective errors against
+the FP64 oracle, the rooflines of the dominant kernels, and extra legs for the
+other workloads: rings (n = 20,000, d = 8, to convergence), blobs (n = 2,000,
+30 passes, L2-resident), the 256-instance batch (one CUDA graph) and the
+n = 200,000 mixture on the recompute path (FP8 and BF16).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload images|rings|blobs|mixture|batched] [--no-extras]
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
 workload (rank 0 only).  Under torchrun each rank runs an independent replica
@@ -32,13 +42,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Kernel K-means iters/s + K-build TFLOP/s, FP32 vs BF16/batched at ≤1e-3 obj err"
-WORKLOAD = "rings"
-WORKLOAD_DESC = ("rings n=20000 d=8 (2 + 6 zero pad) k=4, Gaussian sigma=0.5, random init, "
-                 "passes to convergence (max 100), K materialized FP32 (1.6 GB)")
+WORKLOAD = "images"
+WORKLOAD_DESC = ("images n=70000 d=784 k=10 (integers 0..255/255, 80% of each row zeroed), Gaussian sigma=28, "
+                 "random init, 50 fixed passes, K stored FP32 (block-packed upper triangle)")
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+GB300_SMS = 152
+FP32_LANES_PER_CLK_SM = 128          # FP32 FMA/ADD lanes per clock per SM
+XU_EX2_PER_CLK_SM = 32               # ex2.approx per clock per SM (microbenchmark)
 
 
 def aggregate_over_ranks(times, counts, dist, device):
@@ -62,10 +76,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' legs")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink n (profiling captures only; the reported workload is scale 1)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["rings", "blobs", "images", "mixture", "batched"],
-                    help="rings (default, the reported line), blobs, images, mixture (recompute path), "
+    ap.add_argument("--workload", default=WORKLOAD, choices=["images", "rings", "blobs", "mixture", "batched"],
+                    help="images (default, the reported line), rings, blobs, mixture (recompute path), "
                          "batched (256 instances in one graph)")
     ap.add_argument("--autotune", default="on", choices=["on", "off"],
                     help="time candidate schedules in the warm-up (batched and recompute paths)")
@@ -74,6 +89,8 @@ def parse():
     ap.add_argument("--k-pass", default="auto", choices=["auto", "full", "symmetric"],
                     help="how a pass reads a stored FP32 K: the library's choice, the full square, or the blocks "
                          "on and above the diagonal (row and column sums, then a fold)")
+    ap.add_argument("--sym-tile", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="super-tile edge of the symmetric pass (0: the library's choice)")
     ap.add_argument("--compare", default=None, choices=["paper"],
                     help="paper: also time the paper's formulation through library calls (cuBLAS GEMM + "
                          "elementwise kernel function, cuSPARSE SpMM/SpMV per pass) on the same inputs")
@@ -88,57 +105,26 @@ def dist_env():
 
 
 def peaks():
+    """The roofline denominators: measured HBM copy bandwidth and BF16 GEMM rate, else the fallbacks."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             m = json.load(f)
-        return float(m["hbm_gbs"]), "measured (MEASURED_PEAKS.json: STREAM-style copy)"
+        return {"hbm": float(m["hbm_gbs"]), "bf16": float(m["bf16_tflops"]),
+                "bf16_sustained": float(m.get("bf16_tflops_sustained", m["bf16_tflops"])),
+                "sm_mhz": float(m.get("sm_max_mhz", 2070.0)), "source": "measured (MEASURED_PEAKS.json)"}
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, earlier GB300 copy measurement)"
+        return {"hbm": FALLBACK_HBM_GBS, "bf16": FALLBACK_BF16_TFLOPS, "bf16_sustained": 1700.0, "sm_mhz": 2070.0,
+                "source": "fallback (6.8 TB/s, 1.9 PFLOP/s bf16: an earlier GB300 measurement)"}
 
 
-# exp2 unit (MUFU) rate measured on GB300: 32 ex2.approx per clock per SM (152 SMs)
-XU_EX2_PER_CLK_SM = 32
-GB300_SMS = 152
-
-
-def recompute_rooflines(wl, avg_ms: float, clk: dict):
-    """Rooflines of one recompute pass (sort + tiles + reduction), the binding one first.
-
-    tensor: 2 n^2 d algorithmic MMA flops against the measured BF16 burst peak (FP8:
-    twice that, the nominal FP8/BF16 ratio); alu: n^2 exp2 evaluations (Gaussian)
-    against 32 per clock per SM at the maximum SM clock."""
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            m = json.load(f)
-        bf16, src = float(m["bf16_tflops"]), "measured bf16 burst (MEASURED_PEAKS.json)"
-        sm_mhz = float(m.get("sm_max_mhz", 2070.0))
-    except Exception:
-        bf16, src, sm_mhz = 1900.0, "fallback 1.9 PFLOP/s bf16", 2070.0
-    peak_t = bf16 * (2.0 if wl.precision == "fp8" else 1.0)
-    n, d = float(wl.n), float(wl.d)
-    sec = avg_ms / 1e3 if avg_ms > 0 else float("inf")
-    t_ach = 2.0 * n * n * d / sec / 1e12
-    tensor = {"kernel": "recompute_kernel", "bound": "tensor", "achieved": t_ach, "peak": peak_t,
-              "unit": "TFLOP/s", "frac": t_ach / peak_t, "traffic": None,
-              "peak_source": src + (" x2 for FP8 (nominal ratio)" if wl.precision == "fp8" else ""),
-              "algorithmic_flops_per_launch": 2.0 * n * n * d, "avg_launch_ms": avg_ms}
-    peak_x = XU_EX2_PER_CLK_SM * GB300_SMS * sm_mhz * 1e6 / 1e12
-    x_ach = n * n / sec / 1e12
-    alu = {"kernel": "recompute_kernel", "bound": "alu", "achieved": x_ach, "peak": peak_x,
-           "unit": "Texp2/s", "frac": x_ach / peak_x, "traffic": None,
-           "peak_source": f"{XU_EX2_PER_CLK_SM} ex2/clk/SM x {GB300_SMS} SMs x {sm_mhz:.0f} MHz (ex2 microbenchmark)",
-           "algorithmic_exp2_per_launch": n * n, "avg_launch_ms": avg_ms}
-    if wl.kernel["kind"] != "gaussian":
-        return tensor, None
-    return (tensor, alu) if tensor["frac"] >= alu["frac"] else (alu, tensor)
-
-
-def recorded_traffic(kernel: str, src_file: str):
+def recorded_traffic(kernel: str, src_file: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)[kernel]
+        if t.get("workload") != workload:
+            return None
         with open(os.path.join(ROOT, "paper_2501_05587_gb300", "csrc", src_file), "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
         if t.get("source_sha256") != sha:
@@ -146,6 +132,103 @@ def recorded_traffic(kernel: str, src_file: str):
         return float(t["dram_bytes_per_launch"])
     except Exception:
         return None
+
+
+def sym_bytes(n: int, k: int, nslots: int):
+    """Bytes of one symmetric stream launch: the scope table's algorithmic figure for triangular
+    storage (2 n (n + 1) + n: the unique entries of K once, plus the labels), and what the
+    kernel moves besides: the 128-blocks of the packed triangle, the slot stores."""
+    T = (n + 127) // 128
+    return {"algorithmic": 2.0 * n * (n + 1) + n,
+            "packed_tiles": 65536.0 * T * (T + 1) / 2,
+            "slot_stores": 4.0 * nslots * k * n,
+            "labels": 256.0 * T * (T + 1) / 2}
+
+
+def pass_roofline(wl, prof, pk):
+    """HBM roofline of the dominant kernel of a pass (stored K): the symmetric stream or the
+    full-square reduction.  Its launch time comes from the library's CUDA events on the
+    launching stream (reduce minus fold), averaged over the profiled fits' passes."""
+    n, k = wl.n, wl.k
+    info = prof[-1]["info"]
+    passes = sum(r["iterations"] for r in prof)
+    red = sum(r["info"]["reduce_ms"] for r in prof)
+    fold = sum(r["info"]["fold_ms"] for r in prof)
+    if info["k_pass_used"] == 1:
+        b = sym_bytes(n, k, info["schedule"][2])
+        ms = (red - fold) / max(passes, 1)
+        ach = b["algorithmic"] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        return {"kernel": "reduce_sym_kernel", "bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
+                "frac": ach / pk["hbm"],
+                "traffic": recorded_traffic("reduce_sym_kernel", "reduce_sym.cu", wl.name),
+                "peak_source": pk["source"] + " HBM copy", "algorithmic_bytes_per_launch": b["algorithmic"],
+                "moved_bytes_per_launch": {x: b[x] for x in ("packed_tiles", "slot_stores", "labels")},
+                "avg_launch_ms": ms, "fold_avg_launch_ms": fold / max(passes, 1),
+                "pass_avg_ms": (red + sum(r["info"]["assign_ms"] for r in prof)) / max(passes, 1),
+                "schedule": {"super_tile": info["schedule"][0], "ring": info["schedule"][1],
+                             "slots": info["schedule"][2], "accumulators": info["schedule"][3]}}
+    ms = red / max(passes, 1)
+    alg = 4.0 * n * n + n
+    ach = alg / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"kernel": "reduce_kernel", "bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
+            "frac": ach / pk["hbm"], "traffic": recorded_traffic("reduce_kernel", "iterate.cu", wl.name),
+            "peak_source": pk["source"] + " HBM copy", "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms}
+
+
+def kbuild_roofline(wl, precision, kb_ms, pk):
+    """Roofline of the K build.  FP32 (CUDA cores): bound by the FP32 lanes -- a Gaussian entry
+    takes a subtract and a multiply-add per coordinate, a polynomial / linear one a multiply-add,
+    over the n (n + 1) / 2 unique pairs; peak = 128 lanes x 152 SMs x the maximum SM clock.
+    BF16 / BF16X3 (tcgen05): the executed MMA flops of the row-pair tiles (BF16X3: three
+    products per k-step) against the measured BF16 peak."""
+    n, d = float(wl.n), float(wl.d)
+    sec = kb_ms / 1e3
+    if precision == "fp32":
+        per = 2.0 if wl.kernel["kind"] == "gaussian" else 1.0
+        ops = per * n * (n + 1) / 2 * d
+        peak = FP32_LANES_PER_CLK_SM * GB300_SMS * pk["sm_mhz"] * 1e6 / 1e12
+        ach = ops / sec / 1e12
+        return {"kernel": "kbuild_simt_kernel", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tlane-ops/s",
+                "frac": ach / peak, "traffic": recorded_traffic("kbuild_simt_kernel", "kbuild_simt.cu", wl.name),
+                "peak_source": f"{FP32_LANES_PER_CLK_SM} FP32 lanes/clk/SM x {GB300_SMS} SMs x "
+                               f"{pk['sm_mhz']:.0f} MHz (unit counts and clock)",
+                "algorithmic_lane_ops_per_launch": ops, "avg_launch_ms": kb_ms}
+    T = (wl.n + 127) // 128
+    T2 = (T + 1) // 2
+    tiles = T2 * T - T2 * (T2 - 1)
+    dpad = (wl.d + 63) // 64 * 64
+    depth = dpad * (3 if precision == "bf16x3" else 1)
+    flops = tiles * 2.0 * 128 * 128 * 2.0 * depth
+    ach = flops / sec / 1e12
+    return {"kernel": "kbuild_tc_kernel", "bound": "tensor", "achieved": ach, "peak": pk["bf16"], "unit": "TFLOP/s",
+            "frac": ach / pk["bf16"], "traffic": None, "peak_source": pk["source"] + " bf16 burst",
+            "executed_mma_flops_per_launch": flops, "avg_launch_ms": kb_ms}
+
+
+def recompute_rooflines(wl, avg_ms: float, pk):
+    """Rooflines of one recompute pass (sort + tiles + reduction), the binding one first.
+
+    tensor: 2 n^2 d algorithmic MMA flops against the measured BF16 burst peak (FP8:
+    twice that, the nominal FP8/BF16 ratio); alu: n^2 exp2 evaluations (Gaussian)
+    against 32 per clock per SM at the maximum SM clock."""
+    peak_t = pk["bf16"] * (2.0 if wl.precision == "fp8" else 1.0)
+    n, d = float(wl.n), float(wl.d)
+    sec = avg_ms / 1e3 if avg_ms > 0 else float("inf")
+    t_ach = 2.0 * n * n * d / sec / 1e12
+    tensor = {"kernel": "recompute_kernel", "bound": "tensor", "achieved": t_ach, "peak": peak_t,
+              "unit": "TFLOP/s", "frac": t_ach / peak_t, "traffic": None,
+              "peak_source": pk["source"] + " bf16 burst" + (" x2 for FP8 (nominal ratio)" if wl.precision == "fp8"
+                                                             else ""),
+              "algorithmic_flops_per_launch": 2.0 * n * n * d, "avg_launch_ms": avg_ms}
+    peak_x = XU_EX2_PER_CLK_SM * GB300_SMS * pk["sm_mhz"] * 1e6 / 1e12
+    x_ach = n * n / sec / 1e12
+    alu = {"kernel": "recompute_kernel", "bound": "alu", "achieved": x_ach, "peak": peak_x,
+           "unit": "Texp2/s", "frac": x_ach / peak_x, "traffic": None,
+           "peak_source": f"{XU_EX2_PER_CLK_SM} ex2/clk/SM x {GB300_SMS} SMs x {pk['sm_mhz']:.0f} MHz (ex2 microbenchmark)",
+           "algorithmic_exp2_per_launch": n * n, "avg_launch_ms": avg_ms}
+    if wl.kernel["kind"] != "gaussian":
+        return tensor, None
+    return (tensor, alu) if tensor["frac"] >= alu["frac"] else (alu, tensor)
 
 
 class ClockSampler:
@@ -203,30 +286,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample_rate(wl, n_sample: int, budget_s: float):
-    """The FP64 oracle as it stands, on the first n_sample points of the workload.
-
-    Returns (passes per second on the sample, sample description, passes, seconds).
-    """
-    import oracle
-
-    P = wl.P[:n_sample]
-    lab = wl.init_labels[:n_sample].copy()
-    t0 = time.perf_counter()
-    K = oracle.kernel_matrix(P, wl.kernel)
-    t_build = time.perf_counter() - t0
-    passes = 0
-    t1 = time.perf_counter()
-    while passes < wl.max_iter and time.perf_counter() - t1 < budget_s:
-        st = oracle.step(K, lab, wl.k)
-        passes += 1
-        lab = st["labels"]
-        if st["changed"] == 0:
-            break
-    t_loop = time.perf_counter() - t1
-    return passes, t_build, t_loop
-
-
 def oracle_cores():
     try:
         from threadpoolctl import threadpool_info
@@ -236,15 +295,37 @@ def oracle_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(wl, n_sample=16000, budget_s=25.0):
-    passes, t_build, t_loop = oracle_sample_rate(wl, n_sample, budget_s)
-    # per-pass and K-build work scale with n^2; convert to full-workload iters/s
+def oracle_fit_sample(wl, n_sample: int):
+    """The FP64 oracle as it stands on the first n_sample points of the workload: K build,
+    then the workload's passes from its initial labels.  Returns (K, fit, build s, loop s)."""
+    import oracle
+
+    P = wl.P[:n_sample]
+    lab = wl.init_labels[:n_sample].copy()
+    t0 = time.perf_counter()
+    K = oracle.kernel_matrix(P, wl.kernel)
+    t_build = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    fit = oracle.fit(K, wl.k, lab, wl.max_iter, check_convergence=wl.check_convergence)
+    t_loop = time.perf_counter() - t1
+    return K, fit, t_build, t_loop
+
+
+def cpu_baseline(wl, n_sample: int):
+    """Oracle K build + passes on a bounded sample, its whole-fit rate scaled to the full
+    workload by (n_sample / n)^2 (both the build and each pass scale with n^2)."""
+    K, fit, t_build, t_loop = oracle_fit_sample(wl, n_sample)
     scale = (n_sample / wl.n) ** 2
-    it_s = passes / t_loop * scale if t_loop > 0 else 0.0
-    return {"value": it_s, "unit": "iters/s", "cores": oracle_cores(), "kind": "oracle",
-            "sample": (f"first {n_sample} of {wl.n} points, {passes} FP64 passes in {t_loop:.2f} s "
-                       f"(K build {t_build:.2f} s); rate scaled by (n_sample/n)^2 = {scale:.4f} "
-                       f"to the full workload")}
+    it_s = fit["iterations"] / (t_build + t_loop) * scale
+    base = {"value": it_s, "unit": "iters/s", "cores": oracle_cores(), "kind": "oracle",
+            "sample": (f"first {n_sample} of {wl.n} points: FP64 oracle K build ({t_build:.2f} s) + "
+                       f"{fit['iterations']} passes ({t_loop:.2f} s); whole-fit rate scaled by (n_sample/n)^2 = "
+                       f"{scale:.3g} to the full workload")}
+    return base, K, fit
+
+
+SAMPLE = {"images": 2500, "rings": 12000, "blobs": 2000, "mixture": 6000}
+REF_SAMPLE = {"images": 1200, "rings": 8000, "blobs": 2000, "mixture": 3000}
 
 
 def run_reference(args, rank, world):
@@ -252,84 +333,180 @@ def run_reference(args, rank, world):
         return 0
     import synth
 
-    wl = synth.workload(WORKLOAD)
-    n_sample = 12000
+    wl = synth.workload(args.workload if args.workload != "batched" else WORKLOAD)
+    n_s = REF_SAMPLE.get(wl.name.split("_")[0], 1500)
     for _ in range(args.warmup):
-        oracle_sample_rate(wl, 2000, 2.0)
+        oracle_fit_sample(wl, max(n_s // 2, 16))
     t_all = 0.0
     passes_all = 0
     for _ in range(args.steps):
-        passes, t_build, t_loop = oracle_sample_rate(wl, n_sample, 15.0)
-        t_all += t_build + t_loop
-        passes_all += passes
-    scale = (n_sample / wl.n) ** 2
+        _, fit, tb, tl = oracle_fit_sample(wl, n_s)
+        t_all += tb + tl
+        passes_all += fit["iterations"]
+    scale = (n_s / wl.n) ** 2
     value = passes_all / t_all * scale
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "n": wl.n, "d": wl.d, "k": wl.k},
+            "config": {"workload": WORKLOAD_DESC if wl.name.startswith("images") else wl.name,
+                       "n": wl.n, "d": wl.d, "k": wl.k},
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": oracle_cores(), "kind": "oracle",
-                             "sample": (f"each step: FP64 oracle K build + passes on the first {n_sample} "
-                                        f"points; whole-fit rate scaled by (n_sample/n)^2 = {scale:.4f}")},
+                             "sample": (f"each step: FP64 oracle K build + {wl.max_iter} passes on the first "
+                                        f"{n_s} points; whole-fit rate scaled by (n_sample/n)^2 = {scale:.3g}")},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_batched(args):
-    """256 independent instances (n in [500, 8000], d in {8, 32, 64}, k in [4, 64], polynomial and
-    Gaussian kernels), 30 passes each, one popcorn_fit_batched call per step."""
-    import torch
+def timed(torch, stream, fn, steps, warmup):
+    """warmup untimed calls, then `steps` calls between CUDA events on `stream` (synchronized
+    on both sides); returns (ms, results)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = [fn() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), res
 
+
+def fit_form(pc, torch, stream, wl, P, lab, out, precision, steps, warmup, **kw):
+    """One precision form of the workload: timed fits (no library events), then the same fits
+    with the library's per-kernel events (the breakdown and the kernels' launch times)."""
+    def step(timing=False):
+        return pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
+                              precision=precision, timing=timing, labels_out=out, store_k=wl.store_k, **kw)
+
+    ms, res = timed(torch, stream, step, steps, warmup)
+    prof = [step(True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    iters = sum(r["iterations"] for r in res)
+    kb_ms = sum(r["info"]["kbuild_ms"] for r in prof) / len(prof)
+    red = sum(r["info"]["reduce_ms"] for r in prof) / len(prof)
+    asg = sum(r["info"]["assign_ms"] for r in prof) / len(prof)
+    n, d = wl.n, wl.d
+    return {"ms": ms, "res": res, "prof": prof, "iters": iters,
+            "summary": {"value": iters / (ms / 1e3), "unit": "iters/s", "ms_per_fit": ms / steps,
+                        "passes_per_fit": iters / steps, "objective": res[-1]["objective"],
+                        "kbuild_ms": kb_ms,
+                        "kbuild_tflops": float(n) * (n + 1) * d / (kb_ms / 1e3) / 1e12 if kb_ms > 0 else None,
+                        "kbuild_tflops_gemm_equivalent": 2.0 * n * n * d / (kb_ms / 1e3) / 1e12 if kb_ms > 0 else None,
+                        "breakdown_ms_per_fit": {"kbuild": kb_ms, "reduce": red, "assign": asg},
+                        "k_pass": {0: "recompute", 1: "symmetric", 2: "full"}[prof[-1]["info"]["k_pass_used"]],
+                        "gpu_launches_per_fit": res[-1]["info"]["kernel_launches"]}}
+
+
+def graph_us_per_pass(pc, torch, wl, P, lab, out, precision, steps, **kw):
+    """Fixed-iteration fits with phase events only: the passes run as one CUDA graph, and
+    loop_ms is that graph's time (every pass plus the objective pass)."""
+    res = [pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=False,
+                          precision=precision, timing="phases", labels_out=out, store_k=wl.store_k, **kw)
+           for _ in range(steps)]
+    torch.cuda.synchronize()
+    return 1e3 * sum(r["info"]["loop_ms"] for r in res) / sum(r["iterations"] for r in res)
+
+
+def leg_workload(pc, torch, stream, name, steps, warmup, pk, **kw):
+    """An extra workload leg: its default form, timed like the headline."""
     import synth
-    import paper_2501_05587_gb300 as pc
 
-    prec = args.precision or "fp32"
-    wls = synth.batched_instances(int(256 * args.scale) or 1, seed=0)
+    wl = synth.workload(name)
+    P = torch.from_numpy(wl.P).cuda()
+    lab = torch.from_numpy(wl.init_labels).cuda()
+    out = torch.empty_like(lab)
+    f = fit_form(pc, torch, stream, wl, P, lab, out, wl.precision, steps, warmup, **kw)
+    s = f["summary"]
+    s["workload"] = wl.name
+    if wl.store_k:
+        s["roofline_pass"] = pass_roofline(wl, f["prof"], pk)
+        loop = sum(r["info"]["loop_ms"] for r in f["prof"]) / len(f["prof"])
+        s["loop_us_per_pass_plain_launches"] = 1e3 * loop / max(s["passes_per_fit"], 1)
+        if not wl.check_convergence:
+            s["loop_us_per_pass_graph"] = graph_us_per_pass(pc, torch, wl, P, lab, out, wl.precision, steps, **kw)
+    else:
+        avg = sum(r["info"]["reduce_ms"] for r in f["prof"]) / max(1, sum(r["iterations"] for r in f["prof"]))
+        s["pass_ms"] = avg
+        s["roofline_pass"], s["roofline_pass_secondary"] = recompute_rooflines(wl, avg, pk)
+        s["schedule"] = f["prof"][-1]["info"]["schedule"]
+    return s, wl, f
+
+
+def leg_batched(pc, torch, stream, steps, warmup, precision, autotune, scale=1.0):
+    """256 independent instances (n in [500, 8000], d in {8, 32, 64}, k in [4, 64], polynomial and
+    Gaussian kernels), 30 passes each, one popcorn_fit_batched call (one CUDA graph) per step."""
+    import synth
+
+    wls = synth.batched_instances(int(256 * scale) or 1, seed=0)
     insts = [{"P": torch.from_numpy(w.P).cuda(), "k": w.k, "kernel": w.kernel,
               "init_labels": torch.from_numpy(w.init_labels).cuda()} for w in wls]
 
     def step():
-        return pc.popcorn_fit_batched(insts, max_iter=30, precision=prec, check_convergence=False, timing=True,
-                                      autotune=args.autotune == "on")
+        return pc.popcorn_fit_batched(insts, max_iter=30, precision=precision, check_convergence=False, timing=True,
+                                      autotune=autotune)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    res = [step() for _ in range(args.steps)]
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms, res = timed(torch, stream, step, steps, warmup)
     passes = sum(sum(r["iterations"]) for r in res)
     kbytes = sum(4.0 * w.n * w.n for w in wls)
     graph_ms = sum(r["info"]["loop_ms"] for r in res) / len(res)
-    # the same instances as separate popcorn_fit calls (the unbatched form), one sweep
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
-    e2.record()
+    e2.record(stream)
     for x in insts:
-        pc.popcorn_fit(x["P"], x["k"], x["kernel"], x["init_labels"], max_iter=30, precision=prec,
+        pc.popcorn_fit(x["P"], x["k"], x["kernel"], x["init_labels"], max_iter=30, precision=precision,
                        check_convergence=False)
-    e3.record()
+    e3.record(stream)
     torch.cuda.synchronize()
     seq_ms = e2.elapsed_time(e3)
-    line = {"metric": METRIC, "value": passes / (ms / 1e3), "unit": "instance-passes/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": f"batched: {len(wls)} instances, 30 passes each, K stored FP32 "
-                                   f"({kbytes / 1e9:.1f} GB)", "precision": prec},
+    return {"value": passes / (ms / 1e3), "unit": "instance-passes/s", "ms_per_step": ms / steps,
+            "precision": precision, "instances": len(wls), "K_GB": kbytes / 1e9,
             "graph_ms": graph_ms, "effective_GBps_of_K_reads": kbytes * 30 / (graph_ms / 1e3) / 1e9,
-            "separate_fits_ms": seq_ms, "batched_speedup_vs_separate_fits": seq_ms / (ms / args.steps),
-            "gpu_launches": sum(r["info"]["kernel_launches"] for r in res),
-            "schedule": {"autotune": args.autotune, "columns_per_unit": res[-1]["info"]["schedule"][0],
+            "separate_fits_ms": seq_ms, "batched_speedup_vs_separate_fits": seq_ms / (ms / steps),
+            "gpu_launches_per_step": res[-1]["info"]["kernel_launches"],
+            "schedule": {"autotune": autotune, "columns_per_unit": res[-1]["info"]["schedule"][0],
                          "warps_per_block": res[-1]["info"]["schedule"][1],
                          "blocks_per_sm": res[-1]["info"]["schedule"][2]}}
+
+
+def run_batched(args):
+    import torch
+
+    import paper_2501_05587_gb300 as pc
+
+    prec = args.precision or "fp32"
+    stream = torch.cuda.current_stream()
+    s = leg_batched(pc, torch, stream, args.steps, args.warmup, prec, args.autotune == "on", args.scale)
+    line = {"metric": METRIC, "value": s["value"], "unit": s["unit"], "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": s["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"batched: {s['instances']} instances, 30 passes each, K stored FP32 "
+                                   f"({s['K_GB']:.1f} GB)", "precision": prec},
+            "gpu_launches": s["gpu_launches_per_step"] * args.steps, "batched": s}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def sample_objective_errors(pc, torch, wl, Ko, ofit, n_sample, forms):
+    """GPU fits of each precision form on the oracle's sample (same points, same initial labels,
+    same passes): the FP64 objective of their labels against the objective the oracle's fit
+    reaches, and the reported objective against the FP64 objective of the same labels."""
+    import oracle
+
+    P = torch.from_numpy(np.ascontiguousarray(wl.P[:n_sample])).cuda()
+    lab = torch.from_numpy(np.ascontiguousarray(wl.init_labels[:n_sample])).cuda()
+    out = {}
+    for prec in forms:
+        r = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
+                           precision=prec, store_k=wl.store_k)
+        labels = r["labels"].cpu().numpy()
+        J = oracle.objective(Ko, labels, wl.k)
+        out[prec] = {"objective_rel_err_vs_oracle_fit": abs(J - ofit["objective"]) / abs(ofit["objective"]),
+                     "reported_vs_fp64_of_labels": abs(r["objective"] - J) / abs(J),
+                     "labels_equal_to_oracle_fit": float(np.mean(labels == ofit["labels"]))}
+    return out
 
 
 def run_paper_pipeline(args):
@@ -472,62 +649,36 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    pk = peaks()
     wl = synth.workload(args.workload, scale=args.scale)
     if args.precision:
         wl.precision = args.precision
+    headline = args.workload == WORKLOAD and args.scale == 1.0 and not args.precision
     P = torch.from_numpy(wl.P).cuda()
     lab = torch.from_numpy(wl.init_labels).cuda()
     out = torch.empty_like(lab)
-
     # the recompute path's schedule (row blocks per tile, units per SM) is autotuned in the warm-up
-    tune = args.autotune == "on" and not wl.store_k
-
-    def step(timing=True):
-        return pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
-                              precision=wl.precision, timing=timing, labels_out=out, store_k=wl.store_k,
-                              autotune=tune, k_pass=args.k_pass)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
+    kw = {"autotune": args.autotune == "on" and not wl.store_k, "k_pass": args.k_pass, "sym_tile": args.sym_tile}
 
     stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    results, prof = [], []
     with ClockSampler(local) as clocks:
         barrier()
         torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            results.append(step(timing=False))
-        e1.record(stream)
+        main_form = fit_form(pc, torch, stream, wl, P, lab, out, wl.precision, args.steps, args.warmup, **kw)
         torch.cuda.synchronize()
         barrier()
-        # The same fits again with the library's per-kernel CUDA events (on the launch stream):
-        # the phase breakdown and the roofline kernel's launch time come from these.  The events
-        # cost a few percent of a fit, so they stay out of the timed region above.
-        for _ in range(args.steps):
-            prof.append(step(timing=True))
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
     clk = clocks.summary()
-
-    iters = sum(r["iterations"] for r in results)
-    red_ms = sum(r["info"]["reduce_ms"] for r in prof)
-    red_n = sum(r["info"]["reduce_launches"] for r in prof)
-    asg_ms = sum(r["info"]["assign_ms"] for r in prof)
-    kb_ms = sum(r["info"]["kbuild_ms"] for r in prof)
-    launches = sum(r["info"]["kernel_launches"] for r in results)
+    ms, iters = main_form["ms"], main_form["iters"]
+    launches = sum(r["info"]["kernel_launches"] for r in main_form["res"])
 
     # end to end through the same call with pinned host buffers (copies inside the timed region)
     Ph = torch.from_numpy(wl.P).pin_memory()
     Lh = torch.from_numpy(wl.init_labels).pin_memory()
     Oh = torch.empty(wl.n, dtype=torch.int32).pin_memory()
+
     def host_step():
         return pc.popcorn_fit(Ph, wl.k, wl.kernel, Lh, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
-                              precision=wl.precision, labels_out=Oh, store_k=wl.store_k, autotune=tune,
-                              k_pass=args.k_pass)
+                              precision=wl.precision, labels_out=Oh, store_k=wl.store_k, **kw)
 
     for _ in range(args.warmup):
         host_step()
@@ -546,37 +697,20 @@ def main():
     if rank == 0:
         n, k = wl.n, wl.k
         value = iters_all / (ms / 1e3)
-        kb_flops = float(n) * (n + 1) * wl.d           # algorithmic: n(n+1)/2 unique dot products, 2d flops each
-        alg_bytes = 4.0 * n * n + n                      # K read once + label bytes, per reduction launch
-        avg_red_ms = red_ms / max(red_n, 1)
-        peak, peak_src = peaks()
-        achieved = alg_bytes / (avg_red_ms / 1e3) / 1e9 if avg_red_ms > 0 else 0.0
-        traffic = recorded_traffic("reduce_kernel", "iterate.cu")
-        roof = {"kernel": "reduce_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_red_ms}
-        roof2 = None
-        if results[-1]["info"]["k_pass_used"] == 1:
-            # symmetric pass: the stream kernel alone (its CUDA-event time is the pass's
-            # reduction minus the fold, both recorded by the library on the launch stream)
-            T = (n + 127) // 128
-            tri = sum(min(128, n - 128 * I) * (n - 128 * I) for I in range(T))   # elements of blocks (I, J >= I)
-            fold_ms = sum(r["info"]["fold_ms"] for r in prof)
-            passes = sum(r["iterations"] for r in prof)
-            avg_stream_ms = (red_ms - fold_ms) / max(passes, 1)
-            alg_bytes = 4.0 * tri + 4.0 * T * k * n + 256.0 * T * (T + 1) / 2   # K blocks, slots, labels
-            achieved = alg_bytes / (avg_stream_ms / 1e3) / 1e9 if avg_stream_ms > 0 else 0.0
-            roof = {"kernel": "reduce_sym_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
-                    "unit": "GB/s", "frac": achieved / peak, "traffic": recorded_traffic("reduce_sym_kernel",
-                                                                                         "reduce_sym.cu"),
-                    "peak_source": peak_src, "algorithmic_bytes_per_launch": alg_bytes,
-                    "avg_launch_ms": avg_stream_ms,
-                    "pass": "symmetric: blocks on and above the diagonal, then sym_fold_kernel",
-                    "fold_avg_launch_ms": fold_ms / max(passes, 1)}
-        if not wl.store_k:
-            # recompute pass: tensor cores (2 n^2 d flops) and the exp2 unit (n^2 kernel values)
-            roof, roof2 = recompute_rooflines(wl, avg_red_ms, clk)
+        s = main_form["summary"]
+        prof = main_form["prof"]
+        kb_ms = s["kbuild_ms"]
+        rooflines = []
+        if wl.store_k:
+            rp = pass_roofline(wl, prof, pk)
+            rk = kbuild_roofline(wl, wl.precision, kb_ms, pk)
+            pass_total = s["breakdown_ms_per_fit"]["reduce"] - sum(r["info"]["fold_ms"] for r in prof) / len(prof)
+            # the dominant kernel of a fit: the K build or the stream kernel summed over the passes
+            rooflines = [rk, rp] if kb_ms >= pass_total else [rp, rk]
+            rooflines[0]["share_of_fit"] = (kb_ms if rooflines[0] is rk else pass_total) / s["ms_per_fit"]
+        else:
+            avg = s["breakdown_ms_per_fit"]["reduce"] / max(s["passes_per_fit"], 1)
+            rooflines = [x for x in recompute_rooflines(wl, avg, pk) if x is not None]
         line = {
             "metric": METRIC,
             "value": value,
@@ -590,59 +724,77 @@ def main():
             "vs_baseline": None,
             "dtype": "f32" if wl.precision == "fp32" else f"{wl.precision} operands, f32 accumulate/K",
             "data": "synthetic",
-            "config": {"workload": (WORKLOAD_DESC if args.workload == WORKLOAD and args.scale == 1.0
-                                    else f"{wl.name} scaled x{args.scale}"),
-                       "precision": wl.precision,
-                       "n": n, "d": wl.d, "k": k,
+            "config": {"workload": WORKLOAD_DESC if headline else f"{wl.name} scaled x{args.scale}",
+                       "precision": wl.precision, "n": n, "d": wl.d, "k": k,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": (f"inputs larger than L2 (K = {4 * wl.n * wl.n / 1e9:.2f} GB; "
-                              + ("its upper triangle of 128-blocks" if results[-1]["info"]["k_pass_used"] == 1
-                                 else "all of it") + " streamed every pass)"),
-                       "k_pass": {0: "recompute", 1: "symmetric", 2: "full"}[results[-1]["info"]["k_pass_used"]],
-                       "passes_per_fit": iters / args.steps},
-            "kbuild_tflops": kb_flops / (kb_ms / args.steps / 1e3) / 1e12 if kb_ms > 0 else None,
-            "kbuild_tflops_gemm_equivalent": (2.0 * n * n * wl.d / (kb_ms / args.steps / 1e3) / 1e12
-                                              if kb_ms > 0 else None),
-            "kbuild_ms": kb_ms / args.steps,
-            "loop_iters_per_s": iters / ((red_ms + asg_ms) / 1e3) if red_ms > 0 else None,
-            "breakdown_ms_per_step": {"kbuild": kb_ms / args.steps, "reduce": red_ms / args.steps,
-                                      "assign": asg_ms / args.steps},
-            "roofline": roof,
+                       "l2": (f"inputs larger than L2 (K = {4 * n * n / 1e9:.2f} GB as the full square; "
+                              + ("its block-packed upper triangle" if s["k_pass"] == "symmetric" else
+                                 "all of it" if s["k_pass"] == "full" else "recomputed, never stored")
+                              + " read every pass)"),
+                       "k_pass": s["k_pass"], "passes_per_fit": iters / args.steps},
+            "kbuild_tflops": s["kbuild_tflops"],
+            "kbuild_tflops_gemm_equivalent": s["kbuild_tflops_gemm_equivalent"],
+            "kbuild_ms": kb_ms,
+            "breakdown_ms_per_step": s["breakdown_ms_per_fit"],
+            "pass_ms_graph": (graph_us_per_pass(pc, torch, wl, P, lab, out, wl.precision, args.steps, **kw) / 1e3
+                              if wl.store_k and not wl.check_convergence else None),
+            "objective": s["objective"],
+            "roofline": rooflines[0],
             "e2e": {"value": e2e_iters_all / t_e2e, "unit": "iters/s",
                     "h2d_bytes_per_step": int(e2e_res[0]["info"]["h2d_bytes"]),
                     "d2h_bytes_per_step": int(e2e_res[0]["info"]["d2h_bytes"])},
             "gpu_launches": launches_all,
             "clocks": clk,
         }
-        if roof2 is not None:
-            line["roofline_secondary"] = roof2
-            line["schedule"] = {"autotune": args.autotune, "row_blocks_per_tile": results[-1]["info"]["schedule"][0],
-                                "column_segments": results[-1]["info"]["schedule"][1],
-                                "units_per_sm_target": results[-1]["info"]["schedule"][2]}
-        if args.workload == WORKLOAD and args.scale == 1.0:
-            # the same fits with K stored in FP16: half the bytes per pass (an extra, not the headline)
-            def step16():
-                return pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=True,
-                                      timing=True, labels_out=out, k_storage="fp16")
-            for _ in range(args.warmup):
-                step16()
-            torch.cuda.synchronize()
-            f0 = torch.cuda.Event(enable_timing=True)
-            f1 = torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            r16 = [step16() for _ in range(args.steps)]
-            f1.record(stream)
-            torch.cuda.synchronize()
-            ms16 = f0.elapsed_time(f1)
-            it16 = sum(r["iterations"] for r in r16)
-            red16 = sum(r["info"]["reduce_ms"] for r in r16) / max(1, sum(r["info"]["reduce_launches"] for r in r16))
-            line["k_fp16"] = {"value": it16 / (ms16 / 1e3), "unit": "iters/s", "passes_per_fit": it16 / args.steps,
-                              "objective_rel_diff_vs_fp32_k": abs(r16[0]["objective"] - results[0]["objective"])
-                              / abs(results[0]["objective"]),
-                              "reduce_avg_launch_ms": red16,
-                              "reduce_GBps": (2.0 * n * n + n) / (red16 / 1e3) / 1e9 if red16 > 0 else None}
-        if world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:
-            line["cpu_baseline"] = cpu_baseline(wl)
+        if len(rooflines) > 1:
+            line["roofline_secondary"] = rooflines[1]
+        forms = {}
+        if headline and world == 1:
+            # the tensor-core forms of the same fit: BF16X3 (split-BF16 cross term) and BF16
+            for prec in ("bf16x3", "bf16"):
+                f = fit_form(pc, torch, stream, wl, P, lab, out, prec, args.steps, args.warmup, **kw)
+                fs = f["summary"]
+                fs["objective_rel_diff_vs_fp32_fit"] = abs(fs["objective"] - s["objective"]) / abs(s["objective"])
+                fs["speedup_vs_fp32_fit"] = fs["value"] / value
+                fs["roofline_kbuild"] = kbuild_roofline(wl, prec, fs["kbuild_ms"], pk)
+                fs["roofline_pass"] = pass_roofline(wl, f["prof"], pk)
+                forms[prec] = fs
+                line[prec] = fs
+        if headline and world == 1 and not args.no_extras:
+            extras = {}
+            for name in ("rings", "blobs", "mixture"):
+                try:
+                    kwx = {"autotune": args.autotune == "on"} if name == "mixture" else {}
+                    es, ewl, _ = leg_workload(pc, torch, stream, name, args.steps, args.warmup, pk, **kwx)
+                    if name == "mixture":
+                        ewl.precision = "bf16"
+                        Pm = torch.from_numpy(ewl.P).cuda()
+                        Lm = torch.from_numpy(ewl.init_labels).cuda()
+                        fb = fit_form(pc, torch, stream, ewl, Pm, Lm, torch.empty_like(Lm), "bf16", args.steps,
+                                      args.warmup, **kwx)
+                        avg = fb["summary"]["breakdown_ms_per_fit"]["reduce"] / max(fb["summary"]["passes_per_fit"], 1)
+                        fb["summary"]["pass_ms"] = avg
+                        fb["summary"]["roofline_pass"], _ = recompute_rooflines(ewl, avg, pk)
+                        es = {"fp8": es, "bf16": fb["summary"]}
+                    extras[name] = es
+                except Exception as ex:   # an extra leg never hides the headline
+                    extras[name] = {"error": f"{type(ex).__name__}: {ex}"}
+            for prec in ("fp32", "bf16"):
+                try:
+                    extras[f"batched_{prec}"] = leg_batched(pc, torch, stream, max(3, args.steps // 4), args.warmup,
+                                                            prec, args.autotune == "on")
+                except Exception as ex:
+                    extras[f"batched_{prec}"] = {"error": f"{type(ex).__name__}: {ex}"}
+            line["extras"] = extras
+        if world == 1 and not args.no_cpu_baseline:
+            n_s = min(SAMPLE.get(wl.name.split("_")[0], 2000), wl.n)
+            base, Ko, ofit = cpu_baseline(wl, n_s)
+            line["cpu_baseline"] = base
+            if wl.store_k:
+                errs = sample_objective_errors(pc, torch, wl, Ko, ofit, n_s,
+                                               ["fp32", "bf16x3", "bf16"] if headline else [wl.precision])
+                line["objective_vs_oracle_on_sample"] = {"sample": f"first {n_s} points, same initial labels and "
+                                                                   f"passes as the oracle's fit", **errs}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

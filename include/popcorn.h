@@ -96,7 +96,13 @@ typedef struct {
     int32_t store_k;            /* 1: materialize K once (the paper's design)                */
     int32_t check_convergence;  /* 1: stop when a pass changes no label (or on tol); 0: run
                                    exactly max_iter passes (the paper's fixed-iteration mode) */
-    int32_t timing;             /* 1: record CUDA-event times per phase into popcorn_fit_info */
+    int32_t timing;             /* 1: record CUDA-event times per phase and per kernel of every
+                                   pass into popcorn_fit_info; 2: per phase only (K build,
+                                   passes).  Without per-kernel events (0 or 2), a stored-K fit
+                                   in fixed-iteration mode (check_convergence = 0) runs all its
+                                   passes and the final objective pass as one CUDA graph,
+                                   captured on a private stream and launched on `stream`
+                                   (plain launches when `stream` is itself being captured)   */
     int32_t k_storage;          /* popcorn_k_storage of the stored K (FP32 build only for the
                                    half types); 0 = FP32                                    */
     int32_t autotune;           /* 1: pick the schedule by timing candidates on this workload

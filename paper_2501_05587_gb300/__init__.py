@@ -264,7 +264,9 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
     ``store_k=False`` selects the recompute path (K never stored; precision
     "bf16" or "fp8").  ``k_storage`` ("fp32", "fp16", "bf16") is the element
     type of a stored K.  ``k_pass`` ("auto", "symmetric", "full") is how a pass
-    reads a stored FP32 K; ``sym_tile`` (0 = automatic, 1, 2, 4) is the super-tile edge of
+    reads a stored FP32 K; ``timing`` (False, True / "kernels", "phases") records CUDA-event
+    times per phase and kernel, or per phase only (which leaves a fixed-iteration fit's passes
+    in one CUDA graph); ``sym_tile`` (0 = automatic, 1, 2, 4) is the super-tile edge of
     the symmetric pass.  ``E_out`` (an (n, k) float32 CUDA tensor) receives E = K V^T of the
     labels the last pass started from (stored-K fits).  Returns {"labels", "objective",
     "iterations", "info"};
@@ -289,7 +291,8 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
             labels_out = np.empty(n, dtype=np.int32)
         else:
             labels_out = torch.empty(n, dtype=torch.int32, device=init_labels.device)
-    opt = _Options(PRECISION[precision], 1 if store_k else 0, 1 if check_convergence else 0, 1 if timing else 0,
+    timing = {False: 0, True: 1, "kernels": 1, "phases": 2}[timing]
+    opt = _Options(PRECISION[precision], 1 if store_k else 0, 1 if check_convergence else 0, timing,
                    K_STORAGE[k_storage], 1 if autotune else 0, K_PASS[k_pass], int(sym_tile),
                    (ctypes.c_int64 * 4)())
     info = _FitInfo()

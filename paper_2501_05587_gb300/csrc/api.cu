@@ -647,6 +647,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
     if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)
         return fail(POPCORN_ERR_INVALID, "unknown k_storage %d", opt.k_storage);
+    if (opt.timing < 0 || opt.timing > 2) return fail(POPCORN_ERR_INVALID, "options.timing must be 0, 1 or 2");
     if (opt.store_k != 0 && opt.store_k != 1) return fail(POPCORN_ERR_INVALID, "store_k must be 0 or 1");
     if (opt.store_k == 0 && opt.precision != POPCORN_BF16 && opt.precision != POPCORN_FP8)
         return fail(POPCORN_ERR_UNSUPPORTED, "the recompute path (store_k = 0) runs in POPCORN_BF16 or POPCORN_FP8");
@@ -668,7 +669,9 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // symmetric pass (FP32 K, k <= kSymMaxK; k_pass 0 or 1): the blocks on and above the
     // diagonal, row and column sums into T slots, folded into slot 0
     SymPlan sym{};
-    if (ks == POPCORN_K_FP32 && opt.k_pass != 2)
+    // automatic choice: the symmetric pass for k <= 8 (above that its per-column cluster
+    // branches cost more than the halved K read saves); k_pass = 1 forces it up to kSymMaxK
+    if (ks == POPCORN_K_FP32 && (opt.k_pass == 1 || (opt.k_pass == 0 && k <= 8)))
         sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin, opt.sym_tile);
     const bool use_sym = sym.ok;
     // With the symmetric pass, K is stored block-packed: the upper triangle of 128 x 128
@@ -678,7 +681,8 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     const size_t k_bytes = sym.packed ? (size_t)sym.items * 128 * 128 * 4 : (size_t)ni * (size_t)ldk * kelem;
     const int nslots = use_sym ? sym.nslots : plan.nseg;
     if (use_sym) plan.nseg = 1;             // the assignment reads the folded slot only
-    const bool timing = opt.timing != 0;
+    const bool timing = opt.timing != 0;          // phase events (K build, passes)
+    const bool kernel_events = opt.timing == 1;   // and events around every kernel of every pass
     int launches = 0;
     int64_t h2d = 0, d2h = 0;
 
@@ -722,9 +726,9 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     POPCORN_TRY(ws.alloc(&b.Spart, (size_t)nslots * ni * k, "segment sums"));
     POPCORN_TRY(ws.alloc(&b.zpart, (size_t)(use_sym ? sym.fold_blocks : plan.grid) * k, "block partials"));
     // one pass's reduction: the K stream (for the symmetric pass: stream, then fold with z)
-    auto reduce_pass = [&](int eval, cudaEvent_t mid) -> cudaError_t {
-        if (!use_sym) return launch_reduce(b, plan, eval, s);
-        return launch_reduce_sym(b, sym, &b.st->wait_err, eval, s, mid);
+    auto reduce_pass = [&](int eval, cudaEvent_t mid, cudaStream_t st) -> cudaError_t {
+        if (!use_sym) return launch_reduce(b, plan, eval, st);
+        return launch_reduce_sym(b, sym, &b.st->wait_err, eval, st, mid);
     };
     POPCORN_TRY(ws.alloc(&b.zsum, (size_t)k, "z sums"));
     POPCORN_TRY(ws.alloc(&b.cnorm, (size_t)k, "centroid norms"));
@@ -754,6 +758,47 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         POPCORN_CUDA(cudaEventRecord(ev_b1, s));
     }
 
+    // Fixed-iteration mode (no convergence checking, no per-kernel events): every pass
+    // and the final objective pass are captured once into a CUDA graph on a private
+    // stream and launched on s as one unit, so the passes run back to back without a
+    // host launch between kernels (this matters when K sits in L2 and a pass takes
+    // microseconds).  A caller that is itself capturing s gets the plain launches.
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    POPCORN_CUDA(cudaStreamIsCapturing(s, &cap_status));
+    const bool use_graph =
+        !opt.check_convergence && !kernel_events && max_iter > 0 && cap_status == cudaStreamCaptureStatusNone;
+    cudaGraphExec_t pass_exec = nullptr;
+    struct ExecGuard {
+        cudaGraphExec_t* e;
+        ~ExecGuard() {
+            if (*e) cudaGraphExecDestroy(*e);
+        }
+    } pass_exec_guard{&pass_exec};
+    if (use_graph) {
+        cudaStream_t cs;
+        POPCORN_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        struct StreamGuard {
+            cudaStream_t s;
+            ~StreamGuard() { cudaStreamDestroy(s); }
+        } sg{cs};
+        POPCORN_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaSuccess;
+        for (int t = 0; t < max_iter && ce == cudaSuccess; ++t) {
+            ce = reduce_pass(0, nullptr, cs);
+            if (ce == cudaSuccess) ce = launch_assign(b, plan, cs);
+            launches += use_sym ? 3 : 2;
+        }
+        if (ce == cudaSuccess) ce = reduce_pass(1, nullptr, cs);
+        launches += use_sym ? 2 : 1;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+        if (ce == cudaSuccess) ce = ee;
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&pass_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        POPCORN_CUDA(ce);
+        POPCORN_CUDA(cudaGraphLaunch(pass_exec, s));
+    }
+
     // Assignment passes.  With convergence checking, the host polls the
     // device "done" flag one chunk behind, so at most one chunk of passes is
     // launched after convergence (those return at once on the device).
@@ -766,22 +811,22 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         POPCORN_TRY(g_events.get(&poll_ev[0]));
         POPCORN_TRY(g_events.get(&poll_ev[1]));
     }
-    int launched = 0, pending = -1, slot = 0;
+    int launched = use_graph ? max_iter : 0, pending = -1, slot = 0;
     while (launched < max_iter) {
         const int m = (max_iter - launched < chunk) ? (max_iter - launched) : chunk;
         for (int t = 0; t < m; ++t) {
             cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, em = nullptr;
-            if (timing) {
+            if (kernel_events) {
                 POPCORN_TRY(g_events.get(&e0));
                 POPCORN_TRY(g_events.get(&e1));
                 POPCORN_TRY(g_events.get(&e2));
                 if (use_sym) POPCORN_TRY(g_events.get(&em));
                 POPCORN_CUDA(cudaEventRecord(e0, s));
             }
-            POPCORN_CUDA(reduce_pass(0, em));
-            if (timing) POPCORN_CUDA(cudaEventRecord(e1, s));
+            POPCORN_CUDA(reduce_pass(0, em, s));
+            if (kernel_events) POPCORN_CUDA(cudaEventRecord(e1, s));
             POPCORN_CUDA(launch_assign(b, plan, s));
-            if (timing) {
+            if (kernel_events) {
                 POPCORN_CUDA(cudaEventRecord(e2, s));
                 ev_r.push_back(e0);
                 ev_r.push_back(e1);
@@ -811,9 +856,12 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         POPCORN_TRY(g_events.get(&ev_l1));
         POPCORN_CUDA(cudaEventRecord(ev_l1, s));
     }
-    // J(labels_out): reuses J of the last pass when it changed nothing
-    POPCORN_CUDA(reduce_pass(1, nullptr));
-    launches += use_sym ? 2 : 1;
+    // J(labels_out): reuses J of the last pass when it changed nothing (in the graph above
+    // when there is one)
+    if (!use_graph) {
+        POPCORN_CUDA(reduce_pass(1, nullptr, s));
+        launches += use_sym ? 2 : 1;
+    }
     if (timing) {
         POPCORN_TRY(g_events.get(&ev_e1));
         POPCORN_CUDA(cudaEventRecord(ev_e1, s));

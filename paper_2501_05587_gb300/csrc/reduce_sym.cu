@@ -521,40 +521,29 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, in
     if (k < 1 || k > kSymMaxK || n < 1) return p;
     p.kb = sym_kb(k);
     p.T = (n + kB - 1) / kB;
-    // super-tile edge: the largest of 4, 2, 1 that still leaves about 16 units per SM
-    // (the static round-robin then stays within a few percent of balanced) and fits
-    int cand_a[3] = {4, 2, 1};
-    int na = 3;
-    if (a_req > 0) {
-        cand_a[0] = a_req;
-        na = 1;
-    }
-    for (int ia = 0; ia < na; ++ia) {
-        const int A = cand_a[ia];
-        if (A < 1 || A > kMaxA) continue;
-        const int Ts = (p.T + A - 1) / A;
-        const long long units = (long long)Ts * (Ts + 1) / 2;
-        if (a_req == 0 && A > 1 && units < 16LL * num_sms) continue;
-        // ring depth: 3 blocks when k <= 4 and it fits, else 2
-        int cand_s[2] = {p.kb == 4 ? 3 : 2, 2};
-        if (stages_req > 0) cand_s[0] = cand_s[1] = stages_req;
-        for (int is = 0; is < 2; ++is) {
-            const int S = cand_s[is];
-            if (S < 2 || S > 3) continue;
-            const SymLayout L = sym_layout_rt(p.kb, S, A);
-            if (L.bytes > smem_optin) continue;
-            p.a = A;
-            p.Ts = Ts;
-            p.units = units;
-            p.stages = S;
-            p.smem = (size_t)L.bytes;
-            p.nslots = Ts + (A > 1 ? 1 : 0);
-            p.items = (long long)p.T * (p.T + 1) / 2;
-            p.grid = (int)(units < num_sms ? units : num_sms);
-            p.fold_blocks = (n + kFoldThreads - 1) / kFoldThreads;
-            p.ok = true;
-            return p;
-        }
+    // automatic: single blocks (a = 1) with the deepest ring that fits, the configuration
+    // measured fastest for k <= 8; a forced super-tile edge takes the deepest ring that fits
+    const int A = a_req > 0 ? a_req : 1;
+    if (A > kMaxA) return p;
+    const int Ts = (p.T + A - 1) / A;
+    int cand_s[2] = {3, 2};
+    if (stages_req > 0) cand_s[0] = cand_s[1] = stages_req;
+    for (int is = 0; is < 2; ++is) {
+        const int S = cand_s[is];
+        if (S < 2 || S > 3) continue;
+        const SymLayout L = sym_layout_rt(p.kb, S, A);
+        if (L.bytes > smem_optin) continue;
+        p.a = A;
+        p.Ts = Ts;
+        p.units = (long long)Ts * (Ts + 1) / 2;
+        p.stages = S;
+        p.smem = (size_t)L.bytes;
+        p.nslots = Ts + (A > 1 ? 1 : 0);
+        p.items = (long long)p.T * (p.T + 1) / 2;
+        p.grid = (int)(p.units < num_sms ? p.units : num_sms);
+        p.fold_blocks = (n + kFoldThreads - 1) / kFoldThreads;
+        p.ok = true;
+        return p;
     }
     return p;
 }

@@ -314,3 +314,28 @@ def test_fit_reports_nomem_and_stays_usable(pc):
     wl = synth.workload("blobs", scale=0.1)
     r = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), max_iter=3)
     assert r["iterations"] >= 1
+
+
+@pytest.mark.parametrize("name,scale,k_pass", [("blobs", 1.0, "auto"), ("rings", 0.2, "symmetric"),
+                                               ("rings", 0.2, "full"), ("images", 0.03, "auto")])
+def test_fixed_iteration_graph_equals_plain_launches(pc, name, scale, k_pass):
+    """A fixed-iteration fit without per-kernel events runs all its passes and the objective
+    pass as one CUDA graph.  The kernels, their arguments and their order are those of the
+    plainly launched fit (timing = 1), and every reduction order is fixed, so labels,
+    objective and the J / change histories are bit-identical; phase timing reports the
+    graph's time as loop_ms."""
+    wl = synth.workload(name, scale=scale)
+    P, lab = _dev(wl.P), _dev(wl.init_labels)
+    kw = dict(max_iter=12, check_convergence=False, history=True, k_pass=k_pass)
+    g = pc.popcorn_fit(P, wl.k, wl.kernel, lab, **kw)
+    h = pc.popcorn_fit(P, wl.k, wl.kernel, lab, timing="phases", **kw)
+    p = pc.popcorn_fit(P, wl.k, wl.kernel, lab, timing=True, **kw)
+    for r in (g, h):
+        assert torch.equal(r["labels"], p["labels"])
+        assert r["objective"] == p["objective"]
+        assert r["info"]["J_history"] == p["info"]["J_history"]
+        assert r["info"]["changed_history"] == p["info"]["changed_history"]
+        assert r["iterations"] == p["iterations"] == 12
+        assert r["info"]["kernel_launches"] == p["info"]["kernel_launches"]
+    assert h["info"]["loop_ms"] > 0 and h["info"]["reduce_ms"] == 0 and h["info"]["kbuild_ms"] > 0
+    assert p["info"]["reduce_ms"] > 0
