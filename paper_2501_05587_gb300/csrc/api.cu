@@ -188,7 +188,7 @@ popcorn_status check_kernel(const popcorn_kernel& kern, KernParams* kp) {
 // packed: the build writes the block-packed upper triangle (symmetric pass only).
 popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, const KernParams& kp,
                                    int precision, void* K, int64_t ldk, int k_storage, float* kdiag, Workspace* ws,
-                                   int* err, int num_sms, cudaStream_t s, int* launches, bool packed = false) {
+                                   int* err, int num_sms, cudaStream_t s, int* launches, int packed = 0) {
     if (precision == POPCORN_FP32) {
         POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, k_storage, kdiag, s, launches, packed));
         return POPCORN_OK;
@@ -669,9 +669,8 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // symmetric pass (FP32 K, k <= kSymMaxK; k_pass 0 or 1): the blocks on and above the
     // diagonal, row and column sums into T slots, folded into slot 0
     SymPlan sym{};
-    // automatic choice: the symmetric pass for k <= 8 (above that its per-column cluster
-    // branches cost more than the halved K read saves); k_pass = 1 forces it up to kSymMaxK
-    if (ks == POPCORN_K_FP32 && (opt.k_pass == 1 || (opt.k_pass == 0 && k <= 8)))
+    // automatic choice: the symmetric pass wherever it applies (k <= kSymMaxK)
+    if (ks == POPCORN_K_FP32 && opt.k_pass != 2)
         sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin, opt.sym_tile);
     const bool use_sym = sym.ok;
     // With the symmetric pass, K is stored block-packed: the upper triangle of 128 x 128
@@ -725,7 +724,12 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     POPCORN_TRY(ws.alloc(&b.counts, 2 * (size_t)k, "counts"));
     POPCORN_TRY(ws.alloc(&b.Spart, (size_t)nslots * ni * k, "segment sums"));
     POPCORN_TRY(ws.alloc(&b.zpart, (size_t)(use_sym ? sym.fold_blocks : plan.grid) * k, "block partials"));
+    b.sym_meta = nullptr;
+    if (use_sym && sym.meta_bytes) POPCORN_TRY(ws.alloc(&b.sym_meta, sym.meta_bytes, "block label metadata"));
     // one pass's reduction: the K stream (for the symmetric pass: stream, then fold with z)
+    // kernels of one pass's reduction: the full-square stream; or the symmetric stream and its
+    // fold (the run form first sorts every block's labels)
+    const int red_launches = use_sym ? (sym.runs ? 3 : 2) : 1;
     auto reduce_pass = [&](int eval, cudaEvent_t mid, cudaStream_t st) -> cudaError_t {
         if (!use_sym) return launch_reduce(b, plan, eval, st);
         return launch_reduce_sym(b, sym, &b.st->wait_err, eval, st, mid);
@@ -749,7 +753,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     POPCORN_CUDA(cudaMemsetAsync(b.counts, 0, 2 * (size_t)k * sizeof(int32_t), s));
     POPCORN_CUDA(launch_init_state(b.st, max_iter, opt.check_convergence ? 1 : 0, tol, s));
     POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, ks, kdiag, &ws, &b.st->wait_err,
-                                    dev->sms, s, &launches, sym.packed));
+                                    dev->sms, s, &launches, sym.packed ? sym.layout : 0));
     POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
     POPCORN_CUDA(launch_init_labels(Ld, ni, k, b.lab32, b.lab8, b.counts, b.st, s));
     launches += 3;
@@ -786,10 +790,10 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         for (int t = 0; t < max_iter && ce == cudaSuccess; ++t) {
             ce = reduce_pass(0, nullptr, cs);
             if (ce == cudaSuccess) ce = launch_assign(b, plan, cs);
-            launches += use_sym ? 3 : 2;
+            launches += red_launches + 1;
         }
         if (ce == cudaSuccess) ce = reduce_pass(1, nullptr, cs);
-        launches += use_sym ? 2 : 1;
+        launches += red_launches;
         cudaGraph_t graph = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
         if (ce == cudaSuccess) ce = ee;
@@ -837,7 +841,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
                     ev_f.push_back(e1);
                 }
             }
-            launches += use_sym ? 3 : 2;
+            launches += red_launches + 1;
         }
         launched += m;
         if (opt.check_convergence && launched < max_iter) {
@@ -860,7 +864,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // when there is one)
     if (!use_graph) {
         POPCORN_CUDA(reduce_pass(1, nullptr, s));
-        launches += use_sym ? 2 : 1;
+        launches += red_launches;
     }
     if (timing) {
         POPCORN_TRY(g_events.get(&ev_e1));

@@ -76,7 +76,9 @@ struct TileSmem {
     float Bs[2][KC][LDS];
 };
 
-template <int KIND, typename TK = float, bool ONE_SLICE = false, bool PACKED = false>
+// PACKED: 0 = row-major full square (tile and transpose); kPackedSw16 / kPackedSw4 = the
+// block-packed upper triangle in the tile layout of that name (popcorn_internal.cuh).
+template <int KIND, typename TK = float, bool ONE_SLICE = false, int PACKED = 0>
 __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, int d, int64_t ldp,
                                             const KernParams& kp, TK* __restrict__ K, int64_t ldk,
                                             float* __restrict__ kdiag, int T, long long tile, TileSmem& sm) {
@@ -186,11 +188,16 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         }
     }
 
-    if constexpr (PACKED) {
+    if constexpr (PACKED != 0) {
         // block-packed upper triangle: tile t is 64 KB at K + t * 128 * 128, as four boxes of
-        // 128 rows x 32 columns with the 128-byte swizzle (16-byte chunk j of row r stored at
-        // chunk j ^ (r mod 8)), the layout the symmetric pass loads with one bulk copy.  The
-        // whole tile is written: entries past n are finite and no pass reads them.
+        // 128 rows x 32 columns, the layout the symmetric pass loads with one bulk copy.
+        // kPackedSw16: 16-byte chunk j of row r stored at chunk j ^ (r mod 8) (the 128-byte
+        // swizzle).  kPackedSw4: element c of row r stored at c ^ (r mod 32), so that both a
+        // row and a column of a box are read without bank conflicts.  This thread's 4
+        // consecutive columns (4-aligned) stay in one 16-byte chunk under either layout; under
+        // kPackedSw4 they are permuted inside it by (r mod 4), which is x mod 4 here (a
+        // compile-time constant), so each store is still one float4.  The whole tile is
+        // written: entries past n are finite and no pass reads them.
         static_assert(sizeof(TK) == 4, "packed storage holds FP32 K");
         float* B = reinterpret_cast<float*>(K) + (size_t)tile * (TILE * TILE);
 #pragma unroll
@@ -199,9 +206,16 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int cl = 64 * h + tx * 4;
-                const int j = (cl & 31) >> 2;
-                *reinterpret_cast<float4*>(B + (cl >> 5) * (TILE * 32) + rl * 32 + ((j ^ (rl & 7)) << 2)) =
-                    make_float4(acc[x][4 * h], acc[x][4 * h + 1], acc[x][4 * h + 2], acc[x][4 * h + 3]);
+                const float* v = &acc[x][4 * h];
+                if constexpr (PACKED == kPackedSw16) {
+                    const int j = (cl & 31) >> 2;
+                    *reinterpret_cast<float4*>(B + (cl >> 5) * (TILE * 32) + rl * 32 + ((j ^ (rl & 7)) << 2)) =
+                        make_float4(v[0], v[1], v[2], v[3]);
+                } else {
+                    const int q = x & 3;   // == rl & 3 (the loop is unrolled: a constant)
+                    *reinterpret_cast<float4*>(B + (cl >> 5) * (TILE * 32) + rl * 32 +
+                                               ((cl & 31) ^ (rl & 28))) = make_float4(v[q], v[1 ^ q], v[2 ^ q], v[3 ^ q]);
+                }
             }
         }
         return;
@@ -239,7 +253,7 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
     }
 }
 
-template <int KIND, typename TK, bool PACKED>
+template <int KIND, typename TK, int PACKED>
 __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
                                                           KernParams kp, TK* __restrict__ K, int64_t ldk,
                                                           float* __restrict__ kdiag, int T) {
@@ -250,7 +264,7 @@ __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restric
 // d <= KC: the depth loop is one slice, so no next slice is held in registers;
 // the lighter kernel fits two blocks per SM, which overlaps one block's stores
 // with the other's loads (small d is store-bound)
-template <int KIND, typename TK, bool PACKED>
+template <int KIND, typename TK, int PACKED>
 __global__ void __launch_bounds__(256, 2) kbuild_simt_small_kernel(const float* __restrict__ P, int n, int d,
                                                                    int64_t ldp, KernParams kp, TK* __restrict__ K,
                                                                    int64_t ldk, float* __restrict__ kdiag, int T) {
@@ -258,7 +272,7 @@ __global__ void __launch_bounds__(256, 2) kbuild_simt_small_kernel(const float* 
     kbuild_tile<KIND, TK, true, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm);
 }
 
-template <typename TK, bool PACKED>
+template <typename TK, int PACKED>
 cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernParams kp, TK* K, int64_t ldk,
                               float* kdiag, cudaStream_t s) {
     const int T = (n + TILE - 1) / TILE;
@@ -330,18 +344,19 @@ cudaError_t launch_batched_kbuild_simt(const BatchInst* dI, const BatchPlan& bp,
 }
 
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp, void* K, int64_t ldk,
-                               int k_storage, float* kdiag, cudaStream_t s, int* launches, bool packed) {
+                               int k_storage, float* kdiag, cudaStream_t s, int* launches, int packed) {
     if (launches) ++*launches;
     if (packed) {
         if (k_storage != POPCORN_K_FP32) return cudaErrorInvalidValue;
-        return launch_simt_typed<float, true>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
+        if (packed == kPackedSw4)
+            return launch_simt_typed<float, kPackedSw4>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
+        return launch_simt_typed<float, kPackedSw16>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
     }
     if (k_storage == POPCORN_K_FP16)
-        return launch_simt_typed<__half, false>(P, n, d, ldp, kp, static_cast<__half*>(K), ldk, kdiag, s);
+        return launch_simt_typed<__half, 0>(P, n, d, ldp, kp, static_cast<__half*>(K), ldk, kdiag, s);
     if (k_storage == POPCORN_K_BF16)
-        return launch_simt_typed<__nv_bfloat16, false>(P, n, d, ldp, kp, static_cast<__nv_bfloat16*>(K), ldk, kdiag,
-                                                       s);
-    return launch_simt_typed<float, false>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
+        return launch_simt_typed<__nv_bfloat16, 0>(P, n, d, ldp, kp, static_cast<__nv_bfloat16*>(K), ldk, kdiag, s);
+    return launch_simt_typed<float, 0>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
 }
 
 }  // namespace popcorn

@@ -74,7 +74,9 @@ struct TcArgs {
     int off_sd, off_st, off_rj, off_bar, off_misc;
     long long tiles;          // sum_p (T - 2 p)
     float* Kp;                // block-packed K (tile (I, J), I <= J, at its row-by-row triangle index
-                              // times 16384 floats, four swizzled 128 x 32 boxes), or null
+                              // times 16384 floats, four 128 x 32 boxes), or null
+    int sw4;                  // packed layout kPackedSw4 (element c of row r at c ^ (r mod 32)); else
+                              // kPackedSw16 (the 128-byte swizzle of the staging chunk)
     KernParams kp;
     const float* norms;       // row norms of the represented rows (Gaussian)
     float* kdiag;
@@ -311,11 +313,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     epi_bar();
                     float* sd = reinterpret_cast<float*>(smem + a.off_sd + sbuf * STG_BYTES);
                     float* sx = reinterpret_cast<float*>(smem + a.off_st + sbuf * STG_BYTES);
-                    // direct chunk: row row_local, 8 x 16-byte pieces, piece i at i ^ (row % 8)
+                    if (a.sw4) {
+                        // packed XOR-32 layout: element x of row row_local at x ^ (row_local mod 32)
+                        // (the 32 lanes hold 32 consecutive rows: 32 different banks per store)
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        float4 w = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                        *reinterpret_cast<float4*>(sd + row_local * 32 + ((i ^ (row_local & 7)) * 4)) = w;
+                        for (int x = 0; x < 32; ++x) sd[row_local * 32 + (x ^ lane)] = v[x];
+                    } else {
+                        // direct chunk: row row_local, 8 x 16-byte pieces, piece i at i ^ (row % 8)
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            float4 w = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                            *reinterpret_cast<float4*>(sd + row_local * 32 + ((i ^ (row_local & 7)) * 4)) = w;
+                        }
                     }
                     if (!diag && !a.Kp) {
 #pragma unroll
@@ -427,7 +436,7 @@ cudaError_t configure_kbuild_tc() {
 
 cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
                              int64_t ldk, float* kdiag, void* workspace, int* err, int num_sms, cudaStream_t s,
-                             int* launches, bool packed) {
+                             int* launches, int packed) {
     const int dpad = (d + BK - 1) / BK * BK;
     const int x3 = precision == POPCORN_BF16X3 ? 1 : 0;
     const int64_t ldw = (int64_t)(x3 ? 2 : 1) * dpad;
@@ -475,6 +484,7 @@ cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernPara
     a.off_misc = a.off_bar + 16 * 8;
     a.tiles = (long long)a.T2 * a.T - (long long)a.T2 * (a.T2 - 1);
     a.Kp = packed ? K : nullptr;
+    a.sw4 = packed == kPackedSw4 ? 1 : 0;
     a.kp = kp;
     a.norms = norms;
     a.kdiag = kdiag;

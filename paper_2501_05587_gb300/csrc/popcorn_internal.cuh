@@ -69,11 +69,18 @@ struct ReducePlan {
 // a super-tile's row sums go to one slot of its rows and its column sums to one
 // slot of its columns' rows, so Spart holds nslots = ceil(T / a) (+1 when a > 1)
 // slots; the fold sums them into slot 0 (the assignment then reads slot 0
-// only) and forms z and J.  FP32 K, k <= kSymMaxK.
-constexpr int kSymMaxK = 16;
+// only) and forms z and J.  FP32 K, k <= kSymMaxK: up to kSymBranchMaxK clusters a
+// uniform branch per column / row adds into register sums; above that the run form
+// walks each block in label order (a per-pass sort of every block's labels) and adds
+// runs of one label, with K packed in the XOR-32 layout.
+constexpr int kSymMaxK = 32;
+constexpr int kSymBranchMaxK = 8;
 struct SymPlan {
     bool ok;
-    int kb;             // register accumulators per row / column: 4, 8 or 16 (>= k)
+    bool runs;          // the run form (k > kSymBranchMaxK)
+    int layout;         // packed tile layout the pass reads: kPackedSw16 (branch) or kPackedSw4 (runs)
+    size_t meta_bytes;  // run form: per-pass block metadata (T x 768 bytes)
+    int kb;             // branch form: register sums per row / column, 4 or 8 (>= k)
     int T;              // 128-blocks per side
     int a;              // super-tile edge in blocks (1, 2 or 4)
     int Ts;             // super-tiles per side
@@ -84,7 +91,7 @@ struct SymPlan {
     int grid;           // persistent CTAs of the stream kernel
     int fold_blocks;    // row chunks of the fold (zpart rows)
     size_t smem;
-    bool packed;        // K is block-packed (set by the caller with the K build it chose)
+    bool packed;        // K is block-packed in `layout` (set by the caller with the K build it chose)
 };
 // a_req / stages_req: 0 = the heuristic choice, else that super-tile edge / ring depth
 // (ok = false if it does not fit)
@@ -139,14 +146,20 @@ __device__ __forceinline__ void tri_coords(long long t, int T, int* bi, int* bj)
 // Sets the message popcorn_last_error_message() returns on this thread (api.cu).
 void set_error_message(const char* msg);
 
+// Layouts of the block-packed upper triangle of K (tile t of the row-by-row triangle
+// of 128 x 128 tiles at K + t * 16384 floats, as four boxes of 128 rows x 32 columns,
+// 16 KB each).  kPackedSw16: 16-byte chunk j of row r at chunk j ^ (r mod 8) (the TMA
+// 128-byte swizzle; rows read as float4 chunks).  kPackedSw4: element c of row r at
+// c ^ (r mod 32) (a row and a column of a box are both read conflict-free as scalars).
+constexpr int kPackedSw16 = 1, kPackedSw4 = 2;
+
 // ---- K build (kbuild_simt.cu) ------------------------------------------------
 // K is float, __half or __nv_bfloat16 by k_storage (popcorn_k_storage); ldk in elements.
-// packed: FP32 K as the block-packed upper triangle of 128 x 128 tiles (tile t of
-// the row-by-row triangle at K + t * 16384 floats, swizzled boxes: see
-// kbuild_simt.cu), read by the symmetric pass; ldk is then unused.
+// packed: 0 = full square; kPackedSw16 / kPackedSw4 = FP32 K as the block-packed upper
+// triangle in that layout, read by the symmetric pass (ldk is then unused).
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp,
                                void* K, int64_t ldk, int k_storage, float* kdiag, cudaStream_t s, int* launches,
-                               bool packed = false);
+                               int packed = 0);
 
 // ---- K build on tensor cores (kbuild_tc.cu) ---------------------------------
 // Workspace bytes for the BF16 operand copies and row norms.
@@ -156,11 +169,11 @@ size_t kbuild_tc_workspace(int n, int d, int precision);
 cudaError_t configure_kbuild_tc();
 // precision POPCORN_BF16 or POPCORN_BF16X3; *err (device) becomes nonzero if a
 // bounded wait inside the kernel ran out.
-// packed: K is the block-packed upper triangle (as the FP32 build writes it for the
-// symmetric pass); ldk is then unused.
+// packed: 0 = full square; kPackedSw16 / kPackedSw4 = the block-packed upper triangle
+// in that layout (as the FP32 build writes it for the symmetric pass); ldk is then unused.
 cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
                              int64_t ldk, float* kdiag, void* workspace, int* err, int num_sms, cudaStream_t s,
-                             int* launches, bool packed = false);
+                             int* launches, int packed = 0);
 
 // 2-D tiled TMA descriptor over a row-major matrix (inner = contiguous extent
 // in elements, row_bytes = pitch); false if the driver entry point is missing
@@ -254,6 +267,7 @@ struct PassBuffers {
     double* J_hist;       // [max(1, max_iter)]
     int32_t* changed_hist;
     float* E_out;         // optional n x k
+    uint8_t* sym_meta;    // run form of the symmetric pass: T x 768 bytes of block metadata
 };
 
 // Operand rows for the recompute path, their norms and scales, and diag K.

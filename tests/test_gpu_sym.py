@@ -6,10 +6,12 @@ part of its columns' rows; a fold kernel adds the parts.  So one pass from given
 labels must be the oracle's step exactly as the full-square pass is (labels equal
 except near-ties, objective within the FP32 bar), and whole fits must agree with the
 full-square pass up to FP32 summation order.  The cases cover a single ragged block,
-ragged n over several blocks, n a multiple of 128, k up to its bound (16), a kernel
+ragged n over several blocks, n a multiple of 128, k up to its bound (32), a kernel
 that is not positive semi-definite (symmetry is all the pass needs) and many blocks,
 each with every super-tile edge (1, 2, 4: a super-tile's row and column sums are kept
-over its a x a blocks before they are stored).  The images workload runs through it
+over its a x a blocks before they are stored).  k <= 8 on single blocks runs the
+branch form (register sums per cluster); larger k, or a super-tile edge above 1, the
+run form (blocks walked in label order, one add per run of one label).  The images workload runs through it
 at a tenth of its size against the full oracle step (FP32 build and the packed
 tensor-core BF16X3 build), and at full size (n = 70,000, 547 blocks per side) on
 sampled rows of E = K V^T that the oracle computes row by row, with every row's
@@ -50,10 +52,12 @@ CASES = [
     (1280, 4, 8, _gauss(1.0), 6),        # n a multiple of 128, k at the bound
     (700, 3, 5, POLY3_NEG, 7),           # negative entries: symmetry suffices
     (9001, 4, 5, _gauss(1.0), 5),        # 71 blocks per side
-    (1100, 7, 12, _gauss(2.0), 8),       # 16 register accumulators, ragged
-    (2500, 5, 16, _gauss(1.5), 9),       # k at the bound (16)
+    (1100, 7, 12, _gauss(2.0), 8),       # the run form from here on: ragged
+    (2500, 5, 16, _gauss(1.5), 9),
     (3000, 6, 10, POLY2, 10),
     (9001, 4, 16, _gauss(1.0), 11),
+    (2000, 5, 24, _gauss(1.5), 12),
+    (4099, 6, 32, _gauss(2.0), 13),      # k at the bound (32), n % 128 = 3
 ]
 
 
@@ -127,9 +131,9 @@ def test_symmetric_pass_is_deterministic(pc, name, sym_tile):
 
 def test_symmetric_pass_launches_and_fallback(pc):
     """k_pass = "symmetric" runs the stream and the fold (one launch more per pass than
-    the full square) and is what "auto" picks for an FP32 K with k <= 16; above the
-    cluster bound, or with a half-precision K, both fall back to the full-square pass,
-    with results identical to it."""
+    the full square; the run form one more, its label sort) and is what "auto" picks for
+    an FP32 K with k <= 32; above the cluster bound, or with a half-precision K, both
+    fall back to the full-square pass, with results identical to it."""
     P = torch.from_numpy(synth.gaussian_blobs(600, 3, 6, seed=9, box=3.0)).cuda()
     lab = torch.from_numpy(synth.init_labels(600, 6, seed=19)).cuda()
     a = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_pass="symmetric")
@@ -140,9 +144,9 @@ def test_symmetric_pass_launches_and_fallback(pc):
     assert a["info"]["kernel_launches"] == b["info"]["kernel_launches"] + a["iterations"] + 1
     h = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_storage="fp16")
     assert h["info"]["k_pass_used"] == 2
-    lab20 = torch.from_numpy(synth.init_labels(600, 20, seed=29)).cuda()
-    c = pc.popcorn_fit(P, 20, _gauss(1.0), lab20, max_iter=5, check_convergence=False, k_pass="symmetric")
-    d = pc.popcorn_fit(P, 20, _gauss(1.0), lab20, max_iter=5, check_convergence=False, k_pass="full")
+    lab40 = torch.from_numpy(synth.init_labels(600, 40, seed=29)).cuda()
+    c = pc.popcorn_fit(P, 40, _gauss(1.0), lab40, max_iter=5, check_convergence=False, k_pass="symmetric")
+    d = pc.popcorn_fit(P, 40, _gauss(1.0), lab40, max_iter=5, check_convergence=False, k_pass="full")
     assert c["info"]["kernel_launches"] == d["info"]["kernel_launches"]
     assert c["info"]["k_pass_used"] == 2
     assert np.array_equal(c["labels"].cpu().numpy(), d["labels"].cpu().numpy())
@@ -247,3 +251,13 @@ def test_full_size_images_symmetric_pass_sampled(pc, precision):
     exempt = (part[:, 1] - part[:, 0]) < 1e-6 * np.maximum(np.abs(part[:, 0]), 1.0)
     got = r["labels"].cpu().numpy()
     assert int(((got != pred) & ~exempt).sum()) == 0
+
+
+def test_run_form_launches_its_label_sort(pc):
+    """The run form adds one launch per pass (the per-pass sort of every block's labels)."""
+    P = torch.from_numpy(synth.gaussian_blobs(900, 3, 12, seed=4, box=3.0)).cuda()
+    lab = torch.from_numpy(synth.init_labels(900, 12, seed=14)).cuda()
+    a = pc.popcorn_fit(P, 12, _gauss(1.0), lab, max_iter=4, check_convergence=False, timing=True)
+    b = pc.popcorn_fit(P, 12, _gauss(1.0), lab, max_iter=4, check_convergence=False, timing=True, k_pass="full")
+    assert a["info"]["k_pass_used"] == 1 and b["info"]["k_pass_used"] == 2
+    assert a["info"]["kernel_launches"] == b["info"]["kernel_launches"] + 2 * (a["iterations"] + 1)
