@@ -189,7 +189,8 @@ POPCORN_API int32_t popcorn_version(void);
  * popcorn_kernel_matrix -- K = kappa(P P^T) and diag(K).
  *
  * Sec. 3.2 (polynomial and Gaussian kernels from B = P P^T, Eq. 12 for the
- * Gaussian) and Alg. 2 lines 1-2 (K once, P~ from diag(K)).
+ * Gaussian) and Alg. 2 lines 1-2 (K once, P~ from diag(K)).  The tile schedule
+ * is POPCORN_SCHEDULE_AUTO (see popcorn_kernel_matrix_ex).
  *
  *   P      device, n x d FP32, leading dimension ldp >= d.
  *   K      device, n x n FP32 output, leading dimension ldk >= n; ldk must be
@@ -206,6 +207,37 @@ POPCORN_API popcorn_status popcorn_kernel_matrix(const float* P, int64_t n, int3
                                      popcorn_kernel kern, int32_t precision,
                                      float* K, int64_t ldk, float* kdiag,
                                      popcorn_stream_t stream);
+
+/* Tile schedule of the K build: which 128 x 128 tiles of B = P P^T are formed.  The
+   paper builds B with a GEMM or a SYRK and switches on the shape (Sec. 4.2, n/d
+   threshold; Sec. 5.2 measures both). */
+typedef enum {
+    POPCORN_SCHEDULE_AUTO = 0,       /* the cached tuned choice for this workload signature,
+                                        else SYMMETRIC                                        */
+    POPCORN_SCHEDULE_SYMMETRIC = 1,  /* the tiles on and above the diagonal, each stored with
+                                        its transpose (the SYRK form: n (n + 1) / 2 products) */
+    POPCORN_SCHEDULE_FULL = 2,       /* every tile of the square, each stored once (the GEMM
+                                        form: n^2 products)                                 */
+    POPCORN_SCHEDULE_TUNE = 3        /* time SYMMETRIC and FULL on this call's inputs once per
+                                        workload signature (precision, bucketed n and d,
+                                        kernel kind, SM count), cache the faster, use it     */
+} popcorn_kbuild_schedule;
+
+/*
+ * popcorn_kernel_matrix_ex -- popcorn_kernel_matrix with a chosen tile schedule.
+ *
+ * Sec. 3.2 and Alg. 2 lines 1-2, with the GEMM-or-SYRK choice of Sec. 4.2 made by
+ * `schedule` (popcorn_kbuild_schedule) instead of the paper's fixed n/d threshold.
+ * Arguments and errors as popcorn_kernel_matrix, plus POPCORN_ERR_INVALID for an
+ * unknown schedule.  Under FULL each (i, j) and (j, i) are formed separately: the FP32
+ * build gives the same value for both (the same products in the same order); BF16X3
+ * adds its three partial products in another order for the transposed tile, so the two
+ * may differ in the last bits.  TUNE runs the build several times on the call's stream.
+ */
+POPCORN_API popcorn_status popcorn_kernel_matrix_ex(const float* P, int64_t n, int32_t d, int64_t ldp,
+                                                    popcorn_kernel kern, int32_t precision, int32_t schedule,
+                                                    float* K, int64_t ldk, float* kdiag,
+                                                    popcorn_stream_t stream);
 
 /*
  * popcorn_assign_step -- one pass of the loop body of Alg. 2 on a given K.

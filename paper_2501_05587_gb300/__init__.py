@@ -50,6 +50,8 @@ EXPORTED_SYMBOLS = (
     "popcorn_last_error_message",
     "popcorn_version",
     "popcorn_kernel_matrix",
+    "popcorn_kernel_matrix_ex",
+    "popcorn_kernel_matrix_ex",
     "popcorn_assign_step",
     "popcorn_fit",
     "popcorn_assign_step_noalloc",
@@ -108,6 +110,8 @@ _lib.popcorn_version.restype = _i32
 _lib.popcorn_version.argtypes = []
 _lib.popcorn_kernel_matrix.restype = ctypes.c_int
 _lib.popcorn_kernel_matrix.argtypes = [_vp, _i64, _i32, _i64, _Kernel, _i32, _vp, _i64, _vp, _vp]
+_lib.popcorn_kernel_matrix_ex.restype = ctypes.c_int
+_lib.popcorn_kernel_matrix_ex.argtypes = [_vp, _i64, _i32, _i64, _Kernel, _i32, _i32, _vp, _i64, _vp, _vp]
 _lib.popcorn_assign_step.restype = ctypes.c_int
 _lib.popcorn_assign_step.argtypes = [_vp, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp,
                                      ctypes.POINTER(_dbl), ctypes.POINTER(_i32), _vp]
@@ -173,12 +177,17 @@ def _ptr(x):
     return ctypes.c_void_p(x.data_ptr())
 
 
-def popcorn_kernel_matrix(P, kernel: dict, precision: str = "fp32", K=None, kdiag=None, stream=None):
+SCHEDULE = {"auto": 0, "symmetric": 1, "full": 2, "tune": 3}
+
+
+def popcorn_kernel_matrix(P, kernel: dict, precision: str = "fp32", K=None, kdiag=None, stream=None,
+                          schedule: str = "auto"):
     """K = kappa(P P^T) (full square, FP32) and diag(K) on the device of P.
 
     P is an (n, d) float32 CUDA tensor (rows may be strided: ldp = P.stride(0)).
-    Returns (K, kdiag); K has a leading dimension rounded up to a multiple of 4
-    (the returned tensor is the (n, n) view).
+    ``schedule`` ("auto", "symmetric", "full", "tune") picks the tile schedule
+    (popcorn_kernel_matrix_ex).  Returns (K, kdiag); K has a leading dimension
+    rounded up to a multiple of 4 (the returned tensor is the (n, n) view).
     """
     torch = _torch()
     assert P.is_cuda and P.dtype == torch.float32 and P.dim() == 2 and P.stride(1) == 1
@@ -188,9 +197,9 @@ def popcorn_kernel_matrix(P, kernel: dict, precision: str = "fp32", K=None, kdia
         K = torch.empty((n, ldk), dtype=torch.float32, device=P.device)[:, :n]
     if kdiag is None:
         kdiag = torch.empty(n, dtype=torch.float32, device=P.device)
-    _check(_lib.popcorn_kernel_matrix(_ptr(P), n, d, P.stride(0), _kernel(kernel), PRECISION[precision],
-                                      _ptr(K), K.stride(0), _ptr(kdiag), _stream(stream)),
-           "popcorn_kernel_matrix")
+    _check(_lib.popcorn_kernel_matrix_ex(_ptr(P), n, d, P.stride(0), _kernel(kernel), PRECISION[precision],
+                                         SCHEDULE[schedule], _ptr(K), K.stride(0), _ptr(kdiag), _stream(stream)),
+           "popcorn_kernel_matrix_ex")
     return K, kdiag
 
 

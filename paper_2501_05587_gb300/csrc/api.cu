@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -188,9 +189,10 @@ popcorn_status check_kernel(const popcorn_kernel& kern, KernParams* kp) {
 // packed: the build writes the block-packed upper triangle (symmetric pass only).
 popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, const KernParams& kp,
                                    int precision, void* K, int64_t ldk, int k_storage, float* kdiag, Workspace* ws,
-                                   int* err, int num_sms, cudaStream_t s, int* launches, int packed = 0) {
+                                   int* err, int num_sms, cudaStream_t s, int* launches, int packed = 0,
+                                   int full = 0) {
     if (precision == POPCORN_FP32) {
-        POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, k_storage, kdiag, s, launches, packed));
+        POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, k_storage, kdiag, s, launches, packed, full));
         return POPCORN_OK;
     }
     if (k_storage != POPCORN_K_FP32)
@@ -200,7 +202,7 @@ popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, co
     unsigned char* w;
     POPCORN_TRY(ws->alloc(&w, kbuild_tc_workspace(n, d, precision), "BF16 operands"));
     cudaError_t e = launch_kbuild_tc(P, n, d, ldp, kp, precision, static_cast<float*>(K), ldk, kdiag, w, err, num_sms,
-                                     s, launches, packed);
+                                     s, launches, packed, full);
     if (e == cudaErrorInvalidValue)
         return fail(POPCORN_ERR_CUDA, "tensor map creation failed (cuTensorMapEncodeTiled unavailable or rejected)");
     POPCORN_CUDA(e);
@@ -524,9 +526,9 @@ const char* popcorn_last_error_message(void) { return g_err.c_str(); }
 
 int32_t popcorn_version(void) { return 100; }
 
-popcorn_status popcorn_kernel_matrix(const float* P, int64_t n, int32_t d, int64_t ldp,
-                                     popcorn_kernel kern, int32_t precision, float* K, int64_t ldk,
-                                     float* kdiag, popcorn_stream_t stream) {
+popcorn_status popcorn_kernel_matrix_ex(const float* P, int64_t n, int32_t d, int64_t ldp, popcorn_kernel kern,
+                                        int32_t precision, int32_t schedule, float* K, int64_t ldk, float* kdiag,
+                                        popcorn_stream_t stream) {
     g_err.clear();
     if (!P || !K || !kdiag) return fail(POPCORN_ERR_INVALID, "null pointer argument");
     if (n < 1 || n >= (1LL << 31)) return fail(POPCORN_ERR_INVALID, "n = %lld outside [1, 2^31)", (long long)n);
@@ -535,26 +537,72 @@ popcorn_status popcorn_kernel_matrix(const float* P, int64_t n, int32_t d, int64
     if (ldk < n || ldk % 4 != 0)
         return fail(POPCORN_ERR_INVALID, "ldk = %lld must be >= n and a multiple of 4", (long long)ldk);
     if (reinterpret_cast<uintptr_t>(K) % 16 != 0) return fail(POPCORN_ERR_INVALID, "K must be 16-byte aligned");
+    if (schedule < POPCORN_SCHEDULE_AUTO || schedule > POPCORN_SCHEDULE_TUNE)
+        return fail(POPCORN_ERR_INVALID, "unknown K-build schedule %d", schedule);
+    if (precision != POPCORN_FP32 && precision != POPCORN_BF16 && precision != POPCORN_BF16X3)
+        return fail(POPCORN_ERR_UNSUPPORTED, "precision %d is not available for a stored K", precision);
     KernParams kp;
     POPCORN_TRY(check_kernel(kern, &kp));
     DeviceInfo* dev;
     POPCORN_TRY(device_info(&dev));
     int launches = 0;
     cudaStream_t s = (cudaStream_t)stream;
-    if (precision == POPCORN_FP32)
-        return build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, POPCORN_K_FP32, kdiag, nullptr, nullptr,
-                                   dev->sms, s, &launches);
     Workspace ws(dev->pool, s);
     int* err;
     POPCORN_TRY(ws.alloc(&err, 1, "error flag"));
     POPCORN_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    // AUTO takes the tuned schedule of this workload signature if one is cached, else the
+    // symmetric one; TUNE times both once per signature (best of two after a warm-up), caches
+    // the faster and leaves its K in place
+    const TuneKey key{3, precision, log2_bucket((double)n), log2_bucket((double)d), kp.kind, 0, 0, dev->sms};
+    int use = schedule;
+    if (schedule == POPCORN_SCHEDULE_AUTO || schedule == POPCORN_SCHEDULE_TUNE) {
+        TuneValue tv{};
+        if (tune_lookup(key, &tv)) {
+            use = tv.p[0];
+        } else if (schedule == POPCORN_SCHEDULE_TUNE) {
+            cudaEvent_t t0, t1;
+            g_events.used = 0;
+            POPCORN_TRY(g_events.get(&t0));
+            POPCORN_TRY(g_events.get(&t1));
+            TuneValue best{};
+            best.ms = 3.0e38f;
+            for (int cand : {POPCORN_SCHEDULE_SYMMETRIC, POPCORN_SCHEDULE_FULL}) {
+                float ms = 3.0e38f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    POPCORN_CUDA(cudaEventRecord(t0, s));
+                    POPCORN_TRY(build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, POPCORN_K_FP32, kdiag,
+                                                    &ws, err, dev->sms, s, &launches, 0,
+                                                    cand == POPCORN_SCHEDULE_FULL ? 1 : 0));
+                    POPCORN_CUDA(cudaEventRecord(t1, s));
+                    POPCORN_CUDA(cudaEventSynchronize(t1));
+                    float el = 0.f;
+                    POPCORN_CUDA(cudaEventElapsedTime(&el, t0, t1));
+                    if (rep > 0 && el < ms) ms = el;
+                }
+                if (ms < best.ms) {
+                    best.ms = ms;
+                    best.p[0] = cand;
+                }
+            }
+            tune_store(key, best);
+            use = best.p[0];
+        } else {
+            use = POPCORN_SCHEDULE_SYMMETRIC;
+        }
+    }
     POPCORN_TRY(build_kernel_matrix(P, (int)n, d, ldp, kp, precision, K, ldk, POPCORN_K_FP32, kdiag, &ws, err,
-                                    dev->sms, s, &launches));
+                                    dev->sms, s, &launches, 0, use == POPCORN_SCHEDULE_FULL ? 1 : 0));
     int herr = 0;
     POPCORN_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     POPCORN_CUDA(cudaStreamSynchronize(s));
     if (herr) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the tensor-core K build ran out");
     return POPCORN_OK;
+}
+
+popcorn_status popcorn_kernel_matrix(const float* P, int64_t n, int32_t d, int64_t ldp, popcorn_kernel kern,
+                                     int32_t precision, float* K, int64_t ldk, float* kdiag, popcorn_stream_t stream) {
+    return popcorn_kernel_matrix_ex(P, n, d, ldp, kern, precision, POPCORN_SCHEDULE_AUTO, K, ldk, kdiag, stream);
 }
 
 popcorn_status popcorn_assign_step(const float* K, int64_t ldk, const float* kdiag, int64_t n, int32_t k,
@@ -730,9 +778,21 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // kernels of one pass's reduction: the full-square stream; or the symmetric stream and its
     // fold (the run form first sorts every block's labels)
     const int red_launches = use_sym ? (sym.runs ? 3 : 2) : 1;
+    // Error-path test hook: with POPCORN_TEST_SYM_STALL_MS=<ms> in the environment, the
+    // first symmetric (branch-form) stream launch of this fit leaves one block's copies out
+    // and bounds its waits by <ms>, so the fit reports POPCORN_ERR_TIMEOUT (nothing faults
+    // or hangs; the context stays usable).  Unset in every ordinary run.
+    int stall_ms = 0;
+    if (use_sym && !sym.runs) {
+        const char* env = getenv("POPCORN_TEST_SYM_STALL_MS");
+        if (env && *env) stall_ms = atoi(env);
+        if (stall_ms < 0 || stall_ms > 10000) stall_ms = 0;
+    }
     auto reduce_pass = [&](int eval, cudaEvent_t mid, cudaStream_t st) -> cudaError_t {
         if (!use_sym) return launch_reduce(b, plan, eval, st);
-        return launch_reduce_sym(b, sym, &b.st->wait_err, eval, st, mid);
+        const int stall = stall_ms;
+        stall_ms = 0;
+        return launch_reduce_sym(b, sym, &b.st->wait_err, eval, st, mid, stall);
     };
     POPCORN_TRY(ws.alloc(&b.zsum, (size_t)k, "z sums"));
     POPCORN_TRY(ws.alloc(&b.cnorm, (size_t)k, "centroid norms"));

@@ -81,11 +81,17 @@ struct TileSmem {
 template <int KIND, typename TK = float, bool ONE_SLICE = false, int PACKED = 0>
 __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, int d, int64_t ldp,
                                             const KernParams& kp, TK* __restrict__ K, int64_t ldk,
-                                            float* __restrict__ kdiag, int T, long long tile, TileSmem& sm) {
+                                            float* __restrict__ kdiag, int T, long long tile, TileSmem& sm,
+                                            int full = 0) {
     auto& As = sm.As;
     auto& Bs = sm.Bs;
     int bi, bj;
-    tri_coords(tile, T, &bi, &bj);
+    if (full) {   // every tile of the square, row by row (the GEMM form): no transposes
+        bi = (int)(tile / T);
+        bj = (int)(tile % T);
+    } else {
+        tri_coords(tile, T, &bi, &bj);
+    }
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int row0 = bi * TILE, col0 = bj * TILE;
     const bool vec = (ldp & 3) == 0 && ((uintptr_t)P & 15) == 0;
@@ -238,7 +244,7 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
             }
         }
     }
-    if (bi != bj) {
+    if (bi != bj && !full) {
 #pragma unroll
         for (int y = 0; y < 8; ++y) {
             int c = col0 + tx * 4 + (y & 3) + 64 * (y >> 2);
@@ -256,9 +262,9 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
 template <int KIND, typename TK, int PACKED>
 __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
                                                           KernParams kp, TK* __restrict__ K, int64_t ldk,
-                                                          float* __restrict__ kdiag, int T) {
+                                                          float* __restrict__ kdiag, int T, int full) {
     __shared__ __align__(16) TileSmem sm;
-    kbuild_tile<KIND, TK, false, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm);
+    kbuild_tile<KIND, TK, false, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm, full);
 }
 
 // d <= KC: the depth loop is one slice, so no next slice is held in registers;
@@ -267,45 +273,46 @@ __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restric
 template <int KIND, typename TK, int PACKED>
 __global__ void __launch_bounds__(256, 2) kbuild_simt_small_kernel(const float* __restrict__ P, int n, int d,
                                                                    int64_t ldp, KernParams kp, TK* __restrict__ K,
-                                                                   int64_t ldk, float* __restrict__ kdiag, int T) {
+                                                                   int64_t ldk, float* __restrict__ kdiag, int T,
+                                                                   int full) {
     __shared__ __align__(16) TileSmem sm;
-    kbuild_tile<KIND, TK, true, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm);
+    kbuild_tile<KIND, TK, true, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm, full);
 }
 
 template <typename TK, int PACKED>
 cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernParams kp, TK* K, int64_t ldk,
-                              float* kdiag, cudaStream_t s) {
+                              float* kdiag, cudaStream_t s, int full = 0) {
     const int T = (n + TILE - 1) / TILE;
-    const long long tiles = (long long)T * (T + 1) / 2;
+    const long long tiles = full ? (long long)T * T : (long long)T * (T + 1) / 2;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     dim3 grid((unsigned)tiles), block(256);
     if (d <= KC) {
         switch (kp.kind) {
             case POPCORN_LINEAR:
                 kbuild_simt_small_kernel<POPCORN_LINEAR, TK, PACKED>
-                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
                 break;
             case POPCORN_POLYNOMIAL:
                 kbuild_simt_small_kernel<POPCORN_POLYNOMIAL, TK, PACKED>
-                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
                 break;
             default:
                 kbuild_simt_small_kernel<POPCORN_GAUSSIAN, TK, PACKED>
-                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
                 break;
         }
         return cudaGetLastError();
     }
     switch (kp.kind) {
         case POPCORN_LINEAR:
-            kbuild_simt_kernel<POPCORN_LINEAR, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            kbuild_simt_kernel<POPCORN_LINEAR, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
             break;
         case POPCORN_POLYNOMIAL:
             kbuild_simt_kernel<POPCORN_POLYNOMIAL, TK, PACKED>
-                <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+                <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
             break;
         default:
-            kbuild_simt_kernel<POPCORN_GAUSSIAN, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T);
+            kbuild_simt_kernel<POPCORN_GAUSSIAN, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
             break;
     }
     return cudaGetLastError();
@@ -344,7 +351,7 @@ cudaError_t launch_batched_kbuild_simt(const BatchInst* dI, const BatchPlan& bp,
 }
 
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp, void* K, int64_t ldk,
-                               int k_storage, float* kdiag, cudaStream_t s, int* launches, int packed) {
+                               int k_storage, float* kdiag, cudaStream_t s, int* launches, int packed, int full) {
     if (launches) ++*launches;
     if (packed) {
         if (k_storage != POPCORN_K_FP32) return cudaErrorInvalidValue;
@@ -356,7 +363,7 @@ cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernPa
         return launch_simt_typed<__half, 0>(P, n, d, ldp, kp, static_cast<__half*>(K), ldk, kdiag, s);
     if (k_storage == POPCORN_K_BF16)
         return launch_simt_typed<__nv_bfloat16, 0>(P, n, d, ldp, kp, static_cast<__nv_bfloat16*>(K), ldk, kdiag, s);
-    return launch_simt_typed<float, 0>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
+    return launch_simt_typed<float, 0>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s, full);
 }
 
 }  // namespace popcorn

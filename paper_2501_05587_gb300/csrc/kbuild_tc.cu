@@ -75,6 +75,9 @@ struct TcArgs {
     long long tiles;          // sum_p (T - 2 p)
     float* Kp;                // block-packed K (tile (I, J), I <= J, at its row-by-row triangle index
                               // times 16384 floats, four 128 x 32 boxes), or null
+    int full;                 // 1: every tile of the square (the GEMM form), each stored once; 0: the
+                              // tiles on and above the diagonal (the SYRK form), stored with their
+                              // transposes unless K is packed
     int sw4;                  // packed layout kPackedSw4 (element c of row r at c ^ (r mod 32)); else
                               // kPackedSw16 (the 128-byte swizzle of the staging chunk)
     KernParams kp;
@@ -85,7 +88,13 @@ struct TcArgs {
 
 // tile t -> (row pair p, column block j): row pair p holds tiles j = 2p .. T-1 and
 // starts at off(p) = p T - p (p - 1); a binary search over p (no floating point).
-__device__ __forceinline__ void pair_coords(long long t, int T, int T2, int* p, int* j) {
+// The full schedule (every column block, the GEMM form) has row pair p at p T.
+__device__ __forceinline__ void pair_coords(long long t, int T, int T2, int full, int* p, int* j) {
+    if (full) {
+        *p = (int)(t / T);
+        *j = (int)(t % T);
+        return;
+    }
     int lo = 0, hi = T2 - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -168,7 +177,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             bool ok = true;
             for (long long t = blockIdx.x; t < a.tiles && ok; t += G) {
                 int p, j;
-                pair_coords(t, a.T, a.T2, &p, &j);
+                pair_coords(t, a.T, a.T2, a.full, &p, &j);
                 for (int kb = 0; kb < a.nkb; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.err)) {
                         ok = false;
@@ -261,7 +270,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         bool ok = true;
         for (long long t = blockIdx.x; t < a.tiles; t += G, ++lt) {
             int p, j;
-            pair_coords(t, a.T, a.T2, &p, &j);
+            pair_coords(t, a.T, a.T2, a.full, &p, &j);
             const int ab = lt & 1;
             const uint32_t use = (uint32_t)(lt >> 1);
             // column norms of this tile's column block j
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int row = rb * BM + row_local;
                 const float ri = (a.kp.kind == POPCORN_GAUSSIAN && row < a.n) ? a.norms[row] : 0.f;
                 // blocks past the matrix and block (2p + 1, 2p) below the diagonal are not stored
-                const bool store = rb < a.T && rb <= j;
+                const bool store = rb < a.T && (a.full || rb <= j);
                 const bool diag = (rb == j);
                 for (int c = 0; c < BM / 32; ++c) {
                     float v[32];
@@ -326,7 +335,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             *reinterpret_cast<float4*>(sd + row_local * 32 + ((i ^ (row_local & 7)) * 4)) = w;
                         }
                     }
-                    if (!diag && !a.Kp) {
+                    const bool transpose = !diag && !a.Kp && !a.full;
+                    if (transpose) {
 #pragma unroll
                         for (int x = 0; x < 32; ++x) sx[x * 128 + row_local] = v[x];
                     }
@@ -339,7 +349,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             bulk_store_1d(a.Kp + tri * (BM * BM) + c * (BM * 32), smem_u32(sd), (uint32_t)STG_BYTES);
                         } else {
                             tma_store_2d(&map_kd, j * BM + 32 * c, rb * BM, smem_u32(sd));
-                            if (!diag) tma_store_2d(&map_kt, rb * BM, j * BM + 32 * c, smem_u32(sx));
+                            if (transpose) tma_store_2d(&map_kt, rb * BM, j * BM + 32 * c, smem_u32(sx));
                         }
                         bulk_commit();
                     }
@@ -436,7 +446,7 @@ cudaError_t configure_kbuild_tc() {
 
 cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
                              int64_t ldk, float* kdiag, void* workspace, int* err, int num_sms, cudaStream_t s,
-                             int* launches, int packed) {
+                             int* launches, int packed, int full) {
     const int dpad = (d + BK - 1) / BK * BK;
     const int x3 = precision == POPCORN_BF16X3 ? 1 : 0;
     const int64_t ldw = (int64_t)(x3 ? 2 : 1) * dpad;
@@ -482,7 +492,8 @@ cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernPara
     a.off_rj = a.off_st + a.nstg * STG_BYTES;
     a.off_bar = a.off_rj + BM * 4;
     a.off_misc = a.off_bar + 16 * 8;
-    a.tiles = (long long)a.T2 * a.T - (long long)a.T2 * (a.T2 - 1);
+    a.full = full && !packed ? 1 : 0;
+    a.tiles = a.full ? (long long)a.T2 * a.T : (long long)a.T2 * a.T - (long long)a.T2 * (a.T2 - 1);
     a.Kp = packed ? K : nullptr;
     a.sw4 = packed == kPackedSw4 ? 1 : 0;
     a.kp = kp;

@@ -98,9 +98,12 @@ struct SymPlan {
 SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req = 0, int stages_req = 0);
 cudaError_t configure_reduce_sym(int smem_optin);
 // err: set when a bounded wait of the stream kernel runs out; `between` (may be
-// null) is recorded on s after the stream kernel, before the fold.
+// null) is recorded on s after the stream kernel, before the fold.  stall_ms > 0
+// (branch form; error-path tests only): CTA 0 leaves its first block's copies out,
+// and every wait of the launch gives up after stall_ms, so the launch reports a
+// timed-out wait and the context stays usable.
 cudaError_t launch_reduce_sym(const struct PassBuffers& b, const SymPlan& p, int* err, int eval_only,
-                              cudaStream_t s, cudaEvent_t between);
+                              cudaStream_t s, cudaEvent_t between, int stall_ms = 0);
 
 // Launch with programmatic dependent launch: the grid may be scheduled while the
 // previous kernel in the stream is still finishing, and it must call
@@ -157,9 +160,11 @@ constexpr int kPackedSw16 = 1, kPackedSw4 = 2;
 // K is float, __half or __nv_bfloat16 by k_storage (popcorn_k_storage); ldk in elements.
 // packed: 0 = full square; kPackedSw16 / kPackedSw4 = FP32 K as the block-packed upper
 // triangle in that layout, read by the symmetric pass (ldk is then unused).
+// full = 1 (full square only): every tile of the square computed and stored once (the
+// GEMM form) instead of the upper-triangle tiles stored with their transposes (SYRK form).
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp,
                                void* K, int64_t ldk, int k_storage, float* kdiag, cudaStream_t s, int* launches,
-                               int packed = 0);
+                               int packed = 0, int full = 0);
 
 // ---- K build on tensor cores (kbuild_tc.cu) ---------------------------------
 // Workspace bytes for the BF16 operand copies and row norms.
@@ -173,7 +178,7 @@ cudaError_t configure_kbuild_tc();
 // in that layout (as the FP32 build writes it for the symmetric pass); ldk is then unused.
 cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
                              int64_t ldk, float* kdiag, void* workspace, int* err, int num_sms, cudaStream_t s,
-                             int* launches, int packed = 0);
+                             int* launches, int packed = 0, int full = 0);
 
 // 2-D tiled TMA descriptor over a row-major matrix (inner = contiguous extent
 // in elements, row_bytes = pitch); false if the driver entry point is missing

@@ -94,6 +94,11 @@ struct BranchArgs {
     const LoopState* st;
     int* err;
     int eval_only;
+    // Test hook for the error path (0 in every ordinary launch): CTA 0 never issues the
+    // copies of its block number stall_block - 1, so the waits for it run out after
+    // wait_ns and the launch reports a timed-out wait.
+    int stall_block;
+    unsigned long long wait_ns;
 };
 
 // 16 bytes at (row r, 16-byte chunk j) of a 32-column box under the 128-byte
@@ -160,9 +165,13 @@ __global__ void __launch_bounds__(kSymThreads, 1)
         if (lane == 0) {
             const uint64_t stream_once = tc::l2_evict_first();   // K is read once per pass
             long long t = 0;
+            const long long skip = blockIdx.x == 0 ? (long long)a.stall_block - 1 : -1;
             for (; t < nmine; ++t) {
                 const int s = (int)(t % S);
-                if (t >= S && !tc::mbar_wait(empty_bar(s), (uint32_t)((t / S) - 1) & 1u, abort_flag, a.err)) break;
+                if (t >= S &&
+                    !tc::mbar_wait_for(empty_bar(s), (uint32_t)((t / S) - 1) & 1u, abort_flag, a.err, a.wait_ns))
+                    break;
+                if (t == skip) continue;   // the test hook: this block never arrives
                 int I, J;
                 tri_coords(blockIdx.x + t * G, a.T, &I, &J);
                 ij[s] = make_int2(I, J);   // published by the arrive below (release)
@@ -187,9 +196,10 @@ __global__ void __launch_bounds__(kSymThreads, 1)
                 // leaving early: let this thread's copies land before the CTA's memory goes
                 // (bounded; the consumers may never have waited for them)
                 for (long long t2 = t > S ? t - S : 0; t2 < t; ++t2) {
+                    if (t2 == skip) continue;   // nothing was issued for it
                     const uint32_t bar = full_bar((int)(t2 % S)), par = (uint32_t)(t2 / S) & 1u;
                     const unsigned long long t0 = tc::globaltimer();
-                    while (!tc::mbar_try_wait(bar, par) && tc::globaltimer() - t0 < tc::kWaitLimitNs) {
+                    while (!tc::mbar_try_wait(bar, par) && tc::globaltimer() - t0 < a.wait_ns) {
                     }
                 }
             }
@@ -206,7 +216,7 @@ __global__ void __launch_bounds__(kSymThreads, 1)
     // partials (block t) before their next writes.
     for (long long t = 0; t < nmine; ++t) {
         const int s = (int)(t % S);
-        const bool ok = tc::mbar_wait(full_bar(s), (uint32_t)(t / S) & 1u, abort_flag, a.err);
+        const bool ok = tc::mbar_wait_for(full_bar(s), (uint32_t)(t / S) & 1u, abort_flag, a.err, a.wait_ns);
         if (!tc::named_bar_all(bar_id, kGroup, ok)) break;   // the group leaves together
         const int2 bij = ij[s];
         const int I = bij.x, J = bij.y;
@@ -405,7 +415,7 @@ struct RunArgs {
     int a, Ts;
     long long units;
     int stages;
-    int off_meta, off_accr, off_accc, off_colacc, off_bars, off_flag;
+    int off_meta, off_accr, off_colacc, off_bars, off_flag;
     const uint8_t* meta;       // [T][kMetaBytes]
     float* Spart;              // [nslots][k][n]
     const LoopState* st;
@@ -430,11 +440,13 @@ __device__ __forceinline__ void sum_runs(const float* __restrict__ tile, const u
             v[e] = tile[code ^ key];
         }
         const uint32_t mb = (uint32_t)(mask >> (8 * pc)) & 0xffu;
+        const uint2 lw = *reinterpret_cast<const uint2*>(labels + 8 * pc);   // the chunk's 8 labels
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             run += v[e];
             if (mb & (1u << e)) {   // uniform over the warp
-                float* dst = acc + (int)labels[8 * pc + e] * kB;
+                const uint32_t lab = ((e < 4 ? lw.x : lw.y) >> (8 * (e & 3))) & 0xffu;
+                float* dst = acc + lab * kB;
                 *dst += run;
                 run = 0.f;
             }
@@ -514,8 +526,9 @@ __global__ void __launch_bounds__(kSymThreads, 1) reduce_sym_runs_kernel(RunArgs
     const int mine = 32 * q + lane;
     const uint32_t key = rowg ? (uint32_t)(32 * mine + lane) : (uint32_t)(4096 * q + lane);
     float* accr = reinterpret_cast<float*>(smem + a.off_accr);     // [2][k][128] row sums of the block row
-    float* accc = reinterpret_cast<float*>(smem + a.off_accc);     // [2][k][128] column sums of the block
-    float* my = (rowg ? accr : accc) + (size_t)h * k * kB + mine;  // this lane's sums: my[c * 128]
+    // column sums of the super-tile's block columns, per half: [a][2][k][128]
+    float* colacc = reinterpret_cast<float*>(smem + a.off_colacc);
+    float* my = accr + (size_t)h * k * kB + mine;                  // row group: this lane's sums my[c * 128]
     const int diag_slot = a.Ts;
 
     int t = 0;
@@ -534,8 +547,9 @@ __global__ void __launch_bounds__(kSymThreads, 1) reduce_sym_runs_kernel(RunArgs
                 const uint8_t* mI = smem + a.off_meta + s * 2 * kMetaBytes;
                 const uint8_t* mJ = mI + kMetaBytes;
                 if (rowg) {
-                    // row sums of block I over the columns of block J (sorted by label), kept over
-                    // the super-tile's columns; stored to slot Js after the last one
+                    // row sums of block I over the columns of block J (sorted by label), kept per
+                    // half over the super-tile's columns; the halves are added and stored to slot
+                    // Js after the last one
                     if (J == max(I, w.J0))
                         for (int c = 0; c < k; ++c) my[c * kB] = 0.f;
                     sum_runs(tile, reinterpret_cast<const uint16_t*>(mJ + kMetaColcode) + 64 * h,
@@ -547,8 +561,10 @@ __global__ void __launch_bounds__(kSymThreads, 1) reduce_sym_runs_kernel(RunArgs
                         tc::named_bar<kGroup>(kBarRows);
                         if (u < kB && I * kB + u < n) {
                             float* out = a.Spart + (size_t)w.Js * k * n + I * kB + u;
-                            for (int c = 0; c < k; ++c)
-                                tc::st_hint(out + (size_t)c * n, accr[c * kB + u] + accr[(k + c) * kB + u], keep);
+                            const float* __restrict__ h0 = accr + u;
+                            const float* __restrict__ h1 = accr + (size_t)k * kB + u;
+#pragma unroll 4
+                            for (int c = 0; c < k; ++c) tc::st_hint(out + (size_t)c * n, h0[c * kB] + h1[c * kB], keep);
                         }
                     }
                 } else {
@@ -558,27 +574,28 @@ __global__ void __launch_bounds__(kSymThreads, 1) reduce_sym_runs_kernel(RunArgs
                         if (lane == 0) tc::mbar_arrive(empty_bar(s));
                         continue;
                     }
-                    // column sums of block J over the rows of block I (sorted by label), kept over
-                    // the super-tile's rows in colacc[J - J0]; a diagonal block adds nothing
-                    for (int c = 0; c < k; ++c) my[c * kB] = 0.f;
+                    // column sums of block J over the rows of block I (sorted by label), kept per
+                    // half over the super-tile's rows in colacc[J - J0]; after the last of those
+                    // rows the halves are added and stored to slot Is (the extra slot for a
+                    // diagonal super-tile).  A diagonal block adds nothing.
+                    float* myc = colacc + ((size_t)(J - w.J0) * 2 + h) * k * kB + mine;
+                    if (I == w.I0)
+                        for (int c = 0; c < k; ++c) myc[c * kB] = 0.f;
                     if (!diag)
                         sum_runs(tile, reinterpret_cast<const uint16_t*>(mI + kMetaRowcode) + 64 * h,
                                  mI + kMetaLabel + 64 * h,
-                                 reinterpret_cast<const unsigned long long*>(mI + kMetaMask)[h], key, my);
+                                 reinterpret_cast<const unsigned long long*>(mI + kMetaMask)[h], key, myc);
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(empty_bar(s));
-                    tc::named_bar<kGroup>(kBarCols);
-                    if (u < kB) {
-                        float* ca = reinterpret_cast<float*>(smem + a.off_colacc) + (size_t)(J - w.J0) * k * kB + u;
-                        const bool first = I == w.I0, last = I == min(J, w.I1 - 1);
-                        for (int c = 0; c < k; ++c) {
-                            const float v = accc[c * kB + u] + accc[(k + c) * kB + u];
-                            ca[c * kB] = first ? v : ca[c * kB] + v;
-                        }
-                        if (last && J * kB + u < n) {
+                    if (I == min(J, w.I1 - 1)) {
+                        tc::named_bar<kGroup>(kBarCols);
+                        if (u < kB && J * kB + u < n) {
                             const int slot = w.Is == w.Js ? diag_slot : w.Is;
                             float* out = a.Spart + (size_t)slot * k * n + J * kB + u;
-                            for (int c = 0; c < k; ++c) tc::st_hint(out + (size_t)c * n, ca[c * kB], keep);
+                            const float* __restrict__ h0 = colacc + (size_t)(J - w.J0) * 2 * k * kB + u;
+                            const float* __restrict__ h1 = h0 + (size_t)k * kB;
+#pragma unroll 4
+                            for (int c = 0; c < k; ++c) tc::st_hint(out + (size_t)c * n, h0[c * kB] + h1[c * kB], keep);
                         }
                     }
                 }
@@ -586,16 +603,19 @@ __global__ void __launch_bounds__(kSymThreads, 1) reduce_sym_runs_kernel(RunArgs
     }
 }
 
+// Dynamic shared memory of the run form, in order: the block ring (1024-byte aligned),
+// the metadata ring (row block, column block), the row sums of a block row per half
+// ([2][k][128]), the column sums of the super-tile's block columns per half
+// ([a][2][k][128]), barriers and the abort flag.
 struct RunLayout {
-    int meta, accr, accc, colacc, bars, flag, bytes;
+    int meta, accr, colacc, bars, flag, bytes;
 };
 RunLayout run_layout(int k, int stages, int a) {
     RunLayout L;
     L.meta = stages * kTileBytes;
     L.accr = align128(L.meta + stages * 2 * kMetaBytes);
-    L.accc = align128(L.accr + 2 * k * kB * 4);
-    L.colacc = align128(L.accc + 2 * k * kB * 4);
-    L.bars = align128(L.colacc + a * k * kB * 4);
+    L.colacc = align128(L.accr + 2 * k * kB * 4);
+    L.bars = align128(L.colacc + a * 2 * k * kB * 4);
     L.flag = L.bars + 2 * stages * 8;
     L.bytes = L.flag + 16 + 1024;
     return L;
@@ -738,7 +758,7 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, in
 }
 
 cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, int eval_only, cudaStream_t s,
-                              cudaEvent_t between) {
+                              cudaEvent_t between, int stall_ms) {
     cudaError_t e;
     if (p.runs) {
         if (!p.packed || p.layout != kPackedSw4 || !b.sym_meta) return cudaErrorInvalidValue;
@@ -757,7 +777,6 @@ cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, 
         r.stages = p.stages;
         r.off_meta = L.meta;
         r.off_accr = L.accr;
-        r.off_accc = L.accc;
         r.off_colacc = L.colacc;
         r.off_bars = L.bars;
         r.off_flag = L.flag;
@@ -788,6 +807,8 @@ cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, 
         a.st = b.st;
         a.err = err;
         a.eval_only = eval_only;
+        a.stall_block = stall_ms > 0 ? 1 : 0;
+        a.wait_ns = stall_ms > 0 ? (unsigned long long)stall_ms * 1000000ull : tc::kWaitLimitNs;
         e = b.k <= 4 ? launch_pdl(reduce_sym_kernel<4>, dim3(p.grid), dim3(kSymThreads), p.smem, s, map, a)
                      : launch_pdl(reduce_sym_kernel<8>, dim3(p.grid), dim3(kSymThreads), p.smem, s, map, a);
     }

@@ -1,0 +1,65 @@
+"""Failure detection, tested without a GPU fault.
+
+Every wait inside the library's warp-specialized kernels is bounded: a wait that does
+not see its phase within the limit raises the CTA's abort flag and an error word, every
+role of the CTA leaves its loop, waits (bounded again) for its own copies in flight and
+returns, and the host reports POPCORN_ERR_TIMEOUT.  These tests make such a wait run out
+on purpose through the library's test hook: POPCORN_TEST_SYM_STALL_MS=<ms> makes the first
+symmetric-stream launch of a fit leave one block's copies out (nothing ever arrives on
+that block's barrier) with every wait of the launch bounded by <ms>.  Nothing faults or
+hangs: the kernel returns, the call fails with the timeout status, and the next call on
+the same context gives the reference result.  The other host-side failure paths (an
+allocation the device cannot satisfy, a label out of range) are in test_gpu_parity.py.
+"""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2501_05587_gb300 as mod
+    return mod
+
+
+@pytest.mark.parametrize("check", [False, True], ids=["graph", "plain"])
+def test_stream_wait_timeout_is_reported_and_the_context_survives(pc, monkeypatch, check):
+    wl = synth.workload("rings", scale=0.1)              # n = 2,000: 136 blocks, one a CTA
+    P = torch.from_numpy(wl.P).cuda()
+    lab = torch.from_numpy(wl.init_labels).cuda()
+    kw = dict(max_iter=6, check_convergence=check, history=True, k_pass="symmetric")
+    ref = pc.popcorn_fit(P, wl.k, wl.kernel, lab, **kw)
+    assert ref["info"]["k_pass_used"] == 1
+    monkeypatch.setenv("POPCORN_TEST_SYM_STALL_MS", "200")
+    t0 = time.perf_counter()
+    with pytest.raises(pc.PopcornError) as ei:
+        pc.popcorn_fit(P, wl.k, wl.kernel, lab, **kw)
+    assert ei.value.status == 4, str(ei.value)          # POPCORN_ERR_TIMEOUT
+    assert "bounded wait" in str(ei.value)
+    assert time.perf_counter() - t0 < 60
+    monkeypatch.delenv("POPCORN_TEST_SYM_STALL_MS")
+    torch.cuda.synchronize()                              # the context is intact
+    again = pc.popcorn_fit(P, wl.k, wl.kernel, lab, **kw)
+    assert torch.equal(again["labels"], ref["labels"])
+    assert again["objective"] == ref["objective"]
+    assert again["info"]["J_history"] == ref["info"]["J_history"]
+
+
+def test_stall_hook_is_inert_when_unset(pc):
+    """Without the variable, or with the full-square pass (the hook touches the symmetric
+    stream only), fits are the ordinary ones."""
+    wl = synth.workload("blobs", scale=0.3)
+    P = torch.from_numpy(wl.P).cuda()
+    lab = torch.from_numpy(wl.init_labels).cuda()
+    a = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=4, check_convergence=False, k_pass="full")
+    b = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=4, check_convergence=False, k_pass="full")
+    assert torch.equal(a["labels"], b["labels"]) and a["objective"] == b["objective"]
+    assert np.isfinite(a["objective"])

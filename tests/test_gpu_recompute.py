@@ -143,19 +143,20 @@ def test_recompute_matches_materialized_bf16(pc):
     assert rel_err(b["info"]["J_history"][0], a["info"]["J_history"][0]) <= 1e-5
 
 
-# The FP8 form's objective error on the mixture subsample, measured: E4M3 keeps 3 mantissa bits,
-# so each squared distance (about 256 within a component, from norms near 640) moves by a few
-# units and each kernel value by ~10%.  This misses the 1e-3 bar the reduced-precision forms
-# aim for; it is a stated limit of the FP8 form, not a tolerance of the method.
-FP8_OBJ_LIMIT = 5e-2
+# The reduced-precision forms' bar on the objective: relative error <= 1e-3.  FP8 keeps only
+# 3 mantissa bits per coordinate, so its kernel values carry percent-level errors, but on the
+# mixture subsample those average out in J: measured 3.8e-4 (FP64 objective of its labels
+# against the oracle's fit) and 6.2e-4 (its reported objective against the FP64 objective of
+# the same labels).
+FP8_OBJ_LIMIT = 1e-3
 
 
 def test_recompute_subsample_of_full_draw_vs_oracle_fit(pc):
     """The first 20,000 points of the mixture workload's own n = 200,000 draw, clustered
     from the same initial labels by the BF16 and FP8 recompute fits (20 passes) and by the
     oracle's loop on the FP64 K.  Reported: each GPU fit's objective against the FP64
-    objective of its labels, and against the objective the oracle's fit reaches.  BF16
-    meets the 1e-3 bar; FP8 is held to its measured limit (it misses 1e-3)."""
+    objective of its labels, and against the objective the oracle's fit reaches; both
+    forms are held to the 1e-3 bar."""
     full = synth.workload("mixture")                     # n = 200,000, d = 128, k = 100
     n = 20000
     P, lab = np.ascontiguousarray(full.P[:n]), np.ascontiguousarray(full.init_labels[:n])

@@ -68,8 +68,11 @@ def test_symmetric_pass_is_the_oracle_step(pc, n, d, k, kern, seed, sym_tile):
     lab = synth.init_labels(n, k, seed=seed + 100)
     r = pc.popcorn_fit(torch.from_numpy(P).cuda(), k, kern, torch.from_numpy(lab).cuda(), max_iter=1,
                        check_convergence=False, k_pass="symmetric", sym_tile=sym_tile)
-    assert r["info"]["k_pass_used"] == 1
-    if sym_tile:
+    # single blocks always fit; a forced super-tile whose per-half column sums
+    # (a x 2 x k x 512 bytes) do not fit next to the block ring falls back to the full square
+    if sym_tile <= 1 or k * (1 + sym_tile) <= 64:
+        assert r["info"]["k_pass_used"] == 1
+    if sym_tile and r["info"]["k_pass_used"] == 1:
         assert r["info"]["schedule"][0] == sym_tile
     Ko = oracle.kernel_matrix(P, kern)
     st = oracle.step(Ko, lab, k)
