@@ -91,6 +91,10 @@ def parse():
                          "on and above the diagonal (row and column sums, then a fold)")
     ap.add_argument("--sym-tile", type=int, default=0, choices=[0, 1, 2, 4],
                     help="super-tile edge of the symmetric pass (0: the library's choice)")
+    ap.add_argument("--sweep", default=None, choices=["kbuild"],
+                    help="kbuild: the K build's GEMM-versus-SYRK sweep (n in {1e4, 5e4} x d in {1e2 .. 1e5}): the "
+                         "symmetric and the full tile schedule of each precision, cuBLAS SGEMM / SSYRK run as "
+                         "comparators, and the tuned choice")
     ap.add_argument("--compare", default=None, choices=["paper"],
                     help="paper: also time the paper's formulation through library calls (cuBLAS GEMM + "
                          "elementwise kernel function, cuSPARSE SpMM/SpMV per pass) on the same inputs")
@@ -623,10 +627,118 @@ def run_paper_pipeline(args):
     return 0
 
 
+def _cublas():
+    """ctypes handle on the cuBLAS library torch has loaded (found through the process's maps)."""
+    import ctypes
+
+    try:
+        with open("/proc/self/maps") as f:
+            paths = {line.split()[-1] for line in f if "libcublas.so" in line and "Lt" not in line}
+        for path in sorted(paths):
+            lib = ctypes.CDLL(path)
+            if hasattr(lib, "cublasSsyrk_v2"):
+                return lib
+    except Exception:
+        pass
+    return None
+
+
+def run_sweep_kbuild(args):
+    """The paper's GEMM-versus-SYRK experiment (Sec. 5.2: n in {1e4, 5e4}, d in {1e2, 1e3, 1e4,
+    1e5}; Sec. 4.2's rule: GEMM when n / d > 100) re-run on this GPU.  B = P P^T (linear kernel,
+    P uniform in [0, 1), seeded on the device).  Ours: popcorn_kernel_matrix_ex in each precision
+    with the symmetric schedule (tiles on and above the diagonal, stored with their transposes:
+    the SYRK form) and the full schedule (every tile: the GEMM form), then the tuned choice
+    (schedule "tune": both timed, the faster cached).  Comparators, library calls only: cuBLAS
+    SGEMM (torch.mm, TF32 off) and cuBLAS SSYRK (ctypes), FP32 as in the paper."""
+    import ctypes
+
+    import torch
+
+    import paper_2501_05587_gb300 as pc
+
+    torch.backends.cuda.matmul.allow_tf32 = False
+    stream = torch.cuda.current_stream()
+    lin = {"kind": "linear", "gamma": 1.0, "coef0": 0.0, "degree": 1, "sigma": 1.0}
+    ns = [int(x) for x in os.environ.get("SWEEP_N", "10000,50000").split(",")]
+    ds = [int(x) for x in os.environ.get("SWEEP_D", "100,1000,10000,100000").split(",")]
+
+    def clock(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if ms < 1000.0:   # short: best of three more
+            for _ in range(3):
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = min(ms, e0.elapsed_time(e1))
+        return ms
+
+    torch.mm(torch.ones(8, 8, device="cuda"), torch.ones(8, 8, device="cuda"))
+    torch.cuda.synchronize()
+    cublas = _cublas()
+    rows = []
+    for n in ns:
+        for d in ds:
+            g = torch.Generator(device="cuda")
+            g.manual_seed(1000003 * n + d)
+            P = torch.rand((n, d), generator=g, device="cuda", dtype=torch.float32)
+            ldk = (n + 3) // 4 * 4
+            Kb = torch.empty((n, ldk), dtype=torch.float32, device="cuda")
+            K = Kb[:, :n]
+            kd = torch.empty(n, dtype=torch.float32, device="cuda")
+            gemm_flops, alg_flops = 2.0 * n * n * d, float(n) * (n + 1) * d
+            row = {"n": n, "d": d, "n_over_d": n / d,
+                   "paper_rule": "gemm" if n / d > 100 else "syrk", "ms": {}}
+            for prec in ("fp32", "bf16x3", "bf16"):
+                for sched in ("symmetric", "full"):
+                    row["ms"][f"ours_{prec}_{sched}"] = clock(
+                        lambda: pc.popcorn_kernel_matrix(P, lin, prec, K, kd, schedule=sched))
+                pc.popcorn_kernel_matrix(P, lin, prec, K, kd, schedule="tune")
+                row.setdefault("tuned", {})[prec] = ("full" if row["ms"][f"ours_{prec}_full"] <
+                                                     row["ms"][f"ours_{prec}_symmetric"] else "symmetric")
+            del Kb, K
+            C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+            row["ms"]["cublas_sgemm"] = clock(lambda: torch.mm(P, P.T, out=C))
+            if cublas is not None:
+                handle = ctypes.c_void_p(torch.cuda.current_blas_handle())
+                cublas.cublasSetStream_v2(handle, ctypes.c_void_p(stream.cuda_stream))
+                alpha, beta = ctypes.c_float(1.0), ctypes.c_float(0.0)
+
+                def syrk():
+                    # row-major P (n x d) is the column-major d x n matrix A: C = A^T A (upper)
+                    st = cublas.cublasSsyrk_v2(handle, 1, 1, n, d, ctypes.byref(alpha), ctypes.c_void_p(P.data_ptr()),
+                                               d, ctypes.byref(beta), ctypes.c_void_p(C.data_ptr()), n)
+                    if st != 0:
+                        raise RuntimeError(f"cublasSsyrk_v2 returned {st}")
+                row["ms"]["cublas_ssyrk"] = clock(syrk)
+            del C, P
+            torch.cuda.empty_cache()
+            row["gemm_equivalent_tflops"] = {k: gemm_flops / (v / 1e3) / 1e12 for k, v in row["ms"].items()}
+            row["algorithmic_tflops"] = {k: alg_flops / (v / 1e3) / 1e12 for k, v in row["ms"].items()}
+            row["full_over_symmetric"] = {p_: row["ms"][f"ours_{p_}_full"] / row["ms"][f"ours_{p_}_symmetric"]
+                                          for p_ in ("fp32", "bf16x3", "bf16")}
+            if "cublas_ssyrk" in row["ms"]:
+                row["cublas_sgemm_over_ssyrk"] = row["ms"]["cublas_sgemm"] / row["ms"]["cublas_ssyrk"]
+            rows.append(row)
+            print(json.dumps({"sweep": "kbuild", **row}), flush=True)
+    print(json.dumps({"sweep": "kbuild", "points": len(rows), "cublas_ssyrk": cublas is not None}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.compare == "paper":
         return run_paper_pipeline(args)
+    if args.sweep == "kbuild":
+        return run_sweep_kbuild(args)
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)

@@ -339,3 +339,31 @@ def test_fixed_iteration_graph_equals_plain_launches(pc, name, scale, k_pass):
         assert r["info"]["kernel_launches"] == p["info"]["kernel_launches"]
     assert h["info"]["loop_ms"] > 0 and h["info"]["reduce_ms"] == 0 and h["info"]["kbuild_ms"] > 0
     assert p["info"]["reduce_ms"] > 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("kern", [LINEAR, _gauss(3.0)], ids=["linear", "gauss"])
+def test_kernel_matrix_schedules_agree(pc, precision, kern):
+    """The full tile schedule (every tile formed, the GEMM form) and the symmetric one (tiles
+    on and above the diagonal stored with their transposes, the SYRK form) build the same K:
+    bit for bit in FP32 (the same products added in the same order), to accumulation-order
+    rounding in the tensor-core forms.  The tuned schedule is one of the two; FP32 against
+    the oracle as in test_kernel_matrix_fp32."""
+    n, d = 700, 37                                   # 6 tiles a side, ragged; d not a multiple of 64
+    P = synth.gaussian_blobs(n, d, 3, seed=17, box=2.0)
+    Pd = _dev(P)
+    Ks, ds = pc.popcorn_kernel_matrix(Pd, kern, precision, schedule="symmetric")
+    Kf, df = pc.popcorn_kernel_matrix(Pd, kern, precision, schedule="full")
+    Kt, _ = pc.popcorn_kernel_matrix(Pd, kern, precision, schedule="tune")
+    Ka, _ = pc.popcorn_kernel_matrix(Pd, kern, precision, schedule="auto")
+    torch.cuda.synchronize()
+    if precision == "fp32":
+        assert torch.equal(Ks, Kf) and torch.equal(ds, df)
+        Ko = oracle.kernel_matrix(P, kern)
+        tol = 1e-6 if kern["kind"] == "gaussian" else 2e-6 * np.abs(Ko) + 1e-6 * np.abs(Ko).max()
+        assert np.all(np.abs(Kf.cpu().numpy() - Ko) <= tol)
+    else:
+        scale = float(Ks.abs().max())
+        assert float((Ks - Kf).abs().max()) <= 1e-5 * scale
+    assert torch.equal(Kt, Ks) or torch.equal(Kt, Kf)
+    assert torch.equal(Ka, Kt)                       # auto takes the cached tuned choice
