@@ -113,8 +113,11 @@ typedef struct {
                                    recompute path of popcorn_fit (row blocks per tile, units
                                    per SM).  Results differ only by summation order.        */
     int32_t k_pass;             /* how a pass reads a stored FP32 K.  0 = automatic (the
-                                   default): the symmetric read below wherever it applies
-                                   (FP32 K, k <= 16), else the full square.  1 = symmetric:
+                                   default): the symmetric read below where it has measured
+                                   faster (FP32 K, k <= 4; k <= 8 while its per-block slots,
+                                   4 k n ceil(n / 128) bytes, stay within 64 MB), else the
+                                   full square.  1 = symmetric (FP32 K, k <= 32; larger k
+                                   falls back to the full square):
                                    only the 128 x 128 blocks on and above the diagonal (K is
                                    symmetric, and is then stored as that packed triangle); a
                                    block's row sums serve its rows and its column sums its

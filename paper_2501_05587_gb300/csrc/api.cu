@@ -717,8 +717,14 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // symmetric pass (FP32 K, k <= kSymMaxK; k_pass 0 or 1): the blocks on and above the
     // diagonal, row and column sums into T slots, folded into slot 0
     SymPlan sym{};
-    // automatic choice: the symmetric pass wherever it applies (k <= kSymMaxK)
-    if (ks == POPCORN_K_FP32 && opt.k_pass != 2)
+    // automatic choice, from measurements on GB300: the symmetric pass where it beats the
+    // full square (itself at ~0.99 of HBM) -- the branch form for k <= 4, and for k <= 8
+    // while its slots (one per 128-block a row) stay L2-resident (<= 64 MB).  At the images
+    // size the k = 8 branch form (slots 1.2 GB) and the run form (k = 10) are slower than the
+    // full square, so k_pass = 1 is needed to force them.
+    const double sym_slot_bytes = 4.0 * ((ni + 127) / 128) * (double)k * ni;
+    const bool sym_auto = k <= 4 || (k <= kSymBranchMaxK && sym_slot_bytes <= 64.0 * (1 << 20));
+    if (ks == POPCORN_K_FP32 && (opt.k_pass == 1 || (opt.k_pass == 0 && sym_auto)))
         sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin, opt.sym_tile);
     const bool use_sym = sym.ok;
     // With the symmetric pass, K is stored block-packed: the upper triangle of 128 x 128

@@ -78,8 +78,8 @@ struct TcArgs {
     int full;                 // 1: every tile of the square (the GEMM form), each stored once; 0: the
                               // tiles on and above the diagonal (the SYRK form), stored with their
                               // transposes unless K is packed
-    int sw4;                  // packed layout kPackedSw4 (element c of row r at c ^ (r mod 32)); else
-                              // kPackedSw16 (the 128-byte swizzle of the staging chunk)
+    int sw4;                  // packed layout kPackedSw4 (element c of row r at c ^ (r mod 32)): the
+                              // kernel's SW4 instance; else kPackedSw16 (the 128-byte swizzle)
     KernParams kp;
     const float* norms;       // row norms of the represented rows (Gaussian)
     float* kdiag;
@@ -118,6 +118,9 @@ __device__ __forceinline__ float kappa(float b, float ri, float rj, const KernPa
     return expf(kp.neg_gamma_over_sigma2 * d2);
 }
 
+// SW4: the packed XOR-32 staging layout (kPackedSw4) -- a separate instance, since a
+// runtime choice between the two staging stores slowed the epilogue of both about 2.8x
+template <bool SW4>
 __global__ void __launch_bounds__(NTHREADS, 1)
     kbuild_tc_kernel(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_c,
                      const __grid_constant__ CUtensorMap map_kd, const __grid_constant__ CUtensorMap map_kt,
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     epi_bar();
                     float* sd = reinterpret_cast<float*>(smem + a.off_sd + sbuf * STG_BYTES);
                     float* sx = reinterpret_cast<float*>(smem + a.off_st + sbuf * STG_BYTES);
-                    if (a.sw4) {
+                    if constexpr (SW4) {
                         // packed XOR-32 layout: element x of row row_local at x ^ (row_local mod 32)
                         // (the 32 lanes hold 32 consecutive rows: 32 different banks per store)
 #pragma unroll
@@ -441,7 +444,10 @@ constexpr int kSmemBytes = RING_BYTES + 2 * STG_BYTES + BM * 4 + 16 * 8 + 16 + 1
 
 cudaError_t configure_kbuild_tc() {
     encode_fn();
-    return cudaFuncSetAttribute(kbuild_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    const cudaError_t e = cudaFuncSetAttribute(kbuild_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               kSmemBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kbuild_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
 
 cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
@@ -503,7 +509,10 @@ cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernPara
     const int smem = a.off_misc + 16 + 1024;
     if (smem > kSmemBytes) return cudaErrorInvalidConfiguration;
     const int grid = (int)(a.tiles < num_sms ? a.tiles : num_sms);
-    kbuild_tc_kernel<<<grid, NTHREADS, smem, s>>>(mr, mc, mkd, mkt, a);
+    if (a.sw4)
+        kbuild_tc_kernel<true><<<grid, NTHREADS, smem, s>>>(mr, mc, mkd, mkt, a);
+    else
+        kbuild_tc_kernel<false><<<grid, NTHREADS, smem, s>>>(mr, mc, mkd, mkt, a);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

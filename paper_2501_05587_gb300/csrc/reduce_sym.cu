@@ -424,32 +424,38 @@ struct RunArgs {
 };
 
 // Runs of one half-block (64 sorted positions): v(p) = tile[code(p) ^ key] for this lane;
-// each run of one label (its last position is a set bit of `mask`) is summed in four
-// independent partial sums and added once into acc[label * 128].  The run structure is the
-// same for every lane, so the loop over runs and its trip counts are uniform over the warp.
+// at the end of a run of label c (a set bit of `mask`), acc[c * 128] += the run's sum.
+// The run structure is the same for every lane; the end test is taken as a warp vote so
+// that the add into shared memory is a branch the warp takes together (a run ends at
+// about one position in six at k = 10), not predicated code every position pays for.
 __device__ __forceinline__ void sum_runs(const float* __restrict__ tile, const uint16_t* __restrict__ codes,
                                          const uint8_t* __restrict__ labels, unsigned long long mask, uint32_t key,
                                          float* acc) {
-    int q = 0;   // first position of the next run
-    while (mask) {
-        const int end = __ffsll((long long)mask);   // one past the run's last position
-        mask &= mask - 1;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        if ((q & 1) && q < end) {   // align to a pair of codes
-            s0 += tile[(uint32_t)codes[q] ^ key];
-            ++q;
+    float run = 0.f;
+#pragma unroll 1
+    for (int pc = 0; pc < 8; ++pc) {
+        const uint4 cw = *reinterpret_cast<const uint4*>(codes + 8 * pc);   // 8 codes, the same for every lane
+        const uint32_t c32[4] = {cw.x, cw.y, cw.z, cw.w};
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint32_t code = (c32[e >> 1] >> (16 * (e & 1))) & 0xffffu;
+            v[e] = tile[code ^ key];
         }
-        for (; q + 4 <= end; q += 4) {
-            const uint32_t c01 = *reinterpret_cast<const uint32_t*>(codes + q);
-            const uint32_t c23 = *reinterpret_cast<const uint32_t*>(codes + q + 2);
-            s0 += tile[(c01 ^ key) & 0xffffu];
-            s1 += tile[(c01 >> 16) ^ key];
-            s2 += tile[(c23 ^ key) & 0xffffu];
-            s3 += tile[(c23 >> 16) ^ key];
+        const uint32_t mb = (uint32_t)(mask >> (8 * pc)) & 0xffu;
+        if (mb == 0u) {   // no run ends in these 8 positions (uniform)
+            run += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+            continue;
         }
-        for (; q < end; ++q) s0 += tile[(uint32_t)codes[q] ^ key];
-        float* dst = acc + (uint32_t)labels[end - 1] * kB;
-        *dst += (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            run += v[e];
+            if (__any_sync(0xffffffffu, (mb >> e) & 1u)) {
+                float* dst = acc + (uint32_t)labels[8 * pc + e] * kB;
+                *dst += run;
+                run = 0.f;
+            }
+        }
     }
 }
 

@@ -135,8 +135,9 @@ def test_symmetric_pass_is_deterministic(pc, name, sym_tile):
 def test_symmetric_pass_launches_and_fallback(pc):
     """k_pass = "symmetric" runs the stream and the fold (one launch more per pass than
     the full square; the run form one more, its label sort) and is what "auto" picks for
-    an FP32 K with k <= 32; above the cluster bound, or with a half-precision K, both
-    fall back to the full-square pass, with results identical to it."""
+    an FP32 K with small k (here k = 6, slots far below L2); above the cluster bound (32),
+    or with a half-precision K, both fall back to the full-square pass, with results
+    identical to it."""
     P = torch.from_numpy(synth.gaussian_blobs(600, 3, 6, seed=9, box=3.0)).cuda()
     lab = torch.from_numpy(synth.init_labels(600, 6, seed=19)).cuda()
     a = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_pass="symmetric")
@@ -205,7 +206,7 @@ def test_images_tenth_symmetric_pass_is_the_oracle_step(pc, precision, rel):
 
     def fit(t):
         return pc.popcorn_fit(P, wl.k, wl.kernel, L0, max_iter=t, check_convergence=False, history=True,
-                              precision=precision)
+                              precision=precision, k_pass="symmetric")
 
     r1 = fit(1)
     assert r1["info"]["k_pass_used"] == 1
@@ -219,11 +220,13 @@ def test_images_tenth_symmetric_pass_is_the_oracle_step(pc, precision, rel):
     assert rel_err(b["objective"], oracle.objective(Ko, b["labels"].cpu().numpy(), wl.k)) <= rel
 
 
+@pytest.mark.parametrize("k_pass", ["auto", "symmetric"])
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
-def test_full_size_images_symmetric_pass_sampled(pc, precision):
-    """The images workload at full size (n = 70,000, d = 784, k = 10; K block-packed,
-    547 blocks per side, super-tiles of 4 x 4) in the configuration the bench times: one
-    pass from the initial labels.  Sampled rows of E = K V^T (first, last, block edges,
+def test_full_size_images_pass_sampled(pc, precision, k_pass):
+    """The images workload at full size (n = 70,000, d = 784, k = 10), one pass from the
+    initial labels, through the pass the bench times ("auto": the full square, K 19.6 GB)
+    and through the symmetric pass's run form (K block-packed, 547 blocks per side,
+    super-tiles of 4 x 4).  Sampled rows of E = K V^T (first, last, block edges,
     the ragged tail, random rows) against the oracle's K rows; J against the identity
     J = trace K - sum_c sum_{i in L_c} E_ic; and every row's new label against the argmin
     of D = K_ii - 2 E + ||c||^2 rebuilt from E in FP64 (near-ties exempt)."""
@@ -233,8 +236,11 @@ def test_full_size_images_symmetric_pass_sampled(pc, precision):
     L0 = torch.from_numpy(wl.init_labels).cuda()
     E = torch.empty((n, k), dtype=torch.float32, device="cuda")
     r = pc.popcorn_fit(P, k, wl.kernel, L0, max_iter=1, check_convergence=False, history=True,
-                       precision=precision, E_out=E)
-    assert r["info"]["k_pass_used"] == 1 and r["info"]["schedule"][0] == 4
+                       precision=precision, E_out=E, k_pass=k_pass)
+    if k_pass == "symmetric":
+        assert r["info"]["k_pass_used"] == 1 and r["info"]["schedule"][0] == 4
+    else:
+        assert r["info"]["k_pass_used"] == 2
     Eg = E.cpu().numpy().astype(np.float64)
     lab = wl.init_labels.astype(np.int64)
     m = np.bincount(lab, minlength=k).astype(np.float64)
@@ -260,7 +266,10 @@ def test_run_form_launches_its_label_sort(pc):
     """The run form adds one launch per pass (the per-pass sort of every block's labels)."""
     P = torch.from_numpy(synth.gaussian_blobs(900, 3, 12, seed=4, box=3.0)).cuda()
     lab = torch.from_numpy(synth.init_labels(900, 12, seed=14)).cuda()
-    a = pc.popcorn_fit(P, 12, _gauss(1.0), lab, max_iter=4, check_convergence=False, timing=True)
+    a = pc.popcorn_fit(P, 12, _gauss(1.0), lab, max_iter=4, check_convergence=False, timing=True,
+                       k_pass="symmetric")
     b = pc.popcorn_fit(P, 12, _gauss(1.0), lab, max_iter=4, check_convergence=False, timing=True, k_pass="full")
+    auto = pc.popcorn_fit(P, 12, _gauss(1.0), lab, max_iter=4, check_convergence=False, timing=True)
+    assert auto["info"]["k_pass_used"] == 2          # k > 8: the full square unless forced
     assert a["info"]["k_pass_used"] == 1 and b["info"]["k_pass_used"] == 2
     assert a["info"]["kernel_launches"] == b["info"]["kernel_launches"] + 2 * (a["iterations"] + 1)
