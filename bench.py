@@ -205,7 +205,9 @@ def kbuild_roofline(wl, precision, kb_ms, pk):
     flops = tiles * 2.0 * 128 * 128 * 2.0 * depth
     ach = flops / sec / 1e12
     return {"kernel": "kbuild_tc_kernel", "bound": "tensor", "achieved": ach, "peak": pk["bf16"], "unit": "TFLOP/s",
-            "frac": ach / pk["bf16"], "traffic": None, "peak_source": pk["source"] + " bf16 burst",
+            "frac": ach / pk["bf16"],
+            "traffic": (recorded_traffic("kbuild_tc_kernel", "kbuild_tc.cu", wl.name) if precision == "bf16x3" else None),
+            "peak_source": pk["source"] + " bf16 burst",
             "executed_mma_flops_per_launch": flops, "avg_launch_ms": kb_ms}
 
 
