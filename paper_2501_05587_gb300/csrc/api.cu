@@ -192,7 +192,14 @@ popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, co
                                    int* err, int num_sms, cudaStream_t s, int* launches, int packed = 0,
                                    int full = 0) {
     if (precision == POPCORN_FP32) {
-        POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, k_storage, kdiag, s, launches, packed, full));
+        float* rn = nullptr;
+        unsigned* maxr = nullptr;
+        if (kp.kind == POPCORN_GAUSSIAN && ws) {
+            POPCORN_TRY(ws->alloc(&rn, (size_t)n, "row norms"));
+            POPCORN_TRY(ws->alloc(&maxr, 1, "largest row norm"));
+        }
+        POPCORN_CUDA(launch_kbuild_simt(P, n, d, ldp, kp, K, ldk, k_storage, kdiag, s, launches, packed, full, rn,
+                                        maxr));
         return POPCORN_OK;
     }
     if (k_storage != POPCORN_K_FP32)

@@ -5,10 +5,18 @@
 // paper forms B with GEMM or SYRK plus a triangle copy and a separate
 // transform pass (Sec. 4.2); here one kernel computes each upper-triangle
 // 128 x 128 tile once, applies kappa in registers and stores the tile and its
-// transpose, so B never exists in memory and no copy pass runs.  In this FP32
-// form the Gaussian squared distance is summed from coordinate differences,
-// which keeps full relative accuracy for near-duplicate points (the norm
-// expansion of Eq. 12 cancels there).
+// transpose, so B never exists in memory and no copy pass runs.
+//
+// The Gaussian squared distance takes one of two forms, decided on the device
+// per launch from the largest row norm.  The norm expansion of Eq. 12,
+// r_i + r_j - 2 p_i.p_j, costs one multiply-add per pair and coordinate; its
+// rounding error in a kernel value is about 4 sqrt(d) u max_i r_i gamma /
+// sigma^2 (u = 2^-24: the dot product's and the norms' roundings, the
+// cancellation bounded by the norms), and it is used when that stays below
+// 1e-6, the FP32 parity bar on K.  Otherwise (points far from the origin
+// relative to sigma, where the expansion cancels) the distance is summed from
+// coordinate differences, a subtract and a multiply-add per pair and
+// coordinate, which keeps full relative accuracy for near-duplicate points.
 #include "popcorn_internal.cuh"
 
 #include <cuda_bf16.h>
@@ -22,6 +30,9 @@ constexpr int TILE = 128;
 constexpr int KC = 16;          // depth of one shared-memory slice (double-buffered)
 constexpr int LDS = TILE + 4;   // padded row
 
+// Internal kernel kind: the Gaussian with its distance from the norm expansion (Eq. 12).
+constexpr int kGaussExpand = 3;
+
 template <int KIND>
 __device__ __forceinline__ float apply_kernel(float v, const KernParams& kp) {
     if (KIND == POPCORN_LINEAR) return v;
@@ -32,6 +43,24 @@ __device__ __forceinline__ float apply_kernel(float v, const KernParams& kp) {
         return r;
     }
     return expf(kp.neg_gamma_over_sigma2 * v);   // v = ||p_i - p_j||^2
+}
+
+// Row norms r_i = sum_l p_il^2 (one warp a row, a fixed reduction order) and the largest
+// of them (positive floats order like their bit patterns).
+__global__ void __launch_bounds__(256) row_norms_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
+                                                        float* __restrict__ rn, unsigned* __restrict__ maxr) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float* p = P + (int64_t)row * ldp;
+    float s = 0.f;
+    for (int l = lane; l < d; l += 32) s = fmaf(p[l], p[l], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        rn[row] = s;
+        atomicMax(maxr, __float_as_uint(s));
+    }
 }
 
 // Stored element type of K and its 4-wide packed store.
@@ -82,7 +111,7 @@ template <int KIND, typename TK = float, bool ONE_SLICE = false, int PACKED = 0>
 __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, int d, int64_t ldp,
                                             const KernParams& kp, TK* __restrict__ K, int64_t ldk,
                                             float* __restrict__ kdiag, int T, long long tile, TileSmem& sm,
-                                            int full = 0) {
+                                            int full = 0, const float* __restrict__ rn = nullptr) {
     auto& As = sm.As;
     auto& Bs = sm.Bs;
     int bi, bj;
@@ -155,7 +184,7 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
             for (int x = 0; x < 8; ++x)
 #pragma unroll
                 for (int y = 0; y < 8; ++y) {
-                    if (KIND == POPCORN_GAUSSIAN) {
+                    if constexpr (KIND == POPCORN_GAUSSIAN) {
                         float t = a[x] - b[y];
                         acc[x][y] = fmaf(t, t, acc[x][y]);
                     } else {
@@ -174,10 +203,27 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         buf ^= 1;
     }
     // epilogue: kappa, diagonal, store tile and (off-diagonal tiles) its transpose
+    if constexpr (KIND == kGaussExpand) {
+        // d2 = r_i + r_j - 2 b (Eq. 12), clamped at 0; rows / columns past n take 0
+        float ri[8], rj[8];
 #pragma unroll
-    for (int x = 0; x < 8; ++x)
+        for (int x = 0; x < 8; ++x) {
+            const int r = row0 + ty * 4 + (x & 3) + 64 * (x >> 2);
+            const int c = col0 + tx * 4 + (x & 3) + 64 * (x >> 2);
+            ri[x] = r < n ? rn[r] : 0.f;
+            rj[x] = c < n ? rn[c] : 0.f;
+        }
 #pragma unroll
-        for (int y = 0; y < 8; ++y) acc[x][y] = apply_kernel<KIND>(acc[x][y], kp);
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y)
+                acc[x][y] = apply_kernel<POPCORN_GAUSSIAN>(fmaxf(fmaf(-2.f, acc[x][y], ri[x] + rj[y]), 0.f), kp);
+    } else {
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) acc[x][y] = apply_kernel<KIND>(acc[x][y], kp);
+    }
 
     if (bi == bj) {
 #pragma unroll
@@ -187,7 +233,7 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
             for (int y = 0; y < 8; ++y) {
                 int c = col0 + tx * 4 + (y & 3) + 64 * (y >> 2);
                 if (r == c && r < n) {
-                    if (KIND == POPCORN_GAUSSIAN) acc[x][y] = 1.0f;
+                    if (KIND == POPCORN_GAUSSIAN || KIND == kGaussExpand) acc[x][y] = 1.0f;
                     kdiag[r] = KStore<TK>::round(acc[x][y]);
                 }
             }
@@ -259,12 +305,20 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
     }
 }
 
+// The Gaussian instances choose the distance form here, uniformly for the launch: the norm
+// expansion when expand_coef * max_i r_i <= 1e-6 (rn / maxr from row_norms_kernel).
 template <int KIND, typename TK, int PACKED>
 __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
                                                           KernParams kp, TK* __restrict__ K, int64_t ldk,
-                                                          float* __restrict__ kdiag, int T, int full) {
+                                                          float* __restrict__ kdiag, int T, int full,
+                                                          const float* __restrict__ rn, const unsigned* maxr,
+                                                          float expand_coef) {
     __shared__ __align__(16) TileSmem sm;
-    kbuild_tile<KIND, TK, false, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm, full);
+    if (KIND == POPCORN_GAUSSIAN && rn && __uint_as_float(*maxr) * expand_coef <= 1e-6f)
+        kbuild_tile<kGaussExpand, TK, false, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm,
+                                                     full, rn);
+    else
+        kbuild_tile<KIND, TK, false, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm, full);
 }
 
 // d <= KC: the depth loop is one slice, so no next slice is held in registers;
@@ -274,15 +328,33 @@ template <int KIND, typename TK, int PACKED>
 __global__ void __launch_bounds__(256, 2) kbuild_simt_small_kernel(const float* __restrict__ P, int n, int d,
                                                                    int64_t ldp, KernParams kp, TK* __restrict__ K,
                                                                    int64_t ldk, float* __restrict__ kdiag, int T,
-                                                                   int full) {
+                                                                   int full, const float* __restrict__ rn,
+                                                                   const unsigned* maxr, float expand_coef) {
     __shared__ __align__(16) TileSmem sm;
-    kbuild_tile<KIND, TK, true, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm, full);
+    if (KIND == POPCORN_GAUSSIAN && rn && __uint_as_float(*maxr) * expand_coef <= 1e-6f)
+        kbuild_tile<kGaussExpand, TK, true, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm,
+                                                    full, rn);
+    else
+        kbuild_tile<KIND, TK, true, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm, full);
 }
 
 template <typename TK, int PACKED>
 cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernParams kp, TK* K, int64_t ldk,
-                              float* kdiag, cudaStream_t s, int full = 0) {
+                              float* kdiag, cudaStream_t s, int full, float* rn, unsigned* maxr, int* launches) {
     const int T = (n + TILE - 1) / TILE;
+    // Gaussian: row norms and their maximum first (the build then picks the distance form);
+    // 4 sqrt(d) u gamma / sigma^2 bounds the expansion's error per unit of max_i r_i
+    float expand_coef = 0.f;
+    if (kp.kind == POPCORN_GAUSSIAN && rn && maxr) {
+        cudaError_t e = cudaMemsetAsync(maxr, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        row_norms_kernel<<<(unsigned)(((int64_t)n * 32 + 255) / 256), 256, 0, s>>>(P, n, d, ldp, rn, maxr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (launches) ++*launches;
+        expand_coef = (float)(4.0 * sqrt((double)d) * ldexp(1.0, -24) * fabs((double)kp.neg_gamma_over_sigma2));
+    } else {
+        rn = nullptr;
+    }
     const long long tiles = full ? (long long)T * T : (long long)T * (T + 1) / 2;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     dim3 grid((unsigned)tiles), block(256);
@@ -290,29 +362,29 @@ cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernPar
         switch (kp.kind) {
             case POPCORN_LINEAR:
                 kbuild_simt_small_kernel<POPCORN_LINEAR, TK, PACKED>
-                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
+                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
                 break;
             case POPCORN_POLYNOMIAL:
                 kbuild_simt_small_kernel<POPCORN_POLYNOMIAL, TK, PACKED>
-                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
+                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
                 break;
             default:
                 kbuild_simt_small_kernel<POPCORN_GAUSSIAN, TK, PACKED>
-                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
+                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
                 break;
         }
         return cudaGetLastError();
     }
     switch (kp.kind) {
         case POPCORN_LINEAR:
-            kbuild_simt_kernel<POPCORN_LINEAR, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
+            kbuild_simt_kernel<POPCORN_LINEAR, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
             break;
         case POPCORN_POLYNOMIAL:
             kbuild_simt_kernel<POPCORN_POLYNOMIAL, TK, PACKED>
-                <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
+                <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
             break;
         default:
-            kbuild_simt_kernel<POPCORN_GAUSSIAN, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full);
+            kbuild_simt_kernel<POPCORN_GAUSSIAN, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
             break;
     }
     return cudaGetLastError();
@@ -351,19 +423,25 @@ cudaError_t launch_batched_kbuild_simt(const BatchInst* dI, const BatchPlan& bp,
 }
 
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp, void* K, int64_t ldk,
-                               int k_storage, float* kdiag, cudaStream_t s, int* launches, int packed, int full) {
+                               int k_storage, float* kdiag, cudaStream_t s, int* launches, int packed, int full,
+                               float* rn, unsigned* maxr) {
     if (launches) ++*launches;
     if (packed) {
         if (k_storage != POPCORN_K_FP32) return cudaErrorInvalidValue;
         if (packed == kPackedSw4)
-            return launch_simt_typed<float, kPackedSw4>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
-        return launch_simt_typed<float, kPackedSw16>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s);
+            return launch_simt_typed<float, kPackedSw4>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s, 0,
+                                                        rn, maxr, launches);
+        return launch_simt_typed<float, kPackedSw16>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s, 0, rn,
+                                                     maxr, launches);
     }
     if (k_storage == POPCORN_K_FP16)
-        return launch_simt_typed<__half, 0>(P, n, d, ldp, kp, static_cast<__half*>(K), ldk, kdiag, s);
+        return launch_simt_typed<__half, 0>(P, n, d, ldp, kp, static_cast<__half*>(K), ldk, kdiag, s, 0, rn, maxr,
+                                            launches);
     if (k_storage == POPCORN_K_BF16)
-        return launch_simt_typed<__nv_bfloat16, 0>(P, n, d, ldp, kp, static_cast<__nv_bfloat16*>(K), ldk, kdiag, s);
-    return launch_simt_typed<float, 0>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s, full);
+        return launch_simt_typed<__nv_bfloat16, 0>(P, n, d, ldp, kp, static_cast<__nv_bfloat16*>(K), ldk, kdiag, s, 0,
+                                                   rn, maxr, launches);
+    return launch_simt_typed<float, 0>(P, n, d, ldp, kp, static_cast<float*>(K), ldk, kdiag, s, full, rn, maxr,
+                                       launches);
 }
 
 }  // namespace popcorn

@@ -162,9 +162,12 @@ constexpr int kPackedSw16 = 1, kPackedSw4 = 2;
 // triangle in that layout, read by the symmetric pass (ldk is then unused).
 // full = 1 (full square only): every tile of the square computed and stored once (the
 // GEMM form) instead of the upper-triangle tiles stored with their transposes (SYRK form).
+// rn (n floats) and maxr (one word), both device workspace: for a Gaussian kernel the row
+// norms, from which the build decides on the device whether the norm expansion is accurate
+// enough; null keeps the coordinate-difference form.
 cudaError_t launch_kbuild_simt(const float* P, int n, int d, int64_t ldp, KernParams kp,
                                void* K, int64_t ldk, int k_storage, float* kdiag, cudaStream_t s, int* launches,
-                               int packed = 0, int full = 0);
+                               int packed = 0, int full = 0, float* rn = nullptr, unsigned* maxr = nullptr);
 
 // ---- K build on tensor cores (kbuild_tc.cu) ---------------------------------
 // Workspace bytes for the BF16 operand copies and row norms.

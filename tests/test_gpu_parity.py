@@ -367,3 +367,22 @@ def test_kernel_matrix_schedules_agree(pc, precision, kern):
         assert float((Ks - Kf).abs().max()) <= 1e-5 * scale
     assert torch.equal(Kt, Ks) or torch.equal(Kt, Kf)
     assert torch.equal(Ka, Kt)                       # auto takes the cached tuned choice
+
+
+@pytest.mark.parametrize("n", [700, 1500])
+def test_kernel_matrix_gaussian_norm_expansion(pc, n):
+    """Images-shaped points with the Gaussian sigma = 28: the largest row norm is about 67, so
+    the norm expansion's error bound 4 sqrt(d) u max_i r_i / sigma^2 (~6e-7) is below 1e-6 and
+    the FP32 build forms distances by Eq. 12.  K still matches the oracle's coordinate-
+    difference K within 1e-6 absolute (the FP32 Gaussian bar), is symmetric, and has diag 1;
+    a fit's objective matches the oracle's to 1e-6."""
+    wl = synth.workload("images", scale=n / 70000)
+    P = _dev(wl.P)
+    K, kd = pc.popcorn_kernel_matrix(P, wl.kernel)
+    torch.cuda.synchronize()
+    Kg = K.cpu().numpy().astype(np.float64)
+    Ko = oracle.kernel_matrix(wl.P, wl.kernel)
+    assert np.max(np.abs(Kg - Ko)) <= 1e-6
+    assert np.array_equal(Kg, Kg.T) and np.all(np.diag(Kg) == 1.0)
+    r = pc.popcorn_fit(P, wl.k, wl.kernel, _dev(wl.init_labels), max_iter=5, check_convergence=False)
+    assert rel_err(r["objective"], oracle.objective(Ko, r["labels"].cpu().numpy(), wl.k)) <= FP32_OBJ_REL
