@@ -188,7 +188,17 @@ def kbuild_roofline(wl, precision, kb_ms, pk):
     n, d = float(wl.n), float(wl.d)
     sec = kb_ms / 1e3
     if precision == "fp32":
-        per = 2.0 if wl.kernel["kind"] == "gaussian" else 1.0
+        # the Gaussian's distance form, decided as the library decides it: the norm expansion
+        # (one multiply-add a coordinate) when 4 sqrt(d) u max_i r_i gamma / sigma^2 <= 1e-6,
+        # else coordinate differences (a subtract and a multiply-add)
+        form = None
+        per = 1.0
+        if wl.kernel["kind"] == "gaussian":
+            maxr = float((wl.P.astype(np.float64) ** 2).sum(axis=1).max())
+            c = float(wl.kernel.get("gamma", 1.0)) / float(wl.kernel["sigma"]) ** 2
+            expand = 4.0 * np.sqrt(d) * 2.0 ** -24 * maxr * c <= 1e-6
+            form = "norm expansion (Eq. 12)" if expand else "coordinate differences"
+            per = 1.0 if expand else 2.0
         ops = per * n * (n + 1) / 2 * d
         peak = FP32_LANES_PER_CLK_SM * GB300_SMS * pk["sm_mhz"] * 1e6 / 1e12
         ach = ops / sec / 1e12
@@ -196,7 +206,7 @@ def kbuild_roofline(wl, precision, kb_ms, pk):
                 "frac": ach / peak, "traffic": recorded_traffic("kbuild_simt_kernel", "kbuild_simt.cu", wl.name),
                 "peak_source": f"{FP32_LANES_PER_CLK_SM} FP32 lanes/clk/SM x {GB300_SMS} SMs x "
                                f"{pk['sm_mhz']:.0f} MHz (unit counts and clock)",
-                "algorithmic_lane_ops_per_launch": ops, "avg_launch_ms": kb_ms}
+                "algorithmic_lane_ops_per_launch": ops, "avg_launch_ms": kb_ms, "distance_form": form}
     T = (wl.n + 127) // 128
     T2 = (T + 1) // 2
     tiles = T2 * T - T2 * (T2 - 1)
