@@ -23,6 +23,8 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <type_traits>
+
 namespace popcorn {
 namespace {
 
@@ -95,10 +97,14 @@ template <> struct KStore<__nv_bfloat16> {
     __device__ static void put1(__nv_bfloat16* p, float a) { *p = __float2bfloat16_rn(a); }
 };
 
-// One upper-triangle tile (number `tile`) of K: 256 threads, 8 x 8 outputs each.
-// The depth loop runs over KC-wide slices of the two 128-row operand blocks,
-// double-buffered in shared memory: while a slice is consumed, the next one is
-// already in flight into registers (float4 loads when rows are 16-byte aligned).
+// One upper-triangle tile (number `tile`) of K: RPT x 8 outputs a thread, 256 threads
+// (RPT = 8) or 128 (RPT = 16).  The depth loop runs over KC-wide slices of the two
+// 128-row operand blocks, double-buffered in shared memory: while a slice is consumed,
+// the next one is already in flight into registers (float4 loads when rows are 16-byte
+// aligned).  A thread reads RPT / 4 + 2 float4 a depth step for 8 RPT multiply-adds:
+// RPT = 16 halves the shared-memory traffic a multiply-add, which is what bounds the
+// dot-product kinds (one multiply-add a pair and coordinate) at RPT = 8; the
+// coordinate-difference Gaussian (two operations) keeps RPT = 8.
 // kdiag receives the stored (rounded) diagonal so that diag K and K agree.
 struct TileSmem {
     float As[2][KC][LDS];
@@ -107,7 +113,7 @@ struct TileSmem {
 
 // PACKED: 0 = row-major full square (tile and transpose); kPackedSw16 / kPackedSw4 = the
 // block-packed upper triangle in the tile layout of that name (popcorn_internal.cuh).
-template <int KIND, typename TK = float, bool ONE_SLICE = false, int PACKED = 0>
+template <int KIND, typename TK = float, bool ONE_SLICE = false, int PACKED = 0, int RPT = 8>
 __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, int d, int64_t ldp,
                                             const KernParams& kp, TK* __restrict__ K, int64_t ldk,
                                             float* __restrict__ kdiag, int T, long long tile, TileSmem& sm,
@@ -121,14 +127,18 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
     } else {
         tri_coords(tile, T, &bi, &bj);
     }
+    static_assert(RPT == 8 || RPT == 16, "8 or 16 rows a thread");
+    constexpr int NT = RPT == 8 ? 256 : 128;       // threads
+    constexpr int RS = TILE / (RPT / 4);           // rows between a thread's groups of 4 rows
+    constexpr int NF = (KC / 4) / (NT / 128);      // float4 a thread fetches per operand and slice
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int row0 = bi * TILE, col0 = bj * TILE;
     const bool vec = (ldp & 3) == 0 && ((uintptr_t)P & 15) == 0;
 
-    // slice fill: thread tid carries float4 f = (tid >> 7) + 2 rep of row tid & 127, rep = 0, 1
+    // slice fill: thread tid carries float4 f = (tid >> 7) + (NT / 128) rep of row tid & 127
     const int fr = tid & 127;
     auto fetch = [&](int base, int l0, int rep) -> float4 {
-        const int r = base + fr, gl = l0 + 4 * ((tid >> 7) + 2 * rep);
+        const int r = base + fr, gl = l0 + 4 * ((tid >> 7) + (NT / 128) * rep);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (r < n) {
             const float* p = P + (int64_t)r * ldp + gl;
@@ -144,44 +154,57 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         return v;
     };
     auto put = [&](float (*S)[LDS], int rep, const float4& v) {
-        const int l = 4 * ((tid >> 7) + 2 * rep);
+        const int l = 4 * ((tid >> 7) + (NT / 128) * rep);
         S[l][fr] = v.x;
         S[l + 1][fr] = v.y;
         S[l + 2][fr] = v.z;
         S[l + 3][fr] = v.w;
     };
 
-    float acc[8][8];
+    float acc[RPT][8];
 #pragma unroll
-    for (int x = 0; x < 8; ++x)
+    for (int x = 0; x < RPT; ++x)
 #pragma unroll
         for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
 
-    float4 na0 = fetch(row0, 0, 0), na1 = fetch(row0, 0, 1), nb0 = fetch(col0, 0, 0), nb1 = fetch(col0, 0, 1);
-    put(As[0], 0, na0);
-    put(As[0], 1, na1);
-    put(Bs[0], 0, nb0);
-    put(Bs[0], 1, nb1);
+    float4 na[NF], nb[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) {
+        na[q] = fetch(row0, 0, q);
+        nb[q] = fetch(col0, 0, q);
+    }
+#pragma unroll
+    for (int q = 0; q < NF; ++q) {
+        put(As[0], q, na[q]);
+        put(Bs[0], q, nb[q]);
+    }
     __syncthreads();
     int buf = 0;
     for (int l0 = 0; l0 < d; l0 += KC) {
         const bool more = !ONE_SLICE && l0 + KC < d;
         if (more) {
-            na0 = fetch(row0, l0 + KC, 0);
-            na1 = fetch(row0, l0 + KC, 1);
-            nb0 = fetch(col0, l0 + KC, 0);
-            nb1 = fetch(col0, l0 + KC, 1);
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                na[q] = fetch(row0, l0 + KC, q);
+                nb[q] = fetch(col0, l0 + KC, q);
+            }
         }
 #pragma unroll
         for (int l = 0; l < KC; ++l) {
-            float4 a0 = *reinterpret_cast<const float4*>(&As[buf][l][ty * 4]);
-            float4 a1 = *reinterpret_cast<const float4*>(&As[buf][l][64 + ty * 4]);
-            float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][l][tx * 4]);
-            float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][l][64 + tx * 4]);
-            float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            float a[RPT], b[8];
 #pragma unroll
-            for (int x = 0; x < 8; ++x)
+            for (int m = 0; m < RPT / 4; ++m) {
+                const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][l][RS * m + ty * 4]);
+                a[4 * m] = a4.x;
+                a[4 * m + 1] = a4.y;
+                a[4 * m + 2] = a4.z;
+                a[4 * m + 3] = a4.w;
+            }
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][l][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][l][64 + tx * 4]);
+            b[0] = b0.x, b[1] = b0.y, b[2] = b0.z, b[3] = b0.w, b[4] = b1.x, b[5] = b1.y, b[6] = b1.z, b[7] = b1.w;
+#pragma unroll
+            for (int x = 0; x < RPT; ++x)
 #pragma unroll
                 for (int y = 0; y < 8; ++y) {
                     if constexpr (KIND == POPCORN_GAUSSIAN) {
@@ -194,10 +217,11 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         }
         if (more) {
             // the other buffer was last read before the previous barrier
-            put(As[buf ^ 1], 0, na0);
-            put(As[buf ^ 1], 1, na1);
-            put(Bs[buf ^ 1], 0, nb0);
-            put(Bs[buf ^ 1], 1, nb1);
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                put(As[buf ^ 1], q, na[q]);
+                put(Bs[buf ^ 1], q, nb[q]);
+            }
         }
         __syncthreads();
         buf ^= 1;
@@ -205,30 +229,33 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
     // epilogue: kappa, diagonal, store tile and (off-diagonal tiles) its transpose
     if constexpr (KIND == kGaussExpand) {
         // d2 = r_i + r_j - 2 b (Eq. 12), clamped at 0; rows / columns past n take 0
-        float ri[8], rj[8];
+        float ri[RPT], rj[8];
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            const int r = row0 + ty * 4 + (x & 3) + 64 * (x >> 2);
-            const int c = col0 + tx * 4 + (x & 3) + 64 * (x >> 2);
+        for (int x = 0; x < RPT; ++x) {
+            const int r = row0 + ty * 4 + (x & 3) + RS * (x >> 2);
             ri[x] = r < n ? rn[r] : 0.f;
-            rj[x] = c < n ? rn[c] : 0.f;
         }
 #pragma unroll
-        for (int x = 0; x < 8; ++x)
+        for (int y = 0; y < 8; ++y) {
+            const int c = col0 + tx * 4 + (y & 3) + 64 * (y >> 2);
+            rj[y] = c < n ? rn[c] : 0.f;
+        }
+#pragma unroll
+        for (int x = 0; x < RPT; ++x)
 #pragma unroll
             for (int y = 0; y < 8; ++y)
                 acc[x][y] = apply_kernel<POPCORN_GAUSSIAN>(fmaxf(fmaf(-2.f, acc[x][y], ri[x] + rj[y]), 0.f), kp);
     } else {
 #pragma unroll
-        for (int x = 0; x < 8; ++x)
+        for (int x = 0; x < RPT; ++x)
 #pragma unroll
             for (int y = 0; y < 8; ++y) acc[x][y] = apply_kernel<KIND>(acc[x][y], kp);
     }
 
     if (bi == bj) {
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            int r = row0 + ty * 4 + (x & 3) + 64 * (x >> 2);
+        for (int x = 0; x < RPT; ++x) {
+            int r = row0 + ty * 4 + (x & 3) + RS * (x >> 2);
 #pragma unroll
             for (int y = 0; y < 8; ++y) {
                 int c = col0 + tx * 4 + (y & 3) + 64 * (y >> 2);
@@ -253,8 +280,8 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         static_assert(sizeof(TK) == 4, "packed storage holds FP32 K");
         float* B = reinterpret_cast<float*>(K) + (size_t)tile * (TILE * TILE);
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            const int rl = ty * 4 + (x & 3) + 64 * (x >> 2);
+        for (int x = 0; x < RPT; ++x) {
+            const int rl = ty * 4 + (x & 3) + RS * (x >> 2);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int cl = 64 * h + tx * 4;
@@ -273,8 +300,8 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         return;
     }
 #pragma unroll
-    for (int x = 0; x < 8; ++x) {
-        int r = row0 + ty * 4 + (x & 3) + 64 * (x >> 2);
+    for (int x = 0; x < RPT; ++x) {
+        int r = row0 + ty * 4 + (x & 3) + RS * (x >> 2);
         if (r >= n) continue;
         TK* Kr = K + (int64_t)r * ldk;
 #pragma unroll
@@ -297,8 +324,8 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
             if (c >= n) continue;
             TK* Kc = K + (int64_t)c * ldk;
 #pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                int r = row0 + 64 * g + ty * 4;   // row0 tiles are full (bi < bj => rows < n)
+            for (int g = 0; g < RPT / 4; ++g) {
+                int r = row0 + RS * g + ty * 4;   // row0 tiles are full (bi < bj => rows < n)
                 KStore<TK>::put4(Kc + r, acc[4 * g][y], acc[4 * g + 1][y], acc[4 * g + 2][y], acc[4 * g + 3][y]);
             }
         }
@@ -306,19 +333,42 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
 }
 
 // The Gaussian instances choose the distance form here, uniformly for the launch: the norm
-// expansion when expand_coef * max_i r_i <= 1e-6 (rn / maxr from row_norms_kernel).
+// expansion when expand_coef * max_i r_i <= 1e-6 (rn / maxr from row_norms_kernel).  With
+// dot_expands set, a separate kbuild_dot_kernel launch takes the expansion and this one
+// returns at once when it applies.
+__device__ __forceinline__ bool expansion_applies(const float* rn, const unsigned* maxr, float expand_coef) {
+    return rn && __uint_as_float(*maxr) * expand_coef <= 1e-6f;
+}
+
 template <int KIND, typename TK, int PACKED>
 __global__ void __launch_bounds__(256) kbuild_simt_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
                                                           KernParams kp, TK* __restrict__ K, int64_t ldk,
                                                           float* __restrict__ kdiag, int T, int full,
                                                           const float* __restrict__ rn, const unsigned* maxr,
-                                                          float expand_coef) {
+                                                          float expand_coef, int dot_expands) {
     __shared__ __align__(16) TileSmem sm;
-    if (KIND == POPCORN_GAUSSIAN && rn && __uint_as_float(*maxr) * expand_coef <= 1e-6f)
+    const bool expand = KIND == POPCORN_GAUSSIAN && expansion_applies(rn, maxr, expand_coef);
+    if (expand && dot_expands) return;
+    if (expand)
         kbuild_tile<kGaussExpand, TK, false, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm,
                                                      full, rn);
     else
         kbuild_tile<KIND, TK, false, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm, full);
+}
+
+// The dot-product kinds (linear, polynomial, the Gaussian by the norm expansion) on FP32 K:
+// 16 x 8 outputs a thread, 128 threads.  The Gaussian instance returns at once when the
+// expansion does not apply (the 256-thread kernel then forms coordinate differences).
+template <int KIND, int PACKED>
+__global__ void __launch_bounds__(128, 2) kbuild_dot_kernel(const float* __restrict__ P, int n, int d, int64_t ldp,
+                                                            KernParams kp, float* __restrict__ K, int64_t ldk,
+                                                            float* __restrict__ kdiag, int T, int full,
+                                                            const float* __restrict__ rn, const unsigned* maxr,
+                                                            float expand_coef) {
+    __shared__ __align__(16) TileSmem sm;
+    if (KIND == kGaussExpand && !expansion_applies(rn, maxr, expand_coef)) return;
+    kbuild_tile<KIND, float, false, PACKED, 16>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm, full,
+                                                rn);
 }
 
 // d <= KC: the depth loop is one slice, so no next slice is held in registers;
@@ -331,7 +381,7 @@ __global__ void __launch_bounds__(256, 2) kbuild_simt_small_kernel(const float* 
                                                                    int full, const float* __restrict__ rn,
                                                                    const unsigned* maxr, float expand_coef) {
     __shared__ __align__(16) TileSmem sm;
-    if (KIND == POPCORN_GAUSSIAN && rn && __uint_as_float(*maxr) * expand_coef <= 1e-6f)
+    if (KIND == POPCORN_GAUSSIAN && expansion_applies(rn, maxr, expand_coef))
         kbuild_tile<kGaussExpand, TK, true, PACKED>(P, n, d, ldp, kp, K, ldk, kdiag, T, (long long)blockIdx.x, sm,
                                                     full, rn);
     else
@@ -375,16 +425,44 @@ cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernPar
         }
         return cudaGetLastError();
     }
+    if constexpr (std::is_same<TK, float>::value) {
+        // FP32 K, d > KC: the dot-product kinds on the 16 x 8 kernel; the Gaussian launches both
+        // forms, and the one whose distance form does not apply returns at once
+        dim3 dblock(128);
+        switch (kp.kind) {
+            case POPCORN_LINEAR:
+                kbuild_dot_kernel<POPCORN_LINEAR, PACKED>
+                    <<<grid, dblock, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
+                return cudaGetLastError();
+            case POPCORN_POLYNOMIAL:
+                kbuild_dot_kernel<POPCORN_POLYNOMIAL, PACKED>
+                    <<<grid, dblock, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
+                return cudaGetLastError();
+            default:
+                if (rn) {
+                    kbuild_dot_kernel<kGaussExpand, PACKED>
+                        <<<grid, dblock, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
+                    cudaError_t e = cudaGetLastError();
+                    if (e != cudaSuccess) return e;
+                    if (launches) ++*launches;
+                }
+                kbuild_simt_kernel<POPCORN_GAUSSIAN, TK, PACKED>
+                    <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef, 1);
+                return cudaGetLastError();
+        }
+    }
     switch (kp.kind) {
         case POPCORN_LINEAR:
-            kbuild_simt_kernel<POPCORN_LINEAR, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
+            kbuild_simt_kernel<POPCORN_LINEAR, TK, PACKED>
+                <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef, 0);
             break;
         case POPCORN_POLYNOMIAL:
             kbuild_simt_kernel<POPCORN_POLYNOMIAL, TK, PACKED>
-                <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
+                <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef, 0);
             break;
         default:
-            kbuild_simt_kernel<POPCORN_GAUSSIAN, TK, PACKED><<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef);
+            kbuild_simt_kernel<POPCORN_GAUSSIAN, TK, PACKED>
+                <<<grid, block, 0, s>>>(P, n, d, ldp, kp, K, ldk, kdiag, T, full, rn, maxr, expand_coef, 0);
             break;
     }
     return cudaGetLastError();
