@@ -89,7 +89,7 @@ def parse():
     ap.add_argument("--k-pass", default="auto", choices=["auto", "full", "symmetric"],
                     help="how a pass reads a stored FP32 K: the library's choice, the full square, or the blocks "
                          "on and above the diagonal (row and column sums, then a fold)")
-    ap.add_argument("--sym-tile", type=int, default=0, choices=[0, 1, 2, 4],
+    ap.add_argument("--sym-tile", type=int, default=0, choices=list(range(9)),
                     help="super-tile edge of the symmetric pass (0: the library's choice)")
     ap.add_argument("--sweep", default=None, choices=["kbuild"],
                     help="kbuild: the K build's GEMM-versus-SYRK sweep (n in {1e4, 5e4} x d in {1e2 .. 1e5}): the "
@@ -138,15 +138,19 @@ def recorded_traffic(kernel: str, src_file: str, workload: str):
         return None
 
 
-def sym_bytes(n: int, k: int, nslots: int):
+def sym_bytes(n: int, k: int, nslots: int, sorted_form: bool = True):
     """Bytes of one symmetric stream launch: the scope table's algorithmic figure for triangular
     storage (2 n (n + 1) + n: the unique entries of K once, plus the labels), and what the
-    kernel moves besides: the 128-blocks of the packed triangle, the slot stores."""
+    kernel moves besides: the 128-blocks of the packed triangle, the slot stores, and per
+    block its labels (branch form) or its column and row lists (sorted form: a 128-byte
+    header and 4 bytes an entry, 128 + 3k padded to 4, plus 4; both from L2)."""
     T = (n + 127) // 128
+    blocks = T * (T + 1) / 2
+    lists = 2.0 * (128 + 4 * (((128 + 3 * k + 3) // 4) * 4 + 4))
     return {"algorithmic": 2.0 * n * (n + 1) + n,
-            "packed_tiles": 65536.0 * T * (T + 1) / 2,
+            "packed_tiles": 65536.0 * blocks,
             "slot_stores": 4.0 * nslots * k * n,
-            "labels": 256.0 * T * (T + 1) / 2}
+            "labels": (lists if sorted_form else 256.0) * blocks}
 
 
 def pass_roofline(wl, prof, pk):
@@ -159,12 +163,15 @@ def pass_roofline(wl, prof, pk):
     red = sum(r["info"]["reduce_ms"] for r in prof)
     fold = sum(r["info"]["fold_ms"] for r in prof)
     if info["k_pass_used"] == 1:
-        b = sym_bytes(n, k, info["schedule"][2])
+        b = sym_bytes(n, k, info["schedule"][2], info["schedule"][3] > 8)
         ms = (red - fold) / max(passes, 1)
         ach = b["algorithmic"] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-        return {"kernel": "reduce_sym_kernel", "bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
+        # schedule[3]: register sums per row, 4 or 8 in the branch form, 12 / 16 / 32 in the
+        # sorted form (whose stream launch time here includes its per-pass label sort)
+        kern = "reduce_sym_kernel" if info["schedule"][3] <= 8 else "reduce_sym_sorted_kernel"
+        return {"kernel": kern, "bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
                 "frac": ach / pk["hbm"],
-                "traffic": recorded_traffic("reduce_sym_kernel", "reduce_sym.cu", wl.name),
+                "traffic": recorded_traffic(kern, "reduce_sym.cu", wl.name),
                 "peak_source": pk["source"] + " HBM copy", "algorithmic_bytes_per_launch": b["algorithmic"],
                 "moved_bytes_per_launch": {x: b[x] for x in ("packed_tiles", "slot_stores", "labels")},
                 "avg_launch_ms": ms, "fold_avg_launch_ms": fold / max(passes, 1),

@@ -696,8 +696,8 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
     if (opt.autotune != 0 && opt.autotune != 1) return fail(POPCORN_ERR_INVALID, "options.autotune must be 0 or 1");
     if (opt.k_pass < 0 || opt.k_pass > 2) return fail(POPCORN_ERR_INVALID, "options.k_pass must be 0, 1 or 2");
-    if (opt.sym_tile != 0 && opt.sym_tile != 1 && opt.sym_tile != 2 && opt.sym_tile != 4)
-        return fail(POPCORN_ERR_INVALID, "options.sym_tile must be 0, 1, 2 or 4");
+    if (opt.sym_tile < 0 || opt.sym_tile > 8)
+        return fail(POPCORN_ERR_INVALID, "options.sym_tile must be in [0, 8]");
     for (int r = 0; r < 4; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
     if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)
@@ -724,13 +724,12 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // symmetric pass (FP32 K, k <= kSymMaxK; k_pass 0 or 1): the blocks on and above the
     // diagonal, row and column sums into T slots, folded into slot 0
     SymPlan sym{};
-    // automatic choice, from measurements on GB300: the symmetric pass where it beats the
-    // full square (itself at ~0.99 of HBM) -- the branch form for k <= 4, and for k <= 8
-    // while its slots (one per 128-block a row) stay L2-resident (<= 64 MB).  At the images
-    // size the k = 8 branch form (slots 1.2 GB) and the run form (k = 10) are slower than the
-    // full square, so k_pass = 1 is needed to force them.
-    const double sym_slot_bytes = 4.0 * ((ni + 127) / 128) * (double)k * ni;
-    const bool sym_auto = k <= 4 || (k <= kSymBranchMaxK && sym_slot_bytes <= 64.0 * (1 << 20));
+    // automatic choice, from measurements on GB300: the symmetric pass (sorted form) once K
+    // outgrows L2, where a pass streams it from HBM and reading half of it pays (images,
+    // n = 70,000, k = 10: 1.67 ms a stream plus 0.09 ms of fold against 3.05 ms for the
+    // full square; rings, n = 20,000, k = 4: 0.152 + 0.014 against 0.275).  Below that a
+    // pass is a few microseconds of launches and the full square's two kernels win.
+    const bool sym_auto = ni >= kSymAutoMinN;
     if (ks == POPCORN_K_FP32 && (opt.k_pass == 1 || (opt.k_pass == 0 && sym_auto)))
         sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin, opt.sym_tile);
     const bool use_sym = sym.ok;
@@ -789,14 +788,14 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     if (use_sym && sym.meta_bytes) POPCORN_TRY(ws.alloc(&b.sym_meta, sym.meta_bytes, "block label metadata"));
     // one pass's reduction: the K stream (for the symmetric pass: stream, then fold with z)
     // kernels of one pass's reduction: the full-square stream; or the symmetric stream and its
-    // fold (the run form first sorts every block's labels)
-    const int red_launches = use_sym ? (sym.runs ? 3 : 2) : 1;
+    // fold (the sorted form first sorts every block's labels)
+    const int red_launches = use_sym ? (sym.sorted ? 3 : 2) : 1;
     // Error-path test hook: with POPCORN_TEST_SYM_STALL_MS=<ms> in the environment, the
-    // first symmetric (branch-form) stream launch of this fit leaves one block's copies out
+    // first symmetric stream launch of this fit (either form) leaves one block's copies out
     // and bounds its waits by <ms>, so the fit reports POPCORN_ERR_TIMEOUT (nothing faults
     // or hangs; the context stays usable).  Unset in every ordinary run.
     int stall_ms = 0;
-    if (use_sym && !sym.runs) {
+    if (use_sym) {
         const char* env = getenv("POPCORN_TEST_SYM_STALL_MS");
         if (env && *env) stall_ms = atoi(env);
         if (stall_ms < 0 || stall_ms > 10000) stall_ms = 0;
@@ -1028,8 +1027,8 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
     if (!(tol >= 0) || !std::isfinite(tol)) return fail(POPCORN_ERR_INVALID, "tol must be finite and >= 0");
     if (opt.autotune != 0 && opt.autotune != 1) return fail(POPCORN_ERR_INVALID, "options.autotune must be 0 or 1");
     if (opt.k_pass < 0 || opt.k_pass > 2) return fail(POPCORN_ERR_INVALID, "options.k_pass must be 0, 1 or 2");
-    if (opt.sym_tile != 0 && opt.sym_tile != 1 && opt.sym_tile != 2 && opt.sym_tile != 4)
-        return fail(POPCORN_ERR_INVALID, "options.sym_tile must be 0, 1, 2 or 4");
+    if (opt.sym_tile < 0 || opt.sym_tile > 8)
+        return fail(POPCORN_ERR_INVALID, "options.sym_tile must be in [0, 8]");
     for (int r = 0; r < 4; ++r)
         if (opt.reserved[r] != 0) return fail(POPCORN_ERR_INVALID, "options.reserved[%d] must be 0", r);
     if (opt.k_storage < POPCORN_K_FP32 || opt.k_storage > POPCORN_K_BF16)

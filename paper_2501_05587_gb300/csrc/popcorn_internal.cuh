@@ -67,22 +67,25 @@ struct ReducePlan {
 // Symmetric K stream (reduce_sym.cu): each 128 x 128 block on and above the
 // diagonal is read once.  Blocks are handed out in super-tiles of a x a blocks;
 // a super-tile's row sums go to one slot of its rows and its column sums to one
-// slot of its columns' rows, so Spart holds nslots = ceil(T / a) (+1 when a > 1)
-// slots; the fold sums them into slot 0 (the assignment then reads slot 0
-// only) and forms z and J.  FP32 K, k <= kSymMaxK: up to kSymBranchMaxK clusters a
-// uniform branch per column / row adds into register sums; above that the run form
-// walks each block in label order (a per-pass sort of every block's labels) and adds
-// runs of one label, with K packed in the XOR-32 layout.
+// slot of its columns' rows, so Spart holds nslots = ceil(T / a) (+1 in the sorted
+// form) slots; the fold sums them into slot 0 (the assignment then reads slot 0
+// only) and forms z and J.  FP32 K, k <= kSymMaxK: up to kSymBranchMaxK clusters on
+// single blocks a uniform branch per column / row adds into register sums; otherwise
+// the sorted form walks each block's columns and rows in label order (a per-pass sort
+// of every 128-block's labels) with the sums in registers over a super-tile, K packed
+// in the XOR-32 layout.
 constexpr int kSymMaxK = 32;
 constexpr int kSymBranchMaxK = 8;
+constexpr int kSymAutoMinN = 8192;   // the automatic choice takes the symmetric pass from here
 struct SymPlan {
     bool ok;
-    bool runs;          // the run form (k > kSymBranchMaxK)
-    int layout;         // packed tile layout the pass reads: kPackedSw16 (branch) or kPackedSw4 (runs)
-    size_t meta_bytes;  // run form: per-pass block metadata (T x 768 bytes)
-    int kb;             // branch form: register sums per row / column, 4 or 8 (>= k)
+    bool sorted;        // the sorted form (k > kSymBranchMaxK, or a forced super-tile edge > 1)
+    int layout;         // packed tile layout the pass reads: kPackedSw16 (branch) or kPackedSw4 (sorted)
+    size_t meta_bytes;  // sorted form: per-pass label-sorted lists of every block (column and row lists)
+    int kb;             // register sums per row / column: 4 or 8 (branch form), 12, 16 or 32 (sorted form); >= k
+    int rpl;            // sorted form: rows (columns) a lane owns in a block, 4 or 2 (2: two warps a block row)
     int T;              // 128-blocks per side
-    int a;              // super-tile edge in blocks (1, 2 or 4)
+    int a;              // super-tile edge in blocks (1, 2, 4 or 8)
     int Ts;             // super-tiles per side
     int nslots;         // Spart slots
     int stages;         // block ring depth
@@ -99,7 +102,7 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req = 0
 cudaError_t configure_reduce_sym(int smem_optin);
 // err: set when a bounded wait of the stream kernel runs out; `between` (may be
 // null) is recorded on s after the stream kernel, before the fold.  stall_ms > 0
-// (branch form; error-path tests only): CTA 0 leaves its first block's copies out,
+// (either form; error-path tests only): CTA 0 leaves its first block's copies out,
 // and every wait of the launch gives up after stall_ms, so the launch reports a
 // timed-out wait and the context stays usable.
 cudaError_t launch_reduce_sym(const struct PassBuffers& b, const SymPlan& p, int* err, int eval_only,
@@ -275,7 +278,7 @@ struct PassBuffers {
     double* J_hist;       // [max(1, max_iter)]
     int32_t* changed_hist;
     float* E_out;         // optional n x k
-    uint8_t* sym_meta;    // run form of the symmetric pass: T x 768 bytes of block metadata
+    uint8_t* sym_meta;    // sorted form of the symmetric pass: the label-sorted lists of every block
 };
 
 // Operand rows for the recompute path, their norms and scales, and diag K.

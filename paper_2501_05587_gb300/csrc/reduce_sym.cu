@@ -27,16 +27,18 @@
 //   byte that is the same for the whole warp, so the bucketing of V is a uniform
 //   branch into registers: no data-dependent addressing, no atomics.
 //
-// Run form (k <= kSymMaxK), reduce_sym_runs_kernel: blocks in label order (a
-//   per-pass sort of every block's labels), one shared-memory add per run of one
-//   label, on super-tiles of a x a blocks whose row and column sums are kept over
-//   the super-tile before one store per row: see below.
+// Sorted form (k <= kSymMaxK; also k <= 8 with a forced super-tile edge > 1),
+//   sym_sort_kernel + reduce_sym_sorted_kernel: a per-pass stable sort of every
+//   128-block's labels into lists of tile offsets, cluster after cluster; super-tiles
+//   of a x a blocks, a row warp per block row and a column warp per block column, each
+//   walking its blocks' lists with the per-cluster sums in registers over the whole
+//   super-tile (the loop over clusters is unrolled): see below.
 //
-// Each group's warps split the work and their partials are added in a fixed
-// order: deterministic.  sym_fold_kernel: S_ic = the slots summed in slot order
-// (float-float), written to slot 0, the per-block FP64 partials of
-// sum_{i in L_c} S_ic (z, Eq. 14), and in its last block the pass finalization
-// (||c||^2, J).  The assignment then reads slot 0 alone.
+// Every partial is added in a fixed order and stored once: deterministic.
+// sym_fold_kernel: S_ic = the slots summed in slot order (float-float), written to
+// slot 0, the per-block FP64 partials of sum_{i in L_c} S_ic (z, Eq. 14), and in its
+// last block the pass finalization (||c||^2, J).  The assignment then reads slot 0
+// alone.
 #include <cstring>
 
 #include "popcorn_internal.cuh"
@@ -57,7 +59,6 @@ constexpr int kSymThreads = 2 * kGroup + 32;   // + the producer warp
 constexpr int kConsumerWarps = 2 * kGroup / 32;
 constexpr int kBarRows = 1, kBarCols = 2;      // named barriers of the two groups
 constexpr int kFoldThreads = 256;
-constexpr int kMaxA = 4;                       // largest super-tile edge (run form)
 
 constexpr int align128(int x) { return (x + 127) & ~127; }
 
@@ -339,178 +340,275 @@ __global__ void __launch_bounds__(kSymThreads, 1)
     }
 }
 
-// The blocks of super-tile (Is, Js) of the run form: rows I0 <= I < I1, columns
-// max(I, J0) <= J < J1.
+// The blocks of super-tile (Is, Js): block rows I0 <= I < I0 + a, block columns
+// J0 <= J < J0 + a, those with I <= J < T.
 struct Unit {
-    int Is, Js, I0, I1, J0, J1;
+    int Is, Js, I0, J0;
 };
-__device__ __forceinline__ Unit unit_of(long long u, int T, int a, int Ts) {
+__device__ __forceinline__ Unit unit_of(long long u, int a, int Ts) {
     Unit t;
     tri_coords(u, Ts, &t.Is, &t.Js);
     t.I0 = t.Is * a;
-    t.I1 = min(t.I0 + a, T);
     t.J0 = t.Js * a;
-    t.J1 = min(t.J0 + a, T);
     return t;
 }
 
 // ---------------------------------------------------------------------------
-// The run form of the symmetric pass (k up to kSymRunsMaxK).
+// The sorted form of the symmetric pass (k <= kSymMaxK).
 //
-// Per pass, sym_meta_kernel sorts the labels of every 128-block (a stable counting
-// sort) and writes the block's metadata: for each sorted position p, the box offset
-// of the local index it holds when the block is a column block (colcode) and when it
-// is a row block (rowcode), its label, and a mask of the positions that end a run of
-// one label.  The stream then walks a block in label order: a row-group lane owns a
-// row and adds the row's elements column after column, in sorted order, into one
-// register, and only at the end of a run of one label adds that register to the row's
-// cluster sum in shared memory; a column-group lane owns a column and does the same
-// over the rows.  So shared memory sees one read-add-write per run (at most k per
-// half-block) instead of one per element, and a cluster sum is the same whatever k
-// is.  K is packed in the XOR-32 layout (kPackedSw4): element c of row r of a box at
-// c ^ (r mod 32), so that both the 32 rows of a column and the 32 columns of a row
-// sit in 32 different banks.
-constexpr int kMetaBytes = 768;        // per 128-block
-constexpr int kMetaColcode = 0;        // u16[128]: (box << 12) | (l mod 32)   of local index l
-constexpr int kMetaRowcode = 256;      // u16[128]: 32 l + (l mod 32)
-constexpr int kMetaLabel = 512;        // u8[128]: the label at sorted position p (0xFF past the block's rows)
-constexpr int kMetaMask = 640;         // u64[2]: bit p set where position p ends a run (half 0 also at 63)
+// Per pass, sym_sort_kernel sorts the points of every 128-block by label (stable) and
+// writes two lists for the block: the byte offsets of its points as columns of a tile
+// (column list) and as rows of a tile (row list), cluster after cluster, each cluster's
+// entries padded to a multiple of 4, after a header with each cluster's start and count.
+//
+// The stream takes super-tiles of a x a blocks, one per CTA at a time.  The rows of
+// block row I0 + i are owned by 4 / R row warps (lane l of part h: rows
+// l + 32 (R h + e), e < R), the columns of block column J0 + j by 4 / R column warps
+// the same way.  On its block (I, J) a row warp walks the column list of J cluster by
+// cluster: the columns of cluster c are added into one register per row, and that
+// into acc[c][e], the row's running sum for c -- a register, since the loop over the
+// clusters is unrolled up to KMAX.  A column warp walks the row list of I the same
+// way.  The inner loop is a load of 4 list entries, per entry one XOR for the element
+// offset, and per row (column) a shared-memory load and an add (f32x2, two rows a
+// time): no run-end test, no register indexed by data, no shared-memory accumulator.
+// The sums stay in registers over the super-tile and are stored once per row and
+// cluster (slots shrink a-fold).
+// All consumer warps wait for and release every block of the ring (the two that own it
+// after their work), so no warp runs a phase ahead of another.
+//
+// K is packed in the XOR-32 layout (kPackedSw4): element c of row r of a box at
+// c ^ (r mod 32), so the 32 rows of a column and the 32 columns of a row sit in 32
+// different banks.  In bytes, element (r, C) of the tile is at
+//   16384 (C >> 5) + 128 r + 4 ((C & 31) ^ (r & 31)).
+// Column C's list entry is 16384 (C >> 5) + 4 (C & 31); for row r = l + 32 e of lane l
+// the offset is (entry ^ 132 l) + 4096 e.  Row r's list entry is 128 r + 4 (r & 31); for
+// column C = l + 32 e of lane l it is (entry ^ 4 l) + 16384 e.
+constexpr int kSortHdr = 128;   // bytes: u32 per cluster c < 32, (start << 8) | count
+// Rows (columns) a lane owns in a block: 2, i.e. two warps share a block row (column) --
+// measured on the images workload (n = 70,000, k = 10): 1.67 ms a stream at a = 4 against
+// 2.04 ms with 4 rows a lane at a = 8 (a block's two owners take half as long, so its
+// ring stage comes back sooner).
+constexpr int kSortedRowsPerLane = 2;
 
-__global__ void __launch_bounds__(kB) sym_meta_kernel(const uint8_t* __restrict__ lab8, int n, int k, uint8_t* meta,
-                                                      const LoopState* st, int eval_only) {
+// Entries of one list: every cluster padded to a multiple of 4, plus one chunk of 4
+// that the loop below may read ahead (never used).
+__host__ __device__ constexpr int sort_list_len(int k) { return ((kB + 3 * k + 3) & ~3) + 4; }
+__host__ __device__ constexpr int sort_meta_bytes(int k) { return kSortHdr + 4 * sort_list_len(k); }
+
+__global__ void __launch_bounds__(kB) sym_sort_kernel(const uint8_t* __restrict__ lab8, int n, int k, uint8_t* metaC,
+                                                      uint8_t* metaR, const LoopState* st, int eval_only) {
     grid_dependency_wait();   // the labels come from the previous pass
     if (pass_skip(st, eval_only)) return;
     __shared__ uint8_t lab[kB];
-    __shared__ unsigned long long ends[2];
+    __shared__ int cnt[kSymMaxK], start[kSymMaxK];
+    __shared__ uint32_t cc[sort_list_len(kSymMaxK)], rc[sort_list_len(kSymMaxK)];
     const int b = blockIdx.x, t = threadIdx.x;
     const int i = b * kB + t;
-    // rows past n, and (defensively) any label outside [0, k), take no part in a run: the
-    // stream adds a run into the cluster sum its label indexes
+    const int L = sort_list_len(k);
+    // points past n (and, defensively, a label outside [0, k)) get no entry
     const int l = (i < n && (int)lab8[i] < k) ? (int)lab8[i] : 0xFF;
     lab[t] = (uint8_t)l;
-    if (t < 2) ends[t] = 0ull;
+    for (int e = t; e < L; e += kB) cc[e] = rc[e] = 0u;   // padding entries: offset 0, never added
     __syncthreads();
-    // stable rank: labels below mine, then equal labels before me; is a later one equal?
-    int pos = 0;
-    bool last = true;
-    for (int u = 0; u < kB; ++u) {
-        const int lu = lab[u];
-        pos += (lu < l) || (lu == l && u < t);
-        last = last && !(lu == l && u > t);
+    int rank = 0;   // equal labels before this point (stable order)
+    for (int u = 0; u < t; ++u) rank += lab[u] == l;
+    if (t < k) {
+        int m = 0;
+        for (int u = 0; u < kB; ++u) m += lab[u] == t;
+        cnt[t] = m;
     }
-    uint8_t* m = meta + (size_t)b * kMetaBytes;
-    reinterpret_cast<uint16_t*>(m + kMetaColcode)[pos] = (uint16_t)(((t >> 5) << 12) | (t & 31));
-    reinterpret_cast<uint16_t*>(m + kMetaRowcode)[pos] = (uint16_t)(32 * t + (t & 31));
-    m[kMetaLabel + pos] = (uint8_t)l;
-    // a run of a real label ends here; the first half also ends at position 63 (its
-    // partial sum is stored before the second half's part of the same run)
-    if (l != 0xFF && (last || pos == 63)) atomicOr(&ends[pos >> 6], 1ull << (pos & 63));
     __syncthreads();
-    if (t < 2) reinterpret_cast<unsigned long long*>(m + kMetaMask)[t] = ends[t];
+    if (t < k) {
+        int p = 0;
+        for (int c = 0; c < t; ++c) p += (cnt[c] + 3) & ~3;
+        start[t] = p;
+    }
+    __syncthreads();
+    if (l != 0xFF) {
+        const int pos = start[l] + rank;
+        cc[pos] = (uint32_t)(16384 * (t >> 5) + 4 * (t & 31));
+        rc[pos] = (uint32_t)(128 * t + 4 * (t & 31));
+    }
+    __syncthreads();
+    uint32_t* hC = reinterpret_cast<uint32_t*>(metaC + (size_t)b * sort_meta_bytes(k));
+    uint32_t* hR = reinterpret_cast<uint32_t*>(metaR + (size_t)b * sort_meta_bytes(k));
+    if (t < kSortHdr / 4) {
+        const uint32_t h = t < k ? ((uint32_t)start[t] << 8) | (uint32_t)cnt[t] : 0u;
+        hC[t] = h;
+        hR[t] = h;
+    }
+    for (int e = t; e < L; e += kB) {
+        hC[kSortHdr / 4 + e] = cc[e];
+        hR[kSortHdr / 4 + e] = rc[e];
+    }
 }
 
-struct RunArgs {
+struct SortedArgs {
     const float* Kp;           // block-packed K, kPackedSw4 layout
-    int n, k, T;
-    int a, Ts;
+    int n, k, T, a, Ts;
     long long units;
-    int stages;
-    int off_meta, off_accr, off_colacc, off_bars, off_flag;
-    const uint8_t* meta;       // [T][kMetaBytes]
-    float* Spart;              // [nslots][k][n]
+    int stages, stage_bytes, meta_bytes, off_bars;
+    const uint8_t* metaC;      // [T][meta_bytes] column lists
+    const uint8_t* metaR;      // [T][meta_bytes] row lists
+    float* Spart;              // [Ts + 1][k][n]
     const LoopState* st;
     int* err;
     int eval_only;
+    // Test hook for the error path (0 in every ordinary launch): CTA 0 never issues the
+    // copies of its block number stall_block - 1, so the waits for it run out after
+    // wait_ns and the launch reports a timed-out wait.
+    int stall_block;
+    unsigned long long wait_ns;
 };
 
-// Runs of one half-block (64 sorted positions): v(p) = tile[code(p) ^ key] for this lane;
-// at the end of a run of label c (a set bit of `mask`), acc[c * 128] += the run's sum.
-// The run structure is the same for every lane; the end test is taken as a warp vote so
-// that the add into shared memory is a branch the warp takes together (a run ends at
-// about one position in six at k = 10), not predicated code every position pays for.
-__device__ __forceinline__ void sum_runs(const float* __restrict__ tile, const uint16_t* __restrict__ codes,
-                                         const uint8_t* __restrict__ labels, unsigned long long mask, uint32_t key,
-                                         float* acc) {
-    float run = 0.f;
+// The lane's R rows (STRIDE 4096: rows 32 e apart) or columns (STRIDE 16384) of one
+// tile, added cluster by cluster along a list: acc[c][e] += the elements of the list
+// entries of cluster c.
+template <int KMAX, int R, int STRIDE>
+__device__ __forceinline__ void sum_sorted(const unsigned char* __restrict__ tile, const uint32_t* __restrict__ hdr,
+                                           int k, uint32_t key, float (&acc)[KMAX][R]) {
+    const uint32_t* __restrict__ codes = hdr + kSortHdr / 4;
+    auto ld = [&](uint32_t entry, int e) {
+        return *reinterpret_cast<const float*>(tile + (entry ^ key) + STRIDE * e);
+    };
+#pragma unroll
+    for (int c = 0; c < KMAX; ++c) {
+        if (c < k) {
+            const uint32_t h = hdr[c];
+            const int p0 = (int)(h >> 8), cnt = (int)(h & 0xffu);
+            const int pe = p0 + (cnt & ~3);
+            float s[R];
+#pragma unroll
+            for (int e = 0; e < R; ++e) s[e] = 0.f;
+            uint4 cw = *reinterpret_cast<const uint4*>(codes + p0);
 #pragma unroll 1
-    for (int pc = 0; pc < 8; ++pc) {
-        const uint4 cw = *reinterpret_cast<const uint4*>(codes + 8 * pc);   // 8 codes, the same for every lane
-        const uint32_t c32[4] = {cw.x, cw.y, cw.z, cw.w};
-        float v[8];
+            for (int p = p0; p < pe; p += 4) {
+                const uint4 cur = cw;
+                cw = *reinterpret_cast<const uint4*>(codes + p + 4);   // the next chunk (or the tail)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const uint32_t code = (c32[e >> 1] >> (16 * (e & 1))) & 0xffffu;
-            v[e] = tile[code ^ key];
-        }
-        const uint32_t mb = (uint32_t)(mask >> (8 * pc)) & 0xffu;
-        if (mb == 0u) {   // no run ends in these 8 positions (uniform)
-            run += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
-            continue;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            run += v[e];
-            if (__any_sync(0xffffffffu, (mb >> e) & 1u)) {
-                float* dst = acc + (uint32_t)labels[8 * pc + e] * kB;
-                *dst += run;
-                run = 0.f;
+                for (int e = 0; e < R; e += 2) {
+                    // rows (columns) e and e + 1 as one f32x2 pair: half the add instructions
+                    const unsigned long long w0 = tc::f2pack(ld(cur.x, e), ld(cur.x, e + 1));
+                    const unsigned long long w1 = tc::f2pack(ld(cur.y, e), ld(cur.y, e + 1));
+                    const unsigned long long w2 = tc::f2pack(ld(cur.z, e), ld(cur.z, e + 1));
+                    const unsigned long long w3 = tc::f2pack(ld(cur.w, e), ld(cur.w, e + 1));
+                    float x, y;
+                    tc::f2unpack(tc::f2add(tc::f2add(w0, w1), tc::f2add(w2, w3)), x, y);
+                    const unsigned long long t = tc::f2add(tc::f2pack(s[e], s[e + 1]), tc::f2pack(x, y));
+                    tc::f2unpack(t, s[e], s[e + 1]);
+                }
             }
+            const int rem = cnt & 3;   // the last 1-3 entries of the cluster (uniform)
+            if (rem) {
+#pragma unroll
+                for (int e = 0; e < R; ++e) {
+                    float v = ld(cw.x, e);
+                    if (rem > 1) v += ld(cw.y, e);
+                    if (rem > 2) v += ld(cw.z, e);
+                    s[e] += v;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < R; ++e) acc[c][e] += s[e];
         }
     }
 }
 
-__global__ void __launch_bounds__(kSymThreads, 1) reduce_sym_runs_kernel(RunArgs a) {
-    grid_dependency_wait();   // the block metadata and the loop state come from before this pass
+// Register sums per lane (R KMAX) against the register file: an SM sub-partition holds
+// 16384 registers for its share of the CTA's warps (2a (4 / R) consumers + 1), so the
+// widest super-tile edge with 4 rows a lane is 8 for KMAX = 12 (96 registers a thread),
+// 7 for 16 (128) and 3 for 32 (255); with 2 rows a lane (two warps share a block row or
+// column) it is 4 for KMAX <= 16 (96) and 3 for 32 (128).
+__host__ __device__ constexpr int sorted_max_a(int kmax, int rpl) {
+    return rpl == 4 ? (kmax <= 12 ? 8 : kmax <= 16 ? 7 : 3) : (kmax <= 16 ? 4 : 3);
+}
+__host__ __device__ constexpr int sorted_threads(int a, int rpl) { return 32 * (2 * a * (4 / rpl) + 1); }
+
+template <int KMAX, int R>
+__global__ void __launch_bounds__(sorted_threads(sorted_max_a(KMAX, R), R), 1)
+    reduce_sym_sorted_kernel(SortedArgs a) {
+    grid_dependency_wait();   // the block lists and the loop state come from before this pass
     if (pass_skip(a.st, a.eval_only)) return;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const uint32_t sbase = tc::smem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = a.n, k = a.k, S = a.stages;
+    constexpr int H = 4 / R;   // warps per block row (column)
+    const int A = a.a, nw = 2 * A * H, S = a.stages;
+    const int n = a.n, k = a.k, T = a.T;
     auto full_bar = [&](int s) { return sbase + (uint32_t)a.off_bars + 8u * s; };
     auto empty_bar = [&](int s) { return sbase + (uint32_t)a.off_bars + 8u * (S + s); };
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + a.off_flag);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + a.off_bars + 16 * S);
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             tc::mbar_init(full_bar(s), 1);
-            tc::mbar_init(empty_bar(s), kConsumerWarps);
+            tc::mbar_init(empty_bar(s), (uint32_t)nw);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const long long G = gridDim.x;
+    // the blocks of a super-tile in a Latin-square order: consecutive blocks lie in
+    // different block rows and block columns, so the blocks in the ring keep different
+    // row and column warps busy
+    auto block_of = [&](const Unit& w, int m, int i, int* I, int* J) {
+        const int jj = i + m < A ? i + m : i + m - A;
+        *I = w.I0 + i;
+        *J = w.J0 + jj;
+        return *I < T && *J < T && *J >= *I;
+    };
 
-    if (warp == kConsumerWarps) {
-        // producer: one thread bulk-copies each block and the metadata of its row and column blocks
+    if (warp == nw) {
+        // producer: one thread bulk-copies each block and the lists of its column and row blocks
         if (lane == 0) {
-            const uint64_t stream_once = tc::l2_evict_first();
+            const uint64_t stream_once = tc::l2_evict_first();   // K is read once per pass
+            const long long skip = blockIdx.x == 0 ? (long long)a.stall_block - 1 : -1;
             long long t = 0;
+            int s = 0;
+            uint32_t ph = 0;
             bool ok = true;
             for (long long u = blockIdx.x; u < a.units && ok; u += G) {
-                const Unit w = unit_of(u, a.T, a.a, a.Ts);
-                for (int I = w.I0; I < w.I1 && ok; ++I)
-                    for (int J = max(I, w.J0); J < w.J1; ++J, ++t) {
-                        const int s = (int)(t % S);
-                        if (t >= S && !tc::mbar_wait(empty_bar(s), (uint32_t)((t / S) - 1) & 1u, abort_flag, a.err)) {
+                const Unit w = unit_of(u, A, a.Ts);
+                for (int m = 0; m < A && ok; ++m)
+                    for (int i = 0; i < A; ++i) {
+                        int I, J;
+                        if (!block_of(w, m, i, &I, &J)) continue;
+                        if (t >= S && !tc::mbar_wait_for(empty_bar(s), ph ^ 1u, abort_flag, a.err, a.wait_ns)) {
                             ok = false;
                             break;
                         }
-                        tc::mbar_arrive_expect_tx(full_bar(s), (uint32_t)(kTileBytes + 2 * kMetaBytes));
-                        const long long tri = (long long)I * a.T - (long long)I * (I - 1) / 2 + (J - I);
-                        tc::bulk_load_1d_hint(sbase + (uint32_t)s * kTileBytes, a.Kp + tri * (kB * kB),
-                                              (uint32_t)kTileBytes, full_bar(s), stream_once);
-                        const uint32_t mdst = sbase + (uint32_t)a.off_meta + (uint32_t)s * 2 * kMetaBytes;
-                        tc::bulk_load_1d(mdst, a.meta + (size_t)I * kMetaBytes, (uint32_t)kMetaBytes, full_bar(s));
-                        tc::bulk_load_1d(mdst + kMetaBytes, a.meta + (size_t)J * kMetaBytes, (uint32_t)kMetaBytes,
+                        if (t == skip) {   // the test hook: this block never arrives
+                            ++t;
+                            if (++s == S) {
+                                s = 0;
+                                ph ^= 1u;
+                            }
+                            continue;
+                        }
+                        tc::mbar_arrive_expect_tx(full_bar(s), (uint32_t)(kTileBytes + 2 * a.meta_bytes));
+                        const uint32_t dst = sbase + (uint32_t)s * (uint32_t)a.stage_bytes;
+                        const long long tri = (long long)I * T - (long long)I * (I - 1) / 2 + (J - I);
+                        tc::bulk_load_1d_hint(dst, a.Kp + tri * (kB * kB), (uint32_t)kTileBytes, full_bar(s),
+                                              stream_once);
+                        tc::bulk_load_1d(dst + kTileBytes, a.metaC + (size_t)J * a.meta_bytes, (uint32_t)a.meta_bytes,
                                          full_bar(s));
+                        tc::bulk_load_1d(dst + kTileBytes + a.meta_bytes, a.metaR + (size_t)I * a.meta_bytes,
+                                         (uint32_t)a.meta_bytes, full_bar(s));
+                        ++t;
+                        if (++s == S) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
                     }
             }
             if (*abort_flag) {
+                // leaving early: let this thread's copies land before the CTA's memory goes
                 for (long long t2 = t > S ? t - S : 0; t2 < t; ++t2) {
+                    if (t2 == skip) continue;   // nothing was issued for it
                     const uint32_t bar = full_bar((int)(t2 % S)), par = (uint32_t)(t2 / S) & 1u;
                     const unsigned long long t0 = tc::globaltimer();
-                    while (!tc::mbar_try_wait(bar, par) && tc::globaltimer() - t0 < tc::kWaitLimitNs) {
+                    while (!tc::mbar_try_wait(bar, par) && tc::globaltimer() - t0 < a.wait_ns) {
                     }
                 }
             }
@@ -518,111 +616,83 @@ __global__ void __launch_bounds__(kSymThreads, 1) reduce_sym_runs_kernel(RunArgs
         return;
     }
 
-    const uint64_t keep = tc::l2_evict_last();
-    const bool rowg = warp < kConsumerWarps / 2;
-    const int u = threadIdx.x & (kGroup - 1);
-    const int bar_id = rowg ? kBarRows : kBarCols;
-    const int gw = u >> 5;
-    const int h = gw >> 2;                      // half of the sorted order: positions 64 h .. 64 h + 63
-    const int q = gw & 3;                       // row group: rows 32 q + lane; column group: box q
-    // this lane's row (row group) or column (column group) inside the block, and the XOR key
-    // that turns a code into its element's offset: row group 32 r + (r mod 32) with r its row,
-    // column group 4096 q + lane
-    const int mine = 32 * q + lane;
-    const uint32_t key = rowg ? (uint32_t)(32 * mine + lane) : (uint32_t)(4096 * q + lane);
-    float* accr = reinterpret_cast<float*>(smem + a.off_accr);     // [2][k][128] row sums of the block row
-    // column sums of the super-tile's block columns, per half: [a][2][k][128]
-    float* colacc = reinterpret_cast<float*>(smem + a.off_colacc);
-    float* my = accr + (size_t)h * k * kB + mine;                  // row group: this lane's sums my[c * 128]
-    const int diag_slot = a.Ts;
-
-    int t = 0;
+    const uint64_t keep = tc::l2_evict_last();   // the slots are read back by the fold
+    const bool roww = warp < A * H;
+    const int wr = roww ? warp : warp - A * H;
+    const int mine = wr / H;          // block row (column) of the super-tile
+    const int part = wr % H;          // this warp's rows (columns): 32 (R part + e) + lane, e < R
+    const uint32_t key = roww ? 132u * (uint32_t)lane : 4u * (uint32_t)lane;
+    int s = 0;
+    uint32_t ph = 0;
     bool alive = true;
-    for (long long uu = blockIdx.x; uu < a.units && alive; uu += G) {
-        const Unit w = unit_of(uu, a.T, a.a, a.Ts);
-        for (int I = w.I0; I < w.I1 && alive; ++I)
-            for (int J = max(I, w.J0); J < w.J1; ++J, ++t) {
-                const int s = t % S;
-                const bool ok = tc::mbar_wait(full_bar(s), (uint32_t)(t / S) & 1u, abort_flag, a.err);
-                if (!tc::named_bar_all(bar_id, kGroup, ok)) {
+    for (long long u = blockIdx.x; u < a.units && alive; u += G) {
+        const Unit w = unit_of(u, A, a.Ts);
+        float acc[KMAX][R];
+#pragma unroll
+        for (int c = 0; c < KMAX; ++c)
+#pragma unroll
+            for (int e = 0; e < R; ++e) acc[c][e] = 0.f;
+        for (int m = 0; m < A && alive; ++m)
+            for (int i = 0; i < A; ++i) {
+                int I, J;
+                if (!block_of(w, m, i, &I, &J)) continue;
+                if (!tc::mbar_wait_for(full_bar(s), ph, abort_flag, a.err, a.wait_ns)) {
                     alive = false;
                     break;
                 }
-                const float* tile = reinterpret_cast<const float*>(smem + (size_t)s * kTileBytes);
-                const uint8_t* mI = smem + a.off_meta + s * 2 * kMetaBytes;
-                const uint8_t* mJ = mI + kMetaBytes;
-                if (rowg) {
-                    // row sums of block I over the columns of block J (sorted by label), kept per
-                    // half over the super-tile's columns; the halves are added and stored to slot
-                    // Js after the last one
-                    if (J == max(I, w.J0))
-                        for (int c = 0; c < k; ++c) my[c * kB] = 0.f;
-                    sum_runs(tile, reinterpret_cast<const uint16_t*>(mJ + kMetaColcode) + 64 * h,
-                             mJ + kMetaLabel + 64 * h, reinterpret_cast<const unsigned long long*>(mJ + kMetaMask)[h],
-                             key, my);
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(empty_bar(s));
-                    if (J == w.J1 - 1) {
-                        tc::named_bar<kGroup>(kBarRows);
-                        if (u < kB && I * kB + u < n) {
-                            float* out = a.Spart + (size_t)w.Js * k * n + I * kB + u;
-                            const float* __restrict__ h0 = accr + u;
-                            const float* __restrict__ h1 = accr + (size_t)k * kB + u;
-#pragma unroll 4
-                            for (int c = 0; c < k; ++c) tc::st_hint(out + (size_t)c * n, h0[c * kB] + h1[c * kB], keep);
-                        }
-                    }
-                } else {
-                    const bool diag = I == J;
-                    if (diag && a.a == 1) {
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(empty_bar(s));
-                        continue;
-                    }
-                    // column sums of block J over the rows of block I (sorted by label), kept per
-                    // half over the super-tile's rows in colacc[J - J0]; after the last of those
-                    // rows the halves are added and stored to slot Is (the extra slot for a
-                    // diagonal super-tile).  A diagonal block adds nothing.
-                    float* myc = colacc + ((size_t)(J - w.J0) * 2 + h) * k * kB + mine;
-                    if (I == w.I0)
-                        for (int c = 0; c < k; ++c) myc[c * kB] = 0.f;
-                    if (!diag)
-                        sum_runs(tile, reinterpret_cast<const uint16_t*>(mI + kMetaRowcode) + 64 * h,
-                                 mI + kMetaLabel + 64 * h,
-                                 reinterpret_cast<const unsigned long long*>(mI + kMetaMask)[h], key, myc);
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(empty_bar(s));
-                    if (I == min(J, w.I1 - 1)) {
-                        tc::named_bar<kGroup>(kBarCols);
-                        if (u < kB && J * kB + u < n) {
-                            const int slot = w.Is == w.Js ? diag_slot : w.Is;
-                            float* out = a.Spart + (size_t)slot * k * n + J * kB + u;
-                            const float* __restrict__ h0 = colacc + (size_t)(J - w.J0) * 2 * k * kB + u;
-                            const float* __restrict__ h1 = h0 + (size_t)k * kB;
-#pragma unroll 4
-                            for (int c = 0; c < k; ++c) tc::st_hint(out + (size_t)c * n, h0[c * kB] + h1[c * kB], keep);
-                        }
-                    }
+                const unsigned char* stage = smem + (size_t)s * a.stage_bytes;
+                if (roww) {
+                    // row sums of block I over the columns of block J, by the column list of J
+                    if (i == mine)
+                        sum_sorted<KMAX, R, 4096>(stage + 4096 * R * part,
+                                                  reinterpret_cast<const uint32_t*>(stage + kTileBytes), k, key, acc);
+                } else if (J - w.J0 == mine && I != J) {
+                    // column sums of block J over the rows of block I, by the row list of I (a
+                    // diagonal block's row sums already cover it)
+                    sum_sorted<KMAX, R, 16384>(stage + 16384 * R * part,
+                                               reinterpret_cast<const uint32_t*>(stage + kTileBytes + a.meta_bytes), k,
+                                               key, acc);
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(empty_bar(s));
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1u;
                 }
             }
+        if (!alive) break;
+        // one store per row (column) and cluster: row sums to slot Js of the rows of block
+        // row I; column sums to slot Is of the rows of block column J, or to the extra slot
+        // Ts from a super-tile on the diagonal (its rows also take row sums into slot Js)
+        const int X = (roww ? w.I0 : w.J0) + mine;
+        if (X < T) {
+            const int slot = roww ? w.Js : (w.Is == w.Js ? a.Ts : w.Is);
+            const int r0 = X * kB + 32 * R * part + lane;   // this lane's rows (columns): r0 + 32 e
+            float* out = a.Spart + (size_t)slot * k * n + r0;
+#pragma unroll
+            for (int c = 0; c < KMAX; ++c) {
+                if (c < k) {
+#pragma unroll
+                    for (int e = 0; e < R; ++e)
+                        if (r0 + 32 * e < n) tc::st_hint(out + (size_t)c * n + 32 * e, acc[c][e], keep);
+                }
+            }
+        }
     }
 }
 
-// Dynamic shared memory of the run form, in order: the block ring (1024-byte aligned),
-// the metadata ring (row block, column block), the row sums of a block row per half
-// ([2][k][128]), the column sums of the super-tile's block columns per half
-// ([a][2][k][128]), barriers and the abort flag.
-struct RunLayout {
-    int meta, accr, colacc, bars, flag, bytes;
+// Dynamic shared memory of the sorted form, in order: the ring of stages (a 64 KB tile,
+// the column list of its block column, the row list of its block row), barriers and the
+// abort flag.
+struct SortedLayout {
+    int stage_bytes, meta_bytes, bars, bytes;
 };
-RunLayout run_layout(int k, int stages, int a) {
-    RunLayout L;
-    L.meta = stages * kTileBytes;
-    L.accr = align128(L.meta + stages * 2 * kMetaBytes);
-    L.colacc = align128(L.accr + 2 * k * kB * 4);
-    L.bars = align128(L.colacc + a * 2 * k * kB * 4);
-    L.flag = L.bars + 2 * stages * 8;
-    L.bytes = L.flag + 16 + 1024;
+SortedLayout sorted_layout(int k, int stages) {
+    SortedLayout L;
+    L.meta_bytes = sort_meta_bytes(k);
+    L.stage_bytes = kTileBytes + 2 * L.meta_bytes;
+    L.bars = stages * L.stage_bytes;
+    L.bytes = L.bars + 16 * stages + 16 + 128;   // + slack for the 128-byte alignment
     return L;
 }
 
@@ -697,7 +767,13 @@ cudaError_t configure_reduce_sym(int smem_optin) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(reduce_sym_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(reduce_sym_runs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    void (*sorted[6])(SortedArgs) = {reduce_sym_sorted_kernel<12, 4>, reduce_sym_sorted_kernel<16, 4>,
+                                     reduce_sym_sorted_kernel<32, 4>, reduce_sym_sorted_kernel<12, 2>,
+                                     reduce_sym_sorted_kernel<16, 2>, reduce_sym_sorted_kernel<32, 2>};
+    for (auto f : sorted)
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+            return e;
+    return cudaSuccess;
 }
 
 SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, int stages_req) {
@@ -706,12 +782,13 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, in
     p.T = (n + kB - 1) / kB;
     p.items = (long long)p.T * (p.T + 1) / 2;
     p.fold_blocks = (n + kFoldThreads - 1) / kFoldThreads;
-    // k <= 8 on single blocks: the branch form (register sums, the deepest ring that fits);
-    // above, or for a forced super-tile edge > 1: the run form
-    if (k <= kSymBranchMaxK && a_req <= 1) {
+    // the branch form (k <= 8, single blocks) when asked for with a super-tile edge of 1;
+    // otherwise the sorted form (measured faster on the rings workload too: 0.152 ms a
+    // stream against 0.160)
+    if (k <= kSymBranchMaxK && a_req == 1) {
         const int bytes = k <= 4 ? BranchLayout<4>::bytes : BranchLayout<8>::bytes;
         if (bytes > smem_optin) return p;
-        p.runs = false;
+        p.sorted = false;
         p.kb = k <= 4 ? 4 : 8;
         p.layout = kPackedSw16;
         p.a = 1;
@@ -725,36 +802,39 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, in
         p.ok = true;
         return p;
     }
-    p.runs = true;
-    p.kb = 0;
+    p.sorted = true;
+    p.kb = k <= 12 ? 12 : k <= 16 ? 16 : 32;   // register sums a lane: KMAX clusters x 4 rows
     p.layout = kPackedSw4;
-    int cand_a[3] = {4, 2, 1}, na = 3;
+    // the widest super-tile whose consumer warps fit the register file and that leaves at
+    // least 4 super-tiles per SM for balance
+    p.rpl = kSortedRowsPerLane;
+    const int amax = sorted_max_a(p.kb, p.rpl);
+    int cand_a[5] = {amax, 4, 3, 2, 1}, na = 5;
     if (a_req > 0) {
         cand_a[0] = a_req;
         na = 1;
     }
     for (int ia = 0; ia < na; ++ia) {
         const int A = cand_a[ia];
-        if (A < 1 || A > kMaxA) continue;
+        if (A < 1 || A > amax) continue;
         const int Ts = (p.T + A - 1) / A;
         const long long units = (long long)Ts * (Ts + 1) / 2;
-        // leave about 16 super-tiles per SM, so the static round-robin stays near balance
-        if (a_req == 0 && A > 1 && units < 16LL * num_sms) continue;
+        if (a_req == 0 && A > 1 && units < 4LL * num_sms) continue;
         int cand_s[2] = {3, 2};
         if (stages_req > 0) cand_s[0] = cand_s[1] = stages_req;
         for (int is = 0; is < 2; ++is) {
             const int S = cand_s[is];
             if (S < 2 || S > 3) continue;
-            const int bytes = run_layout(k, S, A).bytes;
+            const int bytes = sorted_layout(k, S).bytes;
             if (bytes > smem_optin) continue;
             p.a = A;
             p.Ts = Ts;
             p.units = units;
             p.stages = S;
             p.smem = (size_t)bytes;
-            p.nslots = Ts + (A > 1 ? 1 : 0);
+            p.nslots = Ts + 1;
             p.grid = (int)(units < num_sms ? units : num_sms);
-            p.meta_bytes = (size_t)p.T * kMetaBytes;
+            p.meta_bytes = 2 * (size_t)p.T * sort_meta_bytes(k);
             p.ok = true;
             return p;
         }
@@ -765,13 +845,15 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, in
 cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, int eval_only, cudaStream_t s,
                               cudaEvent_t between, int stall_ms) {
     cudaError_t e;
-    if (p.runs) {
+    if (p.sorted) {
         if (!p.packed || p.layout != kPackedSw4 || !b.sym_meta) return cudaErrorInvalidValue;
-        e = launch_pdl(sym_meta_kernel, dim3((unsigned)p.T), dim3(kB), 0, s, (const uint8_t*)b.lab8, b.n, b.k,
-                       b.sym_meta, (const LoopState*)b.st, eval_only);
+        const SortedLayout L = sorted_layout(b.k, p.stages);
+        uint8_t* metaC = b.sym_meta;
+        uint8_t* metaR = b.sym_meta + (size_t)p.T * L.meta_bytes;
+        e = launch_pdl(sym_sort_kernel, dim3((unsigned)p.T), dim3(kB), 0, s, (const uint8_t*)b.lab8, b.n, b.k, metaC,
+                       metaR, (const LoopState*)b.st, eval_only);
         if (e != cudaSuccess) return e;
-    const RunLayout L = run_layout(b.k, p.stages, p.a);
-        RunArgs r;
+        SortedArgs r;
         r.Kp = static_cast<const float*>(b.K);
         r.n = b.n;
         r.k = b.k;
@@ -780,17 +862,25 @@ cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, 
         r.Ts = p.Ts;
         r.units = p.units;
         r.stages = p.stages;
-        r.off_meta = L.meta;
-        r.off_accr = L.accr;
-        r.off_colacc = L.colacc;
+        r.stage_bytes = L.stage_bytes;
+        r.meta_bytes = L.meta_bytes;
         r.off_bars = L.bars;
-        r.off_flag = L.flag;
-        r.meta = b.sym_meta;
+        r.metaC = metaC;
+        r.metaR = metaR;
         r.Spart = b.Spart;
         r.st = b.st;
         r.err = err;
         r.eval_only = eval_only;
-        e = launch_pdl(reduce_sym_runs_kernel, dim3(p.grid), dim3(kSymThreads), p.smem, s, r);
+        r.stall_block = stall_ms > 0 ? 1 : 0;
+        r.wait_ns = stall_ms > 0 ? (unsigned long long)stall_ms * 1000000ull : tc::kWaitLimitNs;
+        const dim3 block((unsigned)sorted_threads(p.a, p.rpl));
+        void (*f)(SortedArgs) = p.rpl == 4 ? (p.kb == 12   ? reduce_sym_sorted_kernel<12, 4>
+                                              : p.kb == 16 ? reduce_sym_sorted_kernel<16, 4>
+                                                           : reduce_sym_sorted_kernel<32, 4>)
+                                           : (p.kb == 12   ? reduce_sym_sorted_kernel<12, 2>
+                                              : p.kb == 16 ? reduce_sym_sorted_kernel<16, 2>
+                                                           : reduce_sym_sorted_kernel<32, 2>);
+        e = launch_pdl(f, dim3(p.grid), block, p.smem, s, r);
     } else {
         CUtensorMap map;
         memset(&map, 0, sizeof map);

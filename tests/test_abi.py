@@ -94,8 +94,8 @@ def test_invalid_arguments_rejected_before_any_cuda_call(pc):
     assert fit(opt=ctypes.byref(badk)) == 1                      # store_k must be 0 or 1
     badp = pc._Options(0, 1, 1, 0, 0, 0, 3, 0, (ctypes.c_int64 * 4)())
     assert fit(opt=ctypes.byref(badp)) == 1                      # k_pass must be 0 (auto), 1 or 2
-    badpad = pc._Options(0, 1, 1, 0, 0, 0, 0, 5, (ctypes.c_int64 * 4)())
-    assert fit(opt=ctypes.byref(badpad)) == 1                    # padding must be zero
+    badpad = pc._Options(0, 1, 1, 0, 0, 0, 0, 9, (ctypes.c_int64 * 4)())
+    assert fit(opt=ctypes.byref(badpad)) == 1                    # sym_tile must be in [0, 8]
     # kernel matrix: ldk must be a multiple of 4 and >= n
     st = lib.popcorn_kernel_matrix(P.ctypes.data, 10, 2, 2, kern, 0, out.ctypes.data, 10, out.ctypes.data, None)
     assert st == 1

@@ -8,10 +8,12 @@ except near-ties, objective within the FP32 bar), and whole fits must agree with
 full-square pass up to FP32 summation order.  The cases cover a single ragged block,
 ragged n over several blocks, n a multiple of 128, k up to its bound (32), a kernel
 that is not positive semi-definite (symmetry is all the pass needs) and many blocks,
-each with every super-tile edge (1, 2, 4: a super-tile's row and column sums are kept
-over its a x a blocks before they are stored).  k <= 8 on single blocks runs the
-branch form (register sums per cluster); larger k, or a super-tile edge above 1, the
-run form (blocks walked in label order, one add per run of one label).  The images workload runs through it
+each with every super-tile edge (1, 2, 3, 4, 8: a super-tile's row and column sums are
+kept over its a x a blocks before they are stored; an edge the register file does not
+allow falls back to the full square).  k <= 8 with an edge of 1 runs the branch form
+(register sums per cluster); otherwise the sorted form runs (every block's labels
+sorted each pass, columns and rows walked cluster by cluster, the sums in registers
+over the super-tile).  The images workload runs through it
 at a tenth of its size against the full oracle step (FP32 build and the packed
 tensor-core BF16X3 build), and at full size (n = 70,000, 547 blocks per side) on
 sampled rows of E = K V^T that the oracle computes row by row, with every row's
@@ -52,7 +54,7 @@ CASES = [
     (1280, 4, 8, _gauss(1.0), 6),        # n a multiple of 128, k at the bound
     (700, 3, 5, POLY3_NEG, 7),           # negative entries: symmetry suffices
     (9001, 4, 5, _gauss(1.0), 5),        # 71 blocks per side
-    (1100, 7, 12, _gauss(2.0), 8),       # the run form from here on: ragged
+    (1100, 7, 12, _gauss(2.0), 8),       # k > 8: the sorted form at every edge; ragged
     (2500, 5, 16, _gauss(1.5), 9),
     (3000, 6, 10, POLY2, 10),
     (9001, 4, 16, _gauss(1.0), 11),
@@ -61,17 +63,25 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("sym_tile", [0, 1, 2, 4])
+def _sorted_max_a(k):
+    """Widest super-tile of the sorted form: its 4a consumer warps (two a block row, two a
+    block column), holding 2 KMAX register sums a lane, must fit the register file
+    (KMAX = 12, 16, 32 for k up to 12, 16, 32)."""
+    return 4 if k <= 16 else 3
+
+
+@pytest.mark.parametrize("sym_tile", [0, 1, 2, 3, 4, 8])
 @pytest.mark.parametrize("n,d,k,kern,seed", CASES)
 def test_symmetric_pass_is_the_oracle_step(pc, n, d, k, kern, seed, sym_tile):
     P = synth.gaussian_blobs(n, d, k, seed=seed, box=3.0)
     lab = synth.init_labels(n, k, seed=seed + 100)
     r = pc.popcorn_fit(torch.from_numpy(P).cuda(), k, kern, torch.from_numpy(lab).cuda(), max_iter=1,
                        check_convergence=False, k_pass="symmetric", sym_tile=sym_tile)
-    # single blocks always fit; a forced super-tile whose per-half column sums
-    # (a x 2 x k x 512 bytes) do not fit next to the block ring falls back to the full square
-    if sym_tile <= 1 or k * (1 + sym_tile) <= 64:
+    # a forced super-tile wider than the register file allows falls back to the full square
+    if sym_tile <= _sorted_max_a(k):
         assert r["info"]["k_pass_used"] == 1
+    else:
+        assert r["info"]["k_pass_used"] == 2
     if sym_tile and r["info"]["k_pass_used"] == 1:
         assert r["info"]["schedule"][0] == sym_tile
     Ko = oracle.kernel_matrix(P, kern)
@@ -133,20 +143,30 @@ def test_symmetric_pass_is_deterministic(pc, name, sym_tile):
 
 
 def test_symmetric_pass_launches_and_fallback(pc):
-    """k_pass = "symmetric" runs the stream and the fold (one launch more per pass than
-    the full square; the run form one more, its label sort) and is what "auto" picks for
-    an FP32 K with small k (here k = 6, slots far below L2); above the cluster bound (32),
-    or with a half-precision K, both fall back to the full-square pass, with results
+    """k_pass = "symmetric" runs the label sort, the stream and the fold (two launches more
+    per pass than the full square; the branch form, k <= 8 with a super-tile edge of 1,
+    one more).  "auto" picks the full square below 8,192 points (K fits L2 and a pass is
+    launch-bound) and the symmetric pass from there on.  Above the cluster bound (32), or
+    with a half-precision K, both fall back to the full-square pass, with results
     identical to it."""
     P = torch.from_numpy(synth.gaussian_blobs(600, 3, 6, seed=9, box=3.0)).cuda()
     lab = torch.from_numpy(synth.init_labels(600, 6, seed=19)).cuda()
     a = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_pass="symmetric")
+    br = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_pass="symmetric",
+                        sym_tile=1)
     b = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_pass="full")
     auto = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False)
-    assert a["info"]["k_pass_used"] == 1 and b["info"]["k_pass_used"] == 2 and auto["info"]["k_pass_used"] == 1
-    assert auto["objective"] == a["objective"]
-    assert a["info"]["kernel_launches"] == b["info"]["kernel_launches"] + a["iterations"] + 1
-    h = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_storage="fp16")
+    assert a["info"]["k_pass_used"] == 1 and br["info"]["k_pass_used"] == 1
+    assert b["info"]["k_pass_used"] == 2 and auto["info"]["k_pass_used"] == 2
+    assert auto["objective"] == b["objective"]
+    assert a["info"]["kernel_launches"] == b["info"]["kernel_launches"] + 2 * (a["iterations"] + 1)
+    assert br["info"]["kernel_launches"] == b["info"]["kernel_launches"] + br["iterations"] + 1
+    Pb = torch.from_numpy(synth.gaussian_blobs(9000, 3, 6, seed=9, box=3.0)).cuda()
+    labb = torch.from_numpy(synth.init_labels(9000, 6, seed=19)).cuda()
+    big = pc.popcorn_fit(Pb, 6, _gauss(1.0), labb, max_iter=2, check_convergence=False)
+    assert big["info"]["k_pass_used"] == 1
+    h = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_storage="fp16",
+                       k_pass="symmetric")
     assert h["info"]["k_pass_used"] == 2
     lab40 = torch.from_numpy(synth.init_labels(600, 40, seed=29)).cuda()
     c = pc.popcorn_fit(P, 40, _gauss(1.0), lab40, max_iter=5, check_convergence=False, k_pass="symmetric")
@@ -220,13 +240,13 @@ def test_images_tenth_symmetric_pass_is_the_oracle_step(pc, precision, rel):
     assert rel_err(b["objective"], oracle.objective(Ko, b["labels"].cpu().numpy(), wl.k)) <= rel
 
 
-@pytest.mark.parametrize("k_pass", ["auto", "symmetric"])
+@pytest.mark.parametrize("k_pass", ["auto", "full"])
 @pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 def test_full_size_images_pass_sampled(pc, precision, k_pass):
     """The images workload at full size (n = 70,000, d = 784, k = 10), one pass from the
-    initial labels, through the pass the bench times ("auto": the full square, K 19.6 GB)
-    and through the symmetric pass's run form (K block-packed, 547 blocks per side,
-    super-tiles of 4 x 4).  Sampled rows of E = K V^T (first, last, block edges,
+    initial labels, through the pass the bench times ("auto": the symmetric pass's sorted
+    form, K block-packed, 547 blocks per side, super-tiles of 4 x 4) and through the full
+    square (K 19.6 GB).  Sampled rows of E = K V^T (first, last, block edges,
     the ragged tail, random rows) against the oracle's K rows; J against the identity
     J = trace K - sum_c sum_{i in L_c} E_ic; and every row's new label against the argmin
     of D = K_ii - 2 E + ||c||^2 rebuilt from E in FP64 (near-ties exempt)."""
@@ -237,7 +257,7 @@ def test_full_size_images_pass_sampled(pc, precision, k_pass):
     E = torch.empty((n, k), dtype=torch.float32, device="cuda")
     r = pc.popcorn_fit(P, k, wl.kernel, L0, max_iter=1, check_convergence=False, history=True,
                        precision=precision, E_out=E, k_pass=k_pass)
-    if k_pass == "symmetric":
+    if k_pass == "auto":
         assert r["info"]["k_pass_used"] == 1 and r["info"]["schedule"][0] == 4
     else:
         assert r["info"]["k_pass_used"] == 2
@@ -262,14 +282,16 @@ def test_full_size_images_pass_sampled(pc, precision, k_pass):
     assert int(((got != pred) & ~exempt).sum()) == 0
 
 
-def test_run_form_launches_its_label_sort(pc):
-    """The run form adds one launch per pass (the per-pass sort of every block's labels)."""
+def test_sorted_form_launches_its_label_sort(pc):
+    """The sorted form adds two launches per pass to the full square's one (the per-pass
+    sort of every block's labels, then the stream, then the fold)."""
     P = torch.from_numpy(synth.gaussian_blobs(900, 3, 12, seed=4, box=3.0)).cuda()
     lab = torch.from_numpy(synth.init_labels(900, 12, seed=14)).cuda()
     a = pc.popcorn_fit(P, 12, _gauss(1.0), lab, max_iter=4, check_convergence=False, timing=True,
                        k_pass="symmetric")
     b = pc.popcorn_fit(P, 12, _gauss(1.0), lab, max_iter=4, check_convergence=False, timing=True, k_pass="full")
     auto = pc.popcorn_fit(P, 12, _gauss(1.0), lab, max_iter=4, check_convergence=False, timing=True)
-    assert auto["info"]["k_pass_used"] == 2          # k > 8: the full square unless forced
+    assert auto["info"]["k_pass_used"] == 2          # n < 8,192: the full square unless forced
     assert a["info"]["k_pass_used"] == 1 and b["info"]["k_pass_used"] == 2
+    assert a["info"]["schedule"][3] == 12            # the sorted form's register sums (KMAX)
     assert a["info"]["kernel_launches"] == b["info"]["kernel_launches"] + 2 * (a["iterations"] + 1)

@@ -7,13 +7,16 @@ rows.  The pass hands out super-tiles of a x a blocks: super-tile (Is, Js),
 Is <= Js, accumulates the row sums of each of its block rows over its columns and
 stores them to slot Js of those rows, and the column sums of each of its block
 columns over its rows, stored to slot Is of those rows -- or, for a diagonal
-super-tile with a > 1, to the extra slot Ts.  Every (slot, cluster, row) is
+super-tile of the sorted form, to the extra slot Ts.  Every (slot, cluster, row) is
 written exactly once, and the slots of a row add up to S.  This test builds the
-slots exactly as described (numpy, no GPU) for ragged n and every super-tile edge,
-and compares their sum with the plain definition, so a wrong slot, a missing block
-or a double-counted diagonal would show.  It also checks the block-packed, swizzled
-tile layout the K builds write and the stream's loads expect: every element of the
-triangle is stored once, at a distinct offset, inside its tile.
+slots exactly as the kernels order the blocks (numpy, no GPU) for ragged n and every
+super-tile edge, and compares their sum with the plain definition, so a wrong slot,
+a missing block or a double-counted diagonal would show.  It also checks the
+block-packed, swizzled tile layouts the K builds write and the streams' loads expect
+(every element of the triangle stored once, at a distinct offset, inside its tile),
+and the sorted form's per-block lists: the header, the padded entries and a lane's
+walk over them give the cluster sums of its rows and columns, with every read inside
+the list and the tile.
 """
 import numpy as np
 import pytest
@@ -21,11 +24,17 @@ import pytest
 B = 128
 
 
-def _slots(K, lab, k, a):
+def _slots(K, lab, k, a, extra_slot):
+    """The slots as the stream kernels store them.  Super-tile (Is, Js) is taken block by
+    block in the kernels' Latin-square order; row warp i keeps the row sums of block row
+    I0 + i over the super-tile's columns, column warp j the column sums of block column
+    J0 + j over its rows (diagonal blocks excluded), and each stores once at the end:
+    rows to slot Js, columns to slot Is, or to the extra slot Ts from a diagonal
+    super-tile.  The branch form (a = 1) has no extra slot and skips that store."""
     n = K.shape[0]
     T = (n + B - 1) // B
     Ts = (T + a - 1) // a
-    slots = np.full((Ts + (1 if a > 1 else 0), k, n), np.nan)
+    slots = np.full((Ts + (1 if extra_slot else 0), k, n), np.nan)
 
     def rows(I):
         return slice(I * B, min(n, I * B + B))
@@ -36,31 +45,42 @@ def _slots(K, lab, k, a):
 
     for Is in range(Ts):
         for Js in range(Is, Ts):
-            I0, I1, J0, J1 = Is * a, min(Is * a + a, T), Js * a, min(Js * a + a, T)
-            colacc = {J: np.zeros((k, rows(J).stop - rows(J).start)) for J in range(J0, J1)}
-            for I in range(I0, I1):
-                rowacc = np.zeros((k, rows(I).stop - rows(I).start))
-                for J in range(max(I, J0), J1):
+            I0, J0 = Is * a, Js * a
+            racc = {i: np.zeros((k, B)) for i in range(a)}
+            cacc = {j: np.zeros((k, B)) for j in range(a)}
+            seen = set()
+            for m in range(a):
+                for i in range(a):
+                    I, J = I0 + i, J0 + (i + m) % a
+                    if I >= T or J >= T or J < I:
+                        continue
+                    assert (I, J) not in seen
+                    seen.add((I, J))
                     blk = K[rows(I), rows(J)]
                     for c in range(k):
-                        rowacc[c] += blk[:, lab[rows(J)] == c].sum(axis=1)    # row sums
+                        racc[i][c, :blk.shape[0]] += blk[:, lab[rows(J)] == c].sum(axis=1)
                         if I != J:
-                            colacc[J][c] += blk[lab[rows(I)] == c, :].sum(axis=0)   # column sums
-                    if J == J1 - 1:
-                        store(Js, I, rowacc)
-                    if I == min(J, I1 - 1) and (I != J or a > 1):
-                        store(Ts if Is == Js else Is, J, colacc[J])
+                            cacc[J - J0][c, :blk.shape[1]] += blk[lab[rows(I)] == c, :].sum(axis=0)
+            want = {(I, J) for I in range(I0, min(I0 + a, T)) for J in range(max(I, J0), min(J0 + a, T))}
+            assert seen == want
+            for i in range(a):
+                if I0 + i < T:
+                    store(Js, I0 + i, racc[i][:, :rows(I0 + i).stop - rows(I0 + i).start])
+            for j in range(a):
+                J = J0 + j
+                if J < T and (Is != Js or extra_slot):
+                    store(Ts if Is == Js else Is, J, cacc[j][:, :rows(J).stop - rows(J).start])
     return slots
 
 
-@pytest.mark.parametrize("a", [1, 2, 4])
-@pytest.mark.parametrize("n,k", [(1, 1), (97, 3), (128, 2), (300, 4), (513, 8), (1100, 16)])
-def test_slots_sum_to_segment_sums(n, k, a):
+@pytest.mark.parametrize("a,extra", [(1, False), (1, True), (2, True), (3, True), (4, True), (7, True), (8, True)])
+@pytest.mark.parametrize("n,k", [(1, 1), (97, 3), (128, 2), (300, 4), (513, 8), (1100, 16), (2000, 5)])
+def test_slots_sum_to_segment_sums(n, k, a, extra):
     rng = np.random.default_rng(n * 31 + k)
     X = rng.standard_normal((n, 3))
     K = np.exp(-((X[:, None, :] - X[None, :, :]) ** 2).sum(-1))    # a symmetric K
     lab = rng.integers(0, k, size=n)
-    slots = _slots(K, lab, k, a)
+    slots = _slots(K, lab, k, a, extra)
     assert not np.isnan(slots).any()                                 # every slot written
     S = np.stack([K[:, lab == c].sum(axis=1) for c in range(k)])     # [c][i]
     np.testing.assert_allclose(slots.sum(axis=0), S, rtol=1e-12, atol=1e-12)
@@ -94,7 +114,7 @@ def test_packed_rows_of_a_chunk_hit_distinct_banks():
             assert len(groups) == 8
 
 
-# ---------------------------------------------------------------- the run form's layout and metadata
+# ---------------------------------------------------------------- the XOR-32 layout of the sorted form
 
 def _sw4_offset(r, c):
     """Float offset of element (r, c) of a tile in the XOR-32 packed layout: four boxes of
@@ -114,17 +134,19 @@ def test_sw4_layout_is_a_bijection_and_conflict_free():
             assert len({_sw4_offset(row, cc) % 32 for cc in range(b0, b0 + 32)}) == 32
 
 
-def test_sw4_codes_xor_keys_give_the_offsets():
-    """colcode(l) ^ (32 r + r mod 32) is the offset of (row r, column l), and
-    rowcode(l) ^ (4096 q + lane) that of (row l, column 32 q + lane)."""
+def test_sorted_entries_xor_keys_give_the_offsets():
+    """In bytes: the column entry of point l, 16384 (l >> 5) + 4 (l & 31), XOR 132 lane,
+    plus 4096 e, is element (row lane + 32 e, column l); the row entry 128 l + 4 (l & 31),
+    XOR 4 lane, plus 16384 e, is element (row l, column lane + 32 e).  All inside 64 KB."""
     for l in range(B):
-        colcode = ((l >> 5) << 12) | (l & 31)
-        rowcode = 32 * l + (l & 31)
-        for r in range(B):
-            assert colcode ^ (32 * r + (r & 31)) == _sw4_offset(r, l)
-        for q in range(4):
-            for lane in range(32):
-                assert rowcode ^ (4096 * q + lane) == _sw4_offset(l, 32 * q + lane)
+        colent = 16384 * (l >> 5) + 4 * (l & 31)
+        rowent = 128 * l + 4 * (l & 31)
+        for lane in range(32):
+            for e in range(4):
+                a = (colent ^ (132 * lane)) + 4096 * e
+                b = (rowent ^ (4 * lane)) + 16384 * e
+                assert a == 4 * _sw4_offset(lane + 32 * e, l) and 0 <= a < 65536
+                assert b == 4 * _sw4_offset(l, lane + 32 * e) and 0 <= b < 65536
 
 
 def test_sw4_float4_store_of_the_simt_build():
@@ -137,44 +159,94 @@ def test_sw4_float4_store_of_the_simt_build():
                 assert _sw4_offset(r, cl + e) == base + (e ^ (r & 3))
 
 
-def _meta(labels_block):
-    """The run form's metadata of one 128-block, as sym_meta_kernel defines it: the stable
-    sort of the block's labels (0xFF past the block's rows, sorting last), the label at
-    each sorted position, and the positions that end a run of one real label (the first
-    half also ends at 63)."""
+# ---------------------------------------------------------------- the sorted form's lists
+
+HDR = 32        # header words (u32, one per cluster)
+
+
+def _list_len(k):
+    return ((B + 3 * k + 3) & ~3) + 4
+
+
+def _sorted_lists(labels_block, k):
+    """One 128-block's lists as sym_sort_kernel writes them: a header word per cluster,
+    (start << 8) | count, then the entries cluster after cluster in stable order, each
+    cluster padded to a multiple of 4 with 0; the column list holds the byte offset
+    16384 (l >> 5) + 4 (l & 31) of point l as a column, the row list 128 l + 4 (l & 31)."""
     lab = np.asarray(labels_block)
-    order = np.argsort(lab, kind="stable")
-    slab = lab[order]
-    ends = np.zeros(B, bool)
-    for p in range(B):
-        if slab[p] != 0xFF and (p == B - 1 or slab[p + 1] != slab[p] or p == 63):
-            ends[p] = True
-    return order, slab, ends
+    L = _list_len(k)
+    cnt = [int(np.sum(lab == c)) for c in range(k)]
+    start = np.concatenate([[0], np.cumsum([(m + 3) & ~3 for m in cnt])])[:k]
+    colw = np.zeros(HDR + L, dtype=np.int64)
+    roww = np.zeros(HDR + L, dtype=np.int64)
+    for c in range(k):
+        colw[c] = roww[c] = (int(start[c]) << 8) | cnt[c]
+        for q, l in enumerate(np.nonzero(lab == c)[0]):
+            colw[HDR + start[c] + q] = 16384 * (l >> 5) + 4 * (l & 31)
+            roww[HDR + start[c] + q] = 128 * l + 4 * (l & 31)
+    return colw, roww
 
 
-def _sum_runs(values_in_order, slab, ends, k):
-    """What one lane computes for one block: the two halves' run sums added into per-half
-    cluster sums at each run end, then the halves added."""
-    acc = np.zeros((2, k))
-    for h in range(2):
-        run = 0.0
-        for p in range(64 * h, 64 * h + 64):
-            run += values_in_order[p]
-            if ends[p]:
-                acc[h, slab[p]] += run
-                run = 0.0
-    return acc[0] + acc[1]
+def _sum_sorted(tile_bytes_to_value, words, k, key, stride):
+    """What one lane of sum_sorted computes on one tile: for each cluster, chunks of 4
+    entries (the next chunk read ahead) and a tail of 1-3; element of entry x for the
+    lane's e-th row (column) at (x ^ key) + stride e.  Returns sums [k][4] and checks
+    that every list read stays inside the list and every element read inside the tile."""
+    L = len(words) - HDR
+    acc = np.zeros((k, 4))
+    for c in range(k):
+        h = int(words[c])
+        p0, cnt = h >> 8, h & 0xFF
+        pe = p0 + (cnt & ~3)
+
+        def chunk(p):
+            assert 0 <= p and p + 4 <= L
+            return [int(w) for w in words[HDR + p:HDR + p + 4]]
+
+        cw = chunk(p0)
+        p = p0
+        while p < pe:
+            cur, cw = cw, chunk(p + 4)
+            for x in cur:
+                for e in range(4):
+                    acc[c, e] += tile_bytes_to_value((x ^ key) + stride * e)
+            p += 4
+        for x in cw[:cnt & 3]:
+            for e in range(4):
+                acc[c, e] += tile_bytes_to_value((x ^ key) + stride * e)
+    return acc
 
 
 @pytest.mark.parametrize("valid,k,seed", [(128, 10, 0), (128, 1, 1), (77, 16, 2), (64, 3, 3), (63, 32, 4),
-                                          (1, 5, 5), (128, 32, 6)])
-def test_run_sums_are_the_cluster_sums(valid, k, seed):
+                                          (1, 5, 5), (128, 32, 6), (112, 12, 7), (128, 4, 8)])
+def test_sorted_lists_give_the_cluster_sums(valid, k, seed):
+    """Row warp (key 132 lane, stride 4096) and column warp (key 4 lane, stride 16384) of
+    the sorted form, on a tile in the XOR-32 layout: each lane's sums are the row
+    (column) cluster sums of its 4 rows (columns)."""
     rng = np.random.default_rng(seed)
     lab = np.full(B, 0xFF, dtype=np.int64)
     lab[:valid] = rng.integers(0, k, size=valid)
-    order, slab, ends = _meta(lab)
-    x = rng.standard_normal(B)
-    x[valid:] = np.nan                    # entries past the block's rows are never added
-    got = _sum_runs(x[order], slab, ends, k)
-    ref = np.array([x[:valid][lab[:valid] == c].sum() for c in range(k)])
-    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+    tile = rng.standard_normal((B, B))
+    tile[valid:, :] = np.nan              # entries past the block's points are never read
+    tile[:, valid:] = np.nan
+    mem = np.full(B * B, np.nan)
+    r, c = np.meshgrid(np.arange(B), np.arange(B), indexing="ij")
+    mem[_sw4_offset(r, c).ravel()] = tile.ravel()
+
+    def value(byte_off):
+        assert byte_off % 4 == 0 and 0 <= byte_off < 4 * B * B
+        return mem[byte_off // 4]
+
+    colw, roww = _sorted_lists(lab, k)
+    for lane in range(32):
+        mine = [lane + 32 * e for e in range(4)]
+        got = _sum_sorted(value, colw, k, 132 * lane, 4096)            # row warp: rows lane + 32 e
+        for e, rr in enumerate(mine):
+            if rr < valid:
+                ref = [tile[rr, :valid][lab[:valid] == cc].sum() for cc in range(k)]
+                np.testing.assert_allclose(got[:, e], ref, rtol=1e-12, atol=1e-12)
+        got = _sum_sorted(value, roww, k, 4 * lane, 16384)             # column warp: columns lane + 32 e
+        for e, cl in enumerate(mine):
+            if cl < valid:
+                ref = [tile[:valid, cl][lab[:valid] == cc].sum() for cc in range(k)]
+                np.testing.assert_allclose(got[:, e], ref, rtol=1e-12, atol=1e-12)
