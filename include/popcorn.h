@@ -113,27 +113,28 @@ typedef struct {
                                    recompute path of popcorn_fit (row blocks per tile, units
                                    per SM).  Results differ only by summation order.        */
     int32_t k_pass;             /* how a pass reads a stored FP32 K.  0 = automatic (the
-                                   default): the symmetric read below where it has measured
-                                   faster (FP32 K, k <= 4; k <= 8 while its per-block slots,
-                                   4 k n ceil(n / 128) bytes, stay within 64 MB), else the
-                                   full square.  1 = symmetric (FP32 K, k <= 32; larger k
-                                   falls back to the full square):
-                                   only the 128 x 128 blocks on and above the diagonal (K is
-                                   symmetric, and is then stored as that packed triangle); a
-                                   block's row sums serve its rows and its column sums its
-                                   columns' rows.  Blocks are taken in super-tiles of a x a
-                                   (sym_tile below); each super-tile writes one slot per row
-                                   it touches, and the slots are folded, so a pass reads half
-                                   of K plus about 8 k n ceil(n / 128a) bytes of slots; where
-                                   it does not apply the full square runs.  2 = the full
-                                   square, row by row (the paper's read of K).  The
-                                   recompute path has its own scheme.  Results differ only
-                                   by summation order                                       */
-    int32_t sym_tile;           /* super-tile edge a of the symmetric pass, in 128-blocks:
-                                   0 = automatic (the largest of 4, 2, 1 that leaves about 16
-                                   super-tiles per SM); 1, 2 or 4 to force one (a forced
-                                   edge whose shared memory does not fit falls back to the
-                                   full square)                                            */
+                                   default): the symmetric read below for n >= 8192 (where K
+                                   outgrows L2 and reading half of it pays; measured faster
+                                   on GB300 for every k up to 32), else the full square.
+                                   1 = symmetric (FP32 K, k <= 32; larger k, or a half-
+                                   precision K, falls back to the full square): only the
+                                   128 x 128 blocks on and above the diagonal (K is symmetric,
+                                   and is then stored as that packed triangle); a block's row
+                                   sums serve its rows and its column sums its columns' rows.
+                                   Blocks are taken in super-tiles of a x a (sym_tile below),
+                                   each block's labels sorted once a pass; each super-tile
+                                   writes one slot per row it touches, and the slots are
+                                   folded, so a pass reads half of K plus about
+                                   8 k n ceil(n / 128a) bytes of slots.  2 = the full square,
+                                   row by row (the paper's read of K).  The recompute path has
+                                   its own scheme.  Results differ only by summation order  */
+    int32_t sym_tile;           /* super-tile edge a of the symmetric pass, in 128-blocks,
+                                   0..8: 0 = automatic (the widest the register file allows,
+                                   4 for k <= 16 and 3 for k <= 32, narrowed until there are
+                                   at least 4 super-tiles per SM); 1..8 to force one (an edge
+                                   wider than the register file allows falls back to the full
+                                   square).  k <= 8 with an edge of 1 runs the branch form
+                                   (single blocks, a uniform branch per label)              */
     int64_t reserved[4];        /* must be zero                                              */
 } popcorn_options;
 
@@ -164,7 +165,9 @@ typedef struct {
                                   recompute: {row blocks per tile, column segments,
                                               units per SM target, 0};
                                   symmetric pass: {super-tile edge, block ring depth,
-                                                   slots, register accumulators per row};
+                                                   slots, register sums per row: 4 or 8
+                                                   in the branch form, 12, 16 or 32 in
+                                                   the sorted form};
                                   zeros otherwise                                           */
     double fold_ms;            /* symmetric pass: the slot fold kernel, summed over passes
                                   (part of reduce_ms), when timing = 1                      */

@@ -275,7 +275,7 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
     type of a stored K.  ``k_pass`` ("auto", "symmetric", "full") is how a pass
     reads a stored FP32 K; ``timing`` (False, True / "kernels", "phases") records CUDA-event
     times per phase and kernel, or per phase only (which leaves a fixed-iteration fit's passes
-    in one CUDA graph); ``sym_tile`` (0 = automatic, 1, 2, 4) is the super-tile edge of
+    in one CUDA graph); ``sym_tile`` (0 = automatic, else 1..8) is the super-tile edge of
     the symmetric pass.  ``E_out`` (an (n, k) float32 CUDA tensor) receives E = K V^T of the
     labels the last pass started from (stored-K fits).  Returns {"labels", "objective",
     "iterations", "info"};
