@@ -18,6 +18,7 @@
 // coordinate differences, a subtract and a multiply-add per pair and
 // coordinate, which keeps full relative accuracy for near-duplicate points.
 #include "popcorn_internal.cuh"
+#include "tc_common.cuh"
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -161,11 +162,20 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         S[l + 3][fr] = v.w;
     };
 
+    // The dot-product kinds on 16 x 8 outputs keep their sums as f32x2 pairs (rows 2i and
+    // 2i + 1 of column y): one fma.rn.f32x2 does two multiply-adds, which halves the
+    // instructions the FMA pipe is fed with (each lane rounds exactly as fma.rn.f32).
+    constexpr bool PAIRS = RPT == 16 && KIND != POPCORN_GAUSSIAN;
     float acc[RPT][8];
+    unsigned long long acc2[PAIRS ? RPT / 2 : 1][8];
 #pragma unroll
     for (int x = 0; x < RPT; ++x)
 #pragma unroll
         for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+#pragma unroll
+    for (int i = 0; i < (PAIRS ? RPT / 2 : 1); ++i)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc2[i][y] = 0ull;
 
     float4 na[NF], nb[NF];
 #pragma unroll
@@ -203,17 +213,29 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
             const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][l][tx * 4]);
             const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][l][64 + tx * 4]);
             b[0] = b0.x, b[1] = b0.y, b[2] = b0.z, b[3] = b0.w, b[4] = b1.x, b[5] = b1.y, b[6] = b1.z, b[7] = b1.w;
+            if constexpr (PAIRS) {
+                unsigned long long bb[8];
 #pragma unroll
-            for (int x = 0; x < RPT; ++x)
+                for (int y = 0; y < 8; ++y) bb[y] = tc::f2pack(b[y], b[y]);
 #pragma unroll
-                for (int y = 0; y < 8; ++y) {
-                    if constexpr (KIND == POPCORN_GAUSSIAN) {
-                        float t = a[x] - b[y];
-                        acc[x][y] = fmaf(t, t, acc[x][y]);
-                    } else {
-                        acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
-                    }
+                for (int i = 0; i < RPT / 2; ++i) {
+                    const unsigned long long aa = tc::f2pack(a[2 * i], a[2 * i + 1]);
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) acc2[i][y] = tc::f2fma(aa, bb[y], acc2[i][y]);
                 }
+            } else {
+#pragma unroll
+                for (int x = 0; x < RPT; ++x)
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) {
+                        if constexpr (KIND == POPCORN_GAUSSIAN) {
+                            float t = a[x] - b[y];
+                            acc[x][y] = fmaf(t, t, acc[x][y]);
+                        } else {
+                            acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+                        }
+                    }
+            }
         }
         if (more) {
             // the other buffer was last read before the previous barrier
@@ -225,6 +247,12 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         }
         __syncthreads();
         buf ^= 1;
+    }
+    if constexpr (PAIRS) {
+#pragma unroll
+        for (int i = 0; i < RPT / 2; ++i)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) tc::f2unpack(acc2[i][y], acc[2 * i][y], acc[2 * i + 1][y]);
     }
     // epilogue: kappa, diagonal, store tile and (off-diagonal tiles) its transpose
     if constexpr (KIND == kGaussExpand) {
