@@ -53,6 +53,7 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 GB300_SMS = 152
 FP32_LANES_PER_CLK_SM = 128          # FP32 FMA/ADD lanes per clock per SM
 XU_EX2_PER_CLK_SM = 32               # ex2.approx per clock per SM (microbenchmark)
+L2_INGEST_B_PER_CLK_SM = 36          # bytes per clock an SM takes in from L2 (microbenchmark)
 
 
 def aggregate_over_ranks(times, counts, dist, device):
@@ -178,6 +179,19 @@ def pass_roofline(wl, prof, pk):
                 "pass_avg_ms": (red + sum(r["info"]["assign_ms"] for r in prof)) / max(passes, 1),
                 "schedule": {"super_tile": info["schedule"][0], "ring": info["schedule"][1],
                              "slots": info["schedule"][2], "accumulators": info["schedule"][3]}}
+    if info["k_pass_used"] == 3:
+        # the whole fit in one launch (K in L2): a pass reads the full square from L2; the
+        # ceiling is what the SMs can take in from L2, 36 bytes per clock per SM (measured
+        # by stand-alone probes), and at this size the pass is mostly grid-barrier latency
+        ms = sum(r["info"]["loop_ms"] for r in prof) / max(passes, 1)
+        alg = 4.0 * n * n + n
+        ach = alg / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        peak = L2_INGEST_B_PER_CLK_SM * GB300_SMS * pk["sm_mhz"] * 1e6 / 1e9
+        return {"kernel": "fit_fused_kernel", "bound": "l2", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": f"{L2_INGEST_B_PER_CLK_SM} B/clk/SM L2 ingest (probe) x {GB300_SMS} SMs x "
+                               f"{pk['sm_mhz']:.0f} MHz",
+                "algorithmic_bytes_per_pass": alg, "pass_avg_ms": ms}
     ms = red / max(passes, 1)
     alg = 4.0 * n * n + n
     ach = alg / (ms / 1e3) / 1e9 if ms > 0 else 0.0
@@ -209,8 +223,11 @@ def kbuild_roofline(wl, precision, kb_ms, pk):
         ops = per * n * (n + 1) / 2 * d
         peak = FP32_LANES_PER_CLK_SM * GB300_SMS * pk["sm_mhz"] * 1e6 / 1e12
         ach = ops / sec / 1e12
-        return {"kernel": "kbuild_simt_kernel", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tlane-ops/s",
-                "frac": ach / peak, "traffic": recorded_traffic("kbuild_simt_kernel", "kbuild_simt.cu", wl.name),
+        # d > 16 with a dot-product form (linear, polynomial, Gaussian by the norm expansion)
+        # runs the 16 x 8 f32x2 tile; coordinate differences and d <= 16 the other kernels
+        kern = "kbuild_dot_kernel" if wl.d > 16 and per == 1.0 else "kbuild_simt_kernel"
+        return {"kernel": kern, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tlane-ops/s",
+                "frac": ach / peak, "traffic": recorded_traffic(kern, "kbuild_simt.cu", wl.name),
                 "peak_source": f"{FP32_LANES_PER_CLK_SM} FP32 lanes/clk/SM x {GB300_SMS} SMs x "
                                f"{pk['sm_mhz']:.0f} MHz (unit counts and clock)",
                 "algorithmic_lane_ops_per_launch": ops, "avg_launch_ms": kb_ms, "distance_form": form}
@@ -419,7 +436,8 @@ def fit_form(pc, torch, stream, wl, P, lab, out, precision, steps, warmup, **kw)
                         "kbuild_tflops": float(n) * (n + 1) * d / (kb_ms / 1e3) / 1e12 if kb_ms > 0 else None,
                         "kbuild_tflops_gemm_equivalent": 2.0 * n * n * d / (kb_ms / 1e3) / 1e12 if kb_ms > 0 else None,
                         "breakdown_ms_per_fit": {"kbuild": kb_ms, "reduce": red, "assign": asg},
-                        "k_pass": {0: "recompute", 1: "symmetric", 2: "full"}[prof[-1]["info"]["k_pass_used"]],
+                        "k_pass": {0: "recompute", 1: "symmetric", 2: "full", 3: "fused fit (full square, one launch)"}[
+                            prof[-1]["info"]["k_pass_used"]],
                         "gpu_launches_per_fit": res[-1]["info"]["kernel_launches"]}}
 
 
