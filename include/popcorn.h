@@ -171,7 +171,10 @@ typedef struct {
                                   zeros otherwise                                           */
     double fold_ms;            /* symmetric pass: the slot fold kernel, summed over passes
                                   (part of reduce_ms), when timing = 1                      */
-    int32_t k_pass_used;       /* stored K: 1 = symmetric pass, 2 = full square; 0 recompute */
+    int32_t k_pass_used;       /* stored K: 1 = symmetric pass, 2 = full square, 3 = the whole
+                                  fit in one cooperative launch (automatic choice for an FP32
+                                  K that sits in L2: n <= 6144, k <= 32; it reads the full
+                                  square); 0 recompute                                     */
     int32_t reserved_info;     /* zero                                                     */
     float* E_out;              /* caller-provided DEVICE array of n x k floats (row-major,
                                   ld = k), or NULL.  Stored-K fits with max_iter >= 1: E =

@@ -54,6 +54,7 @@ struct DeviceInfo {
     int reduce_smem = 0;   // dynamic shared memory usable by the reduction kernel
     int recompute_smem = 0;
     int batched_smem = 0;
+    bool coop = false;   // cooperative launches (all CTAs of a grid resident at once)
     cudaMemPool_t pool = nullptr;
     bool ready = false;
 };
@@ -85,6 +86,10 @@ popcorn_status device_info(DeviceInfo** out) {
         POPCORN_CUDA(configure_recompute(d.smem_optin, &d.recompute_smem));
         POPCORN_CUDA(configure_batched(d.smem_optin));
         POPCORN_CUDA(configure_reduce_sym(d.smem_optin));
+        POPCORN_CUDA(configure_fused_fit(d.smem_optin));
+        int coop = 0;
+        POPCORN_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        d.coop = coop != 0;
         d.batched_smem = d.smem_optin - 1024;
         d.ready = true;
     }
@@ -841,8 +846,22 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // microseconds).  A caller that is itself capturing s gets the plain launches.
     cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
     POPCORN_CUDA(cudaStreamIsCapturing(s, &cap_status));
-    const bool use_graph =
-        !opt.check_convergence && !kernel_events && max_iter > 0 && cap_status == cudaStreamCaptureStatusNone;
+    // An FP32 K that sits in L2 (the automatic choice only): the whole fit -- every pass and
+    // the final objective -- in one cooperative launch, with grid barriers between the
+    // phases of a pass instead of three launches a pass.
+    const bool fused = !use_sym && opt.k_pass == 0 && ks == POPCORN_K_FP32 && dev->coop &&
+                       cap_status == cudaStreamCaptureStatusNone &&
+                       fused_fit_applies(ni, k, dev->sms, dev->smem_optin);
+    if (fused) {
+        double* fz;
+        unsigned* fbar;
+        POPCORN_TRY(ws.alloc(&fz, (size_t)dev->sms * k, "fused-fit partials"));
+        POPCORN_TRY(ws.alloc(&fbar, fused_xchg_words(dev->sms, k), "exchange slots"));
+        POPCORN_CUDA(launch_fused_fit(b, fz, fbar, dev->sms, dev->smem_optin, s));
+        launches += 1;
+    }
+    const bool use_graph = !fused && !opt.check_convergence && !kernel_events && max_iter > 0 &&
+                           cap_status == cudaStreamCaptureStatusNone;
     cudaGraphExec_t pass_exec = nullptr;
     struct ExecGuard {
         cudaGraphExec_t* e;
@@ -887,7 +906,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         POPCORN_TRY(g_events.get(&poll_ev[0]));
         POPCORN_TRY(g_events.get(&poll_ev[1]));
     }
-    int launched = use_graph ? max_iter : 0, pending = -1, slot = 0;
+    int launched = (use_graph || fused) ? max_iter : 0, pending = -1, slot = 0;
     while (launched < max_iter) {
         const int m = (max_iter - launched < chunk) ? (max_iter - launched) : chunk;
         for (int t = 0; t < m; ++t) {
@@ -934,7 +953,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     }
     // J(labels_out): reuses J of the last pass when it changed nothing (in the graph above
     // when there is one)
-    if (!use_graph) {
+    if (!use_graph && !fused) {
         POPCORN_CUDA(reduce_pass(1, nullptr, s));
         launches += red_launches;
     }
@@ -957,7 +976,8 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     memcpy(&hs, hs_pin, sizeof hs);
     if (hs.bad_label) return fail(POPCORN_ERR_INVALID, "an initial label is outside [0, %d)", k);
     if (hs.wait_err)
-        return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the tensor-core K build or the symmetric pass ran out");
+        return fail(POPCORN_ERR_TIMEOUT,
+                    "a bounded wait in the tensor-core K build, the symmetric pass or a grid barrier ran out");
     *objective_out = hs.J_eval;
     *iterations_out = hs.iter;
 
@@ -1004,7 +1024,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
             for (size_t t = 0; t + 1 < ev_f.size() && t < 2 * (size_t)iters; t += 2) f += elapsed(ev_f[t], ev_f[t + 1]);
             info->fold_ms = f;
         }
-        info->k_pass_used = use_sym ? 1 : 2;
+        info->k_pass_used = fused ? 3 : use_sym ? 1 : 2;
     }
     return POPCORN_OK;
 }

@@ -204,6 +204,21 @@ __device__ __forceinline__ bool pass_skip(const LoopState* st, int eval) {
     return eval ? (st->iter > 0 && st->last_changed == 0) : (st->done != 0);
 }
 
+// ---- whole fits in one cooperative launch (fused_fit.cu) ----------------------
+// For a stored FP32 K that sits in L2 (n <= kFusedMaxN, k <= kFusedMaxK): every pass of
+// the fit and the final objective in one launch of one CTA per SM, two exchanges between
+// the CTAs a pass; same pass semantics and outputs (labels, LoopState, J / change
+// histories, E) as the launched passes.  zpart: num_sms x k doubles; xchg:
+// fused_xchg_words(num_sms, k) words of workspace.
+constexpr int kFusedMaxN = 6144;
+constexpr int kFusedMaxK = 32;
+bool fused_fit_applies(int n, int k, int num_sms, int smem_optin);
+size_t fused_fit_smem(int n, int k, int num_sms, int64_t ldk, int cache_k);
+size_t fused_xchg_words(int num_sms, int k);
+cudaError_t configure_fused_fit(int smem_optin);
+cudaError_t launch_fused_fit(const struct PassBuffers& b, double* zpart, unsigned* xchg, int num_sms, int smem_optin,
+                             cudaStream_t s);
+
 // ---- recompute path (recompute.cu): K never stored ---------------------------
 struct RecomputePlan {
     int fp8;            // 1: E4M3 operands with per-row scales; 0: BF16

@@ -243,15 +243,23 @@ def test_fit_stopping_rules(pc):
     assert rt["iterations"] == ot["iterations"]
 
 
-def test_fit_repeatable_and_timing_info(pc):
+@pytest.mark.parametrize("k_pass", ["full", "auto"])
+def test_fit_repeatable_and_timing_info(pc, k_pass):
+    """Per-kernel timing of the launched passes ("full"), and of the one-launch fit that the
+    automatic choice takes at this size (n = 2,000: its passes are inside one kernel, so only
+    the build and the loop are timed)."""
     wl = synth.workload("rings", scale=0.1)
     P, lab = _dev(wl.P), _dev(wl.init_labels)
-    a = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=50, timing=True)
-    b = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=50)
+    a = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=50, timing=True, k_pass=k_pass)
+    b = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=50, k_pass=k_pass)
     assert torch.equal(a["labels"], b["labels"]) and a["objective"] == b["objective"]
     inf = a["info"]
     assert inf["reduce_launches"] >= a["iterations"] and inf["assign_launches"] == a["iterations"]
-    assert inf["kbuild_ms"] > 0 and inf["reduce_ms"] > 0 and inf["loop_ms"] >= inf["reduce_ms"]
+    assert inf["kbuild_ms"] > 0 and inf["loop_ms"] > 0
+    if k_pass == "full":
+        assert inf["k_pass_used"] == 2 and inf["reduce_ms"] > 0 and inf["loop_ms"] >= inf["reduce_ms"]
+    else:
+        assert inf["k_pass_used"] == 3 and inf["reduce_ms"] == 0
 
 
 # ------------------------------------------------------------------ full-size checks
@@ -316,8 +324,8 @@ def test_fit_reports_nomem_and_stays_usable(pc):
     assert r["iterations"] >= 1
 
 
-@pytest.mark.parametrize("name,scale,k_pass", [("blobs", 1.0, "auto"), ("rings", 0.2, "symmetric"),
-                                               ("rings", 0.2, "full"), ("images", 0.03, "auto")])
+@pytest.mark.parametrize("name,scale,k_pass", [("blobs", 1.0, "full"), ("rings", 0.2, "symmetric"),
+                                               ("rings", 0.2, "full"), ("images", 0.03, "full")])
 def test_fixed_iteration_graph_equals_plain_launches(pc, name, scale, k_pass):
     """A fixed-iteration fit without per-kernel events runs all its passes and the objective
     pass as one CUDA graph.  The kernels, their arguments and their order are those of the
