@@ -129,12 +129,12 @@ typedef struct {
                                    row by row (the paper's read of K).  The recompute path has
                                    its own scheme.  Results differ only by summation order  */
     int32_t sym_tile;           /* super-tile edge a of the symmetric pass, in 128-blocks,
-                                   0..8: 0 = automatic (the widest the register file allows,
-                                   4 for k <= 16 and 3 for k <= 32, narrowed until there are
-                                   at least 4 super-tiles per SM); 1..8 to force one (an edge
-                                   wider than the register file allows falls back to the full
-                                   square).  k <= 8 with an edge of 1 runs the branch form
-                                   (single blocks, a uniform branch per label)              */
+                                   0..8: 0 = automatic (4 for k <= 16 and 3 for k <= 32,
+                                   narrowed until there are at least 4 super-tiles per SM);
+                                   1..8 to force one (6 or 8 for k <= 12 gives each warp two
+                                   block rows; an edge the register file does not allow falls
+                                   back to the full square).  k <= 8 with an edge of 1 runs
+                                   the branch form (single blocks, a uniform branch a label) */
     int64_t reserved[4];        /* must be zero                                              */
 } popcorn_options;
 

@@ -84,6 +84,7 @@ struct SymPlan {
     size_t meta_bytes;  // sorted form: per-pass label-sorted lists of every block (column and row lists)
     int kb;             // register sums per row / column: 4 or 8 (branch form), 12, 16 or 32 (sorted form); >= k
     int rpl;            // sorted form: rows (columns) a lane owns in a block, 4 or 2 (2: two warps a block row)
+    int pw;             // sorted form: block rows (columns) of the super-tile a warp owns, 1 or 2
     int T;              // 128-blocks per side
     int a;              // super-tile edge in blocks (1, 2, 4 or 8)
     int Ts;             // super-tiles per side

@@ -514,18 +514,22 @@ __device__ __forceinline__ void sum_sorted(const unsigned char* __restrict__ til
     }
 }
 
-// Register sums per lane (R KMAX) against the register file: an SM sub-partition holds
-// 16384 registers for its share of the CTA's warps (2a (4 / R) consumers + 1), so the
+// Register sums per lane (P R KMAX) against the register file: an SM sub-partition holds
+// 16384 registers for its share of the CTA's warps (2a (4 / R) / P consumers + 1), so the
 // widest super-tile edge with 4 rows a lane is 8 for KMAX = 12 (96 registers a thread),
 // 7 for 16 (128) and 3 for 32 (255); with 2 rows a lane (two warps share a block row or
-// column) it is 4 for KMAX <= 16 (96) and 3 for 32 (128).
-__host__ __device__ constexpr int sorted_max_a(int kmax, int rpl) {
-    return rpl == 4 ? (kmax <= 12 ? 8 : kmax <= 16 ? 7 : 3) : (kmax <= 16 ? 4 : 3);
+// column) it is 4 for KMAX <= 16 (96) and 3 for 32 (128), and 8 for KMAX = 12 when each
+// warp owns two block rows (columns) of the super-tile (P = 2: rows i and i + a / 2).
+__host__ __device__ constexpr int sorted_max_a(int kmax, int rpl, int pw = 1) {
+    return rpl == 4 ? (kmax <= 12 ? 8 : kmax <= 16 ? 7 : 3)
+                    : (pw == 2 ? (kmax <= 12 ? 8 : 0) : (kmax <= 16 ? 4 : 3));
 }
-__host__ __device__ constexpr int sorted_threads(int a, int rpl) { return 32 * (2 * a * (4 / rpl) + 1); }
+__host__ __device__ constexpr int sorted_threads(int a, int rpl, int pw = 1) {
+    return 32 * (2 * a * (4 / rpl) / pw + 1);
+}
 
-template <int KMAX, int R>
-__global__ void __launch_bounds__(sorted_threads(sorted_max_a(KMAX, R), R), 1)
+template <int KMAX, int R, int P>
+__global__ void __launch_bounds__(sorted_threads(sorted_max_a(KMAX, R, P), R, P), 1)
     reduce_sym_sorted_kernel(SortedArgs a) {
     grid_dependency_wait();   // the block lists and the loop state come from before this pass
     if (pass_skip(a.st, a.eval_only)) return;
@@ -534,7 +538,8 @@ __global__ void __launch_bounds__(sorted_threads(sorted_max_a(KMAX, R), R), 1)
     const uint32_t sbase = tc::smem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int H = 4 / R;   // warps per block row (column)
-    const int A = a.a, nw = 2 * A * H, S = a.stages;
+    const int A = a.a, nw = 2 * A * H / P, S = a.stages;
+    const int AP = A / P;      // a warp owns block rows (columns) mine + AP q, q < P
     const int n = a.n, k = a.k, T = a.T;
     auto full_bar = [&](int s) { return sbase + (uint32_t)a.off_bars + 8u * s; };
     auto empty_bar = [&](int s) { return sbase + (uint32_t)a.off_bars + 8u * (S + s); };
@@ -617,9 +622,9 @@ __global__ void __launch_bounds__(sorted_threads(sorted_max_a(KMAX, R), R), 1)
     }
 
     const uint64_t keep = tc::l2_evict_last();   // the slots are read back by the fold
-    const bool roww = warp < A * H;
-    const int wr = roww ? warp : warp - A * H;
-    const int mine = wr / H;          // block row (column) of the super-tile
+    const bool roww = warp < AP * H;
+    const int wr = roww ? warp : warp - AP * H;
+    const int mine = wr / H;          // block row (column) of the super-tile, + AP q
     const int part = wr % H;          // this warp's rows (columns): 32 (R part + e) + lane, e < R
     const uint32_t key = roww ? 132u * (uint32_t)lane : 4u * (uint32_t)lane;
     int s = 0;
@@ -627,11 +632,13 @@ __global__ void __launch_bounds__(sorted_threads(sorted_max_a(KMAX, R), R), 1)
     bool alive = true;
     for (long long u = blockIdx.x; u < a.units && alive; u += G) {
         const Unit w = unit_of(u, A, a.Ts);
-        float acc[KMAX][R];
+        float acc[P][KMAX][R];
 #pragma unroll
-        for (int c = 0; c < KMAX; ++c)
+        for (int q = 0; q < P; ++q)
 #pragma unroll
-            for (int e = 0; e < R; ++e) acc[c][e] = 0.f;
+            for (int c = 0; c < KMAX; ++c)
+#pragma unroll
+                for (int e = 0; e < R; ++e) acc[q][c][e] = 0.f;
         for (int m = 0; m < A && alive; ++m)
             for (int i = 0; i < A; ++i) {
                 int I, J;
@@ -641,17 +648,27 @@ __global__ void __launch_bounds__(sorted_threads(sorted_max_a(KMAX, R), R), 1)
                     break;
                 }
                 const unsigned char* stage = smem + (size_t)s * a.stage_bytes;
-                if (roww) {
-                    // row sums of block I over the columns of block J, by the column list of J
-                    if (i == mine)
-                        sum_sorted<KMAX, R, 4096>(stage + 4096 * R * part,
-                                                  reinterpret_cast<const uint32_t*>(stage + kTileBytes), k, key, acc);
-                } else if (J - w.J0 == mine && I != J) {
-                    // column sums of block J over the rows of block I, by the row list of I (a
-                    // diagonal block's row sums already cover it)
-                    sum_sorted<KMAX, R, 16384>(stage + 16384 * R * part,
-                                               reinterpret_cast<const uint32_t*>(stage + kTileBytes + a.meta_bytes), k,
-                                               key, acc);
+                // the accumulator set of this block row (column) when this warp owns it
+                const int x = roww ? i : J - w.J0;
+                const int q = x / AP;
+                if (x - AP * q == mine && (roww || I != J)) {
+                    // row warps: row sums of block I over the columns of block J, by the column
+                    // list of J; column warps: column sums of block J over the rows of block I,
+                    // by the row list of I (a diagonal block's row sums already cover it)
+                    const unsigned char* tile = stage + (roww ? 4096 : 16384) * R * part;
+                    const uint32_t* hdr =
+                        reinterpret_cast<const uint32_t*>(stage + kTileBytes + (roww ? 0 : a.meta_bytes));
+                    if (roww) {
+                        if (P == 1 || q == 0)
+                            sum_sorted<KMAX, R, 4096>(tile, hdr, k, key, acc[0]);
+                        else
+                            sum_sorted<KMAX, R, 4096>(tile, hdr, k, key, acc[P - 1]);
+                    } else {
+                        if (P == 1 || q == 0)
+                            sum_sorted<KMAX, R, 16384>(tile, hdr, k, key, acc[0]);
+                        else
+                            sum_sorted<KMAX, R, 16384>(tile, hdr, k, key, acc[P - 1]);
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(empty_bar(s));
@@ -664,17 +681,20 @@ __global__ void __launch_bounds__(sorted_threads(sorted_max_a(KMAX, R), R), 1)
         // one store per row (column) and cluster: row sums to slot Js of the rows of block
         // row I; column sums to slot Is of the rows of block column J, or to the extra slot
         // Ts from a super-tile on the diagonal (its rows also take row sums into slot Js)
-        const int X = (roww ? w.I0 : w.J0) + mine;
-        if (X < T) {
-            const int slot = roww ? w.Js : (w.Is == w.Js ? a.Ts : w.Is);
-            const int r0 = X * kB + 32 * R * part + lane;   // this lane's rows (columns): r0 + 32 e
-            float* out = a.Spart + (size_t)slot * k * n + r0;
+        const int slot = roww ? w.Js : (w.Is == w.Js ? a.Ts : w.Is);
 #pragma unroll
-            for (int c = 0; c < KMAX; ++c) {
-                if (c < k) {
+        for (int q = 0; q < P; ++q) {
+            const int X = (roww ? w.I0 : w.J0) + mine + AP * q;
+            if (X < T) {
+                const int r0 = X * kB + 32 * R * part + lane;   // this lane's rows (columns): r0 + 32 e
+                float* out = a.Spart + (size_t)slot * k * n + r0;
 #pragma unroll
-                    for (int e = 0; e < R; ++e)
-                        if (r0 + 32 * e < n) tc::st_hint(out + (size_t)c * n + 32 * e, acc[c][e], keep);
+                for (int c = 0; c < KMAX; ++c) {
+                    if (c < k) {
+#pragma unroll
+                        for (int e = 0; e < R; ++e)
+                            if (r0 + 32 * e < n) tc::st_hint(out + (size_t)c * n + 32 * e, acc[q][c][e], keep);
+                    }
                 }
             }
         }
@@ -767,9 +787,10 @@ cudaError_t configure_reduce_sym(int smem_optin) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(reduce_sym_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
-    void (*sorted[6])(SortedArgs) = {reduce_sym_sorted_kernel<12, 4>, reduce_sym_sorted_kernel<16, 4>,
-                                     reduce_sym_sorted_kernel<32, 4>, reduce_sym_sorted_kernel<12, 2>,
-                                     reduce_sym_sorted_kernel<16, 2>, reduce_sym_sorted_kernel<32, 2>};
+    void (*sorted[7])(SortedArgs) = {reduce_sym_sorted_kernel<12, 4, 1>, reduce_sym_sorted_kernel<16, 4, 1>,
+                                     reduce_sym_sorted_kernel<32, 4, 1>, reduce_sym_sorted_kernel<12, 2, 1>,
+                                     reduce_sym_sorted_kernel<16, 2, 1>, reduce_sym_sorted_kernel<32, 2, 1>,
+                                     reduce_sym_sorted_kernel<12, 2, 2>};
     for (auto f : sorted)
         if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
             return e;
@@ -808,15 +829,24 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, in
     // the widest super-tile whose consumer warps fit the register file and that leaves at
     // least 4 super-tiles per SM for balance
     p.rpl = kSortedRowsPerLane;
-    const int amax = sorted_max_a(p.kb, p.rpl);
-    int cand_a[5] = {amax, 4, 3, 2, 1}, na = 5;
+    // edges above 4 with 2 rows a lane: each warp owns two block rows (columns), even edges only
+    auto pw_of = [&](int A) { return p.rpl == 2 && A > 4 ? 2 : 1; };
+    auto fits = [&](int A) {
+        const int pw = pw_of(A);
+        return A >= 1 && A % pw == 0 && A <= sorted_max_a(p.kb, p.rpl, pw);
+    };
+    // automatic: 4 x 4 at most with 2 rows a lane -- the 8 x 8 form (two block rows a warp)
+    // halves the slots but measured slower on images (stream 1.94 ms against 1.70 ms, fold
+    // 0.059 against 0.089), so it runs only when asked for
+    int cand_a[6] = {8, 7, 4, 3, 2, 1}, na = 6;
+    if (p.rpl == 2) cand_a[0] = cand_a[1] = 4;
     if (a_req > 0) {
         cand_a[0] = a_req;
         na = 1;
     }
     for (int ia = 0; ia < na; ++ia) {
         const int A = cand_a[ia];
-        if (A < 1 || A > amax) continue;
+        if (!fits(A)) continue;
         const int Ts = (p.T + A - 1) / A;
         const long long units = (long long)Ts * (Ts + 1) / 2;
         if (a_req == 0 && A > 1 && units < 4LL * num_sms) continue;
@@ -828,6 +858,7 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, in
             const int bytes = sorted_layout(k, S).bytes;
             if (bytes > smem_optin) continue;
             p.a = A;
+            p.pw = pw_of(A);
             p.Ts = Ts;
             p.units = units;
             p.stages = S;
@@ -873,13 +904,14 @@ cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, 
         r.eval_only = eval_only;
         r.stall_block = stall_ms > 0 ? 1 : 0;
         r.wait_ns = stall_ms > 0 ? (unsigned long long)stall_ms * 1000000ull : tc::kWaitLimitNs;
-        const dim3 block((unsigned)sorted_threads(p.a, p.rpl));
-        void (*f)(SortedArgs) = p.rpl == 4 ? (p.kb == 12   ? reduce_sym_sorted_kernel<12, 4>
-                                              : p.kb == 16 ? reduce_sym_sorted_kernel<16, 4>
-                                                           : reduce_sym_sorted_kernel<32, 4>)
-                                           : (p.kb == 12   ? reduce_sym_sorted_kernel<12, 2>
-                                              : p.kb == 16 ? reduce_sym_sorted_kernel<16, 2>
-                                                           : reduce_sym_sorted_kernel<32, 2>);
+        const dim3 block((unsigned)sorted_threads(p.a, p.rpl, p.pw));
+        void (*f)(SortedArgs) = p.rpl == 4 ? (p.kb == 12   ? reduce_sym_sorted_kernel<12, 4, 1>
+                                              : p.kb == 16 ? reduce_sym_sorted_kernel<16, 4, 1>
+                                                           : reduce_sym_sorted_kernel<32, 4, 1>)
+                                : p.pw == 2 ? reduce_sym_sorted_kernel<12, 2, 2>
+                                           : (p.kb == 12   ? reduce_sym_sorted_kernel<12, 2, 1>
+                                              : p.kb == 16 ? reduce_sym_sorted_kernel<16, 2, 1>
+                                                           : reduce_sym_sorted_kernel<32, 2, 1>);
         e = launch_pdl(f, dim3(p.grid), block, p.smem, s, r);
     } else {
         CUtensorMap map;

@@ -64,10 +64,11 @@ CASES = [
 
 
 def _sorted_max_a(k):
-    """Widest super-tile of the sorted form: its 4a consumer warps (two a block row, two a
-    block column), holding 2 KMAX register sums a lane, must fit the register file
-    (KMAX = 12, 16, 32 for k up to 12, 16, 32)."""
-    return 4 if k <= 16 else 3
+    """Widest super-tile of the sorted form: its consumer warps (two a block row, two a
+    block column; above an edge of 4 each warp owns two block rows or columns), holding
+    2 KMAX register sums a lane per block row, must fit the register file (KMAX = 12, 16,
+    32 for k up to 12, 16, 32)."""
+    return 8 if k <= 12 else 4 if k <= 16 else 3
 
 
 @pytest.mark.parametrize("sym_tile", [0, 1, 2, 3, 4, 8])
