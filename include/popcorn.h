@@ -130,7 +130,7 @@ typedef struct {
                                    its own scheme.  Results differ only by summation order  */
     int32_t sym_tile;           /* super-tile edge a of the symmetric pass, in 128-blocks,
                                    0..8: 0 = automatic (4 for k <= 16 and 3 for k <= 32,
-                                   narrowed until there are at least 4 super-tiles per SM);
+                                   narrowed until there are at least 8 super-tiles per SM);
                                    1..8 to force one (6 or 8 for k <= 12 gives each warp two
                                    block rows; an edge the register file does not allow falls
                                    back to the full square).  k <= 8 with an edge of 1 runs
@@ -326,6 +326,36 @@ typedef struct {
     const int32_t* init_labels; /* n labels in [0, k)                                      */
     int32_t* labels_out;        /* n labels (may alias init_labels)                        */
 } popcorn_instance;
+
+/*
+ * popcorn_kmeanspp -- K-means++ seeding in the kernel's feature space: k initial centers
+ * and the initial labels popcorn_fit can start from.
+ *
+ * Sec. 2.1 names K-means++ as the initialization that samples each next centroid from a
+ * weighted distribution favouring points far from those already chosen.  The weight here
+ * is the squared feature-space distance to the nearest chosen point,
+ * D(i) = min_c (K_ii - 2 K_ic + K_cc), with kappa evaluated in FP64 from the points (K is
+ * not formed).  The caller supplies the random numbers: u[0] picks the first point,
+ * floor(u[0] n); for t >= 1, point t is the first i in index order at which the running sum
+ * of D exceeds u[t] sum_i D(i) (floor(u[t] n) when that sum is 0, i.e. every point
+ * coincides with a chosen one).  labels_out[i] is the index t of i's nearest chosen point
+ * (the lowest t on ties).  All sums are taken in a fixed order: repeated calls give the
+ * same result.
+ *
+ *   P           host or device, n x d FP32, leading dimension ldp >= d.
+ *   u           host or device, k doubles in [0, 1).
+ *   labels_out  host or device, n int32 output (values in [0, k)).
+ *   centers_out host or device, k int32 output (the chosen points in order), or NULL.
+ *   stream      work is ordered on it; the call returns after the results are written.
+ *
+ * Errors: POPCORN_ERR_INVALID for null P / u / labels_out, n < 1, d < 1, ldp < d, k outside
+ * [1, min(n, 256)], a host draw outside [0, 1), or an invalid kernel; POPCORN_ERR_UNSUPPORTED
+ * when the per-SM state (about 20 (n / SMs) + 8 d bytes) exceeds shared memory;
+ * POPCORN_ERR_TIMEOUT if a bounded wait between the SMs ran out.
+ */
+POPCORN_API popcorn_status popcorn_kmeanspp(const float* P, int64_t n, int32_t d, int64_t ldp, int32_t k,
+                                            popcorn_kernel kern, const double* u, int32_t* labels_out,
+                                            int32_t* centers_out, popcorn_stream_t stream);
 
 /*
  * popcorn_fit_batched -- many independent Kernel K-means problems at once.

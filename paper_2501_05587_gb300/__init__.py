@@ -6,6 +6,7 @@ behind the C ABI of ``include/popcorn.h``.  Functions carry the C names:
 * ``popcorn_kernel_matrix`` -- K = kappa(P P^T) and diag(K) (Sec. 3.2).
 * ``popcorn_assign_step``   -- one pass of the loop body of Alg. 2 on a given K.
 * ``popcorn_fit``           -- Kernel K-means (Alg. 2) from points and labels.
+* ``popcorn_kmeanspp``      -- K-means++ seeding (Sec. 2.1) in the kernel's feature space.
 
 Device buffers are torch CUDA tensors (PyTorch supplies memory and streams);
 ``popcorn_fit`` also accepts host buffers (CPU tensors or numpy arrays), which
@@ -26,6 +27,7 @@ __all__ = [
     "popcorn_assign_step",
     "popcorn_fit",
     "popcorn_fit_batched",
+    "popcorn_kmeanspp",
     "popcorn_assign_step_noalloc",
     "NOALLOC_SCRATCH_BYTES",
     "popcorn_version",
@@ -56,6 +58,7 @@ EXPORTED_SYMBOLS = (
     "popcorn_fit",
     "popcorn_assign_step_noalloc",
     "popcorn_fit_batched",
+    "popcorn_kmeanspp",
     "popcorn_autotune_entries",
     "popcorn_autotune_clear",
 )
@@ -124,6 +127,8 @@ _lib.popcorn_autotune_entries.restype = _i32
 _lib.popcorn_autotune_entries.argtypes = []
 _lib.popcorn_autotune_clear.restype = None
 _lib.popcorn_autotune_clear.argtypes = []
+_lib.popcorn_kmeanspp.restype = ctypes.c_int
+_lib.popcorn_kmeanspp.argtypes = [_vp, _i64, _i32, _i64, _i32, _Kernel, _vp, _vp, _vp, _vp]
 _lib.popcorn_fit.restype = ctypes.c_int
 _lib.popcorn_fit.argtypes = [_vp, _i64, _i32, _i64, _i32, _Kernel, _vp, _i32, _dbl,
                              ctypes.POINTER(_Options), _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i32),
@@ -361,3 +366,33 @@ def popcorn_fit_batched(instances, max_iter: int, tol: float = 0.0, precision: s
                                     ctypes.byref(info), _stream(stream)), "popcorn_fit_batched")
     out_info = _info_dict(info)
     return {"labels": outs, "objectives": list(objs), "iterations": list(its), "info": out_info}
+
+
+def popcorn_kmeanspp(P, k: int, kernel: dict, u, labels_out=None, stream=None) -> dict:
+    """K-means++ seeding (Sec. 2.1) in the kernel's feature space with the caller's k draws
+    ``u`` (values in [0, 1); a numpy array or a CUDA float64 tensor).  P may live on the host
+    or the device; the labels land on P's side unless ``labels_out`` is given.  Returns
+    {"labels": n initial labels, "centers": the k chosen points in order (numpy)}."""
+    torch = _torch()
+    if isinstance(P, np.ndarray):
+        P = np.ascontiguousarray(P, dtype=np.float32)
+        n, d = P.shape
+        ldp = d
+        on_host = True
+    else:
+        assert P.dtype == torch.float32 and P.dim() == 2 and P.stride(1) == 1
+        n, d = P.shape
+        ldp = P.stride(0)
+        on_host = not P.is_cuda
+    if isinstance(u, np.ndarray) or not hasattr(u, "data_ptr"):
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    else:
+        u = u.to(torch.float64).contiguous()
+    if labels_out is None:
+        labels_out = (np.empty(n, dtype=np.int32) if on_host
+                      else torch.empty(n, dtype=torch.int32, device=P.device))
+    centers = np.empty(int(k), dtype=np.int32)
+    _check(_lib.popcorn_kmeanspp(_ptr(P), n, d, ldp, int(k), _kernel(kernel), _ptr(u), _ptr(labels_out),
+                                 _ptr(centers), _stream(stream)),
+           "popcorn_kmeanspp")
+    return {"labels": labels_out, "centers": centers}

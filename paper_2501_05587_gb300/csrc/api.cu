@@ -87,6 +87,7 @@ popcorn_status device_info(DeviceInfo** out) {
         POPCORN_CUDA(configure_batched(d.smem_optin));
         POPCORN_CUDA(configure_reduce_sym(d.smem_optin));
         POPCORN_CUDA(configure_fused_fit(d.smem_optin));
+        POPCORN_CUDA(configure_kmeanspp(d.smem_optin));
         int coop = 0;
         POPCORN_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         d.coop = coop != 0;
@@ -1029,6 +1030,74 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     return POPCORN_OK;
 }
 
+
+popcorn_status popcorn_kmeanspp(const float* P, int64_t n, int32_t d, int64_t ldp, int32_t k, popcorn_kernel kern,
+                                const double* u, int32_t* labels_out, int32_t* centers_out, popcorn_stream_t stream) {
+    g_err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!P || !u || !labels_out) return fail(POPCORN_ERR_INVALID, "null pointer argument");
+    if (n < 1 || n >= (1LL << 31)) return fail(POPCORN_ERR_INVALID, "n = %lld outside [1, 2^31)", (long long)n);
+    if (d < 1) return fail(POPCORN_ERR_INVALID, "d = %d < 1", d);
+    if (ldp < d) return fail(POPCORN_ERR_INVALID, "ldp = %lld < d = %d", (long long)ldp, d);
+    if (k < 1 || k > n || k > kMaxClusters)
+        return fail(POPCORN_ERR_INVALID, "k = %d outside [1, min(n, %d)]", k, kMaxClusters);
+    KernParams kp;
+    POPCORN_TRY(check_kernel(kern, &kp));
+    const bool u_dev = is_device_pointer(u);
+    if (!u_dev)
+        for (int t = 0; t < k; ++t)
+            if (!(u[t] >= 0.0 && u[t] < 1.0)) return fail(POPCORN_ERR_INVALID, "u[%d] = %g outside [0, 1)", t, u[t]);
+    DeviceInfo* dev;
+    POPCORN_TRY(device_info(&dev));
+    if (!dev->coop) return fail(POPCORN_ERR_UNSUPPORTED, "the device has no cooperative launches");
+    const int ni = (int)n;
+    if (!kmeanspp_fits(ni, d, dev->sms, dev->smem_optin))
+        return fail(POPCORN_ERR_UNSUPPORTED, "n = %d, d = %d: the seeding's per-SM state exceeds shared memory", ni,
+                    d);
+    Workspace ws(dev->pool, s);
+    const float* Pd = P;
+    int64_t ldpd = ldp;
+    if (!is_device_pointer(P)) {
+        float* tmp;
+        POPCORN_TRY(ws.alloc(&tmp, (size_t)ni * d, "points"));
+        POPCORN_CUDA(cudaMemcpy2DAsync(tmp, (size_t)d * sizeof(float), P, (size_t)ldp * sizeof(float),
+                                       (size_t)d * sizeof(float), (size_t)ni, cudaMemcpyHostToDevice, s));
+        Pd = tmp;
+        ldpd = d;
+    }
+    const double* ud = u;
+    if (!u_dev) {
+        double* tmp;
+        POPCORN_TRY(ws.alloc(&tmp, (size_t)k, "draws"));
+        POPCORN_CUDA(cudaMemcpyAsync(tmp, u, (size_t)k * sizeof(double), cudaMemcpyHostToDevice, s));
+        ud = tmp;
+    }
+    const bool lab_dev = is_device_pointer(labels_out);
+    const bool cen_dev = centers_out && is_device_pointer(centers_out);
+    int32_t* labd = labels_out;
+    if (!lab_dev) POPCORN_TRY(ws.alloc(&labd, (size_t)ni, "labels"));
+    int32_t* cend = cen_dev ? centers_out : nullptr;
+    if (!cend) POPCORN_TRY(ws.alloc(&cend, (size_t)k, "centers"));
+    double* part;
+    int* small;   // [0] the chosen point, [1] the error word
+    unsigned* bar;
+    POPCORN_TRY(ws.alloc(&part, (size_t)dev->sms, "seeding partial sums"));
+    POPCORN_TRY(ws.alloc(&small, 2, "seeding words"));
+    POPCORN_TRY(ws.alloc(&bar, 32, "grid barrier"));
+    POPCORN_CUDA(cudaMemsetAsync(small, 0, 2 * sizeof(int), s));
+    POPCORN_CUDA(launch_kmeanspp(Pd, ni, d, ldpd, k, kern, ud, labd, cend, part, small, bar, small + 1, dev->sms, s));
+    void* hpin;
+    POPCORN_TRY(pinned(sizeof(int), &hpin));
+    int* herr = static_cast<int*>(hpin);
+    POPCORN_CUDA(cudaMemcpyAsync(herr, small + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (!lab_dev)
+        POPCORN_CUDA(cudaMemcpyAsync(labels_out, labd, (size_t)ni * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (centers_out && !cen_dev)
+        POPCORN_CUDA(cudaMemcpyAsync(centers_out, cend, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    POPCORN_CUDA(cudaStreamSynchronize(s));
+    if (*herr) return fail(POPCORN_ERR_TIMEOUT, "a bounded grid-barrier wait in the seeding ran out");
+    return POPCORN_OK;
+}
 
 popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, int32_t max_iter, double tol,
                                    const popcorn_options* opt_in, double* objectives_out, int32_t* iterations_out,

@@ -29,6 +29,7 @@
 // hang.
 #include "popcorn_internal.cuh"
 #include "stream_common.cuh"
+#include "grid_sync.cuh"
 #include "tc_common.cuh"
 
 #include <cuda/std/limits>
@@ -82,60 +83,6 @@ __host__ __device__ inline FusedLayout fused_layout(int n, int k, int rows_max, 
     L.Kc = L.lab + (((size_t)n + 15) & ~(size_t)15);
     L.bytes = L.Kc + (cache_k ? (size_t)rows_max * (size_t)ldk * 4 : 0);
     return L;
-}
-
-// Grid-wide barrier of the cooperative launch (all CTAs resident).  After the CTA's own
-// barrier, thread 0 arrives with an acquire-release add on the arrival count (its release
-// covers the CTA's writes, ordered before it by the CTA barrier); the last to arrive resets
-// the count and publishes the next generation with a release store, the others wait for it
-// with acquire loads, bounded.  False when the wait ran out or another CTA gave up, in which
-// case the whole CTA leaves.  (Measured on the blobs workload, this single counter beats a
-// two-level counter tree and per-CTA release flags polled with acquire loads: the cost is
-// round trips to L2, not contention.)
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ bool grid_barrier(unsigned* bar, int* err) {
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile int* verr = err;
-        const unsigned g = ld_acquire(bar + 1);
-        int ok = 1;
-        if (atom_add_acq_rel(bar, 1u) == gridDim.x - 1) {
-            st_relaxed(bar, 0u);
-            st_release(bar + 1, g + 1);
-        } else {
-            const unsigned long long t0 = tc::globaltimer();
-            unsigned spins = 0;
-            while (ld_acquire(bar + 1) == g) {
-                if ((++spins & 63u) == 0u) {
-                    if (*verr || tc::globaltimer() - t0 > tc::kWaitLimitNs) {
-                        if (!*verr) atomicExch(err, 1);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-        }
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
 }
 
 // A float4 of K: from the CTA's copy in shared memory, or from L2.
@@ -351,7 +298,7 @@ __device__ void fit_body(const FusedArgs& a, unsigned char* smem) {
         row_sums<CACHED>(a, lo, hi, lab_s, bins, S, Kc);
         __syncthreads();
         z_partials(a, lo, hi, lab_s, S);
-        if (!grid_barrier(bar, err)) return false;
+        if (!gsync::grid_barrier(bar, err)) return false;
         *J = finalize(a, m_s, trace, cn_s, iv_s);
         return true;
     };
@@ -369,7 +316,7 @@ __device__ void fit_body(const FusedArgs& a, unsigned char* smem) {
             st->J_last = J;
         }
         assign_rows(a, lo, hi, S, cn_s, iv_s, m_s, hist, lab_s, kd_s, hslot, cslot);
-        if (!grid_barrier(bar, err)) return;
+        if (!gsync::grid_barrier(bar, err)) return;
         // exchange B: the next pass's labels (loaded whether or not there is one), its counts
         // and this pass's change count; then the loop decision, taken alike in every CTA
         // (iterate.cu's assign pass)

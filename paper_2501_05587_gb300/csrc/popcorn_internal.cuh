@@ -220,6 +220,17 @@ cudaError_t configure_fused_fit(int smem_optin);
 cudaError_t launch_fused_fit(const struct PassBuffers& b, double* zpart, unsigned* xchg, int num_sms, int smem_optin,
                              cudaStream_t s);
 
+// ---- K-means++ seeding (seeding.cu) --------------------------------------------
+// One cooperative launch (one CTA per SM) for all k steps; kappa in FP64 from the points.
+// u: k draws (device); labels: n, centers: k (device); part: num_sms doubles, chosen: one
+// int, bar: 32 words of workspace; *err (device) set when a grid-barrier wait runs out.
+bool kmeanspp_fits(int n, int d, int num_sms, int smem_optin);
+size_t kmeanspp_smem(int n, int d, int num_sms);
+cudaError_t configure_kmeanspp(int smem_optin);
+cudaError_t launch_kmeanspp(const float* P, int n, int d, int64_t ldp, int k, const popcorn_kernel& kern,
+                            const double* u, int32_t* labels, int32_t* centers, double* part, int* chosen,
+                            unsigned* bar, int* err, int num_sms, cudaStream_t s);
+
 // ---- recompute path (recompute.cu): K never stored ---------------------------
 struct RecomputePlan {
     int fp8;            // 1: E4M3 operands with per-row scales; 0: BF16

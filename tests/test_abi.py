@@ -128,3 +128,23 @@ def test_autotune_cache_file_is_read_by_a_new_process(pc, tmp_path):
     assert r.returncode == 0, r.stderr
     assert r.stdout.split() == ["2", "0"]
     assert path.read_text().count("\n") == 4        # clearing leaves the file alone
+
+
+def test_kmeanspp_arguments_rejected_before_any_cuda_call(pc):
+    lib = pc._lib
+    kern = pc._Kernel(2, 1, 1.0, 0.0, 1.0)
+    P = np.zeros((10, 2), dtype=np.float32)
+    u = np.array([0.1, 0.2, 0.3])
+    lab = np.zeros(10, dtype=np.int32)
+
+    def seed(n=10, d=2, ldp=2, k=3, kern=kern, u=u, P=P, lab=lab):
+        return lib.popcorn_kmeanspp(None if P is None else P.ctypes.data, n, d, ldp, k, kern,
+                                    None if u is None else u.ctypes.data,
+                                    None if lab is None else lab.ctypes.data, None, None)
+
+    assert seed(P=None) == 1 and seed(u=None) == 1 and seed(lab=None) == 1
+    assert seed(k=0) == 1 and seed(k=11) == 1          # 1 <= k <= n
+    assert seed(n=0) == 1 and seed(d=0) == 1 and seed(ldp=1) == 1
+    assert seed(u=np.array([0.1, 1.0, 0.3])) == 1      # a draw outside [0, 1)
+    assert b"u[1]" in lib.popcorn_last_error_message()
+    assert seed(kern=pc._Kernel(2, 1, 1.0, 0.0, 0.0)) == 1   # sigma = 0
