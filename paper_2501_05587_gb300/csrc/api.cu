@@ -850,16 +850,22 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // An FP32 K that sits in L2 (the automatic choice only): the whole fit -- every pass and
     // the final objective -- in one cooperative launch, with grid barriers between the
     // phases of a pass instead of three launches a pass.
-    const bool fused = !use_sym && opt.k_pass == 0 && ks == POPCORN_K_FP32 && dev->coop &&
-                       cap_status == cudaStreamCaptureStatusNone &&
-                       fused_fit_applies(ni, k, dev->sms, dev->smem_optin);
+    bool fused = !use_sym && opt.k_pass == 0 && ks == POPCORN_K_FP32 && dev->coop &&
+                 cap_status == cudaStreamCaptureStatusNone && fused_fit_applies(ni, k, dev->sms, dev->smem_optin);
     if (fused) {
         double* fz;
         unsigned* fbar;
         POPCORN_TRY(ws.alloc(&fz, (size_t)dev->sms * k, "fused-fit partials"));
         POPCORN_TRY(ws.alloc(&fbar, fused_xchg_words(dev->sms, k), "exchange slots"));
-        POPCORN_CUDA(launch_fused_fit(b, fz, fbar, dev->sms, dev->smem_optin, s));
-        launches += 1;
+        const cudaError_t fe = launch_fused_fit(b, fz, fbar, dev->sms, dev->smem_optin, s);
+        if (fe == cudaErrorCooperativeLaunchTooLarge) {
+            // not every SM can hold a CTA now (a shared device): the launched passes instead
+            cudaGetLastError();
+            fused = false;
+        } else {
+            POPCORN_CUDA(fe);
+            launches += 1;
+        }
     }
     const bool use_graph = !fused && !opt.check_convergence && !kernel_events && max_iter > 0 &&
                            cap_status == cudaStreamCaptureStatusNone;

@@ -751,7 +751,11 @@ __global__ void __launch_bounds__(kAssignThreads) batched_assign_kernel(const Ba
 // scattered (across unit boundaries too), and per unit a butterfly reduction
 // for k <= 8 or the rotated walk for larger k.  z and J come from the batched
 // z kernel that follows.
-__global__ void __launch_bounds__(kReduceMaxWarps * 32, 2)
+// U float4 a lane a batch: 4 with two blocks an SM (64 registers); 8 with one block an SM,
+// which keeps twice the bytes in flight where the per-warp cluster columns (kmax x 128 bytes)
+// leave room for only 16 warps an SM.
+template <int U>
+__global__ void __launch_bounds__(kReduceMaxWarps * 32, U == 4 ? 2 : 1)
     batched_reduce_kernel(const BatchInst* I, int count, int units, int kmax, int eval) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int W = blockDim.x >> 5;
@@ -791,23 +795,23 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2)
     };
     Geo cur;
     if (!geom((int)blockIdx.x * W + warp, cur)) return;
-    float4 v[4];
-    uint32_t L[4];
-    load_batch<4, false>(cur.row4, cur.lab4, cur.qb + lane, cur.q1, v, L);
+    float4 v[U];
+    uint32_t L[U];
+    load_batch<U, false>(cur.row4, cur.lab4, cur.qb + lane, cur.q1, v, L);
     while (true) {
-        const bool last = cur.qb + 128 >= cur.q1;
+        const bool last = cur.qb + 32 * U >= cur.q1;
         Geo nxt = cur;
         bool more = true;
         if (last) {
             more = geom(cur.u + GW, nxt);
         } else {
-            nxt.qb = cur.qb + 128;
+            nxt.qb = cur.qb + 32 * U;
         }
-        float4 vn[4];
-        uint32_t Ln[4];
-        if (more) load_batch<4, false>(nxt.row4, nxt.lab4, nxt.qb + lane, nxt.q1, vn, Ln);
+        float4 vn[U];
+        uint32_t Ln[U];
+        if (more) load_batch<U, false>(nxt.row4, nxt.lab4, nxt.qb + lane, nxt.q1, vn, Ln);
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < U; ++x) {
             accl[(L[x] & 0xffu) * 32] += v[x].x;
             accl[((L[x] >> 8) & 0xffu) * 32] += v[x].y;
             accl[((L[x] >> 16) & 0xffu) * 32] += v[x].z;
@@ -854,7 +858,7 @@ __global__ void __launch_bounds__(kReduceMaxWarps * 32, 2)
             cur.qb = nxt.qb;
         }
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < U; ++x) {
             v[x] = vn[x];
             L[x] = Ln[x];
         }
@@ -872,7 +876,7 @@ void plan_batched_reduce(BatchPlan* bp, int num_sms, int smem_budget, int warps,
     bp->warps = w;
     bp->smem = per_warp * w;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_reduce_kernel, 32 * w, bp->smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_reduce_kernel<4>, 32 * w, bp->smem);
     cudaGetLastError();
     if (per_sm_req > 0 && per_sm_req < per_sm) per_sm = per_sm_req;
     if (per_sm < 1) per_sm = 1;
@@ -881,15 +885,21 @@ void plan_batched_reduce(BatchPlan* bp, int num_sms, int smem_budget, int warps,
 }
 
 cudaError_t launch_batched_reduce(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s) {
-    batched_reduce_kernel<<<bp.grid, bp.warps * 32, bp.smem, s>>>(dI, bp.count, bp.units, bp.kmax, eval);
+    if (bp.per_sm == 1)
+        batched_reduce_kernel<8><<<bp.grid, bp.warps * 32, bp.smem, s>>>(dI, bp.count, bp.units, bp.kmax, eval);
+    else
+        batched_reduce_kernel<4><<<bp.grid, bp.warps * 32, bp.smem, s>>>(dI, bp.count, bp.units, bp.kmax, eval);
     return cudaGetLastError();
 }
 
 cudaError_t configure_batched(int smem_optin) {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, batched_reduce_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&fa, batched_reduce_kernel<4>);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(batched_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(batched_reduce_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin_minus_static(smem_optin, fa.sharedSizeBytes));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(batched_reduce_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 optin_minus_static(smem_optin, fa.sharedSizeBytes));
 }
 
@@ -908,7 +918,10 @@ cudaError_t launch_batched_trace(const BatchInst* dI, const BatchPlan& bp, cudaS
 }
 
 cudaError_t launch_batched_pass(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s) {
-    batched_reduce_kernel<<<bp.grid, bp.warps * 32, bp.smem, s>>>(dI, bp.count, bp.units, bp.kmax, eval);
+    if (bp.per_sm == 1)
+        batched_reduce_kernel<8><<<bp.grid, bp.warps * 32, bp.smem, s>>>(dI, bp.count, bp.units, bp.kmax, eval);
+    else
+        batched_reduce_kernel<4><<<bp.grid, bp.warps * 32, bp.smem, s>>>(dI, bp.count, bp.units, bp.kmax, eval);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     batched_zreduce_kernel<<<bp.zblocks, kZReduceRows, 0, s>>>(dI, bp.count, eval);
