@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--k-pass", default="auto", choices=["auto", "full", "symmetric"],
                     help="how a pass reads a stored FP32 K: the library's choice, the full square, or the blocks "
                          "on and above the diagonal (row and column sums, then a fold)")
+    ap.add_argument("--k-storage", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="element type of the stored K (the build is FP32 or tensor-core; K is rounded once)")
     ap.add_argument("--sym-tile", type=int, default=0, choices=list(range(9)),
                     help="super-tile edge of the symmetric pass (0: the library's choice)")
     ap.add_argument("--sweep", default=None, choices=["kbuild"],
@@ -139,43 +141,50 @@ def recorded_traffic(kernel: str, src_file: str, workload: str):
         return None
 
 
-def sym_bytes(n: int, k: int, nslots: int, sorted_form: bool = True):
+def sym_bytes(n: int, k: int, nslots: int, sorted_form: bool = True, ebytes: int = 4):
     """Bytes of one symmetric stream launch: the scope table's algorithmic figure for triangular
-    storage (2 n (n + 1) + n: the unique entries of K once, plus the labels), and what the
-    kernel moves besides: the 128-blocks of the packed triangle, the slot stores, and per
-    block its labels (branch form) or its column and row lists (sorted form: a 128-byte
-    header and 4 bytes an entry, 128 + 3k padded to 4, plus 4; both from L2)."""
+    storage (ebytes n (n + 1) / 2 + n: the unique entries of K once, 4 bytes an entry in FP32
+    and 2 in FP16 / BF16, plus the labels), and what the kernel moves besides: the 128-blocks
+    of the packed triangle, the slot stores, and per block its labels (branch form) or its
+    column and row lists (sorted form: a 128-byte header and 4 bytes an entry, 128 + 3k
+    padded to 4, plus 4; both from L2)."""
     T = (n + 127) // 128
     blocks = T * (T + 1) / 2
     lists = 2.0 * (128 + 4 * (((128 + 3 * k + 3) // 4) * 4 + 4))
-    return {"algorithmic": 2.0 * n * (n + 1) + n,
-            "packed_tiles": 65536.0 * blocks,
+    return {"algorithmic": ebytes * n * (n + 1) / 2.0 + n,
+            "packed_tiles": 16384.0 * ebytes * blocks,
             "slot_stores": 4.0 * nslots * k * n,
             "labels": (lists if sorted_form else 256.0) * blocks}
 
 
-def pass_roofline(wl, prof, pk):
+def pass_roofline(wl, prof, pk, k_storage="fp32"):
     """HBM roofline of the dominant kernel of a pass (stored K): the symmetric stream or the
     full-square reduction.  Its launch time comes from the library's CUDA events on the
     launching stream (reduce minus fold), averaged over the profiled fits' passes."""
     n, k = wl.n, wl.k
+    eb = 4 if k_storage == "fp32" else 2
     info = prof[-1]["info"]
     passes = sum(r["iterations"] for r in prof)
     red = sum(r["info"]["reduce_ms"] for r in prof)
     fold = sum(r["info"]["fold_ms"] for r in prof)
     if info["k_pass_used"] == 1:
-        b = sym_bytes(n, k, info["schedule"][2], info["schedule"][3] > 8)
+        b = sym_bytes(n, k, info["schedule"][2], info["sym_form"] == 2, eb)
+        if info["sym_form"] == 3:
+            # one-hot operands of the block column and the block row with every block (L2)
+            T = (n + 127) // 128
+            b["labels"] = 2.0 * 256 * info["schedule"][3] * T * (T + 1) / 2
         ms = (red - fold) / max(passes, 1)
         ach = b["algorithmic"] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-        # schedule[3]: register sums per row, 4 or 8 in the branch form, 12 / 16 / 32 in the
-        # sorted form (whose stream launch time here includes its per-pass label sort)
-        kern = "reduce_sym_kernel" if info["schedule"][3] <= 8 else "reduce_sym_sorted_kernel"
+        # sym_form: 1 branch, 2 sorted, 3 tensor-core (the stream launch time of the last two
+        # includes their per-pass label kernel: the sort, or the one-hot operand)
+        kern = {1: "reduce_sym_kernel", 2: "reduce_sym_sorted_kernel", 3: "reduce_sym_mma_kernel"}[info["sym_form"]]
         return {"kernel": kern, "bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
                 "frac": ach / pk["hbm"],
-                "traffic": recorded_traffic(kern, "reduce_sym.cu", wl.name),
+                "traffic": recorded_traffic(kern, "reduce_sym_mma.cu" if info["sym_form"] == 3 else "reduce_sym.cu",
+                                            wl.name),
                 "peak_source": pk["source"] + " HBM copy", "algorithmic_bytes_per_launch": b["algorithmic"],
                 "moved_bytes_per_launch": {x: b[x] for x in ("packed_tiles", "slot_stores", "labels")},
-                "avg_launch_ms": ms, "fold_avg_launch_ms": fold / max(passes, 1),
+                "k_storage": k_storage, "avg_launch_ms": ms, "fold_avg_launch_ms": fold / max(passes, 1),
                 "pass_avg_ms": (red + sum(r["info"]["assign_ms"] for r in prof)) / max(passes, 1),
                 "schedule": {"super_tile": info["schedule"][0], "ring": info["schedule"][1],
                              "slots": info["schedule"][2], "accumulators": info["schedule"][3]}}
@@ -193,9 +202,9 @@ def pass_roofline(wl, prof, pk):
                                f"{pk['sm_mhz']:.0f} MHz",
                 "algorithmic_bytes_per_pass": alg, "pass_avg_ms": ms}
     ms = red / max(passes, 1)
-    alg = 4.0 * n * n + n
+    alg = float(eb) * n * n + n
     ach = alg / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-    return {"kernel": "reduce_kernel", "bound": "hbm", "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
+    return {"kernel": "reduce_kernel", "bound": "hbm", "k_storage": k_storage, "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
             "frac": ach / pk["hbm"], "traffic": recorded_traffic("reduce_kernel", "iterate.cu", wl.name),
             "peak_source": pk["source"] + " HBM copy", "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms}
 
@@ -539,12 +548,13 @@ def sample_objective_errors(pc, torch, wl, Ko, ofit, n_sample, forms):
     P = torch.from_numpy(np.ascontiguousarray(wl.P[:n_sample])).cuda()
     lab = torch.from_numpy(np.ascontiguousarray(wl.init_labels[:n_sample])).cuda()
     out = {}
-    for prec in forms:
+    for form in forms:
+        key, prec, kst = form if isinstance(form, tuple) else (form, form, "fp32")
         r = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=wl.max_iter, check_convergence=wl.check_convergence,
-                           precision=prec, store_k=wl.store_k)
+                           precision=prec, store_k=wl.store_k, k_storage=kst)
         labels = r["labels"].cpu().numpy()
         J = oracle.objective(Ko, labels, wl.k)
-        out[prec] = {"objective_rel_err_vs_oracle_fit": abs(J - ofit["objective"]) / abs(ofit["objective"]),
+        out[key] = {"objective_rel_err_vs_oracle_fit": abs(J - ofit["objective"]) / abs(ofit["objective"]),
                      "reported_vs_fp64_of_labels": abs(r["objective"] - J) / abs(J),
                      "labels_equal_to_oracle_fit": float(np.mean(labels == ofit["labels"]))}
     return out
@@ -802,12 +812,13 @@ def main():
     wl = synth.workload(args.workload, scale=args.scale)
     if args.precision:
         wl.precision = args.precision
-    headline = args.workload == WORKLOAD and args.scale == 1.0 and not args.precision
+    headline = args.workload == WORKLOAD and args.scale == 1.0 and not args.precision and args.k_storage == "fp32"
     P = torch.from_numpy(wl.P).cuda()
     lab = torch.from_numpy(wl.init_labels).cuda()
     out = torch.empty_like(lab)
     # the recompute path's schedule (row blocks per tile, units per SM) is autotuned in the warm-up
-    kw = {"autotune": args.autotune == "on" and not wl.store_k, "k_pass": args.k_pass, "sym_tile": args.sym_tile}
+    kw = {"autotune": args.autotune == "on" and not wl.store_k, "k_pass": args.k_pass, "sym_tile": args.sym_tile,
+          "k_storage": args.k_storage}
 
     stream = torch.cuda.current_stream()
     with ClockSampler(local) as clocks:
@@ -851,7 +862,7 @@ def main():
         kb_ms = s["kbuild_ms"]
         rooflines = []
         if wl.store_k:
-            rp = pass_roofline(wl, prof, pk)
+            rp = pass_roofline(wl, prof, pk, args.k_storage)
             rk = kbuild_roofline(wl, wl.precision, kb_ms, pk)
             pass_total = s["breakdown_ms_per_fit"]["reduce"] - sum(r["info"]["fold_ms"] for r in prof) / len(prof)
             # the dominant kernel of a fit: the K build or the stream kernel summed over the passes
@@ -899,16 +910,20 @@ def main():
             line["roofline_secondary"] = rooflines[1]
         forms = {}
         if headline and world == 1:
-            # the tensor-core forms of the same fit: BF16X3 (split-BF16 cross term) and BF16
-            for prec in ("bf16x3", "bf16"):
-                f = fit_form(pc, torch, stream, wl, P, lab, out, prec, args.steps, args.warmup, **kw)
+            # the tensor-core forms of the same fit: BF16X3 (split-BF16 cross term) and BF16,
+            # and BF16X3 with K stored in FP16 (Gaussian K <= 1: 11 significant bits)
+            for key, prec, kst in (("bf16x3", "bf16x3", "fp32"), ("bf16", "bf16", "fp32"),
+                                   ("bf16x3_k_fp16", "bf16x3", "fp16")):
+                f = fit_form(pc, torch, stream, wl, P, lab, out, prec, args.steps, args.warmup,
+                             **{**kw, "k_storage": kst})
                 fs = f["summary"]
+                fs["k_storage"] = kst
                 fs["objective_rel_diff_vs_fp32_fit"] = abs(fs["objective"] - s["objective"]) / abs(s["objective"])
                 fs["speedup_vs_fp32_fit"] = fs["value"] / value
                 fs["roofline_kbuild"] = kbuild_roofline(wl, prec, fs["kbuild_ms"], pk)
-                fs["roofline_pass"] = pass_roofline(wl, f["prof"], pk)
-                forms[prec] = fs
-                line[prec] = fs
+                fs["roofline_pass"] = pass_roofline(wl, f["prof"], pk, kst)
+                forms[key] = fs
+                line[key] = fs
         if headline and world == 1 and not args.no_extras:
             extras = {}
             for name in ("rings", "blobs", "mixture"):
@@ -941,7 +956,8 @@ def main():
             line["cpu_baseline"] = base
             if wl.store_k:
                 errs = sample_objective_errors(pc, torch, wl, Ko, ofit, n_s,
-                                               ["fp32", "bf16x3", "bf16"] if headline else [wl.precision])
+                                               ["fp32", "bf16x3", "bf16", ("bf16x3_k_fp16", "bf16x3", "fp16")]
+                                               if headline else [(wl.precision, wl.precision, args.k_storage)])
                 line["objective_vs_oracle_on_sample"] = {"sample": f"first {n_s} points, same initial labels and "
                                                                    f"passes as the oracle's fit", **errs}
         print(json.dumps(line), flush=True)

@@ -112,14 +112,15 @@ typedef struct {
                                    length, warps per block, blocks per SM) and by the
                                    recompute path of popcorn_fit (row blocks per tile, units
                                    per SM).  Results differ only by summation order.        */
-    int32_t k_pass;             /* how a pass reads a stored FP32 K.  0 = automatic (the
+    int32_t k_pass;             /* how a pass reads a stored K.  0 = automatic (the
                                    default): the symmetric read below for n >= 8192 (where K
                                    outgrows L2 and reading half of it pays; measured faster
                                    on GB300 for every k up to 32), else the full square.
-                                   1 = symmetric (FP32 K, k <= 32; larger k, or a half-
-                                   precision K, falls back to the full square): only the
-                                   128 x 128 blocks on and above the diagonal (K is symmetric,
-                                   and is then stored as that packed triangle); a block's row
+                                   1 = symmetric (k <= 32; larger k falls back to the full
+                                   square): only the 128 x 128 blocks on and above the
+                                   diagonal (K is symmetric, and is then stored as that packed
+                                   triangle; an FP16 / BF16 K is built in FP32, then rounded
+                                   into the triangle by one more launch); a block's row
                                    sums serve its rows and its column sums its columns' rows.
                                    Blocks are taken in super-tiles of a x a (sym_tile below),
                                    each block's labels sorted once a pass; each super-tile
@@ -132,9 +133,10 @@ typedef struct {
                                    0..8: 0 = automatic (4 for k <= 16 and 3 for k <= 32,
                                    narrowed until there are at least 8 super-tiles per SM);
                                    1..8 to force one (6 or 8 for k <= 12 gives each warp two
-                                   block rows; an edge the register file does not allow falls
-                                   back to the full square).  k <= 8 with an edge of 1 runs
-                                   the branch form (single blocks, a uniform branch a label) */
+                                   block rows, FP32 K only; an edge the register file does not
+                                   allow falls back to the full square).  k <= 8 with an edge
+                                   of 1 and an FP32 K runs the branch form (single blocks, a
+                                   uniform branch a label)                                    */
     int64_t reserved[4];        /* must be zero                                              */
 } popcorn_options;
 
@@ -165,9 +167,11 @@ typedef struct {
                                   recompute: {row blocks per tile, column segments,
                                               units per SM target, 0};
                                   symmetric pass: {super-tile edge, block ring depth,
-                                                   slots, register sums per row: 4 or 8
+                                                   slots, sums per row: 4 or 8 registers
                                                    in the branch form, 12, 16 or 32 in
-                                                   the sorted form};
+                                                   the sorted form, 16 or 32 TMEM
+                                                   columns (the MMA's N) in the
+                                                   tensor-core form};
                                   zeros otherwise                                           */
     double fold_ms;            /* symmetric pass: the slot fold kernel, summed over passes
                                   (part of reduce_ms), when timing = 1                      */
@@ -175,7 +179,10 @@ typedef struct {
                                   fit in one cooperative launch (automatic choice for an FP32
                                   K that sits in L2: n <= 6144, k <= 32; it reads the full
                                   square); 0 recompute                                     */
-    int32_t reserved_info;     /* zero                                                     */
+    int32_t sym_form;          /* k_pass_used = 1: the form of the symmetric pass: 1 branch
+                                  (FP32 K, single blocks), 2 sorted (FP32 K, label-sorted
+                                  lists, CUDA cores), 3 tensor-core (FP16 / BF16 K: MMAs of
+                                  the packed tiles against one-hot label operands); else 0  */
     float* E_out;              /* caller-provided DEVICE array of n x k floats (row-major,
                                   ld = k), or NULL.  Stored-K fits with max_iter >= 1: E =
                                   K V^T of the labels the last assignment pass started

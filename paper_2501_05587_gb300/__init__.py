@@ -94,7 +94,7 @@ class _FitInfo(ctypes.Structure):
                 ("changed_history", ctypes.POINTER(ctypes.c_int32)), ("tune_cache_hit", ctypes.c_int32),
                 ("tune_candidates", ctypes.c_int32), ("tune_ms", ctypes.c_double),
                 ("schedule", ctypes.c_int32 * 4), ("fold_ms", ctypes.c_double),
-                ("k_pass_used", ctypes.c_int32), ("reserved_info", ctypes.c_int32),
+                ("k_pass_used", ctypes.c_int32), ("sym_form", ctypes.c_int32),
                 ("E_out", ctypes.c_void_p)]
 
 

@@ -86,6 +86,8 @@ popcorn_status device_info(DeviceInfo** out) {
         POPCORN_CUDA(configure_recompute(d.smem_optin, &d.recompute_smem));
         POPCORN_CUDA(configure_batched(d.smem_optin));
         POPCORN_CUDA(configure_reduce_sym(d.smem_optin));
+        POPCORN_CUDA(configure_pack_half());
+        POPCORN_CUDA(configure_sym_mma(d.smem_optin));
         POPCORN_CUDA(configure_fused_fit(d.smem_optin));
         POPCORN_CUDA(configure_kmeanspp(d.smem_optin));
         int coop = 0;
@@ -125,6 +127,15 @@ class Workspace {
         blocks_.push_back(p);
         *out = static_cast<T*>(p);
         return POPCORN_OK;
+    }
+    // returns one block to the pool now (stream-ordered) instead of at the end
+    void release(void* p) {
+        for (size_t i = 0; i < blocks_.size(); ++i)
+            if (blocks_[i] == p) {
+                cudaFreeAsync(p, s_);
+                blocks_.erase(blocks_.begin() + (long)i);
+                return;
+            }
     }
 
   private:
@@ -499,7 +510,7 @@ popcorn_status fit_recompute(const float* P, int64_t n, int32_t d, int64_t ldp, 
         info->tune_ms = tune_ms;
         info->fold_ms = 0.0;
         info->k_pass_used = 0;
-        info->reserved_info = 0;
+        info->sym_form = 0;
         info->schedule[0] = rp.rbp;
         info->schedule[1] = rp.nseg;
         info->schedule[2] = rp.units_per_sm;
@@ -727,8 +738,9 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     const int64_t ldk = ks == POPCORN_K_FP32 ? (n + 3) / 4 * 4 : (n + 7) / 8 * 8;   // 16-byte rows
     ReducePlan plan = plan_reduce(ni, k, dev->sms, dev->reduce_smem, ks);
     if (plan.grid == 0) return fail(POPCORN_ERR_UNSUPPORTED, "n = %d is too large for the materialized path", ni);
-    // symmetric pass (FP32 K, k <= kSymMaxK; k_pass 0 or 1): the blocks on and above the
-    // diagonal, row and column sums into T slots, folded into slot 0
+    // symmetric pass (k <= kSymMaxK; k_pass 0 or 1): the blocks on and above the diagonal,
+    // row and column sums into slots, folded into slot 0.  An FP16 / BF16 K takes the
+    // tensor-core form (2 bytes an entry).
     SymPlan sym{};
     // automatic choice, from measurements on GB300: the symmetric pass (sorted form) once K
     // outgrows L2, where a pass streams it from HBM and reading half of it pays (images,
@@ -736,14 +748,14 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // full square; rings, n = 20,000, k = 4: 0.152 + 0.014 against 0.275).  Below that a
     // pass is a few microseconds of launches and the full square's two kernels win.
     const bool sym_auto = ni >= kSymAutoMinN;
-    if (ks == POPCORN_K_FP32 && (opt.k_pass == 1 || (opt.k_pass == 0 && sym_auto)))
-        sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin, opt.sym_tile);
+    if (opt.k_pass == 1 || (opt.k_pass == 0 && sym_auto))
+        sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin, opt.sym_tile, 0, (int)kelem);
     const bool use_sym = sym.ok;
     // With the symmetric pass, K is stored block-packed: the upper triangle of 128 x 128
     // tiles only (half the memory; each value written once), by the FP32 build and by the
     // tensor-core builds alike.
     sym.packed = use_sym;
-    const size_t k_bytes = sym.packed ? (size_t)sym.items * 128 * 128 * 4 : (size_t)ni * (size_t)ldk * kelem;
+    const size_t k_bytes = sym.packed ? (size_t)sym.items * 128 * 128 * kelem : (size_t)ni * (size_t)ldk * kelem;
     const int nslots = use_sym ? sym.nslots : plan.nseg;
     if (use_sym) plan.nseg = 1;             // the assignment reads the folded slot only
     const bool timing = opt.timing != 0;          // phase events (K build, passes)
@@ -795,7 +807,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // one pass's reduction: the K stream (for the symmetric pass: stream, then fold with z)
     // kernels of one pass's reduction: the full-square stream; or the symmetric stream and its
     // fold (the sorted form first sorts every block's labels)
-    const int red_launches = use_sym ? (sym.sorted ? 3 : 2) : 1;
+    const int red_launches = use_sym ? (sym.sorted || sym.mma ? 3 : 2) : 1;
     // Error-path test hook: with POPCORN_TEST_SYM_STALL_MS=<ms> in the environment, the
     // first symmetric stream launch of this fit (either form) leaves one block's copies out
     // and bounds its waits by <ms>, so the fit reports POPCORN_ERR_TIMEOUT (nothing faults
@@ -830,8 +842,20 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     }
     POPCORN_CUDA(cudaMemsetAsync(b.counts, 0, 2 * (size_t)k * sizeof(int32_t), s));
     POPCORN_CUDA(launch_init_state(b.st, max_iter, opt.check_convergence ? 1 : 0, tol, s));
-    POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, ks, kdiag, &ws, &b.st->wait_err,
-                                    dev->sms, s, &launches, sym.packed ? sym.layout : 0));
+    if (sym.packed && sym.ebytes == 2) {
+        // half layout: the build writes the FP32 triangle into a temporary, one pack launch
+        // rounds it into K (and rounds diag K with it), and the temporary goes back
+        float* kf;
+        POPCORN_TRY(ws.alloc(&kf, (size_t)sym.items * 128 * 128, "FP32 kernel matrix"));
+        POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, kf, ldk, POPCORN_K_FP32, kdiag, &ws,
+                                        &b.st->wait_err, dev->sms, s, &launches, kPackedSw4));
+        POPCORN_CUDA(launch_pack_half(kf, K, ks, ni, kdiag, s));
+        ++launches;
+        ws.release(kf);
+    } else {
+        POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, ks, kdiag, &ws,
+                                        &b.st->wait_err, dev->sms, s, &launches, sym.packed ? sym.layout : 0));
+    }
     POPCORN_CUDA(launch_trace(kdiag, ni, b.st, s));
     POPCORN_CUDA(launch_init_labels(Ld, ni, k, b.lab32, b.lab8, b.counts, b.st, s));
     launches += 3;
@@ -1003,13 +1027,14 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         info->tune_ms = 0.0;
         info->fold_ms = 0.0;
         info->k_pass_used = 0;
-        info->reserved_info = 0;
+        info->sym_form = 0;
         for (int q = 0; q < 4; ++q) info->schedule[q] = 0;
         if (use_sym) {
             info->schedule[0] = sym.a;
             info->schedule[1] = sym.stages;
             info->schedule[2] = sym.nslots;
             info->schedule[3] = sym.kb;
+            info->sym_form = sym.mma ? 3 : sym.sorted ? 2 : 1;
         }
         // passes that did work (launches after convergence return at once)
         const bool eval_ran = !(hs.iter > 0 && hs.last_changed == 0);
@@ -1423,7 +1448,7 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         info->tune_ms = tune_ms;
         info->fold_ms = 0.0;
         info->k_pass_used = 0;
-        info->reserved_info = 0;
+        info->sym_form = 0;
         info->schedule[0] = sched[0];
         info->schedule[1] = sched[1];
         info->schedule[2] = sched[2];

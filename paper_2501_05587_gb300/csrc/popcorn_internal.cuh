@@ -80,13 +80,18 @@ constexpr int kSymAutoMinN = 8192;   // the automatic choice takes the symmetric
 struct SymPlan {
     bool ok;
     bool sorted;        // the sorted form (k > kSymBranchMaxK, or a forced super-tile edge > 1)
-    int layout;         // packed tile layout the pass reads: kPackedSw16 (branch) or kPackedSw4 (sorted)
-    size_t meta_bytes;  // sorted form: per-pass label-sorted lists of every block (column and row lists)
-    int kb;             // register sums per row / column: 4 or 8 (branch form), 12, 16 or 32 (sorted form); >= k
+    bool mma;           // the tensor-core form (FP16 / BF16 K): E parts as MMAs against one-hot labels
+    int layout;         // packed tile layout the pass reads: kPackedSw16 (branch), kPackedSw4 (sorted)
+                        // or kPackedSw128H (tensor-core form)
+    size_t meta_bytes;  // sorted form: per-pass label-sorted lists of every block (column and row lists);
+                        // tensor-core form: per-pass one-hot label operand of every block
+    int kb;             // sums per row / column: 4 or 8 (branch form), 12, 16 or 32 (sorted form),
+                        // 16 or 32 (tensor-core form: accumulator columns, the MMA's N); >= k
     int rpl;            // sorted form: rows (columns) a lane owns in a block, 4 or 2 (2: two warps a block row)
     int pw;             // sorted form: block rows (columns) of the super-tile a warp owns, 1 or 2
+    int ebytes;         // bytes a stored K entry: 4, or 2 for FP16 / BF16 K in the half layout
     int T;              // 128-blocks per side
-    int a;              // super-tile edge in blocks (1, 2, 4 or 8)
+    int a;              // super-tile edge in blocks (1 to 8)
     int Ts;             // super-tiles per side
     int nslots;         // Spart slots
     int stages;         // block ring depth
@@ -99,8 +104,16 @@ struct SymPlan {
 };
 // a_req / stages_req: 0 = the heuristic choice, else that super-tile edge / ring depth
 // (ok = false if it does not fit)
-SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req = 0, int stages_req = 0);
+// ebytes: 4 (FP32 K: branch or sorted form) or 2 (FP16 / BF16 K: the tensor-core form)
+SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req = 0, int stages_req = 0,
+                        int ebytes = 4);
 cudaError_t configure_reduce_sym(int smem_optin);
+// The tensor-core form (reduce_sym_mma.cu): plan fields for an FP16 / BF16 K, the per-pass
+// one-hot operand and the stream launch (the fold is shared with the other forms).
+bool plan_sym_mma(SymPlan* p, int k, int num_sms, int smem_optin, int a_req, int stages_req);
+cudaError_t configure_sym_mma(int smem_optin);
+cudaError_t launch_sym_mma_stream(const struct PassBuffers& b, const SymPlan& p, int* err, int eval_only,
+                                  cudaStream_t s, int stall_ms);
 // err: set when a bounded wait of the stream kernel runs out; `between` (may be
 // null) is recorded on s after the stream kernel, before the fold.  stall_ms > 0
 // (either form; error-path tests only): CTA 0 leaves its first block's copies out,
@@ -159,6 +172,14 @@ void set_error_message(const char* msg);
 // 128-byte swizzle; rows read as float4 chunks).  kPackedSw4: element c of row r at
 // c ^ (r mod 32) (a row and a column of a box are both read conflict-free as scalars).
 constexpr int kPackedSw16 = 1, kPackedSw4 = 2;
+// kPackedSw128H: the same triangle with FP16 / BF16 entries, 32 KB a tile (kpack.cu):
+// element (r, C) at byte 16384 (C >> 6) + 128 r + 16 (((C >> 3) & 7) ^ (r & 7)) + 2 (C & 7),
+// the tensor cores' 128-byte swizzle; entries past n are zeros.
+constexpr int kPackedSw128H = 4;
+// The FP32 triangle (kPackedSw4) Kf rounded into kPackedSw128H Kh (k_storage FP16 or BF16);
+// diag K rounded the same way.
+cudaError_t configure_pack_half();
+cudaError_t launch_pack_half(const float* Kf, void* Kh, int k_storage, int n, float* kdiag, cudaStream_t s);
 
 // ---- K build (kbuild_simt.cu) ------------------------------------------------
 // K is float, __half or __nv_bfloat16 by k_storage (popcorn_k_storage); ldk in elements.

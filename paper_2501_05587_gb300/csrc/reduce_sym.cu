@@ -797,12 +797,18 @@ cudaError_t configure_reduce_sym(int smem_optin) {
     return cudaSuccess;
 }
 
-SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, int stages_req) {
+SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, int stages_req, int ebytes) {
     SymPlan p{};
-    if (k < 1 || k > kSymMaxK || n < 1) return p;
+    if (k < 1 || k > kSymMaxK || n < 1 || (ebytes != 4 && ebytes != 2)) return p;
+    p.ebytes = ebytes;
     p.T = (n + kB - 1) / kB;
     p.items = (long long)p.T * (p.T + 1) / 2;
     p.fold_blocks = (n + kFoldThreads - 1) / kFoldThreads;
+    // an FP16 / BF16 K: the tensor-core form (reduce_sym_mma.cu)
+    if (ebytes == 2) {
+        if (!plan_sym_mma(&p, k, num_sms, smem_optin, a_req, stages_req)) p.ok = false;
+        return p;
+    }
     // the branch form (k <= 8, single blocks) when asked for with a super-tile edge of 1;
     // otherwise the sorted form (measured faster on the rings workload too: 0.152 ms a
     // stream against 0.160)
@@ -878,7 +884,9 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, in
 cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, int eval_only, cudaStream_t s,
                               cudaEvent_t between, int stall_ms) {
     cudaError_t e;
-    if (p.sorted) {
+    if (p.mma) {
+        e = launch_sym_mma_stream(b, p, err, eval_only, s, stall_ms);
+    } else if (p.sorted) {
         if (!p.packed || p.layout != kPackedSw4 || !b.sym_meta) return cudaErrorInvalidValue;
         const SortedLayout L = sorted_layout(b.k, p.stages);
         uint8_t* metaC = b.sym_meta;

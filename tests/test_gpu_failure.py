@@ -30,18 +30,23 @@ def pc():
     return mod
 
 
-@pytest.mark.parametrize("sym_tile", [0, 1], ids=["sorted", "branch"])
+@pytest.mark.parametrize("sym_tile,storage", [(0, "fp32"), (1, "fp32"), (0, "bf16")],
+                         ids=["sorted", "branch", "tensor_core"])
 @pytest.mark.parametrize("check", [False, True], ids=["graph", "plain"])
-def test_stream_wait_timeout_is_reported_and_the_context_survives(pc, monkeypatch, check, sym_tile):
-    """Both forms of the symmetric stream: the sorted form (the automatic choice) and the
-    branch form (k <= 8 with a super-tile edge of 1)."""
+def test_stream_wait_timeout_is_reported_and_the_context_survives(pc, monkeypatch, check, sym_tile, storage):
+    """Every form of the symmetric stream: the sorted form (the automatic choice on an FP32
+    K), the branch form (k <= 8 with a super-tile edge of 1) and the tensor-core form (a
+    BF16 K: its producer leaves the block out, the MMA issuer's wait runs out)."""
     wl = synth.workload("rings", scale=0.1)              # n = 2,000: 136 blocks, one a CTA
     P = torch.from_numpy(wl.P).cuda()
     lab = torch.from_numpy(wl.init_labels).cuda()
-    kw = dict(max_iter=6, check_convergence=check, history=True, k_pass="symmetric", sym_tile=sym_tile)
+    kw = dict(max_iter=6, check_convergence=check, history=True, k_pass="symmetric", sym_tile=sym_tile,
+              k_storage=storage)
     ref = pc.popcorn_fit(P, wl.k, wl.kernel, lab, **kw)
     assert ref["info"]["k_pass_used"] == 1
-    assert ref["info"]["schedule"][3] == (12 if sym_tile == 0 else 4)   # register sums: sorted 12, branch 4
+    # sums per row: sorted 12 registers, branch 4, tensor-core 16 TMEM columns
+    assert ref["info"]["schedule"][3] == (16 if storage == "bf16" else 12 if sym_tile == 0 else 4)
+    assert ref["info"]["sym_form"] == (3 if storage == "bf16" else 2 if sym_tile == 0 else 1)
     monkeypatch.setenv("POPCORN_TEST_SYM_STALL_MS", "200")
     t0 = time.perf_counter()
     with pytest.raises(pc.PopcornError) as ei:

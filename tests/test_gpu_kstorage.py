@@ -76,3 +76,93 @@ def test_half_k_ragged_and_host_buffers(pc):
     a = pc.popcorn_fit(P, 7, kern, lab, max_iter=20, k_storage="fp16")
     b = pc.popcorn_fit(_dev(P), 7, kern, _dev(lab), max_iter=20, k_storage="fp16")
     assert np.array_equal(a["labels"], b["labels"].cpu().numpy()) and a["objective"] == b["objective"]
+
+
+# ---------------------------------------------------------------- symmetric pass on a half K
+# k_pass="symmetric" stores the packed upper triangle in FP16 / BF16 (the FP32 build's
+# triangle, rounded by one pack launch): the same rounded K as the full-square half path,
+# half the bytes again, read by the tensor-core form (MMAs of each tile against one-hot
+# label operands, FP32 accumulators in TMEM).  Cases span several super-tiles and ragged
+# edges (n not a multiple of 128) and both accumulator widths (N = 16 for k <= 16, 32 up
+# to 32).
+
+SYM_HALF = [("fp16", "rings", 0.1, None), ("bf16", "rings", 0.1, None), ("bf16", "blobs", 0.5, None),
+            ("fp16", "rings", 0.15, 14), ("bf16", "blobs", 0.5, 27)]   # FP16: Gaussian K only (|K| <= 1)
+
+
+@pytest.mark.parametrize("storage,name,scale,k", SYM_HALF)
+def test_half_k_symmetric_first_pass_matches_oracle_on_rounded_k(pc, storage, name, scale, k):
+    wl = synth.workload(name, scale=scale)
+    k = k or wl.k
+    lab = synth.init_labels(wl.P.shape[0], k, seed=8) if k != wl.k else wl.init_labels
+    r = pc.popcorn_fit(_dev(wl.P), k, wl.kernel, _dev(lab), max_iter=1, check_convergence=False,
+                       k_storage=storage, k_pass="symmetric", history=True)
+    assert r["info"]["k_pass_used"] == 1 and r["info"]["sym_form"] == 3
+    assert r["info"]["schedule"][3] == (16 if k <= 16 else 32)
+    K32, _ = pc.popcorn_kernel_matrix(_dev(wl.P), wl.kernel)
+    Kr = _rounded(K32.cpu().numpy(), storage)
+    st = oracle.step(Kr, lab, k)
+    assert rel_err(r["info"]["J_history"][0], st["J"]) <= 1e-5
+    rel = 2.0 ** -11 if storage == "fp16" else 2.0 ** -8
+    assert label_mismatches(r["labels"].cpu().numpy(), st, rel=rel)[0] == 0
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_half_k_symmetric_and_full_square_agree(pc, storage):
+    """Same rounded K, two reads of it: identical labels at every pass up to summation-order
+    near-ties, objectives to 1e-5."""
+    wl = synth.workload("rings", scale=0.15)
+    kw = dict(max_iter=wl.max_iter, check_convergence=False, k_storage=storage, history=True)
+    a = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), k_pass="symmetric", **kw)
+    b = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), k_pass="full", **kw)
+    assert a["info"]["k_pass_used"] == 1 and b["info"]["k_pass_used"] == 2 and a["info"]["sym_form"] == 3
+    Ja, Jb = np.array(a["info"]["J_history"]), np.array(b["info"]["J_history"])
+    assert np.all(np.abs(Ja - Jb) <= 1e-5 * np.abs(Jb))
+
+
+def test_half_k_symmetric_ragged_and_host_buffers(pc):
+    P = synth.gaussian_blobs(1001, 5, 3, seed=4, box=3.0)
+    lab = synth.init_labels(1001, 7, seed=5)
+    kern = {"kind": "gaussian", "gamma": 1.0, "coef0": 0.0, "degree": 1, "sigma": 2.0}
+    a = pc.popcorn_fit(P, 7, kern, lab, max_iter=20, k_storage="bf16", k_pass="symmetric")
+    b = pc.popcorn_fit(_dev(P), 7, kern, _dev(lab), max_iter=20, k_storage="bf16", k_pass="symmetric")
+    assert np.array_equal(a["labels"], b["labels"].cpu().numpy()) and a["objective"] == b["objective"]
+    c = pc.popcorn_fit(_dev(P), 7, kern, _dev(lab), max_iter=20, k_storage="bf16", k_pass="full")
+    assert a["info"]["k_pass_used"] == 1 and c["info"]["k_pass_used"] == 2
+    assert rel_err(a["objective"], c["objective"]) <= 1e-5
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_half_k_symmetric_sampled_rows_at_images_size(pc, storage):
+    """Images at full size (n = 70,000, d = 784, k = 10, Gaussian): the automatic choice
+    takes the symmetric pass on the half K (the packed triangle, 4.9 GB).  One pass from
+    the initial labels: sampled rows of E = K V^T (block edges, the ragged tail, random
+    rows) against the oracle's K rows rounded like the stored K; J against the identity
+    J = trace K - sum_c sum_{i in L_c} E_ic; every row's new label against the argmin of
+    D = K_ii - 2 E + ||c||^2 rebuilt from E in FP64 (near-ties exempt)."""
+    wl = synth.workload("images")
+    n, k = wl.n, wl.k
+    E = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    r = pc.popcorn_fit(_dev(wl.P), k, wl.kernel, _dev(wl.init_labels), max_iter=1, check_convergence=False,
+                       k_storage=storage, history=True, E_out=E)
+    assert r["info"]["k_pass_used"] == 1 and r["info"]["sym_form"] == 3
+    Eg = E.cpu().numpy().astype(np.float64)
+    lab = wl.init_labels.astype(np.int64)
+    m = np.bincount(lab, minlength=k).astype(np.float64)
+    rng = np.random.default_rng(1)
+    rows = np.unique(np.concatenate([[0, 1, 127, 128, 129, n - 129, n - 2, n - 1],
+                                     rng.choice(n, 40, replace=False)]))
+    # the oracle's rows, through FP32 (the build's type) and then the storage type
+    Kr = _rounded(oracle.kernel_matrix(wl.P[rows], wl.kernel, Q=wl.P).astype(np.float32), storage)
+    Eo = np.stack([Kr[:, lab == c].sum(axis=1) / m[c] for c in range(k)], axis=1)
+    assert np.max(np.abs(Eg[rows] - Eo)) <= 1e-5 * np.abs(Eo).max()
+    z = np.array([Eg[lab == c, c].sum() / m[c] for c in range(k)])
+    trace = float(n)                                   # Gaussian: K_ii = 1, exact in both types
+    J_E = trace - sum(Eg[lab == c, c].sum() for c in range(k))
+    assert rel_err(r["info"]["J_history"][0], J_E) <= 1e-6
+    D = 1.0 - 2.0 * Eg + z[None, :]
+    pred = np.argmin(D, axis=1)
+    part = np.partition(D, 1, axis=1)
+    exempt = (part[:, 1] - part[:, 0]) < 1e-6 * np.maximum(np.abs(part[:, 0]), 1.0)
+    got = r["labels"].cpu().numpy()
+    assert int(((got != pred) & ~exempt).sum()) == 0

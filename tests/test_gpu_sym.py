@@ -148,8 +148,9 @@ def test_symmetric_pass_launches_and_fallback(pc):
     per pass than the full square; the branch form, k <= 8 with a super-tile edge of 1,
     one more).  "auto" reads the full square below 8,192 points (K fits L2 and a pass is
     launch-bound, so at this size the whole fit runs in one launch) and takes the symmetric
-    pass from there on.  Above the cluster bound (32), or with a half-precision K, both fall
-    back to the full-square pass, with results identical to it."""
+    pass from there on.  Above the cluster bound (32) both fall back to the full-square pass,
+    with results identical to it; a half-precision K takes the sorted form on the half
+    layout."""
     P = torch.from_numpy(synth.gaussian_blobs(600, 3, 6, seed=9, box=3.0)).cuda()
     lab = torch.from_numpy(synth.init_labels(600, 6, seed=19)).cuda()
     a = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_pass="symmetric")
@@ -168,7 +169,7 @@ def test_symmetric_pass_launches_and_fallback(pc):
     assert big["info"]["k_pass_used"] == 1
     h = pc.popcorn_fit(P, 6, _gauss(1.0), lab, max_iter=5, check_convergence=False, k_storage="fp16",
                        k_pass="symmetric")
-    assert h["info"]["k_pass_used"] == 2
+    assert h["info"]["k_pass_used"] == 1
     lab40 = torch.from_numpy(synth.init_labels(600, 40, seed=29)).cuda()
     c = pc.popcorn_fit(P, 40, _gauss(1.0), lab40, max_iter=5, check_convergence=False, k_pass="symmetric")
     d = pc.popcorn_fit(P, 40, _gauss(1.0), lab40, max_iter=5, check_convergence=False, k_pass="full")

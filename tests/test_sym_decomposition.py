@@ -250,3 +250,56 @@ def test_sorted_lists_give_the_cluster_sums(valid, k, seed):
             if cl < valid:
                 ref = [tile[:valid, cl][lab[:valid] == cc].sum() for cc in range(k)]
                 np.testing.assert_allclose(got[:, e], ref, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------- the half layout (FP16 / BF16 K)
+
+def _sw4h_offset(r, c):
+    """Byte offset of element (r, c) of a tile in the half layout: two boxes of 128 rows x 64
+    columns, the 32-bit word of columns (2w, 2w + 1) of row r at word w ^ (r mod 32)."""
+    return 16384 * (c // 64) + 128 * r + 4 * (((c // 2) % 32) ^ (r % 32)) + 2 * (c % 2)
+
+
+def test_half_layout_is_a_bijection_and_conflict_free():
+    r, c = np.meshgrid(np.arange(B), np.arange(B), indexing="ij")
+    off = _sw4h_offset(r, c)
+    assert sorted(off.ravel().tolist()) == list(range(0, 2 * B * B, 2))
+    for col in range(B):                  # a column read by 32 consecutive rows: 32 banks
+        for r0 in range(0, B, 32):
+            assert len({(_sw4h_offset(rr, col) // 4) % 32 for rr in range(r0, r0 + 32)}) == 32
+    for row in range(B):                  # a box row's 32 words read by 32 lanes: 32 banks
+        for b0 in range(0, B, 64):
+            assert len({(_sw4h_offset(row, cc) // 4) % 32 for cc in range(b0, b0 + 64, 2)}) == 32
+
+
+def test_pack_half_word_mapping():
+    """pack_half_kernel's output word o (box o >> 12, row (o >> 5) & 127, column
+    64 box + 2 ((o & 31) ^ (row & 31))) holds exactly the two elements the half layout puts
+    there, read from the FP32 tile at their XOR-32 offsets."""
+    seen = set()
+    for o in range(8192):
+        b, r = o >> 12, (o >> 5) & 127
+        w = (o & 31) ^ (r & 31)
+        C = 64 * b + 2 * w
+        assert _sw4h_offset(r, C) == 4 * o and _sw4h_offset(r, C + 1) == 4 * o + 2
+        seen.add((r, C))
+    assert len(seen) == 8192
+
+
+def test_half_entries_xor_keys_give_the_offsets():
+    """Row warps keep the FP32 key and stride: the column entry of point l,
+    16384 (l >> 6) + 4 ((l >> 1) & 31) + 2 (l & 1), XOR 132 lane, plus 4096 e, is element
+    (row lane + 32 e, column l).  Column warps read one word: the row entry of point l,
+    128 l + 4 (l & 31), XOR 4 lane, plus 16384 part, is the word of columns
+    64 part + 2 lane and 64 part + 2 lane + 1 of row l.  All inside 32 KB."""
+    for l in range(B):
+        colent = 16384 * (l >> 6) + 4 * ((l >> 1) & 31) + 2 * (l & 1)
+        rowent = 128 * l + 4 * (l & 31)
+        for lane in range(32):
+            for e in range(4):
+                a = (colent ^ (132 * lane)) + 4096 * e
+                assert a == _sw4h_offset(lane + 32 * e, l) and 0 <= a < 32768
+            for part in range(2):
+                b = (rowent ^ (4 * lane)) + 16384 * part
+                assert b == _sw4h_offset(l, 64 * part + 2 * lane) and b + 2 == _sw4h_offset(l, 64 * part + 2 * lane + 1)
+                assert 0 <= b < 32768
