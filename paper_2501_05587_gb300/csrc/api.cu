@@ -219,14 +219,14 @@ popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, co
                                         maxr));
         return POPCORN_OK;
     }
-    if (k_storage != POPCORN_K_FP32)
+    if (k_storage != POPCORN_K_FP32 && packed != kPackedSw128H)
         return fail(POPCORN_ERR_UNSUPPORTED, "FP16/BF16 K storage comes from the FP32 build in this build");
     if (precision != POPCORN_BF16 && precision != POPCORN_BF16X3)
         return fail(POPCORN_ERR_UNSUPPORTED, "precision %d is not available for a stored K", precision);
     unsigned char* w;
     POPCORN_TRY(ws->alloc(&w, kbuild_tc_workspace(n, d, precision), "BF16 operands"));
     cudaError_t e = launch_kbuild_tc(P, n, d, ldp, kp, precision, static_cast<float*>(K), ldk, kdiag, w, err, num_sms,
-                                     s, launches, packed, full);
+                                     s, launches, packed, full, k_storage);
     if (e == cudaErrorInvalidValue)
         return fail(POPCORN_ERR_CUDA, "tensor map creation failed (cuTensorMapEncodeTiled unavailable or rejected)");
     POPCORN_CUDA(e);
@@ -842,9 +842,13 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     }
     POPCORN_CUDA(cudaMemsetAsync(b.counts, 0, 2 * (size_t)k * sizeof(int32_t), s));
     POPCORN_CUDA(launch_init_state(b.st, max_iter, opt.check_convergence ? 1 : 0, tol, s));
-    if (sym.packed && sym.ebytes == 2) {
-        // half layout: the build writes the FP32 triangle into a temporary, one pack launch
-        // rounds it into K (and rounds diag K with it), and the temporary goes back
+    if (sym.packed && sym.ebytes == 2 && opt.precision != POPCORN_FP32) {
+        // half layout from the tensor-core build: its epilogue rounds and stores the tiles
+        POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, ks, kdiag, &ws,
+                                        &b.st->wait_err, dev->sms, s, &launches, kPackedSw128H));
+    } else if (sym.packed && sym.ebytes == 2) {
+        // half layout from the FP32 build: it writes the FP32 triangle into a temporary, one
+        // pack launch rounds it into K (and rounds diag K with it), and the temporary goes back
         float* kf;
         POPCORN_TRY(ws.alloc(&kf, (size_t)sym.items * 128 * 128, "FP32 kernel matrix"));
         POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, kf, ldk, POPCORN_K_FP32, kdiag, &ws,

@@ -43,6 +43,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "popcorn_internal.cuh"
@@ -74,7 +75,8 @@ struct TcArgs {
     int off_sd, off_st, off_rj, off_bar, off_misc;
     long long tiles;          // sum_p (T - 2 p)
     float* Kp;                // block-packed K (tile (I, J), I <= J, at its row-by-row triangle index
-                              // times 16384 floats, four 128 x 32 boxes), or null
+                              // times 16384 floats, four 128 x 32 boxes; FP16 / BF16: times 32 KB,
+                              // two 128 x 64 boxes), or null
     int full;                 // 1: every tile of the square (the GEMM form), each stored once; 0: the
                               // tiles on and above the diagonal (the SYRK form), stored with their
                               // transposes unless K is packed
@@ -118,9 +120,26 @@ __device__ __forceinline__ float kappa(float b, float ri, float rj, const KernPa
     return expf(kp.neg_gamma_over_sigma2 * d2);
 }
 
-// SW4: the packed XOR-32 staging layout (kPackedSw4) -- a separate instance, since a
-// runtime choice between the two staging stores slowed the epilogue of both about 2.8x
-template <bool SW4>
+// Output of the epilogue, one instance each, since a runtime choice between staging stores
+// slowed the epilogue about 2.8x: kOutSw16 (full square through tensor maps, or the packed
+// triangle in the 128-byte swizzle), kOutSw4 (packed XOR-32, kPackedSw4), kOutHalf16 /
+// kOutHalfB16 (packed FP16 / BF16 triangle, kPackedSw128H: each 64-column box is staged
+// whole -- two 32-column chunks -- and stored with one bulk copy; entries past n are zeros).
+constexpr int kOutSw16 = 0, kOutSw4 = 1, kOutHalf16 = 2, kOutHalfB16 = 3;
+
+__device__ __forceinline__ uint32_t pack_half2(float x, float y, bool bf16) {
+    if (bf16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+    const __half2 h = __floats2half2_rn(x, y);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ float round_half(float x, bool bf16) {
+    return bf16 ? __bfloat162float(__float2bfloat16_rn(x)) : __half2float(__float2half_rn(x));
+}
+
+template <int OUT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     kbuild_tc_kernel(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_c,
                      const __grid_constant__ CUtensorMap map_kd, const __grid_constant__ CUtensorMap map_kt,
@@ -307,13 +326,56 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         if (lane == 0) mbar_arrive(acce_bar(ab));
                     }
                     if (!store) continue;
+                    constexpr bool HALF = OUT == kOutHalf16 || OUT == kOutHalfB16;
+                    constexpr bool HB16 = OUT == kOutHalfB16;
 #pragma unroll
                     for (int x = 0; x < 32; ++x) {
                         v[x] = kappa(v[x], ri, rj_s[32 * c + x], a.kp);
                         if (diag && 32 * c + x == row_local) {
                             if (a.kp.kind == POPCORN_GAUSSIAN) v[x] = 1.f;
-                            if (row < a.n) a.kdiag[row] = v[x];
+                            if (row < a.n) a.kdiag[row] = HALF ? round_half(v[x], HB16) : v[x];
                         }
+                    }
+                    if constexpr (HALF) {
+                        // box c / 2 of the half tile: staged over two chunks, stored after the second
+                        const int sbuf = a.nstg == 2 ? ((chunk_ctr >> 1) & 1) : 0;
+                        ++chunk_ctr;
+                        if ((c & 1) == 0) {
+                            // the store that last used this staging buffer has read it
+                            if (et == 0) {
+                                if (a.nstg == 2) bulk_wait_read<1>();
+                                else bulk_wait_read<0>();
+                            }
+                            epi_bar();
+                        }
+                        unsigned char* sb = smem + a.off_sd + sbuf * STG_BYTES;
+                        const int col0 = j * BM + 32 * c;
+                        const bool rv = row < a.n;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            // logical 16-byte chunk 4 (c mod 2) + i of the row, at its swizzled place
+                            uint32_t w[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int x = 8 * i + 2 * e;
+                                const float x0 = (rv && col0 + x < a.n) ? v[x] : 0.f;
+                                const float x1 = (rv && col0 + x + 1 < a.n) ? v[x + 1] : 0.f;
+                                w[e] = pack_half2(x0, x1, HB16);
+                            }
+                            const int pc = (4 * (c & 1) + i) ^ (row_local & 7);
+                            *reinterpret_cast<uint4*>(sb + row_local * 128 + 16 * pc) = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                        if (c & 1) {
+                            fence_proxy_async();
+                            epi_bar();
+                            if (et == 0) {
+                                const long long tri = (long long)rb * a.T - (long long)rb * (rb - 1) / 2 + (j - rb);
+                                bulk_store_1d(reinterpret_cast<unsigned char*>(a.Kp) + tri * 32768 + (c >> 1) * 16384,
+                                              smem_u32(sb), (uint32_t)STG_BYTES);
+                                bulk_commit();
+                            }
+                        }
+                        continue;
                     }
                     const int sbuf = a.nstg == 2 ? (chunk_ctr & 1) : 0;
                     ++chunk_ctr;
@@ -325,7 +387,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     epi_bar();
                     float* sd = reinterpret_cast<float*>(smem + a.off_sd + sbuf * STG_BYTES);
                     float* sx = reinterpret_cast<float*>(smem + a.off_st + sbuf * STG_BYTES);
-                    if constexpr (SW4) {
+                    if constexpr (OUT == kOutSw4) {
                         // packed XOR-32 layout: element x of row row_local at x ^ (row_local mod 32)
                         // (the 32 lanes hold 32 consecutive rows: 32 different banks per store)
 #pragma unroll
@@ -444,15 +506,22 @@ constexpr int kSmemBytes = RING_BYTES + 2 * STG_BYTES + BM * 4 + 16 * 8 + 16 + 1
 
 cudaError_t configure_kbuild_tc() {
     encode_fn();
-    const cudaError_t e = cudaFuncSetAttribute(kbuild_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               kSmemBytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(kbuild_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    decltype(&kbuild_tc_kernel<kOutSw16>) fs[4] = {kbuild_tc_kernel<kOutSw16>, kbuild_tc_kernel<kOutSw4>,
+                                                   kbuild_tc_kernel<kOutHalf16>, kbuild_tc_kernel<kOutHalfB16>};
+    for (auto f : fs) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
                              int64_t ldk, float* kdiag, void* workspace, int* err, int num_sms, cudaStream_t s,
-                             int* launches, int packed, int full) {
+                             int* launches, int packed, int full, int k_storage) {
+    // packed kPackedSw128H: K is the FP16 / BF16 packed triangle (k_storage)
+    const int half = packed == kPackedSw128H ? (k_storage == POPCORN_K_BF16 ? 2 : 1) : 0;
+    if (packed == kPackedSw128H && k_storage != POPCORN_K_FP16 && k_storage != POPCORN_K_BF16)
+        return cudaErrorInvalidValue;
     const int dpad = (d + BK - 1) / BK * BK;
     const int x3 = precision == POPCORN_BF16X3 ? 1 : 0;
     const int64_t ldw = (int64_t)(x3 ? 2 : 1) * dpad;
@@ -509,10 +578,14 @@ cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernPara
     const int smem = a.off_misc + 16 + 1024;
     if (smem > kSmemBytes) return cudaErrorInvalidConfiguration;
     const int grid = (int)(a.tiles < num_sms ? a.tiles : num_sms);
-    if (a.sw4)
-        kbuild_tc_kernel<true><<<grid, NTHREADS, smem, s>>>(mr, mc, mkd, mkt, a);
+    if (half == 1)
+        kbuild_tc_kernel<kOutHalf16><<<grid, NTHREADS, smem, s>>>(mr, mc, mkd, mkt, a);
+    else if (half == 2)
+        kbuild_tc_kernel<kOutHalfB16><<<grid, NTHREADS, smem, s>>>(mr, mc, mkd, mkt, a);
+    else if (a.sw4)
+        kbuild_tc_kernel<kOutSw4><<<grid, NTHREADS, smem, s>>>(mr, mc, mkd, mkt, a);
     else
-        kbuild_tc_kernel<false><<<grid, NTHREADS, smem, s>>>(mr, mc, mkd, mkt, a);
+        kbuild_tc_kernel<kOutSw16><<<grid, NTHREADS, smem, s>>>(mr, mc, mkd, mkt, a);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

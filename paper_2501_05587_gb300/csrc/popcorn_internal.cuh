@@ -203,10 +203,12 @@ cudaError_t configure_kbuild_tc();
 // precision POPCORN_BF16 or POPCORN_BF16X3; *err (device) becomes nonzero if a
 // bounded wait inside the kernel ran out.
 // packed: 0 = full square; kPackedSw16 / kPackedSw4 = the block-packed upper triangle
-// in that layout (as the FP32 build writes it for the symmetric pass); ldk is then unused.
+// in that layout (as the FP32 build writes it for the symmetric pass); kPackedSw128H = the
+// FP16 / BF16 packed triangle (k_storage), written directly with diag K rounded the same
+// way; ldk is then unused.
 cudaError_t launch_kbuild_tc(const float* P, int n, int d, int64_t ldp, KernParams kp, int precision, float* K,
                              int64_t ldk, float* kdiag, void* workspace, int* err, int num_sms, cudaStream_t s,
-                             int* launches, int packed = 0, int full = 0);
+                             int* launches, int packed = 0, int full = 0, int k_storage = POPCORN_K_FP32);
 
 // 2-D tiled TMA descriptor over a row-major matrix (inner = contiguous extent
 // in elements, row_bytes = pitch); false if the driver entry point is missing

@@ -40,6 +40,14 @@ def _rounded(K32, storage):
     return bf16_round64(K32)
 
 
+def _oracle_rounded(P, kern, storage):
+    """The oracle's K, rounded to FP32 (the build's type) and then to the storage type.  The
+    GPU's FP32 build differs from the FP32 rounding of the exact K by an FP32 ulp at most, so
+    the two half roundings differ only where a half boundary falls inside that ulp (about 1
+    entry in 2^13 for FP16): far below the bars below."""
+    return _rounded(oracle.kernel_matrix(P, kern).astype(np.float32), storage)
+
+
 def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
@@ -50,9 +58,7 @@ def test_half_k_first_pass_matches_oracle_on_rounded_k(pc, storage, name, scale)
     wl = synth.workload(name, scale=scale)
     r = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), max_iter=1, check_convergence=False,
                        k_storage=storage, history=True)
-    # the K the GPU rounds: its own FP32 build (checked against the oracle in the FP32 tests)
-    K32, _ = pc.popcorn_kernel_matrix(_dev(wl.P), wl.kernel)
-    Kr = _rounded(K32.cpu().numpy(), storage)
+    Kr = _oracle_rounded(wl.P, wl.kernel, storage)
     st = oracle.step(Kr, wl.init_labels, wl.k)
     assert rel_err(r["info"]["J_history"][0], st["J"]) <= 1e-5
     rel = 2.0 ** -11 if storage == "fp16" else 2.0 ** -8
@@ -99,8 +105,7 @@ def test_half_k_symmetric_first_pass_matches_oracle_on_rounded_k(pc, storage, na
                        k_storage=storage, k_pass="symmetric", history=True)
     assert r["info"]["k_pass_used"] == 1 and r["info"]["sym_form"] == 3
     assert r["info"]["schedule"][3] == (16 if k <= 16 else 32)
-    K32, _ = pc.popcorn_kernel_matrix(_dev(wl.P), wl.kernel)
-    Kr = _rounded(K32.cpu().numpy(), storage)
+    Kr = _oracle_rounded(wl.P, wl.kernel, storage)
     st = oracle.step(Kr, lab, k)
     assert rel_err(r["info"]["J_history"][0], st["J"]) <= 1e-5
     rel = 2.0 ** -11 if storage == "fp16" else 2.0 ** -8
@@ -120,6 +125,41 @@ def test_half_k_symmetric_and_full_square_agree(pc, storage):
     assert np.all(np.abs(Ja - Jb) <= 1e-5 * np.abs(Jb))
 
 
+@pytest.mark.parametrize("storage,precision", [("fp16", "bf16"), ("bf16", "bf16"), ("fp16", "bf16x3"),
+                                               ("bf16", "bf16x3")])
+def test_half_k_from_tensor_core_build_exact_on_small_integers(pc, storage, precision):
+    """The tensor-core builds write the half triangle directly.  Points with small integer
+    coordinates make every product and every entry of the linear K exact in BF16 and in the
+    storage type (|K_ij| <= 36), so one symmetric pass must be the oracle's step on the
+    exact K: labels equal, J to FP32 rounding of exact integer sums."""
+    rng = np.random.default_rng(21)
+    n, k = 3001, 9
+    P = rng.integers(-3, 4, size=(n, 4)).astype(np.float32)
+    lab = synth.init_labels(n, k, seed=22)
+    lin = {"kind": "linear", "gamma": 1.0, "coef0": 0.0, "degree": 1, "sigma": 1.0}
+    r = pc.popcorn_fit(_dev(P), k, lin, _dev(lab), max_iter=1, check_convergence=False, k_storage=storage,
+                       precision=precision, k_pass="symmetric", history=True)
+    assert r["info"]["k_pass_used"] == 1 and r["info"]["sym_form"] == 3
+    st = oracle.step(oracle.kernel_matrix(P, lin), lab, k)
+    assert rel_err(r["info"]["J_history"][0], st["J"]) <= 1e-6
+    assert label_mismatches(r["labels"].cpu().numpy(), st, rel=1e-6)[0] == 0
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_half_k_from_bf16x3_build_gaussian(pc, storage):
+    """BF16X3 build, half K written by its epilogue (the bench's fast form): one pass against
+    the oracle's step on its K rounded to the storage type.  BF16X3 entries carry ~16
+    significant bits (relative error ~1e-5 at this sigma), which the J bar allows for."""
+    wl = synth.workload("rings", scale=0.15)
+    r = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), max_iter=1, check_convergence=False,
+                       k_storage=storage, precision="bf16x3", k_pass="symmetric", history=True)
+    assert r["info"]["k_pass_used"] == 1 and r["info"]["sym_form"] == 3
+    st = oracle.step(_oracle_rounded(wl.P, wl.kernel, storage), wl.init_labels, wl.k)
+    assert rel_err(r["info"]["J_history"][0], st["J"]) <= 5e-5
+    rel = 2.0 ** -10 if storage == "fp16" else 2.0 ** -7
+    assert label_mismatches(r["labels"].cpu().numpy(), st, rel=rel)[0] == 0
+
+
 def test_half_k_symmetric_ragged_and_host_buffers(pc):
     P = synth.gaussian_blobs(1001, 5, 3, seed=4, box=3.0)
     lab = synth.init_labels(1001, 7, seed=5)
@@ -132,8 +172,8 @@ def test_half_k_symmetric_ragged_and_host_buffers(pc):
     assert rel_err(a["objective"], c["objective"]) <= 1e-5
 
 
-@pytest.mark.parametrize("storage", ["fp16", "bf16"])
-def test_half_k_symmetric_sampled_rows_at_images_size(pc, storage):
+@pytest.mark.parametrize("storage,precision", [("fp16", "fp32"), ("bf16", "fp32"), ("fp16", "bf16x3")])
+def test_half_k_symmetric_sampled_rows_at_images_size(pc, storage, precision):
     """Images at full size (n = 70,000, d = 784, k = 10, Gaussian): the automatic choice
     takes the symmetric pass on the half K (the packed triangle, 4.9 GB).  One pass from
     the initial labels: sampled rows of E = K V^T (block edges, the ragged tail, random
@@ -144,7 +184,7 @@ def test_half_k_symmetric_sampled_rows_at_images_size(pc, storage):
     n, k = wl.n, wl.k
     E = torch.empty((n, k), dtype=torch.float32, device="cuda")
     r = pc.popcorn_fit(_dev(wl.P), k, wl.kernel, _dev(wl.init_labels), max_iter=1, check_convergence=False,
-                       k_storage=storage, history=True, E_out=E)
+                       k_storage=storage, precision=precision, history=True, E_out=E)
     assert r["info"]["k_pass_used"] == 1 and r["info"]["sym_form"] == 3
     Eg = E.cpu().numpy().astype(np.float64)
     lab = wl.init_labels.astype(np.int64)
@@ -155,7 +195,8 @@ def test_half_k_symmetric_sampled_rows_at_images_size(pc, storage):
     # the oracle's rows, through FP32 (the build's type) and then the storage type
     Kr = _rounded(oracle.kernel_matrix(wl.P[rows], wl.kernel, Q=wl.P).astype(np.float32), storage)
     Eo = np.stack([Kr[:, lab == c].sum(axis=1) / m[c] for c in range(k)], axis=1)
-    assert np.max(np.abs(Eg[rows] - Eo)) <= 1e-5 * np.abs(Eo).max()
+    # BF16X3 entries carry ~16 significant bits: a looser bar on the sampled rows
+    assert np.max(np.abs(Eg[rows] - Eo)) <= (1e-5 if precision == "fp32" else 5e-5) * np.abs(Eo).max()
     z = np.array([Eg[lab == c, c].sum() / m[c] for c in range(k)])
     trace = float(n)                                   # Gaussian: K_ii = 1, exact in both types
     J_E = trace - sum(Eg[lab == c, c].sum() for c in range(k))

@@ -253,53 +253,93 @@ def test_sorted_lists_give_the_cluster_sums(valid, k, seed):
 
 
 # ---------------------------------------------------------------- the half layout (FP16 / BF16 K)
+# The tensor-core form reads tiles in the 128-byte swizzle of the MMA shared-memory operands:
+# within each 1024-byte group of 8 rows of 128 bytes, 16-byte chunk j of row r sits at chunk
+# j ^ (r mod 8).  Below, the operand views are modelled as the canonical layouts composed
+# with that swizzle, and checked to address the element the math needs.
 
-def _sw4h_offset(r, c):
-    """Byte offset of element (r, c) of a tile in the half layout: two boxes of 128 rows x 64
-    columns, the 32-bit word of columns (2w, 2w + 1) of row r at word w ^ (r mod 32)."""
-    return 16384 * (c // 64) + 128 * r + 4 * (((c // 2) % 32) ^ (r % 32)) + 2 * (c % 2)
+def _sw128h_offset(r, c):
+    """Byte offset of element (r, c) of a tile in the half layout kPackedSw128H: two boxes of
+    128 rows x 64 columns (16 KB each), chunk (c mod 64) // 8 of row r swizzled by r mod 8."""
+    return 16384 * (c // 64) + 128 * r + 16 * (((c % 64) // 8) ^ (r % 8)) + 2 * (c % 8)
 
 
-def test_half_layout_is_a_bijection_and_conflict_free():
+def _swizzle128(addr):
+    """The 128-byte swizzle on byte addresses (1024-byte aligned base): bits 4-6 ^= bits 7-9."""
+    return addr ^ (((addr >> 7) & 7) << 4)
+
+
+def test_half_layout_is_a_bijection_and_the_swizzle_of_row_major_boxes():
     r, c = np.meshgrid(np.arange(B), np.arange(B), indexing="ij")
-    off = _sw4h_offset(r, c)
+    off = _sw128h_offset(r, c)
     assert sorted(off.ravel().tolist()) == list(range(0, 2 * B * B, 2))
-    for col in range(B):                  # a column read by 32 consecutive rows: 32 banks
-        for r0 in range(0, B, 32):
-            assert len({(_sw4h_offset(rr, col) // 4) % 32 for rr in range(r0, r0 + 32)}) == 32
-    for row in range(B):                  # a box row's 32 words read by 32 lanes: 32 banks
-        for b0 in range(0, B, 64):
-            assert len({(_sw4h_offset(row, cc) // 4) % 32 for cc in range(b0, b0 + 64, 2)}) == 32
+    for rr in range(B):
+        for cc in range(B):
+            plain = 16384 * (cc // 64) + 128 * rr + 2 * (cc % 64)      # row-major 128 x 64 boxes
+            assert _sw128h_offset(rr, cc) == _swizzle128(plain)
 
 
 def test_pack_half_word_mapping():
     """pack_half_kernel's output word o (box o >> 12, row (o >> 5) & 127, column
-    64 box + 2 ((o & 31) ^ (row & 31))) holds exactly the two elements the half layout puts
-    there, read from the FP32 tile at their XOR-32 offsets."""
+    64 box + 8 (((o >> 2) & 7) ^ (row & 7)) + 2 (o & 3)) holds the two elements the layout
+    puts at bytes 4 o and 4 o + 2; every element is written once."""
     seen = set()
     for o in range(8192):
         b, r = o >> 12, (o >> 5) & 127
-        w = (o & 31) ^ (r & 31)
-        C = 64 * b + 2 * w
-        assert _sw4h_offset(r, C) == 4 * o and _sw4h_offset(r, C + 1) == 4 * o + 2
+        C = 64 * b + 8 * (((o >> 2) & 7) ^ (r & 7)) + 2 * (o & 3)
+        assert _sw128h_offset(r, C) == 4 * o and _sw128h_offset(r, C + 1) == 4 * o + 2
         seen.add((r, C))
     assert len(seen) == 8192
 
 
-def test_half_entries_xor_keys_give_the_offsets():
-    """Row warps keep the FP32 key and stride: the column entry of point l,
-    16384 (l >> 6) + 4 ((l >> 1) & 31) + 2 (l & 1), XOR 132 lane, plus 4096 e, is element
-    (row lane + 32 e, column l).  Column warps read one word: the row entry of point l,
-    128 l + 4 (l & 31), XOR 4 lane, plus 16384 part, is the word of columns
-    64 part + 2 lane and 64 part + 2 lane + 1 of row l.  All inside 32 KB."""
-    for l in range(B):
-        colent = 16384 * (l >> 6) + 4 * ((l >> 1) & 31) + 2 * (l & 1)
-        rowent = 128 * l + 4 * (l & 31)
-        for lane in range(32):
-            for e in range(4):
-                a = (colent ^ (132 * lane)) + 4096 * e
-                assert a == _sw4h_offset(lane + 32 * e, l) and 0 <= a < 32768
-            for part in range(2):
-                b = (rowent ^ (4 * lane)) + 16384 * part
-                assert b == _sw4h_offset(l, 64 * part + 2 * lane) and b + 2 == _sw4h_offset(l, 64 * part + 2 * lane + 1)
-                assert 0 <= b < 32768
+def _kmajor_sw128(start, m, kidx, sbo=1024):
+    """K-major operand, 128-byte swizzle: row m of 64 elements (128 bytes), 8-row groups sbo
+    apart; element kidx < 16 of the K = 16 slice that starts at byte `start`."""
+    return _swizzle128(start + (m // 8) * sbo + (m % 8) * 128 + 2 * kidx)
+
+
+def _mnmajor_sw128(start, m, kidx, lbo, sbo):
+    """MN-major operand, 128-byte swizzle: atoms of 64 elements along M (one 128-byte row) by
+    8 reduction rows; atoms lbo apart along M, 8-row groups sbo apart along the reduction."""
+    return _swizzle128(start + (m // 64) * lbo + (kidx // 8) * sbo + (kidx % 8) * 128 + 2 * (m % 64))
+
+
+def test_tile_is_the_k_major_operand_of_the_row_sums():
+    """Row sums R = K V_J^T: A[m = r][kk-th slice, element e] must be K[r][16 kk + e], from
+    start = 16384 (kk >> 2) + 32 (kk & 3) (16 columns = 32 bytes along a row, box 2 at 16 KB)."""
+    for kk in range(8):
+        start = 16384 * (kk >> 2) + 32 * (kk & 3)
+        for r in range(B):
+            for e in range(16):
+                assert _kmajor_sw128(start - 32 * (kk & 3), r, 16 * (kk & 3) + e) == _sw128h_offset(r, 16 * kk + e)
+
+
+def test_tile_is_the_mn_major_operand_of_the_column_sums():
+    """Column sums C = K^T V_I^T: A'[m = column c][kk-th slice, element e] must be
+    K[16 kk + e][c], from start = 2048 kk (16 rows), atoms 16 KB apart (lbo), 8-row groups
+    1 KB apart (sbo); and every byte it reads lies inside the 32 KB tile."""
+    for kk in range(8):
+        for c in range(B):
+            for e in range(16):
+                a = _mnmajor_sw128(2048 * kk, c, e, lbo=16384, sbo=1024)
+                assert a == _sw128h_offset(16 * kk + e, c) and 0 <= a < 32768
+
+
+def test_onehot_operand_layout():
+    """sym_onehot_kernel: 16-byte chunk q = (box, c, ch) holds points 64 box + 8 (ch ^ (c mod 8))
+    + 0..7 of cluster row c -- the K-major swizzled operand of N rows: B[n = c][kk-th slice,
+    element e] = V[c][16 kk + e] from start (N x 128) (kk >> 2) + 32 (kk & 3)."""
+    for N in (16, 32):
+        where = {}
+        for q in range(N * 16):
+            box, c, ch = q // (N * 8), (q >> 3) % N, q & 7
+            i0 = 64 * box + 8 * (ch ^ (c & 7))
+            for e in range(8):
+                where[(c, i0 + e)] = 16 * q + 2 * e
+        assert len(where) == N * B
+        for kk in range(8):
+            base = N * 128 * (kk >> 2)
+            for c in range(N):
+                for e in range(16):
+                    i = 16 * kk + e
+                    assert _kmajor_sw128(base, c, 16 * (kk & 3) + e) == where[(c, i)]
