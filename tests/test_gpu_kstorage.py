@@ -207,3 +207,50 @@ def test_half_k_symmetric_sampled_rows_at_images_size(pc, storage, precision):
     exempt = (part[:, 1] - part[:, 0]) < 1e-6 * np.maximum(np.abs(part[:, 0]), 1.0)
     got = r["labels"].cpu().numpy()
     assert int(((got != pred) & ~exempt).sum()) == 0
+
+
+HALF_EDGE_CASES = [
+    # (n, d, k, sigma, seed): Gaussian (|K| <= 1, FP16-safe)
+    (97, 3, 3, 1.0, 1),          # one block, ragged
+    (1030, 9, 8, 2.0, 3),        # ragged
+    (1280, 4, 16, 1.0, 6),       # n a multiple of 128, N = 16 at its bound
+    (2000, 5, 24, 1.5, 12),      # N = 32
+    (4099, 6, 32, 2.0, 13),      # k at the bound (32), n % 128 = 3
+]
+
+
+@pytest.mark.parametrize("sym_tile", [0, 1, 2, 3, 5, 8])
+@pytest.mark.parametrize("n,d,k,sigma,seed", HALF_EDGE_CASES)
+def test_half_k_symmetric_every_super_tile_edge(pc, n, d, k, sigma, seed, sym_tile):
+    """Every super-tile edge of the tensor-core form: the 2a accumulators of N columns,
+    double-buffered, must fit TMEM's 512 columns (a <= 8 for N = 16, a <= 4 for N = 32); a
+    larger forced edge falls back to the full square.  Either way one pass is the oracle's
+    step on the rounded K."""
+    P = synth.gaussian_blobs(n, d, k, seed=seed, box=3.0)
+    lab = synth.init_labels(n, k, seed=seed + 100)
+    kern = {"kind": "gaussian", "gamma": 1.0, "coef0": 0.0, "degree": 1, "sigma": sigma}
+    r = pc.popcorn_fit(_dev(P), k, kern, _dev(lab), max_iter=1, check_convergence=False, k_storage="fp16",
+                       k_pass="symmetric", sym_tile=sym_tile, history=True)
+    amax = 8 if k <= 16 else 4
+    if sym_tile <= amax:
+        assert r["info"]["k_pass_used"] == 1 and r["info"]["sym_form"] == 3
+        if sym_tile:
+            assert r["info"]["schedule"][0] == sym_tile
+            T = (n + 127) // 128
+            assert r["info"]["schedule"][2] == (T + sym_tile - 1) // sym_tile + 1   # slots: Ts + 1
+    else:
+        assert r["info"]["k_pass_used"] == 2
+    st = oracle.step(_oracle_rounded(P, kern, "fp16"), lab, k)
+    assert rel_err(r["info"]["J_history"][0], st["J"]) <= 1e-5
+    assert label_mismatches(r["labels"].cpu().numpy(), st, rel=2.0 ** -11)[0] == 0
+
+
+def test_half_k_symmetric_is_deterministic(pc):
+    """Fixed block order, fixed MMA order into each accumulator, fixed fold order: repeated
+    fits give bit-identical objectives and labels."""
+    wl = synth.workload("rings", scale=0.25)
+    runs = [pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), max_iter=10, check_convergence=False,
+                           k_storage="bf16", k_pass="symmetric", history=True) for _ in range(3)]
+    for r in runs[1:]:
+        assert r["info"]["J_history"] == runs[0]["info"]["J_history"]
+        assert torch.equal(r["labels"], runs[0]["labels"])
