@@ -103,8 +103,11 @@ typedef struct {
                                    passes and the final objective pass as one CUDA graph,
                                    captured on a private stream and launched on `stream`
                                    (plain launches when `stream` is itself being captured)   */
-    int32_t k_storage;          /* popcorn_k_storage of the stored K (FP32 build only for the
-                                   half types); 0 = FP32                                    */
+    int32_t k_storage;          /* popcorn_k_storage of the stored K; 0 = FP32.  FP16 / BF16
+                                   from any build: the FP32 build rounds its K (full square,
+                                   or the packed triangle through one pack launch); the BF16
+                                   / BF16X3 builds write only the packed triangle of the
+                                   symmetric pass (k <= 32)                                  */
     int32_t autotune;           /* 1: pick the schedule by timing candidates on this workload
                                    (first call per workload signature; later calls reuse the
                                    cached choice, see popcorn_autotune_entries); 0: fixed
@@ -115,7 +118,9 @@ typedef struct {
     int32_t k_pass;             /* how a pass reads a stored K.  0 = automatic (the
                                    default): the symmetric read below for n >= 8192 (where K
                                    outgrows L2 and reading half of it pays; measured faster
-                                   on GB300 for every k up to 32), else the full square.
+                                   on GB300 for every k up to 32), and at every n for an
+                                   FP16 / BF16 K from a BF16 / BF16X3 build (that build
+                                   writes only the packed triangle); else the full square.
                                    1 = symmetric (k <= 32; larger k falls back to the full
                                    square): only the 128 x 128 blocks on and above the
                                    diagonal (K is symmetric, and is then stored as that packed
@@ -312,7 +317,8 @@ POPCORN_API popcorn_status popcorn_assign_step(const float* K, int64_t ldk, cons
  * (FP8 runs on the recompute path only), for store_k = 0 with POPCORN_FP32 or
  * POPCORN_BF16X3 (the recompute path runs in POPCORN_BF16 or POPCORN_FP8), and
  * for a recompute request with d or k beyond its limits (d <= 256 for BF16,
- * d <= 512 for FP8); POPCORN_ERR_NOMEM when K (or the workspace) does not fit
+ * d <= 512 for FP8), and for an FP16 / BF16 K from a BF16 / BF16X3 build read
+ * as the full square (k > 32, or k_pass = 2); POPCORN_ERR_NOMEM when K (or the workspace) does not fit
  * in device memory; POPCORN_ERR_TIMEOUT when a bounded wait inside a
  * tensor-core or symmetric-pass kernel ran out (the context stays usable).
  */

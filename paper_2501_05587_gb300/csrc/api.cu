@@ -220,7 +220,9 @@ popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, co
         return POPCORN_OK;
     }
     if (k_storage != POPCORN_K_FP32 && packed != kPackedSw128H)
-        return fail(POPCORN_ERR_UNSUPPORTED, "FP16/BF16 K storage comes from the FP32 build in this build");
+        return fail(POPCORN_ERR_UNSUPPORTED,
+                    "an FP16/BF16 K from a BF16/BF16X3 build is written only as the packed triangle of the "
+                    "symmetric pass (k <= 32, k_pass 0 or 1)");
     if (precision != POPCORN_BF16 && precision != POPCORN_BF16X3)
         return fail(POPCORN_ERR_UNSUPPORTED, "precision %d is not available for a stored K", precision);
     unsigned char* w;
@@ -747,7 +749,9 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // n = 70,000, k = 10: 1.67 ms a stream plus 0.09 ms of fold against 3.05 ms for the
     // full square; rings, n = 20,000, k = 4: 0.152 + 0.014 against 0.275).  Below that a
     // pass is a few microseconds of launches and the full square's two kernels win.
-    const bool sym_auto = ni >= kSymAutoMinN;
+    // A half K from a tensor-core build exists only as the packed triangle (its epilogue
+    // writes FP16 / BF16 boxes for the symmetric pass), so that pairing takes it at every n.
+    const bool sym_auto = ni >= kSymAutoMinN || (ks != POPCORN_K_FP32 && opt.precision != POPCORN_FP32);
     if (opt.k_pass == 1 || (opt.k_pass == 0 && sym_auto))
         sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin, opt.sym_tile, 0, (int)kelem);
     const bool use_sym = sym.ok;

@@ -254,3 +254,24 @@ def test_half_k_symmetric_is_deterministic(pc):
     for r in runs[1:]:
         assert r["info"]["J_history"] == runs[0]["info"]["J_history"]
         assert torch.equal(r["labels"], runs[0]["labels"])
+
+
+def test_half_k_from_tensor_core_build_auto_choice_and_limits(pc):
+    """A half K from a BF16 / BF16X3 build exists only as the packed triangle: the automatic
+    read takes the tensor-core symmetric form at any n (here n = 2,500, below the FP32
+    threshold), and a request that needs the full square (k > 32, or k_pass = "full") is
+    refused with POPCORN_ERR_UNSUPPORTED; the context stays usable."""
+    wl = synth.workload("images", scale=2500 / 70000)
+    n = wl.P.shape[0]
+    r = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), max_iter=3, check_convergence=False,
+                       k_storage="fp16", precision="bf16x3", history=True)
+    assert r["info"]["k_pass_used"] == 1 and r["info"]["sym_form"] == 3
+    for k, kp in ((40, "auto"), (wl.k, "full")):
+        lab = synth.init_labels(n, k, seed=3)
+        with pytest.raises(pc.PopcornError) as ei:
+            pc.popcorn_fit(_dev(wl.P), k, wl.kernel, _dev(lab), max_iter=2, k_storage="bf16", precision="bf16x3",
+                           k_pass=kp)
+        assert ei.value.status == 5          # POPCORN_ERR_UNSUPPORTED
+    again = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), max_iter=3, check_convergence=False,
+                           k_storage="fp16", precision="bf16x3", history=True)
+    assert again["info"]["J_history"] == r["info"]["J_history"]
