@@ -209,7 +209,7 @@ def pass_roofline(wl, prof, pk, k_storage="fp32"):
             "peak_source": pk["source"] + " HBM copy", "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms}
 
 
-def kbuild_roofline(wl, precision, kb_ms, pk):
+def kbuild_roofline(wl, precision, kb_ms, pk, k_storage="fp32"):
     """Roofline of the K build.  FP32 (CUDA cores): bound by the FP32 lanes -- a Gaussian entry
     takes a subtract and a multiply-add per coordinate, a polynomial / linear one a multiply-add,
     over the n (n + 1) / 2 unique pairs; peak = 128 lanes x 152 SMs x the maximum SM clock.
@@ -249,7 +249,9 @@ def kbuild_roofline(wl, precision, kb_ms, pk):
     ach = flops / sec / 1e12
     return {"kernel": "kbuild_tc_kernel", "bound": "tensor", "achieved": ach, "peak": pk["bf16"], "unit": "TFLOP/s",
             "frac": ach / pk["bf16"],
-            "traffic": (recorded_traffic("kbuild_tc_kernel", "kbuild_tc.cu", wl.name) if precision == "bf16x3" else None),
+            "traffic": (recorded_traffic("kbuild_tc_kernel" + ("" if k_storage == "fp32" else f"[{k_storage} K]"),
+                                         "kbuild_tc.cu", wl.name) if precision == "bf16x3" else None),
+            "k_storage": k_storage,
             "peak_source": pk["source"] + " bf16 burst",
             "executed_mma_flops_per_launch": flops, "avg_launch_ms": kb_ms}
 
@@ -863,7 +865,7 @@ def main():
         rooflines = []
         if wl.store_k:
             rp = pass_roofline(wl, prof, pk, args.k_storage)
-            rk = kbuild_roofline(wl, wl.precision, kb_ms, pk)
+            rk = kbuild_roofline(wl, wl.precision, kb_ms, pk, args.k_storage)
             pass_total = s["breakdown_ms_per_fit"]["reduce"] - sum(r["info"]["fold_ms"] for r in prof) / len(prof)
             # the dominant kernel of a fit: the K build or the stream kernel summed over the passes
             rooflines = [rk, rp] if kb_ms >= pass_total else [rp, rk]
@@ -920,7 +922,7 @@ def main():
                 fs["k_storage"] = kst
                 fs["objective_rel_diff_vs_fp32_fit"] = abs(fs["objective"] - s["objective"]) / abs(s["objective"])
                 fs["speedup_vs_fp32_fit"] = fs["value"] / value
-                fs["roofline_kbuild"] = kbuild_roofline(wl, prec, fs["kbuild_ms"], pk)
+                fs["roofline_kbuild"] = kbuild_roofline(wl, prec, fs["kbuild_ms"], pk, kst)
                 fs["roofline_pass"] = pass_roofline(wl, f["prof"], pk, kst)
                 forms[key] = fs
                 line[key] = fs
