@@ -487,7 +487,7 @@ def leg_workload(pc, torch, stream, name, steps, warmup, pk, **kw):
     return s, wl, f
 
 
-def leg_batched(pc, torch, stream, steps, warmup, precision, autotune, scale=1.0):
+def leg_batched(pc, torch, stream, steps, warmup, precision, autotune, scale=1.0, k_storage="fp32"):
     """256 independent instances (n in [500, 8000], d in {8, 32, 64}, k in [4, 64], polynomial and
     Gaussian kernels), 30 passes each, one popcorn_fit_batched call (one CUDA graph) per step."""
     import synth
@@ -498,25 +498,31 @@ def leg_batched(pc, torch, stream, steps, warmup, precision, autotune, scale=1.0
 
     def step():
         return pc.popcorn_fit_batched(insts, max_iter=30, precision=precision, check_convergence=False, timing=True,
-                                      autotune=autotune)
+                                      autotune=autotune, k_storage=k_storage)
 
     ms, res = timed(torch, stream, step, steps, warmup)
     passes = sum(sum(r["iterations"]) for r in res)
-    kbytes = sum(4.0 * w.n * w.n for w in wls)
+    kbytes = sum((4.0 if k_storage == "fp32" else 2.0) * w.n * w.n for w in wls)
     graph_ms = sum(r["info"]["loop_ms"] for r in res) / len(res)
-    e2 = torch.cuda.Event(enable_timing=True)
-    e3 = torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    for x in insts:
-        pc.popcorn_fit(x["P"], x["k"], x["kernel"], x["init_labels"], max_iter=30, precision=precision,
-                       check_convergence=False)
-    e3.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = e2.elapsed_time(e3)
+    # the same instances as separate fits (a half K from a tensor-core build exists only for the
+    # symmetric pass's k <= 32, so that pairing has no separate-fit counterpart for every instance)
+    seq_ms = None
+    if k_storage == "fp32" or precision == "fp32":
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for x in insts:
+            pc.popcorn_fit(x["P"], x["k"], x["kernel"], x["init_labels"], max_iter=30, precision=precision,
+                           check_convergence=False, k_storage=k_storage)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = e2.elapsed_time(e3)
     return {"value": passes / (ms / 1e3), "unit": "instance-passes/s", "ms_per_step": ms / steps,
-            "precision": precision, "instances": len(wls), "K_GB": kbytes / 1e9,
+            "precision": precision, "k_storage": k_storage, "instances": len(wls), "K_GB": kbytes / 1e9,
+            "_objectives": res[-1]["objectives"],
             "graph_ms": graph_ms, "effective_GBps_of_K_reads": kbytes * 30 / (graph_ms / 1e3) / 1e9,
-            "separate_fits_ms": seq_ms, "batched_speedup_vs_separate_fits": seq_ms / (ms / steps),
+            "separate_fits_ms": seq_ms,
+            "batched_speedup_vs_separate_fits": seq_ms / (ms / steps) if seq_ms else None,
             "gpu_launches_per_step": res[-1]["info"]["kernel_launches"],
             "schedule": {"autotune": autotune, "columns_per_unit": res[-1]["info"]["schedule"][0],
                          "warps_per_block": res[-1]["info"]["schedule"][1],
@@ -530,12 +536,14 @@ def run_batched(args):
 
     prec = args.precision or "fp32"
     stream = torch.cuda.current_stream()
-    s = leg_batched(pc, torch, stream, args.steps, args.warmup, prec, args.autotune == "on", args.scale)
+    s = leg_batched(pc, torch, stream, args.steps, args.warmup, prec, args.autotune == "on", args.scale,
+                    k_storage=args.k_storage)
+    s.pop("_objectives", None)
     line = {"metric": METRIC, "value": s["value"], "unit": s["unit"], "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": s["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec, "data": "synthetic",
-            "config": {"workload": f"batched: {s['instances']} instances, 30 passes each, K stored FP32 "
-                                   f"({s['K_GB']:.1f} GB)", "precision": prec},
+            "config": {"workload": f"batched: {s['instances']} instances, 30 passes each, K stored "
+                                   f"{args.k_storage.upper()} ({s['K_GB']:.1f} GB)", "precision": prec},
             "gpu_launches": s["gpu_launches_per_step"] * args.steps, "batched": s}
     print(json.dumps(line), flush=True)
     return 0
@@ -945,12 +953,23 @@ def main():
                     extras[name] = es
                 except Exception as ex:   # an extra leg never hides the headline
                     extras[name] = {"error": f"{type(ex).__name__}: {ex}"}
-            for prec in ("fp32", "bf16"):
+            # batched forms: FP32 and BF16 builds with an FP32 K, and the FP32 build with a BF16 K
+            # (every square rounded once, read by the tensor-core stream); objectives against the
+            # FP32 form's, instance by instance
+            for key, prec, kst in (("batched_fp32", "fp32", "fp32"), ("batched_bf16", "bf16", "fp32"),
+                                   ("batched_fp32_k_bf16", "fp32", "bf16")):
                 try:
-                    extras[f"batched_{prec}"] = leg_batched(pc, torch, stream, max(3, args.steps // 4), args.warmup,
-                                                            prec, args.autotune == "on")
+                    extras[key] = leg_batched(pc, torch, stream, max(3, args.steps // 4), args.warmup, prec,
+                                              args.autotune == "on", k_storage=kst)
                 except Exception as ex:
-                    extras[f"batched_{prec}"] = {"error": f"{type(ex).__name__}: {ex}"}
+                    extras[key] = {"error": f"{type(ex).__name__}: {ex}"}
+            ref = extras.get("batched_fp32", {}).get("_objectives")
+            for key in ("batched_fp32", "batched_bf16", "batched_fp32_k_bf16"):
+                o = extras.get(key, {}).pop("_objectives", None)
+                if ref and o and key != "batched_fp32":
+                    extras[key]["objective_max_rel_diff_vs_fp32_batched"] = max(
+                        abs(a - b) / abs(b) for a, b in zip(o, ref))
+                    extras[key]["speedup_vs_fp32_batched"] = extras[key]["value"] / extras["batched_fp32"]["value"]
             line["extras"] = extras
         if world == 1 and not args.no_cpu_baseline:
             n_s = min(SAMPLE.get(wl.name.split("_")[0], 2000), wl.n)

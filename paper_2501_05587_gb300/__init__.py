@@ -335,11 +335,12 @@ def popcorn_fit(P, k: int, kernel: dict, init_labels, max_iter: int, tol: float 
 
 def popcorn_fit_batched(instances, max_iter: int, tol: float = 0.0, precision: str = "fp32",
                         check_convergence: bool = True, timing: bool = False, autotune: bool = False,
-                        stream=None) -> dict:
+                        k_storage: str = "fp32", stream=None) -> dict:
     """Many independent fits in one captured CUDA graph.
 
     ``instances``: list of dicts {"P": (n, d) float32 CUDA tensor, "k": int, "kernel": dict,
-    "init_labels": (n,) int32 CUDA tensor, optional "labels_out"}.  Returns
+    "init_labels": (n,) int32 CUDA tensor, optional "labels_out"}.  ``k_storage`` ("fp32",
+    "fp16", "bf16"): the element type every instance's stored K is rounded to.  Returns
     {"labels": [tensor], "objectives": [float], "iterations": [int], "info": dict}.
     """
     torch = _torch()
@@ -357,7 +358,7 @@ def popcorn_fit_batched(instances, max_iter: int, tol: float = 0.0, precision: s
         outs.append(out)
         arr[t] = _Instance(P.data_ptr(), P.shape[0], P.shape[1], P.stride(0), int(x["k"]), _kernel(x["kernel"]),
                            lab.data_ptr(), out.data_ptr())
-    opt = _Options(PRECISION[precision], 1, 1 if check_convergence else 0, 1 if timing else 0, 0,
+    opt = _Options(PRECISION[precision], 1, 1 if check_convergence else 0, 1 if timing else 0, K_STORAGE[k_storage],
                    1 if autotune else 0, 0, 0, (ctypes.c_int64 * 4)())
     objs = (ctypes.c_double * len(instances))()
     its = (ctypes.c_int32 * len(instances))()

@@ -3,6 +3,7 @@
 // control lives on the device).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -85,6 +86,7 @@ popcorn_status device_info(DeviceInfo** out) {
         POPCORN_CUDA(configure_kbuild_tc());
         POPCORN_CUDA(configure_recompute(d.smem_optin, &d.recompute_smem));
         POPCORN_CUDA(configure_batched(d.smem_optin));
+        POPCORN_CUDA(configure_batched_mma(d.smem_optin));
         POPCORN_CUDA(configure_reduce_sym(d.smem_optin));
         POPCORN_CUDA(configure_pack_half());
         POPCORN_CUDA(configure_sym_mma(d.smem_optin));
@@ -1183,6 +1185,10 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         size_t K, kdiag, lab32, lab8, counts, Spart, zpart, zsum, cnorm, invm, st, J, ch;
     };
     std::vector<Offs> o(count);
+    // FP16 / BF16 K: every instance's square as half tiles read by the tensor-core stream
+    const int half = opt.k_storage != POPCORN_K_FP32 ? opt.k_storage : 0;
+    bp.half = half;
+    std::vector<size_t> o_kh(count), o_v(count);
     const int hist_len = max_iter > 0 ? max_iter : 1;
     // K-stream unit lengths the autotuner may pick (Spart is sized for the shortest)
     static const int kSegCand[] = {2048, 4096, 8192, 16384};
@@ -1212,8 +1218,8 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         b.ldk = (n + 3) / 4 * 4;
         b.n = n;
         b.k = k;
-        b.seglen = min_seglen;
-        b.nseg = (n + min_seglen - 1) / min_seglen;
+        b.seglen = half ? n : min_seglen;
+        b.nseg = half ? 1 : (n + min_seglen - 1) / min_seglen;   // half K: S written once a row
         b.init_labels = x.init_labels;
         b.labels_out = x.labels_out;
         b.unit0 = bp.units;
@@ -1227,6 +1233,17 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         if (k > bp.kmax) bp.kmax = k;
         const int zb = (n + kZReduceRows - 1) / kZReduceRows;
         o[t].K = take((size_t)n * b.ldk * 4);
+        if (half) {
+            b.N = (k + 15) / 16 * 16;
+            b.htile0 = bp.htiles;
+            bp.htiles += (long long)b.T * b.T;
+            b.vblock0 = bp.vblocks;
+            bp.vblocks += b.T;
+            bp.nunits += b.T;
+            if (b.N > bp.Nmax) bp.Nmax = b.N;
+            o_kh[t] = take((size_t)b.T * b.T * 32768);
+            o_v[t] = take((size_t)b.T * b.N * 256);
+        }
         o[t].kdiag = take((size_t)n * 4);
         o[t].lab32 = take((size_t)n * 4);
         o[t].lab8 = take(((size_t)n + 15) & ~(size_t)15);
@@ -1246,6 +1263,20 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
     }
     if (bp.units <= 0 || bp.units >= (1 << 30)) return fail(POPCORN_ERR_UNSUPPORTED, "batch too large");
     plan_batched_reduce(&bp, dev->sms, dev->batched_smem);
+    // half K: the units (instance, row block), the larger instances first (their units take
+    // longer), so that the static round-robin of the stream ends near balance
+    std::vector<int2> hunits;
+    if (half) {
+        if (!plan_batched_mma(&bp, dev->sms, dev->smem_optin))
+            return fail(POPCORN_ERR_UNSUPPORTED, "the batched tensor-core stream does not fit this device");
+        std::vector<int> order(count);
+        for (int t = 0; t < count; ++t) order[t] = t;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return h[x].T > h[y].T; });
+        hunits.reserve((size_t)bp.nunits);
+        for (int t : order)
+            for (int r = 0; r < h[t].T; ++r) hunits.push_back(make_int2(t, r));
+    }
+    const size_t units_off = half ? take(sizeof(int2) * hunits.size()) : 0;
     const size_t inst_off = take(sizeof(BatchInst) * (size_t)count);
     const size_t tc_off = tc_ws ? take(tc_ws) : 0;
     const size_t err_off = take(sizeof(int));
@@ -1268,7 +1299,15 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         b.st = reinterpret_cast<LoopState*>(base + o[t].st);
         b.J_hist = reinterpret_cast<double*>(base + o[t].J);
         b.changed_hist = reinterpret_cast<int32_t*>(base + o[t].ch);
+        if (half) {
+            b.Kh = base + o_kh[t];
+            b.V = base + o_v[t];
+        }
     }
+    const int2* dunits = half ? reinterpret_cast<const int2*>(base + units_off) : nullptr;
+    if (half)
+        POPCORN_CUDA(cudaMemcpyAsync(base + units_off, hunits.data(), sizeof(int2) * hunits.size(),
+                                     cudaMemcpyHostToDevice, s));
     BatchInst* dI = reinterpret_cast<BatchInst*>(base + inst_off);
     POPCORN_CUDA(cudaMemcpyAsync(dI, h.data(), sizeof(BatchInst) * (size_t)count, cudaMemcpyHostToDevice, s));
     int* err = reinterpret_cast<int*>(base + err_off);
@@ -1287,7 +1326,7 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
     int sched[3] = {kBatchSeg, 0, 0};
     int tune_hit = 0, tune_cands = 0;
     double tune_ms = 0.0;
-    if (opt.autotune) {
+    if (opt.autotune && !half) {   // the half-K stream has no tuned schedule
         double sum_n2 = 0.0, max_n = 0.0;
         for (int t = 0; t < count; ++t) {
             sum_n2 += (double)h[t].n * h[t].n;
@@ -1359,10 +1398,16 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         sched[1] = best.p[1];
         sched[2] = best.p[2];
     }
-    set_seglen(sched[0]);
-    plan_batched_reduce(&bp, dev->sms, dev->batched_smem, sched[1], sched[2]);
-    sched[1] = bp.warps;
-    sched[2] = bp.per_sm;
+    if (!half) {
+        set_seglen(sched[0]);
+        plan_batched_reduce(&bp, dev->sms, dev->batched_smem, sched[1], sched[2]);
+        sched[1] = bp.warps;
+        sched[2] = bp.per_sm;
+    } else {
+        sched[0] = 0;            // whole 128-row blocks a unit
+        sched[1] = bp.mstages;   // ring depth of the tensor-core stream
+        sched[2] = 1;            // one block an SM
+    }
     if (bp.units <= 0 || bp.units >= (1 << 30)) return fail(POPCORN_ERR_UNSUPPORTED, "batch too large");
     POPCORN_CUDA(cudaMemcpyAsync(dI, h.data(), sizeof(BatchInst) * (size_t)count, cudaMemcpyHostToDevice, s));
 
@@ -1395,15 +1440,24 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
                  "tensor-core K build");
         }
     }
+    if (half) {
+        step(launch_batched_pack_half(dI, bp, cs), "batched half-K pack");   // rounds diag K too
+        launches += 1;
+    }
     step(launch_batched_trace(dI, bp, cs), "batched trace");
     launches += 1;
+    auto pass = [&](int eval) -> cudaError_t {
+        if (!half) return launch_batched_pass(dI, bp, eval, cs);
+        const cudaError_t e = launch_batched_mma_stream(dI, dunits, bp, err, eval, cs);
+        return e != cudaSuccess ? e : launch_batched_finish(dI, bp, eval, cs);
+    };
     for (int it = 0; it < max_iter && cap == POPCORN_OK; ++it) {
-        step(launch_batched_pass(dI, bp, 0, cs), "batched pass");
-        launches += 3;
+        step(pass(0), "batched pass");
+        launches += half ? 4 : 3;
     }
-    step(launch_batched_pass(dI, bp, 1, cs), "batched objective pass");
+    step(pass(1), "batched objective pass");
     step(launch_batched_copy_labels(dI, bp, cs), "batched label copy");
-    launches += 3;
+    launches += half ? 4 : 3;
     cudaGraph_t graph = nullptr;
     cudaError_t ec = cudaStreamEndCapture(cs, &graph);
     if (cap != POPCORN_OK) {
@@ -1441,7 +1495,7 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         objectives_out[t] = hs[t].J_eval;
         iterations_out[t] = hs[t].iter;
     }
-    if (herr) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the tensor-core K build ran out");
+    if (herr) return fail(POPCORN_ERR_TIMEOUT, "a bounded wait in the tensor-core K build or K stream ran out");
     if (info) {
         int conv = 1;
         for (int t = 0; t < count; ++t) conv &= hs[t].converged;
@@ -1460,7 +1514,7 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         info->schedule[0] = sched[0];
         info->schedule[1] = sched[1];
         info->schedule[2] = sched[2];
-        info->schedule[3] = 0;
+        info->schedule[3] = half ? bp.Nmax : 0;
     }
     return POPCORN_OK;
 }

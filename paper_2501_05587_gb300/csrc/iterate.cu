@@ -285,12 +285,17 @@ __device__ __forceinline__ void assign_body(const AssignArgs& a, int block, int 
     LoopState* st = a.st;
     if (st->done) return;
     __shared__ int hist[kMaxClusters];
+    __shared__ float cn32[kMaxClusters], im32[kMaxClusters];   // ||c||^2 and 1/|L_c| in FP32
     __shared__ int am_last;
     const int n = a.n, k = a.k;
     const int it = st->iter;
     const int32_t* m = a.counts + (size_t)(it & 1) * k;
     int32_t* mnext = a.counts + (size_t)((it + 1) & 1) * k;
-    for (int c = threadIdx.x; c < k; c += blockDim.x) hist[c] = 0;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        hist[c] = 0;
+        cn32[c] = (float)a.cnorm[c];
+        im32[c] = (float)a.invm[c];
+    }
     __syncthreads();
 
     const int i = block * blockDim.x + threadIdx.x;
@@ -302,18 +307,84 @@ __device__ __forceinline__ void assign_body(const AssignArgs& a, int block, int 
         int bi = li;
         const float* Si = a.Spart + i;               // [s][c][i]: consecutive threads, consecutive rows
         const size_t cs = (size_t)n, ss = (size_t)k * n;
-        for (int c = 0; c < k; ++c) {
-            const int mc = m[c];
-            float hi = 0.f, lo = 0.f;
-#pragma unroll 8
-            for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[s * ss + c * cs]);
-            const double E = ((double)hi + (double)lo) * a.invm[c];   // (K V^T)_ic
-            if (a.E_out) a.E_out[(int64_t)i * k + c] = (float)E;
-            if (mc == 0) continue;
-            const double D = fma(-2.0, E, kd + a.cnorm[c]);
-            if (D < best) {
-                best = D;
-                bi = c;
+        // The argmin in FP32, screened: GB300 runs FP64 at a small fraction of the FP32 rate,
+        // and a pass has n k distances.  Each FP32 distance is within
+        //   B = 16 u (|K_ii| + max_c ||c||^2 + max_c |E_ic|),  u = 2^-24,
+        // of the FP64 one (from the roundings of 1/|L_c|, ||c||^2, the sum, the product and
+        // the multiply-add: under 8.2 u (|E| + ||c||^2 + |K_ii|)).  Where the FP32 best beats
+        // every other cluster by more than 2 B, the FP64 argmin is the same cluster; otherwise
+        // (near-ties, and every row when E is requested) the row is decided in FP64 below.
+        bool decided = false;
+        if (!a.E_out) {
+            const float kd32 = a.kdiag[i];
+            float b1 = cuda::std::numeric_limits<float>::infinity(), b2 = b1, emax = 0.f, cmax = 0.f;
+            int c1 = li;
+            for (int c0 = 0; c0 < k; c0 += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = c0 + u < k ? Si[(size_t)(c0 + u) * cs] : 0.f;
+                float hi[8], lo[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    hi[u] = lo[u] = 0.f;
+                    ff_add(hi[u], lo[u], v[u]);
+                }
+                for (int s = 1; s < a.nseg; ++s) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = c0 + u < k ? Si[s * ss + (size_t)(c0 + u) * cs] : 0.f;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) ff_add(hi[u], lo[u], v[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int c = c0 + u;
+                    if (c >= k) break;
+                    if (m[c] == 0) continue;
+                    const float E = (hi[u] + lo[u]) * im32[c];
+                    const float D = fmaf(-2.f, E, kd32 + cn32[c]);
+                    emax = fmaxf(emax, fabsf(E));
+                    cmax = fmaxf(cmax, fabsf(cn32[c]));
+                    if (D < b1) {
+                        b2 = b1;
+                        b1 = D;
+                        c1 = c;
+                    } else if (D < b2) {
+                        b2 = D;
+                    }
+                }
+            }
+            const float B = 16.f * 0x1p-24f * (fabsf(kd32) + cmax + emax);
+            if (b2 - b1 > 2.f * B) {
+                bi = c1;
+                decided = true;
+            }
+        }
+        // 8 clusters at a time: their segment sums are loaded before any is used, so a thread
+        // keeps 8 loads in flight instead of one (the same additions in the same order)
+        for (int c0 = 0; c0 < k && !decided; c0 += 8) {
+            float hi[8], lo[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) hi[u] = lo[u] = 0.f;
+            for (int s = 0; s < a.nseg; ++s) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = c0 + u < k ? Si[s * ss + (size_t)(c0 + u) * cs] : 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) ff_add(hi[u], lo[u], v[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + u;
+                if (c >= k) break;
+                const int mc = m[c];
+                const double E = ((double)hi[u] + (double)lo[u]) * a.invm[c];   // (K V^T)_ic
+                if (a.E_out) a.E_out[(int64_t)i * k + c] = (float)E;
+                if (mc == 0) continue;
+                const double D = fma(-2.0, E, kd + a.cnorm[c]);
+                if (D < best) {
+                    best = D;
+                    bi = c;
+                }
             }
         }
         newl = bi;
@@ -917,6 +988,14 @@ cudaError_t launch_batched_trace(const BatchInst* dI, const BatchPlan& bp, cudaS
     return cudaGetLastError();
 }
 
+cudaError_t launch_batched_finish(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s) {
+    batched_zreduce_kernel<<<bp.zblocks, kZReduceRows, 0, s>>>(dI, bp.count, eval);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || eval) return e;
+    batched_assign_kernel<<<bp.ablocks, kAssignThreads, 0, s>>>(dI, bp.count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batched_pass(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s) {
     if (bp.per_sm == 1)
         batched_reduce_kernel<8><<<bp.grid, bp.warps * 32, bp.smem, s>>>(dI, bp.count, bp.units, bp.kmax, eval);
@@ -924,11 +1003,7 @@ cudaError_t launch_batched_pass(const BatchInst* dI, const BatchPlan& bp, int ev
         batched_reduce_kernel<4><<<bp.grid, bp.warps * 32, bp.smem, s>>>(dI, bp.count, bp.units, bp.kmax, eval);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    batched_zreduce_kernel<<<bp.zblocks, kZReduceRows, 0, s>>>(dI, bp.count, eval);
-    e = cudaGetLastError();
-    if (e != cudaSuccess || eval) return e;
-    batched_assign_kernel<<<bp.ablocks, kAssignThreads, 0, s>>>(dI, bp.count);
-    return cudaGetLastError();
+    return launch_batched_finish(dI, bp, eval, s);
 }
 
 cudaError_t launch_batched_copy_labels(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s) {

@@ -377,6 +377,13 @@ struct BatchInst {
     const int32_t* init_labels;
     int32_t* labels_out;
     int unit0, zblock0, ablock0, lblock0;
+    // FP16 / BF16 K (batched_mma.cu): every tile of the square in kPackedSw128H, tile (I, J) at
+    // Kh + (I T + J) 32 KB; the per-pass one-hot operands of the T blocks, N rows each
+    unsigned char* Kh;
+    unsigned char* V;
+    int N;                    // accumulator columns: k rounded up to 16
+    long long htile0;         // first flattened tile of the square
+    int vblock0;              // first flattened 128-block
 };
 
 struct BatchPlan {
@@ -386,6 +393,14 @@ struct BatchPlan {
     int kmax;
     int warps, grid, per_sm;  // batched K-stream launch
     size_t smem;
+    // FP16 / BF16 K: the tensor-core stream over (instance, row block) units
+    int half;                 // 0, or the k_storage of every instance's K
+    long long htiles;         // tiles of every instance's square
+    int vblocks;              // 128-blocks of every instance
+    int nunits;               // (instance, row block) units
+    int Nmax;                 // widest accumulator
+    int mstages, mgrid;
+    size_t msmem;
 };
 
 constexpr int kBatchLabelThreads = 256;
@@ -400,7 +415,20 @@ cudaError_t launch_batched_trace(const BatchInst* dI, const BatchPlan& bp, cudaS
 cudaError_t launch_batched_kbuild_simt(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s);
 // one pass over every instance that has not stopped (K stream, z, argmin)
 cudaError_t launch_batched_pass(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s);
+// the rest of a pass after its K stream: z (with per-instance finalization) and the argmin
+cudaError_t launch_batched_finish(const BatchInst* dI, const BatchPlan& bp, int eval, cudaStream_t s);
 cudaError_t launch_batched_copy_labels(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s);
+// FP16 / BF16 K in batched mode (batched_mma.cu).  Plan: ring depth, grid and shared memory of
+// the stream for accumulators up to Nmax columns (false if it does not fit).  Pack: every
+// instance's FP32 square (K, ldk) rounded into its half tiles Kh, diag K rounded with it.
+// Pass: the one-hot operands, then the stream over the units (instance, row block), ordered
+// by the caller (larger instances first), writing each row's k sums to Spart (one segment);
+// *err is set when a bounded wait runs out.
+bool plan_batched_mma(BatchPlan* bp, int num_sms, int smem_optin);
+cudaError_t configure_batched_mma(int smem_optin);
+cudaError_t launch_batched_pack_half(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s);
+cudaError_t launch_batched_mma_stream(const BatchInst* dI, const int2* units, const BatchPlan& bp, int* err,
+                                      int eval, cudaStream_t s);
 // warps / grid / shared memory of the batched K stream for clusters up to kmax;
 // warps = 0 / per_sm = 0 pick the largest that fits / the occupancy limit
 void plan_batched_reduce(BatchPlan* bp, int num_sms, int smem_budget, int warps = 0, int per_sm = 0);

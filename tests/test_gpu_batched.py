@@ -116,3 +116,82 @@ def test_batched_full_size_sampled(pc):
         assert rel_err(r29["objectives"][t], st["J"]) <= FP32_OBJ_REL, t
         assert label_mismatches(lab, st)[0] == 0, t
         assert rel_err(r["objectives"][t], oracle.objective(Ko, lab, w.k)) <= FP32_OBJ_REL, t
+
+
+# ---------------------------------------------------------------- half-precision K
+# k_storage "fp16" / "bf16": every instance's square rounded once (after the FP32 or tensor-
+# core build) into 32 KB tiles read by the tensor-core stream (MMAs of each tile against
+# one-hot label operands, FP32 sums in TMEM).  The method then runs on the rounded K: one
+# pass must be the oracle's step on the oracle's K rounded the same way (through FP32),
+# labels up to near-ties within the storage type's relative rounding.
+
+
+def _rounded_k(P, kern, storage):
+    K32 = oracle.kernel_matrix(P, kern).astype(np.float32)
+    if storage == "fp16":
+        return K32.astype(np.float16).astype(np.float64)
+    u = K32.view(np.uint32).astype(np.uint64)
+    return (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _gauss_only(insts, wls):
+    keep = [t for t, w in enumerate(wls) if w.kernel["kind"] == "gaussian"]   # |K| <= 1: FP16-safe
+    return [insts[t] for t in keep], [wls[t] for t in keep]
+
+
+@pytest.mark.parametrize("storage,precision", [("bf16", "fp32"), ("fp16", "fp32"), ("bf16", "bf16")])
+def test_batched_half_k_one_pass_matches_oracle_on_rounded_k(pc, storage, precision):
+    wls, insts = _batch(count=12, seed=13)
+    if storage == "fp16":
+        insts, wls = _gauss_only(insts, wls)
+    assert len(wls) >= 4
+    r = pc.popcorn_fit_batched(insts, max_iter=1, check_convergence=False, k_storage=storage, precision=precision)
+    rel = 2.0 ** -10 if storage == "fp16" else 2.0 ** -7
+    for t, w in enumerate(wls):
+        P = w.P
+        if precision == "bf16":   # the BF16 build: K of the rounded points
+            P = torch.from_numpy(w.P).to(torch.bfloat16).to(torch.float64).numpy()
+        Kr = _rounded_k(P, w.kernel, storage)
+        st = oracle.step(Kr, w.init_labels, w.k)
+        lab = r["labels"][t].cpu().numpy()
+        assert r["iterations"][t] == 1
+        assert label_mismatches(lab, st, rel=rel)[0] == 0, t
+        assert rel_err(r["objectives"][t], oracle.objective(Kr, lab, w.k)) <= 1e-5, t
+
+
+def test_batched_half_k_whole_fits_and_info(pc):
+    """Whole fits with convergence checking: every instance stops at a fixed point of the
+    oracle's step on its rounded K (up to near-ties), instances stop at different passes,
+    and the reported objective is J of the returned labels on the rounded K; the schedule
+    reports the ring depth and the widest accumulator (k rounded up to 16)."""
+    wls, insts = _batch(count=8, seed=15)
+    r = pc.popcorn_fit_batched(insts, max_iter=60, k_storage="bf16")
+    assert r["info"]["schedule"][3] == max((w.k + 15) // 16 * 16 for w in wls)
+    assert r["info"]["schedule"][1] >= 2
+    assert len(set(r["iterations"])) > 1
+    for t, w in enumerate(wls):
+        Kr = _rounded_k(w.P, w.kernel, "bf16")
+        lab = r["labels"][t].cpu().numpy()
+        assert rel_err(r["objectives"][t], oracle.objective(Kr, lab, w.k)) <= 1e-5, t
+        if r["iterations"][t] < 60:
+            assert label_mismatches(lab, oracle.step(Kr, lab, w.k), rel=2.0 ** -7)[0] == 0, t
+
+
+def test_batched_half_k_full_size_sampled(pc):
+    """The 256-instance batch of the batched workload with a BF16 K: 29 and 30 passes; for
+    sampled instances the oracle's step (rounded K) from the GPU's labels after pass 29 gives
+    the GPU's labels after pass 30 (up to exempt near-ties) and J of those labels."""
+    wls = synth.batched_instances(256, seed=0)
+    insts = [{"P": torch.from_numpy(w.P).cuda(), "k": w.k, "kernel": w.kernel,
+              "init_labels": torch.from_numpy(w.init_labels).cuda()} for w in wls]
+    r29 = pc.popcorn_fit_batched(insts, max_iter=29, check_convergence=False, k_storage="bf16")
+    l29 = [x.cpu().numpy() for x in r29["labels"]]
+    r = pc.popcorn_fit_batched(insts, max_iter=30, check_convergence=False, k_storage="bf16")
+    for t in (0, 1, 77, 200, 255):
+        w = wls[t]
+        Kr = _rounded_k(w.P, w.kernel, "bf16")
+        lab = r["labels"][t].cpu().numpy()
+        st = oracle.step(Kr, l29[t], w.k)
+        assert rel_err(r29["objectives"][t], st["J"]) <= 1e-5, t
+        assert label_mismatches(lab, st, rel=2.0 ** -7)[0] == 0, t
+        assert rel_err(r["objectives"][t], oracle.objective(Kr, lab, w.k)) <= 1e-5, t
