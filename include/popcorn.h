@@ -380,7 +380,12 @@ POPCORN_API popcorn_status popcorn_kmeanspp(const float* P, int64_t n, int32_t d
  * CUDA graph and launched on `stream`; an instance that converges stops
  * doing work on the device while the others go on.  Instances of uneven n,
  * d, k and kernel share every launch: work is flattened over (instance,
- * tile / row segment / row block).
+ * tile / row segment / row block).  options.k_storage FP16 / BF16 stores every
+ * instance's square as 32 KB half tiles (written by the FP32 build, or rounded
+ * from a BF16 / BF16X3 build's FP32 square) and each pass reads them on the
+ * tensor cores: per 128-row block, MMAs of its tiles against one-hot label
+ * operands, the row sums in TMEM.  k_pass and sym_tile do not apply here (each
+ * square is read whole).
  *
  *   instances        host array of `count` descriptors.
  *   objectives_out   host, count doubles: J(labels_out) per instance.

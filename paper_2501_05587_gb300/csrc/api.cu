@@ -1232,7 +1232,10 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
         bp.lblocks += (n + kBatchLabelThreads - 1) / kBatchLabelThreads;
         if (k > bp.kmax) bp.kmax = k;
         const int zb = (n + kZReduceRows - 1) / kZReduceRows;
-        o[t].K = take((size_t)n * b.ldk * 4);
+        // the FP32 square: the K read by the FP32 passes, or the tensor-core builds' output that
+        // the pack rounds into half tiles (the FP32 build writes half tiles directly)
+        const bool fp32_square = !half || opt.precision != POPCORN_FP32;
+        o[t].K = fp32_square ? take((size_t)n * b.ldk * 4) : 0;
         if (half) {
             b.N = (k + 15) / 16 * 16;
             b.htile0 = bp.htiles;
@@ -1286,7 +1289,7 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
     POPCORN_TRY(ws.alloc(&base, bytes, "batch workspace"));
     for (int t = 0; t < count; ++t) {
         BatchInst& b = h[t];
-        b.K = reinterpret_cast<float*>(base + o[t].K);
+        b.K = (!half || opt.precision != POPCORN_FP32) ? reinterpret_cast<float*>(base + o[t].K) : nullptr;
         b.kdiag = reinterpret_cast<float*>(base + o[t].kdiag);
         b.lab32 = reinterpret_cast<int32_t*>(base + o[t].lab32);
         b.lab8 = base + o[t].lab8;
@@ -1440,8 +1443,9 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
                  "tensor-core K build");
         }
     }
-    if (half) {
-        step(launch_batched_pack_half(dI, bp, cs), "batched half-K pack");   // rounds diag K too
+    if (half && opt.precision != POPCORN_FP32) {
+        // the tensor-core builds write FP32 squares: rounded into half tiles (diag K too)
+        step(launch_batched_pack_half(dI, bp, cs), "batched half-K pack");
         launches += 1;
     }
     step(launch_batched_trace(dI, bp, cs), "batched trace");

@@ -295,7 +295,57 @@ __device__ __forceinline__ void kbuild_tile(const float* __restrict__ P, int n, 
         }
     }
 
-    if constexpr (PACKED != 0) {
+    if constexpr (PACKED == kPackedSw128H) {
+        // FP16 / BF16 square as 32 KB tiles (batched mode): tile (I, J) at K + (I T + J) 32 KB,
+        // two boxes of 128 rows x 64 columns in the 128-byte swizzle, element (r, c) at byte
+        // 16384 (c >> 6) + 128 r + 16 (((c >> 3) & 7) ^ (r & 7)) + 2 (c & 7); entries past n
+        // are zeros.  A thread's 4 consecutive columns (4-aligned) are 8 bytes of one 16-byte
+        // chunk; so are its 4 consecutive rows in the transposed tile (J, I).
+        static_assert(sizeof(TK) == 2, "half tiles hold FP16 / BF16 K");
+        unsigned char* base = reinterpret_cast<unsigned char*>(K);
+        auto off = [](int r, int c) { return 16384 * (c >> 6) + 128 * r + 16 * (((c >> 3) & 7) ^ (r & 7)) + 2 * (c & 7); };
+        auto put = [](unsigned char* p, float a, float b, float c, float d) {
+            uint2 u;
+            if constexpr (std::is_same<TK, __half>::value) {
+                __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+                u.x = *reinterpret_cast<uint32_t*>(&lo);
+                u.y = *reinterpret_cast<uint32_t*>(&hi);
+            } else {
+                __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+                u.x = *reinterpret_cast<uint32_t*>(&lo);
+                u.y = *reinterpret_cast<uint32_t*>(&hi);
+            }
+            *reinterpret_cast<uint2*>(p) = u;
+        };
+        unsigned char* Bd = base + ((size_t)bi * T + bj) * 32768;
+#pragma unroll
+        for (int x = 0; x < RPT; ++x) {
+            const int rl = ty * 4 + (x & 3) + RS * (x >> 2);
+            const bool rv = row0 + rl < n;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cl = 64 * h + tx * 4, c = col0 + cl;
+                const float* v = &acc[x][4 * h];
+                put(Bd + off(rl, cl), rv && c < n ? v[0] : 0.f, rv && c + 1 < n ? v[1] : 0.f,
+                    rv && c + 2 < n ? v[2] : 0.f, rv && c + 3 < n ? v[3] : 0.f);
+            }
+        }
+        if (bi != bj) {   // rows of block bi < bj are all below n
+            unsigned char* Bt = base + ((size_t)bj * T + bi) * 32768;
+#pragma unroll
+            for (int y = 0; y < 8; ++y) {
+                const int cl = tx * 4 + (y & 3) + 64 * (y >> 2);
+                const bool cv = col0 + cl < n;
+#pragma unroll
+                for (int g = 0; g < RPT / 4; ++g) {
+                    const int rl = RS * g + ty * 4;
+                    put(Bt + off(cl, rl), cv ? acc[4 * g][y] : 0.f, cv ? acc[4 * g + 1][y] : 0.f,
+                        cv ? acc[4 * g + 2][y] : 0.f, cv ? acc[4 * g + 3][y] : 0.f);
+                }
+            }
+        }
+        return;
+    } else if constexpr (PACKED != 0) {
         // block-packed upper triangle: tile t is 64 KB at K + t * 128 * 128, as four boxes of
         // 128 rows x 32 columns, the layout the symmetric pass loads with one bulk copy.
         // kPackedSw16: 16-byte chunk j of row r stored at chunk j ^ (r mod 8) (the 128-byte
@@ -498,6 +548,9 @@ cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernPar
 
 // All instances of a batch: flattened tile b belongs to the instance whose
 // tile0 is the largest one <= b.
+// TK float: each instance's FP32 square, row-major (K, ldk); TK __half / __nv_bfloat16: its
+// square as half tiles (Kh, kPackedSw128H), for the tensor-core batched stream.
+template <typename TK>
 __global__ void __launch_bounds__(256) batched_kbuild_kernel(const BatchInst* I, int count) {
     const long long b = blockIdx.x;
     int lo = 0, hi = count - 1;
@@ -509,14 +562,18 @@ __global__ void __launch_bounds__(256) batched_kbuild_kernel(const BatchInst* I,
     const BatchInst& x = I[lo];
     const long long t = b - x.tile0;
     __shared__ __align__(16) TileSmem sm;   // one copy for the three kernel functions
+    constexpr int PK = sizeof(TK) == 2 ? kPackedSw128H : 0;
+    TK* K = sizeof(TK) == 2 ? reinterpret_cast<TK*>(x.Kh) : reinterpret_cast<TK*>(x.K);
     switch (x.kp.kind) {
         case POPCORN_LINEAR:
-            kbuild_tile<POPCORN_LINEAR>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t, sm);
+            kbuild_tile<POPCORN_LINEAR, TK, false, PK>(x.P, x.n, x.d, x.ldp, x.kp, K, x.ldk, x.kdiag, x.T, t, sm);
             break;
         case POPCORN_POLYNOMIAL:
-            kbuild_tile<POPCORN_POLYNOMIAL>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t, sm);
+            kbuild_tile<POPCORN_POLYNOMIAL, TK, false, PK>(x.P, x.n, x.d, x.ldp, x.kp, K, x.ldk, x.kdiag, x.T, t, sm);
             break;
-        default: kbuild_tile<POPCORN_GAUSSIAN>(x.P, x.n, x.d, x.ldp, x.kp, x.K, x.ldk, x.kdiag, x.T, t, sm); break;
+        default:
+            kbuild_tile<POPCORN_GAUSSIAN, TK, false, PK>(x.P, x.n, x.d, x.ldp, x.kp, K, x.ldk, x.kdiag, x.T, t, sm);
+            break;
     }
 }
 
@@ -524,7 +581,12 @@ __global__ void __launch_bounds__(256) batched_kbuild_kernel(const BatchInst* I,
 
 cudaError_t launch_batched_kbuild_simt(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s) {
     if (bp.tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    batched_kbuild_kernel<<<(unsigned)bp.tiles, 256, 0, s>>>(dI, bp.count);
+    if (bp.half == POPCORN_K_FP16)
+        batched_kbuild_kernel<__half><<<(unsigned)bp.tiles, 256, 0, s>>>(dI, bp.count);
+    else if (bp.half == POPCORN_K_BF16)
+        batched_kbuild_kernel<__nv_bfloat16><<<(unsigned)bp.tiles, 256, 0, s>>>(dI, bp.count);
+    else
+        batched_kbuild_kernel<float><<<(unsigned)bp.tiles, 256, 0, s>>>(dI, bp.count);
     return cudaGetLastError();
 }
 
