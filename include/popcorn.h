@@ -205,6 +205,9 @@ POPCORN_API const char* popcorn_last_error_message(void);
 
 /* Version of this library as MAJOR*10000 + MINOR*100 + PATCH. */
 POPCORN_API int32_t popcorn_version(void);
+/* Allocations the library has made in this process: blocks of its device workspace pool and
+ * pinned host staging buffers (a diagnostic; popcorn_assign_step_noalloc never adds to it). */
+POPCORN_API int64_t popcorn_allocation_count(void);
 
 /*
  * popcorn_kernel_matrix -- K = kappa(P P^T) and diag(K).

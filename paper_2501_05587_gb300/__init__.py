@@ -61,6 +61,7 @@ EXPORTED_SYMBOLS = (
     "popcorn_kmeanspp",
     "popcorn_autotune_entries",
     "popcorn_autotune_clear",
+    "popcorn_allocation_count",
 )
 
 KIND = {"linear": 0, "polynomial": 1, "gaussian": 2}
@@ -110,6 +111,8 @@ _lib.popcorn_status_string.argtypes = [ctypes.c_int]
 _lib.popcorn_last_error_message.restype = ctypes.c_char_p
 _lib.popcorn_last_error_message.argtypes = []
 _lib.popcorn_version.restype = _i32
+_lib.popcorn_allocation_count.restype = ctypes.c_int64
+_lib.popcorn_allocation_count.argtypes = []
 _lib.popcorn_version.argtypes = []
 _lib.popcorn_kernel_matrix.restype = ctypes.c_int
 _lib.popcorn_kernel_matrix.argtypes = [_vp, _i64, _i32, _i64, _Kernel, _i32, _vp, _i64, _vp, _vp]

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -102,6 +103,10 @@ popcorn_status device_info(DeviceInfo** out) {
     return POPCORN_OK;
 }
 
+// Allocations the library has made (workspace blocks and pinned host staging), for
+// popcorn_allocation_count.
+std::atomic<int64_t> g_alloc_count{0};
+
 // Stream-ordered workspace: every block is returned to the pool (on the
 // stream) when the object goes out of scope, on success and on error paths.
 class Workspace {
@@ -127,6 +132,7 @@ class Workspace {
                         "workspace for %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
         }
         blocks_.push_back(p);
+        g_alloc_count.fetch_add(1, std::memory_order_relaxed);
         *out = static_cast<T*>(p);
         return POPCORN_OK;
     }
@@ -159,6 +165,7 @@ popcorn_status pinned(size_t bytes, void** out) {
         g_pinned.p = nullptr;
         g_pinned.bytes = 0;
         POPCORN_CUDA(cudaMallocHost(&g_pinned.p, bytes));
+        g_alloc_count.fetch_add(1, std::memory_order_relaxed);
         g_pinned.bytes = bytes;
     }
     *out = g_pinned.p;
@@ -553,6 +560,8 @@ const char* popcorn_status_string(popcorn_status status) {
 const char* popcorn_last_error_message(void) { return g_err.c_str(); }
 
 int32_t popcorn_version(void) { return 100; }
+
+int64_t popcorn_allocation_count(void) { return g_alloc_count.load(std::memory_order_relaxed); }
 
 popcorn_status popcorn_kernel_matrix_ex(const float* P, int64_t n, int32_t d, int64_t ldp, popcorn_kernel kern,
                                         int32_t precision, int32_t schedule, float* K, int64_t ldk, float* kdiag,

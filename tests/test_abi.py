@@ -51,6 +51,9 @@ def test_status_strings_and_version(pc):
     assert lib.popcorn_status_string(4) == b"POPCORN_ERR_TIMEOUT"
     assert lib.popcorn_status_string(99) == b"POPCORN_ERR_UNKNOWN"
     assert pc.popcorn_version() >= 100
+    # the allocation counter answers without a device (no call here allocates)
+    a = pc._lib.popcorn_allocation_count()
+    assert a >= 0 and pc._lib.popcorn_allocation_count() == a
 
 
 def test_invalid_arguments_rejected_before_any_cuda_call(pc):

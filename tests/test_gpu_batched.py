@@ -195,3 +195,28 @@ def test_batched_half_k_full_size_sampled(pc):
         assert rel_err(r29["objectives"][t], st["J"]) <= 1e-5, t
         assert label_mismatches(lab, st, rel=2.0 ** -7)[0] == 0, t
         assert rel_err(r["objectives"][t], oracle.objective(Kr, lab, w.k)) <= 1e-5, t
+
+
+def test_batched_half_k_tiny_and_ragged_instances(pc):
+    """Instances smaller than one 128-block, exactly one block, one point past it, and k from
+    1 to n - 1 (N = 16 to 64 accumulator columns) in one half-K batch: one pass each against
+    the oracle's step on the rounded K."""
+    rng = np.random.default_rng(41)
+    shapes = [(2, 1), (5, 4), (40, 39), (127, 20), (128, 64), (129, 3), (300, 1), (700, 50)]
+    wls, insts = [], []
+    for t, (n, k) in enumerate(shapes):
+        P = rng.normal(size=(n, 6)).astype(np.float32) * 2.0
+        lab = synth.init_labels(n, k, seed=60 + t)
+        kern = {"kind": "gaussian", "gamma": 1.0, "coef0": 0.0, "degree": 1, "sigma": 3.0}
+        wls.append((P, lab, k, kern))
+        insts.append({"P": torch.from_numpy(P).cuda(), "k": k, "kernel": kern,
+                      "init_labels": torch.from_numpy(lab).cuda()})
+    for storage in ("fp16", "bf16"):
+        r = pc.popcorn_fit_batched(insts, max_iter=1, check_convergence=False, k_storage=storage)
+        rel = 2.0 ** -10 if storage == "fp16" else 2.0 ** -7
+        for t, (P, lab, k, kern) in enumerate(wls):
+            Kr = _rounded_k(P, kern, storage)
+            st = oracle.step(Kr, lab, k)
+            got = r["labels"][t].cpu().numpy()
+            assert label_mismatches(got, st, rel=rel)[0] == 0, (storage, t)
+            assert rel_err(r["objectives"][t], oracle.objective(Kr, got, k)) <= 1e-5, (storage, t)

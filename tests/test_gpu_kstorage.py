@@ -212,6 +212,7 @@ def test_half_k_symmetric_sampled_rows_at_images_size(pc, storage, precision):
 HALF_EDGE_CASES = [
     # (n, d, k, sigma, seed): Gaussian (|K| <= 1, FP16-safe)
     (97, 3, 3, 1.0, 1),          # one block, ragged
+    (300, 3, 1, 1.0, 20),        # k = 1
     (1030, 9, 8, 2.0, 3),        # ragged
     (1280, 4, 16, 1.0, 6),       # n a multiple of 128, N = 16 at its bound
     (2000, 5, 24, 1.5, 12),      # N = 32

@@ -39,6 +39,7 @@ def _noalloc_raw(pc, K, kd, labels, k):
     ch = ctypes.c_int32(-1)
     torch.cuda.synchronize()
     free_before = torch.cuda.mem_get_info()[0]
+    allocs_before = pc._lib.popcorn_allocation_count()
     st = pc._lib.popcorn_assign_step_noalloc(
         ctypes.c_void_p(K.data_ptr()), K.stride(0), ctypes.c_void_p(kd.data_ptr()), n, k,
         ctypes.c_void_p(labels.data_ptr()), ctypes.c_void_p(new.data_ptr()), ctypes.c_void_p(counts.data_ptr()),
@@ -48,7 +49,8 @@ def _noalloc_raw(pc, K, kd, labels, k):
     free_after = torch.cuda.mem_get_info()[0]
     assert st == 0, pc._lib.popcorn_last_error_message()
     return {"labels": new, "counts": counts, "cnorm": cnorm, "E": E, "J": J.value, "changed": ch.value,
-            "free_delta": free_before - free_after}
+            "free_delta": free_before - free_after,
+            "library_allocs": pc._lib.popcorn_allocation_count() - allocs_before}
 
 
 def _case(n, d, k, seed, kern):
@@ -84,8 +86,21 @@ def test_noalloc_matches_allocating_step_on_consecutive_calls(pc):
         assert label_mismatches(got["labels"].cpu().numpy(), o)[0] == 0
         assert rel_err(got["J"], o["J"]) <= FP32_OBJ_REL
         results.append(got)
-    # after the first call loaded the library's module, the calls allocate nothing
+    # after the first call loaded the library's module, the calls allocate nothing; and no call,
+    # the first included, takes a workspace block or a pinned host buffer from the library
     assert all(r["free_delta"] == 0 for r in results[1:])
+    assert all(r["library_allocs"] == 0 for r in results)
+
+
+def test_allocation_counter_sees_the_allocating_entry_point(pc):
+    """The counter the test above relies on does move for the allocating step."""
+    n, d, k, seed, kern = CASES[0]
+    P, lab, kern = _case(n, d, k, seed, kern)
+    K, kd = pc.popcorn_kernel_matrix(torch.from_numpy(P).cuda(), kern)
+    before = pc._lib.popcorn_allocation_count()
+    pc.popcorn_assign_step(K, kd, torch.from_numpy(lab).cuda(), k, want_E=True)
+    torch.cuda.synchronize()
+    assert pc._lib.popcorn_allocation_count() > before
 
 
 def test_noalloc_repeat_call_is_identical(pc):
