@@ -551,7 +551,7 @@ cudaError_t launch_simt_typed(const float* P, int n, int d, int64_t ldp, KernPar
 // TK float: each instance's FP32 square, row-major (K, ldk); TK __half / __nv_bfloat16: its
 // square as half tiles (Kh, kPackedSw128H), for the tensor-core batched stream.
 template <typename TK>
-__global__ void __launch_bounds__(256) batched_kbuild_kernel(const BatchInst* I, int count) {
+__global__ void __launch_bounds__(256, 2) batched_kbuild_kernel(const BatchInst* I, int count) {
     const long long b = blockIdx.x;
     int lo = 0, hi = count - 1;
     while (lo < hi) {
