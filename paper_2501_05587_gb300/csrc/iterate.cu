@@ -437,9 +437,9 @@ __global__ void __launch_bounds__(kAssignThreads) assign_kernel(AssignArgs a) {
 }
 
 
-// sum_{i in L_c} S_ic for the recompute path, from Spart[s][c][i]: a block takes
-// kZReduceRows consecutive rows; thread c sums its cluster's rows in row
-// order (deterministic), then the last block finalizes the pass.
+// sum_{i in L_c} S_ic for the recompute path and batched mode, from Spart[s][c][i]: a
+// block takes kZReduceRows consecutive rows and sums each cluster's rows in a fixed order
+// (deterministic), then the last block finalizes the pass.
 struct ZArgs {
     int n, k, nseg;
     const float* Spart;
@@ -460,10 +460,19 @@ __device__ __forceinline__ void zreduce_body(const ZArgs& a, int block, int nblo
         if (a.eval_only && block == 0 && threadIdx.x == 0) st->J_eval = st->J_last;
         return;
     }
-    __shared__ int lab_s[kZReduceRows];
-    __shared__ double val_s[kZReduceRows];
+    // The block's rows, stably sorted by label in shared memory, so that each cluster's FP64
+    // sum touches only its own rows (GB300 runs FP64 at a small fraction of the FP32 rate; a
+    // walk of all rows for every cluster issued k x 1024 predicated FP64 adds).  Stable rank
+    // of a row: its rank among the earlier rows of its warp with its label (warp match), plus
+    // the rows with that label in earlier warps and in earlier clusters.
+    constexpr int NW = kZReduceRows / 32;
+    __shared__ double val_s[kZReduceRows];                 // values in sorted order
+    __shared__ unsigned short cnt_s[NW][kMaxClusters];     // per warp and cluster: count, then offset
+    __shared__ int cstart[kMaxClusters + 1];
     __shared__ int am_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = block * kZReduceRows + threadIdx.x;
+    for (int e = threadIdx.x; e < NW * a.k; e += kZReduceRows) cnt_s[e / a.k][e % a.k] = 0;
     int l = -1;
     double v = 0.0;
     if (i < a.n) {
@@ -473,20 +482,42 @@ __device__ __forceinline__ void zreduce_body(const ZArgs& a, int block, int nblo
         for (int s = 0; s < a.nseg; ++s) ff_add(hi, lo, Si[(size_t)s * a.k * a.n]);
         v = (double)hi + (double)lo;
     }
-    lab_s[threadIdx.x] = l;
-    val_s[threadIdx.x] = v;
     __syncthreads();
-    // warp w: clusters w, w + 32, ...; lanes stride the rows, a butterfly adds them (fixed order)
-    {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int c = warp; c < a.k; c += nw) {
-            double t = 0.0;
-            for (int r = lane; r < kZReduceRows; r += 32)
-                if (lab_s[r] == c) t += val_s[r];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) a.zpart[(size_t)block * a.k + c] = t;
+    const unsigned peers = __match_any_sync(0xffffffffu, l);
+    const int wrank = __popc(peers & ((1u << lane) - 1u));
+    if (l >= 0 && wrank == 0) cnt_s[warp][l] = (unsigned short)__popc(peers);
+    __syncthreads();
+    // per cluster: its total, then (after the scan over clusters) each warp's starting offset
+    for (int c = threadIdx.x; c < a.k; c += kZReduceRows) {
+        int t = 0;
+        for (int w = 0; w < NW; ++w) t += cnt_s[w][c];
+        cstart[c + 1] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cstart[0] = 0;
+        for (int c = 0; c < a.k; ++c) cstart[c + 1] += cstart[c];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < a.k; c += kZReduceRows) {
+        int o = cstart[c];
+        for (int w = 0; w < NW; ++w) {
+            const int m = cnt_s[w][c];
+            cnt_s[w][c] = (unsigned short)o;
+            o += m;
         }
+    }
+    __syncthreads();
+    if (l >= 0) val_s[cnt_s[warp][l] + wrank] = v;
+    __syncthreads();
+    // warp w: clusters w, w + 32, ...; lanes stride the cluster's sorted rows, a butterfly adds
+    // the lanes' sums (a fixed order)
+    for (int c = warp; c < a.k; c += NW) {
+        double t = 0.0;
+        for (int r = cstart[c] + lane; r < cstart[c + 1]; r += 32) t += val_s[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) a.zpart[(size_t)block * a.k + c] = t;
     }
     __threadfence();
     __syncthreads();
