@@ -818,7 +818,17 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     POPCORN_TRY(ws.alloc(&b.Spart, (size_t)nslots * ni * k, "segment sums"));
     POPCORN_TRY(ws.alloc(&b.zpart, (size_t)(use_sym ? sym.fold_blocks : plan.grid) * k, "block partials"));
     b.sym_meta = nullptr;
+    b.sym_order = nullptr;
     if (use_sym && sym.meta_bytes) POPCORN_TRY(ws.alloc(&b.sym_meta, sym.meta_bytes, "block label metadata"));
+    std::vector<int> sym_order;
+    if (use_sym && sym.units > 1) {
+        sym_unit_order(sym, &sym_order);
+        int* d_order;
+        POPCORN_TRY(ws.alloc(&d_order, sym_order.size(), "super-tile order"));
+        POPCORN_CUDA(cudaMemcpyAsync(d_order, sym_order.data(), sym_order.size() * sizeof(int),
+                                     cudaMemcpyHostToDevice, s));
+        b.sym_order = d_order;
+    }
     // one pass's reduction: the K stream (for the symmetric pass: stream, then fold with z)
     // kernels of one pass's reduction: the full-square stream; or the symmetric stream and its
     // fold (the sorted form first sorts every block's labels)

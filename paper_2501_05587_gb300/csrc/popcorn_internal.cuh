@@ -108,6 +108,10 @@ struct SymPlan {
 SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req = 0, int stages_req = 0,
                         int ebytes = 4);
 cudaError_t configure_reduce_sym(int smem_optin);
+// The super-tiles of a sorted-form or tensor-core plan by decreasing number of blocks (stable):
+// the diagonal and edge super-tiles hold fewer blocks, so in this order every round of the
+// stream's static round-robin takes units of one size and the small ones come last.
+void sym_unit_order(const SymPlan& p, std::vector<int>* order);
 // The tensor-core form (reduce_sym_mma.cu): plan fields for an FP16 / BF16 K, the per-pass
 // one-hot operand and the stream launch (the fold is shared with the other forms).
 bool plan_sym_mma(SymPlan* p, int k, int num_sms, int smem_optin, int a_req, int stages_req);
@@ -329,6 +333,7 @@ struct PassBuffers {
     int32_t* changed_hist;
     float* E_out;         // optional n x k
     uint8_t* sym_meta;    // sorted form of the symmetric pass: the label-sorted lists of every block
+    const int* sym_order; // symmetric pass: super-tiles in processing order (larger first), or null
 };
 
 // Operand rows for the recompute path, their norms and scales, and diag K.

@@ -39,7 +39,10 @@
 // slot 0, the per-block FP64 partials of sum_{i in L_c} S_ic (z, Eq. 14), and in its
 // last block the pass finalization (||c||^2, J).  The assignment then reads slot 0
 // alone.
+#include <algorithm>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "popcorn_internal.cuh"
 #include "stream_common.cuh"
@@ -459,6 +462,7 @@ struct SortedArgs {
     // wait_ns and the launch reports a timed-out wait.
     int stall_block;
     unsigned long long wait_ns;
+    const int* order;          // super-tiles in processing order (larger first), or null
 };
 
 // The lane's R rows (STRIDE 4096: rows 32 e apart) or columns (STRIDE 16384) of one
@@ -574,7 +578,7 @@ __global__ void __launch_bounds__(sorted_threads(sorted_max_a(KMAX, R, P), R, P)
             uint32_t ph = 0;
             bool ok = true;
             for (long long u = blockIdx.x; u < a.units && ok; u += G) {
-                const Unit w = unit_of(u, A, a.Ts);
+                const Unit w = unit_of(a.order ? a.order[u] : u, A, a.Ts);
                 for (int m = 0; m < A && ok; ++m)
                     for (int i = 0; i < A; ++i) {
                         int I, J;
@@ -631,7 +635,7 @@ __global__ void __launch_bounds__(sorted_threads(sorted_max_a(KMAX, R, P), R, P)
     uint32_t ph = 0;
     bool alive = true;
     for (long long u = blockIdx.x; u < a.units && alive; u += G) {
-        const Unit w = unit_of(u, A, a.Ts);
+        const Unit w = unit_of(a.order ? a.order[u] : u, A, a.Ts);
         float acc[P][KMAX][R];
 #pragma unroll
         for (int q = 0; q < P; ++q)
@@ -881,6 +885,24 @@ SymPlan plan_reduce_sym(int n, int k, int num_sms, int smem_optin, int a_req, in
     return p;
 }
 
+void sym_unit_order(const SymPlan& p, std::vector<int>* order) {
+    // blocks (I, J), J >= I, of super-tile (Is, Js) inside the T x T block triangle
+    std::vector<std::pair<int, int>> size_id;
+    size_id.reserve((size_t)p.units);
+    long long u = 0;
+    for (int Is = 0; Is < p.Ts; ++Is)
+        for (int Js = Is; Js < p.Ts; ++Js, ++u) {
+            int blocks = 0;
+            for (int I = Is * p.a; I < (Is + 1) * p.a && I < p.T; ++I)
+                for (int J = Js * p.a; J < (Js + 1) * p.a && J < p.T; ++J) blocks += J >= I;
+            size_id.push_back({-blocks, (int)u});
+        }
+    std::stable_sort(size_id.begin(), size_id.end(),
+                     [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first < y.first; });
+    order->resize(size_id.size());
+    for (size_t q = 0; q < size_id.size(); ++q) (*order)[q] = size_id[q].second;
+}
+
 cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, int eval_only, cudaStream_t s,
                               cudaEvent_t between, int stall_ms) {
     cudaError_t e;
@@ -914,6 +936,7 @@ cudaError_t launch_reduce_sym(const PassBuffers& b, const SymPlan& p, int* err, 
         r.eval_only = eval_only;
         r.stall_block = stall_ms > 0 ? 1 : 0;
         r.wait_ns = stall_ms > 0 ? (unsigned long long)stall_ms * 1000000ull : tc::kWaitLimitNs;
+        r.order = b.sym_order;
         const dim3 block((unsigned)sorted_threads(p.a, p.rpl, p.pw));
         void (*f)(SortedArgs) = p.rpl == 4 ? (p.kb == 12   ? reduce_sym_sorted_kernel<12, 4, 1>
                                               : p.kb == 16 ? reduce_sym_sorted_kernel<16, 4, 1>

@@ -151,6 +151,7 @@ struct MmaArgs {
     // wait_ns and the launch reports a timed-out wait.
     int stall_block;
     unsigned long long wait_ns;
+    const int* order;          // super-tiles in processing order (larger first), or null
 };
 
 template <bool BF16, int N>
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) reduce_sym_mma_kernel(MmaArgs 
             uint32_t ph = 0;
             bool ok = true;
             for (long long u = blockIdx.x; u < a.units && ok; u += G) {
-                const MmaUnit w = mma_unit(u, A, a.Ts);
+                const MmaUnit w = mma_unit(a.order ? a.order[u] : u, A, a.Ts);
                 for (int m = 0; m < A && ok; ++m)
                     for (int i = 0; i < A; ++i) {
                         int I, J;
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) reduce_sym_mma_kernel(MmaArgs 
                     break;
                 }
                 tc::tc_fence_after();
-                const MmaUnit w = mma_unit(u, A, a.Ts);
+                const MmaUnit w = mma_unit(a.order ? a.order[u] : u, A, a.Ts);
                 uint32_t touched = 0;   // accumulators written in this super-tile
                 for (int m = 0; m < A && ok; ++m)
                     for (int i = 0; i < A; ++i) {
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) reduce_sym_mma_kernel(MmaArgs 
             // all epilogue threads agree before touching TMEM
             if (!tc::named_bar_all(1, 128, ok && !*abort_flag)) break;
             tc::tc_fence_after();
-            const MmaUnit w = mma_unit(u, A, a.Ts);
+            const MmaUnit w = mma_unit(a.order ? a.order[u] : u, A, a.Ts);
             for (int z = 0; z < 2 * A; ++z) {
                 const bool rowsum = z < A;
                 const int X = rowsum ? w.I0 + z : w.J0 + (z - A);   // the block whose rows take these sums
@@ -466,6 +467,7 @@ cudaError_t launch_sym_mma_stream(const PassBuffers& b, const SymPlan& p, int* e
     a.eval_only = eval_only;
     a.stall_block = stall_ms > 0 ? 1 : 0;
     a.wait_ns = stall_ms > 0 ? (unsigned long long)stall_ms * 1000000ull : tc::kWaitLimitNs;
+    a.order = b.sym_order;
     void (*f)(MmaArgs) = bf16 ? (N == 16 ? reduce_sym_mma_kernel<true, 16> : reduce_sym_mma_kernel<true, 32>)
                               : (N == 16 ? reduce_sym_mma_kernel<false, 16> : reduce_sym_mma_kernel<false, 32>);
     return launch_pdl(f, dim3((unsigned)p.grid), dim3(kMmaThreads), p.smem, s, a);
