@@ -1469,9 +1469,19 @@ popcorn_status popcorn_fit_batched(int32_t count, const popcorn_instance* inst, 
     }
     step(launch_batched_trace(dI, bp, cs), "batched trace");
     launches += 1;
+    // Error-path test hook: with POPCORN_TEST_SYM_STALL_MS=<ms> in the environment, the first
+    // tensor-core batched stream of the graph leaves one tile's copies out and bounds its
+    // waits by <ms>, so the fit reports POPCORN_ERR_TIMEOUT.  Unset in every ordinary run.
+    int stall_ms = 0;
+    if (half) {
+        const char* env = getenv("POPCORN_TEST_SYM_STALL_MS");
+        if (env && *env) stall_ms = atoi(env);
+        if (stall_ms < 0 || stall_ms > 10000) stall_ms = 0;
+    }
     auto pass = [&](int eval) -> cudaError_t {
         if (!half) return launch_batched_pass(dI, bp, eval, cs);
-        const cudaError_t e = launch_batched_mma_stream(dI, dunits, bp, err, eval, cs);
+        const cudaError_t e = launch_batched_mma_stream(dI, dunits, bp, err, eval, cs, stall_ms);
+        stall_ms = 0;
         return e != cudaSuccess ? e : launch_batched_finish(dI, bp, eval, cs);
     };
     for (int it = 0; it < max_iter && cap == POPCORN_OK; ++it) {

@@ -154,6 +154,9 @@ struct BatchedMmaArgs {
     int* err;
     int eval;
     unsigned long long wait_ns;
+    // Test hook for the error path (0 in every ordinary launch): CTA 0 never issues the
+    // copies of its tile number stall_block - 1, so the waits for it run out after wait_ns.
+    int stall_block;
 };
 
 template <bool BF16>
@@ -203,6 +206,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) batched_mma_kernel(BatchedMmaA
         if (lane == 0) {
             // ---------------- producer: the tiles of the unit's block row with their V_J
             const uint64_t stream_once = tc::l2_evict_first();   // each tile is read once a pass
+            const long long skip = blockIdx.x == 0 ? (long long)a.stall_block - 1 : -1;
             long long t = 0;
             int s = 0;
             uint32_t ph = 0;
@@ -217,11 +221,13 @@ __global__ void __launch_bounds__(kMmaThreads, 1) batched_mma_kernel(BatchedMmaA
                         ok = false;
                         break;
                     }
-                    tc::mbar_arrive_expect_tx(full_bar(s), (uint32_t)kTileBytes + vbytes);
-                    const uint32_t dst = sbase + (uint32_t)s * (uint32_t)a.stage_bytes;
-                    tc::bulk_load_1d_hint(dst, b.Kh + ((size_t)w.y * b.T + J) * kTileBytes, (uint32_t)kTileBytes,
-                                          full_bar(s), stream_once);
-                    tc::bulk_load_1d(dst + kTileBytes, b.V + (size_t)J * vbytes, vbytes, full_bar(s));
+                    if (t != skip) {   // the test hook: this tile never arrives
+                        tc::mbar_arrive_expect_tx(full_bar(s), (uint32_t)kTileBytes + vbytes);
+                        const uint32_t dst = sbase + (uint32_t)s * (uint32_t)a.stage_bytes;
+                        tc::bulk_load_1d_hint(dst, b.Kh + ((size_t)w.y * b.T + J) * kTileBytes,
+                                              (uint32_t)kTileBytes, full_bar(s), stream_once);
+                        tc::bulk_load_1d(dst + kTileBytes, b.V + (size_t)J * vbytes, vbytes, full_bar(s));
+                    }
                     ++t;
                     if (++s == S) {
                         s = 0;
@@ -232,6 +238,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) batched_mma_kernel(BatchedMmaA
             if (*abort_flag) {
                 // leaving early: let this thread's copies land before the CTA's memory goes
                 for (long long t2 = t > S ? t - S : 0; t2 < t; ++t2) {
+                    if (t2 == skip) continue;   // nothing was issued for it
                     const uint32_t bar = full_bar((int)(t2 % S)), par = (uint32_t)(t2 / S) & 1u;
                     const unsigned long long t0 = tc::globaltimer();
                     while (!tc::mbar_try_wait(bar, par) && tc::globaltimer() - t0 < a.wait_ns) {
@@ -379,7 +386,7 @@ cudaError_t launch_batched_pack_half(const BatchInst* dI, const BatchPlan& bp, c
 }
 
 cudaError_t launch_batched_mma_stream(const BatchInst* dI, const int2* units, const BatchPlan& bp, int* err, int eval,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, int stall_ms) {
     const bool bf16 = bp.half == POPCORN_K_BF16;
     if (!bf16 && bp.half != POPCORN_K_FP16) return cudaErrorInvalidValue;
     if (bf16)
@@ -400,7 +407,8 @@ cudaError_t launch_batched_mma_stream(const BatchInst* dI, const int2* units, co
     a.tmem_cols = cols;
     a.err = err;
     a.eval = eval;
-    a.wait_ns = tc::kWaitLimitNs;
+    a.stall_block = stall_ms > 0 ? 1 : 0;
+    a.wait_ns = stall_ms > 0 ? (unsigned long long)stall_ms * 1000000ull : tc::kWaitLimitNs;
     if (bf16)
         batched_mma_kernel<true><<<bp.mgrid, kMmaThreads, bp.msmem, s>>>(a);
     else

@@ -428,12 +428,13 @@ cudaError_t launch_batched_copy_labels(const BatchInst* dI, const BatchPlan& bp,
 // instance's FP32 square (K, ldk) rounded into its half tiles Kh, diag K rounded with it.
 // Pass: the one-hot operands, then the stream over the units (instance, row block), ordered
 // by the caller (larger instances first), writing each row's k sums to Spart (one segment);
-// *err is set when a bounded wait runs out.
+// *err is set when a bounded wait runs out.  stall_ms > 0 (error-path tests only): CTA 0
+// leaves its first tile's copies out and every wait gives up after stall_ms.
 bool plan_batched_mma(BatchPlan* bp, int num_sms, int smem_optin);
 cudaError_t configure_batched_mma(int smem_optin);
 cudaError_t launch_batched_pack_half(const BatchInst* dI, const BatchPlan& bp, cudaStream_t s);
 cudaError_t launch_batched_mma_stream(const BatchInst* dI, const int2* units, const BatchPlan& bp, int* err,
-                                      int eval, cudaStream_t s);
+                                      int eval, cudaStream_t s, int stall_ms = 0);
 // warps / grid / shared memory of the batched K stream for clusters up to kmax;
 // warps = 0 / per_sm = 0 pick the largest that fits / the occupancy limit
 void plan_batched_reduce(BatchPlan* bp, int num_sms, int smem_budget, int warps = 0, int per_sm = 0);

@@ -5,8 +5,9 @@ not see its phase within the limit raises the CTA's abort flag and an error word
 role of the CTA leaves its loop, waits (bounded again) for its own copies in flight and
 returns, and the host reports POPCORN_ERR_TIMEOUT.  These tests make such a wait run out
 on purpose through the library's test hook: POPCORN_TEST_SYM_STALL_MS=<ms> makes the first
-symmetric-stream launch of a fit leave one block's copies out (nothing ever arrives on
-that block's barrier) with every wait of the launch bounded by <ms>.  Nothing faults or
+symmetric-stream launch of a fit (or the first tensor-core K stream of a batched fit) leave
+one block's copies out (nothing ever arrives on that block's barrier) with every wait of the
+launch bounded by <ms>.  Nothing faults or
 hangs: the kernel returns, the call fails with the timeout status, and the next call on
 the same context gives the reference result.  The other host-side failure paths (an
 allocation the device cannot satisfy, a label out of range) are in test_gpu_parity.py.
@@ -72,3 +73,26 @@ def test_stall_hook_is_inert_when_unset(pc):
     b = pc.popcorn_fit(P, wl.k, wl.kernel, lab, max_iter=4, check_convergence=False, k_pass="full")
     assert torch.equal(a["labels"], b["labels"]) and a["objective"] == b["objective"]
     assert np.isfinite(a["objective"])
+
+
+def test_batched_tensor_core_stream_wait_timeout(pc, monkeypatch):
+    """The batched tensor-core K stream (BF16 K): CTA 0 leaves one tile's copies out, the MMA
+    issuer's bounded wait runs out, every role leaves, and the batch reports
+    POPCORN_ERR_TIMEOUT; the context stays usable and the next batch is the ordinary one."""
+    wls = synth.batched_instances(6, seed=5, n_lo=300, n_hi=1500)
+    insts = [{"P": torch.from_numpy(w.P).cuda(), "k": w.k, "kernel": w.kernel,
+              "init_labels": torch.from_numpy(w.init_labels).cuda()} for w in wls]
+    kw = dict(max_iter=4, check_convergence=False, k_storage="bf16")
+    ref = pc.popcorn_fit_batched(insts, **kw)
+    monkeypatch.setenv("POPCORN_TEST_SYM_STALL_MS", "200")
+    t0 = time.perf_counter()
+    with pytest.raises(pc.PopcornError) as ei:
+        pc.popcorn_fit_batched(insts, **kw)
+    assert ei.value.status == 4, str(ei.value)          # POPCORN_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60
+    monkeypatch.delenv("POPCORN_TEST_SYM_STALL_MS")
+    torch.cuda.synchronize()
+    again = pc.popcorn_fit_batched(insts, **kw)
+    for t in range(len(wls)):
+        assert torch.equal(again["labels"][t], ref["labels"][t])
+        assert again["objectives"][t] == ref["objectives"][t]
