@@ -274,7 +274,7 @@ __device__ void fit_body(const FusedArgs& a, unsigned char* smem) {
     LoopState* st = a.st;
     int* err = &st->wait_err;
     const int n = a.n, k = a.k, G = gridDim.x;
-    unsigned* bar = a.xchg;   // arrival count, generation
+    unsigned* bar = a.xchg;   // the grid barrier's arrival count
     int* hslot = reinterpret_cast<int*>(a.xchg + 32);
     int* cslot = hslot + (size_t)G * k;
     const int lo = (int)((int64_t)blockIdx.x * n / G), hi = (int)((int64_t)(blockIdx.x + 1) * n / G);

@@ -11,14 +11,17 @@ namespace popcorn {
 namespace gsync {
 
 // Grid-wide barrier of the cooperative launch (all CTAs resident).  After the CTA's own
-// barrier, thread 0 arrives with an acquire-release add on the arrival count (its release
-// covers the CTA's writes, ordered before it by the CTA barrier); the last to arrive resets
-// the count and publishes the next generation with a release store, the others wait for it
-// with acquire loads, bounded.  False when the wait ran out or another CTA gave up, in which
-// case the whole CTA leaves.  bar: two words in one 128-byte line, zero before the launch.
-// (Measured on the blobs workload, this single counter beats a two-level counter tree and
-// per-CTA release flags polled with acquire loads: the cost is round trips to L2, not
-// contention.)
+// barrier, thread 0 arrives with an acquire-release add on a monotonic arrival count: the
+// add's release covers the CTA's writes (ordered before it by the CTA barrier), and each add
+// acquires the previous one, so the adds form one chain.  The barrier's target is the next
+// multiple of the grid size above this CTA's arrival; the last to arrive passes at once, the
+// others wait with acquire loads, bounded, until the count reaches the target (a CTA already
+// arriving at the next barrier only raises it further).  No reset and no generation word:
+// one round trip to L2 fewer than a count reset by the last arrival plus a generation flag.
+// False when the wait ran out or another CTA gave up, in which case the whole CTA leaves.
+// bar: a word zero before the launch (at most 2^31 / gridDim.x barriers a launch).
+// (Measured on the blobs workload, one counter beats a two-level counter tree and per-CTA
+// release flags polled with acquire loads: the cost is round trips to L2, not contention.)
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
     unsigned old;
     asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
@@ -41,15 +44,13 @@ __device__ inline bool grid_barrier(unsigned* bar, int* err) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile int* verr = err;
-        const unsigned g = ld_acquire(bar + 1);
+        const unsigned arrival = atom_add_acq_rel(bar, 1u);
+        const unsigned target = (arrival / gridDim.x + 1u) * gridDim.x;
         int ok = 1;
-        if (atom_add_acq_rel(bar, 1u) == gridDim.x - 1) {
-            st_relaxed(bar, 0u);
-            st_release(bar + 1, g + 1);
-        } else {
+        if (arrival + 1u != target) {
             const unsigned long long t0 = tc::globaltimer();
             unsigned spins = 0;
-            while (ld_acquire(bar + 1) == g) {
+            while ((int)(ld_acquire(bar) - target) < 0) {
                 if ((++spins & 63u) == 0u) {
                     if (*verr || tc::globaltimer() - t0 > tc::kWaitLimitNs) {
                         if (!*verr) atomicExch(err, 1);
