@@ -343,3 +343,36 @@ def test_onehot_operand_layout():
                 for e in range(16):
                     i = 16 * kk + e
                     assert _kmajor_sw128(base, c, 16 * (kk & 3) + e) == where[(c, i)]
+
+
+def test_batched_build_half_tile_and_transpose_stores():
+    """The batched FP32 build's half-tile epilogue: a thread's 4 consecutive columns of row r
+    (4-aligned) are one 8-byte store at off(r, c) in tile (I, J), and its 4 consecutive rows
+    of column c are one 8-byte store at off(c, r) in tile (J, I).  Every element of both tiles
+    is written exactly once, each 8-byte store stays inside one 16-byte chunk, and the
+    element the K-major MMA operand reads for (row, column) of tile (J, I) is K[column][row]
+    of tile (I, J)."""
+    def off(r, c):
+        return 16384 * (c >> 6) + 128 * r + 16 * (((c >> 3) & 7) ^ (r & 7)) + 2 * (c & 7)
+
+    direct, trans = {}, {}
+    for r in range(B):
+        for c0 in range(0, B, 4):
+            base = off(r, c0)
+            assert base % 8 == 0 and (base % 16) + 8 <= 16
+            for e in range(4):
+                assert off(r, c0 + e) == base + 2 * e
+                direct[base + 2 * e] = (r, c0 + e)
+    for c in range(B):
+        for r0 in range(0, B, 4):
+            base = off(c, r0)           # transposed tile: row c, columns r0 .. r0 + 3
+            for e in range(4):
+                assert off(c, r0 + e) == base + 2 * e
+                trans[base + 2 * e] = (r0 + e, c)   # holds K[r0 + e][c] of the direct tile
+    assert len(direct) == len(trans) == B * B
+    for kk in range(8):                  # the MMA's K-major reads of the transposed tile
+        start = 16384 * (kk >> 2)
+        for m in range(B):
+            for e in range(16):
+                a = _kmajor_sw128(start, m, 16 * (kk & 3) + e)
+                assert trans[a] == (16 * kk + e, m)   # operand (row m, column 16 kk + e) = K[16 kk + e][m]
