@@ -199,10 +199,12 @@ def test_batched_half_k_full_size_sampled(pc):
 
 def test_batched_half_k_tiny_and_ragged_instances(pc):
     """Instances smaller than one 128-block, exactly one block, one point past it, and k from
-    1 to n - 1 (N = 16 to 64 accumulator columns) in one half-K batch: one pass each against
-    the oracle's step on the rounded K."""
+    1 to n - 1 and up to 200 (N = 16 to 208 accumulator columns) in one half-K batch: one pass
+    each against the oracle's step on the rounded K."""
     rng = np.random.default_rng(41)
-    shapes = [(2, 1), (5, 4), (40, 39), (127, 20), (128, 64), (129, 3), (300, 1), (700, 50)]
+    # k up to 200: N = 208 accumulator columns, two ring stages of 32 KB + 52 KB, 512 TMEM columns
+    shapes = [(2, 1), (5, 4), (40, 39), (127, 20), (128, 64), (129, 3), (300, 1), (700, 50), (900, 130),
+              (1500, 200)]
     wls, insts = [], []
     for t, (n, k) in enumerate(shapes):
         P = rng.normal(size=(n, 6)).astype(np.float32) * 2.0
