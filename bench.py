@@ -204,8 +204,12 @@ def pass_roofline(wl, prof, pk, k_storage="fp32"):
     ms = red / max(passes, 1)
     alg = float(eb) * n * n + n
     ach = alg / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-    return {"kernel": "reduce_kernel", "bound": "hbm", "k_storage": k_storage, "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
-            "frac": ach / pk["hbm"], "traffic": recorded_traffic("reduce_kernel", "iterate.cu", wl.name),
+    # a half K read as the full square runs on the tensor cores (schedule[3]: its TMEM
+    # columns); the launch time here also holds the one-hot operands and the z reduction
+    kern = "batched_mma_kernel" if eb == 2 and info["schedule"][3] > 0 else "reduce_kernel"
+    return {"kernel": kern, "bound": "hbm", "k_storage": k_storage, "achieved": ach, "peak": pk["hbm"], "unit": "GB/s",
+            "frac": ach / pk["hbm"],
+            "traffic": recorded_traffic("reduce_kernel", "iterate.cu", wl.name) if kern == "reduce_kernel" else None,
             "peak_source": pk["source"] + " HBM copy", "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms}
 
 

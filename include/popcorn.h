@@ -104,10 +104,13 @@ typedef struct {
                                    captured on a private stream and launched on `stream`
                                    (plain launches when `stream` is itself being captured)   */
     int32_t k_storage;          /* popcorn_k_storage of the stored K; 0 = FP32.  FP16 / BF16
-                                   from any build: the FP32 build rounds its K (full square,
-                                   or the packed triangle through one pack launch); the BF16
-                                   / BF16X3 builds write only the packed triangle of the
-                                   symmetric pass (k <= 32)                                  */
+                                   from any build, rounded once.  A pass reads it on the tensor
+                                   cores: the symmetric pass's tensor-core form (k <= 32), or,
+                                   read as the full square (k > 32 or k_pass = 2), 32 KB half
+                                   tiles of the square with each 128-row block's row sums as
+                                   MMAs against one-hot label operands (any k; for the FP32
+                                   build from n = 8192, below which a CUDA-core pass reads a
+                                   row-major half K)                                         */
     int32_t autotune;           /* 1: pick the schedule by timing candidates on this workload
                                    (first call per workload signature; later calls reuse the
                                    cached choice, see popcorn_autotune_entries); 0: fixed
@@ -177,6 +180,9 @@ typedef struct {
                                                    the sorted form, 16 or 32 TMEM
                                                    columns (the MMA's N) in the
                                                    tensor-core form};
+                                  full square of a half K on the tensor cores: {0, ring
+                                                   depth, 0, TMEM columns (k rounded up
+                                                   to 16)};
                                   zeros otherwise                                           */
     double fold_ms;            /* symmetric pass: the slot fold kernel, summed over passes
                                   (part of reduce_ms), when timing = 1                      */
@@ -321,7 +327,7 @@ POPCORN_API popcorn_status popcorn_assign_step(const float* K, int64_t ldk, cons
  * POPCORN_BF16X3 (the recompute path runs in POPCORN_BF16 or POPCORN_FP8), and
  * for a recompute request with d or k beyond its limits (d <= 256 for BF16,
  * d <= 512 for FP8), and for an FP16 / BF16 K from a BF16 / BF16X3 build read
- * as the full square (k > 32, or k_pass = 2); POPCORN_ERR_NOMEM when K (or the workspace) does not fit
+ * as the full square inside a caller's stream capture; POPCORN_ERR_NOMEM when K (or the workspace) does not fit
  * in device memory; POPCORN_ERR_TIMEOUT when a bounded wait inside a
  * tensor-core or symmetric-pass kernel ran out (the context stays usable).
  */

@@ -230,8 +230,8 @@ popcorn_status build_kernel_matrix(const float* P, int n, int d, int64_t ldp, co
     }
     if (k_storage != POPCORN_K_FP32 && packed != kPackedSw128H)
         return fail(POPCORN_ERR_UNSUPPORTED,
-                    "an FP16/BF16 K from a BF16/BF16X3 build is written only as the packed triangle of the "
-                    "symmetric pass (k <= 32, k_pass 0 or 1)");
+                    "an FP16/BF16 K from a BF16/BF16X3 build is written as half tiles (not inside a caller's "
+                    "stream capture when read as the full square)");
     if (precision != POPCORN_BF16 && precision != POPCORN_BF16X3)
         return fail(POPCORN_ERR_UNSUPPORTED, "precision %d is not available for a stored K", precision);
     unsigned char* w;
@@ -766,13 +766,40 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     if (opt.k_pass == 1 || (opt.k_pass == 0 && sym_auto))
         sym = plan_reduce_sym(ni, k, dev->sms, dev->smem_optin, opt.sym_tile, 0, (int)kelem);
     const bool use_sym = sym.ok;
+    // A half K read as the full square (k > kSymMaxK, or k_pass = 2) goes through the tensor
+    // cores, as batched mode's one-instance form: every tile of the square in the half tile
+    // layout, each 128-row block's tiles MMA'd against the one-hot label operands with the
+    // row sums in TMEM, one segment, then the z reduction.  Taken when the K build runs on
+    // the tensor cores (they write no row-major half K) or K outgrows L2; below that the
+    // CUDA-core full-square pass reads the row-major half K.
+    // (It uploads a descriptor and its units from the host, so not inside a caller's stream
+    // capture, where a copy would read host memory at replay.)
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    POPCORN_CUDA(cudaStreamIsCapturing(s, &cap_status));
+    const bool capturing = cap_status != cudaStreamCaptureStatusNone;
+    const bool mma_full = !use_sym && ks != POPCORN_K_FP32 && !capturing &&
+                          (opt.precision != POPCORN_FP32 || ni >= kSymAutoMinN);
+    const int Tf = (ni + 127) / 128;
     // With the symmetric pass, K is stored block-packed: the upper triangle of 128 x 128
     // tiles only (half the memory; each value written once), by the FP32 build and by the
     // tensor-core builds alike.
     sym.packed = use_sym;
-    const size_t k_bytes = sym.packed ? (size_t)sym.items * 128 * 128 * kelem : (size_t)ni * (size_t)ldk * kelem;
-    const int nslots = use_sym ? sym.nslots : plan.nseg;
-    if (use_sym) plan.nseg = 1;             // the assignment reads the folded slot only
+    const size_t k_bytes = sym.packed ? (size_t)sym.items * 128 * 128 * kelem
+                           : mma_full ? (size_t)Tf * Tf * 32768
+                                      : (size_t)ni * (size_t)ldk * kelem;
+    const int nslots = use_sym ? sym.nslots : mma_full ? 1 : plan.nseg;
+    if (use_sym || mma_full) plan.nseg = 1;   // the assignment reads one (folded) segment
+    BatchPlan bpf{};
+    if (mma_full) {
+        bpf.count = 1;
+        bpf.half = ks;
+        bpf.htiles = (long long)Tf * Tf;
+        bpf.vblocks = Tf;
+        bpf.nunits = Tf;
+        bpf.Nmax = (k + 15) / 16 * 16;
+        if (!plan_batched_mma(&bpf, dev->sms, dev->smem_optin))
+            return fail(POPCORN_ERR_UNSUPPORTED, "the tensor-core full-square stream does not fit this device");
+    }
     const bool timing = opt.timing != 0;          // phase events (K build, passes)
     const bool kernel_events = opt.timing == 1;   // and events around every kernel of every pass
     int launches = 0;
@@ -816,12 +843,15 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     POPCORN_TRY(ws.alloc(&b.lab8, nlab, "label bytes"));
     POPCORN_TRY(ws.alloc(&b.counts, 2 * (size_t)k, "counts"));
     POPCORN_TRY(ws.alloc(&b.Spart, (size_t)nslots * ni * k, "segment sums"));
-    POPCORN_TRY(ws.alloc(&b.zpart, (size_t)(use_sym ? sym.fold_blocks : plan.grid) * k, "block partials"));
+    const int zblocks_f = (ni + kZReduceRows - 1) / kZReduceRows;
+    POPCORN_TRY(ws.alloc(&b.zpart,
+                         (size_t)(use_sym ? sym.fold_blocks : mma_full ? std::max(plan.grid, zblocks_f) : plan.grid) * k,
+                         "block partials"));
     b.sym_meta = nullptr;
     b.sym_order = nullptr;
     if (use_sym && sym.meta_bytes) POPCORN_TRY(ws.alloc(&b.sym_meta, sym.meta_bytes, "block label metadata"));
     std::vector<int> sym_order;
-    if (use_sym && sym.units > 1) {
+    if (use_sym && sym.units > 1 && !capturing) {   // (the natural order inside a caller's capture)
         sym_unit_order(sym, &sym_order);
         int* d_order;
         POPCORN_TRY(ws.alloc(&d_order, sym_order.size(), "super-tile order"));
@@ -832,20 +862,30 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // one pass's reduction: the K stream (for the symmetric pass: stream, then fold with z)
     // kernels of one pass's reduction: the full-square stream; or the symmetric stream and its
     // fold (the sorted form first sorts every block's labels)
-    const int red_launches = use_sym ? (sym.sorted || sym.mma ? 3 : 2) : 1;
+    const int red_launches = use_sym ? (sym.sorted || sym.mma ? 3 : 2) : mma_full ? 3 : 1;
     // Error-path test hook: with POPCORN_TEST_SYM_STALL_MS=<ms> in the environment, the
     // first symmetric stream launch of this fit (either form) leaves one block's copies out
     // and bounds its waits by <ms>, so the fit reports POPCORN_ERR_TIMEOUT (nothing faults
     // or hangs; the context stays usable).  Unset in every ordinary run.
     int stall_ms = 0;
-    if (use_sym) {
+    if (use_sym || mma_full) {
         const char* env = getenv("POPCORN_TEST_SYM_STALL_MS");
         if (env && *env) stall_ms = atoi(env);
         if (stall_ms < 0 || stall_ms > 10000) stall_ms = 0;
     }
+    // the tensor-core full square: a one-instance batch descriptor and its units (0, row block)
+    BatchInst* dIf = nullptr;
+    int2* unitsf = nullptr;
+    unsigned char* Vf = nullptr;
     auto reduce_pass = [&](int eval, cudaEvent_t mid, cudaStream_t st) -> cudaError_t {
-        if (!use_sym) return launch_reduce(b, plan, eval, st);
         const int stall = stall_ms;
+        if (mma_full) {
+            stall_ms = 0;
+            cudaError_t e = launch_batched_mma_stream(dIf, unitsf, bpf, &b.st->wait_err, eval, st, stall);
+            if (e == cudaSuccess && mid) e = cudaEventRecord(mid, st);
+            return e != cudaSuccess ? e : launch_zreduce(b, 1, eval, st);
+        }
+        if (!use_sym) return launch_reduce(b, plan, eval, st);
         stall_ms = 0;
         return launch_reduce_sym(b, sym, &b.st->wait_err, eval, st, mid, stall);
     };
@@ -881,6 +921,41 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         POPCORN_CUDA(launch_pack_half(kf, K, ks, ni, kdiag, s));
         ++launches;
         ws.release(kf);
+    } else if (mma_full) {
+        // the FP32 square (either build) into a temporary, rounded into the half tiles of K by
+        // the batched pack kernel (diag K with it); the temporary goes back
+        const int64_t ld32 = (n + 3) / 4 * 4;
+        float* kf;
+        POPCORN_TRY(ws.alloc(&kf, (size_t)ni * ld32, "FP32 kernel matrix"));
+        POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, kf, ld32, POPCORN_K_FP32, kdiag, &ws,
+                                        &b.st->wait_err, dev->sms, s, &launches));
+        POPCORN_TRY(ws.alloc(&Vf, (size_t)Tf * bpf.Nmax * 256, "one-hot operands"));
+        BatchInst hf;
+        memset(&hf, 0, sizeof hf);
+        hf.T = Tf;
+        hf.K = kf;
+        hf.ldk = ld32;
+        hf.kdiag = kdiag;
+        hf.n = ni;
+        hf.k = k;
+        hf.nseg = 1;
+        hf.seglen = ni;
+        hf.lab8 = b.lab8;
+        hf.lab32 = b.lab32;
+        hf.Spart = b.Spart;
+        hf.st = b.st;
+        hf.Kh = K;
+        hf.V = Vf;
+        hf.N = bpf.Nmax;
+        std::vector<int2> hu((size_t)Tf);
+        for (int r = 0; r < Tf; ++r) hu[(size_t)r] = make_int2(0, r);
+        POPCORN_TRY(ws.alloc(&dIf, 1, "batch descriptor"));
+        POPCORN_TRY(ws.alloc(&unitsf, (size_t)Tf, "row-block units"));
+        POPCORN_CUDA(cudaMemcpyAsync(dIf, &hf, sizeof hf, cudaMemcpyHostToDevice, s));
+        POPCORN_CUDA(cudaMemcpyAsync(unitsf, hu.data(), sizeof(int2) * hu.size(), cudaMemcpyHostToDevice, s));
+        POPCORN_CUDA(launch_batched_pack_half(dIf, bpf, s));
+        ++launches;
+        ws.release(kf);
     } else {
         POPCORN_TRY(build_kernel_matrix(Pd, ni, d, ldpd, kp, opt.precision, K, ldk, ks, kdiag, &ws,
                                         &b.st->wait_err, dev->sms, s, &launches, sym.packed ? sym.layout : 0));
@@ -898,8 +973,6 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // stream and launched on s as one unit, so the passes run back to back without a
     // host launch between kernels (this matters when K sits in L2 and a pass takes
     // microseconds).  A caller that is itself capturing s gets the plain launches.
-    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
-    POPCORN_CUDA(cudaStreamIsCapturing(s, &cap_status));
     // An FP32 K that sits in L2 (the automatic choice only): the whole fit -- every pass and
     // the final objective -- in one cooperative launch, with grid barriers between the
     // phases of a pass instead of three launches a pass.
@@ -975,7 +1048,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
                 POPCORN_TRY(g_events.get(&e0));
                 POPCORN_TRY(g_events.get(&e1));
                 POPCORN_TRY(g_events.get(&e2));
-                if (use_sym) POPCORN_TRY(g_events.get(&em));
+                if (use_sym || mma_full) POPCORN_TRY(g_events.get(&em));
                 POPCORN_CUDA(cudaEventRecord(e0, s));
             }
             POPCORN_CUDA(reduce_pass(0, em, s));
@@ -987,7 +1060,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
                 ev_r.push_back(e1);
                 ev_a.push_back(e1);
                 ev_a.push_back(e2);
-                if (use_sym) {
+                if (use_sym || mma_full) {
                     ev_f.push_back(em);
                     ev_f.push_back(e1);
                 }
@@ -1064,6 +1137,9 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
             info->schedule[2] = sym.nslots;
             info->schedule[3] = sym.kb;
             info->sym_form = sym.mma ? 3 : sym.sorted ? 2 : 1;
+        } else if (mma_full) {
+            info->schedule[1] = bpf.mstages;
+            info->schedule[3] = bpf.Nmax;
         }
         // passes that did work (launches after convergence return at once)
         const bool eval_ran = !(hs.iter > 0 && hs.last_changed == 0);

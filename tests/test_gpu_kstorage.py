@@ -258,10 +258,10 @@ def test_half_k_symmetric_is_deterministic(pc):
 
 
 def test_half_k_from_tensor_core_build_auto_choice_and_limits(pc):
-    """A half K from a BF16 / BF16X3 build exists only as the packed triangle: the automatic
-    read takes the tensor-core symmetric form at any n (here n = 2,500, below the FP32
-    threshold), and a request that needs the full square (k > 32, or k_pass = "full") is
-    refused with POPCORN_ERR_UNSUPPORTED; the context stays usable."""
+    """A half K from a BF16 / BF16X3 build: the automatic read takes the tensor-core symmetric
+    form at any n (here n = 2,500, below the FP32 threshold); a read of the full square
+    (k > 32, or k_pass = "full") runs on the tensor cores too, as batched mode's one-instance
+    stream (k_pass_used 2, schedule[3] = k rounded up to 16), and repeats bit for bit."""
     wl = synth.workload("images", scale=2500 / 70000)
     n = wl.P.shape[0]
     r = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), max_iter=3, check_convergence=False,
@@ -269,10 +269,34 @@ def test_half_k_from_tensor_core_build_auto_choice_and_limits(pc):
     assert r["info"]["k_pass_used"] == 1 and r["info"]["sym_form"] == 3
     for k, kp in ((40, "auto"), (wl.k, "full")):
         lab = synth.init_labels(n, k, seed=3)
-        with pytest.raises(pc.PopcornError) as ei:
-            pc.popcorn_fit(_dev(wl.P), k, wl.kernel, _dev(lab), max_iter=2, k_storage="bf16", precision="bf16x3",
-                           k_pass=kp)
-        assert ei.value.status == 5          # POPCORN_ERR_UNSUPPORTED
-    again = pc.popcorn_fit(_dev(wl.P), wl.k, wl.kernel, _dev(wl.init_labels), max_iter=3, check_convergence=False,
-                           k_storage="fp16", precision="bf16x3", history=True)
-    assert again["info"]["J_history"] == r["info"]["J_history"]
+        a = pc.popcorn_fit(_dev(wl.P), k, wl.kernel, _dev(lab), max_iter=2, check_convergence=False,
+                           k_storage="bf16", precision="bf16x3", k_pass=kp, history=True)
+        assert a["info"]["k_pass_used"] == 2 and a["info"]["schedule"][3] == (k + 15) // 16 * 16
+        b = pc.popcorn_fit(_dev(wl.P), k, wl.kernel, _dev(lab), max_iter=2, check_convergence=False,
+                           k_storage="bf16", precision="bf16x3", k_pass=kp, history=True)
+        assert a["info"]["J_history"] == b["info"]["J_history"]
+        assert torch.equal(a["labels"], b["labels"])
+
+
+@pytest.mark.parametrize("storage,precision,n,k", [("bf16", "fp32", 9001, 40), ("fp16", "bf16x3", 3000, 100),
+                                                   ("bf16", "bf16", 2500, 64), ("fp16", "fp32", 8300, 33)])
+def test_half_k_full_square_on_tensor_cores(pc, storage, precision, n, k):
+    """A half K read as the full square on the tensor cores (k > 32): the FP32 square of the
+    build rounded into half tiles, each 128-row block's tiles MMA'd against one-hot label
+    operands, one segment, the z reduction and the argmin.  One pass against the oracle's
+    step on the oracle's K rounded to the storage type (for the BF16 build, the K of the
+    BF16-rounded points)."""
+    P = synth.gaussian_blobs(n, 6, 20, seed=k, box=3.0)
+    lab = synth.init_labels(n, k, seed=k + 1)
+    kern = {"kind": "gaussian", "gamma": 1.0, "coef0": 0.0, "degree": 1, "sigma": 2.0}
+    r = pc.popcorn_fit(_dev(P), k, kern, _dev(lab), max_iter=1, check_convergence=False, k_storage=storage,
+                       precision=precision, history=True)
+    assert r["info"]["k_pass_used"] == 2 and r["info"]["schedule"][3] == (k + 15) // 16 * 16
+    Pu = P
+    if precision == "bf16":
+        Pu = torch.from_numpy(P).to(torch.bfloat16).to(torch.float64).numpy()
+    st = oracle.step(_oracle_rounded(Pu, kern, storage), lab, k)
+    bar = 1e-5 if precision == "fp32" else 1e-4
+    assert rel_err(r["info"]["J_history"][0], st["J"]) <= bar
+    rel = 2.0 ** -10 if storage == "fp16" else 2.0 ** -7
+    assert label_mismatches(r["labels"].cpu().numpy(), st, rel=rel)[0] == 0
