@@ -867,8 +867,9 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
     // first symmetric stream launch of this fit (either form) leaves one block's copies out
     // and bounds its waits by <ms>, so the fit reports POPCORN_ERR_TIMEOUT (nothing faults
     // or hangs; the context stays usable).  Unset in every ordinary run.
+    // The same hook makes CTA 0 of the one-launch fit leave before its first grid barrier.
     int stall_ms = 0;
-    if (use_sym || mma_full) {
+    {
         const char* env = getenv("POPCORN_TEST_SYM_STALL_MS");
         if (env && *env) stall_ms = atoi(env);
         if (stall_ms < 0 || stall_ms > 10000) stall_ms = 0;
@@ -983,7 +984,7 @@ popcorn_status popcorn_fit(const float* P, int64_t n, int32_t d, int64_t ldp, in
         unsigned* fbar;
         POPCORN_TRY(ws.alloc(&fz, (size_t)dev->sms * k, "fused-fit partials"));
         POPCORN_TRY(ws.alloc(&fbar, fused_xchg_words(dev->sms, k), "exchange slots"));
-        const cudaError_t fe = launch_fused_fit(b, fz, fbar, dev->sms, dev->smem_optin, s);
+        const cudaError_t fe = launch_fused_fit(b, fz, fbar, dev->sms, dev->smem_optin, s, stall_ms);
         if (fe == cudaErrorCooperativeLaunchTooLarge) {
             // not every SM can hold a CTA now (a shared device): the launched passes instead
             cudaGetLastError();

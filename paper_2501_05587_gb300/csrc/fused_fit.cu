@@ -60,6 +60,10 @@ struct FusedArgs {
     float* E_out;              // optional n x k
     int rows_max;              // ceil(n / gridDim.x)
     int cache_k;               // 1: the CTA's rows of K are copied to shared memory once a fit
+    // Test hook for the error path (0 in every ordinary launch): CTA 0 leaves before its first
+    // grid barrier, so the others' bounded waits there run out after wait_ns.
+    int stall;
+    unsigned long long wait_ns;
 };
 
 // Dynamic shared memory, in order: per-warp bins [kFusedWarps][k][32] floats, the row
@@ -298,7 +302,7 @@ __device__ void fit_body(const FusedArgs& a, unsigned char* smem) {
         row_sums<CACHED>(a, lo, hi, lab_s, bins, S, Kc);
         __syncthreads();
         z_partials(a, lo, hi, lab_s, S);
-        if (!gsync::grid_barrier(bar, err)) return false;
+        if (!gsync::grid_barrier(bar, err, a.wait_ns)) return false;
         *J = finalize(a, m_s, trace, cn_s, iv_s);
         return true;
     };
@@ -308,6 +312,7 @@ __device__ void fit_body(const FusedArgs& a, unsigned char* smem) {
     int it = 0, last_changed = -1;
     double J_last = 0.0, J_prev = 0.0;
     bool done = max_iter <= 0;
+    if (a.stall && blockIdx.x == 0) return;   // the test hook: this CTA never arrives
     while (!done) {
         double J;
         if (!reduce(&J)) return;
@@ -316,7 +321,7 @@ __device__ void fit_body(const FusedArgs& a, unsigned char* smem) {
             st->J_last = J;
         }
         assign_rows(a, lo, hi, S, cn_s, iv_s, m_s, hist, lab_s, kd_s, hslot, cslot);
-        if (!gsync::grid_barrier(bar, err)) return;
+        if (!gsync::grid_barrier(bar, err, a.wait_ns)) return;
         // exchange B: the next pass's labels (loaded whether or not there is one), its counts
         // and this pass's change count; then the loop decision, taken alike in every CTA
         // (iterate.cu's assign pass)
@@ -394,8 +399,10 @@ cudaError_t configure_fused_fit(int smem_optin) {
 size_t fused_xchg_words(int num_sms, int k) { return 32 + (size_t)num_sms * (k + 1); }
 
 cudaError_t launch_fused_fit(const PassBuffers& b, double* zpart, unsigned* xchg, int num_sms, int smem_optin,
-                             cudaStream_t s) {
+                             cudaStream_t s, int stall_ms) {
     FusedArgs a;
+    a.stall = stall_ms > 0 ? 1 : 0;
+    a.wait_ns = stall_ms > 0 ? (unsigned long long)stall_ms * 1000000ull : tc::kWaitLimitNs;
     a.K = static_cast<const float*>(b.K);
     a.ldk = b.ldk;
     a.kdiag = b.kdiag;

@@ -39,7 +39,7 @@ __device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ inline bool grid_barrier(unsigned* bar, int* err) {
+__device__ inline bool grid_barrier(unsigned* bar, int* err, unsigned long long limit_ns = tc::kWaitLimitNs) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -52,7 +52,7 @@ __device__ inline bool grid_barrier(unsigned* bar, int* err) {
             unsigned spins = 0;
             while ((int)(ld_acquire(bar) - target) < 0) {
                 if ((++spins & 63u) == 0u) {
-                    if (*verr || tc::globaltimer() - t0 > tc::kWaitLimitNs) {
+                    if (*verr || tc::globaltimer() - t0 > limit_ns) {
                         if (!*verr) atomicExch(err, 1);
                         ok = 0;
                         break;

@@ -244,8 +244,10 @@ bool fused_fit_applies(int n, int k, int num_sms, int smem_optin);
 size_t fused_fit_smem(int n, int k, int num_sms, int64_t ldk, int cache_k);
 size_t fused_xchg_words(int num_sms, int k);
 cudaError_t configure_fused_fit(int smem_optin);
+// stall_ms > 0 (error-path tests only): CTA 0 leaves before the first grid barrier and every
+// barrier wait gives up after stall_ms, so the fit reports a timed-out wait.
 cudaError_t launch_fused_fit(const struct PassBuffers& b, double* zpart, unsigned* xchg, int num_sms, int smem_optin,
-                             cudaStream_t s);
+                             cudaStream_t s, int stall_ms = 0);
 
 // ---- K-means++ seeding (seeding.cu) --------------------------------------------
 // One cooperative launch (one CTA per SM) for all k steps; kappa in FP64 from the points.

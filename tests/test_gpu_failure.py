@@ -7,7 +7,8 @@ returns, and the host reports POPCORN_ERR_TIMEOUT.  These tests make such a wait
 on purpose through the library's test hook: POPCORN_TEST_SYM_STALL_MS=<ms> makes the first
 symmetric-stream launch of a fit (or the first tensor-core K stream of a batched fit) leave
 one block's copies out (nothing ever arrives on that block's barrier) with every wait of the
-launch bounded by <ms>.  Nothing faults or
+launch bounded by <ms>; in the one-launch fit it makes one CTA leave before its first grid
+barrier, so the others' bounded barrier waits run out.  Nothing faults or
 hangs: the kernel returns, the call fails with the timeout status, and the next call on
 the same context gives the reference result.  The other host-side failure paths (an
 allocation the device cannot satisfy, a label out of range) are in test_gpu_parity.py.
@@ -96,3 +97,27 @@ def test_batched_tensor_core_stream_wait_timeout(pc, monkeypatch):
     for t in range(len(wls)):
         assert torch.equal(again["labels"][t], ref["labels"][t])
         assert again["objectives"][t] == ref["objectives"][t]
+
+
+def test_grid_barrier_timeout_in_the_one_launch_fit(pc, monkeypatch):
+    """The one-launch fit (K in L2, the automatic choice at this size): CTA 0 leaves before
+    its first grid barrier, the other CTAs' bounded barrier waits run out, the fit reports
+    POPCORN_ERR_TIMEOUT, and the next fit on the same context is the reference one."""
+    wl = synth.workload("blobs")
+    P = torch.from_numpy(wl.P).cuda()
+    lab = torch.from_numpy(wl.init_labels).cuda()
+    kw = dict(max_iter=10, check_convergence=False, history=True)
+    ref = pc.popcorn_fit(P, wl.k, wl.kernel, lab, **kw)
+    assert ref["info"]["k_pass_used"] == 3
+    monkeypatch.setenv("POPCORN_TEST_SYM_STALL_MS", "200")
+    t0 = time.perf_counter()
+    with pytest.raises(pc.PopcornError) as ei:
+        pc.popcorn_fit(P, wl.k, wl.kernel, lab, **kw)
+    assert ei.value.status == 4, str(ei.value)          # POPCORN_ERR_TIMEOUT
+    assert "grid barrier" in str(ei.value)
+    assert time.perf_counter() - t0 < 60
+    monkeypatch.delenv("POPCORN_TEST_SYM_STALL_MS")
+    torch.cuda.synchronize()
+    again = pc.popcorn_fit(P, wl.k, wl.kernel, lab, **kw)
+    assert torch.equal(again["labels"], ref["labels"])
+    assert again["info"]["J_history"] == ref["info"]["J_history"]
