@@ -25,6 +25,7 @@
 
 #include <type_traits>
 
+#include "half_common.cuh"
 #include "popcorn_internal.cuh"
 #include "tc_common.cuh"
 
@@ -49,21 +50,8 @@ __device__ __forceinline__ int inst_of(const BatchInst* I, int count, long long 
     return lo;
 }
 
-template <typename TH>
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
-    if constexpr (std::is_same<TH, __half>::value) {
-        const __half2 h = __floats2half2_rn(a, b);
-        return *reinterpret_cast<const uint32_t*>(&h);
-    } else {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<const uint32_t*>(&h);
-    }
-}
-template <typename TH>
-__device__ __forceinline__ float round_trip(float a) {
-    if constexpr (std::is_same<TH, __half>::value) return __half2float(__float2half_rn(a));
-    else return __bfloat162float(__float2bfloat16_rn(a));
-}
+using hstore::pack2;
+using hstore::round_trip;
 
 // One tile of one instance's square, a 64-column box at a time: the FP32 rows (row-major,
 // ldk) into shared memory, then each 32-bit word of the box (row (w >> 5), columns

@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "half_common.cuh"
 #include "popcorn_internal.cuh"
 
 namespace popcorn {
@@ -21,26 +22,8 @@ namespace {
 
 constexpr int kPackThreads = 256;
 
-template <typename TH>
-__device__ __forceinline__ uint32_t pack2(float a, float b);
-template <>
-__device__ __forceinline__ uint32_t pack2<__half>(float a, float b) {
-    const __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<const uint32_t*>(&h);
-}
-template <>
-__device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, float b) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t*>(&h);
-}
-template <typename TH>
-__device__ __forceinline__ float round_trip(float a);
-template <>
-__device__ __forceinline__ float round_trip<__half>(float a) { return __half2float(__float2half_rn(a)); }
-template <>
-__device__ __forceinline__ float round_trip<__nv_bfloat16>(float a) {
-    return __bfloat162float(__float2bfloat16_rn(a));
-}
+using hstore::pack2;
+using hstore::round_trip;
 
 // element (r, C) of an FP32 tile in the XOR-32 layout, in floats
 __device__ __forceinline__ int sw4(int r, int C) { return 4096 * (C >> 5) + 32 * r + ((C & 31) ^ (r & 31)); }
