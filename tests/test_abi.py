@@ -99,6 +99,21 @@ def test_invalid_arguments_rejected_before_any_cuda_call(pc):
     assert fit(opt=ctypes.byref(badp)) == 1                      # k_pass must be 0 (auto), 1 or 2
     badpad = pc._Options(0, 1, 1, 0, 0, 0, 0, 9, (ctypes.c_int64 * 4)())
     assert fit(opt=ctypes.byref(badpad)) == 1                    # sym_tile must be in [0, 8]
+    # batched mode: its options are checked before any CUDA call too
+    inst = (pc._Instance * 1)()
+    inst[0] = pc._Instance(P.ctypes.data, 10, 2, 2, 2, kern, lab.ctypes.data, out.ctypes.data)
+    objs = (ctypes.c_double * 1)()
+    itsb = (ctypes.c_int32 * 1)()
+
+    def batched(opt, count=1, max_iter=5):
+        return lib.popcorn_fit_batched(count, inst, max_iter, 0.0, opt, objs, itsb, None, None)
+
+    assert batched(ctypes.byref(badks)) == 1                     # unknown K storage type
+    assert batched(ctypes.byref(bad)) == 1                       # reserved must be zero
+    assert batched(ctypes.byref(rec)) == 5                       # batched mode stores K
+    assert batched(ctypes.byref(fp8k)) == 5                      # FP8 is the recompute path's only
+    assert batched(None, count=0) == 1
+    assert batched(None, max_iter=-1) == 1
     # kernel matrix: ldk must be a multiple of 4 and >= n
     st = lib.popcorn_kernel_matrix(P.ctypes.data, 10, 2, 2, kern, 0, out.ctypes.data, 10, out.ctypes.data, None)
     assert st == 1
