@@ -122,21 +122,26 @@ typedef struct {
                                    default): the symmetric read below for n >= 8192 (where K
                                    outgrows L2 and reading half of it pays; measured faster
                                    on GB300 for every k up to 32), and at every n for an
-                                   FP16 / BF16 K from a BF16 / BF16X3 build (that build
-                                   writes only the packed triangle); else the full square.
+                                   FP16 / BF16 K from a BF16 / BF16X3 build; else the full
+                                   square.
                                    1 = symmetric (k <= 32; larger k falls back to the full
                                    square): only the 128 x 128 blocks on and above the
                                    diagonal (K is symmetric, and is then stored as that packed
-                                   triangle; an FP16 / BF16 K is built in FP32, then rounded
-                                   into the triangle by one more launch); a block's row
-                                   sums serve its rows and its column sums its columns' rows.
-                                   Blocks are taken in super-tiles of a x a (sym_tile below),
-                                   each block's labels sorted once a pass; each super-tile
-                                   writes one slot per row it touches, and the slots are
-                                   folded, so a pass reads half of K plus about
+                                   triangle; an FP16 / BF16 K is written as half tiles by a
+                                   BF16 / BF16X3 build, or rounded from the FP32 build's
+                                   triangle by one more launch); a block's row sums serve its
+                                   rows and its column sums its columns' rows.  Blocks are
+                                   taken in super-tiles of a x a (sym_tile below), largest
+                                   first; an FP32 K's pass sorts each block's labels once
+                                   (CUDA cores), an FP16 / BF16 K's pass takes each block's
+                                   sums as MMAs against one-hot label operands (tensor cores);
+                                   each super-tile writes one slot per row it touches, and
+                                   the slots are folded, so a pass reads half of K plus about
                                    8 k n ceil(n / 128a) bytes of slots.  2 = the full square,
-                                   row by row (the paper's read of K).  The recompute path has
-                                   its own scheme.  Results differ only by summation order  */
+                                   row by row (the paper's read of K; an FP16 / BF16 K on the
+                                   tensor cores as described under k_storage).  The recompute
+                                   path has its own scheme.  Results differ only by summation
+                                   order                                                     */
     int32_t sym_tile;           /* super-tile edge a of the symmetric pass, in 128-blocks,
                                    0..8: 0 = automatic (4 for k <= 16 and 3 for k <= 32,
                                    narrowed until there are at least 8 super-tiles per SM);
