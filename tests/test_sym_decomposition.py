@@ -376,3 +376,54 @@ def test_batched_build_half_tile_and_transpose_stores():
             for e in range(16):
                 a = _kmajor_sw128(start, m, 16 * (kk & 3) + e)
                 assert trans[a] == (16 * kk + e, m)   # operand (row m, column 16 kk + e) = K[16 kk + e][m]
+
+
+# ---------------------------------------------------------------- the z reduction's in-block sort
+
+def _block_sort_positions(labels, k, nw=32):
+    """zreduce_body's placement of a block's rows, step by step: each warp's rank of a row
+    among its earlier lanes with the same label (match + popcount), the per-warp counts, the
+    cluster starts (a scan over clusters of the warps' totals), each warp's offset inside its
+    cluster (a scan over warps), and the position offset + rank.  -1 labels (rows past n) are
+    not placed."""
+    rows = len(labels)
+    cnt = np.zeros((nw, k), dtype=np.int64)
+    rank = np.zeros(rows, dtype=np.int64)
+    for w in range(nw):
+        for lane in range(32):
+            i = 32 * w + lane
+            if i >= rows or labels[i] < 0:
+                continue
+            rank[i] = sum(1 for l2 in range(lane) if labels[32 * w + l2] == labels[i])
+            cnt[w, labels[i]] += 1
+    totals = cnt.sum(axis=0)
+    cstart = np.concatenate([[0], np.cumsum(totals)])
+    off = np.zeros((nw, k), dtype=np.int64)
+    for c in range(k):
+        o = cstart[c]
+        for w in range(nw):
+            off[w, c] = o
+            o += cnt[w, c]
+    pos = np.full(rows, -1)
+    for i in range(rows):
+        if labels[i] >= 0:
+            pos[i] = off[i // 32, labels[i]] + rank[i]
+    return pos, cstart
+
+
+@pytest.mark.parametrize("k,valid,seed", [(10, 1024, 0), (1, 1024, 1), (64, 1000, 2), (256, 777, 3), (3, 5, 4)])
+def test_zreduce_block_sort_is_a_stable_counting_sort(k, valid, seed):
+    rng = np.random.default_rng(seed)
+    labels = np.full(1024, -1)
+    labels[:valid] = rng.integers(0, k, size=valid)
+    if k > 2:
+        labels[:valid][labels[:valid] == 1] = 0          # an empty cluster
+    pos, cstart = _block_sort_positions(labels, k)
+    placed = pos[pos >= 0]
+    assert sorted(placed.tolist()) == list(range(valid))  # a permutation of the valid rows
+    order = np.argsort(pos[:valid], kind="stable")
+    expect = np.argsort(labels[:valid], kind="stable")    # by label, row order kept among equals
+    np.testing.assert_array_equal(order, expect)
+    for c in range(k):                                     # each cluster's rows sit in its range
+        idx = np.nonzero(labels[:valid] == c)[0]
+        assert np.all((pos[idx] >= cstart[c]) & (pos[idx] < cstart[c + 1]))
